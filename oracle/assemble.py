@@ -1,0 +1,219 @@
+"""Assembly, preconditioner and solvers for the Riesz maps (Eq. (2.8), Sections 6-7).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+* Element matrices are computed by quadrature of the reference basis under
+  the pullbacks of Eq. (2.7) (not through precomputed geometric factors):
+  A_T[i, j] = sum_q w_q |det J| (beta v_i . v_j + alpha d v_i . d v_j) with
+  v = pullback of the reference function at the mapped quadrature point.
+* The preconditioner is the interior/interface splitting of Eq. (6.11) read
+  as one-level additive Schwarz: P^{-1} = D_II^{-1} (+) sum_V R_V^T A_V^{-1} R_V,
+  A_V the assembled matrix restricted to the patch of vertex V, factorised by
+  dense Cholesky.  (The paper's W^k coarse space and multiplicative hybrid
+  weighting, Section 7.1, are not part of this reading.)
+* PCG (Section 7.1) from x0 = 0, stopped when the true relative residual
+  ||b - A x||_2 / ||b||_2 <= rtol.
+"""
+import numpy as np
+import scipy.linalg
+import scipy.sparse
+import scipy.sparse.linalg
+
+from .polys import REF_VERTS, quadrature
+
+
+def jacobians(verts, cells):
+    """J_T (nc, 3, 3) of the affine maps from the reference tetrahedron to sorted cells."""
+    cells = np.sort(cells, axis=1)
+    X = verts[cells]  # (nc, 4, 3)
+    Ep = np.stack([X[:, 1] - X[:, 0], X[:, 2] - X[:, 0], X[:, 3] - X[:, 0]], 2)
+    V = REF_VERTS[3]
+    Er = np.stack([V[1] - V[0], V[2] - V[0], V[3] - V[0]], 1)
+    J = Ep @ np.linalg.inv(Er)
+    return J, X[:, 0]
+
+
+def physical_tabulation(ref, J, vhat, dhat):
+    """Pullbacks (Eq. (2.7)) of reference values/derivatives for every cell.
+
+    vhat (npt, n, ncomp), dhat (npt, n, dcomp) -> v (nc, npt, n, ncomp), d (nc, npt, n, dcomp)
+    """
+    det = np.linalg.det(J)
+    if ref.k == 0:
+        v = np.broadcast_to(vhat[None], (J.shape[0],) + vhat.shape)
+        JiT = np.linalg.inv(J).transpose(0, 2, 1)
+        d = np.einsum("cab,pnb->cpna", JiT, dhat)
+    elif ref.k == 1:
+        JiT = np.linalg.inv(J).transpose(0, 2, 1)
+        v = np.einsum("cab,pnb->cpna", JiT, vhat)
+        d = np.einsum("cab,pnb->cpna", J, dhat) / det[:, None, None, None]
+    else:
+        v = np.einsum("cab,pnb->cpna", J, vhat) / det[:, None, None, None]
+        d = dhat[None] / det[:, None, None, None]
+    return v, d, det
+
+
+def element_matrices(ref, verts, cells, alpha=1.0, beta=1.0, chunk=256):
+    """A_T for every cell by quadrature, (nc, n_ref, n_ref)."""
+    X, w = quadrature(3, ref.p + 2)
+    vhat, dhat = ref.tabulate(X)
+    J, _ = jacobians(verts, cells)
+    nc = J.shape[0]
+    out = np.zeros((nc, ref.ndofs, ref.ndofs))
+    for s in range(0, nc, chunk):
+        v, d, det = physical_tabulation(ref, J[s:s + chunk], vhat, dhat)
+        wq = w[None, :] * np.abs(det)[:, None]
+        out[s:s + chunk] = (beta * np.einsum("epia,epja,ep->eij", v, v, wq)
+                            + alpha * np.einsum("epia,epja,ep->eij", d, d, wq))
+    return out
+
+
+def assemble(md, Ae):
+    """Global CSR matrix from element matrices and the cell DOF map."""
+    nc, n, _ = Ae.shape
+    rows = np.repeat(md.cell_dofs, n, axis=1).ravel()
+    cols = np.tile(md.cell_dofs, (1, n)).ravel()
+    A = scipy.sparse.coo_matrix((Ae.ravel(), (rows, cols)), shape=(md.ndofs, md.ndofs))
+    return A.tocsr()
+
+
+def load_cg_field(ref, md, ref_cg, md_cg, fcoef):
+    """b_i = (f, phi_i) for f with components in the CG_p space of the same mesh.
+
+    fcoef: (ncomp_f, N_CG) global coefficients of each Cartesian component of f
+    in the paper's CG_p basis (a scalar space takes one component).
+    """
+    X, w = quadrature(3, ref.p + 2)
+    vhat, dhat = ref.tabulate(X)
+    chat, _ = ref_cg.tabulate(X)  # (npt, n_cg, 1)
+    J, _ = jacobians(md.verts, md.cells)
+    v, _, det = physical_tabulation(ref, J, vhat, dhat)
+    fq = np.einsum("pa,mea->epm", chat[:, :, 0], fcoef[:, md_cg.cell_dofs])  # (nc, npt, ncomp)
+    be = np.einsum("epm,epim,p,e->ei", fq, v, w, np.abs(det))
+    b = np.zeros(md.ndofs)
+    np.add.at(b, md.cell_dofs, be)
+    return b
+
+
+def load_function(ref, md, f, df=None, alpha=1.0, beta=1.0):
+    """b_i = a(u, phi_i) (df given) or (f, phi_i) for a function of physical x.
+
+    f(x) -> (npt, ncomp); df(x) -> (npt, dcomp) the exterior derivative of f.
+    """
+    X, w = quadrature(3, ref.p + 3)
+    vhat, dhat = ref.tabulate(X)
+    J, x0 = jacobians(md.verts, md.cells)
+    V = REF_VERTS[3]
+    xq = x0[:, None, :] + np.einsum("cab,pb->cpa", J, X - V[0][None, :])
+    v, d, det = physical_tabulation(ref, J, vhat, dhat)
+    nc, npt = xq.shape[:2]
+    fx = f(xq.reshape(-1, 3)).reshape(nc, npt, -1)
+    be = beta * np.einsum("epm,epim,p,e->ei", fx, v, w, np.abs(det))
+    if df is not None:
+        dx = df(xq.reshape(-1, 3)).reshape(nc, npt, -1)
+        be += alpha * np.einsum("epm,epim,p,e->ei", dx, d, w, np.abs(det))
+    b = np.zeros(md.ndofs)
+    np.add.at(b, md.cell_dofs, be)
+    return b
+
+
+def evaluate(ref, md, x, Xref):
+    """Values of the finite element function with coefficients x at mapped reference points."""
+    vhat, dhat = ref.tabulate(Xref)
+    J, x0 = jacobians(md.verts, md.cells)
+    v, _, _ = physical_tabulation(ref, J, vhat, dhat)
+    V = REF_VERTS[3]
+    xq = x0[:, None, :] + np.einsum("cab,pb->cpa", J, Xref - V[0][None, :])
+    return xq, np.einsum("epia,ei->epa", v, x[md.cell_dofs])
+
+
+class Preconditioner:
+    """P^{-1} = D_II^{-1} (+) sum_V R_V^T A_V^{-1} R_V (Eq. (6.11), one-level additive)."""
+
+    def __init__(self, A, md, patches=None):
+        self.N = A.shape[0]
+        self.n_interface = md.n_interface
+        d = A.diagonal()
+        self.dinv_I = 1.0 / d[md.n_interface:]
+        self.patches = md.patches() if patches is None else patches
+        self.factors = []
+        A = A.tocsr()
+        for idx in self.patches:
+            if len(idx) == 0:
+                self.factors.append(None)
+                continue
+            AV = A[idx][:, idx].toarray()
+            self.factors.append(scipy.linalg.cho_factor(AV, lower=True))
+
+    def apply(self, r):
+        z = np.zeros_like(r)
+        z[self.n_interface:] = self.dinv_I * r[self.n_interface:]
+        for idx, fac in zip(self.patches, self.factors):
+            if fac is not None:
+                z[idx] += scipy.linalg.cho_solve(fac, r[idx])
+        return z
+
+    def dense(self):
+        """The explicit matrix P^{-1} (small problems only)."""
+        I = np.eye(self.N)
+        return np.stack([self.apply(I[:, j]) for j in range(self.N)], 1)
+
+
+def pcg(A, b, M=None, rtol=1e-8, maxit=1000):
+    """PCG from x0 = 0; stops on the true relative residual.  Returns (x, iters, relres)."""
+    nb = np.linalg.norm(b)
+    x = np.zeros_like(b)
+    if nb == 0:
+        return x, 0, 0.0
+    r = b.copy()
+    z = M(r) if M is not None else r.copy()
+    p = z.copy()
+    rz = r @ z
+    it = 0
+    while it < maxit:
+        Ap = A @ p
+        a = rz / (p @ Ap)
+        x += a * p
+        r -= a * Ap
+        it += 1
+        if np.linalg.norm(r) <= rtol * nb:
+            rt = b - A @ x
+            if np.linalg.norm(rt) <= rtol * nb:
+                break
+            r = rt
+        z = M(r) if M is not None else r.copy()
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, it, np.linalg.norm(b - A @ x) / nb
+
+
+def direct_solve(A, b):
+    """Sparse direct solve (SuperLU)."""
+    return scipy.sparse.linalg.splu(A.tocsc()).solve(b)
+
+
+def mixed_matrix(ref_test, md_test, ref_trial, md_trial):
+    """B[i, j] = (d phi^trial_j, phi^test_i) on a mesh shared by both spaces.
+
+    Used to check that d maps one space of the complex into the next (Eq. (5.3)).
+    """
+    X, w = quadrature(3, max(ref_test.p, ref_trial.p) + 2)
+    vt, dt = ref_test.tabulate(X)
+    vr, dr = ref_trial.tabulate(X)
+    J, _ = jacobians(md_test.verts, md_test.cells)
+    v_te, _, det = physical_tabulation(ref_test, J, vt, dt)
+    _, d_tr, _ = physical_tabulation(ref_trial, J, vr, dr)
+    Be = np.einsum("epia,epja,p,e->eij", v_te, d_tr, w, np.abs(det))
+    nc, n, m = Be.shape
+    rows = np.repeat(md_test.cell_dofs, m, axis=1).ravel()
+    cols = np.tile(md_trial.cell_dofs, (1, n)).ravel()
+    B = scipy.sparse.coo_matrix((Be.ravel(), (rows, cols)), shape=(md_test.ndofs, md_trial.ndofs))
+    return B.tocsr()
+
+
+def mass_and_stiffness(ref, md):
+    """Global mass and d-stiffness matrices separately (beta, alpha parts of Eq. (2.8))."""
+    M = assemble(md, element_matrices(ref, md.verts, md.cells, alpha=0.0, beta=1.0))
+    K = assemble(md, element_matrices(ref, md.verts, md.cells, alpha=1.0, beta=0.0))
+    return M, K

@@ -1,0 +1,217 @@
+"""Pins of the oracle's assembly, preconditioner and solvers."""
+import numpy as np
+import pytest
+import scipy.sparse
+
+from oracle import assemble as asm
+from oracle.mesh import MeshDofs
+from oracle.polys import REF_VERTS, quadrature
+from oracle.refelem import reference_element, eigenbasis
+from paper_2506_17406_gb300.inputs import kuhn_mesh, normal_coeffs, normal_vector
+
+
+def _poly(deg, ncomp, seed):
+    """Random polynomial field of total degree <= deg in physical coordinates (value, jacobian)."""
+    exps = [(a, b, c) for a in range(deg + 1) for b in range(deg + 1 - a)
+            for c in range(deg + 1 - a - b)]
+    C = normal_coeffs((ncomp, len(exps)), seed)
+
+    def val(x):
+        return np.stack([sum(C[m, k] * x[:, 0] ** a * x[:, 1] ** b * x[:, 2] ** c
+                             for k, (a, b, c) in enumerate(exps)) for m in range(ncomp)], 1)
+
+    def jac(x):
+        J = np.zeros((x.shape[0], ncomp, 3))
+        for m in range(ncomp):
+            for k, (a, b, c) in enumerate(exps):
+                if a:
+                    J[:, m, 0] += C[m, k] * a * x[:, 0] ** (a - 1) * x[:, 1] ** b * x[:, 2] ** c
+                if b:
+                    J[:, m, 1] += C[m, k] * b * x[:, 0] ** a * x[:, 1] ** (b - 1) * x[:, 2] ** c
+                if c:
+                    J[:, m, 2] += C[m, k] * c * x[:, 0] ** a * x[:, 1] ** b * x[:, 2] ** (c - 1)
+        return J
+    return val, jac
+
+
+@pytest.mark.parametrize("space,p", [("CG", 3), ("CG", 4), ("N1curl", 3), ("RT", 3)])
+def test_manufactured_solution_reproduced(space, p):
+    """u in V_h solves the discrete problem exactly: CG_p contains P_p, N1curl_p and RT_p contain P_{p-1}^3."""
+    ref = reference_element(space, p)
+    v, c = kuhn_mesh(2, 0.1, 7)
+    md = MeshDofs(v, c, ref)
+    if space == "CG":
+        val, jac = _poly(p, 1, 11)
+        du = lambda x: jac(x)[:, 0, :]
+    else:
+        val, jac = _poly(p - 1, 3, 12)
+        if space == "N1curl":
+            du = lambda x: np.stack([jac(x)[:, 2, 1] - jac(x)[:, 1, 2], jac(x)[:, 0, 2] - jac(x)[:, 2, 0],
+                                     jac(x)[:, 1, 0] - jac(x)[:, 0, 1]], 1)
+        else:
+            du = lambda x: np.trace(jac(x), axis1=1, axis2=2)[:, None]
+    A = asm.assemble(md, asm.element_matrices(ref, v, c))
+    b = asm.load_function(ref, md, val, du)
+    x = asm.direct_solve(A, b)
+    Xr, _ = quadrature(3, 3)
+    xq, uh = asm.evaluate(ref, md, x, Xr)
+    ue = val(xq.reshape(-1, 3)).reshape(uh.shape)
+    assert np.abs(uh - ue).max() < 1e-9 * np.abs(ue).max()
+
+
+def _dense(md, Ae):
+    A = np.zeros((md.ndofs, md.ndofs))
+    for e in range(md.cells.shape[0]):
+        A[np.ix_(md.cell_dofs[e], md.cell_dofs[e])] += Ae[e]
+    return A
+
+
+@pytest.mark.parametrize("ncell", [1, 2])
+@pytest.mark.parametrize("space,p", [("CG", 3), ("N1curl", 2), ("RT", 3)])
+def test_brute_force_dense_one_and_two_tets(ncell, space, p):
+    """Dense numpy.linalg.solve on 1- and 2-tet meshes vs the sparse direct solve and PCG."""
+    ref = reference_element(space, p)
+    rng = np.random.Generator(np.random.PCG64(5))
+    if ncell == 1:
+        v = rng.standard_normal((4, 3))
+        c = np.array([[0, 1, 2, 3]])
+    else:
+        v = rng.standard_normal((5, 3))
+        c = np.array([[0, 1, 2, 3], [1, 2, 3, 4]])
+    md = MeshDofs(v, c, ref)
+    Ae = asm.element_matrices(ref, v, c)
+    Ad = _dense(md, Ae)
+    As = asm.assemble(md, Ae)
+    assert np.abs(As.toarray() - Ad).max() < 1e-12 * np.abs(Ad).max()
+    b = normal_vector(md.ndofs, 3)
+    xd = np.linalg.solve(Ad, b)
+    assert np.linalg.norm(asm.direct_solve(As, b) - xd) < 1e-10 * np.linalg.norm(xd)
+    P = asm.Preconditioner(As, md)
+    xp, it, rr = asm.pcg(As, b, P.apply, rtol=1e-12, maxit=500)
+    assert rr <= 1e-12
+    assert np.linalg.norm(xp - xd) < 1e-8 * np.linalg.norm(xd)
+
+
+def test_global_complex_d_of_d_is_zero():
+    """Eq. (5.3): grad CG_p = [signed incidence | identity] in N1curl_p, and curl grad = 0,
+    curl N1curl_p lies in RT_p with div curl = 0 (the global bases are conforming)."""
+    p = 3
+    v, c = kuhn_mesh(2, 0.1, 9)
+    cg, ned, rt = (reference_element(s, p) for s in ("CG", "N1curl", "RT"))
+    mcg, mned, mrt = MeshDofs(v, c, cg), MeshDofs(v, c, ned), MeshDofs(v, c, rt)
+    Mn, Kn = asm.mass_and_stiffness(ned, mned)
+    Mr, Kr = asm.mass_and_stiffness(rt, mrt)
+    _, Kc = asm.mass_and_stiffness(cg, mcg)
+    B = asm.mixed_matrix(ned, mned, cg, mcg).toarray()
+    G = np.linalg.solve(Mn.toarray(), B)
+    # exact representation: ||grad phi_j - P grad phi_j||^2 = K_cg[j,j] - b_j . G_j
+    resid = Kc.diagonal() - np.einsum("ij,ij->j", B, G)
+    assert np.abs(resid).max() < 1e-10 * Kc.diagonal().max()
+    # structure: vertex columns = signed edge incidence on the Whitney DOFs, others unit vectors
+    Gexp = np.zeros_like(G)
+    ne_d = mned.per_entity[1]
+    for e, (a, b) in enumerate(mned.edges):
+        Gexp[ne_d * e, a] = -1.0
+        Gexp[ne_d * e, b] = 1.0
+        for m in range(1, ne_d):
+            Gexp[ne_d * e + m, mcg.nverts + (ne_d - 1) * e + m - 1] = 1.0
+    nfI = mned.per_entity[2] - mcg.per_entity[2]
+    for f in range(len(mned.faces)):
+        for m in range(mcg.per_entity[2]):
+            Gexp[mned._offsets[2] + mned.per_entity[2] * f + nfI + m,
+                 mcg._offsets[2] + mcg.per_entity[2] * f + m] = 1.0
+    assert np.abs(G - Gexp).max() < 1e-10
+    assert np.abs(Kn @ G).max() < 1e-10
+    Bc = asm.mixed_matrix(rt, mrt, ned, mned).toarray()
+    C = np.linalg.solve(Mr.toarray(), Bc)
+    resid = Kn.diagonal() - np.einsum("ij,ij->j", Bc, C)
+    assert np.abs(resid).max() < 1e-10 * Kn.diagonal().max()
+    assert np.abs(Kr @ C).max() < 1e-9
+    assert np.abs(C @ G).max() < 1e-10
+
+
+def test_preconditioner_reduces_to_jacobi_at_lowest_order():
+    """CG_1: every vertex patch holds one DOF, so P^{-1} = diag(A)^{-1}."""
+    ref = reference_element("CG", 1)
+    v, c = kuhn_mesh(3, 0.1, 2)
+    md = MeshDofs(v, c, ref)
+    A = asm.assemble(md, asm.element_matrices(ref, v, c))
+    P = asm.Preconditioner(A, md)
+    r = normal_vector(md.ndofs, 4)
+    assert np.allclose(P.apply(r), r / A.diagonal(), rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("space,p", [("CG", 5), ("N1curl", 4), ("RT", 4)])
+def test_interior_diagonal_on_reference_cell(space, p):
+    """Lemma 4.5 on the reference cell as a one-cell mesh: diag(A_II) = [lambda + 1, 1]."""
+    ref = reference_element(space, p)
+    v = REF_VERTS[3].copy()
+    c = np.array([[0, 1, 2, 3]])
+    md = MeshDofs(v, c, ref)
+    A = asm.assemble(md, asm.element_matrices(ref, v, c)).toarray()
+    fam = {"CG": "CG", "N1curl": "N1", "RT": "RT"}[space]
+    lam = eigenbasis(fam, p, 3)[2]
+    d = np.diag(A)[md.n_interface:]
+    exp = np.ones(len(d))
+    exp[:len(lam)] = lam + 1.0
+    assert np.abs(d - exp).max() < 1e-12
+    AII = A[md.n_interface:, md.n_interface:]
+    assert np.abs(AII - np.diag(np.diag(AII))).max() < 1e-12
+
+
+def test_patch_matrices_from_cells_equal_global_restriction():
+    """A_V assembled cell by cell over the star equals A restricted to the patch."""
+    ref = reference_element("N1curl", 2)
+    v, c = kuhn_mesh(2, 0.1, 4)
+    md = MeshDofs(v, c, ref)
+    Ae = asm.element_matrices(ref, v, c)
+    A = asm.assemble(md, Ae)
+    for vi, idx in enumerate(md.patches()):
+        pos = {g: k for k, g in enumerate(idx)}
+        AV = np.zeros((len(idx), len(idx)))
+        _, _, cells = md.vertex_star(vi)
+        for e in cells:
+            loc = [j for j in range(ref.ndofs) if md.cell_dofs[e, j] in pos]
+            gl = [pos[md.cell_dofs[e, j]] for j in loc]
+            AV[np.ix_(gl, gl)] += Ae[e][np.ix_(loc, loc)]
+        assert np.abs(AV - A[idx][:, idx].toarray()).max() < 1e-12 * np.abs(AV).max()
+
+
+@pytest.mark.parametrize("space,p", [("CG", 2), ("N1curl", 2), ("RT", 2)])
+def test_additive_schwarz_spectrum(space, p):
+    """P^{-1} A is similar to an SPD matrix with eigenvalues in (0, 4 + max_T lambda_max(D_T^{-1} A_T,II)]:
+    at most four vertex patches meet on a cell (Section 6, additive Schwarz theory)."""
+    ref = reference_element(space, p)
+    v, c = kuhn_mesh(2, 0.1, 6)
+    md = MeshDofs(v, c, ref)
+    Ae = asm.element_matrices(ref, v, c)
+    A = asm.assemble(md, Ae).toarray()
+    P = asm.Preconditioner(scipy.sparse.csr_matrix(A), md).dense()
+    ev = np.linalg.eigvals(P @ A)
+    assert np.abs(ev.imag).max() < 1e-8
+    I = ref.interior
+    jac = 1.0
+    if I:
+        dI = np.diag(A)[md.n_interface:]
+        for e in range(len(c)):
+            ae = Ae[e][np.ix_(I, I)]
+            de = dI[md.cell_dofs[e, I] - md.n_interface]
+            jac = max(jac, np.linalg.eigvalsh(ae / np.sqrt(np.outer(de, de))).max())
+    assert ev.real.min() > 0
+    assert ev.real.max() <= 4 + jac + 1e-10
+
+
+def test_cg_field_load_matches_function_load():
+    """(f, phi_i) for f in [CG_p]^3 via CG coefficients equals quadrature of the same polynomial."""
+    p = 2
+    v, c = kuhn_mesh(2)  # unperturbed: CG_p interpolates the polynomial exactly
+    ned, cg = reference_element("N1curl", p), reference_element("CG", p)
+    mned, mcg = MeshDofs(v, c, ned), MeshDofs(v, c, cg)
+    val, _ = _poly(1, 3, 21)
+    # CG_p coefficients of a linear field: vertex DOFs are point values, higher DOFs of a
+    # linear function vanish (Lemma 4.1: the vertex functions are the P1 hat functions)
+    f = np.zeros((3, mcg.ndofs))
+    f[:, :mcg.nverts] = val(v).T
+    b1 = asm.load_cg_field(ned, mned, cg, mcg, f)
+    b2 = asm.load_function(ned, mned, val)
+    assert np.abs(b1 - b2).max() < 1e-12 * np.abs(b2).max()
