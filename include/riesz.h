@@ -1,0 +1,170 @@
+/*
+ * riesz.h -- C ABI of the GB300 (sm_103a) solver for the high-order Riesz maps
+ * of the de Rham complex, after Brubeck, Farrell, Kirby & Parker, "Fast solvers
+ * for the high-order FEM simplicial de Rham complex" (arXiv 2506.17406).
+ *
+ * Problem (Eq. (2.8) with alpha = beta = 1, pure Neumann, Section 7.1): find u
+ * in V with (u, v) + (d u, d v) = (f, v) for all v in V, V one of
+ *   RIESZ_H1    CG_p     (d = grad),  Eq. (2.5), k = 0
+ *   RIESZ_HCURL Ned1_p   (d = curl),  Eq. (2.5), k = 1
+ *   RIESZ_HDIV  RT_p     (d = div),   Eq. (2.5), k = 2
+ * on an affine tetrahedral mesh, in the paper's orthogonality-promoting basis
+ * (Sections 3-4: the dual basis of the DOFs of Eqs. (3.14), (3.16), (3.18)).
+ *
+ * Solver: PCG (Section 7.1) preconditioned by the interior/interface splitting
+ * of Eq. (6.11), PAFW_0(X_Gamma) + J(X_I), applied additively:
+ *   P^{-1} = diag(A_II)^{-1}  (+)  sum_V R_V^T A_V^{-1} R_V,
+ * A_V the matrix restricted to the interface DOFs of the star of vertex V,
+ * factorised by dense Cholesky (Section 6.4).
+ *
+ * Global DOF layout (the numbering the paper leaves to the implementation):
+ *   [vertex DOFs | edge DOFs (edge-major) | face DOFs (face-major) |
+ *    interior DOFs (cell-major)]
+ * edges / faces are the sorted vertex pairs / triples of the mesh in
+ * lexicographic order; inside an entity Whitney, type I, type II, each in
+ * eigen order.  Every interface DOF comes before every interior DOF.
+ *
+ * Conventions for every call:
+ *   - Return value: RIESZ_OK (0) or one of the RIESZ_ERR_* codes below;
+ *     riesz_last_error() then returns a message (thread-local, valid until the
+ *     next call on the same thread).  No C++ exception crosses this boundary.
+ *   - "device" pointers are CUDA global-memory pointers on the handle's device,
+ *     owned by the caller, FP64, contiguous, right-hand sides stacked as
+ *     [nrhs][N].  "host" pointers are ordinary CPU memory owned by the caller.
+ *   - stream: a cudaStream_t cast to void*, or NULL for the legacy default
+ *     stream.  Device work is enqueued on it; calls that return host values
+ *     synchronise it.
+ *   - The handle owns its mesh maps, reference tables, factors and workspace
+ *     and frees them in riesz_destroy.  A handle is not thread-safe.
+ */
+#ifndef RIESZ_H
+#define RIESZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct riesz_handle riesz_handle;
+
+enum { RIESZ_H1 = 0, RIESZ_HCURL = 1, RIESZ_HDIV = 2 };
+
+enum {
+  RIESZ_OK = 0,
+  RIESZ_ERR_INVALID_ARG = 1,   /* bad pointer, size, space, degree or option */
+  RIESZ_ERR_BAD_MESH = 2,      /* vertex index out of range, repeated vertex, |det J| ~ 0 */
+  RIESZ_ERR_OOM = 3,           /* device allocation failed */
+  RIESZ_ERR_NOT_CONVERGED = 4, /* maxit reached; x holds the last iterate */
+  RIESZ_ERR_NONFINITE = 5,     /* NaN/Inf in the right-hand side or the recurrence */
+  RIESZ_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+  RIESZ_ERR_INTERNAL = 7,      /* e.g. a patch matrix that is not positive definite */
+  RIESZ_ERR_NO_DEVICE = 8      /* a device call on a handle without device state */
+};
+
+enum { RIESZ_PREC_FP64 = 0, RIESZ_PREC_FP32 = 1 };
+enum { RIESZ_APPLY_MATRIX_FREE = 0, RIESZ_APPLY_ELEMENT = 1 };
+
+typedef struct {
+  /* Precision of the stored patch Cholesky factors and of the triangular
+     sweeps of riesz_precond (the factorisation itself is always FP64).
+     With RIESZ_PREC_FP32 riesz_solve uses flexible (Polak-Ribiere) PCG. */
+  int precond_precision;
+  /* RIESZ_APPLY_MATRIX_FREE: y_T = sum_q g_q(T) R_q x_T with the Q reference
+     matrices (7 for H1 and H(div), 12 for H(curl)) and per-cell geometric
+     factors of the affine pullbacks (Eq. (2.7)).  RIESZ_APPLY_ELEMENT: the
+     same sum formed once per cell at setup and stored (n_ref^2 FP64 per cell),
+     so each apply reads it instead of recontracting. */
+  int apply_mode;
+  double rtol; /* target ||b - A x||_2 / ||b||_2 of riesz_solve (default 1e-8) */
+  int maxit;   /* PCG iteration cap (default 1000) */
+  int nrhs_max;/* largest nrhs passed to apply / precond / solve (default 1) */
+} riesz_opts;
+
+/* Fill *o with the defaults: FP64 preconditioner, element-matrix apply,
+   rtol 1e-8, maxit 1000, nrhs_max 1. */
+void riesz_default_opts(riesz_opts* o);
+
+/* ---- host-only calls (no GPU needed) ---------------------------------- */
+
+/* Build the reference element (Sections 3-4, host FP64, cached per (space,p))
+   and the mesh maps (entities, DOF numbering, vertex-star patches) of a mesh.
+   verts: host [nverts][3] FP64 coordinates; cells: host [ncells][4] vertex
+   indices (any order; each cell's vertices are sorted internally).
+   p: 1..10.  opts may be NULL (defaults).  *out receives a new handle. */
+int riesz_create(int space, int p, int64_t nverts, const double* verts, int64_t ncells,
+                 const int64_t* cells, const riesz_opts* opts, riesz_handle** out);
+
+/* N = total DOFs, n_interior = DOFs of cell interiors (the last n_interior). */
+int riesz_num_dofs(const riesz_handle* h, int64_t* n, int64_t* n_interior);
+
+/* info[0..7] = n_ref, interior DOFs per cell, value components, derivative
+   components, DOFs per vertex, per edge, per face, per cell interior. */
+int riesz_ref_info(const riesz_handle* h, int* info);
+
+/* cell_dofs: host [ncells][n_ref] global DOF of each local reference DOF. */
+int riesz_dof_map(const riesz_handle* h, int32_t* cell_dofs);
+
+/* offsets: host [nverts + 1]; dofs: host [offsets[nverts]] (query the size by
+   passing dofs == NULL).  Patch of vertex v = dofs[offsets[v] .. offsets[v+1]),
+   increasing global DOF indices. */
+int riesz_patch_map(const riesz_handle* h, int64_t* offsets, int32_t* dofs);
+
+/* Tabulate the reference basis of (space, p) at npts points of the reference
+   tetrahedron (edge length 2, centroid 0, vertices (-1,-1/sqrt3,-1/sqrt6),
+   (1,-1/sqrt3,-1/sqrt6), (0,2/sqrt3,-1/sqrt6), (0,0,3/sqrt6)).
+   vals: host [npts][n_ref][ncomp]; dvals: host [npts][n_ref][dcomp] (grad,
+   curl or div); either may be NULL. */
+int riesz_ref_tabulate(int space, int p, int64_t npts, const double* pts, double* vals, double* dvals);
+
+/* ---- device calls ---------------------------------------------------- */
+
+/* Upload the maps and tables to the current CUDA device and run the device
+   setup: per-cell geometric factors, interior diagonal, patch assembly and
+   batched FP64 Cholesky (Section 6.4).  Synchronises the stream. */
+int riesz_setup_device(riesz_handle* h, void* stream);
+
+/* riesz_create followed by riesz_setup_device. */
+int riesz_setup(int space, int p, int64_t nverts, const double* verts, int64_t ncells,
+                const int64_t* cells, const riesz_opts* opts, void* stream, riesz_handle** out);
+
+/* y = A x (matrix-free operator of Eq. (2.8)); x, y: device [nrhs][N]. */
+int riesz_apply(riesz_handle* h, const double* x, double* y, int nrhs, void* stream);
+
+/* z = P^{-1} r (Eq. (6.11), additive); r, z: device [nrhs][N]. */
+int riesz_precond(riesz_handle* h, const double* r, double* z, int nrhs, void* stream);
+
+/* PCG for A x = b to ||b - A x|| <= rtol ||b|| (true residual, checked at
+   exit).  x: device [nrhs][N], the initial guess on entry, the solution on
+   return.  iters, relres: host [nrhs] (may be NULL).  Synchronises. */
+int riesz_solve(riesz_handle* h, const double* b, double* x, int nrhs, void* stream, int* iters,
+                double* relres);
+
+/* riesz_solve with host buffers: b_host, x_host are host [nrhs][N]; the
+   copies to and from the device are part of the call. */
+int riesz_solve_host(riesz_handle* h, const double* b_host, double* x_host, int nrhs, void* stream,
+                     int* iters, double* relres);
+
+/* Number of DOFs of CG_p on the handle's mesh (the space of riesz_load's f). */
+int riesz_num_cg_dofs(const riesz_handle* h, int64_t* n_cg);
+
+/* b_i = (f, phi_i) for f whose Cartesian components lie in CG_p of the same
+   mesh with global coefficients fcg: device [ncomp][n_cg] (ncomp = 1 for H1,
+   3 otherwise).  b: device [N]. */
+int riesz_load(riesz_handle* h, const double* fcg, double* b, void* stream);
+
+/* Timings (ms) and sizes of the last setup / solve:
+   out[0] setup host ms, out[1] setup device ms, out[2] device bytes held,
+   out[3] patch factor bytes, out[4] last solve iterations (rhs 0),
+   out[5] kernels launched by the last riesz_solve. */
+int riesz_stats(const riesz_handle* h, double* out);
+
+int riesz_destroy(riesz_handle* h);
+
+const char* riesz_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RIESZ_H */

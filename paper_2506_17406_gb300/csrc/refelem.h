@@ -1,0 +1,54 @@
+// Host FP64 builder of the paper's orthogonality-promoting reference element
+// (arXiv 2506.17406, Sections 3-4) and of the reference tables the device
+// kernels contract against.
+#pragma once
+#include <vector>
+
+#include "linalg.h"
+
+namespace riesz {
+
+enum Space { H1 = 0, HCURL = 1, HDIV = 2 };
+
+// Orthonormal (Dubiner / PKD) polynomial expansion of total degree <= deg on
+// the equilateral reference simplex of dimension dim (edge length 2).
+struct Expansion {
+  int dim = 0, deg = 0, n = 0;
+  std::vector<double> norm;  // normalisation of each raw PKD function
+  std::vector<int> order;    // (p, q, r) triples flattened
+  Expansion() {}
+  Expansion(int dim, int deg);
+  // values[npt][n], grads[npt][n][dim]
+  void eval(int npt, const double* x, double* values, double* grads) const;
+};
+
+struct Rule {  // quadrature on a reference simplex
+  int dim = 0;
+  std::vector<double> x, w;  // x: npt*dim
+  int npt() const { return (int)w.size(); }
+};
+Rule simplex_rule(int dim, int npts_per_dir);
+
+// A reference element: the dual basis of the paper's DOFs and its tables.
+struct RefElement {
+  int space = 0, p = 0, nref = 0, ninterior = 0;
+  int ncomp = 1, dcomp = 3;  // value / exterior-derivative components
+  int per_entity[4] = {0, 0, 0, 0};  // DOFs per vertex, edge, face, interior
+  Expansion E;                       // expansion (scalar for H1, vector otherwise)
+  Mat Phi;                           // (ncomp * E.n) x nref coefficients
+  double dof_cond = 0.0;
+  // Reference matrices R_q (Q x nref x nref), see geometric_factor_kind below.
+  int Q = 0;
+  std::vector<double> R;
+  // Cross tables for the right-hand side of an [CG_p]^3 (or CG_p) source:
+  // X[l][a][i] = int phi^CG_a v_i^l (l < ncomp), a < ncg.
+  int ncg = 0;
+  std::vector<double> Xcross;
+  // tabulate values (npt x nref x ncomp) and d (npt x nref x dcomp) at points
+  void tabulate(int npt, const double* x, double* vals, double* dvals) const;
+};
+
+// Cached per (space, p).  Throws std::runtime_error on failure.
+const RefElement& reference_element(int space, int p);
+
+}  // namespace riesz

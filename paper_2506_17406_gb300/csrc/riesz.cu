@@ -1,0 +1,721 @@
+// C ABI of the Riesz-map solver: handle, host/device setup, apply, precond,
+// PCG.  See include/riesz.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/riesz.h"
+#include "kernels.cuh"
+#include "mesh.h"
+#include "refelem.h"
+
+using namespace riesz;
+
+namespace {
+
+thread_local std::string g_err;
+
+struct Err : std::runtime_error {
+  int code;
+  Err(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define CK(x)                                                                                        \
+  do {                                                                                               \
+    cudaError_t e_ = (x);                                                                            \
+    if (e_ != cudaSuccess)                                                                           \
+      throw Err(e_ == cudaErrorMemoryAllocation ? RIESZ_ERR_OOM : RIESZ_ERR_CUDA,                    \
+                std::string(#x) + ": " + cudaGetErrorString(e_));                                    \
+  } while (0)
+
+#define KCHECK() CK(cudaGetLastError())
+
+template <typename T>
+struct DBuf {  // device buffer owned by the handle
+  T* p = nullptr;
+  size_t n = 0;
+  void alloc(size_t count) {
+    free();
+    n = count;
+    if (count) CK(cudaMalloc((void**)&p, count * sizeof(T)));
+  }
+  void upload(const std::vector<T>& v, cudaStream_t s) {
+    alloc(v.size());
+    if (n) CK(cudaMemcpyAsync(p, v.data(), n * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  void free() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+};
+
+}  // namespace
+
+struct riesz_handle {
+  int space = 0, p = 0;
+  riesz_opts opts;
+  const RefElement* ref = nullptr;
+  const RefElement* refcg = nullptr;
+  std::vector<double> verts;
+  MeshMaps mesh, meshcg;
+  int nif = 0;  // interface DOFs per cell
+  // host-side plans
+  std::vector<int64_t> sc_ptr;   // interface DOF -> positions in Ycell
+  std::vector<int32_t> sc_pos;
+  std::vector<int32_t> p_n;      // patches in launch order (largest first)
+  std::vector<int64_t> p_doff, p_foff;
+  std::vector<int32_t> p_dofs;
+  std::vector<int64_t> pz_ptr;   // interface DOF -> positions in zpatch
+  std::vector<int32_t> pz_pos;
+  std::vector<int64_t> pb_ptr, pb_off;
+  std::vector<int32_t> pb_cell, pb_ent;
+  int64_t factor_entries = 0;
+  double setup_host_ms = 0.0, setup_dev_ms = 0.0;
+  // device state
+  bool on_device = false;
+  int device = 0;
+  DBuf<double> d_verts, d_g, d_jac, d_R, d_Ae, d_Ycell, d_dinv, d_L64, d_zpatch, d_X;
+  DBuf<float> d_L32;
+  DBuf<int32_t> d_cells, d_cdofs, d_sc_pos, d_pn, d_pdofs, d_pz_pos, d_pb_cell, d_pb_ent, d_cgdofs;
+  DBuf<int64_t> d_sc_ptr, d_pdoff, d_pfoff, d_pz_ptr, d_pb_ptr, d_pb_off;
+  DBuf<int> d_info;
+  // PCG workspace
+  DBuf<double> d_r, d_z, d_zold, d_p, d_Ap, d_part, d_scal, d_tmp, d_xh;
+  double* h_scal = nullptr;  // pinned
+  int last_iters = 0;
+  int64_t launches = 0;
+  int64_t N() const { return mesh.ndofs; }
+  int64_t C() const { return mesh.ncells; }
+  size_t device_bytes() const {
+    return d_verts.bytes() + d_g.bytes() + d_jac.bytes() + d_R.bytes() + d_Ae.bytes() + d_Ycell.bytes() +
+           d_dinv.bytes() + d_L64.bytes() + d_L32.bytes() + d_zpatch.bytes() + d_X.bytes() + d_cells.bytes() +
+           d_cdofs.bytes() + d_sc_pos.bytes() + d_pn.bytes() + d_pdofs.bytes() + d_pz_pos.bytes() +
+           d_pb_cell.bytes() + d_pb_ent.bytes() + d_cgdofs.bytes() + d_sc_ptr.bytes() + d_pdoff.bytes() +
+           d_pfoff.bytes() + d_pz_ptr.bytes() + d_pb_ptr.bytes() + d_pb_off.bytes() + d_r.bytes() + d_z.bytes() +
+           d_zold.bytes() + d_p.bytes() + d_Ap.bytes() + d_part.bytes() + d_scal.bytes() + d_tmp.bytes() + d_xh.bytes();
+  }
+  void free_device() {
+    for (auto* b : {&d_verts, &d_g, &d_jac, &d_R, &d_Ae, &d_Ycell, &d_dinv, &d_L64, &d_zpatch, &d_X, &d_r, &d_z,
+                    &d_zold, &d_p, &d_Ap, &d_part, &d_scal, &d_tmp, &d_xh})
+      b->free();
+    d_L32.free();
+    for (auto* b : {&d_cells, &d_cdofs, &d_sc_pos, &d_pn, &d_pdofs, &d_pz_pos, &d_pb_cell, &d_pb_ent, &d_cgdofs})
+      b->free();
+    for (auto* b : {&d_sc_ptr, &d_pdoff, &d_pfoff, &d_pz_ptr, &d_pb_ptr, &d_pb_off}) b->free();
+    d_info.free();
+    if (h_scal) cudaFreeHost(h_scal);
+    h_scal = nullptr;
+    on_device = false;
+  }
+  ~riesz_handle() { free_device(); }
+};
+
+namespace {
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    f();
+    return RIESZ_OK;
+  } catch (const Err& e) {
+    g_err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return RIESZ_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return RIESZ_ERR_INVALID_ARG;
+  }
+}
+
+void need(bool ok, const char* msg, int code = RIESZ_ERR_INVALID_ARG) {
+  if (!ok) throw Err(code, msg);
+}
+
+// reference edge matrix inverse (columns V1-V0, V2-V0, V3-V0 of the reference tetrahedron)
+dev::Mat3 ref_edge_inverse() {
+  const double s3 = std::sqrt(3.0), s6 = std::sqrt(6.0);
+  const double V[4][3] = {{-1.0, -1.0 / s3, -1.0 / s6}, {1.0, -1.0 / s3, -1.0 / s6}, {0.0, 2.0 / s3, -1.0 / s6},
+                          {0.0, 0.0, 3.0 / s6}};
+  Mat E(3, 3);
+  for (int d = 0; d < 3; ++d)
+    for (int k = 0; k < 3; ++k) E(d, k) = V[k + 1][d] - V[0][d];
+  Mat Ei = inverse(E);
+  dev::Mat3 m;
+  for (int k = 0; k < 9; ++k) m.a[k] = Ei(k / 3, k % 3);
+  return m;
+}
+
+void build_plans(riesz_handle& h) {
+  const MeshMaps& M = h.mesh;
+  const int n = M.nref;
+  const int64_t C = M.ncells;
+  h.nif = n - h.ref->ninterior;
+  // host check of the cell volumes
+  for (int64_t c = 0; c < C; ++c) {
+    double X[4][3];
+    double emax = 0.0;
+    for (int k = 0; k < 4; ++k)
+      for (int d = 0; d < 3; ++d) X[k][d] = h.verts[(size_t)M.cells[c * 4 + k] * 3 + d];
+    double E[3][3];
+    for (int k = 0; k < 3; ++k) {
+      double l = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        E[k][d] = X[k + 1][d] - X[0][d];
+        l += E[k][d] * E[k][d];
+      }
+      emax = std::max(emax, l);
+    }
+    const double det = E[0][0] * (E[1][1] * E[2][2] - E[1][2] * E[2][1]) -
+                       E[0][1] * (E[1][0] * E[2][2] - E[1][2] * E[2][0]) +
+                       E[0][2] * (E[1][0] * E[2][1] - E[1][1] * E[2][0]);
+    if (!(std::fabs(det) > 1e-12 * std::pow(emax, 1.5)) || !std::isfinite(det))
+      throw Err(RIESZ_ERR_BAD_MESH, "degenerate or non-finite cell " + std::to_string(c));
+  }
+  // interface scatter CSR: DOF d <- (j*C + c) for local interface j
+  const int64_t nI = M.n_interface;
+  h.sc_ptr.assign(nI + 1, 0);
+  for (int64_t c = 0; c < C; ++c)
+    for (int j = 0; j < h.nif; ++j) h.sc_ptr[M.cell_dofs[c * n + j] + 1]++;
+  for (int64_t d = 0; d < nI; ++d) h.sc_ptr[d + 1] += h.sc_ptr[d];
+  h.sc_pos.assign(h.sc_ptr[nI], 0);
+  {
+    std::vector<int64_t> cur(h.sc_ptr.begin(), h.sc_ptr.end() - 1);
+    for (int64_t c = 0; c < C; ++c)  // cell order fixes the summation order
+      for (int j = 0; j < h.nif; ++j) h.sc_pos[cur[M.cell_dofs[c * n + j]]++] = (int32_t)((int64_t)j * C + c);
+  }
+  // patches, largest first
+  const int64_t nv = M.nverts;
+  std::vector<int64_t> order(nv);
+  for (int64_t v = 0; v < nv; ++v) order[v] = v;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return (M.patch_ptr[a + 1] - M.patch_ptr[a]) > (M.patch_ptr[b + 1] - M.patch_ptr[b]);
+  });
+  h.p_n.clear();
+  h.p_doff.clear();
+  h.p_foff.clear();
+  h.p_dofs.clear();
+  h.pb_ptr.assign(1, 0);
+  h.pb_off.assign(1, 0);
+  h.pb_cell.clear();
+  h.pb_ent.clear();
+  int64_t foff = 0;
+  for (int64_t v : order) {
+    const int64_t b = M.patch_ptr[v], e = M.patch_ptr[v + 1];
+    const int np = (int)(e - b);
+    if (np == 0) continue;
+    if (np >= (1 << 21)) throw Err(RIESZ_ERR_INVALID_ARG, "patch too large");
+    h.p_n.push_back(np);
+    h.p_doff.push_back((int64_t)h.p_dofs.size());
+    h.p_foff.push_back(foff);
+    foff += (int64_t)np * (np + 1) / 2;
+    h.p_dofs.insert(h.p_dofs.end(), M.patch_dofs.begin() + b, M.patch_dofs.begin() + e);
+    const int32_t* pd = &M.patch_dofs[b];
+    for (int64_t s = M.star_ptr[v]; s < M.star_ptr[v + 1]; ++s) {
+      const int32_t c = M.star_cells[s];
+      int m = 0;
+      for (int j = 0; j < h.nif; ++j) {
+        const int32_t gd = M.cell_dofs[(int64_t)c * n + j];
+        const int32_t* it = std::lower_bound(pd, pd + np, gd);
+        if (it != pd + np && *it == gd) {
+          h.pb_ent.push_back(j | (int32_t)((it - pd) << 10));
+          ++m;
+        }
+      }
+      if (m) {
+        h.pb_cell.push_back(c);
+        h.pb_off.push_back((int64_t)h.pb_ent.size());
+      }
+    }
+    h.pb_ptr.push_back((int64_t)h.pb_cell.size());
+  }
+  h.factor_entries = foff;
+  // interface DOF -> positions in zpatch (patch launch order fixes the sum order)
+  h.pz_ptr.assign(nI + 1, 0);
+  for (int32_t d : h.p_dofs) h.pz_ptr[d + 1]++;
+  for (int64_t d = 0; d < nI; ++d) h.pz_ptr[d + 1] += h.pz_ptr[d];
+  h.pz_pos.assign(h.pz_ptr[nI], 0);
+  {
+    std::vector<int64_t> cur(h.pz_ptr.begin(), h.pz_ptr.end() - 1);
+    for (size_t k = 0; k < h.p_dofs.size(); ++k) h.pz_pos[cur[h.p_dofs[k]]++] = (int32_t)k;
+  }
+}
+
+std::vector<int32_t> transpose_dofs(const std::vector<int32_t>& cd, int64_t C, int n) {
+  std::vector<int32_t> t((size_t)C * n);
+  for (int64_t c = 0; c < C; ++c)
+    for (int j = 0; j < n; ++j) t[(size_t)j * C + c] = cd[(size_t)c * n + j];
+  return t;
+}
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---- operator pieces ------------------------------------------------------
+void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_t s) {
+  const int n = h.mesh.nref;
+  const int64_t C = h.C(), N = h.N();
+  if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
+    const size_t sm = (size_t)n * nrhs * sizeof(double);
+    dev::k_apply_elem<<<(unsigned)C, dev::NT, sm, s>>>(C, n, h.nif, h.d_Ae.p, h.d_cdofs.p, x, y, h.d_Ycell.p, nrhs, N);
+  } else {
+    const size_t sm = ((size_t)n + h.ref->Q) * dev::TC * sizeof(double);
+    dim3 grid(nblk(C, dev::TC), nrhs);
+    dev::k_apply_mf<<<grid, dev::NT, sm, s>>>(C, n, h.nif, h.ref->Q, h.d_R.p, h.d_g.p, h.d_cdofs.p, x, y, h.d_Ycell.p, N);
+  }
+  KCHECK();
+  const int64_t nI = h.mesh.n_interface;
+  dev::k_gather_iface<<<nblk(nI, 256), 256, 0, s>>>(nI, h.d_sc_ptr.p, h.d_sc_pos.p, h.d_Ycell.p, (int64_t)h.nif * C, y, N,
+                                                   nrhs);
+  KCHECK();
+  h.launches += 2;
+}
+
+void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStream_t s) {
+  const int64_t N = h.N();
+  const int npatch = (int)h.p_n.size();
+  const int nmax = h.p_n.empty() ? 0 : h.p_n[0];
+  const int64_t zstride = (int64_t)h.p_dofs.size();
+  if (npatch) {
+    dim3 grid(npatch, nrhs);
+    if (h.opts.precond_precision == RIESZ_PREC_FP32) {
+      dev::k_patch_solve<float><<<grid, dev::NT, (size_t)nmax * sizeof(float), s>>>(
+          h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdofs.p, h.d_L32.p, r, h.d_zpatch.p, N, zstride);
+    } else {
+      dev::k_patch_solve<double><<<grid, dev::NT, (size_t)nmax * sizeof(double), s>>>(
+          h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdofs.p, h.d_L64.p, r, h.d_zpatch.p, N, zstride);
+    }
+    KCHECK();
+    h.launches += 1;
+  }
+  dev::k_precond_gather<<<nblk(N, 256), 256, 0, s>>>(N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p,
+                                                    zstride, h.d_dinv.p, r, z, nrhs);
+  KCHECK();
+  h.launches += 1;
+}
+
+void dot(riesz_handle& h, const double* a, const double* b, const double* c, int op, double* scal, cudaStream_t s) {
+  dev::k_dot2<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(h.N(), a, b, c, h.d_part.p);
+  KCHECK();
+  dev::k_scalar<<<1, dev::NT, 0, s>>>(h.d_part.p, op, scal);
+  KCHECK();
+  h.launches += 2;
+}
+
+void read_scal(riesz_handle& h, const double* scal, cudaStream_t s) {
+  CK(cudaMemcpyAsync(h.h_scal, scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+// PCG for one right-hand side; returns a status code.
+int pcg_one(riesz_handle& h, const double* b, double* x, cudaStream_t s, int* iters_out, double* relres_out) {
+  const int64_t N = h.N();
+  double* scal = h.d_scal.p;
+  const bool flex = h.opts.precond_precision == RIESZ_PREC_FP32;
+  CK(cudaMemsetAsync(scal, 0, 16 * sizeof(double), s));
+  auto residual = [&]() {  // r = b - A x, RR
+    op_apply(h, x, h.d_Ap.p, 1, s);
+    dev::k_residual<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, b, h.d_Ap.p, h.d_r.p, h.d_part.p);
+    KCHECK();
+    dev::k_scalar<<<1, dev::NT, 0, s>>>(h.d_part.p, 1, scal);
+    KCHECK();
+    h.launches += 2;
+  };
+  auto restart = [&]() {  // z = P r, p = z, RZ
+    op_precond(h, h.d_r.p, h.d_z.p, 1, s);
+    dot(h, h.d_r.p, h.d_z.p, nullptr, 5, scal, s);
+    CK(cudaMemcpyAsync(h.d_p.p, h.d_z.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (flex) CK(cudaMemcpyAsync(h.d_zold.p, h.d_z.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  };
+  dot(h, b, b, nullptr, 4, scal, s);
+  residual();
+  read_scal(h, scal, s);
+  const double bb = h.h_scal[dev::S_BB];
+  if (!std::isfinite(bb) || h.h_scal[dev::S_NONFINITE] != 0.0) {
+    g_err = "non-finite right-hand side or initial guess";
+    return RIESZ_ERR_NONFINITE;
+  }
+  const double tol2 = h.opts.rtol * h.opts.rtol * bb;
+  int it = 0;
+  int status = RIESZ_ERR_NOT_CONVERGED;
+  double rr = h.h_scal[dev::S_RR];
+  if (bb == 0.0 || rr <= tol2) {
+    status = RIESZ_OK;
+  } else {
+    restart();
+    while (it < h.opts.maxit) {
+      op_apply(h, h.d_p.p, h.d_Ap.p, 1, s);
+      dot(h, h.d_p.p, h.d_Ap.p, nullptr, 0, scal, s);
+      dev::k_update_xr<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, scal, x, h.d_r.p, h.d_p.p, h.d_Ap.p, h.d_part.p);
+      KCHECK();
+      dev::k_scalar<<<1, dev::NT, 0, s>>>(h.d_part.p, 1, scal);
+      KCHECK();
+      h.launches += 2;
+      ++it;
+      read_scal(h, scal, s);
+      if (h.h_scal[dev::S_NONFINITE] != 0.0 || !std::isfinite(h.h_scal[dev::S_RR])) {
+        status = RIESZ_ERR_NONFINITE;
+        g_err = "non-finite value in the PCG recurrence";
+        break;
+      }
+      if (h.h_scal[dev::S_RR] <= tol2) {
+        residual();  // verify on the true residual
+        read_scal(h, scal, s);
+        if (h.h_scal[dev::S_RR] <= tol2) {
+          status = RIESZ_OK;
+          break;
+        }
+        restart();
+        continue;
+      }
+      op_precond(h, h.d_r.p, h.d_z.p, 1, s);
+      dot(h, h.d_r.p, h.d_z.p, flex ? h.d_zold.p : nullptr, flex ? 3 : 2, scal, s);
+      dev::k_update_p<<<1184, 256, 0, s>>>(N, scal, h.d_z.p, h.d_p.p);
+      KCHECK();
+      h.launches += 1;
+      if (flex) CK(cudaMemcpyAsync(h.d_zold.p, h.d_z.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    if (status == RIESZ_ERR_NOT_CONVERGED) {
+      residual();
+      read_scal(h, scal, s);
+      g_err = "PCG did not reach rtol within maxit";
+    }
+  }
+  if (iters_out) *iters_out = it;
+  if (relres_out) *relres_out = bb > 0 ? std::sqrt(h.h_scal[dev::S_RR] / bb) : 0.0;
+  h.last_iters = it;
+  return status;
+}
+
+void setup_device_impl(riesz_handle& h, cudaStream_t s) {
+  auto t0 = std::chrono::steady_clock::now();
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) throw Err(RIESZ_ERR_CUDA, "no CUDA device");
+  CK(cudaGetDevice(&h.device));
+  h.free_device();
+  const RefElement& R = *h.ref;
+  const MeshMaps& M = h.mesh;
+  const int n = M.nref;
+  const int64_t C = M.ncells, N = M.ndofs;
+  const int nrhs = std::max(1, h.opts.nrhs_max);
+  h.d_verts.upload(h.verts, s);
+  h.d_cells.upload(M.cells, s);
+  h.d_cdofs.upload(transpose_dofs(M.cell_dofs, C, n), s);
+  h.d_R.upload(R.R, s);
+  h.d_g.alloc((size_t)R.Q * C);
+  h.d_jac.alloc((size_t)C * 10);
+  h.d_Ycell.alloc((size_t)nrhs * h.nif * C);
+  h.d_dinv.alloc(std::max<int64_t>(1, M.n_interior));
+  h.d_sc_ptr.upload(h.sc_ptr, s);
+  h.d_sc_pos.upload(h.sc_pos, s);
+  h.d_pn.upload(h.p_n, s);
+  h.d_pdoff.upload(h.p_doff, s);
+  h.d_pfoff.upload(h.p_foff, s);
+  h.d_pdofs.upload(h.p_dofs, s);
+  h.d_pz_ptr.upload(h.pz_ptr, s);
+  h.d_pz_pos.upload(h.pz_pos, s);
+  h.d_pb_ptr.upload(h.pb_ptr, s);
+  h.d_pb_off.upload(h.pb_off, s);
+  h.d_pb_cell.upload(h.pb_cell, s);
+  h.d_pb_ent.upload(h.pb_ent, s);
+  h.d_zpatch.alloc(std::max<size_t>(1, h.p_dofs.size() * nrhs));
+  h.d_X.upload(R.Xcross, s);
+  h.d_cgdofs.upload(transpose_dofs(h.meshcg.cell_dofs, C, h.refcg->nref), s);
+  for (auto* b : {&h.d_r, &h.d_z, &h.d_zold, &h.d_p, &h.d_Ap, &h.d_tmp, &h.d_xh}) b->alloc((size_t)N * nrhs);
+  h.d_part.alloc(2 * dev::RED_BLOCKS);
+  h.d_scal.alloc(16 * (size_t)nrhs);
+  CK(cudaMallocHost((void**)&h.h_scal, 16 * sizeof(double)));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  // a1 geometry
+  dev::k_geom<<<nblk(C, 128), 128, 0, s>>>(h.space, C, h.d_verts.p, h.d_cells.p, ref_edge_inverse(), h.d_g.p, h.d_jac.p);
+  KCHECK();
+  if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
+    h.d_Ae.alloc((size_t)C * n * n);
+    dev::k_elem_matrices<<<(unsigned)C, 256, 0, s>>>(C, n, R.Q, h.d_g.p, h.d_R.p, h.d_Ae.p);
+    KCHECK();
+  } else {
+    const size_t sm = ((size_t)n + R.Q) * dev::TC * sizeof(double);
+    CK(cudaFuncSetAttribute(dev::k_apply_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  }
+  {
+    const size_t sm = (size_t)n * nrhs * sizeof(double);
+    if (sm > 48 * 1024)
+      CK(cudaFuncSetAttribute(dev::k_apply_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  }
+  // a6 interior diagonal
+  if (M.n_interior > 0) {
+    const int64_t cnt = C * (int64_t)(n - h.nif);
+    dev::k_interior_diag<<<nblk(cnt, 256), 256, 0, s>>>(C, n, h.nif, R.Q, h.d_g.p, h.d_R.p, h.d_cdofs.p, M.n_interface,
+                                                       h.d_dinv.p);
+    KCHECK();
+  }
+  // a8 patch assembly + Cholesky
+  const int npatch = (int)h.p_n.size();
+  h.d_info.alloc(std::max(1, npatch));
+  CK(cudaMemsetAsync(h.d_info.p, 0, sizeof(int) * std::max(1, npatch), s));
+  if (npatch) {
+    h.d_L64.alloc((size_t)h.factor_entries);
+    dev::k_patch_assemble<<<npatch, 256, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pb_ptr.p, h.d_pb_cell.p, h.d_pb_off.p,
+                                                 h.d_pb_ent.p, C, n, R.Q, h.d_g.p, h.d_R.p, h.d_Ae.p, h.d_L64.p);
+    KCHECK();
+    dev::k_cholesky<<<npatch, dev::NT, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_L64.p, h.d_info.p);
+    KCHECK();
+    if (h.opts.precond_precision == RIESZ_PREC_FP32) {
+      h.d_L32.alloc((size_t)h.factor_entries);
+      dev::k_to_f32<<<1184, 256, 0, s>>>(h.factor_entries, h.d_L64.p, h.d_L32.p);
+      KCHECK();
+    }
+  }
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  h.setup_dev_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (npatch) {
+    std::vector<int> info(npatch);
+    CK(cudaMemcpy(info.data(), h.d_info.p, sizeof(int) * npatch, cudaMemcpyDeviceToHost));
+    for (int P = 0; P < npatch; ++P)
+      if (info[P]) throw Err(RIESZ_ERR_INTERNAL, "patch matrix not positive definite");
+    if (h.opts.precond_precision == RIESZ_PREC_FP32) h.d_L64.free();
+  }
+  const size_t smp = (size_t)(h.p_n.empty() ? 0 : h.p_n[0]) * sizeof(double);
+  if (smp > 48 * 1024) {
+    CK(cudaFuncSetAttribute(dev::k_patch_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
+    CK(cudaFuncSetAttribute(dev::k_patch_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
+  }
+  h.on_device = true;
+  (void)t0;
+}
+
+void check_dev(const riesz_handle* h) {
+  need(h != nullptr, "null handle");
+  need(h->on_device, "handle has no device state (call riesz_setup_device)", RIESZ_ERR_NO_DEVICE);
+}
+
+}  // namespace
+
+extern "C" {
+
+void riesz_default_opts(riesz_opts* o) {
+  if (!o) return;
+  o->precond_precision = RIESZ_PREC_FP64;
+  o->apply_mode = RIESZ_APPLY_ELEMENT;
+  o->rtol = 1e-8;
+  o->maxit = 1000;
+  o->nrhs_max = 1;
+}
+
+const char* riesz_last_error(void) { return g_err.c_str(); }
+
+int riesz_create(int space, int p, int64_t nverts, const double* verts, int64_t ncells, const int64_t* cells,
+                 const riesz_opts* opts, riesz_handle** out) {
+  return guarded([&] {
+    need(out != nullptr, "out is NULL");
+    *out = nullptr;
+    need(space >= 0 && space <= 2, "space must be RIESZ_H1, RIESZ_HCURL or RIESZ_HDIV");
+    need(p >= 1 && p <= 10, "degree p must be in 1..10");
+    need(verts && cells && nverts > 0 && ncells > 0, "empty mesh", RIESZ_ERR_BAD_MESH);
+    auto t0 = std::chrono::steady_clock::now();
+    auto h = std::make_unique<riesz_handle>();
+    h->space = space;
+    h->p = p;
+    riesz_default_opts(&h->opts);
+    if (opts) h->opts = *opts;
+    need(h->opts.rtol > 0 && h->opts.maxit >= 0 && h->opts.nrhs_max >= 1 && h->opts.nrhs_max <= 64, "bad options");
+    need(h->opts.precond_precision == 0 || h->opts.precond_precision == 1, "bad precond_precision");
+    need(h->opts.apply_mode == 0 || h->opts.apply_mode == 1, "bad apply_mode");
+    for (int64_t i = 0; i < nverts * 3; ++i)
+      need(std::isfinite(verts[i]), "non-finite vertex coordinate", RIESZ_ERR_BAD_MESH);
+    h->verts.assign(verts, verts + nverts * 3);
+    try {
+      h->ref = &reference_element(space, p);
+      h->refcg = &reference_element(RIESZ_H1, p);
+      h->mesh = build_mesh(*h->ref, nverts, ncells, cells);
+      h->meshcg = (space == RIESZ_H1) ? h->mesh : build_mesh(*h->refcg, nverts, ncells, cells);
+    } catch (const Err&) {
+      throw;
+    } catch (const std::exception& e) {
+      throw Err(RIESZ_ERR_BAD_MESH, e.what());
+    }
+    build_plans(*h);
+    h->setup_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = h.release();
+  });
+}
+
+int riesz_num_dofs(const riesz_handle* h, int64_t* n, int64_t* n_interior) {
+  return guarded([&] {
+    need(h != nullptr, "null handle");
+    if (n) *n = h->mesh.ndofs;
+    if (n_interior) *n_interior = h->mesh.n_interior;
+  });
+}
+
+int riesz_num_cg_dofs(const riesz_handle* h, int64_t* n_cg) {
+  return guarded([&] {
+    need(h != nullptr && n_cg != nullptr, "null argument");
+    *n_cg = h->meshcg.ndofs;
+  });
+}
+
+int riesz_ref_info(const riesz_handle* h, int* info) {
+  return guarded([&] {
+    need(h != nullptr && info != nullptr, "null argument");
+    const RefElement& R = *h->ref;
+    info[0] = R.nref;
+    info[1] = R.ninterior;
+    info[2] = R.ncomp;
+    info[3] = R.dcomp;
+    for (int d = 0; d < 4; ++d) info[4 + d] = R.per_entity[d];
+  });
+}
+
+int riesz_dof_map(const riesz_handle* h, int32_t* cell_dofs) {
+  return guarded([&] {
+    need(h != nullptr && cell_dofs != nullptr, "null argument");
+    std::memcpy(cell_dofs, h->mesh.cell_dofs.data(), h->mesh.cell_dofs.size() * sizeof(int32_t));
+  });
+}
+
+int riesz_patch_map(const riesz_handle* h, int64_t* offsets, int32_t* dofs) {
+  return guarded([&] {
+    need(h != nullptr && offsets != nullptr, "null argument");
+    std::memcpy(offsets, h->mesh.patch_ptr.data(), h->mesh.patch_ptr.size() * sizeof(int64_t));
+    if (dofs) std::memcpy(dofs, h->mesh.patch_dofs.data(), h->mesh.patch_dofs.size() * sizeof(int32_t));
+  });
+}
+
+int riesz_ref_tabulate(int space, int p, int64_t npts, const double* pts, double* vals, double* dvals) {
+  return guarded([&] {
+    need(space >= 0 && space <= 2 && p >= 1 && p <= 10, "bad space or degree");
+    need(npts >= 0 && (npts == 0 || pts != nullptr), "bad points");
+    reference_element(space, p).tabulate((int)npts, pts, vals, dvals);
+  });
+}
+
+int riesz_setup_device(riesz_handle* h, void* stream) {
+  return guarded([&] {
+    need(h != nullptr, "null handle");
+    setup_device_impl(*h, S(stream));
+  });
+}
+
+int riesz_setup(int space, int p, int64_t nverts, const double* verts, int64_t ncells, const int64_t* cells,
+                const riesz_opts* opts, void* stream, riesz_handle** out) {
+  int rc = riesz_create(space, p, nverts, verts, ncells, cells, opts, out);
+  if (rc != RIESZ_OK) return rc;
+  rc = riesz_setup_device(*out, stream);
+  if (rc != RIESZ_OK) {
+    delete *out;
+    *out = nullptr;
+  }
+  return rc;
+}
+
+int riesz_apply(riesz_handle* h, const double* x, double* y, int nrhs, void* stream) {
+  return guarded([&] {
+    check_dev(h);
+    need(x && y && nrhs >= 1 && nrhs <= h->opts.nrhs_max, "bad apply arguments");
+    op_apply(*h, x, y, nrhs, S(stream));
+  });
+}
+
+int riesz_precond(riesz_handle* h, const double* r, double* z, int nrhs, void* stream) {
+  return guarded([&] {
+    check_dev(h);
+    need(r && z && nrhs >= 1 && nrhs <= h->opts.nrhs_max, "bad precond arguments");
+    op_precond(*h, r, z, nrhs, S(stream));
+  });
+}
+
+int riesz_solve(riesz_handle* h, const double* b, double* x, int nrhs, void* stream, int* iters, double* relres) {
+  int status = RIESZ_OK;
+  int rc = guarded([&] {
+    check_dev(h);
+    need(b && x && nrhs >= 1, "bad solve arguments");
+    h->launches = 0;
+    const int64_t N = h->N();
+    for (int r = 0; r < nrhs; ++r) {
+      int st = pcg_one(*h, b + r * N, x + r * N, S(stream), iters ? iters + r : nullptr, relres ? relres + r : nullptr);
+      if (st != RIESZ_OK && status == RIESZ_OK) status = st;
+    }
+  });
+  return rc != RIESZ_OK ? rc : status;
+}
+
+int riesz_solve_host(riesz_handle* h, const double* b_host, double* x_host, int nrhs, void* stream, int* iters,
+                     double* relres) {
+  int status = RIESZ_OK;
+  int rc = guarded([&] {
+    check_dev(h);
+    need(b_host && x_host && nrhs >= 1 && nrhs <= h->opts.nrhs_max, "bad solve arguments");
+    const int64_t N = h->N();
+    cudaStream_t s = S(stream);
+    double* db = h->d_tmp.p;  // staging of b
+    double* dx = h->d_xh.p;   // staging of x
+    CK(cudaMemcpyAsync(db, b_host, (size_t)N * nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dx, x_host, (size_t)N * nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+    h->launches = 0;
+    for (int r = 0; r < nrhs; ++r) {
+      int st = pcg_one(*h, db + r * N, dx + r * N, s, iters ? iters + r : nullptr, relres ? relres + r : nullptr);
+      if (st != RIESZ_OK && status == RIESZ_OK) status = st;
+    }
+    CK(cudaMemcpyAsync(x_host, dx, (size_t)N * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  });
+  return rc != RIESZ_OK ? rc : status;
+}
+
+int riesz_load(riesz_handle* h, const double* fcg, double* b, void* stream) {
+  return guarded([&] {
+    check_dev(h);
+    need(fcg && b, "null argument");
+    const int64_t C = h->C(), N = h->N();
+    const int n = h->mesh.nref;
+    const int ncomp = (h->space == RIESZ_H1) ? 1 : 3;
+    const size_t sm = (size_t)ncomp * h->refcg->nref * sizeof(double);
+    cudaStream_t s = S(stream);
+    dev::k_load<<<(unsigned)C, 256, sm, s>>>(h->space, C, n, h->nif, h->refcg->nref, h->d_jac.p, h->d_cgdofs.p, fcg,
+                                           h->meshcg.ndofs, h->d_X.p, h->d_cdofs.p, b, h->d_Ycell.p);
+    KCHECK();
+    const int64_t nI = h->mesh.n_interface;
+    dev::k_gather_iface<<<nblk(nI, 256), 256, 0, s>>>(nI, h->d_sc_ptr.p, h->d_sc_pos.p, h->d_Ycell.p,
+                                                     (int64_t)h->nif * C, b, N, 1);
+    KCHECK();
+  });
+}
+
+int riesz_stats(const riesz_handle* h, double* out) {
+  return guarded([&] {
+    need(h != nullptr && out != nullptr, "null argument");
+    out[0] = h->setup_host_ms;
+    out[1] = h->setup_dev_ms;
+    out[2] = (double)h->device_bytes();
+    out[3] = (double)h->factor_entries * (h->opts.precond_precision == RIESZ_PREC_FP32 ? 4.0 : 8.0);
+    out[4] = h->last_iters;
+    out[5] = (double)h->launches;
+  });
+}
+
+int riesz_destroy(riesz_handle* h) {
+  return guarded([&] { delete h; });
+}
+
+}  // extern "C"

@@ -1,0 +1,222 @@
+"""Thin ctypes binding of the C ABI declared in ``include/riesz.h``.
+
+Argument marshalling only: every step of the solver runs in ``libriesz.so``
+(host C++ for the reference element and mesh maps, sm_103a kernels for the
+rest).  Device arrays are torch CUDA tensors (float64, contiguous); host
+arrays are numpy.  If the library is missing, every call raises -- there is
+no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+H1, HCURL, HDIV = 0, 1, 2
+SPACES = {"CG": H1, "H1": H1, "N1curl": HCURL, "HCURL": HCURL, "RT": HDIV, "HDIV": HDIV}
+PREC_FP64, PREC_FP32 = 0, 1
+APPLY_MATRIX_FREE, APPLY_ELEMENT = 0, 1
+
+ERRORS = {1: "INVALID_ARG", 2: "BAD_MESH", 3: "OOM", 4: "NOT_CONVERGED", 5: "NONFINITE", 6: "CUDA",
+          7: "INTERNAL", 8: "NO_DEVICE"}
+
+
+class RieszError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("riesz error %d (%s): %s" % (code, ERRORS.get(code, "?"), msg))
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precond_precision", ctypes.c_int), ("apply_mode", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("nrhs_max", ctypes.c_int)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.c_int
+
+_SIGS = {
+    "riesz_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "riesz_last_error": (ctypes.c_char_p, []),
+    "riesz_create": (_I, [_I, _I, _I64, _P, _I64, _P, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
+    "riesz_num_dofs": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "riesz_num_cg_dofs": (_I, [_P, ctypes.POINTER(_I64)]),
+    "riesz_ref_info": (_I, [_P, _P]),
+    "riesz_dof_map": (_I, [_P, _P]),
+    "riesz_patch_map": (_I, [_P, _P, _P]),
+    "riesz_ref_tabulate": (_I, [_I, _I, _I64, _P, _P, _P]),
+    "riesz_setup_device": (_I, [_P, _P]),
+    "riesz_setup": (_I, [_I, _I, _I64, _P, _I64, _P, ctypes.POINTER(Opts), _P, ctypes.POINTER(_P)]),
+    "riesz_apply": (_I, [_P, _P, _P, _I, _P]),
+    "riesz_precond": (_I, [_P, _P, _P, _I, _P]),
+    "riesz_solve": (_I, [_P, _P, _P, _I, _P, _P, _P]),
+    "riesz_solve_host": (_I, [_P, _P, _P, _I, _P, _P, _P]),
+    "riesz_load": (_I, [_P, _P, _P, _P]),
+    "riesz_stats": (_I, [_P, _P]),
+    "riesz_destroy": (_I, [_P]),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def load_library(build_if_missing=False):
+    """Load libriesz.so (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libriesz.so is not built (%s); run __graft_entry__.build()" % path)
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise RieszError(rc, _lib.riesz_last_error().decode())
+
+
+def default_opts(**kw):
+    lib = load_library()
+    o = Opts()
+    lib.riesz_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (device or host)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def riesz_ref_tabulate(space, p, pts):
+    """Reference basis at points of the reference tetrahedron: (vals, dvals)."""
+    lib = load_library()
+    space = SPACES.get(space, space)
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    ncomp = 1 if space == H1 else 3
+    dcomp = 1 if space == HDIV else 3
+    nref = {H1: (p + 1) * (p + 2) * (p + 3) // 6, HCURL: p * (p + 2) * (p + 3) // 2,
+            HDIV: p * (p + 1) * (p + 3) // 2}[space]
+    vals = np.zeros((pts.shape[0], nref, ncomp))
+    dvals = np.zeros((pts.shape[0], nref, dcomp))
+    _check(lib.riesz_ref_tabulate(space, p, pts.shape[0], _ptr(pts), _ptr(vals), _ptr(dvals)))
+    return vals, dvals
+
+
+class Riesz:
+    """A solver handle: ``Riesz(space, p, verts, cells, **opts)`` builds the host
+    maps; ``setup_device()`` runs the device setup."""
+
+    def __init__(self, space, p, verts, cells, device=True, stream=None, **opts):
+        self.lib = load_library()
+        self.space = SPACES.get(space, space)
+        self.p = p
+        verts = np.ascontiguousarray(verts, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        self.ncells = cells.shape[0]
+        self.nverts = verts.shape[0]
+        self.opts = default_opts(**opts)
+        h = ctypes.c_void_p()
+        _check(self.lib.riesz_create(self.space, p, verts.shape[0], _ptr(verts), cells.shape[0], _ptr(cells),
+                                     ctypes.byref(self.opts), ctypes.byref(h)))
+        self.h = h
+        n, ni, ncg = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib.riesz_num_dofs(self.h, ctypes.byref(n), ctypes.byref(ni)))
+        _check(self.lib.riesz_num_cg_dofs(self.h, ctypes.byref(ncg)))
+        self.N, self.n_interior, self.n_cg = n.value, ni.value, ncg.value
+        info = np.zeros(8, dtype=np.int32)
+        _check(self.lib.riesz_ref_info(self.h, _ptr(info)))
+        self.nref, self.nint_cell, self.ncomp, self.dcomp = (int(x) for x in info[:4])
+        self.per_entity = tuple(int(x) for x in info[4:])
+        if device:
+            self.setup_device(stream)
+
+    # ----- host queries -----
+    def dof_map(self):
+        out = np.zeros((self.ncells, self.nref), dtype=np.int32)
+        _check(self.lib.riesz_dof_map(self.h, _ptr(out)))
+        return out
+
+    def patch_map(self):
+        off = np.zeros(self.nverts + 1, dtype=np.int64)
+        _check(self.lib.riesz_patch_map(self.h, _ptr(off), None))
+        dofs = np.zeros(int(off[-1]), dtype=np.int32)
+        _check(self.lib.riesz_patch_map(self.h, _ptr(off), _ptr(dofs)))
+        return off, dofs
+
+    def stats(self):
+        out = np.zeros(6)
+        _check(self.lib.riesz_stats(self.h, _ptr(out)))
+        return {"setup_host_ms": out[0], "setup_device_ms": out[1], "device_bytes": out[2],
+                "factor_bytes": out[3], "last_iters": int(out[4]), "launches": int(out[5])}
+
+    # ----- device calls -----
+    def setup_device(self, stream=None):
+        _check(self.lib.riesz_setup_device(self.h, _stream(stream)))
+
+    def apply(self, x, y, nrhs=1, stream=None):
+        _check(self.lib.riesz_apply(self.h, _ptr(x), _ptr(y), nrhs, _stream(stream)))
+        return y
+
+    def precond(self, r, z, nrhs=1, stream=None):
+        _check(self.lib.riesz_precond(self.h, _ptr(r), _ptr(z), nrhs, _stream(stream)))
+        return z
+
+    def solve(self, b, x, nrhs=1, stream=None, check=True):
+        iters = np.zeros(nrhs, dtype=np.int32)
+        relres = np.zeros(nrhs)
+        rc = self.lib.riesz_solve(self.h, _ptr(b), _ptr(x), nrhs, _stream(stream), _ptr(iters), _ptr(relres))
+        if check:
+            _check(rc)
+        return iters, relres, rc
+
+    def solve_host(self, b, x, nrhs=1, stream=None, check=True):
+        iters = np.zeros(nrhs, dtype=np.int32)
+        relres = np.zeros(nrhs)
+        rc = self.lib.riesz_solve_host(self.h, _ptr(b), _ptr(x), nrhs, _stream(stream), _ptr(iters), _ptr(relres))
+        if check:
+            _check(rc)
+        return iters, relres, rc
+
+    def load(self, fcg, b, stream=None):
+        _check(self.lib.riesz_load(self.h, _ptr(fcg), _ptr(b), _stream(stream)))
+        return b
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.riesz_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,107 @@
+"""Host-side parity of libriesz.so (no GPU): exported symbols, reference basis
+and mesh maps against the oracle, input validation."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.mesh import MeshDofs
+from oracle.polys import quadrature
+from oracle.refelem import reference_element
+from paper_2506_17406_gb300 import riesz as rz
+from paper_2506_17406_gb300.inputs import kuhn_mesh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return rz.load_library(build_if_missing=True)
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "riesz.h")).read()
+    names = sorted(set(re.findall(r"\b(riesz_[a-z_0-9]+)\s*\(", hdr)))
+    assert len(names) >= 18
+    cdll = ctypes.CDLL(rz.library_path())
+    for n in names:
+        assert hasattr(cdll, n), n
+
+
+@pytest.mark.parametrize("space", ["CG", "N1curl", "RT"])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_reference_basis_matches_oracle(lib, space, p):
+    """The library's basis (Dubiner expansion, own eigen/null-space code) equals the
+    oracle's (Gram-Schmidt expansion, LAPACK) at points of the reference cell."""
+    X, _ = quadrature(3, 4)
+    v, d = rz.riesz_ref_tabulate(space, p, X)
+    vo, do = reference_element(space, p).tabulate(X)
+    assert np.abs(v - vo).max() <= 1e-11 * np.abs(vo).max()
+    assert np.abs(d - do).max() <= 1e-11 * np.abs(do).max()
+
+
+@pytest.mark.parametrize("space,p,n", [("CG", 3, 4), ("CG", 4, 2), ("N1curl", 3, 3), ("N1curl", 1, 2),
+                                       ("RT", 2, 3), ("RT", 4, 2)])
+def test_dof_and_patch_maps_bit_exact(lib, space, p, n):
+    verts, cells = kuhn_mesh(n, 0.1, 5)
+    # present the cells with scrambled vertex order: both sides must sort them
+    rng = np.random.Generator(np.random.PCG64(1))
+    scr = np.array([rng.permutation(c) for c in cells])
+    s = rz.Riesz(space, p, verts, scr, device=False)
+    md = MeshDofs(verts, scr, reference_element(space, p))
+    assert s.N == md.ndofs and s.n_interior == md.n_interior
+    assert np.array_equal(s.dof_map(), md.cell_dofs)
+    off, dofs = s.patch_map()
+    pts = md.patches()
+    assert len(off) == len(pts) + 1
+    for v, q in enumerate(pts):
+        assert np.array_equal(dofs[off[v]:off[v + 1]], q)
+
+
+def test_dof_counts_large_mesh(lib):
+    """Ned1_6 on 8^3 x 6 tets (405 264 DOFs) and RT_8 on 16^3 x 6 (8 017 920)."""
+    v, c = kuhn_mesh(8, 0.1, 1)
+    s = rz.Riesz("N1curl", 6, v, c, device=False)
+    assert s.N == 405264
+    v, c = kuhn_mesh(16, 0.1, 1)
+    s = rz.Riesz("RT", 8, v, c, device=False)
+    assert s.N == 8017920
+
+
+def test_input_validation(lib):
+    v, c = kuhn_mesh(1)
+    with pytest.raises(rz.RieszError) as e:
+        rz.Riesz("CG", 0, v, c, device=False)
+    assert e.value.code == 1
+    with pytest.raises(rz.RieszError) as e:
+        rz.Riesz(7, 2, v, c, device=False)
+    assert e.value.code == 1
+    bad = c.copy()
+    bad[0, 1] = bad[0, 0]
+    with pytest.raises(rz.RieszError) as e:
+        rz.Riesz("CG", 2, v, bad, device=False)
+    assert e.value.code == 2
+    bad = c.copy()
+    bad[0, 1] = len(v)
+    with pytest.raises(rz.RieszError) as e:
+        rz.Riesz("CG", 2, v, bad, device=False)
+    assert e.value.code == 2
+    flat = v.copy()
+    flat[:, 2] = 0.0  # every cell degenerate
+    with pytest.raises(rz.RieszError) as e:
+        rz.Riesz("CG", 2, flat, c, device=False)
+    assert e.value.code == 2
+    nan = v.copy()
+    nan[3, 0] = np.nan
+    with pytest.raises(rz.RieszError) as e:
+        rz.Riesz("CG", 2, nan, c, device=False)
+    assert e.value.code == 2
+
+
+def test_device_calls_fail_loudly_without_device_state(lib):
+    v, c = kuhn_mesh(1)
+    s = rz.Riesz("CG", 2, v, c, device=False)
+    rc = lib.riesz_apply(s.h, ctypes.c_void_p(8), ctypes.c_void_p(8), 1, None)
+    assert rc == 8  # RIESZ_ERR_NO_DEVICE, nothing launched

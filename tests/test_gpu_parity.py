@@ -1,0 +1,178 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle."""
+import numpy as np
+import pytest
+
+from oracle import assemble as asm
+from oracle.mesh import MeshDofs
+from oracle.refelem import reference_element
+from paper_2506_17406_gb300 import riesz as rz
+from paper_2506_17406_gb300.inputs import kuhn_mesh, normal_coeffs, normal_vector
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = [("CG", 3, 4, 0.0), ("CG", 5, 2, 0.1), ("N1curl", 1, 3, 0.1), ("N1curl", 3, 3, 0.1),
+         ("RT", 1, 3, 0.1), ("RT", 3, 3, 0.1), ("N1curl", 4, 2, 0.1), ("RT", 5, 2, 0.1)]
+_ORACLE = {}
+
+
+def oracle(space, p, n, amp, seed=3):
+    key = (space, p, n, amp, seed)
+    if key not in _ORACLE:
+        verts, cells = kuhn_mesh(n, amp, seed)
+        ref = reference_element(space, p)
+        md = MeshDofs(verts, cells, ref)
+        A = asm.assemble(md, asm.element_matrices(ref, verts, cells))
+        _ORACLE[key] = (verts, cells, ref, md, A)
+    return _ORACLE[key]
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", [rz.APPLY_ELEMENT, rz.APPLY_MATRIX_FREE])
+@pytest.mark.parametrize("space,p,n,amp", CASES)
+def test_apply_matches_oracle(space, p, n, amp, mode):
+    verts, cells, ref, md, A = oracle(space, p, n, amp)
+    s = rz.Riesz(space, p, verts, cells, apply_mode=mode, nrhs_max=2)
+    X = normal_coeffs((2, s.N), 11)
+    y = torch.zeros((2, s.N), dtype=torch.float64, device="cuda")
+    s.apply(dev(X), y, nrhs=2)
+    Y = host(y)
+    for r in range(2):
+        ye = A @ X[r]
+        assert np.abs(Y[r] - ye).max() <= 1e-11 * np.abs(ye).max()
+
+
+@pytest.mark.parametrize("prec,tol", [(rz.PREC_FP64, 1e-10), (rz.PREC_FP32, 1e-4)])
+@pytest.mark.parametrize("space,p,n,amp", CASES)
+def test_precond_matches_oracle(space, p, n, amp, prec, tol):
+    verts, cells, ref, md, A = oracle(space, p, n, amp)
+    s = rz.Riesz(space, p, verts, cells, precond_precision=prec)
+    P = asm.Preconditioner(A, md)
+    r = normal_vector(s.N, 5)
+    z = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    s.precond(dev(r), z)
+    ze = P.apply(r)
+    assert np.abs(host(z) - ze).max() <= tol * np.abs(ze).max()
+
+
+@pytest.mark.parametrize("space,p,n,amp", CASES)
+def test_solve_matches_direct_solve(space, p, n, amp):
+    verts, cells, ref, md, A = oracle(space, p, n, amp)
+    s = rz.Riesz(space, p, verts, cells, rtol=1e-13, maxit=5000)
+    b = normal_vector(s.N, 8)
+    x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    iters, relres, _ = s.solve(dev(b), x)
+    xe = asm.direct_solve(A, b)
+    assert relres[0] <= 1e-13
+    assert np.linalg.norm(host(x) - xe) <= 1e-9 * np.linalg.norm(xe)
+
+
+@pytest.mark.parametrize("prec", [rz.PREC_FP64, rz.PREC_FP32])
+@pytest.mark.parametrize("space,p,n,amp", [("CG", 3, 4, 0.0), ("N1curl", 3, 3, 0.1), ("RT", 3, 3, 0.1)])
+def test_solve_reaches_rtol_on_oracle_residual(space, p, n, amp, prec):
+    """rtol 1e-8 measured with the oracle's assembled matrix; iteration counts close to the oracle PCG."""
+    verts, cells, ref, md, A = oracle(space, p, n, amp)
+    s = rz.Riesz(space, p, verts, cells, precond_precision=prec)
+    b = normal_vector(s.N, 9)
+    x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    iters, relres, _ = s.solve(dev(b), x)
+    xh = host(x)
+    assert np.linalg.norm(b - A @ xh) <= 1.001e-8 * np.linalg.norm(b)
+    P = asm.Preconditioner(A, md)
+    _, it_o, _ = asm.pcg(A, b, P.apply, rtol=1e-8)
+    assert abs(int(iters[0]) - it_o) <= 2
+    xe = asm.direct_solve(A, b)
+    assert np.linalg.norm(xh - xe) <= 1e-5 * np.linalg.norm(xe)
+
+
+def test_manufactured_solution_cfg1():
+    """CG_3 on 4^3 x 6 tets, cubic u with N(0,1) coefficients: b from the oracle's quadrature,
+    x from the GPU solve reproduces u (Section 7.1 setting, exact in V_h)."""
+    verts, cells, ref, md, A = oracle("CG", 3, 4, 0.0)
+    C = normal_coeffs(20, 2)
+    ex = [(a, b_, c) for a in range(4) for b_ in range(4 - a) for c in range(4 - a - b_)]
+    f = lambda x: np.stack([sum(C[k] * x[:, 0] ** a * x[:, 1] ** b_ * x[:, 2] ** c
+                                for k, (a, b_, c) in enumerate(ex))], 1)
+
+    def df(x):
+        g = np.zeros((x.shape[0], 3))
+        for k, (a, b_, c) in enumerate(ex):
+            if a:
+                g[:, 0] += C[k] * a * x[:, 0] ** (a - 1) * x[:, 1] ** b_ * x[:, 2] ** c
+            if b_:
+                g[:, 1] += C[k] * b_ * x[:, 0] ** a * x[:, 1] ** (b_ - 1) * x[:, 2] ** c
+            if c:
+                g[:, 2] += C[k] * c * x[:, 0] ** a * x[:, 1] ** b_ * x[:, 2] ** (c - 1)
+        return g
+    b = asm.load_function(ref, md, f, df)
+    s = rz.Riesz("CG", 3, verts, cells, rtol=1e-12)
+    x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    s.solve(dev(b), x)
+    from oracle.polys import quadrature
+    Xr, _ = quadrature(3, 3)
+    xq, uh = asm.evaluate(ref, md, host(x), Xr)
+    ue = f(xq.reshape(-1, 3)).reshape(uh.shape)
+    assert np.abs(uh - ue).max() <= 1e-9 * np.abs(ue).max()
+
+
+@pytest.mark.parametrize("space,p,n,amp", [("CG", 4, 2, 0.1), ("N1curl", 3, 3, 0.1), ("RT", 3, 3, 0.1)])
+def test_load_matches_oracle(space, p, n, amp):
+    verts, cells, ref, md, A = oracle(space, p, n, amp)
+    s = rz.Riesz(space, p, verts, cells)
+    cg = reference_element("CG", p)
+    mcg = MeshDofs(verts, cells, cg)
+    assert s.n_cg == mcg.ndofs
+    ncomp = 1 if space == "CG" else 3
+    f = normal_coeffs((ncomp, s.n_cg), 4)
+    b = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    s.load(dev(f), b)
+    be = asm.load_cg_field(ref, md, cg, mcg, f)
+    assert np.abs(host(b) - be).max() <= 1e-12 * np.abs(be).max()
+
+
+def test_deterministic_and_edge_cases():
+    verts, cells, ref, md, A = oracle("N1curl", 3, 3, 0.1)
+    s = rz.Riesz("N1curl", 3, verts, cells, maxit=3)
+    xr = dev(normal_vector(s.N, 1))
+    y1 = torch.zeros_like(xr)
+    y2 = torch.zeros_like(xr)
+    s.apply(xr, y1)
+    s.apply(xr, y2)
+    z1 = torch.zeros_like(xr)
+    z2 = torch.zeros_like(xr)
+    s.precond(xr, z1)
+    s.precond(xr, z2)
+    assert torch.equal(y1, y2) and torch.equal(z1, z2)
+    # zero right-hand side: x = 0 returned, no iteration
+    x = torch.zeros_like(xr)
+    it, rr, rc = s.solve(torch.zeros_like(xr), x, check=False)
+    assert rc == 0 and it[0] == 0 and float(x.abs().max()) == 0.0
+    # iteration cap reached
+    x = torch.zeros_like(xr)
+    it, rr, rc = s.solve(xr, x, check=False)
+    assert rc == 4 and it[0] == 3 and rr[0] > 1e-8
+    # non-finite right-hand side is reported, not iterated on
+    bad = xr.clone()
+    bad[5] = float("nan")
+    x = torch.zeros_like(xr)
+    it, rr, rc = s.solve(bad, x, check=False)
+    assert rc == 5
+
+
+def test_solve_host_buffers_match_device_solve():
+    verts, cells, ref, md, A = oracle("RT", 3, 3, 0.1)
+    s = rz.Riesz("RT", 3, verts, cells)
+    b = normal_vector(s.N, 12)
+    x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    s.solve(dev(b), x)
+    xh = np.zeros(s.N)
+    s.solve_host(b, xh)
+    assert np.array_equal(host(x), xh)
