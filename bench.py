@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the Riesz-map PCG solver: DOFs/s solved to 1e-8 relative residual.
+
+One step = one pass of the whole path over one synthetic problem, inputs
+resident in HBM: device setup from the vertex coordinates (geometric factors,
+element matrices, interior diagonal, patch assembly, batched FP64 Cholesky),
+right-hand-side assembly, and PCG to ||b - A x|| <= 1e-8 ||b|| (true residual).
+The host-side reference element and mesh maps are built once before timing.
+
+Default workload: H(curl) Riesz map, first-kind Nedelec p = 6 on the unit cube
+split into 8^3 cubes x 6 tets (3072 tets), interior vertices perturbed by up
+to 0.1 h (seeded), f with N(0,1) CG_6 coefficients per Cartesian component,
+FP64 operator with FP32 patch solves, rtol 1e-8.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: space, p, cubes per edge, perturbation, rhs seed, precond precision, nrhs
+    "hcurl_ned1_p6_n8": dict(space="N1curl", p=6, n=8, amp=0.1, prec=1, nrhs=1,
+                             label="H(curl) Ned1_6 on 8^3 x 6 tets, perturbed 0.1h, FP64 apply + FP32 precond"),
+    "hgrad_cg3_n4": dict(space="CG", p=3, n=4, amp=0.0, prec=0, nrhs=1,
+                         label="H(grad) CG_3 on 4^3 x 6 tets, FP64"),
+    "hdiv_rt8_n16": dict(space="RT", p=8, n=16, amp=0.1, prec=1, nrhs=1,
+                         label="H(div) RT_8 on 16^3 x 6 tets, perturbed 0.1h, FP64 apply + FP32 precond"),
+}
+DEFAULT = "hcurl_ned1_p6_n8"
+METRIC = "DOFs/s solved to 1e-8 rel. residual"
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, the profiling recipe's nominal figure
+# CPU sample for the oracle: same space, degree, perturbation and RHS recipe on 3^3 x 6 tets
+CPU_SAMPLE_N = 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_pass(space, p, n, amp, seed=1):
+    """One pass of the oracle (assembly, load, preconditioner setup, PCG); returns (N, seconds, iters)."""
+    import numpy as np
+    from oracle import assemble as asm
+    from oracle.mesh import MeshDofs
+    from oracle.refelem import reference_element
+    from paper_2506_17406_gb300.inputs import kuhn_mesh, normal_coeffs
+    ref = reference_element(space, p)
+    cg = reference_element("CG", p)
+    verts, cells = kuhn_mesh(n, amp, seed)
+    t0 = time.perf_counter()
+    md = MeshDofs(verts, cells, ref)
+    mcg = MeshDofs(verts, cells, cg)
+    A = asm.assemble(md, asm.element_matrices(ref, verts, cells))
+    f = normal_coeffs((1 if space == "CG" else 3, mcg.ndofs), 2)
+    b = asm.load_cg_field(ref, md, cg, mcg, f)
+    P = asm.Preconditioner(A, md)
+    x, it, rr = asm.pcg(A, b, P.apply, rtol=1e-8)
+    dt = time.perf_counter() - t0
+    assert rr <= 1e-8 * 1.001, rr
+    return md.ndofs, dt, it
+
+
+def cpu_baseline(wl):
+    N, dt, it = oracle_pass(wl["space"], wl["p"], CPU_SAMPLE_N, wl["amp"])
+    return {"value": N / dt, "unit": "DOFs/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%s p=%d on %d^3 x 6 tets (N=%d, same perturbation and RHS recipe), one full oracle pass "
+                      "(numbering, quadrature assembly, load, patch Cholesky, PCG to 1e-8): %.1f s, %d iterations; "
+                      "BLAS threads at library default" % (wl["space"], wl["p"], CPU_SAMPLE_N, N, dt, it)}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_pass(wl["space"], wl["p"], CPU_SAMPLE_N, wl["amp"])
+    tot, N = 0.0, 0
+    for _ in range(args.steps):
+        N, dt, _ = oracle_pass(wl["space"], wl["p"], CPU_SAMPLE_N, wl["amp"])
+        tot += dt
+    value = N * args.steps / tot
+    cb = {"value": value, "unit": "DOFs/s", "cores": os.cpu_count(), "kind": "oracle",
+          "sample": "%s p=%d on %d^3 x 6 tets (N=%d): full oracle pass per step" % (wl["space"], wl["p"],
+                                                                                 CPU_SAMPLE_N, N)}
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOFs/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": wl["label"], "cpu_sample_cubes_per_edge": CPU_SAMPLE_N},
+           "cpu_baseline": cb,
+           "e2e": {"value": value, "unit": "DOFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def patch_flops_bytes(s):
+    """Algorithmic FP64 Cholesky flops (sum n^3/3) and factor entries from the patch map."""
+    import numpy as np
+    off, _ = s.patch_map()
+    n = np.diff(off).astype(np.float64)
+    return float(np.sum(n ** 3 / 3.0)), float(np.sum(n * (n + 1) / 2.0)), float(np.sum(n))
+
+
+def main():
+    args = parse()
+    wl = dict(WORKLOADS[args.workload])
+    if args.precision == "fp64":
+        wl["prec"] = 0
+    elif args.precision == "mixed":
+        wl["prec"] = 1
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, wl, rank, world)
+
+    import numpy as np
+    import torch
+    from paper_2506_17406_gb300 import riesz as rz
+    from paper_2506_17406_gb300.inputs import kuhn_mesh, normal_coeffs
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    verts, cells = kuhn_mesh(wl["n"], wl["amp"], seed=1 + rank)
+    s = rz.Riesz(wl["space"], wl["p"], verts, cells, precond_precision=wl["prec"], nrhs_max=1)
+    stream = torch.cuda.current_stream()
+    verts_d = torch.tensor(verts, device="cuda")
+    ncomp = 1 if wl["space"] == "CG" else 3
+    fcg_h = normal_coeffs((ncomp, s.n_cg), 2 + rank)
+    fcg = torch.tensor(fcg_h, device="cuda")
+    b = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    iters = []
+
+    def step():
+        s.update_geometry(verts_d)
+        s.load(fcg, b)
+        x.zero_()
+        it, rr, _ = s.solve(b, x)
+        iters.append(int(it[0]))
+        return rr[0]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = s.stats()["launches"]
+    s.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    relres = 0.0
+    for _ in range(args.steps):
+        relres = max(relres, step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    prof = s.profile_read()
+    s.profile(False)
+    launches = s.stats()["launches"] - launches0
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        nt = torch.tensor([float(s.N)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(nt)
+        ntot = float(nt.item())
+    else:
+        ntot = float(s.N)
+    value = ntot * args.steps / (ms / 1e3)
+
+    # setup / solve split from the profiler (kernel time only)
+    setup_kinds = ["geom", "elem", "diag", "assemble", "cholesky", "to_f32"]
+    k_ms = {k: v[0] / args.steps for k, v in prof.items()}
+    # dominant kernel and its roofline
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / max(1, prof[dom][1])
+    chol_flops, fentries, psum = patch_flops_bytes(s)
+    n = s.nref
+    C = s.ncells
+    fbytes = 4 if wl["prec"] == 1 else 8
+    peak_hbm = 6701.5
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak_hbm = float(peaks.get("hbm_gbs", peak_hbm))
+    except Exception:
+        pass
+    if dom == "cholesky":
+        achieved = chol_flops / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": "k_cholesky",
+                "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s)",
+                "algorithmic": "sum over patches n_V^3/3 = %.3e flop per launch" % chol_flops}
+    elif dom == "patch_solve":
+        byt = 2 * fentries * fbytes + psum * (4 + 8 + 8)
+        achieved = byt / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                "frac": achieved / peak_hbm, "traffic": None, "kernel": "k_patch_solve",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                "algorithmic": "2 sweeps x %.3e factor bytes + patch vectors = %.3e B per launch"
+                               % (fentries * fbytes, byt)}
+    else:
+        byt = C * n * n * 8.0 + C * n * 12.0 + s.N * 16.0
+        achieved = byt / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                "frac": achieved / peak_hbm, "traffic": None, "kernel": dom,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                "algorithmic": "element matrices + gathered vectors = %.3e B per launch" % byt}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        verts_pin = torch.tensor(verts).pin_memory()
+        fcg_pin = torch.tensor(fcg_h).pin_memory()
+        x_pin = torch.zeros(s.N, dtype=torch.float64).pin_memory()
+        h2d = verts_pin.numel() * 8 + fcg_pin.numel() * 8
+        d2h = s.N * 8
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            verts_d.copy_(verts_pin, non_blocking=True)
+            fcg.copy_(fcg_pin, non_blocking=True)
+            s.update_geometry(verts_d)
+            s.load(fcg, b)
+            x.zero_()
+            s.solve(b, x)
+            x_pin.copy_(x, non_blocking=True)
+            torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": float(s.N) * args.steps / te, "unit": "DOFs/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(wl)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "DOFs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl["prec"] == 0 else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": wl["label"], "space": wl["space"], "p": wl["p"], "cells": C, "dofs": s.N,
+                       "nrhs": 1, "rtol": 1e-8, "step": "device setup + load + PCG solve",
+                       "l2": "inputs larger than L2 (element matrices and patch factors)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "iterations": statistics.median(iters[-args.steps:]), "max_relres": relres,
+            "setup_kernel_ms": sum(k_ms[k] for k in setup_kinds),
+            "solve_kernel_ms": sum(v for k, v in k_ms.items() if k not in setup_kinds),
+            "kernel_ms_per_step": {k: round(v, 4) for k, v in k_ms.items() if v > 0},
+            "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

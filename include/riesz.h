@@ -153,10 +153,43 @@ int riesz_num_cg_dofs(const riesz_handle* h, int64_t* n_cg);
    3 otherwise).  b: device [N]. */
 int riesz_load(riesz_handle* h, const double* fcg, double* b, void* stream);
 
+/* Recompute the device setup (geometric factors, element matrices, interior
+   diagonal, patch assembly and Cholesky) for new vertex coordinates of the
+   same mesh topology.  verts: device [nverts][3] FP64 (copied).  Use after a
+   mesh moves, or to time the device setup from resident data. */
+int riesz_update_geometry(riesz_handle* h, const double* verts, void* stream);
+
+/* Kernel kinds reported by the profiler. */
+enum {
+  RIESZ_K_GEOM = 0,         /* a1 geometric factors                      */
+  RIESZ_K_ELEM = 1,         /* element matrices A_T = sum_q g_q R_q      */
+  RIESZ_K_DIAG = 2,         /* a6 interior diagonal                      */
+  RIESZ_K_ASSEMBLE = 3,     /* a8 patch assembly                         */
+  RIESZ_K_CHOLESKY = 4,     /* a8 batched FP64 Cholesky                  */
+  RIESZ_K_TO_F32 = 5,       /* FP64 -> FP32 factor copy                  */
+  RIESZ_K_APPLY = 6,        /* a3-a4 gather + contraction                */
+  RIESZ_K_GATHER = 7,       /* a5 deterministic interface scatter        */
+  RIESZ_K_PATCH_SOLVE = 8,  /* a7 patch triangular sweeps                */
+  RIESZ_K_PRECOND_GATHER = 9, /* a6 Jacobi + a7 patch-result sum         */
+  RIESZ_K_DOT = 10,         /* a9 dot-product partial sums               */
+  RIESZ_K_SCALAR = 11,      /* a9 reduction finish + scalar update       */
+  RIESZ_K_UPDATE = 12,      /* a9 vector updates                         */
+  RIESZ_K_LOAD = 13,        /* right-hand side assembly                  */
+  RIESZ_NKIND = 14
+};
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around
+   every kernel of the handle.  enable != 0 turns it on and clears the
+   accumulators; riesz_profile_read synchronises the recorded events and
+   returns the summed milliseconds and launch counts per kind (arrays of
+   RIESZ_NKIND entries, either may be NULL). */
+int riesz_profile(riesz_handle* h, int enable);
+int riesz_profile_read(riesz_handle* h, double* ms, int64_t* counts);
+
 /* Timings (ms) and sizes of the last setup / solve:
    out[0] setup host ms, out[1] setup device ms, out[2] device bytes held,
    out[3] patch factor bytes, out[4] last solve iterations (rhs 0),
-   out[5] kernels launched by the last riesz_solve. */
+   out[5] kernels launched by the handle since riesz_create. */
 int riesz_stats(const riesz_handle* h, double* out);
 
 int riesz_destroy(riesz_handle* h);

@@ -63,8 +63,10 @@ def element_matrices(ref, verts, cells, alpha=1.0, beta=1.0, chunk=256):
     for s in range(0, nc, chunk):
         v, d, det = physical_tabulation(ref, J[s:s + chunk], vhat, dhat)
         wq = w[None, :] * np.abs(det)[:, None]
-        out[s:s + chunk] = (beta * np.einsum("epia,epja,ep->eij", v, v, wq)
-                            + alpha * np.einsum("epia,epja,ep->eij", d, d, wq))
+        vw = v * wq[:, :, None, None]
+        dw = d * wq[:, :, None, None]
+        out[s:s + chunk] = (beta * np.einsum("epia,epja->eij", vw, v, optimize=True)
+                            + alpha * np.einsum("epia,epja->eij", dw, d, optimize=True))
     return out
 
 

@@ -94,6 +94,13 @@ struct riesz_handle {
   double* h_scal = nullptr;  // pinned
   int last_iters = 0;
   int64_t launches = 0;
+  // per-kernel CUDA-event profiler (riesz_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> prof_pending;  // (kind, first event index)
+  double prof_ms[RIESZ_NKIND] = {0};
+  int64_t prof_cnt[RIESZ_NKIND] = {0};
   int64_t N() const { return mesh.ndofs; }
   int64_t C() const { return mesh.ncells; }
   size_t device_bytes() const {
@@ -117,7 +124,10 @@ struct riesz_handle {
     h_scal = nullptr;
     on_device = false;
   }
-  ~riesz_handle() { free_device(); }
+  ~riesz_handle() {
+    free_device();
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
 };
 
 namespace {
@@ -141,6 +151,42 @@ int guarded(F&& f) {
 
 void need(bool ok, const char* msg, int code = RIESZ_ERR_INVALID_ARG) {
   if (!ok) throw Err(code, msg);
+}
+
+// Launch a kernel (callable f) of the given kind on stream s; with the
+// profiler on, bracket it with a pair of pooled CUDA events.
+template <typename F>
+void launch(riesz_handle& h, int kind, cudaStream_t s, F&& f) {
+  size_t e = 0;
+  if (h.prof) {
+    while (h.ev_pool.size() < h.ev_used + 2) {
+      cudaEvent_t ev;
+      CK(cudaEventCreate(&ev));
+      h.ev_pool.push_back(ev);
+    }
+    e = h.ev_used;
+    h.ev_used += 2;
+    CK(cudaEventRecord(h.ev_pool[e], s));
+  }
+  f();
+  CK(cudaGetLastError());
+  ++h.launches;
+  if (h.prof) {
+    CK(cudaEventRecord(h.ev_pool[e + 1], s));
+    h.prof_pending.push_back({kind, e});
+  }
+}
+
+void prof_collect(riesz_handle& h) {
+  for (auto& pe : h.prof_pending) {
+    CK(cudaEventSynchronize(h.ev_pool[pe.second + 1]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h.ev_pool[pe.second], h.ev_pool[pe.second + 1]));
+    h.prof_ms[pe.first] += ms;
+    h.prof_cnt[pe.first] += 1;
+  }
+  h.prof_pending.clear();
+  h.ev_used = 0;
 }
 
 // reference edge matrix inverse (columns V1-V0, V2-V0, V3-V0 of the reference tetrahedron)
@@ -269,18 +315,22 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
   const int64_t C = h.C(), N = h.N();
   if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     const size_t sm = (size_t)n * nrhs * sizeof(double);
-    dev::k_apply_elem<<<(unsigned)C, dev::NT, sm, s>>>(C, n, h.nif, h.d_Ae.p, h.d_cdofs.p, x, y, h.d_Ycell.p, nrhs, N);
+    launch(h, RIESZ_K_APPLY, s, [&] {
+      dev::k_apply_elem<<<(unsigned)C, dev::NT, sm, s>>>(C, n, h.nif, h.d_Ae.p, h.d_cdofs.p, x, y, h.d_Ycell.p, nrhs, N);
+    });
   } else {
     const size_t sm = ((size_t)n + h.ref->Q) * dev::TC * sizeof(double);
     dim3 grid(nblk(C, dev::TC), nrhs);
-    dev::k_apply_mf<<<grid, dev::NT, sm, s>>>(C, n, h.nif, h.ref->Q, h.d_R.p, h.d_g.p, h.d_cdofs.p, x, y, h.d_Ycell.p, N);
+    launch(h, RIESZ_K_APPLY, s, [&] {
+      dev::k_apply_mf<<<grid, dev::NT, sm, s>>>(C, n, h.nif, h.ref->Q, h.d_R.p, h.d_g.p, h.d_cdofs.p, x, y, h.d_Ycell.p,
+                                               N);
+    });
   }
-  KCHECK();
   const int64_t nI = h.mesh.n_interface;
-  dev::k_gather_iface<<<nblk(nI, 256), 256, 0, s>>>(nI, h.d_sc_ptr.p, h.d_sc_pos.p, h.d_Ycell.p, (int64_t)h.nif * C, y, N,
-                                                   nrhs);
-  KCHECK();
-  h.launches += 2;
+  launch(h, RIESZ_K_GATHER, s, [&] {
+    dev::k_gather_iface<<<nblk(nI, 256), 256, 0, s>>>(nI, h.d_sc_ptr.p, h.d_sc_pos.p, h.d_Ycell.p, (int64_t)h.nif * C, y,
+                                                     N, nrhs);
+  });
 }
 
 void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStream_t s) {
@@ -291,27 +341,26 @@ void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStrea
   if (npatch) {
     dim3 grid(npatch, nrhs);
     if (h.opts.precond_precision == RIESZ_PREC_FP32) {
-      dev::k_patch_solve<float><<<grid, dev::NT, (size_t)nmax * sizeof(float), s>>>(
-          h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdofs.p, h.d_L32.p, r, h.d_zpatch.p, N, zstride);
+      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
+        dev::k_patch_solve<float><<<grid, dev::NT, (size_t)nmax * sizeof(float), s>>>(
+            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdofs.p, h.d_L32.p, r, h.d_zpatch.p, N, zstride);
+      });
     } else {
-      dev::k_patch_solve<double><<<grid, dev::NT, (size_t)nmax * sizeof(double), s>>>(
-          h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdofs.p, h.d_L64.p, r, h.d_zpatch.p, N, zstride);
+      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
+        dev::k_patch_solve<double><<<grid, dev::NT, (size_t)nmax * sizeof(double), s>>>(
+            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdofs.p, h.d_L64.p, r, h.d_zpatch.p, N, zstride);
+      });
     }
-    KCHECK();
-    h.launches += 1;
   }
-  dev::k_precond_gather<<<nblk(N, 256), 256, 0, s>>>(N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p,
-                                                    zstride, h.d_dinv.p, r, z, nrhs);
-  KCHECK();
-  h.launches += 1;
+  launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
+    dev::k_precond_gather<<<nblk(N, 256), 256, 0, s>>>(N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p,
+                                                      zstride, h.d_dinv.p, r, z, nrhs);
+  });
 }
 
 void dot(riesz_handle& h, const double* a, const double* b, const double* c, int op, double* scal, cudaStream_t s) {
-  dev::k_dot2<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(h.N(), a, b, c, h.d_part.p);
-  KCHECK();
-  dev::k_scalar<<<1, dev::NT, 0, s>>>(h.d_part.p, op, scal);
-  KCHECK();
-  h.launches += 2;
+  launch(h, RIESZ_K_DOT, s, [&] { dev::k_dot2<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(h.N(), a, b, c, h.d_part.p); });
+  launch(h, RIESZ_K_SCALAR, s, [&] { dev::k_scalar<<<1, dev::NT, 0, s>>>(h.d_part.p, op, scal); });
 }
 
 void read_scal(riesz_handle& h, const double* scal, cudaStream_t s) {
@@ -327,11 +376,10 @@ int pcg_one(riesz_handle& h, const double* b, double* x, cudaStream_t s, int* it
   CK(cudaMemsetAsync(scal, 0, 16 * sizeof(double), s));
   auto residual = [&]() {  // r = b - A x, RR
     op_apply(h, x, h.d_Ap.p, 1, s);
-    dev::k_residual<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, b, h.d_Ap.p, h.d_r.p, h.d_part.p);
-    KCHECK();
-    dev::k_scalar<<<1, dev::NT, 0, s>>>(h.d_part.p, 1, scal);
-    KCHECK();
-    h.launches += 2;
+    launch(h, RIESZ_K_UPDATE, s, [&] {
+      dev::k_residual<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, b, h.d_Ap.p, h.d_r.p, h.d_part.p);
+    });
+    launch(h, RIESZ_K_SCALAR, s, [&] { dev::k_scalar<<<1, dev::NT, 0, s>>>(h.d_part.p, 1, scal); });
   };
   auto restart = [&]() {  // z = P r, p = z, RZ
     op_precond(h, h.d_r.p, h.d_z.p, 1, s);
@@ -358,11 +406,10 @@ int pcg_one(riesz_handle& h, const double* b, double* x, cudaStream_t s, int* it
     while (it < h.opts.maxit) {
       op_apply(h, h.d_p.p, h.d_Ap.p, 1, s);
       dot(h, h.d_p.p, h.d_Ap.p, nullptr, 0, scal, s);
-      dev::k_update_xr<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, scal, x, h.d_r.p, h.d_p.p, h.d_Ap.p, h.d_part.p);
-      KCHECK();
-      dev::k_scalar<<<1, dev::NT, 0, s>>>(h.d_part.p, 1, scal);
-      KCHECK();
-      h.launches += 2;
+      launch(h, RIESZ_K_UPDATE, s, [&] {
+        dev::k_update_xr<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, scal, x, h.d_r.p, h.d_p.p, h.d_Ap.p, h.d_part.p);
+      });
+      launch(h, RIESZ_K_SCALAR, s, [&] { dev::k_scalar<<<1, dev::NT, 0, s>>>(h.d_part.p, 1, scal); });
       ++it;
       read_scal(h, scal, s);
       if (h.h_scal[dev::S_NONFINITE] != 0.0 || !std::isfinite(h.h_scal[dev::S_RR])) {
@@ -382,9 +429,7 @@ int pcg_one(riesz_handle& h, const double* b, double* x, cudaStream_t s, int* it
       }
       op_precond(h, h.d_r.p, h.d_z.p, 1, s);
       dot(h, h.d_r.p, h.d_z.p, flex ? h.d_zold.p : nullptr, flex ? 3 : 2, scal, s);
-      dev::k_update_p<<<1184, 256, 0, s>>>(N, scal, h.d_z.p, h.d_p.p);
-      KCHECK();
-      h.launches += 1;
+      launch(h, RIESZ_K_UPDATE, s, [&] { dev::k_update_p<<<1184, 256, 0, s>>>(N, scal, h.d_z.p, h.d_p.p); });
       if (flex) CK(cudaMemcpyAsync(h.d_zold.p, h.d_z.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     if (status == RIESZ_ERR_NOT_CONVERGED) {
@@ -399,8 +444,64 @@ int pcg_one(riesz_handle& h, const double* b, double* x, cudaStream_t s, int* it
   return status;
 }
 
+// Device setup from resident maps and vertex coordinates: a1 geometry,
+// element matrices, a6 interior diagonal, a8 patch assembly + Cholesky.
+void device_compute(riesz_handle& h, cudaStream_t s) {
+  const RefElement& R = *h.ref;
+  const MeshMaps& M = h.mesh;
+  const int n = M.nref;
+  const int64_t C = M.ncells;
+  const int npatch = (int)h.p_n.size();
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  launch(h, RIESZ_K_GEOM, s, [&] {
+    dev::k_geom<<<nblk(C, 128), 128, 0, s>>>(h.space, C, h.d_verts.p, h.d_cells.p, ref_edge_inverse(), h.d_g.p,
+                                              h.d_jac.p);
+  });
+  if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT)
+    launch(h, RIESZ_K_ELEM, s, [&] {
+      dev::k_elem_matrices<<<(unsigned)C, 256, 0, s>>>(C, n, R.Q, h.d_g.p, h.d_R.p, h.d_Ae.p);
+    });
+  if (M.n_interior > 0) {
+    const int64_t cnt = C * (int64_t)(n - h.nif);
+    launch(h, RIESZ_K_DIAG, s, [&] {
+      dev::k_interior_diag<<<nblk(cnt, 256), 256, 0, s>>>(C, n, h.nif, R.Q, h.d_g.p, h.d_R.p, h.d_cdofs.p,
+                                                         M.n_interface, h.d_dinv.p);
+    });
+  }
+  CK(cudaMemsetAsync(h.d_info.p, 0, sizeof(int) * std::max(1, npatch), s));
+  if (npatch) {
+    launch(h, RIESZ_K_ASSEMBLE, s, [&] {
+      dev::k_patch_assemble<<<npatch, 256, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pb_ptr.p, h.d_pb_cell.p, h.d_pb_off.p,
+                                                   h.d_pb_ent.p, C, n, R.Q, h.d_g.p, h.d_R.p, h.d_Ae.p, h.d_L64.p);
+    });
+    launch(h, RIESZ_K_CHOLESKY, s, [&] {
+      dev::k_cholesky<<<npatch, dev::NT, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_L64.p, h.d_info.p);
+    });
+    if (h.opts.precond_precision == RIESZ_PREC_FP32)
+      launch(h, RIESZ_K_TO_F32, s, [&] {
+        dev::k_to_f32<<<1184, 256, 0, s>>>(h.factor_entries, h.d_L64.p, h.d_L32.p);
+      });
+  }
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  h.setup_dev_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (npatch) {
+    std::vector<int> info(npatch);
+    CK(cudaMemcpyAsync(info.data(), h.d_info.p, sizeof(int) * npatch, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int P = 0; P < npatch; ++P)
+      if (info[P]) throw Err(RIESZ_ERR_INTERNAL, "patch matrix not positive definite");
+  }
+}
+
 void setup_device_impl(riesz_handle& h, cudaStream_t s) {
-  auto t0 = std::chrono::steady_clock::now();
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) throw Err(RIESZ_ERR_CUDA, "no CUDA device");
   CK(cudaGetDevice(&h.device));
@@ -437,17 +538,10 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   h.d_part.alloc(2 * dev::RED_BLOCKS);
   h.d_scal.alloc(16 * (size_t)nrhs);
   CK(cudaMallocHost((void**)&h.h_scal, 16 * sizeof(double)));
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  CK(cudaEventRecord(e0, s));
-  // a1 geometry
-  dev::k_geom<<<nblk(C, 128), 128, 0, s>>>(h.space, C, h.d_verts.p, h.d_cells.p, ref_edge_inverse(), h.d_g.p, h.d_jac.p);
-  KCHECK();
+  const int npatch = (int)h.p_n.size();
+  h.d_info.alloc(std::max(1, npatch));
   if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     h.d_Ae.alloc((size_t)C * n * n);
-    dev::k_elem_matrices<<<(unsigned)C, 256, 0, s>>>(C, n, R.Q, h.d_g.p, h.d_R.p, h.d_Ae.p);
-    KCHECK();
   } else {
     const size_t sm = ((size_t)n + R.Q) * dev::TC * sizeof(double);
     CK(cudaFuncSetAttribute(dev::k_apply_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -457,51 +551,17 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     if (sm > 48 * 1024)
       CK(cudaFuncSetAttribute(dev::k_apply_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   }
-  // a6 interior diagonal
-  if (M.n_interior > 0) {
-    const int64_t cnt = C * (int64_t)(n - h.nif);
-    dev::k_interior_diag<<<nblk(cnt, 256), 256, 0, s>>>(C, n, h.nif, R.Q, h.d_g.p, h.d_R.p, h.d_cdofs.p, M.n_interface,
-                                                       h.d_dinv.p);
-    KCHECK();
-  }
-  // a8 patch assembly + Cholesky
-  const int npatch = (int)h.p_n.size();
-  h.d_info.alloc(std::max(1, npatch));
-  CK(cudaMemsetAsync(h.d_info.p, 0, sizeof(int) * std::max(1, npatch), s));
   if (npatch) {
     h.d_L64.alloc((size_t)h.factor_entries);
-    dev::k_patch_assemble<<<npatch, 256, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pb_ptr.p, h.d_pb_cell.p, h.d_pb_off.p,
-                                                 h.d_pb_ent.p, C, n, R.Q, h.d_g.p, h.d_R.p, h.d_Ae.p, h.d_L64.p);
-    KCHECK();
-    dev::k_cholesky<<<npatch, dev::NT, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_L64.p, h.d_info.p);
-    KCHECK();
-    if (h.opts.precond_precision == RIESZ_PREC_FP32) {
-      h.d_L32.alloc((size_t)h.factor_entries);
-      dev::k_to_f32<<<1184, 256, 0, s>>>(h.factor_entries, h.d_L64.p, h.d_L32.p);
-      KCHECK();
-    }
-  }
-  CK(cudaEventRecord(e1, s));
-  CK(cudaEventSynchronize(e1));
-  float ms = 0.f;
-  CK(cudaEventElapsedTime(&ms, e0, e1));
-  h.setup_dev_ms = ms;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (npatch) {
-    std::vector<int> info(npatch);
-    CK(cudaMemcpy(info.data(), h.d_info.p, sizeof(int) * npatch, cudaMemcpyDeviceToHost));
-    for (int P = 0; P < npatch; ++P)
-      if (info[P]) throw Err(RIESZ_ERR_INTERNAL, "patch matrix not positive definite");
-    if (h.opts.precond_precision == RIESZ_PREC_FP32) h.d_L64.free();
+    if (h.opts.precond_precision == RIESZ_PREC_FP32) h.d_L32.alloc((size_t)h.factor_entries);
   }
   const size_t smp = (size_t)(h.p_n.empty() ? 0 : h.p_n[0]) * sizeof(double);
   if (smp > 48 * 1024) {
     CK(cudaFuncSetAttribute(dev::k_patch_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
     CK(cudaFuncSetAttribute(dev::k_patch_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
   }
+  device_compute(h, s);
   h.on_device = true;
-  (void)t0;
 }
 
 void check_dev(const riesz_handle* h) {
@@ -650,7 +710,6 @@ int riesz_solve(riesz_handle* h, const double* b, double* x, int nrhs, void* str
   int rc = guarded([&] {
     check_dev(h);
     need(b && x && nrhs >= 1, "bad solve arguments");
-    h->launches = 0;
     const int64_t N = h->N();
     for (int r = 0; r < nrhs; ++r) {
       int st = pcg_one(*h, b + r * N, x + r * N, S(stream), iters ? iters + r : nullptr, relres ? relres + r : nullptr);
@@ -672,7 +731,6 @@ int riesz_solve_host(riesz_handle* h, const double* b_host, double* x_host, int 
     double* dx = h->d_xh.p;   // staging of x
     CK(cudaMemcpyAsync(db, b_host, (size_t)N * nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(dx, x_host, (size_t)N * nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
-    h->launches = 0;
     for (int r = 0; r < nrhs; ++r) {
       int st = pcg_one(*h, db + r * N, dx + r * N, s, iters ? iters + r : nullptr, relres ? relres + r : nullptr);
       if (st != RIESZ_OK && status == RIESZ_OK) status = st;
@@ -692,13 +750,48 @@ int riesz_load(riesz_handle* h, const double* fcg, double* b, void* stream) {
     const int ncomp = (h->space == RIESZ_H1) ? 1 : 3;
     const size_t sm = (size_t)ncomp * h->refcg->nref * sizeof(double);
     cudaStream_t s = S(stream);
-    dev::k_load<<<(unsigned)C, 256, sm, s>>>(h->space, C, n, h->nif, h->refcg->nref, h->d_jac.p, h->d_cgdofs.p, fcg,
-                                           h->meshcg.ndofs, h->d_X.p, h->d_cdofs.p, b, h->d_Ycell.p);
-    KCHECK();
+    launch(*h, RIESZ_K_LOAD, s, [&] {
+      dev::k_load<<<(unsigned)C, 256, sm, s>>>(h->space, C, n, h->nif, h->refcg->nref, h->d_jac.p, h->d_cgdofs.p, fcg,
+                                             h->meshcg.ndofs, h->d_X.p, h->d_cdofs.p, b, h->d_Ycell.p);
+    });
     const int64_t nI = h->mesh.n_interface;
-    dev::k_gather_iface<<<nblk(nI, 256), 256, 0, s>>>(nI, h->d_sc_ptr.p, h->d_sc_pos.p, h->d_Ycell.p,
-                                                     (int64_t)h->nif * C, b, N, 1);
-    KCHECK();
+    launch(*h, RIESZ_K_GATHER, s, [&] {
+      dev::k_gather_iface<<<nblk(nI, 256), 256, 0, s>>>(nI, h->d_sc_ptr.p, h->d_sc_pos.p, h->d_Ycell.p,
+                                                       (int64_t)h->nif * C, b, N, 1);
+    });
+  });
+}
+
+int riesz_update_geometry(riesz_handle* h, const double* verts, void* stream) {
+  return guarded([&] {
+    check_dev(h);
+    need(verts != nullptr, "null vertex array");
+    cudaStream_t s = S(stream);
+    CK(cudaMemcpyAsync(h->d_verts.p, verts, h->d_verts.bytes(), cudaMemcpyDeviceToDevice, s));
+    device_compute(*h, s);
+  });
+}
+
+int riesz_profile(riesz_handle* h, int enable) {
+  return guarded([&] {
+    need(h != nullptr, "null handle");
+    if (!h->prof_pending.empty()) prof_collect(*h);
+    h->prof = enable != 0;
+    for (int k = 0; k < RIESZ_NKIND; ++k) {
+      h->prof_ms[k] = 0.0;
+      h->prof_cnt[k] = 0;
+    }
+  });
+}
+
+int riesz_profile_read(riesz_handle* h, double* ms, int64_t* counts) {
+  return guarded([&] {
+    need(h != nullptr, "null handle");
+    prof_collect(*h);
+    for (int k = 0; k < RIESZ_NKIND; ++k) {
+      if (ms) ms[k] = h->prof_ms[k];
+      if (counts) counts[k] = h->prof_cnt[k];
+    }
   });
 }
 

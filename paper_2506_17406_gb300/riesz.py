@@ -18,6 +18,9 @@ SPACES = {"CG": H1, "H1": H1, "N1curl": HCURL, "HCURL": HCURL, "RT": HDIV, "HDIV
 PREC_FP64, PREC_FP32 = 0, 1
 APPLY_MATRIX_FREE, APPLY_ELEMENT = 0, 1
 
+KINDS = ["geom", "elem", "diag", "assemble", "cholesky", "to_f32", "apply", "gather", "patch_solve",
+         "precond_gather", "dot", "scalar", "update", "load"]
+
 ERRORS = {1: "INVALID_ARG", 2: "BAD_MESH", 3: "OOM", 4: "NOT_CONVERGED", 5: "NONFINITE", 6: "CUDA",
           7: "INTERNAL", 8: "NO_DEVICE"}
 
@@ -57,6 +60,9 @@ _SIGS = {
     "riesz_solve_host": (_I, [_P, _P, _P, _I, _P, _P, _P]),
     "riesz_load": (_I, [_P, _P, _P, _P]),
     "riesz_stats": (_I, [_P, _P]),
+    "riesz_update_geometry": (_I, [_P, _P, _P]),
+    "riesz_profile": (_I, [_P, _I]),
+    "riesz_profile_read": (_I, [_P, _P, _P]),
     "riesz_destroy": (_I, [_P]),
 }
 
@@ -205,6 +211,18 @@ class Riesz:
         if check:
             _check(rc)
         return iters, relres, rc
+
+    def update_geometry(self, verts_dev, stream=None):
+        _check(self.lib.riesz_update_geometry(self.h, _ptr(verts_dev), _stream(stream)))
+
+    def profile(self, enable=True):
+        _check(self.lib.riesz_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        ms = np.zeros(len(KINDS))
+        cnt = np.zeros(len(KINDS), dtype=np.int64)
+        _check(self.lib.riesz_profile_read(self.h, _ptr(ms), _ptr(cnt)))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KINDS)}
 
     def load(self, fcg, b, stream=None):
         _check(self.lib.riesz_load(self.h, _ptr(fcg), _ptr(b), _stream(stream)))
