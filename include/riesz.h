@@ -189,7 +189,10 @@ int riesz_profile_read(riesz_handle* h, double* ms, int64_t* counts);
 /* Timings (ms) and sizes of the last setup / solve:
    out[0] setup host ms, out[1] setup device ms, out[2] device bytes held,
    out[3] patch factor bytes, out[4] last solve iterations (rhs 0),
-   out[5] kernels launched by the handle since riesz_create. */
+   out[5] kernels launched by the handle since riesz_create,
+   out[6] flops of one tile-sparse patch Cholesky pass (all patches),
+   out[7] bytes one riesz_precond call reads and writes for the patch sweeps
+          (stored factor tiles and diagonal inverses twice, patch vectors). */
 int riesz_stats(const riesz_handle* h, double* out);
 
 int riesz_destroy(riesz_handle* h);

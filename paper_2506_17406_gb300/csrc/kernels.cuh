@@ -6,7 +6,7 @@
 //   R          f64   [Q][n][n]   reference matrices (L2-resident)
 //   Ae         f64   [C][n][n]   optional stored element matrices
 //   Ycell      f64   [nrhs][n_if][C]  per-cell interface results before the scatter
-//   patches    packed lower-triangular row-major factors, one CTA per patch
+//   patches    lower triangle in contiguous 32x32 tiles + inverted diagonal tiles, one CTA per patch
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -16,6 +16,7 @@ namespace dev {
 
 constexpr int NT = 256;   // threads per CTA for the per-patch / per-cell kernels
 constexpr int NB = 32;    // Cholesky / triangular-sweep block size
+constexpr int MAXNB = 128;  // largest patch: 128 blocks of 32 DOFs
 
 __device__ __forceinline__ int64_t tri(int64_t i, int64_t j) { return i * (i + 1) / 2 + j; }
 
@@ -112,7 +113,9 @@ __global__ void k_elem_matrices(int64_t C, int n, int Q, const double* __restric
 // a3-a5: apply.  Gather x on the cell, y_T = A_T x_T, interior rows written
 // directly (each interior DOF belongs to one cell), interface rows to Ycell.
 // ---------------------------------------------------------------------------
-// Element-matrix variant: one CTA per cell, one warp per row (lanes over j).
+// Element-matrix variant: one CTA per cell, one thread per row i.  A_T is
+// symmetric, so y_i = sum_j A_T[j][i] x_j: for each j the threads read the
+// contiguous row j of A_T (coalesced) against a shared-memory x_j.
 __global__ void k_apply_elem(int64_t C, int n, int nif, const double* __restrict__ Ae,
                              const int32_t* __restrict__ cdofs, const double* __restrict__ x, double* __restrict__ y,
                              double* __restrict__ Ycell, int nrhs, int64_t N) {
@@ -124,19 +127,35 @@ __global__ void k_apply_elem(int64_t C, int n, int nif, const double* __restrict
   }
   __syncthreads();
   const double* A = Ae + c * (int64_t)n * n;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = warp; i < n; i += nw) {
-    const double* Ai = A + (int64_t)i * n;
-    for (int r = 0; r < nrhs; ++r) {
-      double s = 0.0;
-      const double* xr = xs + r * n;
-      for (int j = lane; j < n; j += 32) s += Ai[j] * xr[j];
-      s = warp_sum(s);
-      if (lane == 0) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int r0 = 0; r0 < nrhs; r0 += 4) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      const int nr = min(4, nrhs - r0);
+      int j = 0;
+      for (; j + 4 <= n; j += 4) {
+        const double a0 = A[(int64_t)j * n + i], a1 = A[(int64_t)(j + 1) * n + i];
+        const double a2 = A[(int64_t)(j + 2) * n + i], a3 = A[(int64_t)(j + 3) * n + i];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (k < nr) {
+            const double* xr = xs + (r0 + k) * n + j;
+            acc[k] = fma(a0, xr[0], acc[k]);
+            acc[k] = fma(a1, xr[1], acc[k]);
+            acc[k] = fma(a2, xr[2], acc[k]);
+            acc[k] = fma(a3, xr[3], acc[k]);
+          }
+        }
+      }
+      for (; j < n; ++j) {
+        const double a0 = A[(int64_t)j * n + i];
+        for (int k = 0; k < nr; ++k) acc[k] = fma(a0, xs[(r0 + k) * n + j], acc[k]);
+      }
+      for (int k = 0; k < nr; ++k) {
+        const int r = r0 + k;
         if (i >= nif)
-          y[r * N + cdofs[(int64_t)i * C + c]] = s;
+          y[r * N + cdofs[(int64_t)i * C + c]] = acc[k];
         else
-          Ycell[((int64_t)r * nif + i) * C + c] = s;
+          Ycell[((int64_t)r * nif + i) * C + c] = acc[k];
       }
     }
   }
@@ -238,23 +257,35 @@ __global__ void k_interior_diag(int64_t C, int n, int nif, int Q, const double* 
 }
 
 // ---------------------------------------------------------------------------
+// Patch matrices are stored tiled: the lower triangle of the (n x n) patch
+// matrix, padded to nb = ceil(n/32) blocks, as nb(nb+1)/2 contiguous 32x32
+// row-major tiles in block-row order (tile (I,J), J <= I, at index
+// I(I+1)/2 + J).  Padding rows/columns hold the identity.  Besides the factor
+// L, each patch keeps the inverses of its nb diagonal 32x32 blocks of L
+// (Dinv), so both triangular sweeps are block matrix-vector products.
+// ---------------------------------------------------------------------------
+
 // a8: patch assembly.  A_V = sum over star cells of the restriction of A_T.
 // Cells are processed one after the other (no two threads write the same
 // entry within a cell), so the sum order is fixed.
 // blocks of patch P: [pb_ptr[P], pb_ptr[P+1]); block b: cell pb_cell[b],
 // entries pb_ent[pb_off[b] .. pb_off[b+1]) = local j + 1024 * patch index.
-// ---------------------------------------------------------------------------
 __global__ void k_patch_assemble(const int32_t* __restrict__ pn, const int64_t* __restrict__ pfoff,
+                                 const int64_t* __restrict__ pmoff, const int32_t* __restrict__ meta,
                                  const int64_t* __restrict__ pb_ptr, const int32_t* __restrict__ pb_cell,
                                  const int64_t* __restrict__ pb_off, const int32_t* __restrict__ pb_ent,
                                  int64_t C, int n, int Q, const double* __restrict__ g, const double* __restrict__ R,
                                  const double* __restrict__ Ae, double* __restrict__ Lall) {
   const int P = blockIdx.x;
-  const int64_t np = pn[P];
+  const int np = pn[P];
+  const int nb = (np + 31) / 32;
+  const int32_t* tix = meta + pmoff[P];
   double* A = Lall + pfoff[P];
-  const int64_t ntri = np * (np + 1) / 2;
-  for (int64_t t = threadIdx.x; t < ntri; t += blockDim.x) A[t] = 0.0;
+  const int64_t ntot = (int64_t)(tix[(nb - 1) * nb + nb - 1] + 1) * 1024;
+  for (int64_t t = threadIdx.x; t < ntot; t += blockDim.x) A[t] = 0.0;
   __syncthreads();
+  for (int i = np + threadIdx.x; i < nb * 32; i += blockDim.x)
+    A[(int64_t)tix[(i >> 5) * nb + (i >> 5)] * 1024 + (i & 31) * 33] = 1.0;
   const int64_t nn = (int64_t)n * n;
   for (int64_t b = pb_ptr[P]; b < pb_ptr[P + 1]; ++b) {
     const int64_t c = pb_cell[b];
@@ -272,103 +303,124 @@ __global__ void k_patch_assemble(const int32_t* __restrict__ pn, const int64_t* 
         v = 0.0;
         for (int q = 0; q < Q; ++q) v += g[q * C + c] * R[q * nn + (int64_t)js * n + ju];
       }
-      A[tri(ps, pu)] += v;
+      A[(int64_t)tix[(ps >> 5) * nb + (pu >> 5)] * 1024 + (ps & 31) * 32 + (pu & 31)] += v;
     }
     __syncthreads();
   }
 }
 
-// ---------------------------------------------------------------------------
-// a8: batched FP64 Cholesky, one CTA per patch, in place on the packed lower
-// triangle (row-major).  Right-looking, NB-wide panels: factor the diagonal
-// block in shared memory, solve the panel below, update the trailing matrix
-// tile by tile.  A non-positive pivot sets info[P] and is replaced by 1.
-// ---------------------------------------------------------------------------
+// a8: batched FP64 Cholesky on the tiled layout, one CTA per patch.
+// Right-looking by 32-wide block columns: factor the diagonal tile in shared
+// memory and invert it, L_IK = A_IK L_KK^{-T} for the panel, then
+// A_IJ -= L_IK L_JK^T on the trailing tiles.  A non-positive pivot sets
+// info[P] and is replaced by 1.
 __global__ void __launch_bounds__(NT) k_cholesky(const int32_t* __restrict__ pn, const int64_t* __restrict__ pfoff,
-                                                 double* __restrict__ Lall, int* __restrict__ info) {
+                                                 const int64_t* __restrict__ pdoff_inv,
+                                                 const int64_t* __restrict__ pmoff, const int32_t* __restrict__ meta,
+                                                 double* __restrict__ Lall, double* __restrict__ Dall,
+                                                 int* __restrict__ info) {
   const int P = blockIdx.x;
   const int n = pn[P];
+  const int nb = (n + 31) / 32;
+  const int32_t* tix = meta + pmoff[P];
   double* A = Lall + pfoff[P];
-  __shared__ double D[NB][NB + 1];
-  __shared__ double Ti[NB][NB + 1], Tj[NB][NB + 1];
+  double* Dinv = Dall + pdoff_inv[P];
+  __shared__ double D[32][33], Di[32][33];
+  __shared__ double Ta[32][33], Tb[32][33];
+  __shared__ int colI[MAXNB];
+  __shared__ int ncol;
   const int tid = threadIdx.x;
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int kb = min(NB, n - k0);
-    for (int t = tid; t < NB * NB; t += NT) {
-      const int i = t / NB, j = t % NB;
-      D[i][j] = (i < kb && j <= i) ? A[tri(k0 + i, k0 + j)] : 0.0;
+  for (int K = 0; K < nb; ++K) {
+    double* AKK = A + (int64_t)tix[K * nb + K] * 1024;
+    for (int t = tid; t < 1024; t += NT) {
+      const int i = t >> 5, j = t & 31;
+      D[i][j] = (j <= i) ? AKK[t] : 0.0;
+      Di[i][j] = 0.0;
+    }
+    if (tid == 0) {
+      int m = 0;
+      for (int I = K + 1; I < nb; ++I)
+        if (tix[I * nb + K] >= 0) colI[m++] = I;
+      ncol = m;
     }
     __syncthreads();
     if (tid < 32) {
       const int lane = tid;
-      for (int j = 0; j < kb; ++j) {
+      for (int j = 0; j < 32; ++j) {
         if (lane == 0) {
           double d = D[j][j];
           if (!(d > 0.0)) {
-            if (info[P] == 0) info[P] = k0 + j + 1;
+            if (info[P] == 0) info[P] = K * 32 + j + 1;
             d = 1.0;
           }
           D[j][j] = sqrt(d);
         }
         __syncwarp();
         const double djj = D[j][j];
-        if (lane > j && lane < kb) D[lane][j] /= djj;
+        if (lane > j) D[lane][j] /= djj;
         __syncwarp();
-        for (int k = j + 1; k < kb; ++k)
-          if (lane >= k && lane < kb) D[lane][k] -= D[lane][j] * D[k][j];
+        for (int k = j + 1; k < 32; ++k)
+          if (lane >= k) D[lane][k] -= D[lane][j] * D[k][j];
         __syncwarp();
+      }
+      // inverse of the lower-triangular block, column `lane` by forward substitution
+      for (int r = lane; r < 32; ++r) {
+        double s = (r == lane) ? 1.0 : 0.0;
+        for (int k = lane; k < r; ++k) s -= D[r][k] * Di[k][lane];
+        Di[r][lane] = s / D[r][r];
       }
     }
     __syncthreads();
-    for (int t = tid; t < kb * kb; t += NT) {
-      const int i = t / kb, j = t % kb;
-      if (j <= i) A[tri(k0 + i, k0 + j)] = D[i][j];
+    for (int t = tid; t < 1024; t += NT) {
+      const int i = t >> 5, j = t & 31;
+      AKK[t] = (j <= i) ? D[i][j] : 0.0;
+      Dinv[K * 1024 + t] = Di[i][j];
     }
-    // panel: rows below solve x L11^T = a
-    for (int i = k0 + kb + tid; i < n; i += NT) {
-      double xr[NB];
-      double* Ai = A + tri(i, k0);
-#pragma unroll
-      for (int j = 0; j < NB; ++j) xr[j] = (j < kb) ? Ai[j] : 0.0;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        if (j < kb) {
-          double s = xr[j];
-          for (int k = 0; k < j; ++k) s -= xr[k] * D[j][k];
-          xr[j] = s / D[j][j];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < NB; ++j)
-        if (j < kb) Ai[j] = xr[j];
-    }
-    __syncthreads();
-    // trailing update A22 -= L21 L21^T on tiles (I >= J)
-    const int m0 = k0 + kb;
-    const int nt = (n - m0 + NB - 1) / NB;
-    const int ntiles = nt * (nt + 1) / 2;
-    for (int tile = 0; tile < ntiles; ++tile) {
-      int I = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
-      while ((I + 1) * (I + 2) / 2 <= tile) ++I;
-      while (I * (I + 1) / 2 > tile) --I;
-      const int J = tile - I * (I + 1) / 2;
-      const int i0 = m0 + I * NB, j0 = m0 + J * NB;
-      for (int t = tid; t < NB * NB; t += NT) {
-        const int r = t / NB, k = t % NB;
-        Ti[r][k] = (i0 + r < n && k < kb) ? A[tri(i0 + r, k0 + k)] : 0.0;
-        Tj[r][k] = (j0 + r < n && k < kb) ? A[tri(j0 + r, k0 + k)] : 0.0;
+    const int m = ncol;
+    // panel: L_IK = A_IK Linv_KK^T for the nonzero tiles of block column K
+    for (int a = 0; a < m; ++a) {
+      double* AIK = A + (int64_t)tix[colI[a] * nb + K] * 1024;
+      for (int t = tid; t < 1024; t += NT) Ta[t >> 5][t & 31] = AIK[t];
+      __syncthreads();
+      for (int t = tid; t < 1024; t += NT) {
+        const int r = t >> 5, c = t & 31;
+        double acc = 0.0;
+        for (int k = 0; k <= c; ++k) acc = fma(Ta[r][k], Di[c][k], acc);
+        AIK[t] = acc;
       }
       __syncthreads();
-      for (int t = tid; t < NB * NB; t += NT) {
-        const int r = t / NB, s = t % NB;
-        const int gi = i0 + r, gj = j0 + s;
-        if (gi < n && gj < n && gj <= gi) {
-          double acc = 0.0;
-#pragma unroll 8
-          for (int k = 0; k < NB; ++k) acc += Ti[r][k] * Tj[s][k];
-          A[tri(gi, gj)] -= acc;
-        }
+    }
+    // trailing update A_IJ -= L_IK L_JK^T over pairs of the column (I >= J)
+    const int npair = m * (m + 1) / 2;
+    for (int tt = 0; tt < npair; ++tt) {
+      int a = (int)((sqrt(8.0 * tt + 1.0) - 1.0) * 0.5);
+      while ((a + 1) * (a + 2) / 2 <= tt) ++a;
+      while (a * (a + 1) / 2 > tt) --a;
+      const int bb = tt - a * (a + 1) / 2;
+      const int I = colI[a], J = colI[bb];
+      const double* LI = A + (int64_t)tix[I * nb + K] * 1024;
+      const double* LJ = A + (int64_t)tix[J * nb + K] * 1024;
+      for (int t = tid; t < 1024; t += NT) {
+        Ta[t >> 5][t & 31] = LI[t];
+        Tb[t >> 5][t & 31] = LJ[t];
       }
+      __syncthreads();
+      double* AIJ = A + (int64_t)tix[I * nb + J] * 1024;
+      const int r0 = tid >> 4, c0 = tid & 15;
+      double a00 = 0.0, a01 = 0.0, a10 = 0.0, a11 = 0.0;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) {
+        const double x0 = Ta[r0][k], x1 = Ta[r0 + 16][k];
+        const double y0 = Tb[c0][k], y1 = Tb[c0 + 16][k];
+        a00 = fma(x0, y0, a00);
+        a01 = fma(x0, y1, a01);
+        a10 = fma(x1, y0, a10);
+        a11 = fma(x1, y1, a11);
+      }
+      AIJ[r0 * 32 + c0] -= a00;
+      AIJ[r0 * 32 + c0 + 16] -= a01;
+      AIJ[(r0 + 16) * 32 + c0] -= a10;
+      AIJ[(r0 + 16) * 32 + c0 + 16] -= a11;
       __syncthreads();
     }
   }
@@ -379,76 +431,175 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restr
     b[i] = (float)a[i];
 }
 
+// 4-wide vector load of a tile row segment
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  __device__ __forceinline__ static void load(const float* p, float* v) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  __device__ __forceinline__ static void load(const double* p, double* v) {
+    const double2 q0 = *reinterpret_cast<const double2*>(p);
+    const double2 q1 = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = q0.x;
+    v[1] = q0.y;
+    v[2] = q1.x;
+    v[3] = q1.y;
+  }
+};
+
 // ---------------------------------------------------------------------------
-// a7: patch solves z_V = L_V^{-T} L_V^{-1} R_V r, one CTA per patch.
-// Forward sweep: block rows [i0, i0+32): dot products with the solved prefix
-// (warp per row, coalesced row reads), then a 32x32 triangular solve by one
-// warp.  Backward sweep: block columns from the bottom, each row below
-// contributes its 32-wide segment (coalesced), then the 32x32 solve.
-// Every factor entry is read once per sweep.
+// a7: patch solves z_V = L_V^{-T} L_V^{-1} R_V r on the tiled factor, one CTA
+// per patch.  Thread (row r, quarter-group q) = (tid/8, tid%8) owns tile
+// columns 4q..4q+3.
+//   forward:  y_I = Dinv_I (b_I - sum_{J<I} L_IJ y_J)      (block row I, contiguous)
+//   backward: x_I = Dinv_I^T (y_I - sum_{J>I} L_JI^T x_J)  (block column I)
+// Every tile is read once per sweep with 16-byte loads.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(NT) k_patch_solve(const int32_t* __restrict__ pn, const int64_t* __restrict__ pdoff,
-                                                    const int64_t* __restrict__ pfoff, const int32_t* __restrict__ pdofs,
-                                                    const T* __restrict__ Lall, const double* __restrict__ r,
+                                                    const int64_t* __restrict__ pfoff,
+                                                    const int64_t* __restrict__ pdoff_inv,
+                                                    const int64_t* __restrict__ pmoff,
+                                                    const int32_t* __restrict__ meta,
+                                                    const int32_t* __restrict__ pdofs, const T* __restrict__ Lall,
+                                                    const T* __restrict__ Dall, const double* __restrict__ r,
                                                     double* __restrict__ zpatch, int64_t N, int64_t zstride) {
   extern __shared__ unsigned char smraw[];
-  T* y = reinterpret_cast<T*>(smraw);
-  __shared__ T part[NT / 32][32];
+  T* y = reinterpret_cast<T*>(smraw);  // [nb*32]
+  __shared__ T red[NT / 32][32];
+  __shared__ T tvec[32];
+  __shared__ int clist[MAXNB], cJ[MAXNB];
+  __shared__ int ncl;
   const int P = blockIdx.x;
   const int rh = blockIdx.y;
   const int n = pn[P];
+  const int nb = (n + 31) / 32;
+  const int32_t* tix = meta + pmoff[P];
+  const int32_t* tcol = tix + nb * nb;
   const T* L = Lall + pfoff[P];
+  const T* Dv = Dall + pdoff_inv[P];
   const int32_t* dofs = pdofs + pdoff[P];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
-  for (int i = tid; i < n; i += NT) y[i] = (T)r[rh * N + dofs[i]];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int row = tid >> 3, q = tid & 7;
+  for (int i = tid; i < nb * 32; i += NT) y[i] = (i < n) ? (T)r[rh * N + dofs[i]] : (T)0;
   __syncthreads();
-  // forward: L y = b
-  for (int i0 = 0; i0 < n; i0 += 32) {
-    const int kb = min(32, n - i0);
-    for (int rr = warp; rr < kb; rr += nw) {
-      const int i = i0 + rr;
-      const T* Li = L + tri(i, 0);
-      T s = 0;
-      for (int j = lane; j < i0; j += 32) s += Li[j] * y[j];
-      s = warp_sum(s);
-      if (lane == 0) y[i] -= s;
+  // forward: the off-diagonal tiles of block row I are stored contiguously
+  int t0 = 0;
+  for (int I = 0; I < nb; ++I) {
+    const int td = tix[I * nb + I];
+    T acc = 0;
+    const T* base = L + row * 32 + 4 * q;
+    int t = t0;
+    for (; t + 2 <= td; t += 2) {
+      T a[4], b2[4];
+      Vec4<T>::load(base + (int64_t)t * 1024, a);
+      Vec4<T>::load(base + (int64_t)(t + 1) * 1024, b2);
+      const T* y0 = y + tcol[t] * 32 + 4 * q;
+      const T* y1 = y + tcol[t + 1] * 32 + 4 * q;
+      acc += a[0] * y0[0] + a[1] * y0[1] + a[2] * y0[2] + a[3] * y0[3];
+      acc += b2[0] * y1[0] + b2[1] * y1[1] + b2[2] * y1[2] + b2[3] * y1[3];
     }
+    for (; t < td; ++t) {
+      T a[4];
+      Vec4<T>::load(base + (int64_t)t * 1024, a);
+      const T* y0 = y + tcol[t] * 32 + 4 * q;
+      acc += a[0] * y0[0] + a[1] * y0[1] + a[2] * y0[2] + a[3] * y0[3];
+    }
+    t0 = td + 1;
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    if (q == 0) tvec[row] = y[I * 32 + row] - acc;
     __syncthreads();
-    if (warp == 0) {
-      T yi = (lane < kb) ? y[i0 + lane] : (T)0;
-      const T* Lr = L + tri(i0 + min(lane, kb - 1), i0);
-      for (int j = 0; j < kb; ++j) {
-        const T yj = __shfl_sync(0xffffffffu, yi, j) / L[tri(i0 + j, i0 + j)];
-        if (lane == j) yi = yj;
-        if (lane > j && lane < kb) yi -= Lr[j] * yj;
-      }
-      if (lane < kb) y[i0 + lane] = yi;
-    }
+    T a[4];
+    Vec4<T>::load(Dv + I * 1024 + row * 32 + 4 * q, a);
+    T s = a[0] * tvec[4 * q] + a[1] * tvec[4 * q + 1] + a[2] * tvec[4 * q + 2] + a[3] * tvec[4 * q + 3];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    if (q == 0) y[I * 32 + row] = s;
     __syncthreads();
   }
-  // backward: L^T x = y
-  const int nblk = (n + 31) / 32;
-  for (int b = nblk - 1; b >= 0; --b) {
-    const int i0 = b * 32;
-    const int kb = min(32, n - i0);
-    T s = 0;
-    for (int j = i0 + kb + warp; j < n; j += nw) {
-      const T yj = y[j];
-      if (lane < kb) s += L[tri(j, i0 + lane)] * yj;
-    }
-    part[warp][lane] = s;
-    __syncthreads();
-    if (warp == 0) {
-      T acc = 0;
-      for (int w = 0; w < nw; ++w) acc += part[w][lane];
-      T xi = (lane < kb) ? y[i0 + lane] - acc : (T)0;
-      for (int j = kb - 1; j >= 0; --j) {
-        const T xj = __shfl_sync(0xffffffffu, xi, j) / L[tri(i0 + j, i0 + j)];
-        if (lane == j) xi = xj;
-        if (lane < j) xi -= L[tri(i0 + j, i0 + lane)] * xj;
+  // backward: block column I holds the nonzero tiles (J, I), J > I
+  for (int I = nb - 1; I >= 0; --I) {
+    if (tid == 0) {
+      int m = 0;
+      for (int J = I + 1; J < nb; ++J) {
+        const int t = tix[J * nb + I];
+        if (t >= 0) {
+          clist[m] = t;
+          cJ[m] = J;
+          ++m;
+        }
       }
-      if (lane < kb) y[i0 + lane] = xi;
+      ncl = m;
+    }
+    __syncthreads();
+    const int m = ncl;
+    T acc[4] = {0, 0, 0, 0};
+    int k0 = 0;
+    for (; k0 + 2 <= m; k0 += 2) {
+      T a[4], b2[4];
+      Vec4<T>::load(L + (int64_t)clist[k0] * 1024 + row * 32 + 4 * q, a);
+      Vec4<T>::load(L + (int64_t)clist[k0 + 1] * 1024 + row * 32 + 4 * q, b2);
+      const T x0 = y[cJ[k0] * 32 + row], x1 = y[cJ[k0 + 1] * 32 + row];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] += a[k] * x0 + b2[k] * x1;
+    }
+    for (; k0 < m; ++k0) {
+      T a[4];
+      Vec4<T>::load(L + (int64_t)clist[k0] * 1024 + row * 32 + 4 * q, a);
+      const T x0 = y[cJ[k0] * 32 + row];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] += a[k] * x0;
+    }
+    // reduce over the 4 rows of this warp (lanes with equal q), then over warps
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 8);
+      acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 16);
+    }
+    if (lane < 8) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red[warp][4 * q + k] = acc[k];
+    }
+    __syncthreads();
+    if (tid < 32) {
+      T s = 0;
+      for (int w = 0; w < NT / 32; ++w) s += red[w][tid];
+      tvec[tid] = y[I * 32 + tid] - s;
+    }
+    __syncthreads();
+    // x_I = Dinv^T t : x[c] = sum_r Dinv[r][c] t[r]
+    T b4[4];
+    Vec4<T>::load(Dv + I * 1024 + row * 32 + 4 * q, b4);
+    const T tr = tvec[row];
+    T part[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) part[k] = b4[k] * tr;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      part[k] += __shfl_xor_sync(0xffffffffu, part[k], 8);
+      part[k] += __shfl_xor_sync(0xffffffffu, part[k], 16);
+    }
+    if (lane < 8) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red[warp][4 * q + k] = part[k];
+    }
+    __syncthreads();
+    if (tid < 32) {
+      T s = 0;
+      for (int w = 0; w < NT / 32; ++w) s += red[w][tid];
+      y[I * 32 + tid] = s;
     }
     __syncthreads();
   }

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -73,21 +74,24 @@ struct riesz_handle {
   std::vector<int64_t> sc_ptr;   // interface DOF -> positions in Ycell
   std::vector<int32_t> sc_pos;
   std::vector<int32_t> p_n;      // patches in launch order (largest first)
-  std::vector<int64_t> p_doff, p_foff;
+  std::vector<int64_t> p_doff, p_foff, p_dioff, p_moff;  // DOF list, factor tiles, diagonal inverses, tile map
+  std::vector<int32_t> p_meta;  // per patch: tile index map [nb*nb] (-1 = zero tile) then the block column of each stored tile
+  int64_t tile_ops = 0;         // 32x32x32 tile products of the symbolic factorisation (all patches)
+  double chol_flops = 0.0;      // flops of the tile-sparse Cholesky (all patches)
   std::vector<int32_t> p_dofs;
   std::vector<int64_t> pz_ptr;   // interface DOF -> positions in zpatch
   std::vector<int32_t> pz_pos;
   std::vector<int64_t> pb_ptr, pb_off;
   std::vector<int32_t> pb_cell, pb_ent;
-  int64_t factor_entries = 0;
+  int64_t factor_entries = 0, dinv_entries = 0;
   double setup_host_ms = 0.0, setup_dev_ms = 0.0;
   // device state
   bool on_device = false;
   int device = 0;
-  DBuf<double> d_verts, d_g, d_jac, d_R, d_Ae, d_Ycell, d_dinv, d_L64, d_zpatch, d_X;
-  DBuf<float> d_L32;
-  DBuf<int32_t> d_cells, d_cdofs, d_sc_pos, d_pn, d_pdofs, d_pz_pos, d_pb_cell, d_pb_ent, d_cgdofs;
-  DBuf<int64_t> d_sc_ptr, d_pdoff, d_pfoff, d_pz_ptr, d_pb_ptr, d_pb_off;
+  DBuf<double> d_verts, d_g, d_jac, d_R, d_Ae, d_Ycell, d_dinv, d_L64, d_D64, d_zpatch, d_X;
+  DBuf<float> d_L32, d_D32;
+  DBuf<int32_t> d_cells, d_cdofs, d_sc_pos, d_pn, d_pdofs, d_pz_pos, d_pb_cell, d_pb_ent, d_cgdofs, d_meta;
+  DBuf<int64_t> d_sc_ptr, d_pdoff, d_pfoff, d_pdioff, d_pmoff, d_pz_ptr, d_pb_ptr, d_pb_off;
   DBuf<int> d_info;
   // PCG workspace
   DBuf<double> d_r, d_z, d_zold, d_p, d_Ap, d_part, d_scal, d_tmp, d_xh;
@@ -105,20 +109,21 @@ struct riesz_handle {
   int64_t C() const { return mesh.ncells; }
   size_t device_bytes() const {
     return d_verts.bytes() + d_g.bytes() + d_jac.bytes() + d_R.bytes() + d_Ae.bytes() + d_Ycell.bytes() +
-           d_dinv.bytes() + d_L64.bytes() + d_L32.bytes() + d_zpatch.bytes() + d_X.bytes() + d_cells.bytes() +
+           d_dinv.bytes() + d_L64.bytes() + d_L32.bytes() + d_D64.bytes() + d_D32.bytes() + d_zpatch.bytes() + d_X.bytes() + d_cells.bytes() +
            d_cdofs.bytes() + d_sc_pos.bytes() + d_pn.bytes() + d_pdofs.bytes() + d_pz_pos.bytes() +
            d_pb_cell.bytes() + d_pb_ent.bytes() + d_cgdofs.bytes() + d_sc_ptr.bytes() + d_pdoff.bytes() +
-           d_pfoff.bytes() + d_pz_ptr.bytes() + d_pb_ptr.bytes() + d_pb_off.bytes() + d_r.bytes() + d_z.bytes() +
+           d_pfoff.bytes() + d_pdioff.bytes() + d_pmoff.bytes() + d_meta.bytes() + d_pz_ptr.bytes() + d_pb_ptr.bytes() + d_pb_off.bytes() + d_r.bytes() + d_z.bytes() +
            d_zold.bytes() + d_p.bytes() + d_Ap.bytes() + d_part.bytes() + d_scal.bytes() + d_tmp.bytes() + d_xh.bytes();
   }
   void free_device() {
-    for (auto* b : {&d_verts, &d_g, &d_jac, &d_R, &d_Ae, &d_Ycell, &d_dinv, &d_L64, &d_zpatch, &d_X, &d_r, &d_z,
+    for (auto* b : {&d_verts, &d_g, &d_jac, &d_R, &d_Ae, &d_Ycell, &d_dinv, &d_L64, &d_D64, &d_zpatch, &d_X, &d_r, &d_z,
                     &d_zold, &d_p, &d_Ap, &d_part, &d_scal, &d_tmp, &d_xh})
       b->free();
     d_L32.free();
-    for (auto* b : {&d_cells, &d_cdofs, &d_sc_pos, &d_pn, &d_pdofs, &d_pz_pos, &d_pb_cell, &d_pb_ent, &d_cgdofs})
+    d_D32.free();
+    for (auto* b : {&d_cells, &d_cdofs, &d_sc_pos, &d_pn, &d_pdofs, &d_pz_pos, &d_pb_cell, &d_pb_ent, &d_cgdofs, &d_meta})
       b->free();
-    for (auto* b : {&d_sc_ptr, &d_pdoff, &d_pfoff, &d_pz_ptr, &d_pb_ptr, &d_pb_off}) b->free();
+    for (auto* b : {&d_sc_ptr, &d_pdoff, &d_pfoff, &d_pdioff, &d_pmoff, &d_pz_ptr, &d_pb_ptr, &d_pb_off}) b->free();
     d_info.free();
     if (h_scal) cudaFreeHost(h_scal);
     h_scal = nullptr;
@@ -203,6 +208,180 @@ dev::Mat3 ref_edge_inverse() {
   return m;
 }
 
+// Plan one vertex-star patch (Eq. (6.11)): order its DOFs, record the cell
+// contributions for the assembly and the tile structure of its Cholesky factor.
+//
+// The factorisation of P A_V P^T for any permutation P gives the same operator
+// R_V^T A_V^{-1} R_V.  Entities (the vertex, edges and faces of the star) are
+// ordered by a Fiedler-type vector of their adjacency graph (two entities are
+// adjacent when a star cell contains both): power iteration of (c I - Lap)
+// started from the entity midpoints projected on (1,1,1) and orthogonal to the
+// constant.  The link of a vertex is a sphere-like graph, so this orders the
+// DOFs in bands and leaves most 32x32 tiles of the factor zero.  The tile
+// pattern of the factor is the symbolic tile-level Cholesky of the pattern of
+// A_V; only nonzero tiles are stored, in block-row order.
+void plan_patch(riesz_handle& h, int64_t v, int64_t& foff, int64_t& dioff) {
+  const MeshMaps& M = h.mesh;
+  const int n = M.nref;
+  const int64_t b = M.patch_ptr[v], e = M.patch_ptr[v + 1];
+  const int np = (int)(e - b);
+  const int32_t* pd = &M.patch_dofs[b];
+  // entities: contiguous runs of the sorted patch DOF list
+  std::vector<int> ent_start, ent_len, dof_ent(np);
+  std::vector<std::array<double, 3>> mid;
+  const double* X = h.verts.data();
+  for (int k = 0; k < np;) {
+    const int64_t d = pd[k];
+    int kind = (d < M.off[1]) ? 0 : (d < M.off[2] ? 1 : 2);
+    const int per = M.per_entity[kind];
+    const int64_t id = (d - M.off[kind]) / per;
+    std::array<double, 3> m = {0.0, 0.0, 0.0};
+    int nvx = 0;
+    int32_t vv[3];
+    if (kind == 0) {
+      vv[0] = (int32_t)id;
+      nvx = 1;
+    } else if (kind == 1) {
+      vv[0] = M.edges[id * 2];
+      vv[1] = M.edges[id * 2 + 1];
+      nvx = 2;
+    } else {
+      for (int q = 0; q < 3; ++q) vv[q] = M.faces[id * 3 + q];
+      nvx = 3;
+    }
+    for (int q = 0; q < nvx; ++q)
+      for (int c = 0; c < 3; ++c) m[c] += (X[(size_t)vv[q] * 3 + c] - X[(size_t)v * 3 + c]) / nvx;
+    const int ei = (int)ent_start.size();
+    ent_start.push_back(k);
+    ent_len.push_back(per);
+    mid.push_back(m);
+    for (int q = 0; q < per; ++q) dof_ent[k + q] = ei;
+    k += per;
+  }
+  const int ne = (int)ent_start.size();
+  // star cells -> patch entities (and DOF positions)
+  std::vector<std::vector<int>> cell_ents;
+  std::vector<int32_t> cell_ids;
+  std::vector<std::vector<std::pair<int, int>>> cell_locs;  // (local j, sorted patch index)
+  for (int64_t sidx = M.star_ptr[v]; sidx < M.star_ptr[v + 1]; ++sidx) {
+    const int32_t c = M.star_cells[sidx];
+    std::vector<int> ce;
+    std::vector<std::pair<int, int>> loc;
+    for (int j = 0; j < h.nif; ++j) {
+      const int32_t gd = M.cell_dofs[(int64_t)c * n + j];
+      const int32_t* it = std::lower_bound(pd, pd + np, gd);
+      if (it != pd + np && *it == gd) {
+        const int k = (int)(it - pd);
+        loc.push_back({j, k});
+        if (std::find(ce.begin(), ce.end(), dof_ent[k]) == ce.end()) ce.push_back(dof_ent[k]);
+      }
+    }
+    if (!loc.empty()) {
+      cell_ids.push_back(c);
+      cell_ents.push_back(ce);
+      cell_locs.push_back(loc);
+    }
+  }
+  // entity adjacency and the Fiedler-type ordering
+  std::vector<std::vector<int>> adj(ne);
+  for (const auto& ce : cell_ents)
+    for (int a : ce)
+      for (int bb : ce)
+        if (a != bb && std::find(adj[a].begin(), adj[a].end(), bb) == adj[a].end()) adj[a].push_back(bb);
+  size_t maxdeg = 0;
+  for (const auto& l : adj) maxdeg = std::max(maxdeg, l.size());
+  const double cshift = 2.0 * (double)maxdeg + 1.0;
+  std::vector<double> x(ne), y(ne);
+  const double s3 = 1.0 / std::sqrt(3.0);
+  for (int a = 0; a < ne; ++a) x[a] = (mid[a][0] + mid[a][1] + mid[a][2]) * s3;
+  for (int it = 0; it < 60; ++it) {
+    double mean = 0.0;
+    for (int a = 0; a < ne; ++a) mean += x[a];
+    mean /= ne;
+    double nrm = 0.0;
+    for (int a = 0; a < ne; ++a) {
+      x[a] -= mean;
+      nrm += x[a] * x[a];
+    }
+    if (!(nrm > 0.0)) {
+      for (int a = 0; a < ne; ++a) x[a] = a;
+      continue;
+    }
+    nrm = 1.0 / std::sqrt(nrm);
+    for (int a = 0; a < ne; ++a) x[a] *= nrm;
+    for (int a = 0; a < ne; ++a) {
+      double t = (cshift - (double)adj[a].size()) * x[a];
+      for (int bb : adj[a]) t += x[bb];
+      y[a] = t;
+    }
+    x.swap(y);
+  }
+  std::vector<int> eorder(ne);
+  for (int a = 0; a < ne; ++a) eorder[a] = a;
+  std::stable_sort(eorder.begin(), eorder.end(), [&](int a, int bb) { return x[a] < x[bb]; });
+  // new DOF order
+  std::vector<int> newpos(np), ent_new_start(ne);
+  std::vector<int32_t> dofs_new;
+  dofs_new.reserve(np);
+  for (int a : eorder) {
+    ent_new_start[a] = (int)dofs_new.size();
+    for (int q = 0; q < ent_len[a]; ++q) {
+      newpos[ent_start[a] + q] = (int)dofs_new.size();
+      dofs_new.push_back(pd[ent_start[a] + q]);
+    }
+  }
+  // tile pattern of A_V and its symbolic tile Cholesky
+  const int nb = (np + 31) / 32;
+  std::vector<char> nz((size_t)nb * nb, 0);
+  for (int I = 0; I < nb; ++I) nz[(size_t)I * nb + I] = 1;
+  for (const auto& ce : cell_ents)
+    for (int a : ce)
+      for (int bb : ce) {
+        const int r0 = ent_new_start[a] / 32, r1 = (ent_new_start[a] + ent_len[a] - 1) / 32;
+        const int c0 = ent_new_start[bb] / 32, c1 = (ent_new_start[bb] + ent_len[bb] - 1) / 32;
+        for (int I = r0; I <= r1; ++I)
+          for (int J = c0; J <= c1; ++J) nz[(size_t)std::max(I, J) * nb + std::min(I, J)] = 1;
+      }
+  std::vector<int> col;
+  for (int K = 0; K < nb; ++K) {
+    col.clear();
+    for (int I = K + 1; I < nb; ++I)
+      if (nz[(size_t)I * nb + K]) col.push_back(I);
+    h.tile_ops += 1 + (int64_t)col.size() + (int64_t)col.size() * (col.size() + 1) / 2;
+    // diagonal factor (n^3/3) + its inverse (n^3/3), panel (triangular, 32*528 FMA per tile),
+    // trailing tile products (32^3 FMA each)
+    h.chol_flops += 2.0 * 32768.0 / 3.0 + 2.0 * 16896.0 * col.size() + 65536.0 * (col.size() * (col.size() + 1) / 2);
+    for (size_t a = 0; a < col.size(); ++a)
+      for (size_t bb = 0; bb <= a; ++bb) nz[(size_t)col[a] * nb + col[bb]] = 1;
+  }
+  const int64_t moff = (int64_t)h.p_meta.size();
+  h.p_meta.resize(moff + (size_t)nb * nb, -1);
+  int32_t nt = 0;
+  std::vector<int32_t> tcol;
+  for (int I = 0; I < nb; ++I)
+    for (int J = 0; J <= I; ++J)
+      if (nz[(size_t)I * nb + J]) {
+        h.p_meta[moff + (size_t)I * nb + J] = nt++;
+        tcol.push_back(J);
+      }
+  h.p_meta.insert(h.p_meta.end(), tcol.begin(), tcol.end());
+  // record the patch
+  h.p_n.push_back(np);
+  h.p_doff.push_back((int64_t)h.p_dofs.size());
+  h.p_foff.push_back(foff);
+  h.p_dioff.push_back(dioff);
+  h.p_moff.push_back(moff);
+  foff += (int64_t)nt * 1024;
+  dioff += (int64_t)nb * 1024;
+  h.p_dofs.insert(h.p_dofs.end(), dofs_new.begin(), dofs_new.end());
+  for (size_t ci = 0; ci < cell_ids.size(); ++ci) {
+    for (const auto& jk : cell_locs[ci]) h.pb_ent.push_back(jk.first | (int32_t)(newpos[jk.second] << 10));
+    h.pb_cell.push_back(cell_ids[ci]);
+    h.pb_off.push_back((int64_t)h.pb_ent.size());
+  }
+  h.pb_ptr.push_back((int64_t)h.pb_cell.size());
+}
+
 void build_plans(riesz_handle& h) {
   const MeshMaps& M = h.mesh;
   const int n = M.nref;
@@ -251,42 +430,26 @@ void build_plans(riesz_handle& h) {
   h.p_n.clear();
   h.p_doff.clear();
   h.p_foff.clear();
+  h.p_dioff.clear();
+  h.p_moff.clear();
+  h.p_meta.clear();
   h.p_dofs.clear();
   h.pb_ptr.assign(1, 0);
   h.pb_off.assign(1, 0);
   h.pb_cell.clear();
   h.pb_ent.clear();
-  int64_t foff = 0;
+  h.tile_ops = 0;
+  h.chol_flops = 0.0;
+  int64_t foff = 0, dioff = 0;
   for (int64_t v : order) {
     const int64_t b = M.patch_ptr[v], e = M.patch_ptr[v + 1];
     const int np = (int)(e - b);
     if (np == 0) continue;
-    if (np >= (1 << 21)) throw Err(RIESZ_ERR_INVALID_ARG, "patch too large");
-    h.p_n.push_back(np);
-    h.p_doff.push_back((int64_t)h.p_dofs.size());
-    h.p_foff.push_back(foff);
-    foff += (int64_t)np * (np + 1) / 2;
-    h.p_dofs.insert(h.p_dofs.end(), M.patch_dofs.begin() + b, M.patch_dofs.begin() + e);
-    const int32_t* pd = &M.patch_dofs[b];
-    for (int64_t s = M.star_ptr[v]; s < M.star_ptr[v + 1]; ++s) {
-      const int32_t c = M.star_cells[s];
-      int m = 0;
-      for (int j = 0; j < h.nif; ++j) {
-        const int32_t gd = M.cell_dofs[(int64_t)c * n + j];
-        const int32_t* it = std::lower_bound(pd, pd + np, gd);
-        if (it != pd + np && *it == gd) {
-          h.pb_ent.push_back(j | (int32_t)((it - pd) << 10));
-          ++m;
-        }
-      }
-      if (m) {
-        h.pb_cell.push_back(c);
-        h.pb_off.push_back((int64_t)h.pb_ent.size());
-      }
-    }
-    h.pb_ptr.push_back((int64_t)h.pb_cell.size());
+    if (np > 32 * dev::MAXNB) throw Err(RIESZ_ERR_INVALID_ARG, "patch larger than 4096 DOFs");
+    plan_patch(h, v, foff, dioff);
   }
   h.factor_entries = foff;
+  h.dinv_entries = dioff;
   // interface DOF -> positions in zpatch (patch launch order fixes the sum order)
   h.pz_ptr.assign(nI + 1, 0);
   for (int32_t d : h.p_dofs) h.pz_ptr[d + 1]++;
@@ -315,8 +478,9 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
   const int64_t C = h.C(), N = h.N();
   if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     const size_t sm = (size_t)n * nrhs * sizeof(double);
+    const int nt = std::min(1024, (n + 31) / 32 * 32);
     launch(h, RIESZ_K_APPLY, s, [&] {
-      dev::k_apply_elem<<<(unsigned)C, dev::NT, sm, s>>>(C, n, h.nif, h.d_Ae.p, h.d_cdofs.p, x, y, h.d_Ycell.p, nrhs, N);
+      dev::k_apply_elem<<<(unsigned)C, nt, sm, s>>>(C, n, h.nif, h.d_Ae.p, h.d_cdofs.p, x, y, h.d_Ycell.p, nrhs, N);
     });
   } else {
     const size_t sm = ((size_t)n + h.ref->Q) * dev::TC * sizeof(double);
@@ -336,19 +500,23 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
 void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStream_t s) {
   const int64_t N = h.N();
   const int npatch = (int)h.p_n.size();
-  const int nmax = h.p_n.empty() ? 0 : h.p_n[0];
+  const int nbmax = h.p_n.empty() ? 0 : (h.p_n[0] + 31) / 32;
   const int64_t zstride = (int64_t)h.p_dofs.size();
   if (npatch) {
     dim3 grid(npatch, nrhs);
     if (h.opts.precond_precision == RIESZ_PREC_FP32) {
       launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
-        dev::k_patch_solve<float><<<grid, dev::NT, (size_t)nmax * sizeof(float), s>>>(
-            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdofs.p, h.d_L32.p, r, h.d_zpatch.p, N, zstride);
+        dev::k_patch_solve<float><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(float), s>>>(
+            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L32.p,
+            h.d_D32.p, r, h.d_zpatch.p, N,
+            zstride);
       });
     } else {
       launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
-        dev::k_patch_solve<double><<<grid, dev::NT, (size_t)nmax * sizeof(double), s>>>(
-            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdofs.p, h.d_L64.p, r, h.d_zpatch.p, N, zstride);
+        dev::k_patch_solve<double><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(double), s>>>(
+            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L64.p,
+            h.d_D64.p, r, h.d_zpatch.p, N,
+            zstride);
       });
     }
   }
@@ -474,16 +642,23 @@ void device_compute(riesz_handle& h, cudaStream_t s) {
   CK(cudaMemsetAsync(h.d_info.p, 0, sizeof(int) * std::max(1, npatch), s));
   if (npatch) {
     launch(h, RIESZ_K_ASSEMBLE, s, [&] {
-      dev::k_patch_assemble<<<npatch, 256, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pb_ptr.p, h.d_pb_cell.p, h.d_pb_off.p,
+      dev::k_patch_assemble<<<npatch, 256, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pmoff.p, h.d_meta.p, h.d_pb_ptr.p,
+                                                   h.d_pb_cell.p, h.d_pb_off.p,
                                                    h.d_pb_ent.p, C, n, R.Q, h.d_g.p, h.d_R.p, h.d_Ae.p, h.d_L64.p);
     });
     launch(h, RIESZ_K_CHOLESKY, s, [&] {
-      dev::k_cholesky<<<npatch, dev::NT, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_L64.p, h.d_info.p);
+      dev::k_cholesky<<<npatch, dev::NT, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p,
+                                                 h.d_L64.p, h.d_D64.p,
+                                                 h.d_info.p);
     });
-    if (h.opts.precond_precision == RIESZ_PREC_FP32)
+    if (h.opts.precond_precision == RIESZ_PREC_FP32) {
       launch(h, RIESZ_K_TO_F32, s, [&] {
         dev::k_to_f32<<<1184, 256, 0, s>>>(h.factor_entries, h.d_L64.p, h.d_L32.p);
       });
+      launch(h, RIESZ_K_TO_F32, s, [&] {
+        dev::k_to_f32<<<296, 256, 0, s>>>(h.dinv_entries, h.d_D64.p, h.d_D32.p);
+      });
+    }
   }
   CK(cudaEventRecord(e1, s));
   CK(cudaEventSynchronize(e1));
@@ -551,11 +726,18 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     if (sm > 48 * 1024)
       CK(cudaFuncSetAttribute(dev::k_apply_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   }
+  h.d_pdioff.upload(h.p_dioff, s);
+  h.d_pmoff.upload(h.p_moff, s);
+  h.d_meta.upload(h.p_meta, s);
   if (npatch) {
     h.d_L64.alloc((size_t)h.factor_entries);
-    if (h.opts.precond_precision == RIESZ_PREC_FP32) h.d_L32.alloc((size_t)h.factor_entries);
+    h.d_D64.alloc((size_t)h.dinv_entries);
+    if (h.opts.precond_precision == RIESZ_PREC_FP32) {
+      h.d_L32.alloc((size_t)h.factor_entries);
+      h.d_D32.alloc((size_t)h.dinv_entries);
+    }
   }
-  const size_t smp = (size_t)(h.p_n.empty() ? 0 : h.p_n[0]) * sizeof(double);
+  const size_t smp = (size_t)(h.p_n.empty() ? 0 : (h.p_n[0] + 31) / 32 * 32) * sizeof(double);
   if (smp > 48 * 1024) {
     CK(cudaFuncSetAttribute(dev::k_patch_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
     CK(cudaFuncSetAttribute(dev::k_patch_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
@@ -801,9 +983,12 @@ int riesz_stats(const riesz_handle* h, double* out) {
     out[0] = h->setup_host_ms;
     out[1] = h->setup_dev_ms;
     out[2] = (double)h->device_bytes();
-    out[3] = (double)h->factor_entries * (h->opts.precond_precision == RIESZ_PREC_FP32 ? 4.0 : 8.0);
+    out[3] = (double)(h->factor_entries + h->dinv_entries) * (h->opts.precond_precision == RIESZ_PREC_FP32 ? 4.0 : 8.0);
     out[4] = h->last_iters;
     out[5] = (double)h->launches;
+    out[6] = h->chol_flops;
+    const double fb = h->opts.precond_precision == RIESZ_PREC_FP32 ? 4.0 : 8.0;
+    out[7] = 2.0 * (double)(h->factor_entries + h->dinv_entries) * fb + (double)h->p_dofs.size() * 20.0;
   });
 }
 

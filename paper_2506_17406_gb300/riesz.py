@@ -179,10 +179,11 @@ class Riesz:
         return off, dofs
 
     def stats(self):
-        out = np.zeros(6)
+        out = np.zeros(8)
         _check(self.lib.riesz_stats(self.h, _ptr(out)))
         return {"setup_host_ms": out[0], "setup_device_ms": out[1], "device_bytes": out[2],
-                "factor_bytes": out[3], "last_iters": int(out[4]), "launches": int(out[5])}
+                "factor_bytes": out[3], "last_iters": int(out[4]), "launches": int(out[5]),
+                "chol_flops": out[6], "precond_bytes": out[7]}
 
     # ----- device calls -----
     def setup_device(self, stream=None):
