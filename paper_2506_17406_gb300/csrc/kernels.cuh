@@ -113,9 +113,28 @@ __global__ void k_elem_matrices(int64_t C, int n, int Q, const double* __restric
 // a3-a5: apply.  Gather x on the cell, y_T = A_T x_T, interior rows written
 // directly (each interior DOF belongs to one cell), interface rows to Ycell.
 // ---------------------------------------------------------------------------
-// Element-matrix variant: one CTA per cell, one thread per row i.  A_T is
-// symmetric, so y_i = sum_j A_T[j][i] x_j: for each j the threads read the
-// contiguous row j of A_T (coalesced) against a shared-memory x_j.
+// Element-matrix variant: one CTA per cell.  A_T is symmetric, so
+// y_i = sum_j A_T[j][i] x_j: for each j the threads read the contiguous row j
+// of A_T (coalesced).  Each thread owns two adjacent rows (16-byte loads of
+// A_T and of x_j, x_{j+1} from shared memory); odd n_ref takes the scalar path.
+template <int R>
+__device__ __forceinline__ void apply_rows2(const double* __restrict__ A, const double* __restrict__ xs, int n,
+                                            int i0, double (&acc)[2][4]) {
+  const double* p = A + i0;
+  for (int j = 0; j < n; j += 2) {
+    const double2 a0 = *reinterpret_cast<const double2*>(p + (int64_t)j * n);
+    const double2 a1 = *reinterpret_cast<const double2*>(p + (int64_t)(j + 1) * n);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const double2 xv = *reinterpret_cast<const double2*>(xs + r * n + j);
+      acc[0][r] = fma(a0.x, xv.x, acc[0][r]);
+      acc[1][r] = fma(a0.y, xv.x, acc[1][r]);
+      acc[0][r] = fma(a1.x, xv.y, acc[0][r]);
+      acc[1][r] = fma(a1.y, xv.y, acc[1][r]);
+    }
+  }
+}
+
 __global__ void k_apply_elem(int64_t C, int n, int nif, const double* __restrict__ Ae,
                              const int32_t* __restrict__ cdofs, const double* __restrict__ x, double* __restrict__ y,
                              double* __restrict__ Ycell, int nrhs, int64_t N) {
@@ -127,35 +146,38 @@ __global__ void k_apply_elem(int64_t C, int n, int nif, const double* __restrict
   }
   __syncthreads();
   const double* A = Ae + c * (int64_t)n * n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    for (int r0 = 0; r0 < nrhs; r0 += 4) {
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
-      const int nr = min(4, nrhs - r0);
-      int j = 0;
-      for (; j + 4 <= n; j += 4) {
-        const double a0 = A[(int64_t)j * n + i], a1 = A[(int64_t)(j + 1) * n + i];
-        const double a2 = A[(int64_t)(j + 2) * n + i], a3 = A[(int64_t)(j + 3) * n + i];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if (k < nr) {
-            const double* xr = xs + (r0 + k) * n + j;
-            acc[k] = fma(a0, xr[0], acc[k]);
-            acc[k] = fma(a1, xr[1], acc[k]);
-            acc[k] = fma(a2, xr[2], acc[k]);
-            acc[k] = fma(a3, xr[3], acc[k]);
-          }
+  auto store = [&](int i, int r, double v) {
+    if (i >= nif)
+      y[r * N + cdofs[(int64_t)i * C + c]] = v;
+    else
+      Ycell[((int64_t)r * nif + i) * C + c] = v;
+  };
+  if ((n & 1) == 0) {
+    for (int i0 = 2 * threadIdx.x; i0 < n; i0 += 2 * blockDim.x) {
+      for (int r0 = 0; r0 < nrhs; r0 += 4) {
+        double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+        const int nr = min(4, nrhs - r0);
+        const double* xr = xs + r0 * n;
+        if (nr == 1)
+          apply_rows2<1>(A, xr, n, i0, acc);
+        else if (nr == 2)
+          apply_rows2<2>(A, xr, n, i0, acc);
+        else if (nr == 3)
+          apply_rows2<3>(A, xr, n, i0, acc);
+        else
+          apply_rows2<4>(A, xr, n, i0, acc);
+        for (int k = 0; k < nr; ++k) {
+          store(i0, r0 + k, acc[0][k]);
+          store(i0 + 1, r0 + k, acc[1][k]);
         }
       }
-      for (; j < n; ++j) {
-        const double a0 = A[(int64_t)j * n + i];
-        for (int k = 0; k < nr; ++k) acc[k] = fma(a0, xs[(r0 + k) * n + j], acc[k]);
-      }
-      for (int k = 0; k < nr; ++k) {
-        const int r = r0 + k;
-        if (i >= nif)
-          y[r * N + cdofs[(int64_t)i * C + c]] = acc[k];
-        else
-          Ycell[((int64_t)r * nif + i) * C + c] = acc[k];
+    }
+  } else {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      for (int r = 0; r < nrhs; ++r) {
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc = fma(A[(int64_t)j * n + i], xs[r * n + j], acc);
+        store(i, r, acc);
       }
     }
   }

@@ -478,7 +478,8 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
   const int64_t C = h.C(), N = h.N();
   if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     const size_t sm = (size_t)n * nrhs * sizeof(double);
-    const int nt = std::min(1024, (n + 31) / 32 * 32);
+    const int rows = (n % 2 == 0) ? n / 2 : n;
+    const int nt = std::min(1024, (rows + 31) / 32 * 32);
     launch(h, RIESZ_K_APPLY, s, [&] {
       dev::k_apply_elem<<<(unsigned)C, nt, sm, s>>>(C, n, h.nif, h.d_Ae.p, h.d_cdofs.p, x, y, h.d_Ycell.p, nrhs, N);
     });
