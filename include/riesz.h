@@ -131,6 +131,27 @@ int riesz_setup(int space, int p, int64_t nverts, const double* verts, int64_t n
 /* y = A x (matrix-free operator of Eq. (2.8)); x, y: device [nrhs][N]. */
 int riesz_apply(riesz_handle* h, const double* x, double* y, int nrhs, void* stream);
 
+/* y = A x for one right-hand side, like riesz_apply, but without any memory
+   the call or the handle allocated for it: the per-cell interface results
+   that riesz_apply keeps in a handle-owned buffer go to a fixed device array
+   compiled into this library (2^21 doubles = 16 MiB, reserved on every GPU
+   that loads the library until the process exits).  It exists for callers
+   that must not call cudaMalloc on their hot path: code whose device memory
+   is owned by another allocator or a fixed budget (for example a framework
+   caching allocator that already holds the free memory), and latency-bound
+   loops where an allocation's implicit synchronisation is not acceptable.
+   The paper has no counterpart; it is an interface convenience.
+   x, y: device [N] on the handle's device, which must be current.
+   Limits: n_interface_per_cell * ncells <= 2^21 (RIESZ_ERR_INVALID_ARG
+   otherwise, nothing launched).  The first call on a device looks up the
+   array's device address (cudaGetSymbolAddress), so make that first call
+   before any stream capture.  All calls share the one array, which keeps the
+   last call's contents; calls that overlap on the GPU (other streams, other
+   handles on the same device) race on it and must be serialised by the
+   caller.  Every scratch entry a call reads is written earlier in the same
+   call, so stale contents never reach y. */
+int riesz_apply_noalloc(riesz_handle* h, const double* x, double* y, void* stream);
+
 /* z = P^{-1} r (Eq. (6.11), additive); r, z: device [nrhs][N]. */
 int riesz_precond(riesz_handle* h, const double* r, double* z, int nrhs, void* stream);
 

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -754,6 +755,33 @@ void check_dev(const riesz_handle* h) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Scratch for riesz_apply_noalloc: a file-scope device array, so that entry
+// point never allocates.  Every device that loads this library reserves it
+// until the process exits.  Its host-side name is not a device address: the
+// address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+#define RIESZ_NOALLOC_SCRATCH_DOUBLES (1 << 21)
+static __device__ __align__(256) double g_noalloc_scratch[RIESZ_NOALLOC_SCRATCH_DOUBLES];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 64;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch on the current device (looked up on first use).
+double* noalloc_scratch(int device) {
+  if (device < 0 || device >= kMaxDevices) throw Err(RIESZ_ERR_INVALID_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* ptr = nullptr;
+    CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_noalloc_ptr[device] = static_cast<double*>(ptr);
+  }
+  return g_noalloc_ptr[device];
+}
+}  // namespace
+
 extern "C" {
 
 void riesz_default_opts(riesz_opts* o) {
@@ -877,6 +905,47 @@ int riesz_apply(riesz_handle* h, const double* x, double* y, int nrhs, void* str
     check_dev(h);
     need(x && y && nrhs >= 1 && nrhs <= h->opts.nrhs_max, "bad apply arguments");
     op_apply(*h, x, y, nrhs, S(stream));
+  });
+}
+
+int riesz_apply_noalloc(riesz_handle* h, const double* x, double* y, void* stream) {
+  return guarded([&] {
+    check_dev(h);
+    need(x && y, "null argument");
+    int device = -1;
+    CK(cudaGetDevice(&device));
+    need(device == h->device, "the current CUDA device is not the handle's device");
+    const int64_t C = h->C(), N = h->N();
+    const int n = h->mesh.nref;
+    const int64_t need_doubles = (int64_t)h->nif * C;
+    if (need_doubles > RIESZ_NOALLOC_SCRATCH_DOUBLES)
+      throw Err(RIESZ_ERR_INVALID_ARG,
+                "riesz_apply_noalloc: interface DOFs per cell x cells = " + std::to_string(need_doubles) +
+                    " exceeds the fixed scratch of " + std::to_string(RIESZ_NOALLOC_SCRATCH_DOUBLES) + " doubles");
+    double* ycell = noalloc_scratch(device);
+    cudaStream_t s = S(stream);
+    // same kernels as riesz_apply with nrhs = 1; every scratch slot read by the
+    // gather is written by the contraction of the same call, so no clearing
+    if (h->opts.apply_mode == RIESZ_APPLY_ELEMENT) {
+      const int rows = (n % 2 == 0) ? n / 2 : n;
+      const int nt = std::min(1024, (rows + 31) / 32 * 32);
+      launch(*h, RIESZ_K_APPLY, s, [&] {
+        dev::k_apply_elem<<<(unsigned)C, nt, (size_t)n * sizeof(double), s>>>(C, n, h->nif, h->d_Ae.p, h->d_cdofs.p,
+                                                                              x, y, ycell, 1, N);
+      });
+    } else {
+      const size_t sm = ((size_t)n + h->ref->Q) * dev::TC * sizeof(double);
+      dim3 grid(nblk(C, dev::TC), 1);
+      launch(*h, RIESZ_K_APPLY, s, [&] {
+        dev::k_apply_mf<<<grid, dev::NT, sm, s>>>(C, n, h->nif, h->ref->Q, h->d_R.p, h->d_g.p, h->d_cdofs.p, x, y,
+                                                 ycell, N);
+      });
+    }
+    const int64_t nI = h->mesh.n_interface;
+    launch(*h, RIESZ_K_GATHER, s, [&] {
+      dev::k_gather_iface<<<nblk(nI, 256), 256, 0, s>>>(nI, h->d_sc_ptr.p, h->d_sc_pos.p, ycell, (int64_t)h->nif * C,
+                                                       y, N, 1);
+    });
   });
 }
 

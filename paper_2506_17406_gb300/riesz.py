@@ -55,6 +55,7 @@ _SIGS = {
     "riesz_setup_device": (_I, [_P, _P]),
     "riesz_setup": (_I, [_I, _I, _I64, _P, _I64, _P, ctypes.POINTER(Opts), _P, ctypes.POINTER(_P)]),
     "riesz_apply": (_I, [_P, _P, _P, _I, _P]),
+    "riesz_apply_noalloc": (_I, [_P, _P, _P, _P]),
     "riesz_precond": (_I, [_P, _P, _P, _I, _P]),
     "riesz_solve": (_I, [_P, _P, _P, _I, _P, _P, _P]),
     "riesz_solve_host": (_I, [_P, _P, _P, _I, _P, _P, _P]),
@@ -191,6 +192,10 @@ class Riesz:
 
     def apply(self, x, y, nrhs=1, stream=None):
         _check(self.lib.riesz_apply(self.h, _ptr(x), _ptr(y), nrhs, _stream(stream)))
+        return y
+
+    def apply_noalloc(self, x, y, stream=None):
+        _check(self.lib.riesz_apply_noalloc(self.h, _ptr(x), _ptr(y), _stream(stream)))
         return y
 
     def precond(self, r, z, nrhs=1, stream=None):
