@@ -200,8 +200,9 @@ enum {
 };
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around
-   every kernel of the handle.  enable != 0 turns it on and clears the
-   accumulators; riesz_profile_read synchronises the recorded events and
+   the kernels of the handle.  enable is a bit mask of kinds (bit k records
+   kind k; -1 records all, 0 turns the profiler off); every call clears the
+   accumulators.  riesz_profile_read synchronises the recorded events and
    returns the summed milliseconds and launch counts per kind (arrays of
    RIESZ_NKIND entries, either may be NULL). */
 int riesz_profile(riesz_handle* h, int enable);

@@ -219,3 +219,58 @@ def mass_and_stiffness(ref, md):
     M = assemble(md, element_matrices(ref, md.verts, md.cells, alpha=0.0, beta=1.0))
     K = assemble(md, element_matrices(ref, md.verts, md.cells, alpha=1.0, beta=0.0))
     return M, K
+
+
+def cells_of_dofs(md, dofs):
+    """For each DOF: the (cell, local index) pairs that touch it."""
+    out = []
+    for d in dofs:
+        c, j = np.nonzero(md.cell_dofs == d)
+        out.append(list(zip(c.tolist(), j.tolist())))
+    return out
+
+
+def sampled_apply(ref, md, dofs, x):
+    """(A x)[dofs] from the element matrices of the cells touching each DOF only."""
+    touch = cells_of_dofs(md, dofs)
+    cells = sorted({c for t in touch for c, _ in t})
+    Ae = element_matrices(ref, md.verts, md.cells[cells])
+    k = {c: i for i, c in enumerate(cells)}
+    y = np.zeros(len(dofs))
+    for m, t in enumerate(touch):
+        for c, j in t:
+            y[m] += Ae[k[c]][j] @ x[md.cell_dofs[c]]
+    return y
+
+
+def patch_matrix(ref, md, v):
+    """A_V for vertex v assembled from the element matrices of its star cells."""
+    idx = md.patches_of([v])[0]
+    pos = {g: i for i, g in enumerate(idx)}
+    _, _, cells = md.vertex_star(v)
+    Ae = element_matrices(ref, md.verts, md.cells[cells])
+    AV = np.zeros((len(idx), len(idx)))
+    for a, c in enumerate(cells):
+        loc = [j for j in range(ref.ndofs) if md.cell_dofs[c, j] in pos]
+        gl = [pos[md.cell_dofs[c, j]] for j in loc]
+        AV[np.ix_(gl, gl)] += Ae[a][np.ix_(loc, loc)]
+    return idx, AV
+
+
+def sampled_precond(ref, md, dofs, r):
+    """(P^{-1} r)[dofs] for the preconditioner of Eq. (6.11), patch by patch."""
+    z = np.zeros(len(dofs))
+    cache = {}
+    for m, d in enumerate(dofs):
+        if d >= md.n_interface:
+            (c, j), = cells_of_dofs(md, [d])[0]
+            Ae = element_matrices(ref, md.verts, md.cells[[c]])[0]
+            z[m] = r[d] / Ae[j, j]
+            continue
+        for v in md.vertices_of_dof(d):
+            if v not in cache:
+                idx, AV = patch_matrix(ref, md, v)
+                cache[v] = (idx, scipy.linalg.cho_solve(scipy.linalg.cho_factor(AV, lower=True), r[idx]))
+            idx, zv = cache[v]
+            z[m] += zv[np.searchsorted(idx, d)]
+    return z

@@ -82,3 +82,26 @@ class MeshDofs:
             d += [off_f + nf_d * x + m for x in f for m in range(nf_d)]
             out.append(np.array(sorted(d), dtype=np.int64))
         return out
+
+    def patches_of(self, verts):
+        """Sorted interface DOFs of the stars of the given vertices."""
+        nv_d, ne_d, nf_d, _ = self.per_entity
+        off_v, off_e, off_f = self._offsets
+        out = []
+        for v in verts:
+            e, f, _ = self.vertex_star(v)
+            d = [off_v + nv_d * v + m for m in range(nv_d)]
+            d += [off_e + ne_d * x + m for x in e for m in range(ne_d)]
+            d += [off_f + nf_d * x + m for x in f for m in range(nf_d)]
+            out.append(np.array(sorted(d), dtype=np.int64))
+        return out
+
+    def vertices_of_dof(self, d):
+        """Mesh vertices of the entity that owns interface DOF d."""
+        nv_d, ne_d, nf_d, _ = self.per_entity
+        off_v, off_e, off_f = self._offsets
+        if d < off_e:
+            return [int((d - off_v) // nv_d)]
+        if d < off_f:
+            return [int(v) for v in self.edges[(d - off_e) // ne_d]]
+        return [int(v) for v in self.faces[(d - off_f) // nf_d]]

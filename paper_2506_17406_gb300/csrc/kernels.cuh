@@ -336,7 +336,7 @@ __global__ void k_patch_assemble(const int32_t* __restrict__ pn, const int64_t* 
 // memory and invert it, L_IK = A_IK L_KK^{-T} for the panel, then
 // A_IJ -= L_IK L_JK^T on the trailing tiles.  A non-positive pivot sets
 // info[P] and is replaced by 1.
-__global__ void __launch_bounds__(NT) k_cholesky(const int32_t* __restrict__ pn, const int64_t* __restrict__ pfoff,
+__global__ void __launch_bounds__(NT, 6) k_cholesky(const int32_t* __restrict__ pn, const int64_t* __restrict__ pfoff,
                                                  const int64_t* __restrict__ pdoff_inv,
                                                  const int64_t* __restrict__ pmoff, const int32_t* __restrict__ meta,
                                                  double* __restrict__ Lall, double* __restrict__ Dall,
@@ -652,54 +652,74 @@ __global__ void k_precond_gather(int64_t N, int64_t nifd, const int64_t* __restr
 // a9: PCG vector kernels with deterministic two-stage reductions.
 // scal layout (per right-hand side, stride 16): see riesz.cu
 // ---------------------------------------------------------------------------
-constexpr int RED_BLOCKS = 592;  // 4 x 148 partials, reduced in a fixed order
+constexpr int RED_BLOCKS = 608;  // 4 x 152 partials, reduced in a fixed order
 
-template <int K>
-__device__ __forceinline__ void block_reduce_store(double (&v)[K], double* __restrict__ out) {
-  __shared__ double sh[K][NT / 32];
+// Scalar slots (per right-hand side, stride 16).
+enum ScalarSlot { S_RZ = 0, S_PAP = 1, S_ALPHA = 2, S_RR = 3, S_BETA = 4, S_BB = 5, S_NONFINITE = 6 };
+
+// Apply the scalar step of a finished reduction.  op: 0 pAp -> alpha; 1 rr;
+// 2 rz -> beta (classic); 3 rz, r.zold -> beta (Polak-Ribiere); 4 bb; 5 rz.
+__device__ __forceinline__ void scalar_op(int op, double s0, double s1, double* __restrict__ scal) {
+  if (!isfinite(s0) || !isfinite(s1)) scal[S_NONFINITE] = 1.0;
+  if (op == 0) {
+    scal[S_PAP] = s0;
+    scal[S_ALPHA] = scal[S_RZ] / s0;
+  } else if (op == 1) {
+    scal[S_RR] = s0;
+  } else if (op == 2) {
+    scal[S_BETA] = s0 / scal[S_RZ];
+    scal[S_RZ] = s0;
+  } else if (op == 3) {
+    scal[S_BETA] = (s0 - s1) / scal[S_RZ];
+    scal[S_RZ] = s0;
+  } else if (op == 4) {
+    scal[S_BB] = s0;
+  } else if (op == 5) {
+    scal[S_RZ] = s0;
+  }
+}
+
+// Two-stage deterministic reduction in one launch: every block stores its two
+// partial sums; the last block to finish (atomic ticket after a fence) adds
+// the RED_BLOCKS partials in a fixed order, applies the scalar step and resets
+// the ticket.  No block waits for another.
+__device__ __forceinline__ void reduce2_finish(double v0, double v1, double* __restrict__ part,
+                                               unsigned* __restrict__ ticket, int op, double* __restrict__ scal) {
+  __shared__ double sh[2][NT / 32];
+  __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double s = warp_sum(v[k]);
-    if (lane == 0) sh[k][warp] = s;
+  v0 = warp_sum(v0);
+  v1 = warp_sum(v1);
+  if (lane == 0) {
+    sh[0][warp] = v0;
+    sh[1][warp] = v1;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double s = (lane < NT / 32) ? sh[k][lane] : 0.0;
-      s = warp_sum(s);
-      if (lane == 0) out[k * RED_BLOCKS + blockIdx.x] = s;
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < NT / 32; ++w) {
+      a += sh[0][w];
+      b += sh[1][w];
     }
+    part[blockIdx.x] = a;
+    part[RED_BLOCKS + blockIdx.x] = b;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == (unsigned)(gridDim.x - 1));
   }
-}
-
-// partial sums of a.b (and a.c when c != nullptr)
-__global__ void __launch_bounds__(NT) k_dot2(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
-                                            const double* __restrict__ c, double* __restrict__ part) {
-  double v[2] = {0.0, 0.0};
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * NT) {
-    const double ai = a[i];
-    v[0] = fma(ai, b[i], v[0]);
-    if (c) v[1] = fma(ai, c[i], v[1]);
-  }
-  block_reduce_store<2>(v, part);
-}
-
-// Scalar step after a reduction.  op: 0 pAp -> alpha; 1 rr; 2 rz -> beta
-// (classic); 3 rz, r.zold -> beta (Polak-Ribiere); 4 bb; 5 initial rz.
-enum ScalarSlot { S_RZ = 0, S_PAP = 1, S_ALPHA = 2, S_RR = 3, S_BETA = 4, S_BB = 5, S_NONFINITE = 6 };
-__global__ void k_scalar(const double* __restrict__ part, int op, double* __restrict__ scal) {
-  __shared__ double sh[2][NT / 32];
-  double v[2] = {0.0, 0.0};
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < RED_BLOCKS; i += NT) {
-    v[0] += part[i];
-    v[1] += part[RED_BLOCKS + i];
+    a += __ldcg(part + i);
+    b += __ldcg(part + RED_BLOCKS + i);
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = 0; k < 2; ++k) {
-    double s = warp_sum(v[k]);
-    if (lane == 0) sh[k][warp] = s;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if (lane == 0) {
+    sh[0][warp] = a;
+    sh[1][warp] = b;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -708,39 +728,38 @@ __global__ void k_scalar(const double* __restrict__ part, int op, double* __rest
       s0 += sh[0][w];
       s1 += sh[1][w];
     }
-    if (!isfinite(s0) || !isfinite(s1)) scal[S_NONFINITE] = 1.0;
-    if (op == 0) {
-      scal[S_PAP] = s0;
-      scal[S_ALPHA] = scal[S_RZ] / s0;
-    } else if (op == 1) {
-      scal[S_RR] = s0;
-    } else if (op == 2) {
-      scal[S_BETA] = s0 / scal[S_RZ];
-      scal[S_RZ] = s0;
-    } else if (op == 3) {
-      scal[S_BETA] = (s0 - s1) / scal[S_RZ];
-      scal[S_RZ] = s0;
-    } else if (op == 4) {
-      scal[S_BB] = s0;
-    } else if (op == 5) {
-      scal[S_RZ] = s0;
-    }
+    scalar_op(op, s0, s1, scal);
+    *ticket = 0u;
   }
 }
 
-// x += alpha p ; r -= alpha Ap ; partial r.r
-__global__ void __launch_bounds__(NT) k_update_xr(int64_t n, const double* __restrict__ scal, double* __restrict__ x,
+// a.b (and a.c when c != nullptr) followed by the scalar step op
+__global__ void __launch_bounds__(NT) k_dot2(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                                            const double* __restrict__ c, double* __restrict__ part,
+                                            unsigned* __restrict__ ticket, int op, double* __restrict__ scal) {
+  double v0 = 0.0, v1 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * NT) {
+    const double ai = a[i];
+    v0 = fma(ai, b[i], v0);
+    if (c) v1 = fma(ai, c[i], v1);
+  }
+  reduce2_finish(v0, v1, part, ticket, op, scal);
+}
+
+// x += alpha p ; r -= alpha Ap ; r.r -> RR
+__global__ void __launch_bounds__(NT) k_update_xr(int64_t n, double* __restrict__ scal, double* __restrict__ x,
                                                  double* __restrict__ r, const double* __restrict__ p,
-                                                 const double* __restrict__ Ap, double* __restrict__ part) {
+                                                 const double* __restrict__ Ap, double* __restrict__ part,
+                                                 unsigned* __restrict__ ticket) {
   const double alpha = scal[S_ALPHA];
-  double v[2] = {0.0, 0.0};
+  double v0 = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * NT) {
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, Ap[i], r[i]);
     r[i] = ri;
-    v[0] = fma(ri, ri, v[0]);
+    v0 = fma(ri, ri, v0);
   }
-  block_reduce_store<2>(v, part);
+  reduce2_finish(v0, 0.0, part, ticket, 1, scal);
 }
 
 // p = z + beta p
@@ -751,17 +770,46 @@ __global__ void k_update_p(int64_t n, const double* __restrict__ scal, const dou
     p[i] = fma(beta, p[i], z[i]);
 }
 
-// r = b - Ap ; partial r.r
+// r = b - Ap ; r.r -> RR
 __global__ void __launch_bounds__(NT) k_residual(int64_t n, const double* __restrict__ b,
                                                 const double* __restrict__ Ax, double* __restrict__ r,
-                                                double* __restrict__ part) {
-  double v[2] = {0.0, 0.0};
+                                                double* __restrict__ part, unsigned* __restrict__ ticket,
+                                                double* __restrict__ scal) {
+  double v0 = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * NT) {
     const double ri = b[i] - Ax[i];
     r[i] = ri;
-    v[0] = fma(ri, ri, v[0]);
+    v0 = fma(ri, ri, v0);
   }
-  block_reduce_store<2>(v, part);
+  reduce2_finish(v0, 0.0, part, ticket, 1, scal);
+}
+
+// Preconditioner gather fused with the next PCG reduction (single right-hand
+// side): z = Jacobi / patch sum as k_precond_gather, then r.z (and r.zold for
+// the flexible variant) -> scalar step op.
+__global__ void __launch_bounds__(NT) k_precond_gather_dot(int64_t N, int64_t nifd, const int64_t* __restrict__ ptr,
+                                                          const int32_t* __restrict__ pos,
+                                                          const double* __restrict__ zpatch,
+                                                          const double* __restrict__ dinv,
+                                                          const double* __restrict__ r, double* __restrict__ z,
+                                                          const double* __restrict__ zold, double* __restrict__ part,
+                                                          unsigned* __restrict__ ticket, int op,
+                                                          double* __restrict__ scal) {
+  double v0 = 0.0, v1 = 0.0;
+  for (int64_t d = blockIdx.x * (int64_t)NT + threadIdx.x; d < N; d += (int64_t)RED_BLOCKS * NT) {
+    double zi;
+    if (d < nifd) {
+      zi = 0.0;
+      for (int64_t k = ptr[d]; k < ptr[d + 1]; ++k) zi += zpatch[pos[k]];
+    } else {
+      zi = dinv[d - nifd] * r[d];
+    }
+    z[d] = zi;
+    const double ri = r[d];
+    v0 = fma(ri, zi, v0);
+    if (zold) v1 = fma(ri, zold[d], v1);
+  }
+  reduce2_finish(v0, v1, part, ticket, op, scal);
 }
 
 // ---------------------------------------------------------------------------

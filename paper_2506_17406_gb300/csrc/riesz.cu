@@ -93,14 +93,17 @@ struct riesz_handle {
   DBuf<float> d_L32, d_D32;
   DBuf<int32_t> d_cells, d_cdofs, d_sc_pos, d_pn, d_pdofs, d_pz_pos, d_pb_cell, d_pb_ent, d_cgdofs, d_meta;
   DBuf<int64_t> d_sc_ptr, d_pdoff, d_pfoff, d_pdioff, d_pmoff, d_pz_ptr, d_pb_ptr, d_pb_off;
-  DBuf<int> d_info;
+  DBuf<int> d_info;  // Cholesky status per patch
+  DBuf<unsigned> d_ticket;    // last-block ticket of the fused reductions
   // PCG workspace
   DBuf<double> d_r, d_z, d_zold, d_p, d_Ap, d_part, d_scal, d_tmp, d_xh;
   double* h_scal = nullptr;  // pinned
+  cudaEvent_t ev_scal = nullptr;  // marks the arrival of h_scal
   int last_iters = 0;
   int64_t launches = 0;
   // per-kernel CUDA-event profiler (riesz_profile)
   bool prof = false;
+  unsigned prof_mask = 0;  // kinds recorded by the profiler (bit k = kind k)
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<std::pair<int, size_t>> prof_pending;  // (kind, first event index)
@@ -126,12 +129,14 @@ struct riesz_handle {
       b->free();
     for (auto* b : {&d_sc_ptr, &d_pdoff, &d_pfoff, &d_pdioff, &d_pmoff, &d_pz_ptr, &d_pb_ptr, &d_pb_off}) b->free();
     d_info.free();
+    d_ticket.free();
     if (h_scal) cudaFreeHost(h_scal);
     h_scal = nullptr;
     on_device = false;
   }
   ~riesz_handle() {
     free_device();
+    if (ev_scal) cudaEventDestroy(ev_scal);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   }
 };
@@ -164,7 +169,8 @@ void need(bool ok, const char* msg, int code = RIESZ_ERR_INVALID_ARG) {
 template <typename F>
 void launch(riesz_handle& h, int kind, cudaStream_t s, F&& f) {
   size_t e = 0;
-  if (h.prof) {
+  const bool rec = h.prof && ((h.prof_mask >> kind) & 1u);
+  if (rec) {
     while (h.ev_pool.size() < h.ev_used + 2) {
       cudaEvent_t ev;
       CK(cudaEventCreate(&ev));
@@ -177,7 +183,7 @@ void launch(riesz_handle& h, int kind, cudaStream_t s, F&& f) {
   f();
   CK(cudaGetLastError());
   ++h.launches;
-  if (h.prof) {
+  if (rec) {
     CK(cudaEventRecord(h.ev_pool[e + 1], s));
     h.prof_pending.push_back({kind, e});
   }
@@ -510,15 +516,13 @@ void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStrea
       launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
         dev::k_patch_solve<float><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(float), s>>>(
             h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L32.p,
-            h.d_D32.p, r, h.d_zpatch.p, N,
-            zstride);
+            h.d_D32.p, r, h.d_zpatch.p, N, zstride);
       });
     } else {
       launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
         dev::k_patch_solve<double><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(double), s>>>(
             h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L64.p,
-            h.d_D64.p, r, h.d_zpatch.p, N,
-            zstride);
+            h.d_D64.p, r, h.d_zpatch.p, N, zstride);
       });
     }
   }
@@ -528,9 +532,40 @@ void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStrea
   });
 }
 
+// z = P^{-1} r for one right-hand side followed by (r, z) [and (r, zold)] -> scalar op.
+void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* zold, int op, double* scal,
+                    cudaStream_t s) {
+  const int64_t N = h.N();
+  const int npatch = (int)h.p_n.size();
+  const int nbmax = h.p_n.empty() ? 0 : (h.p_n[0] + 31) / 32;
+  const int64_t zstride = (int64_t)h.p_dofs.size();
+  if (npatch) {
+    dim3 grid(npatch, 1);
+    if (h.opts.precond_precision == RIESZ_PREC_FP32) {
+      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
+        dev::k_patch_solve<float><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(float), s>>>(
+            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L32.p,
+            h.d_D32.p, r, h.d_zpatch.p, N, zstride);
+      });
+    } else {
+      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
+        dev::k_patch_solve<double><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(double), s>>>(
+            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L64.p,
+            h.d_D64.p, r, h.d_zpatch.p, N, zstride);
+      });
+    }
+  }
+  launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
+    dev::k_precond_gather_dot<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p,
+                                                                  h.d_zpatch.p, h.d_dinv.p, r, z, zold, h.d_part.p,
+                                                                  h.d_ticket.p, op, scal);
+  });
+}
+
 void dot(riesz_handle& h, const double* a, const double* b, const double* c, int op, double* scal, cudaStream_t s) {
-  launch(h, RIESZ_K_DOT, s, [&] { dev::k_dot2<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(h.N(), a, b, c, h.d_part.p); });
-  launch(h, RIESZ_K_SCALAR, s, [&] { dev::k_scalar<<<1, dev::NT, 0, s>>>(h.d_part.p, op, scal); });
+  launch(h, RIESZ_K_DOT, s, [&] {
+    dev::k_dot2<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(h.N(), a, b, c, h.d_part.p, h.d_ticket.p, op, scal);
+  });
 }
 
 void read_scal(riesz_handle& h, const double* scal, cudaStream_t s) {
@@ -547,13 +582,11 @@ int pcg_one(riesz_handle& h, const double* b, double* x, cudaStream_t s, int* it
   auto residual = [&]() {  // r = b - A x, RR
     op_apply(h, x, h.d_Ap.p, 1, s);
     launch(h, RIESZ_K_UPDATE, s, [&] {
-      dev::k_residual<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, b, h.d_Ap.p, h.d_r.p, h.d_part.p);
+      dev::k_residual<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, b, h.d_Ap.p, h.d_r.p, h.d_part.p, h.d_ticket.p, scal);
     });
-    launch(h, RIESZ_K_SCALAR, s, [&] { dev::k_scalar<<<1, dev::NT, 0, s>>>(h.d_part.p, 1, scal); });
   };
   auto restart = [&]() {  // z = P r, p = z, RZ
-    op_precond(h, h.d_r.p, h.d_z.p, 1, s);
-    dot(h, h.d_r.p, h.d_z.p, nullptr, 5, scal, s);
+    op_precond_dot(h, h.d_r.p, h.d_z.p, nullptr, 5, scal, s);
     CK(cudaMemcpyAsync(h.d_p.p, h.d_z.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (flex) CK(cudaMemcpyAsync(h.d_zold.p, h.d_z.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   };
@@ -577,11 +610,17 @@ int pcg_one(riesz_handle& h, const double* b, double* x, cudaStream_t s, int* it
       op_apply(h, h.d_p.p, h.d_Ap.p, 1, s);
       dot(h, h.d_p.p, h.d_Ap.p, nullptr, 0, scal, s);
       launch(h, RIESZ_K_UPDATE, s, [&] {
-        dev::k_update_xr<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, scal, x, h.d_r.p, h.d_p.p, h.d_Ap.p, h.d_part.p);
+        dev::k_update_xr<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, scal, x, h.d_r.p, h.d_p.p, h.d_Ap.p, h.d_part.p,
+                                                             h.d_ticket.p);
       });
-      launch(h, RIESZ_K_SCALAR, s, [&] { dev::k_scalar<<<1, dev::NT, 0, s>>>(h.d_part.p, 1, scal); });
       ++it;
-      read_scal(h, scal, s);
+      // Copy the scalars back, then enqueue the next iteration's preconditioner
+      // before waiting for them, so the GPU is busy while the host checks
+      // convergence.  If this iteration converged, that work is discarded.
+      CK(cudaMemcpyAsync(h.h_scal, scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaEventRecord(h.ev_scal, s));
+      op_precond_dot(h, h.d_r.p, h.d_z.p, flex ? h.d_zold.p : nullptr, flex ? 3 : 2, scal, s);
+      CK(cudaEventSynchronize(h.ev_scal));
       if (h.h_scal[dev::S_NONFINITE] != 0.0 || !std::isfinite(h.h_scal[dev::S_RR])) {
         status = RIESZ_ERR_NONFINITE;
         g_err = "non-finite value in the PCG recurrence";
@@ -597,8 +636,6 @@ int pcg_one(riesz_handle& h, const double* b, double* x, cudaStream_t s, int* it
         restart();
         continue;
       }
-      op_precond(h, h.d_r.p, h.d_z.p, 1, s);
-      dot(h, h.d_r.p, h.d_z.p, flex ? h.d_zold.p : nullptr, flex ? 3 : 2, scal, s);
       launch(h, RIESZ_K_UPDATE, s, [&] { dev::k_update_p<<<1184, 256, 0, s>>>(N, scal, h.d_z.p, h.d_p.p); });
       if (flex) CK(cudaMemcpyAsync(h.d_zold.p, h.d_z.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
@@ -645,13 +682,12 @@ void device_compute(riesz_handle& h, cudaStream_t s) {
   if (npatch) {
     launch(h, RIESZ_K_ASSEMBLE, s, [&] {
       dev::k_patch_assemble<<<npatch, 256, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pmoff.p, h.d_meta.p, h.d_pb_ptr.p,
-                                                   h.d_pb_cell.p, h.d_pb_off.p,
-                                                   h.d_pb_ent.p, C, n, R.Q, h.d_g.p, h.d_R.p, h.d_Ae.p, h.d_L64.p);
+                                                   h.d_pb_cell.p, h.d_pb_off.p, h.d_pb_ent.p, C, n, R.Q, h.d_g.p,
+                                                   h.d_R.p, h.d_Ae.p, h.d_L64.p);
     });
     launch(h, RIESZ_K_CHOLESKY, s, [&] {
       dev::k_cholesky<<<npatch, dev::NT, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p,
-                                                 h.d_L64.p, h.d_D64.p,
-                                                 h.d_info.p);
+                                                 h.d_L64.p, h.d_D64.p, h.d_info.p);
     });
     if (h.opts.precond_precision == RIESZ_PREC_FP32) {
       launch(h, RIESZ_K_TO_F32, s, [&] {
@@ -715,6 +751,7 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   h.d_part.alloc(2 * dev::RED_BLOCKS);
   h.d_scal.alloc(16 * (size_t)nrhs);
   CK(cudaMallocHost((void**)&h.h_scal, 16 * sizeof(double)));
+  if (!h.ev_scal) CK(cudaEventCreateWithFlags(&h.ev_scal, cudaEventDisableTiming));
   const int npatch = (int)h.p_n.size();
   h.d_info.alloc(std::max(1, npatch));
   if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
@@ -744,6 +781,10 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     CK(cudaFuncSetAttribute(dev::k_patch_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
     CK(cudaFuncSetAttribute(dev::k_patch_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
   }
+  h.d_ticket.alloc(1);
+  CK(cudaMemsetAsync(h.d_ticket.p, 0, sizeof(unsigned), s));
+  CK(cudaFuncSetAttribute(dev::k_cholesky, cudaFuncAttributePreferredSharedMemoryCarveout,
+                          (int)cudaSharedmemCarveoutMaxShared));
   device_compute(h, s);
   h.on_device = true;
 }
@@ -1029,6 +1070,7 @@ int riesz_profile(riesz_handle* h, int enable) {
     need(h != nullptr, "null handle");
     if (!h->prof_pending.empty()) prof_collect(*h);
     h->prof = enable != 0;
+    h->prof_mask = (unsigned)enable;
     for (int k = 0; k < RIESZ_NKIND; ++k) {
       h->prof_ms[k] = 0.0;
       h->prof_cnt[k] = 0;

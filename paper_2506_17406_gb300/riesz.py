@@ -221,8 +221,12 @@ class Riesz:
     def update_geometry(self, verts_dev, stream=None):
         _check(self.lib.riesz_update_geometry(self.h, _ptr(verts_dev), _stream(stream)))
 
-    def profile(self, enable=True):
-        _check(self.lib.riesz_profile(self.h, 1 if enable else 0))
+    def profile(self, enable=True, kinds=None):
+        """Turn the per-kernel CUDA-event profiler on (all kinds, or the named ones) or off."""
+        mask = 0
+        if enable:
+            mask = -1 if kinds is None else sum(1 << KINDS.index(k) for k in kinds)
+        _check(self.lib.riesz_profile(self.h, mask))
 
     def profile_read(self):
         ms = np.zeros(len(KINDS))

@@ -215,3 +215,17 @@ def test_cg_field_load_matches_function_load():
     b1 = asm.load_cg_field(ned, mned, cg, mcg, f)
     b2 = asm.load_function(ned, mned, val)
     assert np.abs(b1 - b2).max() < 1e-12 * np.abs(b2).max()
+
+
+def test_sampled_oracle_rows_match_full_oracle():
+    """The sampled apply/preconditioner helpers used at full size equal the assembled ones."""
+    ref = reference_element("RT", 3)
+    v, c = kuhn_mesh(3, 0.1, 2)
+    md = MeshDofs(v, c, ref)
+    A = asm.assemble(md, asm.element_matrices(ref, v, c))
+    P = asm.Preconditioner(A, md)
+    x = normal_vector(md.ndofs, 1)
+    d = np.sort(np.random.Generator(np.random.PCG64(0)).choice(md.ndofs, 40, replace=False))
+    assert np.abs(asm.sampled_apply(ref, md, d, x) - (A @ x)[d]).max() < 1e-12 * np.abs(A @ x).max()
+    ze = P.apply(x)
+    assert np.abs(asm.sampled_precond(ref, md, d, x) - ze[d]).max() < 1e-11 * np.abs(ze).max()
