@@ -35,8 +35,9 @@ WORKLOADS = {
                                    "(small case for kernel profiles)"),
     "hgrad_cg3_n4": dict(space="CG", p=3, n=4, amp=0.0, prec=0, nrhs=1,
                          label="H(grad) CG_3 on 4^3 x 6 tets, FP64"),
-    "hdiv_rt8_n16": dict(space="RT", p=8, n=16, amp=0.1, prec=1, nrhs=1,
-                         label="H(div) RT_8 on 16^3 x 6 tets, perturbed 0.1h, FP64 apply + FP32 precond"),
+    "hdiv_rt8_n16": dict(space="RT", p=8, n=16, amp=0.1, prec=1, nrhs=8, a32=1,
+                         label="H(div) RT_8 on 16^3 x 6 tets, perturbed 0.1h, 8 RHS in lockstep, FP32 inner "
+                               "products and patch solves, FP64 residuals"),
 }
 DEFAULT = "hcurl_ned1_p6_n8"
 METRIC = "DOFs/s solved to 1e-8 rel. residual"
@@ -52,7 +53,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+                    help="patch solves in FP64, or FP32 (mixed)")
+    ap.add_argument("--apply-precision", default=None, choices=["fp64", "fp32"],
+                    help="precision of the operator products inside PCG (FP64 residuals either way)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -218,6 +222,10 @@ def main():
         wl["prec"] = 0
     elif args.precision == "mixed":
         wl["prec"] = 1
+    if args.apply_precision == "fp64":
+        wl["a32"] = 0
+    elif args.apply_precision == "fp32":
+        wl["a32"] = 1
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -235,23 +243,31 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     verts, cells = kuhn_mesh(wl["n"], wl["amp"], seed=1 + rank)
-    s = rz.Riesz(wl["space"], wl["p"], verts, cells, precond_precision=wl["prec"], nrhs_max=1)
+    nrhs = wl.get("nrhs", 1)
+    s = rz.Riesz(wl["space"], wl["p"], verts, cells, precond_precision=wl["prec"], nrhs_max=nrhs,
+                 apply_precision=wl.get("a32", 0))
     stream = torch.cuda.current_stream()
     verts_d = torch.tensor(verts, device="cuda")
     ncomp = 1 if wl["space"] == "CG" else 3
-    fcg_h = normal_coeffs((ncomp, s.n_cg), 2 + rank)
+    if nrhs == 1:  # f with N(0,1) CG_p coefficients per Cartesian component, b = (f, phi)
+        fcg_h = normal_coeffs((ncomp, s.n_cg), 2 + rank)
+    else:  # the paper's random right-hand side vectors (Section 7.1), one per RHS
+        fcg_h = normal_coeffs((nrhs, s.N), 2 + rank)
     fcg = torch.tensor(fcg_h, device="cuda")
-    b = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    b = torch.zeros((nrhs, s.N), dtype=torch.float64, device="cuda")
     x = torch.zeros_like(b)
     iters = []
 
     def step():
         s.update_geometry(verts_d)
-        s.load(fcg, b)
+        if nrhs == 1:
+            s.load(fcg, b)
+        else:
+            b.copy_(fcg)
         x.zero_()
-        it, rr, _ = s.solve(b, x)
+        it, rr, _ = s.solve(b, x, nrhs=nrhs)
         iters.append(int(it[0]))
-        return rr[0]
+        return float(np.max(rr))
 
     for _ in range(args.warmup):
         step()
@@ -282,7 +298,7 @@ def main():
     prof = s.profile_read()
     s.profile(False)
     ms, ntot = combine_ranks(ms, s.N, dist, device="cuda")
-    value = ntot * args.steps / (ms / 1e3)
+    value = ntot * nrhs * args.steps / (ms / 1e3)
 
     # setup / solve split from the profiler (kernel time only)
     setup_kinds = ["geom", "elem", "diag", "assemble", "cholesky", "to_f32"]
@@ -334,22 +350,25 @@ def main():
     if not args.no_e2e:
         verts_pin = torch.tensor(verts).pin_memory()
         fcg_pin = torch.tensor(fcg_h).pin_memory()
-        x_pin = torch.zeros(s.N, dtype=torch.float64).pin_memory()
+        x_pin = torch.zeros((nrhs, s.N), dtype=torch.float64).pin_memory()
         h2d = verts_pin.numel() * 8 + fcg_pin.numel() * 8
-        d2h = s.N * 8
+        d2h = s.N * nrhs * 8
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             verts_d.copy_(verts_pin, non_blocking=True)
             fcg.copy_(fcg_pin, non_blocking=True)
             s.update_geometry(verts_d)
-            s.load(fcg, b)
+            if nrhs == 1:
+                s.load(fcg, b)
+            else:
+                b.copy_(fcg)
             x.zero_()
-            s.solve(b, x)
+            s.solve(b, x, nrhs=nrhs)
             x_pin.copy_(x, non_blocking=True)
             torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        e2e = {"value": float(s.N) * args.steps / te, "unit": "DOFs/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": float(s.N) * nrhs * args.steps / te, "unit": "DOFs/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
     cb = None
@@ -363,7 +382,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl["prec"] == 0 else "f64+f32",
             "data": "synthetic",
             "config": {"workload": wl["label"], "space": wl["space"], "p": wl["p"], "cells": C, "dofs": s.N,
-                       "nrhs": 1, "rtol": 1e-8, "step": "device setup + load + PCG solve",
+                       "nrhs": nrhs, "apply_precision": "fp32" if wl.get("a32", 0) else "fp64",
+                       "precond_precision": "fp32" if wl["prec"] == 1 else "fp64",
+                       "rtol": 1e-8, "step": "device setup + load + PCG solve",
                        "l2": "inputs larger than L2 (element matrices and patch factors)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "iterations": statistics.median(iters[-args.steps:]), "max_relres": relres,

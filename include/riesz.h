@@ -3,8 +3,9 @@
  * of the de Rham complex, after Brubeck, Farrell, Kirby & Parker, "Fast solvers
  * for the high-order FEM simplicial de Rham complex" (arXiv 2506.17406).
  *
- * Problem (Eq. (2.8) with alpha = beta = 1, pure Neumann, Section 7.1): find u
- * in V with (u, v) + (d u, d v) = (f, v) for all v in V, V one of
+ * Problem (Eq. (2.8), pure Neumann, Section 7.1): find u in V with
+ * beta (u, v) + alpha (d u, d v) = (f, v) for all v in V (alpha = beta = 1 by
+ * default: the Riesz map), V one of
  *   RIESZ_H1    CG_p     (d = grad),  Eq. (2.5), k = 0
  *   RIESZ_HCURL Ned1_p   (d = curl),  Eq. (2.5), k = 1
  *   RIESZ_HDIV  RT_p     (d = div),   Eq. (2.5), k = 2
@@ -79,10 +80,21 @@ typedef struct {
   double rtol; /* target ||b - A x||_2 / ||b||_2 of riesz_solve (default 1e-8) */
   int maxit;   /* PCG iteration cap (default 1000) */
   int nrhs_max;/* largest nrhs passed to apply / precond / solve (default 1) */
+  /* Coefficients of Eq. (2.8): a(u, v) = beta (u, v) + alpha (d u, d v), both
+     positive constants (default 1, 1: the Riesz map). */
+  double alpha, beta;
+  /* Precision of the operator products inside riesz_solve's iterations
+     (RIESZ_APPLY_ELEMENT only).  RIESZ_PREC_FP32 keeps an FP32 copy of the
+     element matrices for the search-direction products and recovers FP64
+     accuracy by replacing the recursive residual with the FP64 true residual
+     b - A x whenever a right-hand side gains three digits and at convergence
+     (the stopping test is always on the FP64 residual).  riesz_apply is always
+     FP64.  Default RIESZ_PREC_FP64. */
+  int apply_precision;
 } riesz_opts;
 
 /* Fill *o with the defaults: FP64 preconditioner, element-matrix apply,
-   rtol 1e-8, maxit 1000, nrhs_max 1. */
+   rtol 1e-8, maxit 1000, nrhs_max 1, alpha = beta = 1. */
 void riesz_default_opts(riesz_opts* o);
 
 /* ---- host-only calls (no GPU needed) ---------------------------------- */
@@ -157,7 +169,10 @@ int riesz_precond(riesz_handle* h, const double* r, double* z, int nrhs, void* s
 
 /* PCG for A x = b to ||b - A x|| <= rtol ||b|| (true residual, checked at
    exit).  x: device [nrhs][N], the initial guess on entry, the solution on
-   return.  iters, relres: host [nrhs] (may be NULL).  Synchronises. */
+   return.  The right-hand sides advance in lockstep (one operator and one
+   preconditioner launch per iteration for all of them) until every one has
+   converged; iters[k] is that common count.  nrhs <= opts.nrhs_max.
+   iters, relres: host [nrhs] (may be NULL).  Synchronises. */
 int riesz_solve(riesz_handle* h, const double* b, double* x, int nrhs, void* stream, int* iters,
                 double* relres);
 

@@ -28,7 +28,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // ---------------------------------------------------------------------------
-// a1: geometry.  J = [x1-x0, x2-x0, x3-x0] * Er^{-1}; factors per space:
+// a1: geometry.  J = [x1-x0, x2-x0, x3-x0] * Er^{-1}; factors per space
+// (before the alpha/beta scaling of Eq. (2.8)):
 //   H1   : |det|, G = |det| J^{-1} J^{-T} (6)
 //   HCURL: G (6), H = J^T J / |det| (6)
 //   HDIV : H (6), 1/|det|
@@ -39,7 +40,7 @@ struct Mat3 {
 };
 
 __global__ void k_geom(int space, int64_t C, const double* __restrict__ verts, const int32_t* __restrict__ cells,
-                       Mat3 Erinv, double* __restrict__ g, double* __restrict__ jac) {
+                       Mat3 Erinv, double alpha, double beta, double* __restrict__ g, double* __restrict__ jac) {
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= C) return;
   double X[4][3];
@@ -81,15 +82,16 @@ __global__ void k_geom(int space, int64_t C, const double* __restrict__ verts, c
     G[q] = ad * s;
     H[q] = t / ad;
   }
+  // beta scales the mass factors, alpha the d-stiffness factors (Eq. (2.8))
   if (space == 0) {
-    g[c] = ad;
-    for (int q = 0; q < 6; ++q) g[(1 + q) * C + c] = G[q];
+    g[c] = beta * ad;
+    for (int q = 0; q < 6; ++q) g[(1 + q) * C + c] = alpha * G[q];
   } else if (space == 1) {
-    for (int q = 0; q < 6; ++q) g[q * C + c] = G[q];
-    for (int q = 0; q < 6; ++q) g[(6 + q) * C + c] = H[q];
+    for (int q = 0; q < 6; ++q) g[q * C + c] = beta * G[q];
+    for (int q = 0; q < 6; ++q) g[(6 + q) * C + c] = alpha * H[q];
   } else {
-    for (int q = 0; q < 6; ++q) g[q * C + c] = H[q];
-    g[6 * C + c] = 1.0 / ad;
+    for (int q = 0; q < 6; ++q) g[q * C + c] = beta * H[q];
+    g[6 * C + c] = alpha / ad;
   }
   for (int k = 0; k < 9; ++k) jac[c * 10 + k] = J[k / 3][k % 3];
   jac[c * 10 + 9] = det;
@@ -117,55 +119,83 @@ __global__ void k_elem_matrices(int64_t C, int n, int Q, const double* __restric
 // y_i = sum_j A_T[j][i] x_j: for each j the threads read the contiguous row j
 // of A_T (coalesced).  Each thread owns two adjacent rows (16-byte loads of
 // A_T and of x_j, x_{j+1} from shared memory); odd n_ref takes the scalar path.
-template <int R>
-__device__ __forceinline__ void apply_rows2(const double* __restrict__ A, const double* __restrict__ xs, int n,
-                                            int i0, double (&acc)[2][4]) {
-  const double* p = A + i0;
+template <int R, typename T>
+__device__ __forceinline__ void apply_rows2(const T* __restrict__ A, const T* __restrict__ xs, int n, int i0,
+                                            T (&acc)[2][8]) {
+  const T* p = A + i0;
   for (int j = 0; j < n; j += 2) {
-    const double2 a0 = *reinterpret_cast<const double2*>(p + (int64_t)j * n);
-    const double2 a1 = *reinterpret_cast<const double2*>(p + (int64_t)(j + 1) * n);
+    T a0x, a0y, a1x, a1y;
+    if constexpr (sizeof(T) == 8) {
+      const double2 a0 = *reinterpret_cast<const double2*>(p + (int64_t)j * n);
+      const double2 a1 = *reinterpret_cast<const double2*>(p + (int64_t)(j + 1) * n);
+      a0x = a0.x; a0y = a0.y; a1x = a1.x; a1y = a1.y;
+    } else {
+      const float2 a0 = *reinterpret_cast<const float2*>(p + (int64_t)j * n);
+      const float2 a1 = *reinterpret_cast<const float2*>(p + (int64_t)(j + 1) * n);
+      a0x = a0.x; a0y = a0.y; a1x = a1.x; a1y = a1.y;
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const double2 xv = *reinterpret_cast<const double2*>(xs + r * n + j);
-      acc[0][r] = fma(a0.x, xv.x, acc[0][r]);
-      acc[1][r] = fma(a0.y, xv.x, acc[1][r]);
-      acc[0][r] = fma(a1.x, xv.y, acc[0][r]);
-      acc[1][r] = fma(a1.y, xv.y, acc[1][r]);
+      T x0, x1;
+      if constexpr (sizeof(T) == 8) {
+        const double2 xv = *reinterpret_cast<const double2*>(xs + r * n + j);
+        x0 = xv.x;
+        x1 = xv.y;
+      } else {
+        const float2 xv = *reinterpret_cast<const float2*>(xs + r * n + j);
+        x0 = xv.x;
+        x1 = xv.y;
+      }
+      acc[0][r] = fma(a0x, x0, acc[0][r]);
+      acc[1][r] = fma(a0y, x0, acc[1][r]);
+      acc[0][r] = fma(a1x, x1, acc[0][r]);
+      acc[1][r] = fma(a1y, x1, acc[1][r]);
     }
   }
 }
 
-__global__ void k_apply_elem(int64_t C, int n, int nif, const double* __restrict__ Ae,
-                             const int32_t* __restrict__ cdofs, const double* __restrict__ x, double* __restrict__ y,
-                             double* __restrict__ Ycell, int nrhs, int64_t N) {
-  extern __shared__ double xs[];  // [nrhs][n]
+// T = double: the FP64 operator; T = float: FP32 copy of the element matrices
+// and FP32 arithmetic (inner applies of the mixed-precision solver).
+template <typename T, int RB>
+__global__ void k_apply_elem(int64_t C, int n, int nif, const T* __restrict__ Ae, const int32_t* __restrict__ cdofs,
+                             const double* __restrict__ x, double* __restrict__ y, double* __restrict__ Ycell,
+                             int nrhs, int64_t N) {
+  extern __shared__ unsigned char smraw_apply[];
+  T* xs = reinterpret_cast<T*>(smraw_apply);  // [nrhs][n]
   const int64_t c = blockIdx.x;
   for (int t = threadIdx.x; t < n * nrhs; t += blockDim.x) {
     const int r = t / n, j = t % n;
-    xs[t] = x[r * N + cdofs[(int64_t)j * C + c]];
+    xs[t] = (T)x[r * N + cdofs[(int64_t)j * C + c]];
   }
   __syncthreads();
-  const double* A = Ae + c * (int64_t)n * n;
-  auto store = [&](int i, int r, double v) {
+  const T* A = Ae + c * (int64_t)n * n;
+  auto store = [&](int i, int r, T v) {
     if (i >= nif)
-      y[r * N + cdofs[(int64_t)i * C + c]] = v;
+      y[r * N + cdofs[(int64_t)i * C + c]] = (double)v;
     else
-      Ycell[((int64_t)r * nif + i) * C + c] = v;
+      Ycell[((int64_t)r * nif + i) * C + c] = (double)v;
   };
   if ((n & 1) == 0) {
     for (int i0 = 2 * threadIdx.x; i0 < n; i0 += 2 * blockDim.x) {
-      for (int r0 = 0; r0 < nrhs; r0 += 4) {
-        double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-        const int nr = min(4, nrhs - r0);
-        const double* xr = xs + r0 * n;
-        if (nr == 1)
-          apply_rows2<1>(A, xr, n, i0, acc);
-        else if (nr == 2)
-          apply_rows2<2>(A, xr, n, i0, acc);
-        else if (nr == 3)
-          apply_rows2<3>(A, xr, n, i0, acc);
-        else
-          apply_rows2<4>(A, xr, n, i0, acc);
+      for (int r0 = 0; r0 < nrhs; r0 += RB) {
+        T acc[2][8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[0][k] = acc[1][k] = (T)0;
+        const int nr = min(RB, nrhs - r0);
+        const T* xr = xs + r0 * n;
+        if (RB == 1 || nr == RB) {
+          apply_rows2<RB>(A, xr, n, i0, acc);
+        } else {
+          switch (nr) {
+            case 1: apply_rows2<1>(A, xr, n, i0, acc); break;
+            case 2: apply_rows2<2>(A, xr, n, i0, acc); break;
+            case 3: apply_rows2<3>(A, xr, n, i0, acc); break;
+            case 4: apply_rows2<4>(A, xr, n, i0, acc); break;
+            case 5: apply_rows2<5>(A, xr, n, i0, acc); break;
+            case 6: apply_rows2<6>(A, xr, n, i0, acc); break;
+            default: apply_rows2<7>(A, xr, n, i0, acc); break;
+          }
+        }
         for (int k = 0; k < nr; ++k) {
           store(i0, r0 + k, acc[0][k]);
           store(i0 + 1, r0 + k, acc[1][k]);
@@ -175,7 +205,7 @@ __global__ void k_apply_elem(int64_t C, int n, int nif, const double* __restrict
   } else {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       for (int r = 0; r < nrhs; ++r) {
-        double acc = 0.0;
+        T acc = 0;
         for (int j = 0; j < n; ++j) acc = fma(A[(int64_t)j * n + i], xs[r * n + j], acc);
         store(i, r, acc);
       }
@@ -629,6 +659,169 @@ __global__ void __launch_bounds__(NT) k_patch_solve(const int32_t* __restrict__ 
   for (int i = tid; i < n; i += NT) zp[i] = (double)y[i];
 }
 
+// a7 for several right-hand sides at once (2..8): every factor tile is loaded
+// once and applied to all of them, so the HBM traffic per right-hand side
+// drops by their number.  Same tiling and thread mapping as k_patch_solve.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_patch_solve_multi(
+    const int32_t* __restrict__ pn, const int64_t* __restrict__ pdoff, const int64_t* __restrict__ pfoff,
+    const int64_t* __restrict__ pdoff_inv, const int64_t* __restrict__ pmoff, const int32_t* __restrict__ meta,
+    const int32_t* __restrict__ pdofs, const T* __restrict__ Lall, const T* __restrict__ Dall,
+    const double* __restrict__ r, double* __restrict__ zpatch, int64_t N, int64_t zstride, int nr) {
+  constexpr int RM = 8;
+  extern __shared__ unsigned char smraw[];
+  __shared__ T red2[NT / 32][RM][32];
+  __shared__ T tvec[RM][32];
+  __shared__ int clist[MAXNB], cJ[MAXNB];
+  __shared__ int ncl;
+  const int P = blockIdx.x;
+  const int n = pn[P];
+  const int nb = (n + 31) / 32;
+  const int ld = nb * 32;
+  T* y = reinterpret_cast<T*>(smraw);  // [nr][nb*32]
+  const int32_t* tix = meta + pmoff[P];
+  const int32_t* tcol = tix + nb * nb;
+  const T* L = Lall + pfoff[P];
+  const T* Dv = Dall + pdoff_inv[P];
+  const int32_t* dofs = pdofs + pdoff[P];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int row = tid >> 3, q = tid & 7;
+  for (int t = tid; t < nr * ld; t += NT) {
+    const int rh = t / ld, i = t % ld;
+    y[t] = (i < n) ? (T)r[rh * N + dofs[i]] : (T)0;
+  }
+  __syncthreads();
+  // forward
+  int t0 = 0;
+  for (int I = 0; I < nb; ++I) {
+    const int td = tix[I * nb + I];
+    T acc[RM];
+#pragma unroll
+    for (int k = 0; k < RM; ++k) acc[k] = 0;
+    const T* base = L + row * 32 + 4 * q;
+    for (int t = t0; t < td; ++t) {
+      T a[4];
+      Vec4<T>::load(base + (int64_t)t * 1024, a);
+      const int off = tcol[t] * 32 + 4 * q;
+#pragma unroll
+      for (int k = 0; k < RM; ++k)
+        if (k < nr) {
+          const T* yk = y + k * ld + off;
+          acc[k] += a[0] * yk[0] + a[1] * yk[1] + a[2] * yk[2] + a[3] * yk[3];
+        }
+    }
+    t0 = td + 1;
+#pragma unroll
+    for (int k = 0; k < RM; ++k) {
+      if (k < nr) {
+        T v = acc[k];
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        if (q == 0) tvec[k][row] = y[k * ld + I * 32 + row] - v;
+      }
+    }
+    __syncthreads();
+    T a[4];
+    Vec4<T>::load(Dv + I * 1024 + row * 32 + 4 * q, a);
+#pragma unroll
+    for (int k = 0; k < RM; ++k) {
+      if (k < nr) {
+        T v = a[0] * tvec[k][4 * q] + a[1] * tvec[k][4 * q + 1] + a[2] * tvec[k][4 * q + 2] + a[3] * tvec[k][4 * q + 3];
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        if (q == 0) y[k * ld + I * 32 + row] = v;
+      }
+    }
+    __syncthreads();
+  }
+  // backward
+  for (int I = nb - 1; I >= 0; --I) {
+    if (tid == 0) {
+      int m = 0;
+      for (int J = I + 1; J < nb; ++J) {
+        const int t = tix[J * nb + I];
+        if (t >= 0) {
+          clist[m] = t;
+          cJ[m] = J;
+          ++m;
+        }
+      }
+      ncl = m;
+    }
+    __syncthreads();
+    const int m = ncl;
+    T acc[RM][4];
+#pragma unroll
+    for (int k = 0; k < RM; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0;
+    for (int kk = 0; kk < m; ++kk) {
+      T a[4];
+      Vec4<T>::load(L + (int64_t)clist[kk] * 1024 + row * 32 + 4 * q, a);
+      const int off = cJ[kk] * 32 + row;
+#pragma unroll
+      for (int k = 0; k < RM; ++k)
+        if (k < nr) {
+          const T xr = y[k * ld + off];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[k][c] += a[c] * xr;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < RM; ++k)
+      if (k < nr) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[k][c] += __shfl_xor_sync(0xffffffffu, acc[k][c], 8);
+          acc[k][c] += __shfl_xor_sync(0xffffffffu, acc[k][c], 16);
+        }
+        if (lane < 8) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) red2[warp][k][4 * q + c] = acc[k][c];
+        }
+      }
+    __syncthreads();
+    for (int t = tid; t < nr * 32; t += NT) {
+      const int k = t >> 5, c = t & 31;
+      T sum = 0;
+      for (int w = 0; w < NT / 32; ++w) sum += red2[w][k][c];
+      tvec[k][c] = y[k * ld + I * 32 + c] - sum;
+    }
+    __syncthreads();
+    // x_I = Dinv^T t for every right-hand side
+    T b4[4];
+    Vec4<T>::load(Dv + I * 1024 + row * 32 + 4 * q, b4);
+#pragma unroll
+    for (int k = 0; k < RM; ++k)
+      if (k < nr) {
+        const T tr = tvec[k][row];
+        T part[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          part[c] = b4[c] * tr;
+          part[c] += __shfl_xor_sync(0xffffffffu, part[c], 8);
+          part[c] += __shfl_xor_sync(0xffffffffu, part[c], 16);
+        }
+        if (lane < 8) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) red2[warp][k][4 * q + c] = part[c];
+        }
+      }
+    __syncthreads();
+    for (int t = tid; t < nr * 32; t += NT) {
+      const int k = t >> 5, c = t & 31;
+      T sum = 0;
+      for (int w = 0; w < NT / 32; ++w) sum += red2[w][k][c];
+      y[k * ld + I * 32 + c] = sum;
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < nr * n; t += NT) {
+    const int rh = t / n, i = t % n;
+    zpatch[rh * zstride + pdoff[P] + i] = (double)y[rh * ld + i];
+  }
+}
+
 // z = diag(A_II)^{-1} r on the interior, sum of patch results on the interface.
 __global__ void k_precond_gather(int64_t N, int64_t nifd, const int64_t* __restrict__ ptr,
                                  const int32_t* __restrict__ pos, const double* __restrict__ zpatch, int64_t zstride,
@@ -655,23 +848,28 @@ __global__ void k_precond_gather(int64_t N, int64_t nifd, const int64_t* __restr
 constexpr int RED_BLOCKS = 608;  // 4 x 152 partials, reduced in a fixed order
 
 // Scalar slots (per right-hand side, stride 16).
-enum ScalarSlot { S_RZ = 0, S_PAP = 1, S_ALPHA = 2, S_RR = 3, S_BETA = 4, S_BB = 5, S_NONFINITE = 6 };
+// S_RZNEW holds (r, z) of a preconditioner step until k_update_p commits it to
+// S_RZ, so a speculative step can be recomputed after a residual replacement.
+enum ScalarSlot { S_RZ = 0, S_PAP = 1, S_ALPHA = 2, S_RR = 3, S_BETA = 4, S_BB = 5, S_NONFINITE = 6, S_RZNEW = 7 };
+constexpr int SCAL_STRIDE = 16;  // doubles of scalars per right-hand side
 
 // Apply the scalar step of a finished reduction.  op: 0 pAp -> alpha; 1 rr;
-// 2 rz -> beta (classic); 3 rz, r.zold -> beta (Polak-Ribiere); 4 bb; 5 rz.
+// 2 rz -> beta (classic); 3 rz, r.zold -> beta (Polak-Ribiere); 4 bb;
+// 5 rz (restart).  A zero denominator (a right-hand side that has converged
+// exactly while others iterate) gives a zero step.
 __device__ __forceinline__ void scalar_op(int op, double s0, double s1, double* __restrict__ scal) {
   if (!isfinite(s0) || !isfinite(s1)) scal[S_NONFINITE] = 1.0;
   if (op == 0) {
     scal[S_PAP] = s0;
-    scal[S_ALPHA] = scal[S_RZ] / s0;
+    scal[S_ALPHA] = (s0 != 0.0) ? scal[S_RZ] / s0 : 0.0;
   } else if (op == 1) {
     scal[S_RR] = s0;
   } else if (op == 2) {
-    scal[S_BETA] = s0 / scal[S_RZ];
-    scal[S_RZ] = s0;
+    scal[S_BETA] = (scal[S_RZ] != 0.0) ? s0 / scal[S_RZ] : 0.0;
+    scal[S_RZNEW] = s0;
   } else if (op == 3) {
-    scal[S_BETA] = (s0 - s1) / scal[S_RZ];
-    scal[S_RZ] = s0;
+    scal[S_BETA] = (scal[S_RZ] != 0.0) ? (s0 - s1) / scal[S_RZ] : 0.0;
+    scal[S_RZNEW] = s0;
   } else if (op == 4) {
     scal[S_BB] = s0;
   } else if (op == 5) {
@@ -685,6 +883,10 @@ __device__ __forceinline__ void scalar_op(int op, double s0, double s1, double* 
 // the ticket.  No block waits for another.
 __device__ __forceinline__ void reduce2_finish(double v0, double v1, double* __restrict__ part,
                                                unsigned* __restrict__ ticket, int op, double* __restrict__ scal) {
+  // one grid row per right-hand side
+  part += (int64_t)blockIdx.y * 2 * RED_BLOCKS;
+  ticket += blockIdx.y;
+  scal += blockIdx.y * SCAL_STRIDE;
   __shared__ double sh[2][NT / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -737,6 +939,9 @@ __device__ __forceinline__ void reduce2_finish(double v0, double v1, double* __r
 __global__ void __launch_bounds__(NT) k_dot2(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
                                             const double* __restrict__ c, double* __restrict__ part,
                                             unsigned* __restrict__ ticket, int op, double* __restrict__ scal) {
+  a += blockIdx.y * n;
+  b += blockIdx.y * n;
+  if (c) c += blockIdx.y * n;
   double v0 = 0.0, v1 = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * NT) {
     const double ai = a[i];
@@ -751,7 +956,12 @@ __global__ void __launch_bounds__(NT) k_update_xr(int64_t n, double* __restrict_
                                                  double* __restrict__ r, const double* __restrict__ p,
                                                  const double* __restrict__ Ap, double* __restrict__ part,
                                                  unsigned* __restrict__ ticket) {
-  const double alpha = scal[S_ALPHA];
+  const int64_t o = blockIdx.y * n;
+  x += o;
+  r += o;
+  p += o;
+  Ap += o;
+  const double alpha = scal[blockIdx.y * SCAL_STRIDE + S_ALPHA];
   double v0 = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * NT) {
     x[i] = fma(alpha, p[i], x[i]);
@@ -762,12 +972,15 @@ __global__ void __launch_bounds__(NT) k_update_xr(int64_t n, double* __restrict_
   reduce2_finish(v0, 0.0, part, ticket, 1, scal);
 }
 
-// p = z + beta p
-__global__ void k_update_p(int64_t n, const double* __restrict__ scal, const double* __restrict__ z,
+// p = z + beta p, and commit (r, z) of this step: RZ = RZNEW
+__global__ void k_update_p(int64_t n, double* __restrict__ scal, const double* __restrict__ z,
                            double* __restrict__ p) {
+  const int64_t o = blockIdx.y * n;
+  scal += blockIdx.y * SCAL_STRIDE;
   const double beta = scal[S_BETA];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fma(beta, p[i], z[i]);
+    p[o + i] = fma(beta, p[o + i], z[o + i]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) scal[S_RZ] = scal[S_RZNEW];
 }
 
 // r = b - Ap ; r.r -> RR
@@ -775,6 +988,10 @@ __global__ void __launch_bounds__(NT) k_residual(int64_t n, const double* __rest
                                                 const double* __restrict__ Ax, double* __restrict__ r,
                                                 double* __restrict__ part, unsigned* __restrict__ ticket,
                                                 double* __restrict__ scal) {
+  const int64_t o = blockIdx.y * n;
+  b += o;
+  Ax += o;
+  r += o;
   double v0 = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * NT) {
     const double ri = b[i] - Ax[i];
@@ -784,9 +1001,9 @@ __global__ void __launch_bounds__(NT) k_residual(int64_t n, const double* __rest
   reduce2_finish(v0, 0.0, part, ticket, 1, scal);
 }
 
-// Preconditioner gather fused with the next PCG reduction (single right-hand
-// side): z = Jacobi / patch sum as k_precond_gather, then r.z (and r.zold for
-// the flexible variant) -> scalar step op.
+// Preconditioner gather fused with the next PCG reduction (one grid row per
+// right-hand side): z = Jacobi / patch sum as k_precond_gather, then r.z (and
+// r.zold for the flexible variant) -> scalar step op.
 __global__ void __launch_bounds__(NT) k_precond_gather_dot(int64_t N, int64_t nifd, const int64_t* __restrict__ ptr,
                                                           const int32_t* __restrict__ pos,
                                                           const double* __restrict__ zpatch,
@@ -794,7 +1011,12 @@ __global__ void __launch_bounds__(NT) k_precond_gather_dot(int64_t N, int64_t ni
                                                           const double* __restrict__ r, double* __restrict__ z,
                                                           const double* __restrict__ zold, double* __restrict__ part,
                                                           unsigned* __restrict__ ticket, int op,
-                                                          double* __restrict__ scal) {
+                                                          double* __restrict__ scal, int64_t zstride) {
+  const int64_t o = blockIdx.y * N;
+  zpatch += blockIdx.y * zstride;
+  r += o;
+  z += o;
+  if (zold) zold += o;
   double v0 = 0.0, v1 = 0.0;
   for (int64_t d = blockIdx.x * (int64_t)NT + threadIdx.x; d < N; d += (int64_t)RED_BLOCKS * NT) {
     double zi;

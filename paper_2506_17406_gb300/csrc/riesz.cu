@@ -90,7 +90,8 @@ struct riesz_handle {
   bool on_device = false;
   int device = 0;
   DBuf<double> d_verts, d_g, d_jac, d_R, d_Ae, d_Ycell, d_dinv, d_L64, d_D64, d_zpatch, d_X;
-  DBuf<float> d_L32, d_D32;
+  DBuf<float> d_L32, d_D32, d_Ae32;
+  int multi_group = 8;  // right-hand sides per k_patch_solve_multi launch
   DBuf<int32_t> d_cells, d_cdofs, d_sc_pos, d_pn, d_pdofs, d_pz_pos, d_pb_cell, d_pb_ent, d_cgdofs, d_meta;
   DBuf<int64_t> d_sc_ptr, d_pdoff, d_pfoff, d_pdioff, d_pmoff, d_pz_ptr, d_pb_ptr, d_pb_off;
   DBuf<int> d_info;  // Cholesky status per patch
@@ -113,7 +114,7 @@ struct riesz_handle {
   int64_t C() const { return mesh.ncells; }
   size_t device_bytes() const {
     return d_verts.bytes() + d_g.bytes() + d_jac.bytes() + d_R.bytes() + d_Ae.bytes() + d_Ycell.bytes() +
-           d_dinv.bytes() + d_L64.bytes() + d_L32.bytes() + d_D64.bytes() + d_D32.bytes() + d_zpatch.bytes() + d_X.bytes() + d_cells.bytes() +
+           d_dinv.bytes() + d_L64.bytes() + d_L32.bytes() + d_Ae32.bytes() + d_D64.bytes() + d_D32.bytes() + d_zpatch.bytes() + d_X.bytes() + d_cells.bytes() +
            d_cdofs.bytes() + d_sc_pos.bytes() + d_pn.bytes() + d_pdofs.bytes() + d_pz_pos.bytes() +
            d_pb_cell.bytes() + d_pb_ent.bytes() + d_cgdofs.bytes() + d_sc_ptr.bytes() + d_pdoff.bytes() +
            d_pfoff.bytes() + d_pdioff.bytes() + d_pmoff.bytes() + d_meta.bytes() + d_pz_ptr.bytes() + d_pb_ptr.bytes() + d_pb_off.bytes() + d_r.bytes() + d_z.bytes() +
@@ -125,6 +126,7 @@ struct riesz_handle {
       b->free();
     d_L32.free();
     d_D32.free();
+    d_Ae32.free();
     for (auto* b : {&d_cells, &d_cdofs, &d_sc_pos, &d_pn, &d_pdofs, &d_pz_pos, &d_pb_cell, &d_pb_ent, &d_cgdofs, &d_meta})
       b->free();
     for (auto* b : {&d_sc_ptr, &d_pdoff, &d_pfoff, &d_pdioff, &d_pmoff, &d_pz_ptr, &d_pb_ptr, &d_pb_off}) b->free();
@@ -480,16 +482,35 @@ cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // ---- operator pieces ------------------------------------------------------
-void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_t s) {
+// y = A x for nrhs right-hand sides; fp32 selects the FP32 copy of the element
+// matrices (inner applies of the mixed-precision solver).
+void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_t s, bool fp32 = false) {
   const int n = h.mesh.nref;
   const int64_t C = h.C(), N = h.N();
   if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
-    const size_t sm = (size_t)n * nrhs * sizeof(double);
     const int rows = (n % 2 == 0) ? n / 2 : n;
     const int nt = std::min(1024, (rows + 31) / 32 * 32);
-    launch(h, RIESZ_K_APPLY, s, [&] {
-      dev::k_apply_elem<<<(unsigned)C, nt, sm, s>>>(C, n, h.nif, h.d_Ae.p, h.d_cdofs.p, x, y, h.d_Ycell.p, nrhs, N);
-    });
+    if (fp32) {
+      const size_t sm = (size_t)n * nrhs * sizeof(float);
+      launch(h, RIESZ_K_APPLY, s, [&] {
+        if (nrhs == 1)
+          dev::k_apply_elem<float, 1><<<(unsigned)C, nt, sm, s>>>(C, n, h.nif, h.d_Ae32.p, h.d_cdofs.p, x, y,
+                                                                  h.d_Ycell.p, nrhs, N);
+        else
+          dev::k_apply_elem<float, 8><<<(unsigned)C, nt, sm, s>>>(C, n, h.nif, h.d_Ae32.p, h.d_cdofs.p, x, y,
+                                                                  h.d_Ycell.p, nrhs, N);
+      });
+    } else {
+      const size_t sm = (size_t)n * nrhs * sizeof(double);
+      launch(h, RIESZ_K_APPLY, s, [&] {
+        if (nrhs == 1)
+          dev::k_apply_elem<double, 1><<<(unsigned)C, nt, sm, s>>>(C, n, h.nif, h.d_Ae.p, h.d_cdofs.p, x, y,
+                                                                   h.d_Ycell.p, nrhs, N);
+        else
+          dev::k_apply_elem<double, 8><<<(unsigned)C, nt, sm, s>>>(C, n, h.nif, h.d_Ae.p, h.d_cdofs.p, x, y,
+                                                                   h.d_Ycell.p, nrhs, N);
+      });
+    }
   } else {
     const size_t sm = ((size_t)n + h.ref->Q) * dev::TC * sizeof(double);
     dim3 grid(nblk(C, dev::TC), nrhs);
@@ -505,148 +526,196 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
   });
 }
 
+// Patch sweeps for nrhs right-hand sides into zpatch.
+void op_patch_solves(riesz_handle& h, const double* r, int nrhs, cudaStream_t s) {
+  const int64_t N = h.N();
+  const int npatch = (int)h.p_n.size();
+  if (!npatch) return;
+  const int nbmax = (h.p_n[0] + 31) / 32;
+  const int64_t zstride = (int64_t)h.p_dofs.size();
+  const bool f32 = h.opts.precond_precision == RIESZ_PREC_FP32;
+  if (nrhs == 1) {
+    dim3 grid(npatch, 1);
+    if (f32)
+      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
+        dev::k_patch_solve<float><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(float), s>>>(
+            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L32.p,
+            h.d_D32.p, r, h.d_zpatch.p, N, zstride);
+      });
+    else
+      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
+        dev::k_patch_solve<double><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(double), s>>>(
+            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L64.p,
+            h.d_D64.p, r, h.d_zpatch.p, N, zstride);
+      });
+    return;
+  }
+  for (int r0 = 0; r0 < nrhs; r0 += h.multi_group) {
+    const int nr = std::min(h.multi_group, nrhs - r0);
+    const double* rr = r + (int64_t)r0 * N;
+    double* zp = h.d_zpatch.p + (int64_t)r0 * zstride;
+    if (f32)
+      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
+        dev::k_patch_solve_multi<float><<<npatch, dev::NT, (size_t)nr * nbmax * 32 * sizeof(float), s>>>(
+            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L32.p,
+            h.d_D32.p, rr, zp, N, zstride, nr);
+      });
+    else
+      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
+        dev::k_patch_solve_multi<double><<<npatch, dev::NT, (size_t)nr * nbmax * 32 * sizeof(double), s>>>(
+            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L64.p,
+            h.d_D64.p, rr, zp, N, zstride, nr);
+      });
+  }
+}
+
 void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStream_t s) {
   const int64_t N = h.N();
-  const int npatch = (int)h.p_n.size();
-  const int nbmax = h.p_n.empty() ? 0 : (h.p_n[0] + 31) / 32;
-  const int64_t zstride = (int64_t)h.p_dofs.size();
-  if (npatch) {
-    dim3 grid(npatch, nrhs);
-    if (h.opts.precond_precision == RIESZ_PREC_FP32) {
-      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
-        dev::k_patch_solve<float><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(float), s>>>(
-            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L32.p,
-            h.d_D32.p, r, h.d_zpatch.p, N, zstride);
-      });
-    } else {
-      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
-        dev::k_patch_solve<double><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(double), s>>>(
-            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L64.p,
-            h.d_D64.p, r, h.d_zpatch.p, N, zstride);
-      });
-    }
-  }
+  op_patch_solves(h, r, nrhs, s);
   launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
     dev::k_precond_gather<<<nblk(N, 256), 256, 0, s>>>(N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p,
-                                                      zstride, h.d_dinv.p, r, z, nrhs);
+                                                      (int64_t)h.p_dofs.size(), h.d_dinv.p, r, z, nrhs);
   });
 }
 
-// z = P^{-1} r for one right-hand side followed by (r, z) [and (r, zold)] -> scalar op.
-void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* zold, int op, double* scal,
+// z = P^{-1} r followed by (r, z) [and (r, zold)] -> scalar op, per right-hand side.
+void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* zold, int op, double* scal, int nrhs,
                     cudaStream_t s) {
   const int64_t N = h.N();
-  const int npatch = (int)h.p_n.size();
-  const int nbmax = h.p_n.empty() ? 0 : (h.p_n[0] + 31) / 32;
-  const int64_t zstride = (int64_t)h.p_dofs.size();
-  if (npatch) {
-    dim3 grid(npatch, 1);
-    if (h.opts.precond_precision == RIESZ_PREC_FP32) {
-      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
-        dev::k_patch_solve<float><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(float), s>>>(
-            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L32.p,
-            h.d_D32.p, r, h.d_zpatch.p, N, zstride);
-      });
-    } else {
-      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
-        dev::k_patch_solve<double><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(double), s>>>(
-            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L64.p,
-            h.d_D64.p, r, h.d_zpatch.p, N, zstride);
-      });
-    }
-  }
+  op_patch_solves(h, r, nrhs, s);
   launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
-    dev::k_precond_gather_dot<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p,
-                                                                  h.d_zpatch.p, h.d_dinv.p, r, z, zold, h.d_part.p,
-                                                                  h.d_ticket.p, op, scal);
+    dev::k_precond_gather_dot<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(
+        N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p, h.d_dinv.p, r, z, zold, h.d_part.p,
+        h.d_ticket.p, op, scal, (int64_t)h.p_dofs.size());
   });
 }
 
-void dot(riesz_handle& h, const double* a, const double* b, const double* c, int op, double* scal, cudaStream_t s) {
+void dot(riesz_handle& h, const double* a, const double* b, const double* c, int op, double* scal, int nrhs,
+         cudaStream_t s) {
   launch(h, RIESZ_K_DOT, s, [&] {
-    dev::k_dot2<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(h.N(), a, b, c, h.d_part.p, h.d_ticket.p, op, scal);
+    dev::k_dot2<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(h.N(), a, b, c, h.d_part.p, h.d_ticket.p, op, scal);
   });
 }
 
-void read_scal(riesz_handle& h, const double* scal, cudaStream_t s) {
-  CK(cudaMemcpyAsync(h.h_scal, scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+void read_scal(riesz_handle& h, const double* scal, int nrhs, cudaStream_t s) {
+  CK(cudaMemcpyAsync(h.h_scal, scal, (size_t)nrhs * dev::SCAL_STRIDE * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
 }
 
-// PCG for one right-hand side; returns a status code.
-int pcg_one(riesz_handle& h, const double* b, double* x, cudaStream_t s, int* iters_out, double* relres_out) {
+// PCG for nrhs right-hand sides in lockstep (Section 7.1): one apply and one
+// preconditioner launch serve all of them.  With apply_precision FP32 the
+// search-direction products use the FP32 element matrices and the residual is
+// replaced by the FP64 true residual whenever a right-hand side has gained
+// three more digits (reliable updates), and at convergence.
+int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_t s, int* iters_out,
+              double* relres_out) {
   const int64_t N = h.N();
   double* scal = h.d_scal.p;
-  const bool flex = h.opts.precond_precision == RIESZ_PREC_FP32;
-  CK(cudaMemsetAsync(scal, 0, 16 * sizeof(double), s));
-  auto residual = [&]() {  // r = b - A x, RR
-    op_apply(h, x, h.d_Ap.p, 1, s);
+  const int SS = dev::SCAL_STRIDE;
+  const bool a32 = h.opts.apply_precision == RIESZ_PREC_FP32 && h.opts.apply_mode == RIESZ_APPLY_ELEMENT;
+  const bool flex = h.opts.precond_precision == RIESZ_PREC_FP32 || a32;
+  double* r = h.d_r.p;
+  double* z = h.d_z.p;
+  double* zold = h.d_zold.p;
+  double* p = h.d_p.p;
+  double* Ap = h.d_Ap.p;
+  CK(cudaMemsetAsync(scal, 0, (size_t)nrhs * SS * sizeof(double), s));
+  auto residual = [&]() {  // r = b - A x (FP64), RR
+    op_apply(h, x, Ap, nrhs, s);
     launch(h, RIESZ_K_UPDATE, s, [&] {
-      dev::k_residual<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, b, h.d_Ap.p, h.d_r.p, h.d_part.p, h.d_ticket.p, scal);
+      dev::k_residual<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(N, b, Ap, r, h.d_part.p, h.d_ticket.p, scal);
     });
   };
   auto restart = [&]() {  // z = P r, p = z, RZ
-    op_precond_dot(h, h.d_r.p, h.d_z.p, nullptr, 5, scal, s);
-    CK(cudaMemcpyAsync(h.d_p.p, h.d_z.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (flex) CK(cudaMemcpyAsync(h.d_zold.p, h.d_z.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    op_precond_dot(h, r, z, nullptr, 5, scal, nrhs, s);
+    CK(cudaMemcpyAsync(p, z, (size_t)nrhs * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (flex) CK(cudaMemcpyAsync(zold, z, (size_t)nrhs * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   };
-  dot(h, b, b, nullptr, 4, scal, s);
+  auto nonfinite = [&]() {
+    for (int k = 0; k < nrhs; ++k)
+      if (h.h_scal[k * SS + dev::S_NONFINITE] != 0.0 || !std::isfinite(h.h_scal[k * SS + dev::S_RR])) return true;
+    return false;
+  };
+  dot(h, b, b, nullptr, 4, scal, nrhs, s);
   residual();
-  read_scal(h, scal, s);
-  const double bb = h.h_scal[dev::S_BB];
-  if (!std::isfinite(bb) || h.h_scal[dev::S_NONFINITE] != 0.0) {
+  read_scal(h, scal, nrhs, s);
+  std::vector<double> bb(nrhs), tol2(nrhs), rr_last(nrhs);
+  for (int k = 0; k < nrhs; ++k) {
+    bb[k] = h.h_scal[k * SS + dev::S_BB];
+    tol2[k] = h.opts.rtol * h.opts.rtol * bb[k];
+    rr_last[k] = h.h_scal[k * SS + dev::S_RR];
+  }
+  if (nonfinite()) {
     g_err = "non-finite right-hand side or initial guess";
     return RIESZ_ERR_NONFINITE;
   }
-  const double tol2 = h.opts.rtol * h.opts.rtol * bb;
+  auto all_below = [&]() {
+    for (int k = 0; k < nrhs; ++k)
+      if (!(h.h_scal[k * SS + dev::S_RR] <= tol2[k])) return false;
+    return true;
+  };
   int it = 0;
   int status = RIESZ_ERR_NOT_CONVERGED;
-  double rr = h.h_scal[dev::S_RR];
-  if (bb == 0.0 || rr <= tol2) {
+  if (all_below()) {
     status = RIESZ_OK;
   } else {
     restart();
     while (it < h.opts.maxit) {
-      op_apply(h, h.d_p.p, h.d_Ap.p, 1, s);
-      dot(h, h.d_p.p, h.d_Ap.p, nullptr, 0, scal, s);
+      op_apply(h, p, Ap, nrhs, s, a32);
+      dot(h, p, Ap, nullptr, 0, scal, nrhs, s);
       launch(h, RIESZ_K_UPDATE, s, [&] {
-        dev::k_update_xr<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(N, scal, x, h.d_r.p, h.d_p.p, h.d_Ap.p, h.d_part.p,
-                                                             h.d_ticket.p);
+        dev::k_update_xr<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(N, scal, x, r, p, Ap, h.d_part.p,
+                                                                          h.d_ticket.p);
       });
       ++it;
-      // Copy the scalars back, then enqueue the next iteration's preconditioner
-      // before waiting for them, so the GPU is busy while the host checks
-      // convergence.  If this iteration converged, that work is discarded.
-      CK(cudaMemcpyAsync(h.h_scal, scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      // Copy the scalars back, then enqueue the next preconditioner step before
+      // waiting for them, so the GPU is busy while the host checks convergence.
+      CK(cudaMemcpyAsync(h.h_scal, scal, (size_t)nrhs * SS * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaEventRecord(h.ev_scal, s));
-      op_precond_dot(h, h.d_r.p, h.d_z.p, flex ? h.d_zold.p : nullptr, flex ? 3 : 2, scal, s);
+      op_precond_dot(h, r, z, flex ? zold : nullptr, flex ? 3 : 2, scal, nrhs, s);
       CK(cudaEventSynchronize(h.ev_scal));
-      if (h.h_scal[dev::S_NONFINITE] != 0.0 || !std::isfinite(h.h_scal[dev::S_RR])) {
+      if (nonfinite()) {
         status = RIESZ_ERR_NONFINITE;
         g_err = "non-finite value in the PCG recurrence";
         break;
       }
-      if (h.h_scal[dev::S_RR] <= tol2) {
+      if (all_below()) {
         residual();  // verify on the true residual
-        read_scal(h, scal, s);
-        if (h.h_scal[dev::S_RR] <= tol2) {
+        read_scal(h, scal, nrhs, s);
+        if (all_below()) {
           status = RIESZ_OK;
           break;
         }
+        for (int k = 0; k < nrhs; ++k) rr_last[k] = h.h_scal[k * SS + dev::S_RR];
         restart();
         continue;
       }
-      launch(h, RIESZ_K_UPDATE, s, [&] { dev::k_update_p<<<1184, 256, 0, s>>>(N, scal, h.d_z.p, h.d_p.p); });
-      if (flex) CK(cudaMemcpyAsync(h.d_zold.p, h.d_z.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if (a32) {  // reliable update: three more digits on some right-hand side
+        bool replace = false;
+        for (int k = 0; k < nrhs; ++k) {
+          const double rrk = h.h_scal[k * SS + dev::S_RR];
+          if (rrk > tol2[k] && rrk <= 1e-6 * rr_last[k]) replace = true;
+        }
+        if (replace) {
+          residual();
+          read_scal(h, scal, nrhs, s);
+          for (int k = 0; k < nrhs; ++k) rr_last[k] = h.h_scal[k * SS + dev::S_RR];
+          op_precond_dot(h, r, z, zold, 3, scal, nrhs, s);  // redo the step on the replaced residual
+        }
+      }
+      launch(h, RIESZ_K_UPDATE, s, [&] { dev::k_update_p<<<dim3(296, nrhs), 256, 0, s>>>(N, scal, z, p); });
+      if (flex) CK(cudaMemcpyAsync(zold, z, (size_t)nrhs * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     if (status == RIESZ_ERR_NOT_CONVERGED) {
       residual();
-      read_scal(h, scal, s);
+      read_scal(h, scal, nrhs, s);
       g_err = "PCG did not reach rtol within maxit";
     }
   }
-  if (iters_out) *iters_out = it;
-  if (relres_out) *relres_out = bb > 0 ? std::sqrt(h.h_scal[dev::S_RR] / bb) : 0.0;
+  for (int k = 0; k < nrhs; ++k) {
+    if (iters_out) iters_out[k] = it;
+    if (relres_out) relres_out[k] = bb[k] > 0 ? std::sqrt(h.h_scal[k * SS + dev::S_RR] / bb[k]) : 0.0;
+  }
   h.last_iters = it;
   return status;
 }
@@ -664,13 +733,18 @@ void device_compute(riesz_handle& h, cudaStream_t s) {
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, s));
   launch(h, RIESZ_K_GEOM, s, [&] {
-    dev::k_geom<<<nblk(C, 128), 128, 0, s>>>(h.space, C, h.d_verts.p, h.d_cells.p, ref_edge_inverse(), h.d_g.p,
-                                              h.d_jac.p);
+    dev::k_geom<<<nblk(C, 128), 128, 0, s>>>(h.space, C, h.d_verts.p, h.d_cells.p, ref_edge_inverse(),
+                                              h.opts.alpha, h.opts.beta, h.d_g.p, h.d_jac.p);
   });
-  if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT)
+  if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     launch(h, RIESZ_K_ELEM, s, [&] {
       dev::k_elem_matrices<<<(unsigned)C, 256, 0, s>>>(C, n, R.Q, h.d_g.p, h.d_R.p, h.d_Ae.p);
     });
+    if (h.d_Ae32.p)
+      launch(h, RIESZ_K_TO_F32, s, [&] {
+        dev::k_to_f32<<<1184, 256, 0, s>>>((int64_t)h.d_Ae.n, h.d_Ae.p, h.d_Ae32.p);
+      });
+  }
   if (M.n_interior > 0) {
     const int64_t cnt = C * (int64_t)(n - h.nif);
     launch(h, RIESZ_K_DIAG, s, [&] {
@@ -748,22 +822,34 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   h.d_X.upload(R.Xcross, s);
   h.d_cgdofs.upload(transpose_dofs(h.meshcg.cell_dofs, C, h.refcg->nref), s);
   for (auto* b : {&h.d_r, &h.d_z, &h.d_zold, &h.d_p, &h.d_Ap, &h.d_tmp, &h.d_xh}) b->alloc((size_t)N * nrhs);
-  h.d_part.alloc(2 * dev::RED_BLOCKS);
+  h.d_part.alloc((size_t)2 * dev::RED_BLOCKS * nrhs);
   h.d_scal.alloc(16 * (size_t)nrhs);
-  CK(cudaMallocHost((void**)&h.h_scal, 16 * sizeof(double)));
+  CK(cudaMallocHost((void**)&h.h_scal, (size_t)16 * nrhs * sizeof(double)));
   if (!h.ev_scal) CK(cudaEventCreateWithFlags(&h.ev_scal, cudaEventDisableTiming));
   const int npatch = (int)h.p_n.size();
   h.d_info.alloc(std::max(1, npatch));
   if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     h.d_Ae.alloc((size_t)C * n * n);
+    if (h.opts.apply_precision == RIESZ_PREC_FP32) h.d_Ae32.alloc((size_t)C * n * n);
   } else {
     const size_t sm = ((size_t)n + R.Q) * dev::TC * sizeof(double);
     CK(cudaFuncSetAttribute(dev::k_apply_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   }
   {
     const size_t sm = (size_t)n * nrhs * sizeof(double);
-    if (sm > 48 * 1024)
-      CK(cudaFuncSetAttribute(dev::k_apply_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (sm > 48 * 1024) {
+      CK(cudaFuncSetAttribute(dev::k_apply_elem<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      CK(cudaFuncSetAttribute(dev::k_apply_elem<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    }
+  }
+  {  // right-hand sides per multi-RHS sweep launch: as many as fit in shared memory (<= 8)
+    const size_t per = (size_t)(h.p_n.empty() ? 32 : (h.p_n[0] + 31) / 32 * 32) *
+                       (h.opts.precond_precision == RIESZ_PREC_FP32 ? sizeof(float) : sizeof(double));
+    const size_t budget = 160 * 1024;  // dynamic share, leaves room for the static reduction buffers
+    h.multi_group = (int)std::max<size_t>(1, std::min<size_t>(8, budget / per));
+    const int smm = (int)(per * h.multi_group);
+    CK(cudaFuncSetAttribute(dev::k_patch_solve_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smm));
+    CK(cudaFuncSetAttribute(dev::k_patch_solve_multi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smm));
   }
   h.d_pdioff.upload(h.p_dioff, s);
   h.d_pmoff.upload(h.p_moff, s);
@@ -781,8 +867,8 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     CK(cudaFuncSetAttribute(dev::k_patch_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
     CK(cudaFuncSetAttribute(dev::k_patch_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
   }
-  h.d_ticket.alloc(1);
-  CK(cudaMemsetAsync(h.d_ticket.p, 0, sizeof(unsigned), s));
+  h.d_ticket.alloc(nrhs);
+  CK(cudaMemsetAsync(h.d_ticket.p, 0, sizeof(unsigned) * nrhs, s));
   CK(cudaFuncSetAttribute(dev::k_cholesky, cudaFuncAttributePreferredSharedMemoryCarveout,
                           (int)cudaSharedmemCarveoutMaxShared));
   device_compute(h, s);
@@ -832,6 +918,9 @@ void riesz_default_opts(riesz_opts* o) {
   o->rtol = 1e-8;
   o->maxit = 1000;
   o->nrhs_max = 1;
+  o->alpha = 1.0;
+  o->beta = 1.0;
+  o->apply_precision = RIESZ_PREC_FP64;
 }
 
 const char* riesz_last_error(void) { return g_err.c_str(); }
@@ -853,6 +942,9 @@ int riesz_create(int space, int p, int64_t nverts, const double* verts, int64_t 
     need(h->opts.rtol > 0 && h->opts.maxit >= 0 && h->opts.nrhs_max >= 1 && h->opts.nrhs_max <= 64, "bad options");
     need(h->opts.precond_precision == 0 || h->opts.precond_precision == 1, "bad precond_precision");
     need(h->opts.apply_mode == 0 || h->opts.apply_mode == 1, "bad apply_mode");
+    need(h->opts.alpha > 0 && h->opts.beta > 0 && std::isfinite(h->opts.alpha) && std::isfinite(h->opts.beta),
+         "alpha and beta must be positive and finite");
+    need(h->opts.apply_precision == 0 || h->opts.apply_precision == 1, "bad apply_precision");
     for (int64_t i = 0; i < nverts * 3; ++i)
       need(std::isfinite(verts[i]), "non-finite vertex coordinate", RIESZ_ERR_BAD_MESH);
     h->verts.assign(verts, verts + nverts * 3);
@@ -971,7 +1063,7 @@ int riesz_apply_noalloc(riesz_handle* h, const double* x, double* y, void* strea
       const int rows = (n % 2 == 0) ? n / 2 : n;
       const int nt = std::min(1024, (rows + 31) / 32 * 32);
       launch(*h, RIESZ_K_APPLY, s, [&] {
-        dev::k_apply_elem<<<(unsigned)C, nt, (size_t)n * sizeof(double), s>>>(C, n, h->nif, h->d_Ae.p, h->d_cdofs.p,
+        dev::k_apply_elem<double, 1><<<(unsigned)C, nt, (size_t)n * sizeof(double), s>>>(C, n, h->nif, h->d_Ae.p, h->d_cdofs.p,
                                                                               x, y, ycell, 1, N);
       });
     } else {
@@ -1003,11 +1095,8 @@ int riesz_solve(riesz_handle* h, const double* b, double* x, int nrhs, void* str
   int rc = guarded([&] {
     check_dev(h);
     need(b && x && nrhs >= 1, "bad solve arguments");
-    const int64_t N = h->N();
-    for (int r = 0; r < nrhs; ++r) {
-      int st = pcg_one(*h, b + r * N, x + r * N, S(stream), iters ? iters + r : nullptr, relres ? relres + r : nullptr);
-      if (st != RIESZ_OK && status == RIESZ_OK) status = st;
-    }
+    need(nrhs <= h->opts.nrhs_max, "nrhs exceeds opts.nrhs_max");
+    status = pcg_batch(*h, b, x, nrhs, S(stream), iters, relres);
   });
   return rc != RIESZ_OK ? rc : status;
 }
@@ -1024,10 +1113,7 @@ int riesz_solve_host(riesz_handle* h, const double* b_host, double* x_host, int 
     double* dx = h->d_xh.p;   // staging of x
     CK(cudaMemcpyAsync(db, b_host, (size_t)N * nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(dx, x_host, (size_t)N * nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
-    for (int r = 0; r < nrhs; ++r) {
-      int st = pcg_one(*h, db + r * N, dx + r * N, s, iters ? iters + r : nullptr, relres ? relres + r : nullptr);
-      if (st != RIESZ_OK && status == RIESZ_OK) status = st;
-    }
+    status = pcg_batch(*h, db, dx, nrhs, s, iters, relres);
     CK(cudaMemcpyAsync(x_host, dx, (size_t)N * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   });

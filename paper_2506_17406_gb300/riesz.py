@@ -33,7 +33,8 @@ class RieszError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("precond_precision", ctypes.c_int), ("apply_mode", ctypes.c_int), ("rtol", ctypes.c_double),
-                ("maxit", ctypes.c_int), ("nrhs_max", ctypes.c_int)]
+                ("maxit", ctypes.c_int), ("nrhs_max", ctypes.c_int), ("alpha", ctypes.c_double),
+                ("beta", ctypes.c_double), ("apply_precision", ctypes.c_int)]
 
 
 _lib = None

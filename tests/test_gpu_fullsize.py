@@ -108,3 +108,23 @@ def test_fullsize_rt8_eight_rhs_apply_and_precond():
         assert np.abs(Y[r, d] - ye).max() <= FP64_TOL * np.abs(ye).max()
         ze = asm.sampled_precond(ref, md, d, X[r])
         assert np.abs(Z[r, d] - ze).max() <= 1e-4 * np.abs(ze).max()
+
+
+def test_fullsize_rt8_eight_rhs_mixed_solve():
+    """RT_8 on 16^3 x 6 tets, 8 seeded random right-hand sides, lockstep PCG with FP32 inner products
+    and patch solves, FP64 residuals: every right-hand side reaches 1e-8 on the FP64 residual, and
+    the oracle's residual at sampled DOFs confirms it."""
+    verts, cells = kuhn_mesh(16, 0.1, 1)
+    ref = reference_element("RT", 8)
+    md = MeshDofs(verts, cells, ref)
+    s = rz.Riesz("RT", 8, verts, cells, precond_precision=rz.PREC_FP32, apply_precision=rz.PREC_FP32,
+                 nrhs_max=8, maxit=3000)
+    B = normal_coeffs((8, s.N), 8)
+    X = torch.zeros((8, s.N), dtype=torch.float64, device="cuda")
+    it, rr, rc = s.solve(torch.tensor(B, device="cuda"), X, nrhs=8)
+    assert rc == 0 and np.all(rr <= 1e-8)
+    d = sample_dofs(md, s, 4, 9)
+    Xh = X.cpu().numpy()
+    for k in (0, 5):
+        res = B[k, d] - asm.sampled_apply(ref, md, d, Xh[k])
+        assert np.abs(res).max() <= 1.01e-8 * np.linalg.norm(B[k])
