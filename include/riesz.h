@@ -87,8 +87,9 @@ typedef struct {
      (RIESZ_APPLY_ELEMENT only).  RIESZ_PREC_FP32 keeps an FP32 copy of the
      element matrices for the search-direction products and recovers FP64
      accuracy by replacing the recursive residual with the FP64 true residual
-     b - A x whenever a right-hand side gains three digits and at convergence
-     (the stopping test is always on the FP64 residual).  riesz_apply is always
+     b - A x whenever a right-hand side gains four digits
+     and at convergence (the stopping test is always on the FP64 residual);
+     the first residual needs no product when x = 0.  riesz_apply is always
      FP64.  Default RIESZ_PREC_FP64. */
   int apply_precision;
 } riesz_opts;
@@ -211,7 +212,8 @@ enum {
   RIESZ_K_SCALAR = 11,      /* a9 reduction finish + scalar update       */
   RIESZ_K_UPDATE = 12,      /* a9 vector updates                         */
   RIESZ_K_LOAD = 13,        /* right-hand side assembly                  */
-  RIESZ_NKIND = 14
+  RIESZ_K_APPLY32 = 14,     /* a3-a4 with the FP32 element matrices      */
+  RIESZ_NKIND = 15
 };
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around

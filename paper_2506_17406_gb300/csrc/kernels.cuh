@@ -552,18 +552,18 @@ __global__ void __launch_bounds__(NT) k_patch_solve(const int32_t* __restrict__ 
     const T* base = L + row * 32 + 4 * q;
     int t = t0;
     for (; t + 2 <= td; t += 2) {
-      T a[4], b2[4];
+      T a[4], b2[4], y0[4], y1[4];
       Vec4<T>::load(base + (int64_t)t * 1024, a);
       Vec4<T>::load(base + (int64_t)(t + 1) * 1024, b2);
-      const T* y0 = y + tcol[t] * 32 + 4 * q;
-      const T* y1 = y + tcol[t + 1] * 32 + 4 * q;
+      Vec4<T>::load(y + tcol[t] * 32 + 4 * q, y0);
+      Vec4<T>::load(y + tcol[t + 1] * 32 + 4 * q, y1);
       acc += a[0] * y0[0] + a[1] * y0[1] + a[2] * y0[2] + a[3] * y0[3];
       acc += b2[0] * y1[0] + b2[1] * y1[1] + b2[2] * y1[2] + b2[3] * y1[3];
     }
     for (; t < td; ++t) {
-      T a[4];
+      T a[4], y0[4];
       Vec4<T>::load(base + (int64_t)t * 1024, a);
-      const T* y0 = y + tcol[t] * 32 + 4 * q;
+      Vec4<T>::load(y + tcol[t] * 32 + 4 * q, y0);
       acc += a[0] * y0[0] + a[1] * y0[1] + a[2] * y0[2] + a[3] * y0[3];
     }
     t0 = td + 1;
@@ -706,7 +706,8 @@ __global__ void __launch_bounds__(NT) k_patch_solve_multi(
 #pragma unroll
       for (int k = 0; k < RM; ++k)
         if (k < nr) {
-          const T* yk = y + k * ld + off;
+          T yk[4];
+          Vec4<T>::load(y + k * ld + off, yk);
           acc[k] += a[0] * yk[0] + a[1] * yk[1] + a[2] * yk[2] + a[3] * yk[3];
         }
     }
@@ -850,12 +851,13 @@ constexpr int RED_BLOCKS = 608;  // 4 x 152 partials, reduced in a fixed order
 // Scalar slots (per right-hand side, stride 16).
 // S_RZNEW holds (r, z) of a preconditioner step until k_update_p commits it to
 // S_RZ, so a speculative step can be recomputed after a residual replacement.
-enum ScalarSlot { S_RZ = 0, S_PAP = 1, S_ALPHA = 2, S_RR = 3, S_BETA = 4, S_BB = 5, S_NONFINITE = 6, S_RZNEW = 7 };
+enum ScalarSlot { S_RZ = 0, S_PAP = 1, S_ALPHA = 2, S_RR = 3, S_BETA = 4, S_BB = 5, S_NONFINITE = 6, S_RZNEW = 7,
+                  S_XX = 8 };
 constexpr int SCAL_STRIDE = 16;  // doubles of scalars per right-hand side
 
 // Apply the scalar step of a finished reduction.  op: 0 pAp -> alpha; 1 rr;
 // 2 rz -> beta (classic); 3 rz, r.zold -> beta (Polak-Ribiere); 4 bb;
-// 5 rz (restart).  A zero denominator (a right-hand side that has converged
+// 5 rz (restart); 6 x.x.  A zero denominator (a right-hand side that has converged
 // exactly while others iterate) gives a zero step.
 __device__ __forceinline__ void scalar_op(int op, double s0, double s1, double* __restrict__ scal) {
   if (!isfinite(s0) || !isfinite(s1)) scal[S_NONFINITE] = 1.0;
@@ -874,6 +876,8 @@ __device__ __forceinline__ void scalar_op(int op, double s0, double s1, double* 
     scal[S_BB] = s0;
   } else if (op == 5) {
     scal[S_RZ] = s0;
+  } else if (op == 6) {
+    scal[S_XX] = s0;
   }
 }
 
@@ -983,18 +987,18 @@ __global__ void k_update_p(int64_t n, double* __restrict__ scal, const double* _
   if (blockIdx.x == 0 && threadIdx.x == 0) scal[S_RZ] = scal[S_RZNEW];
 }
 
-// r = b - Ap ; r.r -> RR
+// r = b - Ax (r = b when Ax is null: zero initial guess) ; r.r -> RR
 __global__ void __launch_bounds__(NT) k_residual(int64_t n, const double* __restrict__ b,
                                                 const double* __restrict__ Ax, double* __restrict__ r,
                                                 double* __restrict__ part, unsigned* __restrict__ ticket,
                                                 double* __restrict__ scal) {
   const int64_t o = blockIdx.y * n;
   b += o;
-  Ax += o;
+  if (Ax) Ax += o;
   r += o;
   double v0 = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * NT) {
-    const double ri = b[i] - Ax[i];
+    const double ri = Ax ? b[i] - Ax[i] : b[i];
     r[i] = ri;
     v0 = fma(ri, ri, v0);
   }

@@ -492,7 +492,7 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
     const int nt = std::min(1024, (rows + 31) / 32 * 32);
     if (fp32) {
       const size_t sm = (size_t)n * nrhs * sizeof(float);
-      launch(h, RIESZ_K_APPLY, s, [&] {
+      launch(h, RIESZ_K_APPLY32, s, [&] {
         if (nrhs == 1)
           dev::k_apply_elem<float, 1><<<(unsigned)C, nt, sm, s>>>(C, n, h.nif, h.d_Ae32.p, h.d_cdofs.p, x, y,
                                                                   h.d_Ycell.p, nrhs, N);
@@ -606,7 +606,10 @@ void read_scal(riesz_handle& h, const double* scal, int nrhs, cudaStream_t s) {
 // preconditioner launch serve all of them.  With apply_precision FP32 the
 // search-direction products use the FP32 element matrices and the residual is
 // replaced by the FP64 true residual whenever a right-hand side has gained
-// three more digits (reliable updates), and at convergence.
+// four more digits (reliable updates: the FP32 product error, ~1e-7 relative
+// per step, stays well below the recursive residual) and when the recursive
+// residual claims convergence; the search direction is kept across a
+// replacement.
 int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_t s, int* iters_out,
               double* relres_out) {
   const int64_t N = h.N();
@@ -620,10 +623,11 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
   double* p = h.d_p.p;
   double* Ap = h.d_Ap.p;
   CK(cudaMemsetAsync(scal, 0, (size_t)nrhs * SS * sizeof(double), s));
-  auto residual = [&]() {  // r = b - A x (FP64), RR
-    op_apply(h, x, Ap, nrhs, s);
+  auto residual = [&](bool x_is_zero = false) {  // r = b - A x (FP64), RR
+    if (!x_is_zero) op_apply(h, x, Ap, nrhs, s);
     launch(h, RIESZ_K_UPDATE, s, [&] {
-      dev::k_residual<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(N, b, Ap, r, h.d_part.p, h.d_ticket.p, scal);
+      dev::k_residual<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(N, b, x_is_zero ? nullptr : Ap, r, h.d_part.p,
+                                                                      h.d_ticket.p, scal);
     });
   };
   auto restart = [&]() {  // z = P r, p = z, RZ
@@ -637,7 +641,11 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
     return false;
   };
   dot(h, b, b, nullptr, 4, scal, nrhs, s);
-  residual();
+  dot(h, x, x, nullptr, 6, scal, nrhs, s);
+  read_scal(h, scal, nrhs, s);
+  bool x_zero = true;  // a zero initial guess needs no operator product for r = b
+  for (int k = 0; k < nrhs; ++k) x_zero = x_zero && h.h_scal[k * SS + dev::S_XX] == 0.0;
+  residual(x_zero);
   read_scal(h, scal, nrhs, s);
   std::vector<double> bb(nrhs), tol2(nrhs), rr_last(nrhs);
   for (int k = 0; k < nrhs; ++k) {
@@ -679,6 +687,7 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
         g_err = "non-finite value in the PCG recurrence";
         break;
       }
+      bool replace = false;
       if (all_below()) {
         residual();  // verify on the true residual
         read_scal(h, scal, nrhs, s);
@@ -686,22 +695,25 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
           status = RIESZ_OK;
           break;
         }
-        for (int k = 0; k < nrhs; ++k) rr_last[k] = h.h_scal[k * SS + dev::S_RR];
-        restart();
-        continue;
-      }
-      if (a32) {  // reliable update: three more digits on some right-hand side
-        bool replace = false;
+        if (!a32) {  // FP64 operator: the recurrence drifted; start afresh from the true residual
+          for (int k = 0; k < nrhs; ++k) rr_last[k] = h.h_scal[k * SS + dev::S_RR];
+          restart();
+          continue;
+        }
+        replace = true;  // FP32 products: keep the search direction, continue from the true residual
+      } else if (a32) {  // reliable update: four more digits on some right-hand side
         for (int k = 0; k < nrhs; ++k) {
           const double rrk = h.h_scal[k * SS + dev::S_RR];
-          if (rrk > tol2[k] && rrk <= 1e-6 * rr_last[k]) replace = true;
+          if (rrk > tol2[k] && rrk <= 1e-8 * rr_last[k]) replace = true;
         }
         if (replace) {
           residual();
           read_scal(h, scal, nrhs, s);
-          for (int k = 0; k < nrhs; ++k) rr_last[k] = h.h_scal[k * SS + dev::S_RR];
-          op_precond_dot(h, r, z, zold, 3, scal, nrhs, s);  // redo the step on the replaced residual
         }
+      }
+      if (replace) {
+        for (int k = 0; k < nrhs; ++k) rr_last[k] = h.h_scal[k * SS + dev::S_RR];
+        op_precond_dot(h, r, z, zold, 3, scal, nrhs, s);  // redo the step on the replaced residual
       }
       launch(h, RIESZ_K_UPDATE, s, [&] { dev::k_update_p<<<dim3(296, nrhs), 256, 0, s>>>(N, scal, z, p); });
       if (flex) CK(cudaMemcpyAsync(zold, z, (size_t)nrhs * N * sizeof(double), cudaMemcpyDeviceToDevice, s));

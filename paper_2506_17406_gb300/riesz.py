@@ -19,7 +19,7 @@ PREC_FP64, PREC_FP32 = 0, 1
 APPLY_MATRIX_FREE, APPLY_ELEMENT = 0, 1
 
 KINDS = ["geom", "elem", "diag", "assemble", "cholesky", "to_f32", "apply", "gather", "patch_solve",
-         "precond_gather", "dot", "scalar", "update", "load"]
+         "precond_gather", "dot", "scalar", "update", "load", "apply32"]
 
 ERRORS = {1: "INVALID_ARG", 2: "BAD_MESH", 3: "OOM", 4: "NOT_CONVERGED", 5: "NONFINITE", 6: "CUDA",
           7: "INTERNAL", 8: "NO_DEVICE"}

@@ -1,0 +1,158 @@
+"""Continuous-batching server for Riesz-map solves.
+
+Requests (space, degree, mesh, right-hand side) arrive over time; each is
+admitted as soon as a slot is free and its device footprint fits the HBM
+budget, then set up and solved on its own CUDA stream by its own host thread
+(the C calls release the GIL), so the kernels of concurrent requests overlap on
+the GPU.  Completed requests free their memory and slots, which admits the
+next ones.  Per request the server records queueing delay, latency and
+iterations; overall it reports DOFs/s and p50/p99 latency.
+
+The footprint of a request is known before any device allocation: the host
+part (reference element, mesh maps, patch plans) is built first and its sizes
+give the device bytes; requests whose element matrices would not fit use the
+matrix-free operator.
+"""
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import riesz as rz
+from .inputs import kuhn_mesh, normal_vector
+
+
+@dataclass
+class Request:
+    rid: int
+    space: str
+    p: int
+    n: int                 # cubes per edge of the Kuhn mesh
+    amp: float = 0.1       # vertex perturbation (fraction of h)
+    seed: int = 0
+    arrival: float = 0.0   # seconds after the start of the stream
+    rtol: float = 1e-8
+    # filled in by the server
+    N: int = 0
+    iters: int = 0
+    relres: float = float("nan")
+    status: int = -1
+    t_admit: float = float("nan")
+    t_done: float = float("nan")
+    footprint: int = 0
+    x: np.ndarray = field(default=None, repr=False)
+
+    @property
+    def latency(self):
+        return self.t_done - self.arrival
+
+    @property
+    def queue_delay(self):
+        return self.t_admit - self.arrival
+
+
+def poisson_stream(count, rate, seed, spaces=("CG", "N1curl", "RT"), degrees=(3, 4, 5, 6), sizes=(4, 5, 6, 8)):
+    """Seeded Poisson arrivals with mean rate `rate` per second and a random mix of problems."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += rng.exponential(1.0 / rate)
+        out.append(Request(rid=i, space=str(rng.choice(spaces)), p=int(rng.choice(degrees)),
+                           n=int(rng.choice(sizes)), seed=int(rng.integers(1 << 30)), arrival=t))
+    return out
+
+
+def estimate_footprint(h, opts):
+    """Device bytes of a created (host-only) handle for the given apply mode."""
+    st = h.stats()
+    N = h.N
+    n = h.nref
+    elem = h.ncells * n * n * 8 if opts.get("apply_mode", rz.APPLY_ELEMENT) == rz.APPLY_ELEMENT else 0
+    factor64 = st["factor_bytes"] * (2 if opts.get("precond_precision", 0) == rz.PREC_FP32 else 1)
+    vectors = 10 * N * 8
+    maps = h.ncells * n * 4 * 3 + 4 * N * 8
+    return int(elem + factor64 + vectors + maps)
+
+
+class Server:
+    def __init__(self, hbm_budget_bytes=150 << 30, max_slots=4, precond_precision=rz.PREC_FP32):
+        self.budget = hbm_budget_bytes
+        self.max_slots = max_slots
+        self.prec = precond_precision
+        self.lock = threading.Condition()
+        self.in_use = 0
+        self.active = 0
+
+    def _prepare(self, req):
+        verts, cells = kuhn_mesh(req.n, req.amp, req.seed % 1000)
+        opts = dict(precond_precision=self.prec, rtol=req.rtol, maxit=5000)
+        h = rz.Riesz(req.space, req.p, verts, cells, device=False, **opts)
+        fp = estimate_footprint(h, opts)
+        if fp > self.budget // 2:  # element matrices too large: matrix-free operator
+            h.close()
+            opts["apply_mode"] = rz.APPLY_MATRIX_FREE
+            h = rz.Riesz(req.space, req.p, verts, cells, device=False, **opts)
+            fp = estimate_footprint(h, opts)
+        return h, fp
+
+    def _run(self, req, h, t0):
+        import torch
+        try:
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                h.setup_device(stream)
+                b = torch.tensor(normal_vector(h.N, req.seed % 7919), device="cuda")
+                x = torch.zeros_like(b)
+                it, rr, rc = h.solve(b, x, stream=stream, check=False)
+                stream.synchronize()
+                req.x = x.cpu().numpy()
+            req.N, req.iters, req.relres, req.status = h.N, int(it[0]), float(rr[0]), int(rc)
+        finally:
+            req.t_done = time.perf_counter() - t0
+            h.close()
+            with self.lock:
+                self.in_use -= req.footprint
+                self.active -= 1
+                self.lock.notify_all()
+
+    def run(self, requests, realtime=True):
+        """Serve the requests (sorted by arrival); returns them with timings filled in."""
+        t0 = time.perf_counter()
+        threads = []
+        for req in sorted(requests, key=lambda r: r.arrival):
+            if realtime:
+                delay = req.arrival - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+            h, fp = self._prepare(req)
+            if fp > self.budget:
+                h.close()
+                req.status = 3  # RIESZ_ERR_OOM: larger than the whole budget
+                req.t_admit = req.t_done = time.perf_counter() - t0
+                continue
+            req.footprint = fp
+            with self.lock:
+                while self.active >= self.max_slots or self.in_use + fp > self.budget:
+                    self.lock.wait()
+                self.in_use += fp
+                self.active += 1
+            req.t_admit = time.perf_counter() - t0
+            th = threading.Thread(target=self._run, args=(req, h, t0), daemon=True)
+            th.start()
+            threads.append(th)
+        for th in threads:
+            th.join()
+        self.wall = time.perf_counter() - t0
+        return requests
+
+
+def summary(requests, wall):
+    done = [r for r in requests if r.status == 0]
+    lat = np.array([r.latency for r in done]) if done else np.zeros(1)
+    return {"requests": len(requests), "completed": len(done),
+            "dofs_per_s": float(sum(r.N for r in done) / wall) if wall > 0 else 0.0,
+            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+            "queue_p50_s": float(np.percentile([r.queue_delay for r in done], 50)) if done else 0.0,
+            "wall_s": wall}
