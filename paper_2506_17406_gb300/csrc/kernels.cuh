@@ -11,6 +11,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace riesz {
 namespace dev {
 
@@ -122,34 +124,38 @@ __global__ void k_elem_matrices(int64_t C, int n, int Q, const double* __restric
 template <int R, typename T>
 __device__ __forceinline__ void apply_rows2(const T* __restrict__ A, const T* __restrict__ xs, int n, int i0,
                                             T (&acc)[2][8]) {
+  using V2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
   const T* p = A + i0;
-  for (int j = 0; j < n; j += 2) {
-    T a0x, a0y, a1x, a1y;
-    if constexpr (sizeof(T) == 8) {
-      const double2 a0 = *reinterpret_cast<const double2*>(p + (int64_t)j * n);
-      const double2 a1 = *reinterpret_cast<const double2*>(p + (int64_t)(j + 1) * n);
-      a0x = a0.x; a0y = a0.y; a1x = a1.x; a1y = a1.y;
-    } else {
-      const float2 a0 = *reinterpret_cast<const float2*>(p + (int64_t)j * n);
-      const float2 a1 = *reinterpret_cast<const float2*>(p + (int64_t)(j + 1) * n);
-      a0x = a0.x; a0y = a0.y; a1x = a1.x; a1y = a1.y;
-    }
+  // J columns of A_T per step: J independent 2-wide loads in flight per thread
+  // (J = 4 for FP32, which is bandwidth-bound; 2 for FP64, which is FP64-bound)
+  constexpr int J = (sizeof(T) == 8) ? 2 : 4;
+  int j = 0;
+  for (; j + J <= n; j += J) {
+    V2 a[J];
+#pragma unroll
+    for (int u = 0; u < J; ++u) a[u] = *reinterpret_cast<const V2*>(p + (int64_t)(j + u) * n);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      T x0, x1;
-      if constexpr (sizeof(T) == 8) {
-        const double2 xv = *reinterpret_cast<const double2*>(xs + r * n + j);
-        x0 = xv.x;
-        x1 = xv.y;
-      } else {
-        const float2 xv = *reinterpret_cast<const float2*>(xs + r * n + j);
-        x0 = xv.x;
-        x1 = xv.y;
+#pragma unroll
+      for (int u = 0; u < J; u += 2) {
+        const V2 xv = *reinterpret_cast<const V2*>(xs + r * n + j + u);
+        acc[0][r] = fma(a[u].x, xv.x, acc[0][r]);
+        acc[1][r] = fma(a[u].y, xv.x, acc[1][r]);
+        acc[0][r] = fma(a[u + 1].x, xv.y, acc[0][r]);
+        acc[1][r] = fma(a[u + 1].y, xv.y, acc[1][r]);
       }
-      acc[0][r] = fma(a0x, x0, acc[0][r]);
-      acc[1][r] = fma(a0y, x0, acc[1][r]);
-      acc[0][r] = fma(a1x, x1, acc[0][r]);
-      acc[1][r] = fma(a1y, x1, acc[1][r]);
+    }
+  }
+  for (; j < n; j += 2) {  // n is even
+    const V2 a0 = *reinterpret_cast<const V2*>(p + (int64_t)j * n);
+    const V2 a1 = *reinterpret_cast<const V2*>(p + (int64_t)(j + 1) * n);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const V2 xv = *reinterpret_cast<const V2*>(xs + r * n + j);
+      acc[0][r] = fma(a0.x, xv.x, acc[0][r]);
+      acc[1][r] = fma(a0.y, xv.x, acc[1][r]);
+      acc[0][r] = fma(a1.x, xv.y, acc[0][r]);
+      acc[1][r] = fma(a1.y, xv.y, acc[1][r]);
     }
   }
 }
@@ -699,7 +705,23 @@ __global__ void __launch_bounds__(NT) k_patch_solve_multi(
 #pragma unroll
     for (int k = 0; k < RM; ++k) acc[k] = 0;
     const T* base = L + row * 32 + 4 * q;
-    for (int t = t0; t < td; ++t) {
+    int t = t0;
+    for (; t + 2 <= td; t += 2) {  // two tiles' loads in flight
+      T a[4], b2[4];
+      Vec4<T>::load(base + (int64_t)t * 1024, a);
+      Vec4<T>::load(base + (int64_t)(t + 1) * 1024, b2);
+      const int off = tcol[t] * 32 + 4 * q, off2 = tcol[t + 1] * 32 + 4 * q;
+#pragma unroll
+      for (int k = 0; k < RM; ++k)
+        if (k < nr) {
+          T yk[4], yl[4];
+          Vec4<T>::load(y + k * ld + off, yk);
+          Vec4<T>::load(y + k * ld + off2, yl);
+          acc[k] += a[0] * yk[0] + a[1] * yk[1] + a[2] * yk[2] + a[3] * yk[3] + b2[0] * yl[0] + b2[1] * yl[1] +
+                    b2[2] * yl[2] + b2[3] * yl[3];
+        }
+    }
+    for (; t < td; ++t) {
       T a[4];
       Vec4<T>::load(base + (int64_t)t * 1024, a);
       const int off = tcol[t] * 32 + 4 * q;
@@ -756,7 +778,21 @@ __global__ void __launch_bounds__(NT) k_patch_solve_multi(
     T acc[RM][4];
 #pragma unroll
     for (int k = 0; k < RM; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0;
-    for (int kk = 0; kk < m; ++kk) {
+    int kk = 0;
+    for (; kk + 2 <= m; kk += 2) {  // two tiles' loads in flight
+      T a[4], b2[4];
+      Vec4<T>::load(L + (int64_t)clist[kk] * 1024 + row * 32 + 4 * q, a);
+      Vec4<T>::load(L + (int64_t)clist[kk + 1] * 1024 + row * 32 + 4 * q, b2);
+      const int off = cJ[kk] * 32 + row, off2 = cJ[kk + 1] * 32 + row;
+#pragma unroll
+      for (int k = 0; k < RM; ++k)
+        if (k < nr) {
+          const T xr = y[k * ld + off], xs2 = y[k * ld + off2];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[k][c] += a[c] * xr + b2[c] * xs2;
+        }
+    }
+    for (; kk < m; ++kk) {
       T a[4];
       Vec4<T>::load(L + (int64_t)clist[kk] * 1024 + row * 32 + 4 * q, a);
       const int off = cJ[kk] * 32 + row;

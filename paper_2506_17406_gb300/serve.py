@@ -1,8 +1,9 @@
 """Continuous-batching server for Riesz-map solves.
 
-Requests (space, degree, mesh, right-hand side) arrive over time; each is
-admitted as soon as a slot is free and its device footprint fits the HBM
-budget, then set up and solved on its own CUDA stream by its own host thread
+Requests (space, degree, mesh, right-hand side) arrive over time; each gets
+its own host thread at arrival, which builds the request's host maps (in
+parallel with other arrivals), waits until a slot is free and its device
+footprint fits the HBM budget, then sets up and solves on its own CUDA stream
 (the C calls release the GIL), so the kernels of concurrent requests overlap on
 the GPU.  Completed requests free their memory and slots, which admits the
 next ones.  Per request the server records queueing delay, latency and
@@ -117,8 +118,26 @@ class Server:
                 self.active -= 1
                 self.lock.notify_all()
 
+    def _serve_one(self, req, t0):
+        """Host preparation, admission, device setup and solve of one request (own thread)."""
+        h, fp = self._prepare(req)
+        if fp > self.budget:
+            h.close()
+            req.status = 3  # RIESZ_ERR_OOM: larger than the whole budget
+            req.t_admit = req.t_done = time.perf_counter() - t0
+            return
+        req.footprint = fp
+        with self.lock:
+            while self.active >= self.max_slots or self.in_use + fp > self.budget:
+                self.lock.wait()
+            self.in_use += fp
+            self.active += 1
+        req.t_admit = time.perf_counter() - t0
+        self._run(req, h, t0)
+
     def run(self, requests, realtime=True):
-        """Serve the requests (sorted by arrival); returns them with timings filled in."""
+        """Serve the requests; each gets its own thread at its arrival time, which prepares the
+        host maps (in parallel with the others), waits for a slot and memory, then solves."""
         t0 = time.perf_counter()
         threads = []
         for req in sorted(requests, key=lambda r: r.arrival):
@@ -126,20 +145,7 @@ class Server:
                 delay = req.arrival - (time.perf_counter() - t0)
                 if delay > 0:
                     time.sleep(delay)
-            h, fp = self._prepare(req)
-            if fp > self.budget:
-                h.close()
-                req.status = 3  # RIESZ_ERR_OOM: larger than the whole budget
-                req.t_admit = req.t_done = time.perf_counter() - t0
-                continue
-            req.footprint = fp
-            with self.lock:
-                while self.active >= self.max_slots or self.in_use + fp > self.budget:
-                    self.lock.wait()
-                self.in_use += fp
-                self.active += 1
-            req.t_admit = time.perf_counter() - t0
-            th = threading.Thread(target=self._run, args=(req, h, t0), daemon=True)
+            th = threading.Thread(target=self._serve_one, args=(req, t0), daemon=True)
             th.start()
             threads.append(th)
         for th in threads:
