@@ -12,7 +12,10 @@ split into 8^3 cubes x 6 tets (3072 tets), interior vertices perturbed by up
 to 0.1 h (seeded), f with N(0,1) CG_6 coefficients per Cartesian component,
 FP64 operator with FP32 patch solves, rtol 1e-8.
 
-Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
+Prints one JSON line (rank 0) with per-step latency (p50/p99 over the timed
+steps) and, for the mixed-precision workloads, the same workload timed with the
+plain FP64 solver (FP64 operator and FP64 patch solves) on the same GPU.
+--impl reference times the CPU oracle instead.
 """
 import argparse
 import json
@@ -62,6 +65,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-plain", action="store_true",
+                    help="skip the comparison run of the plain FP64 solver on the same workload")
     return ap.parse_args()
 
 
@@ -275,31 +280,47 @@ def main():
         dist.init_process_group("nccl")
     verts, cells = kuhn_mesh(wl["n"], wl["amp"], seed=1 + rank)
     nrhs = wl.get("nrhs", 1)
-    s = rz.Riesz(wl["space"], wl["p"], verts, cells, precond_precision=wl["prec"], nrhs_max=nrhs,
-                 apply_precision=wl.get("a32", 0))
     stream = torch.cuda.current_stream()
     verts_d = torch.tensor(verts, device="cuda")
     ncomp = 1 if wl["space"] == "CG" else 3
-    if nrhs == 1:  # f with N(0,1) CG_p coefficients per Cartesian component, b = (f, phi)
-        fcg_h = normal_coeffs((ncomp, s.n_cg), 2 + rank)
-    else:  # the paper's random right-hand side vectors (Section 7.1), one per RHS
-        fcg_h = normal_coeffs((nrhs, s.N), 2 + rank)
-    fcg = torch.tensor(fcg_h, device="cuda")
-    b = torch.zeros((nrhs, s.N), dtype=torch.float64, device="cuda")
-    x = torch.zeros_like(b)
-    iters = []
 
-    def step():
-        s.update_geometry(verts_d)
-        if nrhs == 1:
-            s.load(fcg, b)
-        else:
-            b.copy_(fcg)
-        x.zero_()
-        it, rr, _ = s.solve(b, x, nrhs=nrhs)
-        iters.append(int(it[0]))
-        return float(np.max(rr))
+    def make(prec, a32):
+        """A solver handle for the workload and its step closure (device setup + load + solve)."""
+        s = rz.Riesz(wl["space"], wl["p"], verts, cells, precond_precision=prec, nrhs_max=nrhs,
+                     apply_precision=a32)
+        if nrhs == 1:  # f with N(0,1) CG_p coefficients per Cartesian component, b = (f, phi)
+            fcg_h = normal_coeffs((ncomp, s.n_cg), 2 + rank)
+        else:  # the paper's random right-hand side vectors (Section 7.1), one per RHS
+            fcg_h = normal_coeffs((nrhs, s.N), 2 + rank)
+        fcg = torch.tensor(fcg_h, device="cuda")
+        b = torch.zeros((nrhs, s.N), dtype=torch.float64, device="cuda")
+        x = torch.zeros_like(b)
+        iters, relres = [], []
 
+        def step():
+            s.update_geometry(verts_d)
+            if nrhs == 1:
+                s.load(fcg, b)
+            else:
+                b.copy_(fcg)
+            x.zero_()
+            it, rr, _ = s.solve(b, x, nrhs=nrhs)
+            iters.append(int(it[0]))
+            relres.append(float(np.max(rr)))
+
+        return s, step, iters, relres, fcg, fcg_h, b, x
+
+    def timed(step, steps):
+        """Per-step device times (CUDA events on the launching stream between consecutive steps)."""
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(stream)
+        for i in range(steps):
+            step()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        return [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+
+    s, step, iters, relres_l, fcg, fcg_h, b, x = make(wl["prec"], wl.get("a32", 0))
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -310,15 +331,10 @@ def main():
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    relres = 0.0
-    for _ in range(args.steps):
-        relres = max(relres, step())
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    per_step = timed(step, args.steps)
+    ms = sum(per_step)
     clk = clocks.stop()
+    relres = max(relres_l[-args.steps:])
     live = s.profile_read()
     s.profile(False)
     launches = s.stats()["launches"] - launches0
@@ -403,6 +419,22 @@ def main():
         e2e = {"value": float(s.N) * nrhs * args.steps / te, "unit": "DOFs/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    # the same workload with the plain FP64 solver (FP64 operator and FP64 patch solves)
+    plain = None
+    if (wl["prec"] != 0 or wl.get("a32", 0)) and not args.no_fp64_plain:
+        s64, step64, it64, rr64, *_ = make(0, 0)
+        for _ in range(args.warmup):
+            step64()
+        per64 = timed(step64, args.steps)
+        ms64, _ = combine_ranks(sum(per64), s64.N, dist, device="cuda")
+        plain = {"value": ntot * nrhs * args.steps / (ms64 / 1e3), "unit": "DOFs/s",
+                 "ms_per_step": ms64 / args.steps,
+                 "latency_p50_ms": float(np.percentile(per64, 50)),
+                 "latency_p99_ms": float(np.percentile(per64, 99)),
+                 "iterations": statistics.median(it64[-args.steps:]), "max_relres": max(rr64[-args.steps:]),
+                 "config": "same mesh, right-hand side and rtol; FP64 operator and FP64 patch solves"}
+        s64.close()
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(wl)
@@ -420,6 +452,10 @@ def main():
                        "l2": "inputs larger than L2 (element matrices and patch factors)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "iterations": statistics.median(iters[-args.steps:]), "max_relres": relres,
+            "latency_p50_ms": float(np.percentile(per_step, 50)),
+            "latency_p99_ms": float(np.percentile(per_step, 99)),
+            "fp64_plain": plain,
+            "speedup_vs_fp64_plain": (value / plain["value"]) if plain else None,
             "setup_kernel_ms": sum(k_ms[k] for k in setup_kinds),
             "solve_kernel_ms": sum(v for k, v in k_ms.items() if k not in setup_kinds),
             "kernel_ms_per_step": {k: round(v, 4) for k, v in k_ms.items() if v > 0},
