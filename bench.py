@@ -63,6 +63,14 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving run: Poisson stream of mixed solves, reports DOFs/s and p50/p99 latency")
     ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--batch", action="store_true",
+                    help="batched run: seeded mixed systems solved in one graph launch per HBM wave")
+    ap.add_argument("--systems", type=int, default=64)
+    ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
+    ap.add_argument("--pcg-loop", default="graph", choices=["graph", "host"],
+                    help="device-driven (CUDA graph) or host-driven PCG iterations; same kernels, same results")
+    ap.add_argument("--p-sweep", action="store_true",
+                    help="iteration counts against the degree p on a fixed mesh (p-robustness table)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true",
@@ -193,15 +201,15 @@ def combine_ranks(ms, n_local, dist=None, device=None):
     return float(tm.item()), float(tn.item())
 
 
-LIVE_KINDS = ["cholesky", "patch_solve", "apply", "apply32"]  # recorded with CUDA events inside the timed region
+# kernel kinds launched inside the PCG loop (timing one per launch needs the host-driven loop)
+LOOP_KIND_NAMES = {"apply", "apply32", "gather", "patch_solve", "precond_gather", "dot", "scalar", "update"}
 
 
 def kernel_source_hash():
+    """sha256 of the device code (every kernel lives in kernels.cuh)."""
     import hashlib
-    h = hashlib.sha256()
-    for f in ("kernels.cuh", "riesz.cu"):
-        h.update(open(os.path.join(ROOT, "paper_2506_17406_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()
+    return hashlib.sha256(open(os.path.join(ROOT, "paper_2506_17406_gb300", "csrc", "kernels.cuh"), "rb").read()
+                          ).hexdigest()
 
 
 def measured_traffic(workload, kernel):
@@ -249,10 +257,154 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
+def batch_draws(count, seed=4, degrees=(2, 10), sizes=(4, 12)):
+    """Seeded draws (space, p, cubes per edge) with p and n uniform in the given ranges."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [(str(rng.choice(["CG", "N1curl", "RT"])), int(rng.integers(degrees[0], degrees[1] + 1)),
+             int(rng.integers(sizes[0], sizes[1] + 1))) for _ in range(count)]
+
+
+def run_batch(args):
+    """Batched solves: seeded draws over spaces {CG, Ned1, RT}, p in 2..10, n^3 x 6 tets with n in 4..12,
+    perturbed 0.1h, one seeded random right-hand side each, FP32 inner products and patch sweeps with FP64
+    residuals.  The systems are packed into waves that fit the HBM budget; a wave's device setups run back to
+    back and its solves run as one graph launch (riesz_solve_batch).  The same systems are then solved one
+    after the other for comparison."""
+    import numpy as np
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2506_17406_gb300 import riesz as rz
+    from paper_2506_17406_gb300 import serve
+    from paper_2506_17406_gb300.inputs import kuhn_mesh, normal_vector
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    draws = batch_draws(args.systems)
+    opts = dict(precond_precision=rz.PREC_FP32, apply_precision=rz.PREC_FP32, rtol=1e-8, maxit=5000)
+
+    def prep(i):
+        space, p, n = draws[i]
+        verts, cells = kuhn_mesh(n, 0.1, 1000 + i)
+        h = rz.Riesz(space, p, verts, cells, device=False, **opts)
+        return h, verts, serve.estimate_footprint(h, opts)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        prepared = list(ex.map(prep, range(len(draws))))
+    host_s = time.perf_counter() - t0
+    budget = int(args.hbm_budget_gb * (1 << 30))
+    waves, cur, used = [], [], 0
+    for i, (_, _, fp) in enumerate(prepared):
+        if cur and used + fp > budget:
+            waves.append(cur)
+            cur, used = [], 0
+        cur.append(i)
+        used += fp
+    if cur:
+        waves.append(cur)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    setup_ms = solve_ms = seq_ms = 0.0
+    iters, relres, status, ndofs = [], [], [], []
+    launches = 0
+    for wave in waves:
+        hs = [prepared[i][0] for i in wave]
+        for h in hs:
+            h.setup_device()
+        verts_d = [torch.tensor(prepared[i][1], device="cuda") for i in wave]
+        bs = [torch.tensor(normal_vector(h.N, 500 + i), device="cuda").reshape(1, -1) for h, i in zip(hs, wave)]
+        xs = [torch.zeros_like(b) for b in bs]
+        l0 = sum(h.stats()["launches"] for h in hs)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        for h, v in zip(hs, verts_d):
+            h.update_geometry(v)
+        e[1].record(stream)
+        it, rr, st = rz.solve_batch(hs, bs, xs)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        setup_ms += e[0].elapsed_time(e[1])
+        solve_ms += e[1].elapsed_time(e[2])
+        launches += sum(h.stats()["launches"] for h in hs) - l0
+        iters += [int(k) for k in it]
+        relres += [float(r) for r in rr]
+        status += [int(k) for k in st]
+        ndofs += [h.N for h in hs]
+        # the same systems solved one after the other
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for h, b, x in zip(hs, bs, xs):
+            h.solve(b, x, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms += e0.elapsed_time(e1)
+        for h in hs:
+            h.close()
+        del verts_d, bs, xs
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    ntot = float(sum(ndofs))
+    by_space = {}
+    for (space, p, n), it in zip(draws, iters):
+        by_space.setdefault(space, {}).setdefault(p, []).append(it)
+    out = {"metric": "batched: DOFs/s solved to 1e-8 (device setup + one-launch solve per wave)",
+           "value": ntot / ((setup_ms + solve_ms) / 1e3), "unit": "DOFs/s", "n_gpus": 1, "higher_is_better": True,
+           "data": "synthetic", "dtype": "f64+f32",
+           "config": {"workload": "%d seeded draws: space in {CG, Ned1, RT}, p in 2..10, n^3 x 6 tets with n in "
+                                  "4..12, perturbed 0.1h, random RHS, FP32 products and patch sweeps, FP64 "
+                                  "residuals, rtol 1e-8" % len(draws),
+                      "hbm_budget_gb": args.hbm_budget_gb, "waves": [len(w) for w in waves]},
+           "dofs": int(ntot), "setup_ms": setup_ms, "solve_ms": solve_ms,
+           "solve_dofs_per_s": ntot / (solve_ms / 1e3),
+           "sequential_solve_ms": seq_ms, "batch_speedup_vs_sequential_solves": seq_ms / solve_ms,
+           "converged": sum(1 for k in status if k == 0), "max_relres": max(relres),
+           "iterations_by_space_and_p": {sp: {str(p): sorted(v) for p, v in sorted(d.items())}
+                                         for sp, d in by_space.items()},
+           "host_prep_s": host_s, "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
+def run_p_sweep(args):
+    """PCG iterations to 1e-8 against the degree on fixed perturbed meshes (Section 7.1 setting: random
+    right-hand side, zero initial guess), FP64 and mixed precision, for each space."""
+    import numpy as np
+    import torch
+    from paper_2506_17406_gb300 import riesz as rz
+    from paper_2506_17406_gb300.inputs import kuhn_mesh, normal_vector
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    table = {}
+    for n in (2, 4):
+        verts, cells = kuhn_mesh(n, 0.1, 1)
+        for space in ("CG", "N1curl", "RT"):
+            for p in range(1, 11):
+                row = {}
+                for name, kw in (("fp64", {}), ("mixed", dict(precond_precision=rz.PREC_FP32))):
+                    s = rz.Riesz(space, p, verts, cells, maxit=5000, **kw)
+                    b = torch.tensor(normal_vector(s.N, 7), device="cuda")
+                    x = torch.zeros_like(b)
+                    it, rr, rc = s.solve(b, x, check=False)
+                    row[name] = int(it[0]) if rc == 0 else None
+                    row["dofs"] = s.N
+                    s.close()
+                table.setdefault("n=%d" % n, {}).setdefault(space, {})[str(p)] = row
+    print(json.dumps({"metric": "PCG iterations to 1e-8 vs degree p", "data": "synthetic",
+                      "config": {"meshes": "n^3 x 6 Kuhn tets, perturbed 0.1h", "rhs": "N(0,1) vector",
+                                 "preconditioner": "interior Jacobi + vertex-star patches (additive)"},
+                      "iterations": table}), flush=True)
+
+
 def main():
     args = parse()
+    if args.p_sweep:
+        return run_p_sweep(args)
     if args.serve:
         return run_serving(args)
+    if args.batch:
+        return run_batch(args)
     wl = dict(WORKLOADS[args.workload])
     if args.precision == "fp64":
         wl["prec"] = 0
@@ -287,7 +439,7 @@ def main():
     def make(prec, a32):
         """A solver handle for the workload and its step closure (device setup + load + solve)."""
         s = rz.Riesz(wl["space"], wl["p"], verts, cells, precond_precision=prec, nrhs_max=nrhs,
-                     apply_precision=a32)
+                     apply_precision=a32, loop=rz.LOOP_HOST if args.pcg_loop == "host" else rz.LOOP_GRAPH)
         if nrhs == 1:  # f with N(0,1) CG_p coefficients per Cartesian component, b = (f, phi)
             fcg_h = normal_coeffs((ncomp, s.n_cg), 2 + rank)
         else:  # the paper's random right-hand side vectors (Section 7.1), one per RHS
@@ -323,9 +475,20 @@ def main():
     s, step, iters, relres_l, fcg, fcg_h, b, x = make(wl["prec"], wl.get("a32", 0))
     for _ in range(args.warmup):
         step()
+    # full per-kernel breakdown from one untimed step with every kernel bracketed
+    # by CUDA events (the PCG loop is host-driven while loop kernels are timed)
+    s.profile(True)
+    step()
+    torch.cuda.synchronize()
+    prof = s.profile_read()
+    s.profile(False)
+    dom = max(prof, key=lambda k: prof[k][0])
+    # timed region: only the dominant kernel is timed per launch; if it runs inside
+    # the PCG loop, the loop is host-driven there (graph passes cannot be timed per launch)
+    loop_driver = "host" if (dom in LOOP_KIND_NAMES or args.pcg_loop == "host") else "graph"
     torch.cuda.synchronize()
     launches0 = s.stats()["launches"]
-    s.profile(True, kinds=LIVE_KINDS)
+    s.profile(True, kinds=[dom])
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -338,12 +501,6 @@ def main():
     live = s.profile_read()
     s.profile(False)
     launches = s.stats()["launches"] - launches0
-    # full per-kernel breakdown from one extra, untimed, profiled step
-    s.profile(True)
-    step()
-    torch.cuda.synchronize()
-    prof = s.profile_read()
-    s.profile(False)
     ms, ntot = combine_ranks(ms, s.N, dist, device="cuda")
     value = ntot * nrhs * args.steps / (ms / 1e3)
 
@@ -351,7 +508,6 @@ def main():
     setup_kinds = ["geom", "elem", "diag", "assemble", "cholesky", "to_f32"]
     k_ms = {k: v[0] for k, v in prof.items()}
     # dominant kernel and its roofline (average launch time measured live in the timed region)
-    dom = max(prof, key=lambda k: prof[k][0])
     src = live if live[dom][1] > 0 else prof
     dom_ms = src[dom][0] / max(1, src[dom][1])
     st = s.stats()
@@ -449,6 +605,8 @@ def main():
                        "nrhs": nrhs, "apply_precision": "fp32" if wl.get("a32", 0) else "fp64",
                        "precond_precision": "fp32" if wl["prec"] == 1 else "fp64",
                        "rtol": 1e-8, "step": "device setup + load + PCG solve",
+                       "pcg_loop": loop_driver,
+                       "autotuned": s.tuning(),
                        "l2": "inputs larger than L2 (element matrices and patch factors)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "iterations": statistics.median(iters[-args.steps:]), "max_relres": relres,
@@ -459,7 +617,8 @@ def main():
             "setup_kernel_ms": sum(k_ms[k] for k in setup_kinds),
             "solve_kernel_ms": sum(v for k, v in k_ms.items() if k not in setup_kinds),
             "kernel_ms_per_step": {k: round(v, 4) for k, v in k_ms.items() if v > 0},
-            "kernel_ms_per_step_source": "one extra untimed step with every kernel bracketed by CUDA events",
+            "kernel_ms_per_step_source": "one untimed step before the timed region with every kernel bracketed "
+                                         "by CUDA events (host-driven PCG loop)",
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk,
         }

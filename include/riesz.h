@@ -65,6 +65,7 @@ enum {
 
 enum { RIESZ_PREC_FP64 = 0, RIESZ_PREC_FP32 = 1 };
 enum { RIESZ_APPLY_MATRIX_FREE = 0, RIESZ_APPLY_ELEMENT = 1 };
+enum { RIESZ_LOOP_HOST = 0, RIESZ_LOOP_GRAPH = 1 };
 
 typedef struct {
   /* Precision of the stored patch Cholesky factors and of the triangular
@@ -92,10 +93,31 @@ typedef struct {
      the first residual needs no product when x = 0.  riesz_apply is always
      FP64.  Default RIESZ_PREC_FP64. */
   int apply_precision;
+  /* Who drives the PCG iterations of riesz_solve.  RIESZ_LOOP_GRAPH (default):
+     the iterations run as a CUDA graph whose WHILE node repeats the body
+     (preconditioner, search-direction update, operator product, x/r update)
+     until a one-thread control kernel finds every right-hand side below rtol,
+     a reliable update due, a non-finite value or maxit; the host only acts
+     between graph launches (true-residual check, residual replacement,
+     restart), so there is no host round trip per iteration.  RIESZ_LOOP_HOST:
+     the host launches every kernel and reads the scalars each iteration
+     (overlapped with the next preconditioner step).  Both run the same
+     kernels in the same order and give bitwise equal results.  While the
+     profiler records any kind launched inside the loop, riesz_solve uses the
+     host-driven loop (CUDA events cannot time the passes of a graph loop). */
+  int loop;
+  /* 1 (default): riesz_setup_device times the patch Cholesky with 2, 3, 4 and
+     the maximum number of resident CTAs per SM on the handle's own patches
+     and keeps the fastest (see riesz_tuning); done only when the mesh has
+     more patches than SMs and at most 24 per SM, where the residency decides
+     how evenly the patches spread over the SMs.  The factors are bitwise the
+     same for every choice.  0: maximum residency, no timing runs. */
+  int autotune;
 } riesz_opts;
 
 /* Fill *o with the defaults: FP64 preconditioner, element-matrix apply,
-   rtol 1e-8, maxit 1000, nrhs_max 1, alpha = beta = 1. */
+   rtol 1e-8, maxit 1000, nrhs_max 1, alpha = beta = 1, FP64 apply,
+   graph-driven loop, autotune on. */
 void riesz_default_opts(riesz_opts* o);
 
 /* ---- host-only calls (no GPU needed) ---------------------------------- */
@@ -177,6 +199,25 @@ int riesz_precond(riesz_handle* h, const double* r, double* z, int nrhs, void* s
 int riesz_solve(riesz_handle* h, const double* b, double* x, int nrhs, void* stream, int* iters,
                 double* relres);
 
+/* Solve count independent systems together: the PCG loops of all handles are
+   branches of one CUDA graph (each a device-driven loop as with
+   RIESZ_LOOP_GRAPH), launched once, so the kernels of different systems run
+   concurrently on the GPU and no host round trip separates iterations.
+   Handles whose loops stop for a host step (true-residual check, residual
+   replacement, restart) continue in further launches.  The systems may differ
+   in space, degree, mesh and options.
+   hs: host [count] distinct handles with device state on the current device;
+   b[i], x[i]: device [nrhs[i]][N_i] (x[i] the initial guess on entry);
+   nrhs: host [count] (NULL = 1 each, each <= its handle's nrhs_max);
+   iters, relres: host [sum of nrhs] in handle order (may be NULL);
+   status: host [count] per-system status (may be NULL).
+   Returns RIESZ_OK when every system converged, else the first non-OK status
+   in handle order.  Uses the graph-driven loop whatever opts.loop says; with
+   the profiler recording a loop kind on any handle it returns
+   RIESZ_ERR_INVALID_ARG.  Synchronises the stream. */
+int riesz_solve_batch(riesz_handle* const* hs, int count, const double* const* b, double* const* x,
+                      const int* nrhs, void* stream, int* iters, double* relres, int* status);
+
 /* riesz_solve with host buffers: b_host, x_host are host [nrhs][N]; the
    copies to and from the device are part of the call. */
 int riesz_solve_host(riesz_handle* h, const double* b_host, double* x_host, int nrhs, void* stream,
@@ -224,6 +265,10 @@ enum {
    RIESZ_NKIND entries, either may be NULL). */
 int riesz_profile(riesz_handle* h, int enable);
 int riesz_profile_read(riesz_handle* h, double* ms, int64_t* counts);
+
+/* Choices of the setup autotuner: out[0] = resident k_cholesky CTAs per SM
+   (0: no limit), out[1] = candidates timed (0 when tuning was skipped). */
+int riesz_tuning(const riesz_handle* h, int* out);
 
 /* Timings (ms) and sizes of the last setup / solve:
    out[0] setup host ms, out[1] setup device ms, out[2] device bytes held,

@@ -887,13 +887,14 @@ constexpr int RED_BLOCKS = 608;  // 4 x 152 partials, reduced in a fixed order
 // Scalar slots (per right-hand side, stride 16).
 // S_RZNEW holds (r, z) of a preconditioner step until k_update_p commits it to
 // S_RZ, so a speculative step can be recomputed after a residual replacement.
+// S_RRLAST is r.r at the last true-residual computation (reliable updates).
 enum ScalarSlot { S_RZ = 0, S_PAP = 1, S_ALPHA = 2, S_RR = 3, S_BETA = 4, S_BB = 5, S_NONFINITE = 6, S_RZNEW = 7,
-                  S_XX = 8 };
+                  S_XX = 8, S_RRLAST = 9 };
 constexpr int SCAL_STRIDE = 16;  // doubles of scalars per right-hand side
 
 // Apply the scalar step of a finished reduction.  op: 0 pAp -> alpha; 1 rr;
 // 2 rz -> beta (classic); 3 rz, r.zold -> beta (Polak-Ribiere); 4 bb;
-// 5 rz (restart); 6 x.x.  A zero denominator (a right-hand side that has converged
+// 5 rz (restart); 6 x.x; 7 rr of a true residual (also kept as RRLAST).  A zero denominator (a right-hand side that has converged
 // exactly while others iterate) gives a zero step.
 __device__ __forceinline__ void scalar_op(int op, double s0, double s1, double* __restrict__ scal) {
   if (!isfinite(s0) || !isfinite(s1)) scal[S_NONFINITE] = 1.0;
@@ -914,6 +915,9 @@ __device__ __forceinline__ void scalar_op(int op, double s0, double s1, double* 
     scal[S_RZ] = s0;
   } else if (op == 6) {
     scal[S_XX] = s0;
+  } else if (op == 7) {
+    scal[S_RR] = s0;
+    scal[S_RRLAST] = s0;
   }
 }
 
@@ -1012,15 +1016,46 @@ __global__ void __launch_bounds__(NT) k_update_xr(int64_t n, double* __restrict_
   reduce2_finish(v0, 0.0, part, ticket, 1, scal);
 }
 
-// p = z + beta p, and commit (r, z) of this step: RZ = RZNEW
+// p = z + beta p, and commit (r, z) of this step: RZ = RZNEW.  With zold
+// non-null also zold = z (the flexible variant keeps the previous z).
 __global__ void k_update_p(int64_t n, double* __restrict__ scal, const double* __restrict__ z,
-                           double* __restrict__ p) {
+                           double* __restrict__ p, double* __restrict__ zold) {
   const int64_t o = blockIdx.y * n;
   scal += blockIdx.y * SCAL_STRIDE;
   const double beta = scal[S_BETA];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[o + i] = fma(beta, p[o + i], z[o + i]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = z[o + i];
+    p[o + i] = fma(beta, p[o + i], zi);
+    if (zold) zold[o + i] = zi;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) scal[S_RZ] = scal[S_RZNEW];
+}
+
+// Convergence control of the device-driven PCG loop (one thread), run after
+// each x, r update.  ctl[0] counts iterations, ctl[1] is the iteration limit,
+// ctl[2] receives the reason to leave the loop: 0 continue, 1 non-finite value,
+// 2 every right-hand side below rtol (recursive residual), 3 a reliable update
+// is due (FP32 products: some right-hand side gained eight orders of r.r since
+// the last true residual), 4 iteration limit.  The loop body runs again only
+// for reason 0, and ctl[0] grows by one per pass, so the loop ends after at
+// most ctl[1] passes whatever the scalars hold.
+__global__ void k_pcg_control(cudaGraphConditionalHandle cond, const double* __restrict__ scal, int nrhs,
+                              double rtol2, int reliable, int* __restrict__ ctl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int it = ctl[0] + 1;
+  ctl[0] = it;
+  bool all = true, nonfinite = false, replace = false;
+  for (int k = 0; k < nrhs; ++k) {
+    const double* sk = scal + k * SCAL_STRIDE;
+    const double rr = sk[S_RR], tol2 = rtol2 * sk[S_BB];
+    if (sk[S_NONFINITE] != 0.0 || !isfinite(rr)) nonfinite = true;
+    const bool below = rr <= tol2;
+    if (!below) all = false;
+    if (reliable && !below && rr <= 1e-8 * sk[S_RRLAST]) replace = true;
+  }
+  const int reason = nonfinite ? 1 : all ? 2 : replace ? 3 : (it >= ctl[1]) ? 4 : 0;
+  ctl[2] = reason;
+  cudaGraphSetConditional(cond, reason == 0 ? 1u : 0u);
 }
 
 // r = b - Ax (r = b when Ax is null: zero initial guess) ; r.r -> RR
@@ -1038,7 +1073,7 @@ __global__ void __launch_bounds__(NT) k_residual(int64_t n, const double* __rest
     r[i] = ri;
     v0 = fma(ri, ri, v0);
   }
-  reduce2_finish(v0, 0.0, part, ticket, 1, scal);
+  reduce2_finish(v0, 0.0, part, ticket, 7, scal);
 }
 
 // Preconditioner gather fused with the next PCG reduction (one grid row per

@@ -1,11 +1,75 @@
 #include "linalg.h"
 
 #include <algorithm>
+#include <exception>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <stdexcept>
 #include <string>
 
 namespace riesz {
+
+void parallel_for(int n, const std::function<void(int)>& fn) {
+  const int nt = std::max(1, std::min<int>(n, (int)std::thread::hardware_concurrency()));
+  if (nt <= 1) {
+    for (int i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  std::exception_ptr err = nullptr;
+  std::mutex mu;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      try {
+        for (int i = t; i < n; i += nt) fn(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!err) err = std::current_exception();
+      }
+    });
+  for (auto& x : th) x.join();
+  if (err) std::rethrow_exception(err);
+}
+
+Mat gram_tn(const Mat& A, const std::vector<double>& w, const Mat& B) {
+  if (A.m != B.m || (int)w.size() != A.m) throw std::runtime_error("gram_tn: shape mismatch");
+  const bool sym = &A == &B;
+  const int q = A.m, m = A.n, n = B.n;
+  // operands with the summation index contiguous: At [m][q], WBt [n][q] = (diag(w) B)^T
+  std::vector<double> At((size_t)m * q), WBt((size_t)n * q);
+  for (int k = 0; k < q; ++k) {
+    for (int i = 0; i < m; ++i) At[(size_t)i * q + k] = A(k, i);
+    for (int j = 0; j < n; ++j) WBt[(size_t)j * q + k] = w[k] * B(k, j);
+  }
+  Mat C(m, n);
+  constexpr int BI = 4, BJ = 4;
+  const int nbi = (m + BI - 1) / BI;
+  parallel_for(nbi, [&](int bi) {
+    const int i0 = bi * BI;
+    const int j_start = sym ? i0 : 0;
+    for (int j0 = j_start; j0 < n; j0 += BJ) {
+      double acc[BI][BJ] = {};
+      const double* a[BI];
+      const double* b[BJ];
+      for (int r = 0; r < BI; ++r) a[r] = &At[(size_t)std::min(i0 + r, m - 1) * q];
+      for (int c = 0; c < BJ; ++c) b[c] = &WBt[(size_t)std::min(j0 + c, n - 1) * q];
+      for (int k = 0; k < q; ++k) {
+        double av[BI], bv[BJ];
+        for (int r = 0; r < BI; ++r) av[r] = a[r][k];
+        for (int c = 0; c < BJ; ++c) bv[c] = b[c][k];
+        for (int r = 0; r < BI; ++r)
+          for (int c = 0; c < BJ; ++c) acc[r][c] += av[r] * bv[c];
+      }
+      for (int r = 0; r < BI && i0 + r < m; ++r)
+        for (int c = 0; c < BJ && j0 + c < n; ++c) C(i0 + r, j0 + c) = acc[r][c];
+    }
+  });
+  if (sym)
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < i; ++j) C(i, j) = C(j, i);
+  return C;
+}
 
 Mat matmul(const Mat& A, const Mat& B) {
   if (A.n != B.m) throw std::runtime_error("matmul: shape mismatch");

@@ -2,6 +2,7 @@
 // Row-major matrices; no external BLAS/LAPACK.
 #pragma once
 #include <cstddef>
+#include <functional>
 #include <vector>
 
 namespace riesz {
@@ -19,6 +20,14 @@ struct Mat {
     return I;
   }
 };
+
+// Run fn(i) for i in [0, n) on up to hardware_concurrency() threads
+// (interleaved static schedule; fn must be safe to call concurrently).
+void parallel_for(int n, const std::function<void(int)>& fn);
+
+// C = A^T diag(w) B for A [q][m], B [q][n] (blocked, threaded).  With B the
+// same object as A only the upper triangle is computed and mirrored.
+Mat gram_tn(const Mat& A, const std::vector<double>& w, const Mat& B);
 
 Mat matmul(const Mat& A, const Mat& B);      // A B
 Mat matmul_tn(const Mat& A, const Mat& B);   // A^T B

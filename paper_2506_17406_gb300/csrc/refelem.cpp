@@ -36,6 +36,7 @@
 #include <mutex>
 #include <stdexcept>
 #include <string>
+#include <tuple>
 
 namespace riesz {
 
@@ -679,17 +680,36 @@ EigenBasis eigenbasis(int fam, int p, int dim) {
 }
 
 // cache of eigenbases
-std::recursive_mutex g_mu;
-std::map<std::tuple<int, int, int>, std::shared_ptr<EigenBasis>> g_eig;
+// Build-once cache: the global lock only guards the map; each entry is built
+// under its own once-flag, so different keys build concurrently and a build
+// may look up other keys.
+template <typename K, typename V>
+struct OnceCache {
+  struct Entry {
+    std::once_flag once;
+    std::shared_ptr<V> val;
+  };
+  std::mutex mu;
+  std::map<K, std::shared_ptr<Entry>> m;
+  template <typename F>
+  const V& get(const K& k, F&& make) {
+    std::shared_ptr<Entry> e;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      auto& slot = m[k];
+      if (!slot) slot = std::make_shared<Entry>();
+      e = slot;
+    }
+    std::call_once(e->once, [&] { e->val = make(); });
+    return *e->val;
+  }
+};
+
+OnceCache<std::tuple<int, int, int>, EigenBasis> g_eig;
 
 const EigenBasis& eig_cached(int fam, int p, int dim) {
-  std::lock_guard<std::recursive_mutex> lk(g_mu);
-  auto key = std::make_tuple(fam, p, dim);
-  auto it = g_eig.find(key);
-  if (it != g_eig.end()) return *it->second;
-  auto eb = std::make_shared<EigenBasis>(eigenbasis(fam, p, dim));
-  g_eig[key] = eb;
-  return *eb;
+  return g_eig.get(std::make_tuple(fam, p, dim),
+                   [&] { return std::make_shared<EigenBasis>(eigenbasis(fam, p, dim)); });
 }
 
 // Tabulate an eigenbasis at points: values (npt x ne x ncomp), d (npt x ne x nd)
@@ -939,18 +959,23 @@ static void build_element(RefElement& R, int space, int p) {
   std::vector<double> v((size_t)Q.npt() * nref * R.ncomp), d((size_t)Q.npt() * nref * R.dcomp);
   R.tabulate(Q.npt(), Q.x.data(), v.data(), d.data());
   const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  auto component = [&](const std::vector<double>& t, int nc, int a) {  // [q][i] = t_i^a(x_q)
+    Mat T(Q.npt(), nref);
+    for (int q = 0; q < Q.npt(); ++q)
+      for (int i = 0; i < nref; ++i) T(q, i) = t[((size_t)q * nref + i) * nc + a];
+    return T;
+  };
   auto comp_matrix = [&](const std::vector<double>& t, int nc, int a, int b, double* out) {
-    // out[i][j] = sum_q w t_i^a t_j^b (+ transpose part when a != b)
-    for (int i = 0; i < nref; ++i)
-      for (int j = 0; j < nref; ++j) {
-        double s = 0.0;
-        for (int q = 0; q < Q.npt(); ++q) {
-          const double* tq = &t[(size_t)q * nref * nc];
-          s += Q.w[q] * tq[i * nc + a] * tq[j * nc + b];
-          if (a != b) s += Q.w[q] * tq[i * nc + b] * tq[j * nc + a];
-        }
-        out[(size_t)i * nref + j] = s;
-      }
+    // out[i][j] = sum_q w t_i^a t_j^b (+ the transposed term when a != b)
+    const Mat Ta = component(t, nc, a);
+    if (a == b) {
+      const Mat G = gram_tn(Ta, Q.w, Ta);
+      std::copy(G.a.begin(), G.a.end(), out);
+    } else {
+      const Mat G = gram_tn(Ta, Q.w, component(t, nc, b));
+      for (int i = 0; i < nref; ++i)
+        for (int j = 0; j < nref; ++j) out[(size_t)i * nref + j] = G(i, j) + G(j, i);
+    }
   };
   const size_t nn = (size_t)nref * nref;
   if (space == H1) {
@@ -975,9 +1000,9 @@ void RefElement::tabulate(int npt, const double* x, double* vals, double* dvals)
   Tab T = tabulate_expansion(E, ncomp, npt, x);
   const int nE = E.n;
   const int dfam = space == H1 ? 0 : (space == HCURL ? 1 : 2);
-  double D[3];
-  int nd;
-  for (int i = 0; i < npt; ++i) {
+  parallel_for(npt, [&](int i) {
+    double D[3];
+    int nd;
     if (vals) std::fill(vals + (size_t)i * nref * ncomp, vals + (size_t)(i + 1) * nref * ncomp, 0.0);
     if (dvals) std::fill(dvals + (size_t)i * nref * dcomp, dvals + (size_t)(i + 1) * nref * dcomp, 0.0);
     for (int c = 0; c < ncomp; ++c)
@@ -992,7 +1017,7 @@ void RefElement::tabulate(int npt, const double* x, double* vals, double* dvals)
             for (int dd = 0; dd < nd; ++dd) dvals[((size_t)i * nref + j) * dcomp + dd] += D[dd] * y;
         }
       }
-  }
+  });
 }
 
 static void build_cross(RefElement& R, const RefElement& cg) {
@@ -1002,29 +1027,28 @@ static void build_cross(RefElement& R, const RefElement& cg) {
   cg.tabulate(Q.npt(), Q.x.data(), c.data(), nullptr);
   R.ncg = cg.nref;
   R.Xcross.assign((size_t)R.ncomp * cg.nref * R.nref, 0.0);
-  for (int l = 0; l < R.ncomp; ++l)
-    for (int a = 0; a < cg.nref; ++a)
-      for (int i = 0; i < R.nref; ++i) {
-        double s = 0.0;
-        for (int q = 0; q < Q.npt(); ++q)
-          s += Q.w[q] * c[(size_t)q * cg.nref + a] * v[((size_t)q * R.nref + i) * R.ncomp + l];
-        R.Xcross[((size_t)l * cg.nref + a) * R.nref + i] = s;
-      }
+  // Xcross[l][a][i] = sum_q w_q c_a(x_q) v_i^l(x_q)
+  Mat Cm(Q.npt(), cg.nref), Vl(Q.npt(), R.nref);
+  for (int q = 0; q < Q.npt(); ++q)
+    for (int a = 0; a < cg.nref; ++a) Cm(q, a) = c[(size_t)q * cg.nref + a];
+  for (int l = 0; l < R.ncomp; ++l) {
+    for (int q = 0; q < Q.npt(); ++q)
+      for (int i = 0; i < R.nref; ++i) Vl(q, i) = v[((size_t)q * R.nref + i) * R.ncomp + l];
+    const Mat X = gram_tn(Cm, Q.w, Vl);
+    std::copy(X.a.begin(), X.a.end(), R.Xcross.begin() + (size_t)l * cg.nref * R.nref);
+  }
 }
 
 const RefElement& reference_element(int space, int p) {
-  static std::map<std::pair<int, int>, std::shared_ptr<RefElement>> cache;
-  std::lock_guard<std::recursive_mutex> lk(g_mu);
-  auto key = std::make_pair(space, p);
-  auto it = cache.find(key);
-  if (it != cache.end()) return *it->second;
+  static OnceCache<std::pair<int, int>, RefElement> cache;
   if (p < 1 || p > 12 || space < 0 || space > 2) throw std::runtime_error("reference_element: unsupported (space, p)");
-  auto R = std::make_shared<RefElement>();
-  build_element(*R, space, p);
-  const RefElement& cg = (space == H1) ? *R : reference_element(H1, p);
-  build_cross(*R, cg);
-  cache[key] = R;
-  return *R;
+  return cache.get(std::make_pair(space, p), [&] {
+    auto R = std::make_shared<RefElement>();
+    build_element(*R, space, p);
+    const RefElement& cg = (space == H1) ? *R : reference_element(H1, p);
+    build_cross(*R, cg);
+    return R;
+  });
 }
 
 }  // namespace riesz

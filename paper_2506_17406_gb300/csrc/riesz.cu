@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <stdexcept>
@@ -92,13 +93,23 @@ struct riesz_handle {
   DBuf<double> d_verts, d_g, d_jac, d_R, d_Ae, d_Ycell, d_dinv, d_L64, d_D64, d_zpatch, d_X;
   DBuf<float> d_L32, d_D32, d_Ae32;
   int multi_group = 8;  // right-hand sides per k_patch_solve_multi launch
+  int chol_ctas = 0;    // resident k_cholesky CTAs per SM picked by the autotuner (0: no limit)
+  int chol_tuned = 0;   // candidates the autotuner timed
   DBuf<int32_t> d_cells, d_cdofs, d_sc_pos, d_pn, d_pdofs, d_pz_pos, d_pb_cell, d_pb_ent, d_cgdofs, d_meta;
   DBuf<int64_t> d_sc_ptr, d_pdoff, d_pfoff, d_pdioff, d_pmoff, d_pz_ptr, d_pb_ptr, d_pb_off;
   DBuf<int> d_info;  // Cholesky status per patch
   DBuf<unsigned> d_ticket;    // last-block ticket of the fused reductions
   // PCG workspace
-  DBuf<double> d_r, d_z, d_zold, d_p, d_Ap, d_part, d_scal, d_tmp, d_xh;
+  DBuf<double> d_r, d_z, d_zold, d_p, d_Ap, d_part, d_scal, d_tmp, d_xh, d_xw;
   double* h_scal = nullptr;  // pinned
+  // device-driven PCG loop: control words, their pinned copy, the capture
+  // stream and the instantiated loop graphs (entry after a restart, resume)
+  DBuf<int> d_ctl;
+  int* h_ctl = nullptr;  // pinned [4]
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t g_entry = nullptr, g_resume = nullptr;
+  int g_nrhs = 0;
+  int64_t g_pro_launches = 0, g_body_launches = 0;
   cudaEvent_t ev_scal = nullptr;  // marks the arrival of h_scal
   int last_iters = 0;
   int64_t launches = 0;
@@ -118,12 +129,23 @@ struct riesz_handle {
            d_cdofs.bytes() + d_sc_pos.bytes() + d_pn.bytes() + d_pdofs.bytes() + d_pz_pos.bytes() +
            d_pb_cell.bytes() + d_pb_ent.bytes() + d_cgdofs.bytes() + d_sc_ptr.bytes() + d_pdoff.bytes() +
            d_pfoff.bytes() + d_pdioff.bytes() + d_pmoff.bytes() + d_meta.bytes() + d_pz_ptr.bytes() + d_pb_ptr.bytes() + d_pb_off.bytes() + d_r.bytes() + d_z.bytes() +
-           d_zold.bytes() + d_p.bytes() + d_Ap.bytes() + d_part.bytes() + d_scal.bytes() + d_tmp.bytes() + d_xh.bytes();
+           d_zold.bytes() + d_p.bytes() + d_Ap.bytes() + d_part.bytes() + d_scal.bytes() + d_tmp.bytes() + d_xh.bytes() +
+           d_xw.bytes() + d_ctl.bytes();
+  }
+  void drop_graphs() {
+    if (g_entry) cudaGraphExecDestroy(g_entry);
+    if (g_resume) cudaGraphExecDestroy(g_resume);
+    g_entry = g_resume = nullptr;
+    g_nrhs = 0;
   }
   void free_device() {
+    drop_graphs();
     for (auto* b : {&d_verts, &d_g, &d_jac, &d_R, &d_Ae, &d_Ycell, &d_dinv, &d_L64, &d_D64, &d_zpatch, &d_X, &d_r, &d_z,
-                    &d_zold, &d_p, &d_Ap, &d_part, &d_scal, &d_tmp, &d_xh})
+                    &d_zold, &d_p, &d_Ap, &d_part, &d_scal, &d_tmp, &d_xh, &d_xw})
       b->free();
+    d_ctl.free();
+    if (h_ctl) cudaFreeHost(h_ctl);
+    h_ctl = nullptr;
     d_L32.free();
     d_D32.free();
     d_Ae32.free();
@@ -139,6 +161,7 @@ struct riesz_handle {
   ~riesz_handle() {
     free_device();
     if (ev_scal) cudaEventDestroy(ev_scal);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   }
 };
@@ -715,8 +738,9 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
         for (int k = 0; k < nrhs; ++k) rr_last[k] = h.h_scal[k * SS + dev::S_RR];
         op_precond_dot(h, r, z, zold, 3, scal, nrhs, s);  // redo the step on the replaced residual
       }
-      launch(h, RIESZ_K_UPDATE, s, [&] { dev::k_update_p<<<dim3(296, nrhs), 256, 0, s>>>(N, scal, z, p); });
-      if (flex) CK(cudaMemcpyAsync(zold, z, (size_t)nrhs * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      launch(h, RIESZ_K_UPDATE, s, [&] {
+        dev::k_update_p<<<dim3(296, nrhs), 256, 0, s>>>(N, scal, z, p, flex ? zold : nullptr);
+      });
     }
     if (status == RIESZ_ERR_NOT_CONVERGED) {
       residual();
@@ -730,6 +754,399 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
   }
   h.last_iters = it;
   return status;
+}
+
+// ---- device-driven PCG loop (CUDA graph with a WHILE node) ------------------
+// One pass of the loop body is one PCG iteration in the order
+//   z = P^{-1} r with (r, z) -> beta;  p = z + beta p;  Ap = A p;  (p, Ap) -> alpha;
+//   x += alpha p, r -= alpha Ap with (r, r);  control
+// which is the host-driven loop's order rotated so that the control kernel,
+// which decides whether another pass runs, comes last.  The entry graph runs
+// the second half once (after a restart) before the WHILE node; the resume
+// graph starts with the body (after a residual replacement).  Both use only
+// handle-owned buffers (x is the handle's working copy d_xw), so they are
+// built once per handle and nrhs and relaunched.
+
+constexpr unsigned LOOP_KINDS = (1u << RIESZ_K_APPLY) | (1u << RIESZ_K_APPLY32) | (1u << RIESZ_K_GATHER) |
+                                (1u << RIESZ_K_PATCH_SOLVE) | (1u << RIESZ_K_PRECOND_GATHER) | (1u << RIESZ_K_DOT) |
+                                (1u << RIESZ_K_SCALAR) | (1u << RIESZ_K_UPDATE);
+
+bool profiling_loop(const riesz_handle& h) { return h.prof && (h.prof_mask & LOOP_KINDS) != 0u; }
+
+bool use_a32(const riesz_handle& h) {
+  return h.opts.apply_precision == RIESZ_PREC_FP32 && h.opts.apply_mode == RIESZ_APPLY_ELEMENT;
+}
+bool use_flex(const riesz_handle& h) { return h.opts.precond_precision == RIESZ_PREC_FP32 || use_a32(h); }
+
+// Ap = A p; (p, Ap) -> alpha; x += alpha p, r -= alpha Ap; (r, r) -> RR
+void iter_tail(riesz_handle& h, double* x, int nrhs, cudaStream_t s) {
+  const int64_t N = h.N();
+  op_apply(h, h.d_p.p, h.d_Ap.p, nrhs, s, use_a32(h));
+  dot(h, h.d_p.p, h.d_Ap.p, nullptr, 0, h.d_scal.p, nrhs, s);
+  launch(h, RIESZ_K_UPDATE, s, [&] {
+    dev::k_update_xr<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(N, h.d_scal.p, x, h.d_r.p, h.d_p.p, h.d_Ap.p,
+                                                                      h.d_part.p, h.d_ticket.p);
+  });
+}
+
+// z = P^{-1} r with (r, z) [and (r, zold)] -> beta; p = z + beta p [zold = z]
+void iter_head(riesz_handle& h, int nrhs, cudaStream_t s) {
+  const bool flex = use_flex(h);
+  op_precond_dot(h, h.d_r.p, h.d_z.p, flex ? h.d_zold.p : nullptr, flex ? 3 : 2, h.d_scal.p, nrhs, s);
+  launch(h, RIESZ_K_UPDATE, s, [&] {
+    dev::k_update_p<<<dim3(296, nrhs), 256, 0, s>>>(h.N(), h.d_scal.p, h.d_z.p, h.d_p.p, flex ? h.d_zold.p : nullptr);
+  });
+}
+
+// Add handle h's loop to graph G as a new root branch: [tail, control] then
+// WHILE { head, tail, control } (entry), or the WHILE node alone with its
+// condition starting at 1 (resume).  Returns the launches of the prologue and
+// of one body pass.
+std::pair<int64_t, int64_t> add_loop(riesz_handle& h, cudaGraph_t G, int nrhs, bool entry) {
+  cudaStream_t cs = h.cap_stream;
+  const int64_t l0 = h.launches;
+  int64_t pro = 0, body = 0;
+  cudaGraphConditionalHandle hc;
+  CK(cudaGraphConditionalHandleCreate(&hc, G, entry ? 0u : 1u, cudaGraphCondAssignDefault));
+  const double rtol2 = h.opts.rtol * h.opts.rtol;
+  const int reliable = use_a32(h) ? 1 : 0;
+  auto control = [&] {
+    launch(h, RIESZ_K_SCALAR, cs, [&] {
+      dev::k_pcg_control<<<1, 32, 0, cs>>>(hc, h.d_scal.p, nrhs, rtol2, reliable, h.d_ctl.p);
+    });
+  };
+  auto captured = [&](cudaGraph_t target, auto&& body_fn, std::vector<cudaGraphNode_t>* leaves) {
+    CK(cudaStreamBeginCaptureToGraph(cs, target, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+      body_fn();
+      if (leaves) {
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t* d = nullptr;
+        size_t nd = 0;
+        CK(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &d, nullptr, &nd));
+        leaves->assign(d, d + nd);
+      }
+    } catch (...) {
+      cudaGraph_t g;
+      cudaStreamEndCapture(cs, &g);
+      cudaGetLastError();
+      throw;
+    }
+    cudaGraph_t g;
+    CK(cudaStreamEndCapture(cs, &g));
+  };
+  std::vector<cudaGraphNode_t> deps;
+  if (entry) {
+    captured(G, [&] { iter_tail(h, h.d_xw.p, nrhs, cs); control(); }, &deps);
+    pro = h.launches - l0;
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wn;
+  CK(cudaGraphAddNode(&wn, G, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &cp));
+  const int64_t l1 = h.launches;
+  captured(cp.conditional.phGraph_out[0], [&] { iter_head(h, nrhs, cs); iter_tail(h, h.d_xw.p, nrhs, cs); control(); },
+           nullptr);
+  body = h.launches - l1;
+  h.launches = l0;  // captured, not launched: counted per executed pass instead
+  return {pro, body};
+}
+
+cudaGraphExec_t instantiate(cudaGraph_t G) {
+  cudaGraphExec_t e = nullptr;
+  const cudaError_t rc = cudaGraphInstantiate(&e, G, 0);
+  cudaGraphDestroy(G);
+  CK(rc);
+  return e;
+}
+
+// The handle's cached entry and resume graphs for nrhs right-hand sides.
+void ensure_graphs(riesz_handle& h, int nrhs) {
+  if (h.g_entry && h.g_nrhs == nrhs) return;
+  h.drop_graphs();
+  cudaGraph_t G;
+  CK(cudaGraphCreate(&G, 0));
+  auto pb = add_loop(h, G, nrhs, true);
+  h.g_entry = instantiate(G);
+  CK(cudaGraphCreate(&G, 0));
+  add_loop(h, G, nrhs, false);
+  h.g_resume = instantiate(G);
+  h.g_nrhs = nrhs;
+  h.g_pro_launches = pb.first;
+  h.g_body_launches = pb.second;
+}
+
+// Host-side state of one system solved with the device-driven loop.
+struct LoopSolve {
+  riesz_handle* h = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  int nrhs = 1;
+  std::vector<double> bb, tol2;
+  int status = RIESZ_ERR_NOT_CONVERGED;
+  bool done = false;
+  int next = 0;     // graph to launch: 1 entry, 2 resume
+  int pending = 0;  // host step waiting for scalars: 1 convergence check, 2 replacement, 3 final residual
+  int it_before = 0;  // iterations done before the current launch
+  int64_t pro = 0, body = 0;  // launches of the current graph's prologue and of one body pass
+  std::string err;
+};
+
+void ls_read(LoopSolve& L, cudaStream_t s, bool ctl) {
+  riesz_handle& h = *L.h;
+  CK(cudaMemcpyAsync(h.h_scal, h.d_scal.p, (size_t)L.nrhs * dev::SCAL_STRIDE * sizeof(double),
+                     cudaMemcpyDeviceToHost, s));
+  if (ctl) CK(cudaMemcpyAsync(h.h_ctl, h.d_ctl.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+}
+
+double ls_scal(const LoopSolve& L, int k, int slot) { return L.h->h_scal[k * dev::SCAL_STRIDE + slot]; }
+
+bool ls_all_below(const LoopSolve& L) {
+  for (int k = 0; k < L.nrhs; ++k)
+    if (!(ls_scal(L, k, dev::S_RR) <= L.tol2[k])) return false;
+  return true;
+}
+
+bool ls_nonfinite(const LoopSolve& L) {
+  for (int k = 0; k < L.nrhs; ++k)
+    if (ls_scal(L, k, dev::S_NONFINITE) != 0.0 || !std::isfinite(ls_scal(L, k, dev::S_RR))) return true;
+  return false;
+}
+
+// r = b - A x on the working copy (FP64), RR and RRLAST
+void ls_residual(LoopSolve& L, cudaStream_t s, bool x_is_zero) {
+  riesz_handle& h = *L.h;
+  const int64_t N = h.N();
+  if (!x_is_zero) op_apply(h, h.d_xw.p, h.d_Ap.p, L.nrhs, s);
+  launch(h, RIESZ_K_UPDATE, s, [&] {
+    dev::k_residual<<<dim3(dev::RED_BLOCKS, L.nrhs), dev::NT, 0, s>>>(
+        N, L.b, x_is_zero ? nullptr : h.d_Ap.p, h.d_r.p, h.d_part.p, h.d_ticket.p, h.d_scal.p);
+  });
+}
+
+// z = P r, p = z (and zold = z), RZ
+void ls_restart(LoopSolve& L, cudaStream_t s) {
+  riesz_handle& h = *L.h;
+  const size_t bytes = (size_t)L.nrhs * h.N() * sizeof(double);
+  op_precond_dot(h, h.d_r.p, h.d_z.p, nullptr, 5, h.d_scal.p, L.nrhs, s);
+  CK(cudaMemcpyAsync(h.d_p.p, h.d_z.p, bytes, cudaMemcpyDeviceToDevice, s));
+  if (use_flex(h)) CK(cudaMemcpyAsync(h.d_zold.p, h.d_z.p, bytes, cudaMemcpyDeviceToDevice, s));
+}
+
+void ls_finish(LoopSolve& L, int status, const char* msg) {
+  L.status = status;
+  L.done = true;
+  L.next = 0;
+  if (msg) L.err = msg;
+}
+
+// Solve the systems with the device-driven loop; every phase enqueues the
+// work of all systems before one synchronisation.
+void solve_graph(std::vector<LoopSolve>& Ls, cudaStream_t s) {
+  auto sync = [&] { CK(cudaStreamSynchronize(s)); };
+  // phase 1: working copy of x, (b, b) and (x, x)
+  for (auto& L : Ls) {
+    riesz_handle& h = *L.h;
+    const size_t bytes = (size_t)L.nrhs * h.N() * sizeof(double);
+    CK(cudaMemcpyAsync(h.d_xw.p, L.x, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(h.d_scal.p, 0, (size_t)L.nrhs * dev::SCAL_STRIDE * sizeof(double), s));
+    dot(h, L.b, L.b, nullptr, 4, h.d_scal.p, L.nrhs, s);
+    dot(h, h.d_xw.p, h.d_xw.p, nullptr, 6, h.d_scal.p, L.nrhs, s);
+    ls_read(L, s, false);
+  }
+  sync();
+  // phase 2: initial residual (no product for a zero initial guess)
+  for (auto& L : Ls) {
+    bool x_zero = true;
+    for (int k = 0; k < L.nrhs; ++k) x_zero = x_zero && ls_scal(L, k, dev::S_XX) == 0.0;
+    ls_residual(L, s, x_zero);
+    ls_read(L, s, false);
+  }
+  sync();
+  // phase 3: tolerances, early exits, first restart
+  for (auto& L : Ls) {
+    riesz_handle& h = *L.h;
+    L.bb.resize(L.nrhs);
+    L.tol2.resize(L.nrhs);
+    for (int k = 0; k < L.nrhs; ++k) {
+      L.bb[k] = ls_scal(L, k, dev::S_BB);
+      L.tol2[k] = h.opts.rtol * h.opts.rtol * L.bb[k];
+    }
+    if (ls_nonfinite(L)) {
+      ls_finish(L, RIESZ_ERR_NONFINITE, "non-finite right-hand side or initial guess");
+      continue;
+    }
+    if (ls_all_below(L)) {
+      ls_finish(L, RIESZ_OK, nullptr);
+      continue;
+    }
+    h.h_ctl[0] = 0;
+    h.h_ctl[1] = h.opts.maxit;
+    h.h_ctl[2] = 0;
+    h.h_ctl[3] = 0;
+    CK(cudaMemcpyAsync(h.d_ctl.p, h.h_ctl, 4 * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (h.opts.maxit <= 0) {
+      L.pending = 3;  // no iteration allowed: report the initial residual
+      L.status = RIESZ_ERR_NOT_CONVERGED;
+      continue;
+    }
+    ls_restart(L, s);
+    L.next = 1;
+  }
+  // the copies of h_ctl above must land before the pinned words are reused
+  sync();
+  for (auto& L : Ls)
+    if (L.pending == 3) ls_finish(L, RIESZ_ERR_NOT_CONVERGED, "PCG did not reach rtol within maxit");
+  // loop launches until every system is done
+  for (int round = 0;; ++round) {
+    std::vector<LoopSolve*> act;
+    for (auto& L : Ls)
+      if (!L.done && L.next) act.push_back(&L);
+    if (act.empty()) break;
+    if (act.size() == 1) {  // the handle's cached graphs
+      LoopSolve& L = *act[0];
+      ensure_graphs(*L.h, L.nrhs);
+      L.pro = L.next == 1 ? L.h->g_pro_launches : 0;
+      L.body = L.h->g_body_launches;
+      CK(cudaGraphLaunch(L.next == 1 ? L.h->g_entry : L.h->g_resume, s));
+    } else {  // one graph with a branch per system
+      cudaGraph_t G;
+      CK(cudaGraphCreate(&G, 0));
+      try {
+        for (LoopSolve* L : act) {
+          const auto pb = add_loop(*L->h, G, L->nrhs, L->next == 1);
+          L->pro = pb.first;
+          L->body = pb.second;
+        }
+      } catch (...) {
+        cudaGraphDestroy(G);
+        throw;
+      }
+      cudaGraphExec_t e = instantiate(G);
+      const cudaError_t rc = cudaGraphLaunch(e, s);
+      cudaGraphExecDestroy(e);  // freed once the launch completes
+      CK(rc);
+    }
+    for (LoopSolve* L : act) ls_read(*L, s, true);
+    sync();
+    // launches that ran: the prologue once (entry) and the body once per further pass
+    for (LoopSolve* L : act) {
+      riesz_handle& h = *L->h;
+      const int it = h.h_ctl[0];
+      const int64_t passes = it - L->it_before - (L->next == 1 ? 1 : 0);
+      h.launches += L->pro + std::max<int64_t>(0, passes) * L->body;
+      L->it_before = it;
+    }
+    bool any_pending = false;
+    for (LoopSolve* L : act) {
+      const int reason = L->h->h_ctl[2];
+      L->next = 0;
+      if (reason == 1) {
+        ls_finish(*L, RIESZ_ERR_NONFINITE, "non-finite value in the PCG recurrence");
+      } else if (reason == 2 || reason == 3 || reason == 4) {
+        ls_residual(*L, s, false);
+        ls_read(*L, s, false);
+        L->pending = reason == 2 ? 1 : reason == 3 ? 2 : 3;
+        any_pending = true;
+      } else {
+        ls_finish(*L, RIESZ_ERR_INTERNAL, "device loop stopped without a reason");
+      }
+    }
+    if (any_pending) sync();
+    for (LoopSolve* L : act) {
+      if (!L->pending) continue;
+      const int p = L->pending;
+      L->pending = 0;
+      riesz_handle& h = *L->h;
+      if (p == 1 && ls_all_below(*L)) {
+        ls_finish(*L, RIESZ_OK, nullptr);
+      } else if (p == 3 || h.h_ctl[0] >= h.opts.maxit) {
+        ls_finish(*L, RIESZ_ERR_NOT_CONVERGED, "PCG did not reach rtol within maxit");
+      } else if (p == 1 && !use_a32(h)) {
+        ls_restart(*L, s);  // FP64 operator: the recurrence drifted; start afresh from the true residual
+        L->next = 1;
+      } else {
+        L->next = 2;  // FP32 products: keep the search direction, continue from the true residual
+      }
+    }
+  }
+  for (auto& L : Ls) L.h->last_iters = L.it_before;
+  // results back to the caller's x
+  for (auto& L : Ls) {
+    riesz_handle& h = *L.h;
+    CK(cudaMemcpyAsync(L.x, h.d_xw.p, (size_t)L.nrhs * h.N() * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  sync();
+}
+
+// One system: the device-driven loop unless the handle asks for the host loop
+// or the profiler times loop kernels.
+int solve_one(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_t s, int* iters, double* relres) {
+  if (h.opts.loop != RIESZ_LOOP_GRAPH || profiling_loop(h)) return pcg_batch(h, b, x, nrhs, s, iters, relres);
+  std::vector<LoopSolve> Ls(1);
+  Ls[0].h = &h;
+  Ls[0].b = b;
+  Ls[0].x = x;
+  Ls[0].nrhs = nrhs;
+  solve_graph(Ls, s);
+  const LoopSolve& L = Ls[0];
+  for (int k = 0; k < nrhs; ++k) {
+    if (iters) iters[k] = L.it_before;
+    if (relres) relres[k] = L.bb[k] > 0 ? std::sqrt(ls_scal(L, k, dev::S_RR) / L.bb[k]) : 0.0;
+  }
+  if (L.status != RIESZ_OK) g_err = L.err;
+  return L.status;
+}
+
+// The dynamic shared-memory limit of a kernel is a property of the function
+// in the device's context, shared by every handle: only ever raise it, so a
+// handle with smaller needs cannot lower it below another live handle's.
+template <typename K>
+void raise_smem_limit(K* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limit[{dev, (const void*)kernel}];
+  if (bytes <= cur) return;
+  CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cur = bytes;
+}
+
+// Dynamic shared memory that limits k_cholesky to `ctas` resident CTAs per SM
+// (0: no limit beyond registers and its static shared memory).  With fewer
+// resident CTAs than patches, the patches left over start as CTAs finish, in
+// launch order (largest first), which balances the SMs' work when a few large
+// patches would otherwise pile up on some SMs.
+size_t chol_pad(int ctas) {
+  if (ctas <= 0) return 0;
+  static std::mutex mu;
+  static std::map<int, std::array<long, 3>> dev_info;  // smem per SM, reserved per CTA, static smem
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::array<long, 3> di;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = dev_info.find(dev);
+    if (it == dev_info.end()) {
+      int smem_sm = 0, reserved = 0;
+      CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+      CK(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+      cudaFuncAttributes fa;
+      CK(cudaFuncGetAttributes(&fa, dev::k_cholesky));
+      it = dev_info.emplace(dev, std::array<long, 3>{smem_sm, reserved, (long)fa.sharedSizeBytes}).first;
+    }
+    di = it->second;
+  }
+  const long per_cta = (di[0] / ctas) / 1024 * 1024;  // ctas fit, ctas + 1 do not
+  const long pad = per_cta - di[2] - di[1];
+  if (pad <= 0) return 0;
+  raise_smem_limit(dev::k_cholesky, (size_t)pad);
+  return (size_t)pad;
 }
 
 // Device setup from resident maps and vertex coordinates: a1 geometry,
@@ -772,8 +1189,9 @@ void device_compute(riesz_handle& h, cudaStream_t s) {
                                                    h.d_R.p, h.d_Ae.p, h.d_L64.p);
     });
     launch(h, RIESZ_K_CHOLESKY, s, [&] {
-      dev::k_cholesky<<<npatch, dev::NT, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p,
-                                                 h.d_L64.p, h.d_D64.p, h.d_info.p);
+      dev::k_cholesky<<<npatch, dev::NT, chol_pad(h.chol_ctas), s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pdioff.p,
+                                                                     h.d_pmoff.p, h.d_meta.p, h.d_L64.p, h.d_D64.p,
+                                                                     h.d_info.p);
     });
     if (h.opts.precond_precision == RIESZ_PREC_FP32) {
       launch(h, RIESZ_K_TO_F32, s, [&] {
@@ -798,6 +1216,52 @@ void device_compute(riesz_handle& h, cudaStream_t s) {
     for (int P = 0; P < npatch; ++P)
       if (info[P]) throw Err(RIESZ_ERR_INTERNAL, "patch matrix not positive definite");
   }
+}
+
+// Autotuner of the patch factorisation's residency: with between one and 24
+// patches per SM the balance of work over the SMs depends on how many CTAs
+// are resident at once (all at once: fixed round-robin placement; fewer:
+// later patches go to whichever SM frees a slot first).  Each candidate is
+// timed on the handle's own patches (assembly untimed, then the Cholesky
+// launch between CUDA events) and the fastest is kept; the factors are then
+// recomputed with it.  Every candidate computes bitwise the same factors.
+void tune_cholesky(riesz_handle& h, cudaStream_t s) {
+  const int npatch = (int)h.p_n.size();
+  int nsm = 0;
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h.device));
+  h.chol_ctas = 0;
+  h.chol_tuned = 0;
+  if (!h.opts.autotune || npatch <= nsm || npatch > 24 * nsm) return;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 0.f;
+  int best_c = 0;
+  for (int c : {0, 4, 3, 2}) {
+    CK(cudaMemsetAsync(h.d_info.p, 0, sizeof(int) * npatch, s));
+    dev::k_patch_assemble<<<npatch, 256, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pmoff.p, h.d_meta.p, h.d_pb_ptr.p,
+                                                 h.d_pb_cell.p, h.d_pb_off.p, h.d_pb_ent.p, h.C(), h.mesh.nref,
+                                                 h.ref->Q, h.d_g.p, h.d_R.p, h.d_Ae.p, h.d_L64.p);
+    KCHECK();
+    CK(cudaEventRecord(e0, s));
+    dev::k_cholesky<<<npatch, dev::NT, chol_pad(c), s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p,
+                                                         h.d_meta.p, h.d_L64.p, h.d_D64.p, h.d_info.p);
+    KCHECK();
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    h.launches += 2;
+    ++h.chol_tuned;
+    if (c == 0 || ms < best) {
+      best = ms;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h.chol_ctas = best_c;
+  device_compute(h, s);  // factors (and their FP32 copies) with the chosen residency
 }
 
 void setup_device_impl(riesz_handle& h, cudaStream_t s) {
@@ -833,7 +1297,10 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   h.d_zpatch.alloc(std::max<size_t>(1, h.p_dofs.size() * nrhs));
   h.d_X.upload(R.Xcross, s);
   h.d_cgdofs.upload(transpose_dofs(h.meshcg.cell_dofs, C, h.refcg->nref), s);
-  for (auto* b : {&h.d_r, &h.d_z, &h.d_zold, &h.d_p, &h.d_Ap, &h.d_tmp, &h.d_xh}) b->alloc((size_t)N * nrhs);
+  for (auto* b : {&h.d_r, &h.d_z, &h.d_zold, &h.d_p, &h.d_Ap, &h.d_tmp, &h.d_xh, &h.d_xw}) b->alloc((size_t)N * nrhs);
+  h.d_ctl.alloc(4);
+  CK(cudaMallocHost((void**)&h.h_ctl, 4 * sizeof(int)));
+  if (!h.cap_stream) CK(cudaStreamCreateWithFlags(&h.cap_stream, cudaStreamNonBlocking));
   h.d_part.alloc((size_t)2 * dev::RED_BLOCKS * nrhs);
   h.d_scal.alloc(16 * (size_t)nrhs);
   CK(cudaMallocHost((void**)&h.h_scal, (size_t)16 * nrhs * sizeof(double)));
@@ -845,13 +1312,13 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     if (h.opts.apply_precision == RIESZ_PREC_FP32) h.d_Ae32.alloc((size_t)C * n * n);
   } else {
     const size_t sm = ((size_t)n + R.Q) * dev::TC * sizeof(double);
-    CK(cudaFuncSetAttribute(dev::k_apply_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    raise_smem_limit(dev::k_apply_mf, (size_t)sm);
   }
   {
     const size_t sm = (size_t)n * nrhs * sizeof(double);
     if (sm > 48 * 1024) {
-      CK(cudaFuncSetAttribute(dev::k_apply_elem<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      CK(cudaFuncSetAttribute(dev::k_apply_elem<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      raise_smem_limit(dev::k_apply_elem<double, 8>, (size_t)sm);
+      raise_smem_limit(dev::k_apply_elem<float, 8>, (size_t)sm);
     }
   }
   {  // right-hand sides per multi-RHS sweep launch: as many as fit in shared memory (<= 8)
@@ -860,8 +1327,8 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     const size_t budget = 160 * 1024;  // dynamic share, leaves room for the static reduction buffers
     h.multi_group = (int)std::max<size_t>(1, std::min<size_t>(8, budget / per));
     const int smm = (int)(per * h.multi_group);
-    CK(cudaFuncSetAttribute(dev::k_patch_solve_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smm));
-    CK(cudaFuncSetAttribute(dev::k_patch_solve_multi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smm));
+    raise_smem_limit(dev::k_patch_solve_multi<float>, (size_t)smm);
+    raise_smem_limit(dev::k_patch_solve_multi<double>, (size_t)smm);
   }
   h.d_pdioff.upload(h.p_dioff, s);
   h.d_pmoff.upload(h.p_moff, s);
@@ -876,14 +1343,15 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   }
   const size_t smp = (size_t)(h.p_n.empty() ? 0 : (h.p_n[0] + 31) / 32 * 32) * sizeof(double);
   if (smp > 48 * 1024) {
-    CK(cudaFuncSetAttribute(dev::k_patch_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
-    CK(cudaFuncSetAttribute(dev::k_patch_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
+    raise_smem_limit(dev::k_patch_solve<double>, (size_t)smp);
+    raise_smem_limit(dev::k_patch_solve<float>, (size_t)smp);
   }
   h.d_ticket.alloc(nrhs);
   CK(cudaMemsetAsync(h.d_ticket.p, 0, sizeof(unsigned) * nrhs, s));
   CK(cudaFuncSetAttribute(dev::k_cholesky, cudaFuncAttributePreferredSharedMemoryCarveout,
                           (int)cudaSharedmemCarveoutMaxShared));
   device_compute(h, s);
+  tune_cholesky(h, s);
   h.on_device = true;
 }
 
@@ -933,6 +1401,8 @@ void riesz_default_opts(riesz_opts* o) {
   o->alpha = 1.0;
   o->beta = 1.0;
   o->apply_precision = RIESZ_PREC_FP64;
+  o->loop = RIESZ_LOOP_GRAPH;
+  o->autotune = 1;
 }
 
 const char* riesz_last_error(void) { return g_err.c_str(); }
@@ -957,6 +1427,8 @@ int riesz_create(int space, int p, int64_t nverts, const double* verts, int64_t 
     need(h->opts.alpha > 0 && h->opts.beta > 0 && std::isfinite(h->opts.alpha) && std::isfinite(h->opts.beta),
          "alpha and beta must be positive and finite");
     need(h->opts.apply_precision == 0 || h->opts.apply_precision == 1, "bad apply_precision");
+    need(h->opts.loop == RIESZ_LOOP_HOST || h->opts.loop == RIESZ_LOOP_GRAPH, "bad loop");
+    need(h->opts.autotune == 0 || h->opts.autotune == 1, "bad autotune");
     for (int64_t i = 0; i < nverts * 3; ++i)
       need(std::isfinite(verts[i]), "non-finite vertex coordinate", RIESZ_ERR_BAD_MESH);
     h->verts.assign(verts, verts + nverts * 3);
@@ -1108,9 +1580,48 @@ int riesz_solve(riesz_handle* h, const double* b, double* x, int nrhs, void* str
     check_dev(h);
     need(b && x && nrhs >= 1, "bad solve arguments");
     need(nrhs <= h->opts.nrhs_max, "nrhs exceeds opts.nrhs_max");
-    status = pcg_batch(*h, b, x, nrhs, S(stream), iters, relres);
+    status = solve_one(*h, b, x, nrhs, S(stream), iters, relres);
   });
   return rc != RIESZ_OK ? rc : status;
+}
+
+int riesz_solve_batch(riesz_handle* const* hs, int count, const double* const* b, double* const* x,
+                      const int* nrhs, void* stream, int* iters, double* relres, int* status) {
+  int first = RIESZ_OK;
+  int rc = guarded([&] {
+    need(count >= 0 && (count == 0 || (hs && b && x)), "bad batch arguments");
+    int dev_now = 0;
+    CK(cudaGetDevice(&dev_now));
+    std::vector<LoopSolve> Ls(count);
+    for (int i = 0; i < count; ++i) {
+      check_dev(hs[i]);
+      need(hs[i]->device == dev_now, "a handle of the batch is not on the current CUDA device");
+      for (int j = 0; j < i; ++j) need(hs[j] != hs[i], "a handle appears twice in the batch");
+      const int nr = nrhs ? nrhs[i] : 1;
+      need(b[i] && x[i] && nr >= 1 && nr <= hs[i]->opts.nrhs_max, "bad solve arguments in the batch");
+      need(!profiling_loop(*hs[i]), "the profiler records loop kernels on a handle of the batch");
+      Ls[i].h = hs[i];
+      Ls[i].b = b[i];
+      Ls[i].x = x[i];
+      Ls[i].nrhs = nr;
+    }
+    if (count == 0) return;
+    solve_graph(Ls, S(stream));
+    int off = 0;
+    for (int i = 0; i < count; ++i) {
+      const LoopSolve& L = Ls[i];
+      for (int k = 0; k < L.nrhs; ++k, ++off) {
+        if (iters) iters[off] = L.it_before;
+        if (relres) relres[off] = L.bb[k] > 0 ? std::sqrt(ls_scal(L, k, dev::S_RR) / L.bb[k]) : 0.0;
+      }
+      if (status) status[i] = L.status;
+      if (L.status != RIESZ_OK && first == RIESZ_OK) {
+        first = L.status;
+        g_err = "system " + std::to_string(i) + ": " + L.err;
+      }
+    }
+  });
+  return rc != RIESZ_OK ? rc : first;
 }
 
 int riesz_solve_host(riesz_handle* h, const double* b_host, double* x_host, int nrhs, void* stream, int* iters,
@@ -1125,7 +1636,7 @@ int riesz_solve_host(riesz_handle* h, const double* b_host, double* x_host, int 
     double* dx = h->d_xh.p;   // staging of x
     CK(cudaMemcpyAsync(db, b_host, (size_t)N * nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(dx, x_host, (size_t)N * nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
-    status = pcg_batch(*h, db, dx, nrhs, s, iters, relres);
+    status = solve_one(*h, db, dx, nrhs, s, iters, relres);
     CK(cudaMemcpyAsync(x_host, dx, (size_t)N * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   });
@@ -1160,6 +1671,15 @@ int riesz_update_geometry(riesz_handle* h, const double* verts, void* stream) {
     cudaStream_t s = S(stream);
     CK(cudaMemcpyAsync(h->d_verts.p, verts, h->d_verts.bytes(), cudaMemcpyDeviceToDevice, s));
     device_compute(*h, s);
+  });
+}
+
+int riesz_tuning(const riesz_handle* h, int* out) {
+  return guarded([&] {
+    check_dev(h);
+    need(out != nullptr, "null argument");
+    out[0] = h->chol_ctas;
+    out[1] = h->chol_tuned;
   });
 }
 

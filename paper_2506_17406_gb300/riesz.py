@@ -17,6 +17,7 @@ H1, HCURL, HDIV = 0, 1, 2
 SPACES = {"CG": H1, "H1": H1, "N1curl": HCURL, "HCURL": HCURL, "RT": HDIV, "HDIV": HDIV}
 PREC_FP64, PREC_FP32 = 0, 1
 APPLY_MATRIX_FREE, APPLY_ELEMENT = 0, 1
+LOOP_HOST, LOOP_GRAPH = 0, 1
 
 KINDS = ["geom", "elem", "diag", "assemble", "cholesky", "to_f32", "apply", "gather", "patch_solve",
          "precond_gather", "dot", "scalar", "update", "load", "apply32"]
@@ -34,7 +35,8 @@ class RieszError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precond_precision", ctypes.c_int), ("apply_mode", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("nrhs_max", ctypes.c_int), ("alpha", ctypes.c_double),
-                ("beta", ctypes.c_double), ("apply_precision", ctypes.c_int)]
+                ("beta", ctypes.c_double), ("apply_precision", ctypes.c_int), ("loop", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 _lib = None
@@ -60,8 +62,10 @@ _SIGS = {
     "riesz_precond": (_I, [_P, _P, _P, _I, _P]),
     "riesz_solve": (_I, [_P, _P, _P, _I, _P, _P, _P]),
     "riesz_solve_host": (_I, [_P, _P, _P, _I, _P, _P, _P]),
+    "riesz_solve_batch": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "riesz_load": (_I, [_P, _P, _P, _P]),
     "riesz_stats": (_I, [_P, _P]),
+    "riesz_tuning": (_I, [_P, _P]),
     "riesz_update_geometry": (_I, [_P, _P, _P]),
     "riesz_profile": (_I, [_P, _I]),
     "riesz_profile_read": (_I, [_P, _P, _P]),
@@ -139,6 +143,29 @@ def riesz_ref_tabulate(space, p, pts):
     return vals, dvals
 
 
+def solve_batch(solvers, bs, xs, nrhs=None, stream=None):
+    """Solve independent systems in one graph launch (riesz_solve_batch).
+
+    solvers: list of Riesz handles; bs, xs: matching device tensors [nrhs_i][N_i].
+    Returns (iters, relres, status) with iters/relres concatenated over the
+    systems' right-hand sides and status per system."""
+    lib = load_library()
+    n = len(solvers)
+    nr = [1] * n if nrhs is None else [int(k) for k in nrhs]
+    hs = (ctypes.c_void_p * n)(*[s.h.value for s in solvers])
+    bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    nra = np.asarray(nr, dtype=np.int32)
+    iters = np.zeros(sum(nr), dtype=np.int32)
+    relres = np.zeros(sum(nr))
+    status = np.zeros(n, dtype=np.int32)
+    rc = lib.riesz_solve_batch(ctypes.cast(hs, _P), n, ctypes.cast(bp, _P), ctypes.cast(xp, _P), _ptr(nra),
+                               _stream(stream), _ptr(iters), _ptr(relres), _ptr(status))
+    if rc not in (0, 4, 5):  # per-system convergence failures are reported in status
+        _check(rc)
+    return iters, relres, status
+
+
 class Riesz:
     """A solver handle: ``Riesz(space, p, verts, cells, **opts)`` builds the host
     maps; ``setup_device()`` runs the device setup."""
@@ -186,6 +213,11 @@ class Riesz:
         return {"setup_host_ms": out[0], "setup_device_ms": out[1], "device_bytes": out[2],
                 "factor_bytes": out[3], "last_iters": int(out[4]), "launches": int(out[5]),
                 "chol_flops": out[6], "precond_bytes": out[7]}
+
+    def tuning(self):
+        out = np.zeros(2, dtype=np.int32)
+        _check(self.lib.riesz_tuning(self.h, _ptr(out)))
+        return {"cholesky_ctas_per_sm": int(out[0]), "candidates_timed": int(out[1])}
 
     # ----- device calls -----
     def setup_device(self, stream=None):

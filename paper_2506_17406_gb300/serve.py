@@ -70,9 +70,11 @@ def estimate_footprint(h, opts):
     st = h.stats()
     N = h.N
     n = h.nref
-    elem = h.ncells * n * n * 8 if opts.get("apply_mode", rz.APPLY_ELEMENT) == rz.APPLY_ELEMENT else 0
+    elem = 0
+    if opts.get("apply_mode", rz.APPLY_ELEMENT) == rz.APPLY_ELEMENT:
+        elem = h.ncells * n * n * (12 if opts.get("apply_precision", rz.PREC_FP64) == rz.PREC_FP32 else 8)
     factor64 = st["factor_bytes"] * (2 if opts.get("precond_precision", 0) == rz.PREC_FP32 else 1)
-    vectors = 10 * N * 8
+    vectors = 11 * N * 8 * opts.get("nrhs_max", 1)
     maps = h.ncells * n * 4 * 3 + 4 * N * 8
     return int(elem + factor64 + vectors + maps)
 

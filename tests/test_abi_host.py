@@ -105,3 +105,24 @@ def test_device_calls_fail_loudly_without_device_state(lib):
     s = rz.Riesz("CG", 2, v, c, device=False)
     rc = lib.riesz_apply(s.h, ctypes.c_void_p(8), ctypes.c_void_p(8), 1, None)
     assert rc == 8  # RIESZ_ERR_NO_DEVICE, nothing launched
+
+
+def test_option_validation(lib):
+    v, c = kuhn_mesh(1)
+    for kw in [dict(loop=2), dict(loop=-1), dict(apply_precision=3), dict(alpha=0.0), dict(beta=-1.0),
+               dict(nrhs_max=0), dict(rtol=0.0)]:
+        with pytest.raises(rz.RieszError) as e:
+            rz.Riesz("CG", 2, v, c, device=False, **kw)
+        assert e.value.code == 1, kw
+    o = rz.default_opts()
+    assert o.loop == rz.LOOP_GRAPH and o.apply_precision == rz.PREC_FP64
+
+
+def test_batch_without_device_state(lib):
+    v, c = kuhn_mesh(1)
+    s = rz.Riesz("CG", 2, v, c, device=False)
+    hs = (ctypes.c_void_p * 1)(s.h.value)
+    ptrs = (ctypes.c_void_p * 1)(8)
+    rc = lib.riesz_solve_batch(ctypes.cast(hs, ctypes.c_void_p), 1, ctypes.cast(ptrs, ctypes.c_void_p),
+                               ctypes.cast(ptrs, ctypes.c_void_p), None, None, None, None, None)
+    assert rc in (6, 8)  # no CUDA device here (6) or no device state (8); nothing launched
