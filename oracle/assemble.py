@@ -161,6 +161,47 @@ class Preconditioner:
         return np.stack([self.apply(I[:, j]) for j in range(self.N)], 1)
 
 
+def coarse_dofs(md):
+    """Global indices of the lowest-order DOFs: the first type-I DOF of every vertex (H1), edge
+    (H(curl)) or face (H(div)).  By Lemma 4.1 their basis functions are the Whitney forms, so
+    they span W^k, the first summand of the PAFW decomposition (Section 6.2)."""
+    nv_d, ne_d, nf_d, _ = md.per_entity
+    off_v, off_e, off_f = md._offsets
+    if nv_d:
+        return off_v + nv_d * np.arange(md.nverts)
+    if ne_d:
+        return off_e + ne_d * np.arange(len(md.edges))
+    return off_f + nf_d * np.arange(len(md.faces))
+
+
+class TwoLevelPreconditioner:
+    """P^{-1} = D_II^{-1} (+) sum_V R_V^T A_V^{-1} R_V + R_0^T A_0^{-1} R_0: the one-level operator
+    plus an exact solve on W^k (the PAFW decomposition's coarse summand, Section 6.2), with
+    A_0 = R_0 A R_0^T the restriction of A to the lowest-order DOFs.  Additive and unweighted
+    (the paper combines the summands multiplicatively with eigenvalue-based weights)."""
+
+    def __init__(self, A, md, patches=None):
+        self.one = Preconditioner(A, md, patches)
+        self.N = self.one.N
+        self.W = coarse_dofs(md)
+        A = A.tocsr()
+        self.A0 = A[self.W][:, self.W].toarray()
+        self.fac0 = scipy.linalg.cho_factor(self.A0, lower=True)
+
+    def coarse(self, r):
+        """R_0^T A_0^{-1} R_0 r"""
+        z = np.zeros_like(r)
+        z[self.W] = scipy.linalg.cho_solve(self.fac0, r[self.W])
+        return z
+
+    def apply(self, r):
+        return self.one.apply(r) + self.coarse(r)
+
+    def dense(self):
+        I = np.eye(self.N)
+        return np.stack([self.apply(I[:, j]) for j in range(self.N)], 1)
+
+
 def pcg(A, b, M=None, rtol=1e-8, maxit=1000):
     """PCG from x0 = 0; stops on the true relative residual.  Returns (x, iters, relres)."""
     nb = np.linalg.norm(b)

@@ -515,155 +515,238 @@ struct Vec4<double> {
 };
 
 // ---------------------------------------------------------------------------
-// a7: patch solves z_V = L_V^{-T} L_V^{-1} R_V r on the tiled factor, one CTA
-// per patch.  Thread (row r, quarter-group q) = (tid/8, tid%8) owns tile
-// columns 4q..4q+3.
-//   forward:  y_I = Dinv_I (b_I - sum_{J<I} L_IJ y_J)      (block row I, contiguous)
-//   backward: x_I = Dinv_I^T (y_I - sum_{J>I} L_JI^T x_J)  (block column I)
-// Every tile is read once per sweep with 16-byte loads.
+// Bulk asynchronous copies (TMA, non-tensor form) into shared memory with
+// mbarrier completion.  Every wait is bounded: after ~1 s of SM clocks it
+// records a timeout in *err and returns false, so no thread can hang.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(NT) k_patch_solve(const int32_t* __restrict__ pn, const int64_t* __restrict__ pdoff,
-                                                    const int64_t* __restrict__ pfoff,
-                                                    const int64_t* __restrict__ pdoff_inv,
-                                                    const int64_t* __restrict__ pmoff,
-                                                    const int32_t* __restrict__ meta,
-                                                    const int32_t* __restrict__ pdofs, const T* __restrict__ Lall,
-                                                    const T* __restrict__ Dall, const double* __restrict__ r,
-                                                    double* __restrict__ zpatch, int64_t N, int64_t zstride) {
-  extern __shared__ unsigned char smraw[];
-  T* y = reinterpret_cast<T*>(smraw);  // [nb*32]
-  __shared__ T red[NT / 32][32];
-  __shared__ T tvec[32];
-  __shared__ int clist[MAXNB], cJ[MAXNB];
-  __shared__ int ncl;
+constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  const uint32_t a = smem_addr(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+// bytes (multiple of 16, both addresses 16-byte aligned) from global to shared,
+// completing on bar's transaction count
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// a7 (bulk-copy pipeline): patch solves z_V = L_V^{-T} L_V^{-1} R_V r with the
+// factor streamed through shared memory.  One CTA per patch: warp 8 (one
+// lane) copies 32x32 tiles in sweep order into a ring of S slots with
+// cp.async.bulk; warps 0-7 consume them, one tile per warp.
+//   forward, block row I in order:  t = b_I - sum_{J<I} L_IJ y_J  (tiles of
+//     row I, contiguous in storage, spread over the warps), then
+//     y_I = Dinv_I t (warp 0).
+//   backward, block row I in reverse: x_I = Dinv_I^T y_I (warp 0), then
+//     y_J -= L_IJ^T x_I for the tiles of row I (one warp per tile, distinct J).
+// Tile sequence (k = 0, 1, ...): forward rows I = 0..nb-1: [L tiles of row I,
+// Dinv_I]; backward rows I = nb-1..0: [Dinv_I, L tiles of row I].  Tile k sits
+// in slot k % S with phase (k / S) & 1.  Warp w takes the row tiles j = w,
+// w + 8, ..., so with S >= 8 the previous occupant of the slot a warp waits on
+// is always consumed already (its own previous tile or one of an earlier row)
+// and a parity wait can never match a phase two uses behind.  A wait that
+// times out (never in a correct run) sets *err and the patch result becomes
+// NaN.
+// ---------------------------------------------------------------------------
+constexpr int SWEEP_WARPS = 8;                    // consumer warps
+constexpr int SWEEP_NT = (SWEEP_WARPS + 1) * 32;  // + one producer warp
+
+// barrier among the consumer warps only (named barrier 1); the producer warp
+// never waits on it
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(SWEEP_WARPS * 32) : "memory");
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(SWEEP_NT) k_patch_sweep(const int32_t* __restrict__ pn,
+                                                          const int64_t* __restrict__ pdoff,
+                                                          const int64_t* __restrict__ pfoff,
+                                                          const int64_t* __restrict__ pdoff_inv,
+                                                          const int64_t* __restrict__ pmoff,
+                                                          const int32_t* __restrict__ meta,
+                                                          const int32_t* __restrict__ pdofs, const T* __restrict__ Lall,
+                                                          const T* __restrict__ Dall, const double* __restrict__ r,
+                                                          double* __restrict__ zpatch, int* __restrict__ err) {
+  static_assert(S >= SWEEP_WARPS, "a slot must not be reused before every consumer warp has moved past it");
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T* ring = reinterpret_cast<T*>(smraw);  // [S][1024]
+  T* y = ring + S * 1024;                 // [nb*32]
+  __shared__ __align__(8) uint64_t full[S], empty[S];
+  __shared__ T red[SWEEP_WARPS][32];
+  __shared__ int failed;
   const int P = blockIdx.x;
-  const int rh = blockIdx.y;
   const int n = pn[P];
   const int nb = (n + 31) / 32;
   const int32_t* tix = meta + pmoff[P];
-  const int32_t* tcol = tix + nb * nb;
+  const int32_t* tcol = tix + nb * nb;  // block column of each stored tile
   const T* L = Lall + pfoff[P];
   const T* Dv = Dall + pdoff_inv[P];
   const int32_t* dofs = pdofs + pdoff[P];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int row = tid >> 3, q = tid & 7;
-  for (int i = tid; i < nb * 32; i += NT) y[i] = (i < n) ? (T)r[rh * N + dofs[i]] : (T)0;
+  if (tid == 0) {
+    for (int k = 0; k < S; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 1);
+    }
+    failed = 0;
+    mbar_fence_init();
+  }
+  for (int i = tid; i < nb * 32; i += SWEEP_NT) y[i] = (i < n) ? (T)r[dofs[i]] : (T)0;
   __syncthreads();
-  // forward: the off-diagonal tiles of block row I are stored contiguously
-  int t0 = 0;
-  for (int I = 0; I < nb; ++I) {
-    const int td = tix[I * nb + I];
-    T acc = 0;
-    const T* base = L + row * 32 + 4 * q;
-    int t = t0;
-    for (; t + 2 <= td; t += 2) {
-      T a[4], b2[4], y0[4], y1[4];
-      Vec4<T>::load(base + (int64_t)t * 1024, a);
-      Vec4<T>::load(base + (int64_t)(t + 1) * 1024, b2);
-      Vec4<T>::load(y + tcol[t] * 32 + 4 * q, y0);
-      Vec4<T>::load(y + tcol[t + 1] * 32 + 4 * q, y1);
-      acc += a[0] * y0[0] + a[1] * y0[1] + a[2] * y0[2] + a[3] * y0[3];
-      acc += b2[0] * y1[0] + b2[1] * y1[1] + b2[2] * y1[2] + b2[3] * y1[3];
-    }
-    for (; t < td; ++t) {
-      T a[4], y0[4];
-      Vec4<T>::load(base + (int64_t)t * 1024, a);
-      Vec4<T>::load(y + tcol[t] * 32 + 4 * q, y0);
-      acc += a[0] * y0[0] + a[1] * y0[1] + a[2] * y0[2] + a[3] * y0[3];
-    }
-    t0 = td + 1;
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-    if (q == 0) tvec[row] = y[I * 32 + row] - acc;
-    __syncthreads();
-    T a[4];
-    Vec4<T>::load(Dv + I * 1024 + row * 32 + 4 * q, a);
-    T s = a[0] * tvec[4 * q] + a[1] * tvec[4 * q + 1] + a[2] * tvec[4 * q + 2] + a[3] * tvec[4 * q + 3];
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    s += __shfl_xor_sync(0xffffffffu, s, 4);
-    if (q == 0) y[I * 32 + row] = s;
-    __syncthreads();
-  }
-  // backward: block column I holds the nonzero tiles (J, I), J > I
-  for (int I = nb - 1; I >= 0; --I) {
-    if (tid == 0) {
-      int m = 0;
-      for (int J = I + 1; J < nb; ++J) {
-        const int t = tix[J * nb + I];
-        if (t >= 0) {
-          clist[m] = t;
-          cJ[m] = J;
-          ++m;
-        }
+  const int ntile = tix[(nb - 1) * nb + (nb - 1)] + 1;  // stored tiles, the last one diagonal
+  const int ktot = 2 * ntile;
+  constexpr uint32_t TB = 1024 * sizeof(T);
+  int bad = 0;
+  if (warp == SWEEP_WARPS) {  // producer
+    if (lane == 0) {
+      int k = 0;
+      auto issue = [&](const T* src) {
+        const int slot = k % S;
+        if (k >= S && !mbar_wait(&empty[slot], ((k / S) - 1) & 1, err)) bad = 1;
+        mbar_expect_tx(&full[slot], TB);
+        bulk_g2s(ring + slot * 1024, src, TB, &full[slot]);
+        ++k;
+      };
+      int rs = 0;
+      for (int I = 0; I < nb; ++I) {  // forward
+        const int td = tix[I * nb + I];
+        for (int t = rs; t < td; ++t) issue(L + (int64_t)t * 1024);
+        issue(Dv + (int64_t)I * 1024);
+        rs = td + 1;
       }
-      ncl = m;
+      for (int I = nb - 1; I >= 0; --I) {  // backward
+        const int td = tix[I * nb + I];
+        const int r0 = I ? tix[(I - 1) * nb + (I - 1)] + 1 : 0;
+        issue(Dv + (int64_t)I * 1024);
+        for (int t = r0; t < td; ++t) issue(L + (int64_t)t * 1024);
+      }
+      // every copy has completed before the consumers finish; after a timeout,
+      // wait (bounded) for the copies still in flight before leaving
+      if (bad || *err)
+        for (int j = (ktot > S ? ktot - S : 0); j < ktot; ++j) mbar_wait(&full[j % S], (j / S) & 1, err);
     }
-    __syncthreads();
-    const int m = ncl;
-    T acc[4] = {0, 0, 0, 0};
-    int k0 = 0;
-    for (; k0 + 2 <= m; k0 += 2) {
-      T a[4], b2[4];
-      Vec4<T>::load(L + (int64_t)clist[k0] * 1024 + row * 32 + 4 * q, a);
-      Vec4<T>::load(L + (int64_t)clist[k0 + 1] * 1024 + row * 32 + 4 * q, b2);
-      const T x0 = y[cJ[k0] * 32 + row], x1 = y[cJ[k0 + 1] * 32 + row];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[k] += a[k] * x0 + b2[k] * x1;
+    __syncwarp();  // the whole producer warp reaches the final CTA barrier together
+  } else {  // consumers
+    int k = 0;  // sequence index of the first tile of the current row
+    // forward
+    int rs = 0;
+    for (int I = 0; I < nb; ++I) {
+      const int td = tix[I * nb + I];
+      const int m = td - rs;  // off-diagonal tiles of row I
+      T acc = 0;
+      for (int j = warp; j < m; j += SWEEP_WARPS) {
+        const int kk = k + j, slot = kk % S;
+        if (!mbar_wait(&full[slot], (kk / S) & 1, err)) bad = 1;
+        const T* A = ring + slot * 1024;
+        const T* yJ = y + 32 * tcol[rs + j];
+#pragma unroll 8
+        for (int c = 0; c < 32; ++c) {
+          const int cc = (c + lane) & 31;
+          acc += A[lane * 32 + cc] * yJ[cc];
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+      }
+      red[warp][lane] = acc;
+      consumer_sync();
+      if (warp == 0) {
+        T t = y[I * 32 + lane];
+        for (int w = 0; w < SWEEP_WARPS; ++w) t -= red[w][lane];
+        const int kk = k + m, slot = kk % S;
+        if (!mbar_wait(&full[slot], (kk / S) & 1, err)) bad = 1;
+        const T* D = ring + slot * 1024;
+        T s = 0;
+#pragma unroll 8
+        for (int c = 0; c < 32; ++c) {
+          const int cc = (c + lane) & 31;
+          s += D[lane * 32 + cc] * __shfl_sync(0xffffffffu, t, cc);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        y[I * 32 + lane] = s;
+      }
+      consumer_sync();
+      k += m + 1;
+      rs = td + 1;
     }
-    for (; k0 < m; ++k0) {
-      T a[4];
-      Vec4<T>::load(L + (int64_t)clist[k0] * 1024 + row * 32 + 4 * q, a);
-      const T x0 = y[cJ[k0] * 32 + row];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[k] += a[k] * x0;
+    // backward
+    for (int I = nb - 1; I >= 0; --I) {
+      const int td = tix[I * nb + I];
+      const int r0 = I ? tix[(I - 1) * nb + (I - 1)] + 1 : 0;
+      const int m = td - r0;
+      if (warp == 0) {
+        const int slot = k % S;
+        if (!mbar_wait(&full[slot], (k / S) & 1, err)) bad = 1;
+        const T* D = ring + slot * 1024;
+        const T t = y[I * 32 + lane];
+        T s = 0;
+#pragma unroll 8
+        for (int rr = 0; rr < 32; ++rr) s += D[rr * 32 + lane] * __shfl_sync(0xffffffffu, t, rr);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        y[I * 32 + lane] = s;
+      }
+      consumer_sync();
+      const T* xI = y + I * 32;
+      for (int j = warp; j < m; j += SWEEP_WARPS) {
+        const int kk = k + 1 + j, slot = kk % S;
+        if (!mbar_wait(&full[slot], (kk / S) & 1, err)) bad = 1;
+        const T* A = ring + slot * 1024;
+        T s = 0;
+#pragma unroll 8
+        for (int rr = 0; rr < 32; ++rr) s += A[rr * 32 + lane] * xI[rr];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        y[32 * tcol[r0 + j] + lane] -= s;
+      }
+      consumer_sync();
+      k += m + 1;
     }
-    // reduce over the 4 rows of this warp (lanes with equal q), then over warps
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 8);
-      acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 16);
-    }
-    if (lane < 8) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) red[warp][4 * q + k] = acc[k];
-    }
-    __syncthreads();
-    if (tid < 32) {
-      T s = 0;
-      for (int w = 0; w < NT / 32; ++w) s += red[w][tid];
-      tvec[tid] = y[I * 32 + tid] - s;
-    }
-    __syncthreads();
-    // x_I = Dinv^T t : x[c] = sum_r Dinv[r][c] t[r]
-    T b4[4];
-    Vec4<T>::load(Dv + I * 1024 + row * 32 + 4 * q, b4);
-    const T tr = tvec[row];
-    T part[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) part[k] = b4[k] * tr;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      part[k] += __shfl_xor_sync(0xffffffffu, part[k], 8);
-      part[k] += __shfl_xor_sync(0xffffffffu, part[k], 16);
-    }
-    if (lane < 8) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) red[warp][4 * q + k] = part[k];
-    }
-    __syncthreads();
-    if (tid < 32) {
-      T s = 0;
-      for (int w = 0; w < NT / 32; ++w) s += red[w][tid];
-      y[I * 32 + tid] = s;
-    }
-    __syncthreads();
   }
-  double* zp = zpatch + rh * zstride + pdoff[P];
-  for (int i = tid; i < n; i += NT) zp[i] = (double)y[i];
+  if (bad) atomicExch(&failed, 1);
+  __syncthreads();
+  double* zp = zpatch + pdoff[P];
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  for (int i = tid; i < n; i += SWEEP_NT) zp[i] = failed ? nan : (double)y[i];
 }
+
 
 // a7 for several right-hand sides at once (2..8): every factor tile is loaded
 // once and applied to all of them, so the HBM traffic per right-hand side

@@ -106,6 +106,7 @@ struct riesz_handle {
   // stream and the instantiated loop graphs (entry after a restart, resume)
   DBuf<int> d_ctl;
   int* h_ctl = nullptr;  // pinned [4]
+  DBuf<int> d_flags;     // [0]: a bulk-copy wait of the patch sweeps timed out
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t g_entry = nullptr, g_resume = nullptr;
   int g_nrhs = 0;
@@ -130,7 +131,7 @@ struct riesz_handle {
            d_pb_cell.bytes() + d_pb_ent.bytes() + d_cgdofs.bytes() + d_sc_ptr.bytes() + d_pdoff.bytes() +
            d_pfoff.bytes() + d_pdioff.bytes() + d_pmoff.bytes() + d_meta.bytes() + d_pz_ptr.bytes() + d_pb_ptr.bytes() + d_pb_off.bytes() + d_r.bytes() + d_z.bytes() +
            d_zold.bytes() + d_p.bytes() + d_Ap.bytes() + d_part.bytes() + d_scal.bytes() + d_tmp.bytes() + d_xh.bytes() +
-           d_xw.bytes() + d_ctl.bytes();
+           d_xw.bytes() + d_ctl.bytes() + d_flags.bytes();
   }
   void drop_graphs() {
     if (g_entry) cudaGraphExecDestroy(g_entry);
@@ -144,6 +145,7 @@ struct riesz_handle {
                     &d_zold, &d_p, &d_Ap, &d_part, &d_scal, &d_tmp, &d_xh, &d_xw})
       b->free();
     d_ctl.free();
+    d_flags.free();
     if (h_ctl) cudaFreeHost(h_ctl);
     h_ctl = nullptr;
     d_L32.free();
@@ -549,6 +551,13 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
   });
 }
 
+// Ring slots of the bulk-copy sweep kernel (tiles of 4 KB in FP32, 8 KB in FP64).
+constexpr int SWEEP_SLOTS_F32 = 8, SWEEP_SLOTS_F64 = 8;
+template <typename T>
+size_t sweep_smem(int slots, int nbmax) {
+  return (size_t)slots * 1024 * sizeof(T) + (size_t)nbmax * 32 * sizeof(T);
+}
+
 // Patch sweeps for nrhs right-hand sides into zpatch.
 void op_patch_solves(riesz_handle& h, const double* r, int nrhs, cudaStream_t s) {
   const int64_t N = h.N();
@@ -557,19 +566,18 @@ void op_patch_solves(riesz_handle& h, const double* r, int nrhs, cudaStream_t s)
   const int nbmax = (h.p_n[0] + 31) / 32;
   const int64_t zstride = (int64_t)h.p_dofs.size();
   const bool f32 = h.opts.precond_precision == RIESZ_PREC_FP32;
-  if (nrhs == 1) {
-    dim3 grid(npatch, 1);
+  if (nrhs == 1) {  // factor tiles streamed through shared memory by bulk copies
     if (f32)
       launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
-        dev::k_patch_solve<float><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(float), s>>>(
+        dev::k_patch_sweep<float, SWEEP_SLOTS_F32><<<npatch, dev::SWEEP_NT, sweep_smem<float>(SWEEP_SLOTS_F32, nbmax), s>>>(
             h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L32.p,
-            h.d_D32.p, r, h.d_zpatch.p, N, zstride);
+            h.d_D32.p, r, h.d_zpatch.p, h.d_flags.p);
       });
     else
       launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
-        dev::k_patch_solve<double><<<grid, dev::NT, (size_t)nbmax * 32 * sizeof(double), s>>>(
+        dev::k_patch_sweep<double, SWEEP_SLOTS_F64><<<npatch, dev::SWEEP_NT, sweep_smem<double>(SWEEP_SLOTS_F64, nbmax), s>>>(
             h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L64.p,
-            h.d_D64.p, r, h.d_zpatch.p, N, zstride);
+            h.d_D64.p, r, h.d_zpatch.p, h.d_flags.p);
       });
     return;
   }
@@ -1299,6 +1307,8 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   h.d_cgdofs.upload(transpose_dofs(h.meshcg.cell_dofs, C, h.refcg->nref), s);
   for (auto* b : {&h.d_r, &h.d_z, &h.d_zold, &h.d_p, &h.d_Ap, &h.d_tmp, &h.d_xh, &h.d_xw}) b->alloc((size_t)N * nrhs);
   h.d_ctl.alloc(4);
+  h.d_flags.alloc(4);
+  CK(cudaMemsetAsync(h.d_flags.p, 0, 4 * sizeof(int), s));
   CK(cudaMallocHost((void**)&h.h_ctl, 4 * sizeof(int)));
   if (!h.cap_stream) CK(cudaStreamCreateWithFlags(&h.cap_stream, cudaStreamNonBlocking));
   h.d_part.alloc((size_t)2 * dev::RED_BLOCKS * nrhs);
@@ -1341,10 +1351,10 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
       h.d_D32.alloc((size_t)h.dinv_entries);
     }
   }
-  const size_t smp = (size_t)(h.p_n.empty() ? 0 : (h.p_n[0] + 31) / 32 * 32) * sizeof(double);
-  if (smp > 48 * 1024) {
-    raise_smem_limit(dev::k_patch_solve<double>, (size_t)smp);
-    raise_smem_limit(dev::k_patch_solve<float>, (size_t)smp);
+  {
+    const int nbm = h.p_n.empty() ? 1 : (h.p_n[0] + 31) / 32;
+    raise_smem_limit(dev::k_patch_sweep<float, SWEEP_SLOTS_F32>, sweep_smem<float>(SWEEP_SLOTS_F32, nbm));
+    raise_smem_limit(dev::k_patch_sweep<double, SWEEP_SLOTS_F64>, sweep_smem<double>(SWEEP_SLOTS_F64, nbm));
   }
   h.d_ticket.alloc(nrhs);
   CK(cudaMemsetAsync(h.d_ticket.p, 0, sizeof(unsigned) * nrhs, s));

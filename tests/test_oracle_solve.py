@@ -229,3 +229,76 @@ def test_sampled_oracle_rows_match_full_oracle():
     assert np.abs(asm.sampled_apply(ref, md, d, x) - (A @ x)[d]).max() < 1e-12 * np.abs(A @ x).max()
     ze = P.apply(x)
     assert np.abs(asm.sampled_precond(ref, md, d, x) - ze[d]).max() < 1e-11 * np.abs(ze).max()
+
+
+@pytest.mark.parametrize("space,p", [("CG", 3), ("N1curl", 2), ("RT", 2)])
+def test_coarse_dofs_are_the_first_dof_of_each_entity(space, p):
+    """W^k (Lemma 4.1): one DOF per vertex / edge / face, the entity's first type-I DOF in every cell."""
+    ref = reference_element(space, p)
+    v, c = kuhn_mesh(2, 0.1, 4)
+    md = MeshDofs(v, c, ref)
+    W = asm.coarse_dofs(md)
+    k = {"CG": 0, "N1curl": 1, "RT": 2}[space]
+    nent = {0: md.nverts, 1: len(md.edges), 2: len(md.faces)}[k]
+    assert len(W) == nent == len(np.unique(W))
+    seen = set()
+    for e in range(len(c)):
+        for s in range({0: 4, 1: 6, 2: 4}[k]):
+            seen.add(int(md.cell_dofs[e, ref.entity_dofs[(k, s)][0]]))
+    assert seen == set(int(w) for w in W)
+
+
+@pytest.mark.parametrize("space,p", [("CG", 3), ("N1curl", 3), ("RT", 3)])
+def test_coarse_correction_reproduces_coarse_functions(space, p):
+    """For u = R_0^T w in W^k and r = A u, the coarse summand returns u exactly (A_0 = R_0 A R_0^T)."""
+    ref = reference_element(space, p)
+    v, c = kuhn_mesh(3, 0.1, 5)
+    md = MeshDofs(v, c, ref)
+    A = asm.assemble(md, asm.element_matrices(ref, v, c))
+    P2 = asm.TwoLevelPreconditioner(A, md)
+    w = normal_vector(len(P2.W), 3)
+    u = np.zeros(md.ndofs)
+    u[P2.W] = w
+    z = P2.coarse(A @ u)
+    assert np.abs(z - u).max() <= 1e-10 * np.abs(u).max()
+
+
+@pytest.mark.parametrize("space,p", [("CG", 2), ("N1curl", 2), ("RT", 2)])
+def test_two_level_spectrum(space, p):
+    """Adding the PSD coarse term to P^{-1} can only raise every eigenvalue of P^{-1} A (Courant-Fischer in
+    the A inner product), and raises the additive upper bound by one summand: 5 + lambda_J."""
+    ref = reference_element(space, p)
+    v, c = kuhn_mesh(2, 0.1, 6)
+    md = MeshDofs(v, c, ref)
+    Ae = asm.element_matrices(ref, v, c)
+    A = asm.assemble(md, Ae)
+    Ad = A.toarray()
+    e1 = np.sort(np.linalg.eigvals(asm.Preconditioner(A, md).dense() @ Ad).real)
+    e2 = np.sort(np.linalg.eigvals(asm.TwoLevelPreconditioner(A, md).dense() @ Ad).real)
+    assert e1.min() > 0
+    assert np.all(e2 >= e1 * (1 - 1e-10))
+    I = ref.interior
+    jac = 1.0
+    if I:
+        dI = np.diag(Ad)[md.n_interface:]
+        for e in range(len(c)):
+            ae = Ae[e][np.ix_(I, I)]
+            de = dI[md.cell_dofs[e, I] - md.n_interface]
+            jac = max(jac, np.linalg.eigvalsh(ae / np.sqrt(np.outer(de, de))).max())
+    assert e2.max() <= 5 + jac + 1e-10
+
+
+def test_two_level_iterations_do_not_grow_with_refinement():
+    """With W^k the iteration count stays flat from 2^3 to 4^3 cubes while the one-level count grows."""
+    ref = reference_element("CG", 3)
+    its1, its2 = [], []
+    for n in (2, 4):
+        v, c = kuhn_mesh(n, 0.1, 1)
+        md = MeshDofs(v, c, ref)
+        A = asm.assemble(md, asm.element_matrices(ref, v, c))
+        b = normal_vector(md.ndofs, 3)
+        its1.append(asm.pcg(A, b, asm.Preconditioner(A, md).apply)[1])
+        its2.append(asm.pcg(A, b, asm.TwoLevelPreconditioner(A, md).apply)[1])
+    assert its1[1] > 1.3 * its1[0]
+    assert its2[1] <= 1.15 * its2[0] + 1
+    assert its2[1] < its1[1]
