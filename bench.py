@@ -202,7 +202,8 @@ def combine_ranks(ms, n_local, dist=None, device=None):
 
 
 # kernel kinds launched inside the PCG loop (timing one per launch needs the host-driven loop)
-LOOP_KIND_NAMES = {"apply", "apply32", "gather", "patch_solve", "precond_gather", "dot", "scalar", "update"}
+LOOP_KIND_NAMES = {"apply", "apply32", "gather", "patch_solve", "precond_gather", "dot", "scalar", "update",
+                   "coarse_apply"}
 
 
 def kernel_source_hash():
@@ -505,7 +506,7 @@ def main():
     value = ntot * nrhs * args.steps / (ms / 1e3)
 
     # setup / solve split from the profiler (kernel time only)
-    setup_kinds = ["geom", "elem", "diag", "assemble", "cholesky", "to_f32"]
+    setup_kinds = ["geom", "elem", "diag", "assemble", "cholesky", "to_f32", "coarse"]
     k_ms = {k: v[0] for k, v in prof.items()}
     # dominant kernel and its roofline (average launch time measured live in the timed region)
     src = live if live[dom][1] > 0 else prof

@@ -113,11 +113,22 @@ typedef struct {
      how evenly the patches spread over the SMs.  The factors are bitwise the
      same for every choice.  0: maximum residency, no timing runs. */
   int autotune;
+  /* 1 (default): add the lowest-order space W^k to the preconditioner (the
+     first summand of the PAFW decomposition, Section 6.2; by Lemma 4.1 its
+     basis is the first DOF of every vertex (H1), edge (H(curl)) or face
+     (H(div))): z += R_0^T A_0^{-1} R_0 r with A_0 = R_0 A R_0^T, additive and
+     unweighted.  A_0 is assembled densely and inverted in FP32 at device
+     setup (block Gauss-Jordan) and applied as a dense product, so it is used
+     only when W^k has at most 6144 DOFs (otherwise the preconditioner stays
+     one-level; riesz_tuning reports the coarse size).  Its FP32 rounding only
+     perturbs the preconditioner: solves run flexible PCG and stop on the FP64
+     true residual.  0: one-level preconditioner. */
+  int coarse;
 } riesz_opts;
 
 /* Fill *o with the defaults: FP64 preconditioner, element-matrix apply,
    rtol 1e-8, maxit 1000, nrhs_max 1, alpha = beta = 1, FP64 apply,
-   graph-driven loop, autotune on. */
+   graph-driven loop, autotune on, coarse space on. */
 void riesz_default_opts(riesz_opts* o);
 
 /* ---- host-only calls (no GPU needed) ---------------------------------- */
@@ -254,7 +265,9 @@ enum {
   RIESZ_K_UPDATE = 12,      /* a9 vector updates                         */
   RIESZ_K_LOAD = 13,        /* right-hand side assembly                  */
   RIESZ_K_APPLY32 = 14,     /* a3-a4 with the FP32 element matrices      */
-  RIESZ_NKIND = 15
+  RIESZ_K_COARSE = 15,      /* W^k: A_0 assembly and block inversion     */
+  RIESZ_K_COARSE_APPLY = 16,/* W^k: coarse correction A_0^{-1} R_0 r     */
+  RIESZ_NKIND = 17
 };
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around
@@ -266,8 +279,9 @@ enum {
 int riesz_profile(riesz_handle* h, int enable);
 int riesz_profile_read(riesz_handle* h, double* ms, int64_t* counts);
 
-/* Choices of the setup autotuner: out[0] = resident k_cholesky CTAs per SM
-   (0: no limit), out[1] = candidates timed (0 when tuning was skipped). */
+/* Choices made at setup: out[0] = resident k_cholesky CTAs per SM picked by
+   the autotuner (0: no limit), out[1] = candidates timed (0 when tuning was
+   skipped), out[2] = DOFs of the W^k coarse space (0 when it is off). */
 int riesz_tuning(const riesz_handle* h, int* out);
 
 /* Timings (ms) and sizes of the last setup / solve:

@@ -174,6 +174,27 @@ def coarse_dofs(md):
     return off_f + nf_d * np.arange(len(md.faces))
 
 
+def coarse_matrix(ref, md, alpha=1.0, beta=1.0):
+    """A_0 = R_0 A R_0^T by quadrature of the lowest-order basis functions only (one per k-entity
+    of each cell), assembled in the numbering of coarse_dofs; cheap at any mesh size."""
+    k = ref.k
+    nloc = {0: 4, 1: 6, 2: 4}[k]
+    loc = [ref.entity_dofs[(k, s)][0] for s in range(nloc)]
+    X, w = quadrature(3, ref.p + 2)
+    vhat, dhat = ref.tabulate(X)
+    J, _ = jacobians(md.verts, md.cells)
+    v, d, det = physical_tabulation(ref, J, vhat[:, loc], dhat[:, loc])
+    wq = w[None, :] * np.abs(det)[:, None]
+    Ae = (beta * np.einsum("epia,epja,ep->eij", v, v, wq) + alpha * np.einsum("epia,epja,ep->eij", d, d, wq))
+    W = coarse_dofs(md)
+    cidx = -np.ones(md.ndofs, dtype=np.int64)
+    cidx[W] = np.arange(len(W))
+    ce = cidx[md.cell_dofs[:, loc]]
+    rows = np.repeat(ce, nloc, axis=1).ravel()
+    cols = np.tile(ce, (1, nloc)).ravel()
+    return scipy.sparse.coo_matrix((Ae.ravel(), (rows, cols)), shape=(len(W), len(W))).tocsr()
+
+
 class TwoLevelPreconditioner:
     """P^{-1} = D_II^{-1} (+) sum_V R_V^T A_V^{-1} R_V + R_0^T A_0^{-1} R_0: the one-level operator
     plus an exact solve on W^k (the PAFW decomposition's coarse summand, Section 6.2), with

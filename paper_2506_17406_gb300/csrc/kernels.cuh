@@ -946,7 +946,7 @@ __global__ void __launch_bounds__(NT) k_patch_solve_multi(
 __global__ void k_precond_gather(int64_t N, int64_t nifd, const int64_t* __restrict__ ptr,
                                  const int32_t* __restrict__ pos, const double* __restrict__ zpatch, int64_t zstride,
                                  const double* __restrict__ dinv, const double* __restrict__ r, double* __restrict__ z,
-                                 int nrhs) {
+                                 int nrhs, const int32_t* __restrict__ cidx, const double* __restrict__ zc, int64_t n0) {
   const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (d >= N) return;
   for (int rh = 0; rh < nrhs; ++rh) {
@@ -954,10 +954,254 @@ __global__ void k_precond_gather(int64_t N, int64_t nifd, const int64_t* __restr
     if (d < nifd) {
       s = 0.0;
       for (int64_t k = ptr[d]; k < ptr[d + 1]; ++k) s += zpatch[rh * zstride + pos[k]];
+      if (cidx && cidx[d] >= 0) s += zc[rh * n0 + cidx[d]];
     } else {
       s = dinv[d - nifd] * r[rh * N + d];
     }
     z[rh * N + d] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// W^k coarse space (the first summand of the PAFW decomposition, Section 6.2;
+// by Lemma 4.1 its basis is the lowest-order DOF of each vertex, edge or face):
+// A_0 = R_0 A R_0^T assembled densely in FP32, inverted in place by block
+// Gauss-Jordan sweeps (SPD: the pivots are Schur-complement diagonal blocks,
+// no pivoting), applied as a dense product per preconditioner call.
+// ---------------------------------------------------------------------------
+constexpr int CB = 64;  // block size of the coarse sweeps
+
+// A0 [N0p][N0p] (zeroed before): row I of the coarse matrix from its contribution list
+// (ptr, J, cell, local a | b << 16), entries sum_q g_q(cell) R_q[a][b] in list order;
+// the padding rows get 1 on the diagonal.
+__global__ void k_coarse_assemble(int N0, int N0p, const int64_t* __restrict__ ptr, const int32_t* __restrict__ cJ,
+                                  const int32_t* __restrict__ ccell, const int32_t* __restrict__ cab, int64_t C, int n,
+                                  int Q, const double* __restrict__ g, const double* __restrict__ R,
+                                  float* __restrict__ A0) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= N0p) return;
+  if (I >= N0) {
+    A0[(int64_t)I * N0p + I] = 1.f;
+    return;
+  }
+  const int64_t nn = (int64_t)n * n;
+  int64_t e = ptr[I];
+  const int64_t e1 = ptr[I + 1];
+  while (e < e1) {
+    const int J = cJ[e];
+    double s = 0.0;
+    for (; e < e1 && cJ[e] == J; ++e) {
+      const int64_t c = ccell[e];
+      const int a = cab[e] & 0xffff, b = cab[e] >> 16;
+      for (int q = 0; q < Q; ++q) s += g[q * C + c] * R[q * nn + (int64_t)a * n + b];
+    }
+    A0[(int64_t)I * N0p + J] = (float)s;
+  }
+}
+
+constexpr int CBP = CB + 4;  // shared row stride of a 64x64 FP32 tile (16-byte rows, few bank conflicts)
+
+// 64x64 tile, row-major with leading dimension ld, into shared memory; with
+// transpose the tile's transpose is stored.  16-byte global loads.
+__device__ __forceinline__ void load_tile64(float (*S)[CBP], const float* __restrict__ src, int64_t ld,
+                                            bool transpose) {
+  for (int t = threadIdx.x; t < CB * CB / 4; t += blockDim.x) {
+    const int r = t / (CB / 4), c = 4 * (t % (CB / 4));
+    const float4 v = *reinterpret_cast<const float4*>(src + r * ld + c);
+    if (transpose) {
+      S[c][r] = v.x;
+      S[c + 1][r] = v.y;
+      S[c + 2][r] = v.z;
+      S[c + 3][r] = v.w;
+    } else {
+      *reinterpret_cast<float4*>(&S[r][c]) = v;
+    }
+  }
+}
+
+// acc[a][b] = sum_k As[ty + 16 a][k] Bs[k][4 tx + b]  (ty = tid / 16, tx = tid % 16)
+__device__ __forceinline__ void tile64_mma(const float (*As)[CBP], const float (*Bs)[CBP], int ty, int tx,
+                                           float acc[4][4]) {
+#pragma unroll 8
+  for (int k = 0; k < CB; ++k) {
+    float av[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = As[ty + 16 * a][k];
+    const float4 b = *reinterpret_cast<const float4*>(&Bs[k][4 * tx]);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      acc[a][0] = fmaf(av[a], b.x, acc[a][0]);
+      acc[a][1] = fmaf(av[a], b.y, acc[a][1]);
+      acc[a][2] = fmaf(av[a], b.z, acc[a][2]);
+      acc[a][3] = fmaf(av[a], b.w, acc[a][3]);
+    }
+  }
+}
+
+// The sweeps keep only the block lower triangle (tiles i >= j; diagonal tiles
+// full).  Tile (i, j) of the symmetric matrix: stored, or the transpose of (j, i).
+__device__ __forceinline__ const float* tile_ptr(const float* A, int N0p, int i, int j) {
+  return A + (int64_t)i * CB * N0p + (int64_t)j * CB;
+}
+
+// Sweep of block k, step 1 (one CTA): Dinv = A_kk^{-1} by Gauss-Jordan in shared memory.
+__global__ void __launch_bounds__(256) k_gj_pivot(int N0p, int k, const float* __restrict__ A, float* __restrict__ Dinv) {
+  __shared__ __align__(16) float D[CB][CBP];
+  load_tile64(D, tile_ptr(A, N0p, k, k), N0p, false);
+  for (int p = 0; p < CB; ++p) {
+    __syncthreads();
+    const float pv = D[p][p];
+    float old[16], fi[16], pr[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int e = threadIdx.x + 256 * m, i = e / CB, j = e % CB;
+      old[m] = D[i][j];
+      fi[m] = D[i][p];
+      pr[m] = D[p][j];
+    }
+    __syncthreads();
+    const float ipv = 1.f / pv;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int e = threadIdx.x + 256 * m, i = e / CB, j = e % CB;
+      float v;
+      if (i == p)
+        v = (j == p) ? ipv : pr[m] * ipv;
+      else
+        v = (j == p) ? -fi[m] * ipv : old[m] - fi[m] * pr[m] * ipv;
+      D[i][j] = v;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < CB * CB; t += blockDim.x) Dinv[t] = D[t / CB][t % CB];
+}
+
+// step 2 (a CTA per column block j != k): Rb[:, j] = Dinv A_kj
+__global__ void __launch_bounds__(256) k_gj_row(int N0p, int k, const float* __restrict__ A,
+                                               const float* __restrict__ Dinv, float* __restrict__ Rb) {
+  const int j = blockIdx.x;
+  if (j == k) return;
+  __shared__ __align__(16) float As[CB][CBP], Bs[CB][CBP];
+  load_tile64(As, Dinv, CB, false);
+  if (j < k)
+    load_tile64(Bs, tile_ptr(A, N0p, k, j), N0p, false);
+  else
+    load_tile64(Bs, tile_ptr(A, N0p, j, k), N0p, true);
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  float acc[4][4] = {};
+  tile64_mma(As, Bs, ty, tx, acc);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+    *reinterpret_cast<float4*>(Rb + (int64_t)(ty + 16 * a) * N0p + j * CB + 4 * tx) =
+        make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+}
+
+// step 3 (a CTA per lower tile (i, j), i >= j, i, j != k): A_ij -= A_ik Rb[:, j]
+__global__ void __launch_bounds__(256) k_gj_update(int N0p, int k, float* __restrict__ A, const float* __restrict__ Rb) {
+  const int t = blockIdx.x;  // lower-triangle tile index: t = i (i + 1) / 2 + j
+  int i = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  while (i * (i + 1) / 2 > t) --i;
+  const int j = t - i * (i + 1) / 2;
+  if (i == k || j == k) return;
+  __shared__ __align__(16) float As[CB][CBP], Bs[CB][CBP];
+  if (i > k)
+    load_tile64(As, tile_ptr(A, N0p, i, k), N0p, false);
+  else
+    load_tile64(As, tile_ptr(A, N0p, k, i), N0p, true);
+  load_tile64(Bs, Rb + (int64_t)j * CB, N0p, false);
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  float acc[4][4] = {};
+  tile64_mma(As, Bs, ty, tx, acc);
+  float* Aij = A + (int64_t)i * CB * N0p + (int64_t)j * CB;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    float4* q = reinterpret_cast<float4*>(Aij + (int64_t)(ty + 16 * a) * N0p + 4 * tx);
+    float4 v = *q;
+    v.x -= acc[a][0];
+    v.y -= acc[a][1];
+    v.z -= acc[a][2];
+    v.w -= acc[a][3];
+    *q = v;
+  }
+}
+
+// step 4 (a CTA per block j): A_kj = Rb[:, j] (j < k), A_jk = Rb[:, j]^T (j > k),
+// A_kk = -Dinv.  After every block has been swept, the lower triangle holds -A_0^{-1}.
+__global__ void __launch_bounds__(256) k_gj_finish(int N0p, int k, float* __restrict__ A, const float* __restrict__ Dinv,
+                                                  const float* __restrict__ Rb) {
+  const int j = blockIdx.x;
+  for (int t = threadIdx.x; t < CB * CB; t += blockDim.x) {
+    const int r = t / CB, c = t % CB;
+    if (j == k) {
+      A[(int64_t)(k * CB + r) * N0p + k * CB + c] = -Dinv[t];
+    } else {
+      const float v = Rb[(int64_t)r * N0p + j * CB + c];
+      if (j < k)
+        A[(int64_t)(k * CB + r) * N0p + j * CB + c] = v;
+      else
+        A[(int64_t)(j * CB + c) * N0p + k * CB + r] = v;
+    }
+  }
+}
+
+// Fill the upper tiles from the lower ones (full rows for the coarse product).
+__global__ void __launch_bounds__(256) k_coarse_mirror(int N0p, float* __restrict__ A) {
+  const int t = blockIdx.x;  // strictly lower tile index
+  int i = (int)((sqrtf(8.f * t + 1.f) + 1.f) * 0.5f);
+  while (i * (i - 1) / 2 > t) --i;
+  while ((i + 1) * i / 2 <= t) ++i;
+  const int j = t - i * (i - 1) / 2;
+  for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+    const int r = e / CB, c = e % CB;
+    A[(int64_t)(j * CB + c) * N0p + i * CB + r] = A[(int64_t)(i * CB + r) * N0p + j * CB + c];
+  }
+}
+
+// r0[rh][j] = r[rh][cw[j]] in FP32 (zero padding up to N0p)
+__global__ void k_coarse_gather(int N0, int N0p, const int32_t* __restrict__ cw, const double* __restrict__ r,
+                                int64_t N, int nrhs, float* __restrict__ r0) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrhs * N0p) return;
+  const int rh = t / N0p, j = t % N0p;
+  r0[t] = j < N0 ? (float)r[rh * N + cw[j]] : 0.f;
+}
+
+// zc[rh][i] = sum_j A0inv[i][j] r0[rh][j] with A0inv = -A (the swept, mirrored
+// matrix): r0 staged in shared memory, one warp per row, every matrix row read
+// once for all right-hand sides.
+__global__ void __launch_bounds__(256) k_coarse_apply(int N0, int N0p, const float* __restrict__ A,
+                                                     const float* __restrict__ r0g, int nrhs,
+                                                     double* __restrict__ zc) {
+  extern __shared__ __align__(16) float r0[];  // [nrhs][N0p]
+  for (int t = threadIdx.x; t < nrhs * N0p / 4; t += blockDim.x)
+    reinterpret_cast<float4*>(r0)[t] = reinterpret_cast<const float4*>(r0g)[t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int wg = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), nw = gridDim.x * (blockDim.x / 32);
+  for (int i = wg; i < N0; i += nw) {
+    const float4* row = reinterpret_cast<const float4*>(A + (int64_t)i * N0p);
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q = lane; q < N0p / 4; q += 32) {
+      const float4 a = row[q];
+#pragma unroll
+      for (int rh = 0; rh < 8; ++rh) {
+        if (rh < nrhs) {
+          const float4 x = reinterpret_cast<const float4*>(r0 + rh * N0p)[q];
+          s[rh] += a.x * x.x + a.y * x.y + a.z * x.z + a.w * x.w;
+        }
+      }
+    }
+#pragma unroll
+    for (int rh = 0; rh < 8; ++rh) {
+      if (rh < nrhs) {
+        float v = s[rh];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) zc[(int64_t)rh * N0 + i] = -(double)v;
+      }
+    }
   }
 }
 
@@ -1169,7 +1413,9 @@ __global__ void __launch_bounds__(NT) k_precond_gather_dot(int64_t N, int64_t ni
                                                           const double* __restrict__ r, double* __restrict__ z,
                                                           const double* __restrict__ zold, double* __restrict__ part,
                                                           unsigned* __restrict__ ticket, int op,
-                                                          double* __restrict__ scal, int64_t zstride) {
+                                                          double* __restrict__ scal, int64_t zstride,
+                                                          const int32_t* __restrict__ cidx,
+                                                          const double* __restrict__ zc, int64_t n0) {
   const int64_t o = blockIdx.y * N;
   zpatch += blockIdx.y * zstride;
   r += o;
@@ -1181,6 +1427,7 @@ __global__ void __launch_bounds__(NT) k_precond_gather_dot(int64_t N, int64_t ni
     if (d < nifd) {
       zi = 0.0;
       for (int64_t k = ptr[d]; k < ptr[d + 1]; ++k) zi += zpatch[pos[k]];
+      if (cidx && cidx[d] >= 0) zi += zc[blockIdx.y * n0 + cidx[d]];
     } else {
       zi = dinv[d - nifd] * r[d];
     }

@@ -92,6 +92,17 @@ struct riesz_handle {
   int device = 0;
   DBuf<double> d_verts, d_g, d_jac, d_R, d_Ae, d_Ycell, d_dinv, d_L64, d_D64, d_zpatch, d_X;
   DBuf<float> d_L32, d_D32, d_Ae32;
+  // W^k coarse space: coarse DOF -> global DOF, interface DOF -> coarse index,
+  // per coarse row the (J, cell, local a | b << 16) contributions of A_0
+  bool coarse_on = false;
+  int N0 = 0, N0p = 0, coarse_group = 8;
+  std::vector<int32_t> c_w, c_idx, c_J, c_cell, c_ab;
+  std::vector<int64_t> c_ptr;
+  DBuf<int32_t> d_cw, d_cidx, d_cJ, d_ccell, d_cab;
+  DBuf<int64_t> d_cptr;
+  DBuf<float> d_A0, d_Dinv0, d_Rb0;  // swept coarse matrix (-A_0^{-1} when done), pivot inverse, sweep row
+  DBuf<float> d_r0;                   // R_0 r in FP32 [nrhs][N0p]
+  DBuf<double> d_zc;                  // coarse corrections [nrhs][N0]
   int multi_group = 8;  // right-hand sides per k_patch_solve_multi launch
   int chol_ctas = 0;    // resident k_cholesky CTAs per SM picked by the autotuner (0: no limit)
   int chol_tuned = 0;   // candidates the autotuner timed
@@ -131,7 +142,9 @@ struct riesz_handle {
            d_pb_cell.bytes() + d_pb_ent.bytes() + d_cgdofs.bytes() + d_sc_ptr.bytes() + d_pdoff.bytes() +
            d_pfoff.bytes() + d_pdioff.bytes() + d_pmoff.bytes() + d_meta.bytes() + d_pz_ptr.bytes() + d_pb_ptr.bytes() + d_pb_off.bytes() + d_r.bytes() + d_z.bytes() +
            d_zold.bytes() + d_p.bytes() + d_Ap.bytes() + d_part.bytes() + d_scal.bytes() + d_tmp.bytes() + d_xh.bytes() +
-           d_xw.bytes() + d_ctl.bytes() + d_flags.bytes();
+           d_xw.bytes() + d_ctl.bytes() + d_flags.bytes() + d_cw.bytes() + d_cidx.bytes() + d_cJ.bytes() +
+           d_ccell.bytes() + d_cab.bytes() + d_cptr.bytes() + d_A0.bytes() + d_Dinv0.bytes() + d_Rb0.bytes() +
+           d_r0.bytes() + d_zc.bytes();
   }
   void drop_graphs() {
     if (g_entry) cudaGraphExecDestroy(g_entry);
@@ -146,6 +159,13 @@ struct riesz_handle {
       b->free();
     d_ctl.free();
     d_flags.free();
+    for (auto* b : {&d_cw, &d_cidx, &d_cJ, &d_ccell, &d_cab}) b->free();
+    d_cptr.free();
+    d_A0.free();
+    d_Dinv0.free();
+    d_Rb0.free();
+    d_r0.free();
+    d_zc.free();
     if (h_ctl) cudaFreeHost(h_ctl);
     h_ctl = nullptr;
     d_L32.free();
@@ -416,6 +436,59 @@ void plan_patch(riesz_handle& h, int64_t v, int64_t& foff, int64_t& dioff) {
   h.pb_ptr.push_back((int64_t)h.pb_cell.size());
 }
 
+// W^k (Lemma 4.1: the first type-I DOF of each vertex, edge or face carries
+// the Whitney form) and the contribution lists of A_0 = R_0 A R_0^T.
+constexpr int COARSE_MAX = 6144;  // largest dense coarse problem (FP32 inverse: 151 MB)
+
+void plan_coarse(riesz_handle& h) {
+  const MeshMaps& M = h.mesh;
+  const int k = h.space;  // entity dimension of the Whitney DOFs: 0, 1, 2
+  const int nd = M.per_entity[k];
+  const int64_t nent = k == 0 ? M.nverts : (k == 1 ? M.nedges : M.nfaces);
+  h.coarse_on = false;
+  if (!h.opts.coarse || nd == 0 || nent > COARSE_MAX) return;
+  const int N0 = (int)nent;
+  const int nloc = k == 1 ? 6 : 4;
+  const int loc0 = k == 0 ? 0 : (k == 1 ? 4 * M.per_entity[0] : 4 * M.per_entity[0] + 6 * M.per_entity[1]);
+  h.N0 = N0;
+  h.N0p = (N0 + dev::CB - 1) / dev::CB * dev::CB;
+  h.c_w.resize(N0);
+  for (int e = 0; e < N0; ++e) h.c_w[e] = (int32_t)(M.off[k] + (int64_t)nd * e);
+  h.c_idx.assign(M.n_interface, -1);
+  for (int e = 0; e < N0; ++e) h.c_idx[h.c_w[e]] = e;
+  struct Con {
+    int32_t I, J, cell, ab;
+  };
+  std::vector<Con> con;
+  con.reserve((size_t)M.ncells * nloc * nloc);
+  for (int64_t c = 0; c < M.ncells; ++c) {
+    int32_t loc[6], ce[6];
+    for (int t = 0; t < nloc; ++t) {
+      loc[t] = loc0 + t * nd;
+      const int64_t gd = M.cell_dofs[c * M.nref + loc[t]];
+      ce[t] = h.c_idx[gd];
+      if (ce[t] < 0) throw Err(RIESZ_ERR_INTERNAL, "coarse DOF map inconsistent with the cell DOFs");
+    }
+    for (int a = 0; a < nloc; ++a)
+      for (int b = 0; b < nloc; ++b) con.push_back({ce[a], ce[b], (int32_t)c, loc[a] | (loc[b] << 16)});
+  }
+  std::sort(con.begin(), con.end(), [](const Con& x, const Con& y) {
+    return x.I != y.I ? x.I < y.I : (x.J != y.J ? x.J < y.J : x.cell < y.cell);
+  });
+  h.c_ptr.assign(N0 + 1, 0);
+  h.c_J.resize(con.size());
+  h.c_cell.resize(con.size());
+  h.c_ab.resize(con.size());
+  for (size_t e = 0; e < con.size(); ++e) {
+    ++h.c_ptr[con[e].I + 1];
+    h.c_J[e] = con[e].J;
+    h.c_cell[e] = con[e].cell;
+    h.c_ab[e] = con[e].ab;
+  }
+  for (int i = 0; i < N0; ++i) h.c_ptr[i + 1] += h.c_ptr[i];
+  h.coarse_on = true;
+}
+
 void build_plans(riesz_handle& h) {
   const MeshMaps& M = h.mesh;
   const int n = M.nref;
@@ -600,12 +673,32 @@ void op_patch_solves(riesz_handle& h, const double* r, int nrhs, cudaStream_t s)
   }
 }
 
+// Coarse corrections zc = A_0^{-1} R_0 r (W^k), when the handle has a coarse space.
+void op_coarse(riesz_handle& h, const double* r, int nrhs, cudaStream_t s) {
+  if (!h.coarse_on) return;
+  const int64_t N = h.N();
+  const unsigned grid = (unsigned)std::min<int64_t>((h.N0 + 7) / 8, 608);
+  launch(h, RIESZ_K_COARSE_APPLY, s, [&] {
+    dev::k_coarse_gather<<<nblk((int64_t)nrhs * h.N0p, 256), 256, 0, s>>>(h.N0, h.N0p, h.d_cw.p, r, N, nrhs,
+                                                                          h.d_r0.p);
+  });
+  for (int r0 = 0; r0 < nrhs; r0 += h.coarse_group) {
+    const int nr = std::min(h.coarse_group, nrhs - r0);
+    launch(h, RIESZ_K_COARSE_APPLY, s, [&] {
+      dev::k_coarse_apply<<<grid, 256, (size_t)nr * h.N0p * sizeof(float), s>>>(
+          h.N0, h.N0p, h.d_A0.p, h.d_r0.p + (int64_t)r0 * h.N0p, nr, h.d_zc.p + (int64_t)r0 * h.N0);
+    });
+  }
+}
+
 void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStream_t s) {
   const int64_t N = h.N();
   op_patch_solves(h, r, nrhs, s);
+  op_coarse(h, r, nrhs, s);
   launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
     dev::k_precond_gather<<<nblk(N, 256), 256, 0, s>>>(N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p,
-                                                      (int64_t)h.p_dofs.size(), h.d_dinv.p, r, z, nrhs);
+                                                      (int64_t)h.p_dofs.size(), h.d_dinv.p, r, z, nrhs,
+                                                      h.coarse_on ? h.d_cidx.p : nullptr, h.d_zc.p, h.N0);
   });
 }
 
@@ -614,10 +707,11 @@ void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* z
                     cudaStream_t s) {
   const int64_t N = h.N();
   op_patch_solves(h, r, nrhs, s);
+  op_coarse(h, r, nrhs, s);
   launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
     dev::k_precond_gather_dot<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(
         N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p, h.d_dinv.p, r, z, zold, h.d_part.p,
-        h.d_ticket.p, op, scal, (int64_t)h.p_dofs.size());
+        h.d_ticket.p, op, scal, (int64_t)h.p_dofs.size(), h.coarse_on ? h.d_cidx.p : nullptr, h.d_zc.p, h.N0);
   });
 }
 
@@ -633,6 +727,15 @@ void read_scal(riesz_handle& h, const double* scal, int nrhs, cudaStream_t s) {
   CK(cudaStreamSynchronize(s));
 }
 
+bool use_a32(const riesz_handle& h) {
+  return h.opts.apply_precision == RIESZ_PREC_FP32 && h.opts.apply_mode == RIESZ_APPLY_ELEMENT;
+}
+// Flexible (Polak-Ribiere) beta whenever an FP32 piece enters the preconditioner
+// or the search-direction product.
+bool use_flex(const riesz_handle& h) {
+  return h.opts.precond_precision == RIESZ_PREC_FP32 || use_a32(h) || h.coarse_on;
+}
+
 // PCG for nrhs right-hand sides in lockstep (Section 7.1): one apply and one
 // preconditioner launch serve all of them.  With apply_precision FP32 the
 // search-direction products use the FP32 element matrices and the residual is
@@ -646,8 +749,8 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
   const int64_t N = h.N();
   double* scal = h.d_scal.p;
   const int SS = dev::SCAL_STRIDE;
-  const bool a32 = h.opts.apply_precision == RIESZ_PREC_FP32 && h.opts.apply_mode == RIESZ_APPLY_ELEMENT;
-  const bool flex = h.opts.precond_precision == RIESZ_PREC_FP32 || a32;
+  const bool a32 = use_a32(h);
+  const bool flex = use_flex(h);
   double* r = h.d_r.p;
   double* z = h.d_z.p;
   double* zold = h.d_zold.p;
@@ -777,14 +880,9 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
 
 constexpr unsigned LOOP_KINDS = (1u << RIESZ_K_APPLY) | (1u << RIESZ_K_APPLY32) | (1u << RIESZ_K_GATHER) |
                                 (1u << RIESZ_K_PATCH_SOLVE) | (1u << RIESZ_K_PRECOND_GATHER) | (1u << RIESZ_K_DOT) |
-                                (1u << RIESZ_K_SCALAR) | (1u << RIESZ_K_UPDATE);
+                                (1u << RIESZ_K_SCALAR) | (1u << RIESZ_K_UPDATE) | (1u << RIESZ_K_COARSE_APPLY);
 
 bool profiling_loop(const riesz_handle& h) { return h.prof && (h.prof_mask & LOOP_KINDS) != 0u; }
-
-bool use_a32(const riesz_handle& h) {
-  return h.opts.apply_precision == RIESZ_PREC_FP32 && h.opts.apply_mode == RIESZ_APPLY_ELEMENT;
-}
-bool use_flex(const riesz_handle& h) { return h.opts.precond_precision == RIESZ_PREC_FP32 || use_a32(h); }
 
 // Ap = A p; (p, Ap) -> alpha; x += alpha p, r -= alpha Ap; (r, r) -> RR
 void iter_tail(riesz_handle& h, double* x, int nrhs, cudaStream_t s) {
@@ -1157,6 +1255,28 @@ size_t chol_pad(int ctas) {
   return (size_t)pad;
 }
 
+// A_0 from the geometric factors, then -A_0^{-1} in place by block sweeps.
+void coarse_setup(riesz_handle& h, cudaStream_t s) {
+  const int nbk = h.N0p / dev::CB;
+  const RefElement& R = *h.ref;
+  CK(cudaMemsetAsync(h.d_A0.p, 0, h.d_A0.bytes(), s));
+  launch(h, RIESZ_K_COARSE, s, [&] {
+    dev::k_coarse_assemble<<<nblk(h.N0p, 128), 128, 0, s>>>(h.N0, h.N0p, h.d_cptr.p, h.d_cJ.p, h.d_ccell.p, h.d_cab.p,
+                                                            h.C(), h.mesh.nref, R.Q, h.d_g.p, h.d_R.p, h.d_A0.p);
+  });
+  for (int k = 0; k < nbk; ++k) {
+    launch(h, RIESZ_K_COARSE, s, [&] { dev::k_gj_pivot<<<1, 256, 0, s>>>(h.N0p, k, h.d_A0.p, h.d_Dinv0.p); });
+    launch(h, RIESZ_K_COARSE, s,
+           [&] { dev::k_gj_row<<<nbk, 256, 0, s>>>(h.N0p, k, h.d_A0.p, h.d_Dinv0.p, h.d_Rb0.p); });
+    launch(h, RIESZ_K_COARSE, s,
+           [&] { dev::k_gj_update<<<nbk * (nbk + 1) / 2, 256, 0, s>>>(h.N0p, k, h.d_A0.p, h.d_Rb0.p); });
+    launch(h, RIESZ_K_COARSE, s,
+           [&] { dev::k_gj_finish<<<nbk, 256, 0, s>>>(h.N0p, k, h.d_A0.p, h.d_Dinv0.p, h.d_Rb0.p); });
+  }
+  if (nbk > 1)
+    launch(h, RIESZ_K_COARSE, s, [&] { dev::k_coarse_mirror<<<nbk * (nbk - 1) / 2, 256, 0, s>>>(h.N0p, h.d_A0.p); });
+}
+
 // Device setup from resident maps and vertex coordinates: a1 geometry,
 // element matrices, a6 interior diagonal, a8 patch assembly + Cholesky.
 void device_compute(riesz_handle& h, cudaStream_t s) {
@@ -1173,6 +1293,7 @@ void device_compute(riesz_handle& h, cudaStream_t s) {
     dev::k_geom<<<nblk(C, 128), 128, 0, s>>>(h.space, C, h.d_verts.p, h.d_cells.p, ref_edge_inverse(),
                                               h.opts.alpha, h.opts.beta, h.d_g.p, h.d_jac.p);
   });
+  if (h.coarse_on) coarse_setup(h, s);
   if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     launch(h, RIESZ_K_ELEM, s, [&] {
       dev::k_elem_matrices<<<(unsigned)C, 256, 0, s>>>(C, n, R.Q, h.d_g.p, h.d_R.p, h.d_Ae.p);
@@ -1343,6 +1464,22 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   h.d_pdioff.upload(h.p_dioff, s);
   h.d_pmoff.upload(h.p_moff, s);
   h.d_meta.upload(h.p_meta, s);
+  if (h.coarse_on) {
+    h.d_cw.upload(h.c_w, s);
+    h.d_cidx.upload(h.c_idx, s);
+    h.d_cptr.upload(h.c_ptr, s);
+    h.d_cJ.upload(h.c_J, s);
+    h.d_ccell.upload(h.c_cell, s);
+    h.d_cab.upload(h.c_ab, s);
+    h.d_A0.alloc((size_t)h.N0p * h.N0p);
+    h.d_Dinv0.alloc((size_t)dev::CB * dev::CB);
+    h.d_Rb0.alloc((size_t)dev::CB * h.N0p);
+    h.d_zc.alloc((size_t)nrhs * h.N0);
+    h.d_r0.alloc((size_t)nrhs * h.N0p);
+    const size_t per = (size_t)h.N0p * sizeof(float);
+    h.coarse_group = (int)std::max<size_t>(1, std::min<size_t>(8, (160 * 1024) / per));
+    raise_smem_limit(dev::k_coarse_apply, per * h.coarse_group);
+  }
   if (npatch) {
     h.d_L64.alloc((size_t)h.factor_entries);
     h.d_D64.alloc((size_t)h.dinv_entries);
@@ -1413,6 +1550,7 @@ void riesz_default_opts(riesz_opts* o) {
   o->apply_precision = RIESZ_PREC_FP64;
   o->loop = RIESZ_LOOP_GRAPH;
   o->autotune = 1;
+  o->coarse = 1;
 }
 
 const char* riesz_last_error(void) { return g_err.c_str(); }
@@ -1439,6 +1577,7 @@ int riesz_create(int space, int p, int64_t nverts, const double* verts, int64_t 
     need(h->opts.apply_precision == 0 || h->opts.apply_precision == 1, "bad apply_precision");
     need(h->opts.loop == RIESZ_LOOP_HOST || h->opts.loop == RIESZ_LOOP_GRAPH, "bad loop");
     need(h->opts.autotune == 0 || h->opts.autotune == 1, "bad autotune");
+    need(h->opts.coarse == 0 || h->opts.coarse == 1, "bad coarse");
     for (int64_t i = 0; i < nverts * 3; ++i)
       need(std::isfinite(verts[i]), "non-finite vertex coordinate", RIESZ_ERR_BAD_MESH);
     h->verts.assign(verts, verts + nverts * 3);
@@ -1453,6 +1592,7 @@ int riesz_create(int space, int p, int64_t nverts, const double* verts, int64_t 
       throw Err(RIESZ_ERR_BAD_MESH, e.what());
     }
     build_plans(*h);
+    plan_coarse(*h);
     h->setup_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = h.release();
   });
@@ -1690,6 +1830,7 @@ int riesz_tuning(const riesz_handle* h, int* out) {
     need(out != nullptr, "null argument");
     out[0] = h->chol_ctas;
     out[1] = h->chol_tuned;
+    out[2] = h->coarse_on ? h->N0 : 0;
   });
 }
 

@@ -20,7 +20,7 @@ APPLY_MATRIX_FREE, APPLY_ELEMENT = 0, 1
 LOOP_HOST, LOOP_GRAPH = 0, 1
 
 KINDS = ["geom", "elem", "diag", "assemble", "cholesky", "to_f32", "apply", "gather", "patch_solve",
-         "precond_gather", "dot", "scalar", "update", "load", "apply32"]
+         "precond_gather", "dot", "scalar", "update", "load", "apply32", "coarse", "coarse_apply"]
 
 ERRORS = {1: "INVALID_ARG", 2: "BAD_MESH", 3: "OOM", 4: "NOT_CONVERGED", 5: "NONFINITE", 6: "CUDA",
           7: "INTERNAL", 8: "NO_DEVICE"}
@@ -36,7 +36,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precond_precision", ctypes.c_int), ("apply_mode", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("nrhs_max", ctypes.c_int), ("alpha", ctypes.c_double),
                 ("beta", ctypes.c_double), ("apply_precision", ctypes.c_int), ("loop", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("coarse", ctypes.c_int)]
 
 
 _lib = None
@@ -215,9 +215,9 @@ class Riesz:
                 "chol_flops": out[6], "precond_bytes": out[7]}
 
     def tuning(self):
-        out = np.zeros(2, dtype=np.int32)
+        out = np.zeros(3, dtype=np.int32)
         _check(self.lib.riesz_tuning(self.h, _ptr(out)))
-        return {"cholesky_ctas_per_sm": int(out[0]), "candidates_timed": int(out[1])}
+        return {"cholesky_ctas_per_sm": int(out[0]), "candidates_timed": int(out[1]), "coarse_dofs": int(out[2])}
 
     # ----- device calls -----
     def setup_device(self, stream=None):

@@ -64,8 +64,8 @@ def test_graph_loop_launch_count():
     """The launch counter follows the passes of the graph loop: one control kernel
     per iteration more than the host loop, which also runs one speculative
     preconditioner step (patch sweeps + gather) after the last iteration."""
-    _, itg, _, _, lg = solve_with(rz.LOOP_GRAPH, "CG", 3, 4, 0.0, {}, 1)
-    _, ith, _, _, lh = solve_with(rz.LOOP_HOST, "CG", 3, 4, 0.0, {}, 1)
+    _, itg, _, _, lg = solve_with(rz.LOOP_GRAPH, "CG", 3, 4, 0.0, dict(coarse=0), 1)
+    _, ith, _, _, lh = solve_with(rz.LOOP_HOST, "CG", 3, 4, 0.0, dict(coarse=0), 1)
     assert itg[0] == ith[0] > 0
     assert lg == lh + int(itg[0]) - 2
 

@@ -23,7 +23,8 @@ def test_autotuned_factors_equal_untuned():
     plain = rz.Riesz("N1curl", 2, verts, cells, autotune=0)
     t = tuned.tuning()
     assert t["candidates_timed"] == 4 and t["cholesky_ctas_per_sm"] in (0, 2, 3, 4)
-    assert plain.tuning() == {"cholesky_ctas_per_sm": 0, "candidates_timed": 0}
+    tp = plain.tuning()
+    assert tp["cholesky_ctas_per_sm"] == 0 and tp["candidates_timed"] == 0
     r = torch.tensor(normal_vector(tuned.N, 3), device="cuda")
     assert torch.equal(precond_of(tuned, r), precond_of(plain, r))
     # the same for every residency after a geometry update

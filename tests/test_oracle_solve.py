@@ -302,3 +302,16 @@ def test_two_level_iterations_do_not_grow_with_refinement():
     assert its1[1] > 1.3 * its1[0]
     assert its2[1] <= 1.15 * its2[0] + 1
     assert its2[1] < its1[1]
+
+
+@pytest.mark.parametrize("space,p", [("CG", 3), ("N1curl", 3), ("RT", 2)])
+def test_coarse_matrix_by_quadrature_equals_restriction(space, p):
+    """A_0 from the lowest-order basis functions alone equals R_0 A R_0^T of the full assembly."""
+    ref = reference_element(space, p)
+    v, c = kuhn_mesh(2, 0.1, 8)
+    md = MeshDofs(v, c, ref)
+    A = asm.assemble(md, asm.element_matrices(ref, v, c))
+    W = asm.coarse_dofs(md)
+    A0 = asm.coarse_matrix(ref, md).toarray()
+    ref0 = A.tocsr()[W][:, W].toarray()
+    assert np.abs(A0 - ref0).max() <= 1e-12 * np.abs(ref0).max()
