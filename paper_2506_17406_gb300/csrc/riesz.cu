@@ -119,6 +119,8 @@ struct riesz_handle {
   int* h_ctl = nullptr;  // pinned [4]
   DBuf<int> d_flags;     // [0]: a bulk-copy wait of the patch sweeps timed out
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side_stream = nullptr;  // setup work that runs beside the patch factorisation
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_pfork = nullptr, ev_pjoin = nullptr;
   cudaGraphExec_t g_entry = nullptr, g_resume = nullptr;
   int g_nrhs = 0;
   int64_t g_pro_launches = 0, g_body_launches = 0;
@@ -184,6 +186,11 @@ struct riesz_handle {
     free_device();
     if (ev_scal) cudaEventDestroy(ev_scal);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (side_stream) cudaStreamDestroy(side_stream);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_pfork) cudaEventDestroy(ev_pfork);
+    if (ev_pjoin) cudaEventDestroy(ev_pjoin);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   }
 };
@@ -691,10 +698,24 @@ void op_coarse(riesz_handle& h, const double* r, int nrhs, cudaStream_t s) {
   }
 }
 
+// The coarse correction reads only r: it runs on the side stream beside the
+// patch sweeps and joins before the gather (a fork/join when captured).
+void coarse_fork(riesz_handle& h, const double* r, int nrhs, cudaStream_t s) {
+  if (!h.coarse_on) return;
+  CK(cudaEventRecord(h.ev_pfork, s));
+  CK(cudaStreamWaitEvent(h.side_stream, h.ev_pfork, 0));
+  op_coarse(h, r, nrhs, h.side_stream);
+  CK(cudaEventRecord(h.ev_pjoin, h.side_stream));
+}
+void coarse_join(riesz_handle& h, cudaStream_t s) {
+  if (h.coarse_on) CK(cudaStreamWaitEvent(s, h.ev_pjoin, 0));
+}
+
 void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStream_t s) {
   const int64_t N = h.N();
+  coarse_fork(h, r, nrhs, s);
   op_patch_solves(h, r, nrhs, s);
-  op_coarse(h, r, nrhs, s);
+  coarse_join(h, s);
   launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
     dev::k_precond_gather<<<nblk(N, 256), 256, 0, s>>>(N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p,
                                                       (int64_t)h.p_dofs.size(), h.d_dinv.p, r, z, nrhs,
@@ -706,8 +727,9 @@ void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStrea
 void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* zold, int op, double* scal, int nrhs,
                     cudaStream_t s) {
   const int64_t N = h.N();
+  coarse_fork(h, r, nrhs, s);
   op_patch_solves(h, r, nrhs, s);
-  op_coarse(h, r, nrhs, s);
+  coarse_join(h, s);
   launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
     dev::k_precond_gather_dot<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(
         N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p, h.d_dinv.p, r, z, zold, h.d_part.p,
@@ -1293,7 +1315,12 @@ void device_compute(riesz_handle& h, cudaStream_t s) {
     dev::k_geom<<<nblk(C, 128), 128, 0, s>>>(h.space, C, h.d_verts.p, h.d_cells.p, ref_edge_inverse(),
                                               h.opts.alpha, h.opts.beta, h.d_g.p, h.d_jac.p);
   });
-  if (h.coarse_on) coarse_setup(h, s);
+  if (h.coarse_on) {  // the coarse setup (FP32) needs only g: run it beside the FP64 patch factorisation
+    CK(cudaEventRecord(h.ev_fork, s));
+    CK(cudaStreamWaitEvent(h.side_stream, h.ev_fork, 0));
+    coarse_setup(h, h.side_stream);
+    CK(cudaEventRecord(h.ev_join, h.side_stream));
+  }
   if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     launch(h, RIESZ_K_ELEM, s, [&] {
       dev::k_elem_matrices<<<(unsigned)C, 256, 0, s>>>(C, n, R.Q, h.d_g.p, h.d_R.p, h.d_Ae.p);
@@ -1331,6 +1358,7 @@ void device_compute(riesz_handle& h, cudaStream_t s) {
       });
     }
   }
+  if (h.coarse_on) CK(cudaStreamWaitEvent(s, h.ev_join, 0));
   CK(cudaEventRecord(e1, s));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;
@@ -1432,6 +1460,11 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   CK(cudaMemsetAsync(h.d_flags.p, 0, 4 * sizeof(int), s));
   CK(cudaMallocHost((void**)&h.h_ctl, 4 * sizeof(int)));
   if (!h.cap_stream) CK(cudaStreamCreateWithFlags(&h.cap_stream, cudaStreamNonBlocking));
+  if (!h.side_stream) CK(cudaStreamCreateWithFlags(&h.side_stream, cudaStreamNonBlocking));
+  if (!h.ev_fork) CK(cudaEventCreateWithFlags(&h.ev_fork, cudaEventDisableTiming));
+  if (!h.ev_join) CK(cudaEventCreateWithFlags(&h.ev_join, cudaEventDisableTiming));
+  if (!h.ev_pfork) CK(cudaEventCreateWithFlags(&h.ev_pfork, cudaEventDisableTiming));
+  if (!h.ev_pjoin) CK(cudaEventCreateWithFlags(&h.ev_pjoin, cudaEventDisableTiming));
   h.d_part.alloc((size_t)2 * dev::RED_BLOCKS * nrhs);
   h.d_scal.alloc(16 * (size_t)nrhs);
   CK(cudaMallocHost((void**)&h.h_scal, (size_t)16 * nrhs * sizeof(double)));
