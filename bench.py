@@ -206,22 +206,36 @@ LOOP_KIND_NAMES = {"apply", "apply32", "gather", "patch_solve", "precond_gather"
                    "coarse_apply"}
 
 
-def kernel_source_hash():
-    """sha256 of the device code (every kernel lives in kernels.cuh)."""
+def kernel_source_hash(name):
+    """sha256 of one kernel's source text in kernels.cuh: from the line that declares `name(` to the
+    brace that closes its body (None if not found)."""
     import hashlib
-    return hashlib.sha256(open(os.path.join(ROOT, "paper_2506_17406_gb300", "csrc", "kernels.cuh"), "rb").read()
-                          ).hexdigest()
+    src = open(os.path.join(ROOT, "paper_2506_17406_gb300", "csrc", "kernels.cuh")).read()
+    i = src.find(" " + name + "(")
+    if i < 0:
+        return None
+    i = src.rfind("\n", 0, i) + 1
+    j = src.index("{", i)
+    depth, k = 0, j
+    while k < len(src):
+        depth += {"{": 1, "}": -1}.get(src[k], 0)
+        k += 1
+        if depth == 0:
+            break
+    return hashlib.sha256(src[i:k].encode()).hexdigest()
 
 
 def measured_traffic(workload, kernel):
-    """DRAM bytes per launch from the committed ncu summary, if the kernels have not changed since."""
+    """DRAM bytes per launch from the committed ncu summary, if that kernel's source has not changed
+    since the counters were taken."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     except Exception:
         return None
-    if t.get("kernels_sha256") != kernel_source_hash():
+    e = t.get("workloads", {}).get(workload, {}).get(kernel)
+    if not e or e.get("sha256") != kernel_source_hash(e.get("function", kernel)):
         return None
-    return t.get("workloads", {}).get(workload, {}).get(kernel)
+    return e.get("bytes")
 
 
 def patch_flops_bytes(s):
@@ -383,7 +397,8 @@ def run_p_sweep(args):
         for space in ("CG", "N1curl", "RT"):
             for p in range(1, 11):
                 row = {}
-                for name, kw in (("fp64", {}), ("mixed", dict(precond_precision=rz.PREC_FP32))):
+                for name, kw in (("one_level", dict(coarse=0)), ("two_level", dict(coarse=1)),
+                                 ("two_level_mixed", dict(coarse=1, precond_precision=rz.PREC_FP32))):
                     s = rz.Riesz(space, p, verts, cells, maxit=5000, **kw)
                     b = torch.tensor(normal_vector(s.N, 7), device="cuda")
                     x = torch.zeros_like(b)
@@ -394,7 +409,9 @@ def run_p_sweep(args):
                 table.setdefault("n=%d" % n, {}).setdefault(space, {})[str(p)] = row
     print(json.dumps({"metric": "PCG iterations to 1e-8 vs degree p", "data": "synthetic",
                       "config": {"meshes": "n^3 x 6 Kuhn tets, perturbed 0.1h", "rhs": "N(0,1) vector",
-                                 "preconditioner": "interior Jacobi + vertex-star patches (additive)"},
+                                 "preconditioner": "interior Jacobi + vertex-star patches (one_level), "
+                                                   "+ W^k coarse space (two_level), additive; two_level_mixed "
+                                                   "with FP32 patch sweeps"},
                       "iterations": table}), flush=True)
 
 
@@ -536,7 +553,7 @@ def main():
         achieved = byt / (dom_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
                 "frac": achieved / peak_hbm, "traffic": measured_traffic(args.workload, "k_patch_solve"),
-                "kernel": "k_patch_solve",
+                "kernel": "k_patch_sweep" if nrhs == 1 else "k_patch_solve_multi",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                 "algorithmic": "2 sweeps over the stored factor tiles and diagonal inverses + patch "
                                "vectors = %.3e B per launch" % byt}

@@ -116,8 +116,9 @@ typedef struct {
   /* 1 (default): add the lowest-order space W^k to the preconditioner (the
      first summand of the PAFW decomposition, Section 6.2; by Lemma 4.1 its
      basis is the first DOF of every vertex (H1), edge (H(curl)) or face
-     (H(div))): z += R_0^T A_0^{-1} R_0 r with A_0 = R_0 A R_0^T, additive and
-     unweighted.  A_0 is assembled densely and inverted in FP32 at device
+     (H(div))): z += w R_0^T A_0^{-1} R_0 r with A_0 = R_0 A R_0^T, additive
+     with weight w = 1/2 (every W^k function also lies in the vertex-star
+     spaces, so the unweighted sum over-corrects).  A_0 is assembled densely and inverted in FP32 at device
      setup (block Gauss-Jordan) and applied as a dense product, so it is used
      only when W^k has at most 6144 DOFs (otherwise the preconditioner stays
      one-level; riesz_tuning reports the coarse size).  Its FP32 rounding only

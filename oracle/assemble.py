@@ -196,12 +196,15 @@ def coarse_matrix(ref, md, alpha=1.0, beta=1.0):
 
 
 class TwoLevelPreconditioner:
-    """P^{-1} = D_II^{-1} (+) sum_V R_V^T A_V^{-1} R_V + R_0^T A_0^{-1} R_0: the one-level operator
+    """P^{-1} = D_II^{-1} (+) sum_V R_V^T A_V^{-1} R_V + w R_0^T A_0^{-1} R_0: the one-level operator
     plus an exact solve on W^k (the PAFW decomposition's coarse summand, Section 6.2), with
-    A_0 = R_0 A R_0^T the restriction of A to the lowest-order DOFs.  Additive and unweighted
-    (the paper combines the summands multiplicatively with eigenvalue-based weights)."""
+    A_0 = R_0 A R_0^T the restriction of A to the lowest-order DOFs.  Additive, with the coarse
+    correction weighted by w = 1/2 (the paper combines the summands multiplicatively with weights
+    from eigenvalue estimates; every W^k function also lies in the vertex-star spaces, so the plain
+    sum over-corrects, most for H(div))."""
 
-    def __init__(self, A, md, patches=None):
+    def __init__(self, A, md, patches=None, weight=0.5):
+        self.weight = weight
         self.one = Preconditioner(A, md, patches)
         self.N = self.one.N
         self.W = coarse_dofs(md)
@@ -216,7 +219,7 @@ class TwoLevelPreconditioner:
         return z
 
     def apply(self, r):
-        return self.one.apply(r) + self.coarse(r)
+        return self.one.apply(r) + self.weight * self.coarse(r)
 
     def dense(self):
         I = np.eye(self.N)

@@ -1169,11 +1169,11 @@ __global__ void k_coarse_gather(int N0, int N0p, const int32_t* __restrict__ cw,
   r0[t] = j < N0 ? (float)r[rh * N + cw[j]] : 0.f;
 }
 
-// zc[rh][i] = sum_j A0inv[i][j] r0[rh][j] with A0inv = -A (the swept, mirrored
-// matrix): r0 staged in shared memory, one warp per row, every matrix row read
-// once for all right-hand sides.
+// zc[rh][i] = w sum_j A0inv[i][j] r0[rh][j] with A0inv = -A (the swept, mirrored
+// matrix) and w the coarse weight: r0 staged in shared memory, one warp per
+// row, every matrix row read once for all right-hand sides.
 __global__ void __launch_bounds__(256) k_coarse_apply(int N0, int N0p, const float* __restrict__ A,
-                                                     const float* __restrict__ r0g, int nrhs,
+                                                     const float* __restrict__ r0g, int nrhs, double weight,
                                                      double* __restrict__ zc) {
   extern __shared__ __align__(16) float r0[];  // [nrhs][N0p]
   for (int t = threadIdx.x; t < nrhs * N0p / 4; t += blockDim.x)
@@ -1199,7 +1199,7 @@ __global__ void __launch_bounds__(256) k_coarse_apply(int N0, int N0p, const flo
       if (rh < nrhs) {
         float v = s[rh];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) zc[(int64_t)rh * N0 + i] = -(double)v;
+        if (lane == 0) zc[(int64_t)rh * N0 + i] = -weight * (double)v;
       }
     }
   }

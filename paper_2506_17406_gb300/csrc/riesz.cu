@@ -446,6 +446,9 @@ void plan_patch(riesz_handle& h, int64_t v, int64_t& foff, int64_t& dioff) {
 // W^k (Lemma 4.1: the first type-I DOF of each vertex, edge or face carries
 // the Whitney form) and the contribution lists of A_0 = R_0 A R_0^T.
 constexpr int COARSE_MAX = 6144;  // largest dense coarse problem (FP32 inverse: 151 MB)
+// Weight of the additive coarse correction: every W^k function also lies in the
+// vertex-star spaces, so the unweighted sum over-corrects (most for H(div)).
+constexpr double COARSE_WEIGHT = 0.5;
 
 void plan_coarse(riesz_handle& h) {
   const MeshMaps& M = h.mesh;
@@ -693,7 +696,7 @@ void op_coarse(riesz_handle& h, const double* r, int nrhs, cudaStream_t s) {
     const int nr = std::min(h.coarse_group, nrhs - r0);
     launch(h, RIESZ_K_COARSE_APPLY, s, [&] {
       dev::k_coarse_apply<<<grid, 256, (size_t)nr * h.N0p * sizeof(float), s>>>(
-          h.N0, h.N0p, h.d_A0.p, h.d_r0.p + (int64_t)r0 * h.N0p, nr, h.d_zc.p + (int64_t)r0 * h.N0);
+          h.N0, h.N0p, h.d_A0.p, h.d_r0.p + (int64_t)r0 * h.N0p, nr, COARSE_WEIGHT, h.d_zc.p + (int64_t)r0 * h.N0);
     });
   }
 }
