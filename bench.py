@@ -201,6 +201,7 @@ def combine_ranks(ms, n_local, dist=None, device=None):
     return float(tm.item()), float(tn.item())
 
 
+SIDE_STREAM_KINDS = {"coarse", "coarse_apply"}
 # kernel kinds launched inside the PCG loop (timing one per launch needs the host-driven loop)
 LOOP_KIND_NAMES = {"apply", "apply32", "gather", "patch_solve", "precond_gather", "dot", "scalar", "update",
                    "coarse_apply"}
@@ -500,7 +501,9 @@ def main():
     torch.cuda.synchronize()
     prof = s.profile_read()
     s.profile(False)
-    dom = max(prof, key=lambda k: prof[k][0])
+    # the coarse setup and the coarse correction run on a side stream beside k_cholesky and the patch
+    # sweeps: their event spans overlap other kernels, so they are not candidates for the dominant kernel
+    dom = max((k for k in prof if k not in SIDE_STREAM_KINDS), key=lambda k: prof[k][0])
     # timed region: only the dominant kernel is timed per launch; if it runs inside
     # the PCG loop, the loop is host-driven there (graph passes cannot be timed per launch)
     loop_driver = "host" if (dom in LOOP_KIND_NAMES or args.pcg_loop == "host") else "graph"
@@ -632,11 +635,12 @@ def main():
             "latency_p99_ms": float(np.percentile(per_step, 99)),
             "fp64_plain": plain,
             "speedup_vs_fp64_plain": (value / plain["value"]) if plain else None,
-            "setup_kernel_ms": sum(k_ms[k] for k in setup_kinds),
-            "solve_kernel_ms": sum(v for k, v in k_ms.items() if k not in setup_kinds),
+            "setup_kernel_ms": sum(k_ms[k] for k in setup_kinds if k not in SIDE_STREAM_KINDS),
+            "solve_kernel_ms": sum(v for k, v in k_ms.items() if k not in setup_kinds and k not in SIDE_STREAM_KINDS),
             "kernel_ms_per_step": {k: round(v, 4) for k, v in k_ms.items() if v > 0},
             "kernel_ms_per_step_source": "one untimed step before the timed region with every kernel bracketed "
-                                         "by CUDA events (host-driven PCG loop)",
+                                         "by CUDA events (host-driven PCG loop); coarse and coarse_apply run on "
+                                         "a side stream beside cholesky and patch_solve, so their spans overlap",
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk,
         }

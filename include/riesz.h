@@ -106,12 +106,14 @@ typedef struct {
      profiler records any kind launched inside the loop, riesz_solve uses the
      host-driven loop (CUDA events cannot time the passes of a graph loop). */
   int loop;
-  /* 1 (default): riesz_setup_device times the patch Cholesky with 2, 3, 4 and
-     the maximum number of resident CTAs per SM on the handle's own patches
-     and keeps the fastest (see riesz_tuning); done only when the mesh has
-     more patches than SMs and at most 24 per SM, where the residency decides
-     how evenly the patches spread over the SMs.  The factors are bitwise the
-     same for every choice.  0: maximum residency, no timing runs. */
+  /* 1 (default): riesz_setup_device times the patch Cholesky with one CTA per
+     patch and with a 2-CTA cluster per patch, each with 2, 3, 4 and the
+     maximum number of resident CTAs per SM, on the handle's own patches, and
+     keeps the fastest (see riesz_tuning); done only when the mesh has more
+     patches than SMs and at most 24 per SM, where these choices decide how
+     evenly the work spreads over the SMs.  The factors are bitwise the same
+     for every choice.  0: one CTA per patch, maximum residency, no timing.
+     2: 2-CTA clusters per patch, maximum residency, no timing. */
   int autotune;
   /* 1 (default): add the lowest-order space W^k to the preconditioner (the
      first summand of the PAFW decomposition, Section 6.2; by Lemma 4.1 its
@@ -282,7 +284,9 @@ int riesz_profile_read(riesz_handle* h, double* ms, int64_t* counts);
 
 /* Choices made at setup: out[0] = resident k_cholesky CTAs per SM picked by
    the autotuner (0: no limit), out[1] = candidates timed (0 when tuning was
-   skipped), out[2] = DOFs of the W^k coarse space (0 when it is off). */
+   skipped), out[2] = DOFs of the W^k coarse space (0 when it is off),
+   out[3] = CTAs per patch in the factorisation (1, or 2 for a 2-CTA cluster
+   that shares each patch). */
 int riesz_tuning(const riesz_handle* h, int* out);
 
 /* Timings (ms) and sizes of the last setup / solve:

@@ -367,17 +367,43 @@ __global__ void k_patch_assemble(const int32_t* __restrict__ pn, const int64_t* 
   }
 }
 
-// a8: batched FP64 Cholesky on the tiled layout, one CTA per patch.
+// a8: batched FP64 Cholesky on the tiled layout.  SPLIT = 1: one CTA per
+// patch.  SPLIT = 2: a cluster of two CTAs per patch (on two SMs) shares it,
+// so a few large patches no longer pile up on single SMs.
 // Right-looking by 32-wide block columns: factor the diagonal tile in shared
-// memory and invert it, L_IK = A_IK L_KK^{-T} for the panel, then
-// A_IJ -= L_IK L_JK^T on the trailing tiles.  A non-positive pivot sets
-// info[P] and is replaced by 1.
+// memory and invert it (cluster rank 0), L_IK = A_IK L_KK^{-T} for the panel,
+// then A_IJ -= L_IK L_JK^T on the trailing tiles; panel tiles and trailing
+// tile pairs are dealt round-robin to the CTAs of the patch, with a cluster
+// barrier (release/acquire) between the phases and L2 loads (ld.global.cg) for
+// tiles the other CTA wrote.  Every tile is computed by the same code in the
+// same order for either SPLIT, so the factors are bitwise the same.  A
+// non-positive pivot sets info[P] and is replaced by 1.
+template <int SPLIT>
+__device__ __forceinline__ double ldt(const double* p) {
+  if constexpr (SPLIT == 1)
+    return *p;
+  else
+    return __ldcg(p);
+}
+
+template <int SPLIT>
+__device__ __forceinline__ void patch_sync() {
+  if constexpr (SPLIT == 1) {
+    __syncthreads();
+  } else {
+    __syncthreads();
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  }
+}
+
+template <int SPLIT>
 __global__ void __launch_bounds__(NT, 6) k_cholesky(const int32_t* __restrict__ pn, const int64_t* __restrict__ pfoff,
                                                  const int64_t* __restrict__ pdoff_inv,
                                                  const int64_t* __restrict__ pmoff, const int32_t* __restrict__ meta,
                                                  double* __restrict__ Lall, double* __restrict__ Dall,
                                                  int* __restrict__ info) {
-  const int P = blockIdx.x;
+  const int P = blockIdx.x / SPLIT;
+  const int rank = blockIdx.x % SPLIT;  // cluster rank (clusters are consecutive CTAs along x)
   const int n = pn[P];
   const int nb = (n + 31) / 32;
   const int32_t* tix = meta + pmoff[P];
@@ -390,55 +416,63 @@ __global__ void __launch_bounds__(NT, 6) k_cholesky(const int32_t* __restrict__ 
   const int tid = threadIdx.x;
   for (int K = 0; K < nb; ++K) {
     double* AKK = A + (int64_t)tix[K * nb + K] * 1024;
-    for (int t = tid; t < 1024; t += NT) {
-      const int i = t >> 5, j = t & 31;
-      D[i][j] = (j <= i) ? AKK[t] : 0.0;
-      Di[i][j] = 0.0;
-    }
     if (tid == 0) {
       int m = 0;
       for (int I = K + 1; I < nb; ++I)
         if (tix[I * nb + K] >= 0) colI[m++] = I;
       ncol = m;
     }
-    __syncthreads();
-    if (tid < 32) {
-      const int lane = tid;
-      for (int j = 0; j < 32; ++j) {
-        if (lane == 0) {
-          double d = D[j][j];
-          if (!(d > 0.0)) {
-            if (info[P] == 0) info[P] = K * 32 + j + 1;
-            d = 1.0;
+    if (rank == 0) {
+      for (int t = tid; t < 1024; t += NT) {
+        const int i = t >> 5, j = t & 31;
+        D[i][j] = (j <= i) ? ldt<SPLIT>(AKK + t) : 0.0;
+        Di[i][j] = 0.0;
+      }
+      __syncthreads();
+      if (tid < 32) {
+        const int lane = tid;
+        for (int j = 0; j < 32; ++j) {
+          if (lane == 0) {
+            double d = D[j][j];
+            if (!(d > 0.0)) {
+              if (info[P] == 0) info[P] = K * 32 + j + 1;
+              d = 1.0;
+            }
+            D[j][j] = sqrt(d);
           }
-          D[j][j] = sqrt(d);
+          __syncwarp();
+          const double djj = D[j][j];
+          if (lane > j) D[lane][j] /= djj;
+          __syncwarp();
+          for (int k = j + 1; k < 32; ++k)
+            if (lane >= k) D[lane][k] -= D[lane][j] * D[k][j];
+          __syncwarp();
         }
-        __syncwarp();
-        const double djj = D[j][j];
-        if (lane > j) D[lane][j] /= djj;
-        __syncwarp();
-        for (int k = j + 1; k < 32; ++k)
-          if (lane >= k) D[lane][k] -= D[lane][j] * D[k][j];
-        __syncwarp();
+        // inverse of the lower-triangular block, column `lane` by forward substitution
+        for (int r = lane; r < 32; ++r) {
+          double s = (r == lane) ? 1.0 : 0.0;
+          for (int k = lane; k < r; ++k) s -= D[r][k] * Di[k][lane];
+          Di[r][lane] = s / D[r][r];
+        }
       }
-      // inverse of the lower-triangular block, column `lane` by forward substitution
-      for (int r = lane; r < 32; ++r) {
-        double s = (r == lane) ? 1.0 : 0.0;
-        for (int k = lane; k < r; ++k) s -= D[r][k] * Di[k][lane];
-        Di[r][lane] = s / D[r][r];
+      __syncthreads();
+      for (int t = tid; t < 1024; t += NT) {
+        const int i = t >> 5, j = t & 31;
+        AKK[t] = (j <= i) ? D[i][j] : 0.0;
+        Dinv[K * 1024 + t] = Di[i][j];
       }
+    }
+    if constexpr (SPLIT > 1) {
+      patch_sync<SPLIT>();  // the factored diagonal tile and its inverse are in global memory
+      if (rank != 0)
+        for (int t = tid; t < 1024; t += NT) Di[t >> 5][t & 31] = ldt<SPLIT>(Dinv + K * 1024 + t);
     }
     __syncthreads();
-    for (int t = tid; t < 1024; t += NT) {
-      const int i = t >> 5, j = t & 31;
-      AKK[t] = (j <= i) ? D[i][j] : 0.0;
-      Dinv[K * 1024 + t] = Di[i][j];
-    }
     const int m = ncol;
     // panel: L_IK = A_IK Linv_KK^T for the nonzero tiles of block column K
-    for (int a = 0; a < m; ++a) {
+    for (int a = rank; a < m; a += SPLIT) {
       double* AIK = A + (int64_t)tix[colI[a] * nb + K] * 1024;
-      for (int t = tid; t < 1024; t += NT) Ta[t >> 5][t & 31] = AIK[t];
+      for (int t = tid; t < 1024; t += NT) Ta[t >> 5][t & 31] = ldt<SPLIT>(AIK + t);
       __syncthreads();
       for (int t = tid; t < 1024; t += NT) {
         const int r = t >> 5, c = t & 31;
@@ -448,9 +482,10 @@ __global__ void __launch_bounds__(NT, 6) k_cholesky(const int32_t* __restrict__ 
       }
       __syncthreads();
     }
+    if constexpr (SPLIT > 1) patch_sync<SPLIT>();  // every panel tile is written
     // trailing update A_IJ -= L_IK L_JK^T over pairs of the column (I >= J)
     const int npair = m * (m + 1) / 2;
-    for (int tt = 0; tt < npair; ++tt) {
+    for (int tt = rank; tt < npair; tt += SPLIT) {
       int a = (int)((sqrt(8.0 * tt + 1.0) - 1.0) * 0.5);
       while ((a + 1) * (a + 2) / 2 <= tt) ++a;
       while (a * (a + 1) / 2 > tt) --a;
@@ -459,8 +494,8 @@ __global__ void __launch_bounds__(NT, 6) k_cholesky(const int32_t* __restrict__ 
       const double* LI = A + (int64_t)tix[I * nb + K] * 1024;
       const double* LJ = A + (int64_t)tix[J * nb + K] * 1024;
       for (int t = tid; t < 1024; t += NT) {
-        Ta[t >> 5][t & 31] = LI[t];
-        Tb[t >> 5][t & 31] = LJ[t];
+        Ta[t >> 5][t & 31] = ldt<SPLIT>(LI + t);
+        Tb[t >> 5][t & 31] = ldt<SPLIT>(LJ + t);
       }
       __syncthreads();
       double* AIJ = A + (int64_t)tix[I * nb + J] * 1024;
@@ -475,12 +510,13 @@ __global__ void __launch_bounds__(NT, 6) k_cholesky(const int32_t* __restrict__ 
         a10 = fma(x1, y0, a10);
         a11 = fma(x1, y1, a11);
       }
-      AIJ[r0 * 32 + c0] -= a00;
-      AIJ[r0 * 32 + c0 + 16] -= a01;
-      AIJ[(r0 + 16) * 32 + c0] -= a10;
-      AIJ[(r0 + 16) * 32 + c0 + 16] -= a11;
+      AIJ[r0 * 32 + c0] = ldt<SPLIT>(AIJ + r0 * 32 + c0) - a00;
+      AIJ[r0 * 32 + c0 + 16] = ldt<SPLIT>(AIJ + r0 * 32 + c0 + 16) - a01;
+      AIJ[(r0 + 16) * 32 + c0] = ldt<SPLIT>(AIJ + (r0 + 16) * 32 + c0) - a10;
+      AIJ[(r0 + 16) * 32 + c0 + 16] = ldt<SPLIT>(AIJ + (r0 + 16) * 32 + c0 + 16) - a11;
       __syncthreads();
     }
+    if constexpr (SPLIT > 1) patch_sync<SPLIT>();  // trailing tiles done before the next diagonal
   }
 }
 

@@ -106,6 +106,7 @@ struct riesz_handle {
   int multi_group = 8;  // right-hand sides per k_patch_solve_multi launch
   int chol_ctas = 0;    // resident k_cholesky CTAs per SM picked by the autotuner (0: no limit)
   int chol_tuned = 0;   // candidates the autotuner timed
+  int chol_split = 1;   // CTAs per patch in the factorisation (1, or a 2-CTA cluster)
   DBuf<int32_t> d_cells, d_cdofs, d_sc_pos, d_pn, d_pdofs, d_pz_pos, d_pb_cell, d_pb_ent, d_cgdofs, d_meta;
   DBuf<int64_t> d_sc_ptr, d_pdoff, d_pfoff, d_pdioff, d_pmoff, d_pz_ptr, d_pb_ptr, d_pb_off;
   DBuf<int> d_info;  // Cholesky status per patch
@@ -1268,7 +1269,7 @@ size_t chol_pad(int ctas) {
       CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
       CK(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
       cudaFuncAttributes fa;
-      CK(cudaFuncGetAttributes(&fa, dev::k_cholesky));
+      CK(cudaFuncGetAttributes(&fa, dev::k_cholesky<1>));
       it = dev_info.emplace(dev, std::array<long, 3>{smem_sm, reserved, (long)fa.sharedSizeBytes}).first;
     }
     di = it->second;
@@ -1276,8 +1277,37 @@ size_t chol_pad(int ctas) {
   const long per_cta = (di[0] / ctas) / 1024 * 1024;  // ctas fit, ctas + 1 do not
   const long pad = per_cta - di[2] - di[1];
   if (pad <= 0) return 0;
-  raise_smem_limit(dev::k_cholesky, (size_t)pad);
+  raise_smem_limit(dev::k_cholesky<1>, (size_t)pad);
+  raise_smem_limit(dev::k_cholesky<2>, (size_t)pad);
   return (size_t)pad;
+}
+
+// The patch factorisation with `split` CTAs per patch (1, or a 2-CTA cluster)
+// and `ctas` resident CTAs per SM (0: no limit).
+void launch_cholesky(riesz_handle& h, int split, int ctas, cudaStream_t s) {
+  const int npatch = (int)h.p_n.size();
+  const size_t pad = chol_pad(ctas);
+  if (split == 1) {
+    dev::k_cholesky<1><<<npatch, dev::NT, pad, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p,
+                                                    h.d_L64.p, h.d_D64.p, h.d_info.p);
+    KCHECK();
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * npatch));
+  cfg.blockDim = dim3(dev::NT);
+  cfg.dynamicSmemBytes = pad;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CK(cudaLaunchKernelEx(&cfg, dev::k_cholesky<2>, (const int32_t*)h.d_pn.p, (const int64_t*)h.d_pfoff.p,
+                        (const int64_t*)h.d_pdioff.p, (const int64_t*)h.d_pmoff.p, (const int32_t*)h.d_meta.p,
+                        h.d_L64.p, h.d_D64.p, h.d_info.p));
 }
 
 // A_0 from the geometric factors, then -A_0^{-1} in place by block sweeps.
@@ -1348,9 +1378,7 @@ void device_compute(riesz_handle& h, cudaStream_t s) {
                                                    h.d_R.p, h.d_Ae.p, h.d_L64.p);
     });
     launch(h, RIESZ_K_CHOLESKY, s, [&] {
-      dev::k_cholesky<<<npatch, dev::NT, chol_pad(h.chol_ctas), s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pdioff.p,
-                                                                     h.d_pmoff.p, h.d_meta.p, h.d_L64.p, h.d_D64.p,
-                                                                     h.d_info.p);
+      launch_cholesky(h, h.chol_split, h.chol_ctas, s);
     });
     if (h.opts.precond_precision == RIESZ_PREC_FP32) {
       launch(h, RIESZ_K_TO_F32, s, [&] {
@@ -1390,37 +1418,43 @@ void tune_cholesky(riesz_handle& h, cudaStream_t s) {
   int nsm = 0;
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h.device));
   h.chol_ctas = 0;
+  h.chol_split = h.opts.autotune == 2 ? 2 : 1;
   h.chol_tuned = 0;
+  if (h.opts.autotune == 2) {  // fixed: 2-CTA clusters, maximum residency
+    device_compute(h, s);
+    return;
+  }
   if (!h.opts.autotune || npatch <= nsm || npatch > 24 * nsm) return;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 0.f;
-  int best_c = 0;
-  for (int c : {0, 4, 3, 2}) {
-    CK(cudaMemsetAsync(h.d_info.p, 0, sizeof(int) * npatch, s));
-    dev::k_patch_assemble<<<npatch, 256, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pmoff.p, h.d_meta.p, h.d_pb_ptr.p,
-                                                 h.d_pb_cell.p, h.d_pb_off.p, h.d_pb_ent.p, h.C(), h.mesh.nref,
-                                                 h.ref->Q, h.d_g.p, h.d_R.p, h.d_Ae.p, h.d_L64.p);
-    KCHECK();
-    CK(cudaEventRecord(e0, s));
-    dev::k_cholesky<<<npatch, dev::NT, chol_pad(c), s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p,
-                                                         h.d_meta.p, h.d_L64.p, h.d_D64.p, h.d_info.p);
-    KCHECK();
-    CK(cudaEventRecord(e1, s));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    h.launches += 2;
-    ++h.chol_tuned;
-    if (c == 0 || ms < best) {
-      best = ms;
-      best_c = c;
+  int best_c = 0, best_split = 1;
+  for (int split : {1, 2})
+    for (int c : {0, 4, 3, 2}) {
+      CK(cudaMemsetAsync(h.d_info.p, 0, sizeof(int) * npatch, s));
+      dev::k_patch_assemble<<<npatch, 256, 0, s>>>(h.d_pn.p, h.d_pfoff.p, h.d_pmoff.p, h.d_meta.p, h.d_pb_ptr.p,
+                                                   h.d_pb_cell.p, h.d_pb_off.p, h.d_pb_ent.p, h.C(), h.mesh.nref,
+                                                   h.ref->Q, h.d_g.p, h.d_R.p, h.d_Ae.p, h.d_L64.p);
+      KCHECK();
+      CK(cudaEventRecord(e0, s));
+      launch_cholesky(h, split, c, s);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      h.launches += 2;
+      ++h.chol_tuned;
+      if (h.chol_tuned == 1 || ms < best) {
+        best = ms;
+        best_c = c;
+        best_split = split;
+      }
     }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h.chol_ctas = best_c;
+  h.chol_split = best_split;
   device_compute(h, s);  // factors (and their FP32 copies) with the chosen residency
 }
 
@@ -1531,7 +1565,9 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   }
   h.d_ticket.alloc(nrhs);
   CK(cudaMemsetAsync(h.d_ticket.p, 0, sizeof(unsigned) * nrhs, s));
-  CK(cudaFuncSetAttribute(dev::k_cholesky, cudaFuncAttributePreferredSharedMemoryCarveout,
+  CK(cudaFuncSetAttribute(dev::k_cholesky<1>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                          (int)cudaSharedmemCarveoutMaxShared));
+  CK(cudaFuncSetAttribute(dev::k_cholesky<2>, cudaFuncAttributePreferredSharedMemoryCarveout,
                           (int)cudaSharedmemCarveoutMaxShared));
   device_compute(h, s);
   tune_cholesky(h, s);
@@ -1612,7 +1648,7 @@ int riesz_create(int space, int p, int64_t nverts, const double* verts, int64_t 
          "alpha and beta must be positive and finite");
     need(h->opts.apply_precision == 0 || h->opts.apply_precision == 1, "bad apply_precision");
     need(h->opts.loop == RIESZ_LOOP_HOST || h->opts.loop == RIESZ_LOOP_GRAPH, "bad loop");
-    need(h->opts.autotune == 0 || h->opts.autotune == 1, "bad autotune");
+    need(h->opts.autotune >= 0 && h->opts.autotune <= 2, "bad autotune");
     need(h->opts.coarse == 0 || h->opts.coarse == 1, "bad coarse");
     for (int64_t i = 0; i < nverts * 3; ++i)
       need(std::isfinite(verts[i]), "non-finite vertex coordinate", RIESZ_ERR_BAD_MESH);
@@ -1867,6 +1903,7 @@ int riesz_tuning(const riesz_handle* h, int* out) {
     out[0] = h->chol_ctas;
     out[1] = h->chol_tuned;
     out[2] = h->coarse_on ? h->N0 : 0;
+    out[3] = h->chol_split;
   });
 }
 

@@ -215,9 +215,10 @@ class Riesz:
                 "chol_flops": out[6], "precond_bytes": out[7]}
 
     def tuning(self):
-        out = np.zeros(3, dtype=np.int32)
+        out = np.zeros(4, dtype=np.int32)
         _check(self.lib.riesz_tuning(self.h, _ptr(out)))
-        return {"cholesky_ctas_per_sm": int(out[0]), "candidates_timed": int(out[1]), "coarse_dofs": int(out[2])}
+        return {"cholesky_ctas_per_sm": int(out[0]), "candidates_timed": int(out[1]), "coarse_dofs": int(out[2]),
+                "cholesky_ctas_per_patch": int(out[3])}
 
     # ----- device calls -----
     def setup_device(self, stream=None):

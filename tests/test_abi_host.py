@@ -109,7 +109,7 @@ def test_device_calls_fail_loudly_without_device_state(lib):
 
 def test_option_validation(lib):
     v, c = kuhn_mesh(1)
-    for kw in [dict(loop=2), dict(loop=-1), dict(apply_precision=3), dict(alpha=0.0), dict(beta=-1.0),
+    for kw in [dict(loop=2), dict(loop=-1), dict(autotune=3), dict(coarse=2), dict(apply_precision=3), dict(alpha=0.0), dict(beta=-1.0),
                dict(nrhs_max=0), dict(rtol=0.0)]:
         with pytest.raises(rz.RieszError) as e:
             rz.Riesz("CG", 2, v, c, device=False, **kw)
