@@ -111,8 +111,11 @@ typedef struct {
      maximum number of resident CTAs per SM, on the handle's own patches, and
      keeps the fastest (see riesz_tuning); done only when the mesh has more
      patches than SMs and at most 24 per SM, where these choices decide how
-     evenly the work spreads over the SMs.  The factors are bitwise the same
-     for every choice.  0: one CTA per patch, maximum residency, no timing.
+     evenly the work spreads over the SMs.  The choice is kept per device,
+     space, degree and patch structure for the life of the process, so later
+     handles of the same shape reuse it without timing.  The factors are
+     bitwise the same for every choice.  0: one CTA per patch, maximum
+     residency, no timing.
      2: 2-CTA clusters per patch, maximum residency, no timing. */
   int autotune;
   /* 1 (default): add the lowest-order space W^k to the preconditioner (the
@@ -283,8 +286,8 @@ int riesz_profile(riesz_handle* h, int enable);
 int riesz_profile_read(riesz_handle* h, double* ms, int64_t* counts);
 
 /* Choices made at setup: out[0] = resident k_cholesky CTAs per SM picked by
-   the autotuner (0: no limit), out[1] = candidates timed (0 when tuning was
-   skipped), out[2] = DOFs of the W^k coarse space (0 when it is off),
+   the autotuner (0: no limit), out[1] = candidates timed for this shape (by
+   this handle or an earlier one; 0 when tuning does not apply), out[2] = DOFs of the W^k coarse space (0 when it is off),
    out[3] = CTAs per patch in the factorisation (1, or 2 for a 2-CTA cluster
    that shares each patch). */
 int riesz_tuning(const riesz_handle* h, int* out);

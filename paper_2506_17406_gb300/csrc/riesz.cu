@@ -1425,6 +1425,21 @@ void tune_cholesky(riesz_handle& h, cudaStream_t s) {
     return;
   }
   if (!h.opts.autotune || npatch <= nsm || npatch > 24 * nsm) return;
+  // a decision taken for the same space, degree and patch structure on this device is reused
+  static std::mutex mu;
+  static std::map<std::array<int64_t, 6>, std::array<int, 3>> done;  // split, ctas, candidates timed
+  const std::array<int64_t, 6> key{h.device, h.space, h.p, npatch, (int64_t)h.factor_entries, h.C()};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find(key);
+    if (it != done.end()) {
+      h.chol_split = it->second[0];
+      h.chol_ctas = it->second[1];
+      h.chol_tuned = it->second[2];
+      if (h.chol_split != 1 || h.chol_ctas != 0) device_compute(h, s);
+      return;
+    }
+  }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -1455,6 +1470,10 @@ void tune_cholesky(riesz_handle& h, cudaStream_t s) {
   cudaEventDestroy(e1);
   h.chol_ctas = best_c;
   h.chol_split = best_split;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    done[key] = {best_split, best_c, h.chol_tuned};
+  }
   device_compute(h, s);  // factors (and their FP32 copies) with the chosen residency
 }
 

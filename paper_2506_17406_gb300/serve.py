@@ -90,7 +90,8 @@ class Server:
 
     def _prepare(self, req):
         verts, cells = kuhn_mesh(req.n, req.amp, req.seed % 1000)
-        opts = dict(precond_precision=self.prec, rtol=req.rtol, maxit=5000)
+        # no setup-time autotuning: its timing runs would add latency and compete with the other requests
+        opts = dict(precond_precision=self.prec, rtol=req.rtol, maxit=5000, autotune=0)
         h = rz.Riesz(req.space, req.p, verts, cells, device=False, **opts)
         fp = estimate_footprint(h, opts)
         if fp > self.budget // 2:  # element matrices too large: matrix-free operator
