@@ -130,11 +130,19 @@ typedef struct {
      perturbs the preconditioner: solves run flexible PCG and stop on the FP64
      true residual.  0: one-level preconditioner. */
   int coarse;
+  /* 0 (default): pure Neumann (the paper's benchmarks).  1: homogeneous
+     Dirichlet conditions on the whole boundary (X_{p,D} of Eq. (2.8) with
+     Gamma_D the boundary): every DOF of a boundary vertex, edge or face is
+     fixed (riesz_dirichlet_map lists them).  The system becomes
+     [A_ff 0; 0 I]: riesz_apply gives y_f = A_ff x_f, y_d = x_d;
+     riesz_precond gives z_d = r_d and leaves the fixed DOFs out of every
+     patch and of W^k; riesz_load writes b_d = 0; a solve returns x_d = b_d. */
+  int dirichlet;
 } riesz_opts;
 
 /* Fill *o with the defaults: FP64 preconditioner, element-matrix apply,
    rtol 1e-8, maxit 1000, nrhs_max 1, alpha = beta = 1, FP64 apply,
-   graph-driven loop, autotune on, coarse space on. */
+   graph-driven loop, autotune on, coarse space on, Neumann boundary. */
 void riesz_default_opts(riesz_opts* o);
 
 /* ---- host-only calls (no GPU needed) ---------------------------------- */
@@ -157,9 +165,14 @@ int riesz_ref_info(const riesz_handle* h, int* info);
 /* cell_dofs: host [ncells][n_ref] global DOF of each local reference DOF. */
 int riesz_dof_map(const riesz_handle* h, int32_t* cell_dofs);
 
+/* mask: host [N]; 1 for the DOFs fixed by the Dirichlet condition
+   (opts.dirichlet), 0 otherwise. */
+int riesz_dirichlet_map(const riesz_handle* h, uint8_t* mask);
+
 /* offsets: host [nverts + 1]; dofs: host [offsets[nverts]] (query the size by
    passing dofs == NULL).  Patch of vertex v = dofs[offsets[v] .. offsets[v+1]),
-   increasing global DOF indices. */
+   increasing global DOF indices (without the Dirichlet DOFs when
+   opts.dirichlet is set). */
 int riesz_patch_map(const riesz_handle* h, int64_t* offsets, int32_t* dofs);
 
 /* Tabulate the reference basis of (space, p) at npts points of the reference

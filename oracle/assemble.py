@@ -195,6 +195,55 @@ def coarse_matrix(ref, md, alpha=1.0, beta=1.0):
     return scipy.sparse.coo_matrix((Ae.ravel(), (rows, cols)), shape=(len(W), len(W))).tocsr()
 
 
+def dirichlet_dofs(md):
+    """DOFs fixed by a homogeneous Dirichlet condition on the whole boundary (X_{p,D} of Eq. (2.8)):
+    every DOF of a vertex, edge or face of a boundary face (a face of exactly one cell)."""
+    _, cnt = np.unique(md.cell_faces.ravel(), return_counts=True)
+    bfaces = np.nonzero(cnt == 1)[0]
+    nv_d, ne_d, nf_d, _ = md.per_entity
+    off_v, off_e, off_f = md._offsets
+    tri = md.faces[bfaces]
+    bverts = np.unique(tri.ravel())
+    pairs = np.unique(np.concatenate([tri[:, [0, 1]], tri[:, [0, 2]], tri[:, [1, 2]]]), axis=0)
+    eidx = {tuple(e): i for i, e in enumerate(md.edges.tolist())}
+    bedges = np.array([eidx[tuple(e)] for e in pairs.tolist()], dtype=np.int64)
+    d = [off_v + nv_d * v + m for v in bverts for m in range(nv_d)]
+    d += [off_e + ne_d * e + m for e in bedges for m in range(ne_d)]
+    d += [off_f + nf_d * f + m for f in bfaces for m in range(nf_d)]
+    return np.array(sorted(d), dtype=np.int64)
+
+
+def constrained(A, D):
+    """[A_ff 0; 0 I]: the Dirichlet DOFs D decoupled, with unit diagonal."""
+    A = A.tocsr()
+    keep = np.ones(A.shape[0])
+    keep[D] = 0.0
+    K = scipy.sparse.diags(keep)
+    I_D = scipy.sparse.diags(1.0 - keep)
+    return (K @ A @ K + I_D).tocsr()
+
+
+class DirichletPreconditioner:
+    """The one- or two-level preconditioner of the free DOFs (patches and W^k without the fixed DOFs)
+    with the identity on the fixed DOFs."""
+
+    def __init__(self, A, md, D, two_level=True, weight=0.5):
+        self.D = np.asarray(D)
+        fixed = np.zeros(md.ndofs, dtype=bool)
+        fixed[self.D] = True
+        patches = [p[~fixed[p]] for p in md.patches()]
+        Ac = constrained(A, self.D)
+        if two_level:
+            self.P = TwoLevelPreconditioner(Ac, md, patches, weight, W=coarse_dofs(md)[~fixed[coarse_dofs(md)]])
+        else:
+            self.P = Preconditioner(Ac, md, patches)
+
+    def apply(self, r):
+        z = self.P.apply(r)
+        z[self.D] = r[self.D]
+        return z
+
+
 class TwoLevelPreconditioner:
     """P^{-1} = D_II^{-1} (+) sum_V R_V^T A_V^{-1} R_V + w R_0^T A_0^{-1} R_0: the one-level operator
     plus an exact solve on W^k (the PAFW decomposition's coarse summand, Section 6.2), with
@@ -203,11 +252,11 @@ class TwoLevelPreconditioner:
     from eigenvalue estimates; every W^k function also lies in the vertex-star spaces, so the plain
     sum over-corrects, most for H(div))."""
 
-    def __init__(self, A, md, patches=None, weight=0.5):
+    def __init__(self, A, md, patches=None, weight=0.5, W=None):
         self.weight = weight
         self.one = Preconditioner(A, md, patches)
         self.N = self.one.N
-        self.W = coarse_dofs(md)
+        self.W = coarse_dofs(md) if W is None else np.asarray(W)
         A = A.tocsr()
         self.A0 = A[self.W][:, self.W].toarray()
         self.fac0 = scipy.linalg.cho_factor(self.A0, lower=True)

@@ -162,16 +162,19 @@ __device__ __forceinline__ void apply_rows2(const T* __restrict__ A, const T* __
 
 // T = double: the FP64 operator; T = float: FP32 copy of the element matrices
 // and FP32 arithmetic (inner applies of the mixed-precision solver).
+// With a Dirichlet mask the masked (interface) entries of x are read as zero, so
+// the free rows see only the free unknowns.
 template <typename T, int RB>
 __global__ void k_apply_elem(int64_t C, int n, int nif, const T* __restrict__ Ae, const int32_t* __restrict__ cdofs,
                              const double* __restrict__ x, double* __restrict__ y, double* __restrict__ Ycell,
-                             int nrhs, int64_t N) {
+                             int nrhs, int64_t N, const uint8_t* __restrict__ dmask) {
   extern __shared__ unsigned char smraw_apply[];
   T* xs = reinterpret_cast<T*>(smraw_apply);  // [nrhs][n]
   const int64_t c = blockIdx.x;
   for (int t = threadIdx.x; t < n * nrhs; t += blockDim.x) {
     const int r = t / n, j = t % n;
-    xs[t] = (T)x[r * N + cdofs[(int64_t)j * C + c]];
+    const int64_t dof = cdofs[(int64_t)j * C + c];
+    xs[t] = (dmask && j < nif && dmask[dof]) ? (T)0 : (T)x[r * N + dof];
   }
   __syncthreads();
   const T* A = Ae + c * (int64_t)n * n;
@@ -226,7 +229,8 @@ constexpr int TC = 32;
 constexpr int RB = 8;  // rows per thread per pass
 __global__ void k_apply_mf(int64_t C, int n, int nif, int Q, const double* __restrict__ R,
                            const double* __restrict__ g, const int32_t* __restrict__ cdofs,
-                           const double* __restrict__ x, double* __restrict__ y, double* __restrict__ Ycell, int64_t N) {
+                           const double* __restrict__ x, double* __restrict__ y, double* __restrict__ Ycell, int64_t N,
+                           const uint8_t* __restrict__ dmask) {
   extern __shared__ double sm[];
   double* Xs = sm;               // [n][TC]
   double* Gs = sm + n * TC;      // [Q][TC]
@@ -236,7 +240,12 @@ __global__ void k_apply_mf(int64_t C, int n, int nif, int Q, const double* __res
   for (int t = threadIdx.x; t < n * TC; t += blockDim.x) {
     const int j = t / TC, cc = t % TC;
     const int64_t c = c0 + cc;
-    Xs[t] = (c < C) ? x[r * N + cdofs[(int64_t)j * C + c]] : 0.0;
+    if (c < C) {
+      const int64_t dof = cdofs[(int64_t)j * C + c];
+      Xs[t] = (dmask && j < nif && dmask[dof]) ? 0.0 : x[r * N + dof];
+    } else {
+      Xs[t] = 0.0;
+    }
   }
   for (int t = threadIdx.x; t < Q * TC; t += blockDim.x) {
     const int q = t / TC, cc = t % TC;
@@ -284,15 +293,22 @@ __global__ void k_apply_mf(int64_t C, int n, int nif, int Q, const double* __res
 
 // Deterministic scatter of the interface rows: y[d] = sum over the cells that
 // share DOF d, in a fixed order (CSR built on the host).
+// With a Dirichlet mask (homogeneous Dirichlet DOFs) the masked rows carry the
+// identity: y_d = xd_d (0 when xd is null).
 __global__ void k_gather_iface(int64_t nifd, const int64_t* __restrict__ ptr, const int32_t* __restrict__ pos,
                                const double* __restrict__ Ycell, int64_t ystride, double* __restrict__ y,
-                               int64_t N, int nrhs) {
+                               int64_t N, int nrhs, const uint8_t* __restrict__ dmask,
+                               const double* __restrict__ xd) {
   const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (d >= nifd) return;
   const int64_t b = ptr[d], e = ptr[d + 1];
+  const bool fixed = dmask && dmask[d];
   for (int r = 0; r < nrhs; ++r) {
     double s = 0.0;
-    for (int64_t k = b; k < e; ++k) s += Ycell[r * ystride + pos[k]];
+    if (fixed)
+      s = xd ? xd[r * N + d] : 0.0;
+    else
+      for (int64_t k = b; k < e; ++k) s += Ycell[r * ystride + pos[k]];
     y[r * N + d] = s;
   }
 }
@@ -982,12 +998,15 @@ __global__ void __launch_bounds__(NT) k_patch_solve_multi(
 __global__ void k_precond_gather(int64_t N, int64_t nifd, const int64_t* __restrict__ ptr,
                                  const int32_t* __restrict__ pos, const double* __restrict__ zpatch, int64_t zstride,
                                  const double* __restrict__ dinv, const double* __restrict__ r, double* __restrict__ z,
-                                 int nrhs, const int32_t* __restrict__ cidx, const double* __restrict__ zc, int64_t n0) {
+                                 int nrhs, const int32_t* __restrict__ cidx, const double* __restrict__ zc, int64_t n0,
+                                 const uint8_t* __restrict__ dmask) {
   const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (d >= N) return;
   for (int rh = 0; rh < nrhs; ++rh) {
     double s;
-    if (d < nifd) {
+    if (d < nifd && dmask && dmask[d]) {
+      s = r[rh * N + d];  // identity block of a Dirichlet DOF
+    } else if (d < nifd) {
       s = 0.0;
       for (int64_t k = ptr[d]; k < ptr[d + 1]; ++k) s += zpatch[rh * zstride + pos[k]];
       if (cidx && cidx[d] >= 0) s += zc[rh * n0 + cidx[d]];
@@ -1451,7 +1470,8 @@ __global__ void __launch_bounds__(NT) k_precond_gather_dot(int64_t N, int64_t ni
                                                           unsigned* __restrict__ ticket, int op,
                                                           double* __restrict__ scal, int64_t zstride,
                                                           const int32_t* __restrict__ cidx,
-                                                          const double* __restrict__ zc, int64_t n0) {
+                                                          const double* __restrict__ zc, int64_t n0,
+                                                          const uint8_t* __restrict__ dmask) {
   const int64_t o = blockIdx.y * N;
   zpatch += blockIdx.y * zstride;
   r += o;
@@ -1460,7 +1480,9 @@ __global__ void __launch_bounds__(NT) k_precond_gather_dot(int64_t N, int64_t ni
   double v0 = 0.0, v1 = 0.0;
   for (int64_t d = blockIdx.x * (int64_t)NT + threadIdx.x; d < N; d += (int64_t)RED_BLOCKS * NT) {
     double zi;
-    if (d < nifd) {
+    if (d < nifd && dmask && dmask[d]) {
+      zi = r[d];  // identity block of a Dirichlet DOF
+    } else if (d < nifd) {
       zi = 0.0;
       for (int64_t k = ptr[d]; k < ptr[d + 1]; ++k) zi += zpatch[pos[k]];
       if (cidx && cidx[d] >= 0) zi += zc[blockIdx.y * n0 + cidx[d]];

@@ -92,6 +92,10 @@ struct riesz_handle {
   int device = 0;
   DBuf<double> d_verts, d_g, d_jac, d_R, d_Ae, d_Ycell, d_dinv, d_L64, d_D64, d_zpatch, d_X;
   DBuf<float> d_L32, d_D32, d_Ae32;
+  // homogeneous Dirichlet DOFs (all DOFs of boundary entities), flag per interface DOF
+  std::vector<uint8_t> dir_mask;
+  DBuf<uint8_t> d_dmask;
+  const uint8_t* dmask() const { return opts.dirichlet ? d_dmask.p : nullptr; }
   // W^k coarse space: coarse DOF -> global DOF, interface DOF -> coarse index,
   // per coarse row the (J, cell, local a | b << 16) contributions of A_0
   bool coarse_on = false;
@@ -145,7 +149,7 @@ struct riesz_handle {
            d_pb_cell.bytes() + d_pb_ent.bytes() + d_cgdofs.bytes() + d_sc_ptr.bytes() + d_pdoff.bytes() +
            d_pfoff.bytes() + d_pdioff.bytes() + d_pmoff.bytes() + d_meta.bytes() + d_pz_ptr.bytes() + d_pb_ptr.bytes() + d_pb_off.bytes() + d_r.bytes() + d_z.bytes() +
            d_zold.bytes() + d_p.bytes() + d_Ap.bytes() + d_part.bytes() + d_scal.bytes() + d_tmp.bytes() + d_xh.bytes() +
-           d_xw.bytes() + d_ctl.bytes() + d_flags.bytes() + d_cw.bytes() + d_cidx.bytes() + d_cJ.bytes() +
+           d_xw.bytes() + d_ctl.bytes() + d_flags.bytes() + d_dmask.bytes() + d_cw.bytes() + d_cidx.bytes() + d_cJ.bytes() +
            d_ccell.bytes() + d_cab.bytes() + d_cptr.bytes() + d_A0.bytes() + d_Dinv0.bytes() + d_Rb0.bytes() +
            d_r0.bytes() + d_zc.bytes();
   }
@@ -162,6 +166,7 @@ struct riesz_handle {
       b->free();
     d_ctl.free();
     d_flags.free();
+    d_dmask.free();
     for (auto* b : {&d_cw, &d_cidx, &d_cJ, &d_ccell, &d_cab}) b->free();
     d_cptr.free();
     d_A0.free();
@@ -444,6 +449,55 @@ void plan_patch(riesz_handle& h, int64_t v, int64_t& foff, int64_t& dioff) {
   h.pb_ptr.push_back((int64_t)h.pb_cell.size());
 }
 
+// Homogeneous Dirichlet conditions on the whole boundary (X_{p,D} with
+// Gamma_D the boundary, Eq. (2.8)): a function has zero trace there exactly
+// when every DOF of every boundary vertex, edge and face is zero.  Marks those
+// DOFs and removes them from the vertex-star patches.
+void plan_dirichlet(riesz_handle& h) {
+  MeshMaps& M = h.mesh;
+  h.dir_mask.assign(M.n_interface, 0);
+  std::vector<int> cnt(M.nfaces, 0);
+  for (int64_t c = 0; c < M.ncells; ++c)
+    for (int f = 0; f < 4; ++f) ++cnt[M.cell_faces[c * 4 + f]];
+  auto edge_index = [&](int32_t a, int32_t b) -> int64_t {  // edges: sorted pairs, lexicographic
+    int64_t lo = 0, hi = M.nedges;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      const int32_t* e = &M.edges[mid * 2];
+      if (e[0] < a || (e[0] == a && e[1] < b))
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    if (lo >= M.nedges || M.edges[lo * 2] != a || M.edges[lo * 2 + 1] != b)
+      throw Err(RIESZ_ERR_INTERNAL, "boundary edge not found");
+    return lo;
+  };
+  auto mark = [&](int k, int64_t ent) {
+    const int nd = M.per_entity[k];
+    for (int m = 0; m < nd; ++m) h.dir_mask[M.off[k] + (int64_t)nd * ent + m] = 1;
+  };
+  for (int64_t f = 0; f < M.nfaces; ++f) {
+    if (cnt[f] != 1) continue;
+    const int32_t* v = &M.faces[f * 3];
+    mark(2, f);
+    for (int a = 0; a < 3; ++a) mark(0, v[a]);
+    mark(1, edge_index(v[0], v[1]));
+    mark(1, edge_index(v[0], v[2]));
+    mark(1, edge_index(v[1], v[2]));
+  }
+  std::vector<int64_t> ptr(M.nverts + 1, 0);
+  std::vector<int32_t> dofs;
+  dofs.reserve(M.patch_dofs.size());
+  for (int64_t v = 0; v < M.nverts; ++v) {
+    for (int64_t k = M.patch_ptr[v]; k < M.patch_ptr[v + 1]; ++k)
+      if (!h.dir_mask[M.patch_dofs[k]]) dofs.push_back(M.patch_dofs[k]);
+    ptr[v + 1] = (int64_t)dofs.size();
+  }
+  M.patch_ptr.swap(ptr);
+  M.patch_dofs.swap(dofs);
+}
+
 // W^k (Lemma 4.1: the first type-I DOF of each vertex, edge or face carries
 // the Whitney form) and the contribution lists of A_0 = R_0 A R_0^T.
 constexpr int COARSE_MAX = 6144;  // largest dense coarse problem (FP32 inverse: 151 MB)
@@ -457,14 +511,20 @@ void plan_coarse(riesz_handle& h) {
   const int nd = M.per_entity[k];
   const int64_t nent = k == 0 ? M.nverts : (k == 1 ? M.nedges : M.nfaces);
   h.coarse_on = false;
-  if (!h.opts.coarse || nd == 0 || nent > COARSE_MAX) return;
-  const int N0 = (int)nent;
+  if (!h.opts.coarse || nd == 0) return;
+  // Dirichlet entities carry no coarse DOF
+  std::vector<int32_t> w;
+  for (int64_t e = 0; e < nent; ++e) {
+    const int64_t gd = M.off[k] + (int64_t)nd * e;
+    if (h.dir_mask.empty() || !h.dir_mask[gd]) w.push_back((int32_t)gd);
+  }
+  if (w.empty() || (int64_t)w.size() > COARSE_MAX) return;
+  const int N0 = (int)w.size();
   const int nloc = k == 1 ? 6 : 4;
   const int loc0 = k == 0 ? 0 : (k == 1 ? 4 * M.per_entity[0] : 4 * M.per_entity[0] + 6 * M.per_entity[1]);
   h.N0 = N0;
   h.N0p = (N0 + dev::CB - 1) / dev::CB * dev::CB;
-  h.c_w.resize(N0);
-  for (int e = 0; e < N0; ++e) h.c_w[e] = (int32_t)(M.off[k] + (int64_t)nd * e);
+  h.c_w.swap(w);
   h.c_idx.assign(M.n_interface, -1);
   for (int e = 0; e < N0; ++e) h.c_idx[h.c_w[e]] = e;
   struct Con {
@@ -478,10 +538,12 @@ void plan_coarse(riesz_handle& h) {
       loc[t] = loc0 + t * nd;
       const int64_t gd = M.cell_dofs[c * M.nref + loc[t]];
       ce[t] = h.c_idx[gd];
-      if (ce[t] < 0) throw Err(RIESZ_ERR_INTERNAL, "coarse DOF map inconsistent with the cell DOFs");
+      if (ce[t] < 0 && (h.dir_mask.empty() || !h.dir_mask[gd]))
+        throw Err(RIESZ_ERR_INTERNAL, "coarse DOF map inconsistent with the cell DOFs");
     }
     for (int a = 0; a < nloc; ++a)
-      for (int b = 0; b < nloc; ++b) con.push_back({ce[a], ce[b], (int32_t)c, loc[a] | (loc[b] << 16)});
+      for (int b = 0; b < nloc; ++b)
+        if (ce[a] >= 0 && ce[b] >= 0) con.push_back({ce[a], ce[b], (int32_t)c, loc[a] | (loc[b] << 16)});
   }
   std::sort(con.begin(), con.end(), [](const Con& x, const Con& y) {
     return x.I != y.I ? x.I < y.I : (x.J != y.J ? x.J < y.J : x.cell < y.cell);
@@ -604,20 +666,20 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
       launch(h, RIESZ_K_APPLY32, s, [&] {
         if (nrhs == 1)
           dev::k_apply_elem<float, 1><<<(unsigned)C, nt, sm, s>>>(C, n, h.nif, h.d_Ae32.p, h.d_cdofs.p, x, y,
-                                                                  h.d_Ycell.p, nrhs, N);
+                                                                  h.d_Ycell.p, nrhs, N, h.dmask());
         else
           dev::k_apply_elem<float, 8><<<(unsigned)C, nt, sm, s>>>(C, n, h.nif, h.d_Ae32.p, h.d_cdofs.p, x, y,
-                                                                  h.d_Ycell.p, nrhs, N);
+                                                                  h.d_Ycell.p, nrhs, N, h.dmask());
       });
     } else {
       const size_t sm = (size_t)n * nrhs * sizeof(double);
       launch(h, RIESZ_K_APPLY, s, [&] {
         if (nrhs == 1)
           dev::k_apply_elem<double, 1><<<(unsigned)C, nt, sm, s>>>(C, n, h.nif, h.d_Ae.p, h.d_cdofs.p, x, y,
-                                                                   h.d_Ycell.p, nrhs, N);
+                                                                   h.d_Ycell.p, nrhs, N, h.dmask());
         else
           dev::k_apply_elem<double, 8><<<(unsigned)C, nt, sm, s>>>(C, n, h.nif, h.d_Ae.p, h.d_cdofs.p, x, y,
-                                                                   h.d_Ycell.p, nrhs, N);
+                                                                   h.d_Ycell.p, nrhs, N, h.dmask());
       });
     }
   } else {
@@ -625,13 +687,13 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
     dim3 grid(nblk(C, dev::TC), nrhs);
     launch(h, RIESZ_K_APPLY, s, [&] {
       dev::k_apply_mf<<<grid, dev::NT, sm, s>>>(C, n, h.nif, h.ref->Q, h.d_R.p, h.d_g.p, h.d_cdofs.p, x, y, h.d_Ycell.p,
-                                               N);
+                                               N, h.dmask());
     });
   }
   const int64_t nI = h.mesh.n_interface;
   launch(h, RIESZ_K_GATHER, s, [&] {
     dev::k_gather_iface<<<nblk(nI, 256), 256, 0, s>>>(nI, h.d_sc_ptr.p, h.d_sc_pos.p, h.d_Ycell.p, (int64_t)h.nif * C, y,
-                                                     N, nrhs);
+                                                     N, nrhs, h.dmask(), x);
   });
 }
 
@@ -723,7 +785,7 @@ void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStrea
   launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
     dev::k_precond_gather<<<nblk(N, 256), 256, 0, s>>>(N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p,
                                                       (int64_t)h.p_dofs.size(), h.d_dinv.p, r, z, nrhs,
-                                                      h.coarse_on ? h.d_cidx.p : nullptr, h.d_zc.p, h.N0);
+                                                      h.coarse_on ? h.d_cidx.p : nullptr, h.d_zc.p, h.N0, h.dmask());
   });
 }
 
@@ -737,7 +799,8 @@ void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* z
   launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
     dev::k_precond_gather_dot<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(
         N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p, h.d_dinv.p, r, z, zold, h.d_part.p,
-        h.d_ticket.p, op, scal, (int64_t)h.p_dofs.size(), h.coarse_on ? h.d_cidx.p : nullptr, h.d_zc.p, h.N0);
+        h.d_ticket.p, op, scal, (int64_t)h.p_dofs.size(), h.coarse_on ? h.d_cidx.p : nullptr, h.d_zc.p, h.N0,
+        h.dmask());
   });
 }
 
@@ -1553,6 +1616,7 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   h.d_pdioff.upload(h.p_dioff, s);
   h.d_pmoff.upload(h.p_moff, s);
   h.d_meta.upload(h.p_meta, s);
+  if (h.opts.dirichlet) h.d_dmask.upload(h.dir_mask, s);
   if (h.coarse_on) {
     h.d_cw.upload(h.c_w, s);
     h.d_cidx.upload(h.c_idx, s);
@@ -1642,6 +1706,7 @@ void riesz_default_opts(riesz_opts* o) {
   o->loop = RIESZ_LOOP_GRAPH;
   o->autotune = 1;
   o->coarse = 1;
+  o->dirichlet = 0;
 }
 
 const char* riesz_last_error(void) { return g_err.c_str(); }
@@ -1669,6 +1734,7 @@ int riesz_create(int space, int p, int64_t nverts, const double* verts, int64_t 
     need(h->opts.loop == RIESZ_LOOP_HOST || h->opts.loop == RIESZ_LOOP_GRAPH, "bad loop");
     need(h->opts.autotune >= 0 && h->opts.autotune <= 2, "bad autotune");
     need(h->opts.coarse == 0 || h->opts.coarse == 1, "bad coarse");
+    need(h->opts.dirichlet == 0 || h->opts.dirichlet == 1, "bad dirichlet");
     for (int64_t i = 0; i < nverts * 3; ++i)
       need(std::isfinite(verts[i]), "non-finite vertex coordinate", RIESZ_ERR_BAD_MESH);
     h->verts.assign(verts, verts + nverts * 3);
@@ -1682,6 +1748,7 @@ int riesz_create(int space, int p, int64_t nverts, const double* verts, int64_t 
     } catch (const std::exception& e) {
       throw Err(RIESZ_ERR_BAD_MESH, e.what());
     }
+    if (h->opts.dirichlet) plan_dirichlet(*h);
     build_plans(*h);
     plan_coarse(*h);
     h->setup_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1789,20 +1856,20 @@ int riesz_apply_noalloc(riesz_handle* h, const double* x, double* y, void* strea
       const int nt = std::min(1024, (rows + 31) / 32 * 32);
       launch(*h, RIESZ_K_APPLY, s, [&] {
         dev::k_apply_elem<double, 1><<<(unsigned)C, nt, (size_t)n * sizeof(double), s>>>(C, n, h->nif, h->d_Ae.p, h->d_cdofs.p,
-                                                                              x, y, ycell, 1, N);
+                                                                              x, y, ycell, 1, N, h->dmask());
       });
     } else {
       const size_t sm = ((size_t)n + h->ref->Q) * dev::TC * sizeof(double);
       dim3 grid(nblk(C, dev::TC), 1);
       launch(*h, RIESZ_K_APPLY, s, [&] {
         dev::k_apply_mf<<<grid, dev::NT, sm, s>>>(C, n, h->nif, h->ref->Q, h->d_R.p, h->d_g.p, h->d_cdofs.p, x, y,
-                                                 ycell, N);
+                                                 ycell, N, h->dmask());
       });
     }
     const int64_t nI = h->mesh.n_interface;
     launch(*h, RIESZ_K_GATHER, s, [&] {
       dev::k_gather_iface<<<nblk(nI, 256), 256, 0, s>>>(nI, h->d_sc_ptr.p, h->d_sc_pos.p, ycell, (int64_t)h->nif * C,
-                                                       y, N, 1);
+                                                       y, N, 1, h->dmask(), x);
     });
   });
 }
@@ -1900,7 +1967,7 @@ int riesz_load(riesz_handle* h, const double* fcg, double* b, void* stream) {
     const int64_t nI = h->mesh.n_interface;
     launch(*h, RIESZ_K_GATHER, s, [&] {
       dev::k_gather_iface<<<nblk(nI, 256), 256, 0, s>>>(nI, h->d_sc_ptr.p, h->d_sc_pos.p, h->d_Ycell.p,
-                                                       (int64_t)h->nif * C, b, N, 1);
+                                                       (int64_t)h->nif * C, b, N, 1, h->dmask(), nullptr);
     });
   });
 }
@@ -1912,6 +1979,15 @@ int riesz_update_geometry(riesz_handle* h, const double* verts, void* stream) {
     cudaStream_t s = S(stream);
     CK(cudaMemcpyAsync(h->d_verts.p, verts, h->d_verts.bytes(), cudaMemcpyDeviceToDevice, s));
     device_compute(*h, s);
+  });
+}
+
+int riesz_dirichlet_map(const riesz_handle* h, uint8_t* mask) {
+  return guarded([&] {
+    need(h != nullptr && mask != nullptr, "null argument");
+    const int64_t N = h->mesh.ndofs;
+    std::fill(mask, mask + N, (uint8_t)0);
+    if (h->opts.dirichlet) std::copy(h->dir_mask.begin(), h->dir_mask.end(), mask);
   });
 }
 

@@ -36,7 +36,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precond_precision", ctypes.c_int), ("apply_mode", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("nrhs_max", ctypes.c_int), ("alpha", ctypes.c_double),
                 ("beta", ctypes.c_double), ("apply_precision", ctypes.c_int), ("loop", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("coarse", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("coarse", ctypes.c_int), ("dirichlet", ctypes.c_int)]
 
 
 _lib = None
@@ -66,6 +66,7 @@ _SIGS = {
     "riesz_load": (_I, [_P, _P, _P, _P]),
     "riesz_stats": (_I, [_P, _P]),
     "riesz_tuning": (_I, [_P, _P]),
+    "riesz_dirichlet_map": (_I, [_P, _P]),
     "riesz_update_geometry": (_I, [_P, _P, _P]),
     "riesz_profile": (_I, [_P, _I]),
     "riesz_profile_read": (_I, [_P, _P, _P]),
@@ -213,6 +214,12 @@ class Riesz:
         return {"setup_host_ms": out[0], "setup_device_ms": out[1], "device_bytes": out[2],
                 "factor_bytes": out[3], "last_iters": int(out[4]), "launches": int(out[5]),
                 "chol_flops": out[6], "precond_bytes": out[7]}
+
+    def dirichlet_map(self):
+        """Flags (uint8, [N]) of the DOFs fixed by the Dirichlet condition."""
+        out = np.zeros(self.N, dtype=np.uint8)
+        _check(self.lib.riesz_dirichlet_map(self.h, _ptr(out)))
+        return out
 
     def tuning(self):
         out = np.zeros(4, dtype=np.int32)

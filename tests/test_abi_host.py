@@ -126,3 +126,25 @@ def test_batch_without_device_state(lib):
     rc = lib.riesz_solve_batch(ctypes.cast(hs, ctypes.c_void_p), 1, ctypes.cast(ptrs, ctypes.c_void_p),
                                ctypes.cast(ptrs, ctypes.c_void_p), None, None, None, None, None)
     assert rc in (6, 8)  # no CUDA device here (6) or no device state (8); nothing launched
+
+
+@pytest.mark.parametrize("space,p", [("CG", 3), ("N1curl", 2), ("RT", 3)])
+def test_dirichlet_map_bit_exact(lib, space, p):
+    """The library's fixed DOFs equal the oracle's, and the patches leave them out."""
+    from oracle import assemble as asm
+    from oracle.mesh import MeshDofs
+    from oracle.refelem import reference_element
+    v, c = kuhn_mesh(3, 0.1, 2)
+    s = rz.Riesz(space, p, v, c, device=False, dirichlet=1)
+    md = MeshDofs(v, c, reference_element(space, p))
+    D = asm.dirichlet_dofs(md)
+    mask = s.dirichlet_map()
+    assert np.array_equal(np.nonzero(mask)[0], D)
+    off, dofs = s.patch_map()
+    fixed = np.zeros(s.N, dtype=bool)
+    fixed[D] = True
+    for vv in range(len(off) - 1):
+        exp = md.patches_of([vv])[0]
+        assert np.array_equal(dofs[off[vv]:off[vv + 1]], exp[~fixed[exp]])
+    s0 = rz.Riesz(space, p, v, c, device=False)
+    assert s0.dirichlet_map().sum() == 0

@@ -315,3 +315,81 @@ def test_coarse_matrix_by_quadrature_equals_restriction(space, p):
     A0 = asm.coarse_matrix(ref, md).toarray()
     ref0 = A.tocsr()[W][:, W].toarray()
     assert np.abs(A0 - ref0).max() <= 1e-12 * np.abs(ref0).max()
+
+
+@pytest.mark.parametrize("space,p", [("CG", 2), ("CG", 3), ("N1curl", 2), ("N1curl", 3), ("RT", 2), ("RT", 3)])
+def test_dirichlet_dofs_count_and_place(space, p):
+    """The fixed DOFs of a whole-boundary Dirichlet condition: their number is the closed form
+    nv (6n^2+2) + ne 18 n^2 + nf 12 n^2 of the cube's surface triangulation (6n^2+2 vertices, 18n^2
+    edges, 12n^2 triangles), and every one belongs to an entity whose vertices lie on one cube face."""
+    ref = reference_element(space, p)
+    for n in (1, 2):
+        v, c = kuhn_mesh(n, 0.0, 1)
+        md = MeshDofs(v, c, ref)
+        D = asm.dirichlet_dofs(md)
+        nv, ne, nf, _ = md.per_entity
+        assert len(D) == nv * (6 * n * n + 2) + ne * 18 * n * n + nf * 12 * n * n
+        for d in D:
+            X = md.verts[md.vertices_of_dof(int(d))]
+            assert any(np.all(np.isclose(X[:, a], b)) for a in range(3) for b in (0.0, 1.0))
+
+
+def _bubble():
+    def u(x):
+        return (x[:, 0] * (1 - x[:, 0]) * x[:, 1] * (1 - x[:, 1]) * x[:, 2] * (1 - x[:, 2]))[:, None]
+
+    def grad(x):
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        bx, by, bz = X * (1 - X), Y * (1 - Y), Z * (1 - Z)
+        return np.stack([(1 - 2 * X) * by * bz, bx * (1 - 2 * Y) * bz, bx * by * (1 - 2 * Z)], 1)
+    return u, grad
+
+
+@pytest.mark.parametrize("space", ["CG", "N1curl"])
+def test_dirichlet_manufactured_solution(space):
+    """u with zero trace lying in V_h (CG_6: the cubic bubble xyz(1-x)(1-y)(1-z); Ned1_6: its gradient,
+    whose tangential trace vanishes and whose curl is zero) is reproduced by the constrained system."""
+    p = 6
+    ref = reference_element(space, p)
+    v, c = kuhn_mesh(1, 0.0, 1)
+    md = MeshDofs(v, c, ref)
+    A = asm.assemble(md, asm.element_matrices(ref, v, c))
+    D = asm.dirichlet_dofs(md)
+    ub, gb = _bubble()
+    if space == "CG":
+        f, df = ub, gb
+    else:
+        f, df = gb, (lambda x: np.zeros((x.shape[0], 3)))
+    b = asm.load_function(ref, md, f, df)
+    b[D] = 0.0
+    x = asm.direct_solve(asm.constrained(A, D), b)
+    assert np.abs(x[D]).max() == 0.0
+    X, _ = quadrature(3, 3)
+    xq, val = asm.evaluate(ref, md, x, X)
+    ue = f(xq.reshape(-1, 3)).reshape(val.shape)
+    assert np.abs(val - ue).max() <= 1e-10 * np.abs(ue).max()
+
+
+def test_dirichlet_solution_has_zero_trace():
+    """For a random right-hand side the constrained solution vanishes at points of boundary faces."""
+    ref = reference_element("CG", 3)
+    v, c = kuhn_mesh(2, 0.1, 3)
+    md = MeshDofs(v, c, ref)
+    A = asm.assemble(md, asm.element_matrices(ref, v, c))
+    D = asm.dirichlet_dofs(md)
+    b = normal_vector(md.ndofs, 4)
+    b[D] = 0.0
+    x = asm.direct_solve(asm.constrained(A, D), b)
+    # points on the reference faces, mapped in every cell; keep those on the cube's surface
+    Vr = REF_VERTS[3]
+    rng = np.random.default_rng(0)
+    pts = []
+    for f in [(0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)]:
+        lam = rng.dirichlet(np.ones(3), 5)
+        pts.append(lam @ Vr[list(f)])
+    xq, val = asm.evaluate(ref, md, x, np.concatenate(pts))
+    xq = xq.reshape(-1, 3)
+    on = np.any(np.isclose(xq, 0.0) | np.isclose(xq, 1.0), axis=1)
+    assert on.sum() > 20
+    assert np.abs(val.reshape(-1)[on]).max() <= 1e-12 * np.abs(x).max()
+    assert np.abs(val.reshape(-1)[~on]).max() > 1e-3 * np.abs(x).max()
