@@ -800,6 +800,248 @@ __global__ void __launch_bounds__(SWEEP_NT) k_patch_sweep(const int32_t* __restr
 }
 
 
+// a7 for up to 8 right-hand sides in FP32 on the bulk-copy pipeline: the
+// tiles are read once for all of them.  Patch vectors are interleaved in
+// shared memory, y[(i * 8) + k] for DOF i and right-hand side k, so the eight
+// values a tile row or column needs are two 16-byte broadcasts.  The forward
+// sweep streams the transposed copies of the tiles (LT, DT: entry (c, r) of a
+// tile holds L[r][c]) so that lane r reads column entries without bank
+// conflicts; the backward sweep streams the tiles as stored.  Same tile order,
+// ring, producer and bounded waits as k_patch_sweep.
+template <int S>
+__global__ void __launch_bounds__(SWEEP_NT) k_patch_sweep8(const int32_t* __restrict__ pn,
+                                                           const int64_t* __restrict__ pdoff,
+                                                           const int64_t* __restrict__ pfoff,
+                                                           const int64_t* __restrict__ pdoff_inv,
+                                                           const int64_t* __restrict__ pmoff,
+                                                           const int32_t* __restrict__ meta,
+                                                           const int32_t* __restrict__ pdofs,
+                                                           const float* __restrict__ Lall,
+                                                           const float* __restrict__ Dall,
+                                                           const float* __restrict__ LTall,
+                                                           const float* __restrict__ DTall,
+                                                           const double* __restrict__ r, double* __restrict__ zpatch,
+                                                           int64_t N, int64_t zstride, int nr,
+                                                           int* __restrict__ err) {
+  static_assert(S >= SWEEP_WARPS, "a slot must not be reused before every consumer warp has moved past it");
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float* ring = reinterpret_cast<float*>(smraw);  // [S][1024]
+  float* y = ring + S * 1024;                      // [nb*32][8]
+  __shared__ __align__(8) uint64_t full[S], empty[S];
+  __shared__ __align__(16) float red[SWEEP_WARPS][8][32];
+  __shared__ __align__(16) float tv[32][8];
+  __shared__ int failed;
+  const int P = blockIdx.x;
+  const int n = pn[P];
+  const int nb = (n + 31) / 32;
+  const int32_t* tix = meta + pmoff[P];
+  const int32_t* tcol = tix + nb * nb;
+  const float* L = Lall + pfoff[P];
+  const float* Dv = Dall + pdoff_inv[P];
+  const float* LT = LTall + pfoff[P];
+  const float* DT = DTall + pdoff_inv[P];
+  const int32_t* dofs = pdofs + pdoff[P];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    for (int k = 0; k < S; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 1);
+    }
+    failed = 0;
+    mbar_fence_init();
+  }
+  for (int t = tid; t < nb * 32 * 8; t += SWEEP_NT) {
+    const int i = t >> 3, k = t & 7;
+    y[t] = (i < n && k < nr) ? (float)r[k * N + dofs[i]] : 0.f;
+  }
+  __syncthreads();
+  const int ntile = tix[(nb - 1) * nb + (nb - 1)] + 1;
+  const int ktot = 2 * ntile;
+  constexpr uint32_t TB = 1024 * sizeof(float);
+  int bad = 0;
+  if (warp == SWEEP_WARPS) {  // producer
+    if (lane == 0) {
+      int k = 0;
+      auto issue = [&](const float* src) {
+        const int slot = k % S;
+        if (k >= S && !mbar_wait(&empty[slot], ((k / S) - 1) & 1, err)) bad = 1;
+        mbar_expect_tx(&full[slot], TB);
+        bulk_g2s(ring + slot * 1024, src, TB, &full[slot]);
+        ++k;
+      };
+      int rs = 0;
+      for (int I = 0; I < nb; ++I) {  // forward: transposed copies
+        const int td = tix[I * nb + I];
+        for (int t = rs; t < td; ++t) issue(LT + (int64_t)t * 1024);
+        issue(DT + (int64_t)I * 1024);
+        rs = td + 1;
+      }
+      for (int I = nb - 1; I >= 0; --I) {  // backward: tiles as stored
+        const int td = tix[I * nb + I];
+        const int r0 = I ? tix[(I - 1) * nb + (I - 1)] + 1 : 0;
+        issue(Dv + (int64_t)I * 1024);
+        for (int t = r0; t < td; ++t) issue(L + (int64_t)t * 1024);
+      }
+      if (bad || *err)
+        for (int j = (ktot > S ? ktot - S : 0); j < ktot; ++j) mbar_wait(&full[j % S], (j / S) & 1, err);
+    }
+    __syncwarp();
+  } else {  // consumers
+    int k = 0;
+    int rs = 0;
+    for (int I = 0; I < nb; ++I) {  // forward: t_I = b_I - sum_J L_IJ y_J, y_I = Dinv_I t_I
+      const int td = tix[I * nb + I];
+      const int m = td - rs;
+      float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int j = warp; j < m; j += SWEEP_WARPS) {
+        const int kk = k + j, slot = kk % S;
+        if (!mbar_wait(&full[slot], (kk / S) & 1, err)) bad = 1;
+        const float* AT = ring + slot * 1024;  // AT[c][r] = L[r][c]
+        const float* yJ = y + tcol[rs + j] * 32 * 8;
+#pragma unroll 4
+        for (int c = 0; c < 32; ++c) {
+          const float a = AT[c * 32 + lane];
+          const float4 y0 = *reinterpret_cast<const float4*>(yJ + c * 8);
+          const float4 y1 = *reinterpret_cast<const float4*>(yJ + c * 8 + 4);
+          acc[0] = fmaf(a, y0.x, acc[0]);
+          acc[1] = fmaf(a, y0.y, acc[1]);
+          acc[2] = fmaf(a, y0.z, acc[2]);
+          acc[3] = fmaf(a, y0.w, acc[3]);
+          acc[4] = fmaf(a, y1.x, acc[4]);
+          acc[5] = fmaf(a, y1.y, acc[5]);
+          acc[6] = fmaf(a, y1.z, acc[6]);
+          acc[7] = fmaf(a, y1.w, acc[7]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) red[warp][q][lane] = acc[q];
+      consumer_sync();
+      if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float t = y[(I * 32 + lane) * 8 + q];
+          for (int w = 0; w < SWEEP_WARPS; ++w) t -= red[w][q][lane];
+          tv[lane][q] = t;
+        }
+        __syncwarp();
+        const int kk = k + m, slot = kk % S;
+        if (!mbar_wait(&full[slot], (kk / S) & 1, err)) bad = 1;
+        const float* DTt = ring + slot * 1024;  // DTt[c][r] = Dinv[r][c]
+        float s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+        for (int c = 0; c < 32; ++c) {
+          const float a = DTt[c * 32 + lane];
+          const float4 t0 = *reinterpret_cast<const float4*>(&tv[c][0]);
+          const float4 t1 = *reinterpret_cast<const float4*>(&tv[c][4]);
+          s8[0] = fmaf(a, t0.x, s8[0]);
+          s8[1] = fmaf(a, t0.y, s8[1]);
+          s8[2] = fmaf(a, t0.z, s8[2]);
+          s8[3] = fmaf(a, t0.w, s8[3]);
+          s8[4] = fmaf(a, t1.x, s8[4]);
+          s8[5] = fmaf(a, t1.y, s8[5]);
+          s8[6] = fmaf(a, t1.z, s8[6]);
+          s8[7] = fmaf(a, t1.w, s8[7]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        float* yI = y + (I * 32 + lane) * 8;
+        *reinterpret_cast<float4*>(yI) = make_float4(s8[0], s8[1], s8[2], s8[3]);
+        *reinterpret_cast<float4*>(yI + 4) = make_float4(s8[4], s8[5], s8[6], s8[7]);
+      }
+      consumer_sync();
+      k += m + 1;
+      rs = td + 1;
+    }
+    for (int I = nb - 1; I >= 0; --I) {  // backward: x_I = Dinv_I^T y_I, y_J -= L_IJ^T x_I
+      const int td = tix[I * nb + I];
+      const int r0 = I ? tix[(I - 1) * nb + (I - 1)] + 1 : 0;
+      const int m = td - r0;
+      if (warp == 0) {
+        const int slot = k % S;
+        if (!mbar_wait(&full[slot], (k / S) & 1, err)) bad = 1;
+        const float* D = ring + slot * 1024;  // D[r][c]
+        const float* yI = y + I * 32 * 8;
+        float s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+          const float a = D[rr * 32 + lane];
+          const float4 t0 = *reinterpret_cast<const float4*>(yI + rr * 8);
+          const float4 t1 = *reinterpret_cast<const float4*>(yI + rr * 8 + 4);
+          s8[0] = fmaf(a, t0.x, s8[0]);
+          s8[1] = fmaf(a, t0.y, s8[1]);
+          s8[2] = fmaf(a, t0.z, s8[2]);
+          s8[3] = fmaf(a, t0.w, s8[3]);
+          s8[4] = fmaf(a, t1.x, s8[4]);
+          s8[5] = fmaf(a, t1.y, s8[5]);
+          s8[6] = fmaf(a, t1.z, s8[6]);
+          s8[7] = fmaf(a, t1.w, s8[7]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        float* yo = y + (I * 32 + lane) * 8;
+        *reinterpret_cast<float4*>(yo) = make_float4(s8[0], s8[1], s8[2], s8[3]);
+        *reinterpret_cast<float4*>(yo + 4) = make_float4(s8[4], s8[5], s8[6], s8[7]);
+      }
+      consumer_sync();
+      const float* xI = y + I * 32 * 8;
+      for (int j = warp; j < m; j += SWEEP_WARPS) {
+        const int kk = k + 1 + j, slot = kk % S;
+        if (!mbar_wait(&full[slot], (kk / S) & 1, err)) bad = 1;
+        const float* A = ring + slot * 1024;  // A[r][c]
+        float s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+          const float a = A[rr * 32 + lane];
+          const float4 t0 = *reinterpret_cast<const float4*>(xI + rr * 8);
+          const float4 t1 = *reinterpret_cast<const float4*>(xI + rr * 8 + 4);
+          s8[0] = fmaf(a, t0.x, s8[0]);
+          s8[1] = fmaf(a, t0.y, s8[1]);
+          s8[2] = fmaf(a, t0.z, s8[2]);
+          s8[3] = fmaf(a, t0.w, s8[3]);
+          s8[4] = fmaf(a, t1.x, s8[4]);
+          s8[5] = fmaf(a, t1.y, s8[5]);
+          s8[6] = fmaf(a, t1.z, s8[6]);
+          s8[7] = fmaf(a, t1.w, s8[7]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        float* yJ = y + (tcol[r0 + j] * 32 + lane) * 8;
+        float4 v0 = *reinterpret_cast<float4*>(yJ), v1 = *reinterpret_cast<float4*>(yJ + 4);
+        v0.x -= s8[0];
+        v0.y -= s8[1];
+        v0.z -= s8[2];
+        v0.w -= s8[3];
+        v1.x -= s8[4];
+        v1.y -= s8[5];
+        v1.z -= s8[6];
+        v1.w -= s8[7];
+        *reinterpret_cast<float4*>(yJ) = v0;
+        *reinterpret_cast<float4*>(yJ + 4) = v1;
+      }
+      consumer_sync();
+      k += m + 1;
+    }
+  }
+  if (bad) atomicExch(&failed, 1);
+  __syncthreads();
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  for (int t = tid; t < n * nr; t += SWEEP_NT) {
+    const int q = t / n, i = t % n;
+    zpatch[q * zstride + pdoff[P] + i] = failed ? nan : (double)y[i * 8 + q];
+  }
+}
+
+// FP64 factor tiles to FP32, each 32x32 tile transposed (the forward sweep of k_patch_sweep8)
+__global__ void k_to_f32_tiles_t(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e >> 10;
+    const int w = (int)(e & 1023), rr = w >> 5, c = w & 31;
+    b[(t << 10) + c * 32 + rr] = (float)a[e];
+  }
+}
+
 // a7 for several right-hand sides at once (2..8): every factor tile is loaded
 // once and applied to all of them, so the HBM traffic per right-hand side
 // drops by their number.  Same tiling and thread mapping as k_patch_solve.

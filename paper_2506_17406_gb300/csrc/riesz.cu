@@ -92,6 +92,7 @@ struct riesz_handle {
   int device = 0;
   DBuf<double> d_verts, d_g, d_jac, d_R, d_Ae, d_Ycell, d_dinv, d_L64, d_D64, d_zpatch, d_X;
   DBuf<float> d_L32, d_D32, d_Ae32;
+  DBuf<float> d_L32T, d_D32T;  // tile-transposed FP32 factors (forward sweep of several right-hand sides)
   // homogeneous Dirichlet DOFs (all DOFs of boundary entities), flag per interface DOF
   std::vector<uint8_t> dir_mask;
   DBuf<uint8_t> d_dmask;
@@ -144,7 +145,7 @@ struct riesz_handle {
   int64_t C() const { return mesh.ncells; }
   size_t device_bytes() const {
     return d_verts.bytes() + d_g.bytes() + d_jac.bytes() + d_R.bytes() + d_Ae.bytes() + d_Ycell.bytes() +
-           d_dinv.bytes() + d_L64.bytes() + d_L32.bytes() + d_Ae32.bytes() + d_D64.bytes() + d_D32.bytes() + d_zpatch.bytes() + d_X.bytes() + d_cells.bytes() +
+           d_dinv.bytes() + d_L64.bytes() + d_L32.bytes() + d_L32T.bytes() + d_D32T.bytes() + d_Ae32.bytes() + d_D64.bytes() + d_D32.bytes() + d_zpatch.bytes() + d_X.bytes() + d_cells.bytes() +
            d_cdofs.bytes() + d_sc_pos.bytes() + d_pn.bytes() + d_pdofs.bytes() + d_pz_pos.bytes() +
            d_pb_cell.bytes() + d_pb_ent.bytes() + d_cgdofs.bytes() + d_sc_ptr.bytes() + d_pdoff.bytes() +
            d_pfoff.bytes() + d_pdioff.bytes() + d_pmoff.bytes() + d_meta.bytes() + d_pz_ptr.bytes() + d_pb_ptr.bytes() + d_pb_off.bytes() + d_r.bytes() + d_z.bytes() +
@@ -177,6 +178,8 @@ struct riesz_handle {
     if (h_ctl) cudaFreeHost(h_ctl);
     h_ctl = nullptr;
     d_L32.free();
+    d_L32T.free();
+    d_D32T.free();
     d_D32.free();
     d_Ae32.free();
     for (auto* b : {&d_cells, &d_cdofs, &d_sc_pos, &d_pn, &d_pdofs, &d_pz_pos, &d_pb_cell, &d_pb_ent, &d_cgdofs, &d_meta})
@@ -703,6 +706,9 @@ template <typename T>
 size_t sweep_smem(int slots, int nbmax) {
   return (size_t)slots * 1024 * sizeof(T) + (size_t)nbmax * 32 * sizeof(T);
 }
+size_t sweep8_smem(int nbmax) {  // ring + patch vectors of 8 right-hand sides (FP32)
+  return (size_t)SWEEP_SLOTS_F32 * 1024 * sizeof(float) + (size_t)nbmax * 32 * 8 * sizeof(float);
+}
 
 // Patch sweeps for nrhs right-hand sides into zpatch.
 void op_patch_solves(riesz_handle& h, const double* r, int nrhs, cudaStream_t s) {
@@ -727,22 +733,27 @@ void op_patch_solves(riesz_handle& h, const double* r, int nrhs, cudaStream_t s)
       });
     return;
   }
+  if (f32) {  // up to 8 right-hand sides per launch on the bulk-copy pipeline
+    for (int r0 = 0; r0 < nrhs; r0 += 8) {
+      const int nr = std::min(8, nrhs - r0);
+      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
+        dev::k_patch_sweep8<SWEEP_SLOTS_F32><<<npatch, dev::SWEEP_NT, sweep8_smem(nbmax), s>>>(
+            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L32.p,
+            h.d_D32.p, h.d_L32T.p, h.d_D32T.p, r + (int64_t)r0 * N, h.d_zpatch.p + (int64_t)r0 * zstride, N, zstride,
+            nr, h.d_flags.p);
+      });
+    }
+    return;
+  }
   for (int r0 = 0; r0 < nrhs; r0 += h.multi_group) {
     const int nr = std::min(h.multi_group, nrhs - r0);
     const double* rr = r + (int64_t)r0 * N;
     double* zp = h.d_zpatch.p + (int64_t)r0 * zstride;
-    if (f32)
-      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
-        dev::k_patch_solve_multi<float><<<npatch, dev::NT, (size_t)nr * nbmax * 32 * sizeof(float), s>>>(
-            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L32.p,
-            h.d_D32.p, rr, zp, N, zstride, nr);
-      });
-    else
-      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
-        dev::k_patch_solve_multi<double><<<npatch, dev::NT, (size_t)nr * nbmax * 32 * sizeof(double), s>>>(
-            h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L64.p,
-            h.d_D64.p, rr, zp, N, zstride, nr);
-      });
+    launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
+      dev::k_patch_solve_multi<double><<<npatch, dev::NT, (size_t)nr * nbmax * 32 * sizeof(double), s>>>(
+          h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L64.p,
+          h.d_D64.p, rr, zp, N, zstride, nr);
+    });
   }
 }
 
@@ -1447,6 +1458,14 @@ void device_compute(riesz_handle& h, cudaStream_t s) {
       launch(h, RIESZ_K_TO_F32, s, [&] {
         dev::k_to_f32<<<1184, 256, 0, s>>>(h.factor_entries, h.d_L64.p, h.d_L32.p);
       });
+      if (h.d_L32T.p) {
+        launch(h, RIESZ_K_TO_F32, s, [&] {
+          dev::k_to_f32_tiles_t<<<1184, 256, 0, s>>>(h.factor_entries, h.d_L64.p, h.d_L32T.p);
+        });
+        launch(h, RIESZ_K_TO_F32, s, [&] {
+          dev::k_to_f32_tiles_t<<<296, 256, 0, s>>>(h.dinv_entries, h.d_D64.p, h.d_D32T.p);
+        });
+      }
       launch(h, RIESZ_K_TO_F32, s, [&] {
         dev::k_to_f32<<<296, 256, 0, s>>>(h.dinv_entries, h.d_D64.p, h.d_D32.p);
       });
@@ -1610,8 +1629,9 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     const size_t budget = 160 * 1024;  // dynamic share, leaves room for the static reduction buffers
     h.multi_group = (int)std::max<size_t>(1, std::min<size_t>(8, budget / per));
     const int smm = (int)(per * h.multi_group);
-    raise_smem_limit(dev::k_patch_solve_multi<float>, (size_t)smm);
     raise_smem_limit(dev::k_patch_solve_multi<double>, (size_t)smm);
+    const int nbm = h.p_n.empty() ? 1 : (h.p_n[0] + 31) / 32;
+    raise_smem_limit(dev::k_patch_sweep8<SWEEP_SLOTS_F32>, sweep8_smem(nbm));
   }
   h.d_pdioff.upload(h.p_dioff, s);
   h.d_pmoff.upload(h.p_moff, s);
@@ -1638,6 +1658,10 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     h.d_D64.alloc((size_t)h.dinv_entries);
     if (h.opts.precond_precision == RIESZ_PREC_FP32) {
       h.d_L32.alloc((size_t)h.factor_entries);
+      if (nrhs > 1) {
+        h.d_L32T.alloc((size_t)h.factor_entries);
+        h.d_D32T.alloc((size_t)h.dinv_entries);
+      }
       h.d_D32.alloc((size_t)h.dinv_entries);
     }
   }
