@@ -36,6 +36,12 @@ WORKLOADS = {
     "hcurl_ned1_p6_n4": dict(space="N1curl", p=6, n=4, amp=0.1, prec=1, nrhs=1,
                              label="H(curl) Ned1_6 on 4^3 x 6 tets, perturbed 0.1h, FP64 apply + FP32 precond "
                                    "(small case for kernel profiles)"),
+    "hcurl_ned1_p6_n6": dict(space="N1curl", p=6, n=6, amp=0.1, prec=1, nrhs=1,
+                             label="H(curl) Ned1_6 on 6^3 x 6 tets, perturbed 0.1h, FP64 apply + FP32 precond "
+                                   "(medium case for kernel profiles)"),
+    "hdiv_rt8_n4": dict(space="RT", p=8, n=4, amp=0.1, prec=1, nrhs=8, a32=1,
+                        label="H(div) RT_8 on 4^3 x 6 tets, perturbed 0.1h, 8 RHS, FP32 inner products and patch "
+                              "solves (small case for kernel profiles)"),
     "hgrad_cg3_n4": dict(space="CG", p=3, n=4, amp=0.0, prec=0, nrhs=1,
                          label="H(grad) CG_3 on 4^3 x 6 tets, FP64"),
     "hdiv_rt8_n16": dict(space="RT", p=8, n=16, amp=0.1, prec=1, nrhs=8, a32=1,
