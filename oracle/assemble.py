@@ -244,6 +244,91 @@ class DirichletPreconditioner:
         return z
 
 
+def gradient_matrix(md_ned, md_cg):
+    """Ned1_p coefficients of the gradients of the CG_p basis functions on the same mesh: signed
+    vertex-edge incidence on the Whitney DOFs and the identity from CG type-I edge/face DOFs onto
+    Ned1_p type-II edge/face DOFs (Eq. (5.3), Lemma 4.3: type II = d of type I).  Interface part only."""
+    rows, cols, vals = [], [], []
+    ne_d, nf_d = md_ned.per_entity[1], md_ned.per_entity[2]
+    ce, cf = md_cg.per_entity[1], md_cg.per_entity[2]
+    off_e, off_f = md_ned._offsets[1], md_ned._offsets[2]
+    coff_e, coff_f = md_cg._offsets[1], md_cg._offsets[2]
+    for e, (a, b) in enumerate(md_ned.edges):
+        rows += [off_e + ne_d * e] * 2
+        cols += [int(a), int(b)]
+        vals += [-1.0, 1.0]
+        for m in range(ce):
+            rows.append(off_e + ne_d * e + 1 + m)
+            cols.append(coff_e + ce * e + m)
+            vals.append(1.0)
+    nfI = nf_d - cf
+    for f in range(len(md_ned.faces)):
+        for m in range(cf):
+            rows.append(off_f + nf_d * f + nfI + m)
+            cols.append(coff_f + cf * f + m)
+            vals.append(1.0)
+    return scipy.sparse.csr_matrix((vals, (rows, cols)), shape=(md_ned.ndofs, md_cg.ndofs))
+
+
+def edge_star_type1_dofs(md_ned, md_cg):
+    """Per edge L: the Whitney DOF of L and the type-I DOFs of every face containing L (interface
+    DOFs of X^{1,I} on the star of L), sorted."""
+    ne_d, nf_d = md_ned.per_entity[1], md_ned.per_entity[2]
+    nfI = nf_d - md_cg.per_entity[2]
+    off_e, off_f = md_ned._offsets[1], md_ned._offsets[2]
+    faces_of = {}
+    for f, tri in enumerate(md_ned.faces.tolist()):
+        for a, b in ((tri[0], tri[1]), (tri[0], tri[2]), (tri[1], tri[2])):
+            faces_of.setdefault((a, b), []).append(f)
+    out = []
+    for e, (a, b) in enumerate(md_ned.edges.tolist()):
+        d = [off_e + ne_d * e]
+        for f in faces_of.get((a, b), []):
+            d += [off_f + nf_d * f + m for m in range(nfI)]
+        out.append(np.array(sorted(d), dtype=np.int64))
+    return out
+
+
+class HTPreconditioner:
+    """The Hiptmair-Toselli splitting of Eq. (6.19) for H(curl) with the interface/interior split:
+    P^{-1} = D_II^{-1} + sum_L R_L^T A_L^{-1} R_L (edge stars of type-I interface DOFs)
+           + G sum_J R_J^T (G^T A G)_J^{-1} R_J G^T (gradients of CG_p interface functions on vertex
+             stars, the potential problems of Eq. (6.18)) + w R_0^T A_0^{-1} R_0 (W^1).
+    Additive; the coarse weight w = 1/2 as for the vertex-star preconditioner."""
+
+    def __init__(self, A, md_ned, md_cg, weight=0.5):
+        self.N = A.shape[0]
+        A = A.tocsr()
+        self.nI = md_ned.n_interface
+        self.dinv_I = 1.0 / A.diagonal()[self.nI:]
+        self.G = gradient_matrix(md_ned, md_cg).tocsc()
+        K = (self.G.T @ A @ self.G).tocsr()
+        self.pot = [(idx, scipy.linalg.cho_factor(K[idx][:, idx].toarray(), lower=True))
+                    for idx in md_cg.patches() if len(idx)]
+        self.est = [(idx, scipy.linalg.cho_factor(A[idx][:, idx].toarray(), lower=True))
+                    for idx in edge_star_type1_dofs(md_ned, md_cg)]
+        self.W = coarse_dofs(md_ned)
+        self.weight = weight
+        self.fac0 = scipy.linalg.cho_factor(A[self.W][:, self.W].toarray(), lower=True)
+
+    def apply(self, r):
+        z = np.zeros_like(r)
+        z[self.nI:] = self.dinv_I * r[self.nI:]
+        for idx, f in self.est:
+            z[idx] += scipy.linalg.cho_solve(f, r[idx])
+        rc = self.G.T @ r
+        zc = np.zeros_like(rc)
+        for idx, f in self.pot:
+            zc[idx] += scipy.linalg.cho_solve(f, rc[idx])
+        z += self.G @ zc
+        z[self.W] += self.weight * scipy.linalg.cho_solve(self.fac0, r[self.W])
+        return z
+
+    def dense(self):
+        I = np.eye(self.N)
+        return np.stack([self.apply(I[:, j]) for j in range(self.N)], 1)
+
+
 class TwoLevelPreconditioner:
     """P^{-1} = D_II^{-1} (+) sum_V R_V^T A_V^{-1} R_V + w R_0^T A_0^{-1} R_0: the one-level operator
     plus an exact solve on W^k (the PAFW decomposition's coarse summand, Section 6.2), with

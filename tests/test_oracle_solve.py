@@ -393,3 +393,52 @@ def test_dirichlet_solution_has_zero_trace():
     assert on.sum() > 20
     assert np.abs(val.reshape(-1)[on]).max() <= 1e-12 * np.abs(x).max()
     assert np.abs(val.reshape(-1)[~on]).max() > 1e-3 * np.abs(x).max()
+
+
+def test_ht_potential_matrices_are_cg_stiffness():
+    """G^T A G on the CG interface DOFs is beta times the CG_p stiffness (d o d = 0 removes the curl
+    term), assembled independently from CG element matrices."""
+    p = 3
+    v, c = kuhn_mesh(2, 0.1, 4)
+    rn, rc = reference_element("N1curl", p), reference_element("CG", p)
+    mn, mc = MeshDofs(v, c, rn), MeshDofs(v, c, rc)
+    A = asm.assemble(mn, asm.element_matrices(rn, v, c, alpha=1.3, beta=0.7))
+    G = asm.gradient_matrix(mn, mc)
+    K = (G.T @ A @ G).toarray()[:mc.n_interface, :mc.n_interface]
+    Kc = asm.assemble(mc, asm.element_matrices(rc, v, c, alpha=0.7, beta=0.0)).toarray()
+    Kc = Kc[:mc.n_interface, :mc.n_interface]
+    assert np.abs(K - Kc).max() <= 1e-11 * np.abs(Kc).max()
+
+
+def test_ht_edge_stars():
+    """Edge-star type-I DOFs: the edge's Whitney DOF and the type-I DOFs of each face containing it."""
+    p = 4
+    v, c = kuhn_mesh(2, 0.1, 4)
+    rn, rc = reference_element("N1curl", p), reference_element("CG", p)
+    mn, mc = MeshDofs(v, c, rn), MeshDofs(v, c, rc)
+    stars = asm.edge_star_type1_dofs(mn, mc)
+    nfI = mn.per_entity[2] - mc.per_entity[2]  # face type-I DOFs: the face DOFs that are not gradients
+    assert nfI > 0
+    for e, (a, b) in enumerate(mn.edges):
+        nf = int(np.sum(np.isin(mn.faces, [a, b]).sum(1) == 2))
+        assert len(stars[e]) == 1 + nfI * nf
+        assert stars[e][0] == mn._offsets[1] + mn.per_entity[1] * e
+
+
+def test_ht_preconditioner_spd_and_refinement_robust():
+    """The HT preconditioner is SPD on A (positive spectrum of P^{-1}A) and its PCG count stays
+    flat from 2^3 to 4^3 cubes, like the vertex-star two-level one."""
+    rn, rc = reference_element("N1curl", 2), reference_element("CG", 2)
+    v, c = kuhn_mesh(2, 0.1, 6)
+    mn, mc = MeshDofs(v, c, rn), MeshDofs(v, c, rc)
+    A = asm.assemble(mn, asm.element_matrices(rn, v, c))
+    ev = np.linalg.eigvals(asm.HTPreconditioner(A, mn, mc).dense() @ A.toarray())
+    assert np.abs(ev.imag).max() < 1e-8 and ev.real.min() > 0
+    its = []
+    for n in (2, 4):
+        v, c = kuhn_mesh(n, 0.1, 1)
+        mn, mc = MeshDofs(v, c, rn), MeshDofs(v, c, rc)
+        A = asm.assemble(mn, asm.element_matrices(rn, v, c))
+        b = normal_vector(mn.ndofs, 3)
+        its.append(asm.pcg(A, b, asm.HTPreconditioner(A, mn, mc).apply)[1])
+    assert its[1] <= 1.2 * its[0] + 2
