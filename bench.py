@@ -73,6 +73,9 @@ def parse():
                     help="batched run: seeded mixed systems solved in one graph launch per HBM wave")
     ap.add_argument("--systems", type=int, default=64)
     ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
+    ap.add_argument("--decomposition", default="vertex_star", choices=["vertex_star", "ht"],
+                    help="H(curl) subspace decomposition: vertex stars (Eq. 6.11) or Hiptmair-Toselli "
+                         "edge stars + gradient potential problems (Eq. 6.19)")
     ap.add_argument("--pcg-loop", default="graph", choices=["graph", "host"],
                     help="device-driven (CUDA graph) or host-driven PCG iterations; same kernels, same results")
     ap.add_argument("--p-sweep", action="store_true",
@@ -464,7 +467,8 @@ def main():
     def make(prec, a32):
         """A solver handle for the workload and its step closure (device setup + load + solve)."""
         s = rz.Riesz(wl["space"], wl["p"], verts, cells, precond_precision=prec, nrhs_max=nrhs,
-                     apply_precision=a32, loop=rz.LOOP_HOST if args.pcg_loop == "host" else rz.LOOP_GRAPH)
+                     apply_precision=a32, loop=rz.LOOP_HOST if args.pcg_loop == "host" else rz.LOOP_GRAPH,
+                     decomposition=rz.DECOMP_HT if args.decomposition == "ht" else rz.DECOMP_VERTEX_STAR)
         if nrhs == 1:  # f with N(0,1) CG_p coefficients per Cartesian component, b = (f, phi)
             fcg_h = normal_coeffs((ncomp, s.n_cg), 2 + rank)
         else:  # the paper's random right-hand side vectors (Section 7.1), one per RHS
@@ -632,7 +636,7 @@ def main():
                        "nrhs": nrhs, "apply_precision": "fp32" if wl.get("a32", 0) else "fp64",
                        "precond_precision": "fp32" if wl["prec"] == 1 else "fp64",
                        "rtol": 1e-8, "step": "device setup + load + PCG solve",
-                       "pcg_loop": loop_driver,
+                       "pcg_loop": loop_driver, "decomposition": args.decomposition,
                        "autotuned": s.tuning(),
                        "l2": "inputs larger than L2 (element matrices and patch factors)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -66,6 +66,7 @@ enum {
 enum { RIESZ_PREC_FP64 = 0, RIESZ_PREC_FP32 = 1 };
 enum { RIESZ_APPLY_MATRIX_FREE = 0, RIESZ_APPLY_ELEMENT = 1 };
 enum { RIESZ_LOOP_HOST = 0, RIESZ_LOOP_GRAPH = 1 };
+enum { RIESZ_DECOMP_VERTEX_STAR = 0, RIESZ_DECOMP_HT = 1 };
 
 typedef struct {
   /* Precision of the stored patch Cholesky factors and of the triangular
@@ -138,11 +139,26 @@ typedef struct {
      riesz_precond gives z_d = r_d and leaves the fixed DOFs out of every
      patch and of W^k; riesz_load writes b_d = 0; a solve returns x_d = b_d. */
   int dirichlet;
+  /* Space decomposition of the interface preconditioner.
+     RIESZ_DECOMP_VERTEX_STAR (default): PAFW vertex stars (Eq. (6.11)).
+     RIESZ_DECOMP_HT (H(curl) only, Neumann): the Hiptmair-Toselli splitting
+     of Eq. (6.19) with the interface/interior split: exact solves on the
+     type-I interface DOFs of every edge star (the edge's Whitney DOF and the
+     type-I DOFs of the faces containing it) plus gradients of CG_p interface
+     functions on every vertex star, whose potential problems
+     (grad u, beta grad v) are factored in a CG_p handle owned by this one
+     (Eq. (6.18)); the gradient map is the signed incidence / identity of
+     Eq. (5.3).  Interior Jacobi and W^k as for the vertex stars.  The
+     patches are much smaller (Ned1_6: 431-DOF potential and 121-DOF edge
+     problems instead of 1164-DOF vertex stars), so the FP64 factorisation
+     is far cheaper; PCG takes somewhat more iterations. */
+  int decomposition;
 } riesz_opts;
 
 /* Fill *o with the defaults: FP64 preconditioner, element-matrix apply,
    rtol 1e-8, maxit 1000, nrhs_max 1, alpha = beta = 1, FP64 apply,
-   graph-driven loop, autotune on, coarse space on, Neumann boundary. */
+   graph-driven loop, autotune on, coarse space on, Neumann boundary,
+   vertex-star decomposition. */
 void riesz_default_opts(riesz_opts* o);
 
 /* ---- host-only calls (no GPU needed) ---------------------------------- */
@@ -286,7 +302,8 @@ enum {
   RIESZ_K_APPLY32 = 14,     /* a3-a4 with the FP32 element matrices      */
   RIESZ_K_COARSE = 15,      /* W^k: A_0 assembly and block inversion     */
   RIESZ_K_COARSE_APPLY = 16,/* W^k: coarse correction A_0^{-1} R_0 r     */
-  RIESZ_NKIND = 17
+  RIESZ_K_HT = 17,          /* HT: gradient map and potential gather     */
+  RIESZ_NKIND = 18
 };
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around

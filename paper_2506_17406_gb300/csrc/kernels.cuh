@@ -1241,7 +1241,7 @@ __global__ void k_precond_gather(int64_t N, int64_t nifd, const int64_t* __restr
                                  const int32_t* __restrict__ pos, const double* __restrict__ zpatch, int64_t zstride,
                                  const double* __restrict__ dinv, const double* __restrict__ r, double* __restrict__ z,
                                  int nrhs, const int32_t* __restrict__ cidx, const double* __restrict__ zc, int64_t n0,
-                                 const uint8_t* __restrict__ dmask) {
+                                 const uint8_t* __restrict__ dmask, const double* __restrict__ zg) {
   const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (d >= N) return;
   for (int rh = 0; rh < nrhs; ++rh) {
@@ -1252,6 +1252,7 @@ __global__ void k_precond_gather(int64_t N, int64_t nifd, const int64_t* __restr
       s = 0.0;
       for (int64_t k = ptr[d]; k < ptr[d + 1]; ++k) s += zpatch[rh * zstride + pos[k]];
       if (cidx && cidx[d] >= 0) s += zc[rh * n0 + cidx[d]];
+      if (zg) s += zg[rh * nifd + d];
     } else {
       s = dinv[d - nifd] * r[rh * N + d];
     }
@@ -1503,6 +1504,36 @@ __global__ void __launch_bounds__(256) k_coarse_apply(int N0, int N0p, const flo
 }
 
 // ---------------------------------------------------------------------------
+// Hiptmair-Toselli decomposition (Eq. (6.19)): the gradient map G between CG_p
+// and Ned1_p interface coefficients (Eq. (5.3)) as signed CSR lists.
+// ---------------------------------------------------------------------------
+// out[rh][i] = sum_k sgn_k in[rh][idx_k] over the list of row i (G^T r, or G z)
+__global__ void k_ht_map(int64_t nrow, const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                         const float* __restrict__ sgn, const double* __restrict__ in, int64_t in_stride,
+                         double* __restrict__ out, int64_t out_stride, int nrhs) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nrow) return;
+  for (int rh = 0; rh < nrhs; ++rh) {
+    double s = 0.0;
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) s += (double)sgn[k] * in[rh * in_stride + idx[k]];
+    out[rh * out_stride + i] = s;
+  }
+}
+
+// zc[rh][i] = sum of the patch results of CG interface DOF i (potential problems)
+__global__ void k_ht_gather(int64_t nrow, const int64_t* __restrict__ ptr, const int32_t* __restrict__ pos,
+                            const double* __restrict__ zpatch, int64_t zstride, double* __restrict__ zc,
+                            int64_t zc_stride, int nrhs) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nrow) return;
+  for (int rh = 0; rh < nrhs; ++rh) {
+    double s = 0.0;
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) s += zpatch[rh * zstride + pos[k]];
+    zc[rh * zc_stride + i] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // a9: PCG vector kernels with deterministic two-stage reductions.
 // scal layout (per right-hand side, stride 16): see riesz.cu
 // ---------------------------------------------------------------------------
@@ -1713,7 +1744,8 @@ __global__ void __launch_bounds__(NT) k_precond_gather_dot(int64_t N, int64_t ni
                                                           double* __restrict__ scal, int64_t zstride,
                                                           const int32_t* __restrict__ cidx,
                                                           const double* __restrict__ zc, int64_t n0,
-                                                          const uint8_t* __restrict__ dmask) {
+                                                          const uint8_t* __restrict__ dmask,
+                                                          const double* __restrict__ zg) {
   const int64_t o = blockIdx.y * N;
   zpatch += blockIdx.y * zstride;
   r += o;
@@ -1728,6 +1760,7 @@ __global__ void __launch_bounds__(NT) k_precond_gather_dot(int64_t N, int64_t ni
       zi = 0.0;
       for (int64_t k = ptr[d]; k < ptr[d + 1]; ++k) zi += zpatch[pos[k]];
       if (cidx && cidx[d] >= 0) zi += zc[blockIdx.y * n0 + cidx[d]];
+      if (zg) zi += zg[blockIdx.y * nifd + d];
     } else {
       zi = dinv[d - nifd] * r[d];
     }

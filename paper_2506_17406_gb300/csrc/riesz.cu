@@ -93,6 +93,21 @@ struct riesz_handle {
   DBuf<double> d_verts, d_g, d_jac, d_R, d_Ae, d_Ycell, d_dinv, d_L64, d_D64, d_zpatch, d_X;
   DBuf<float> d_L32, d_D32, d_Ae32;
   DBuf<float> d_L32T, d_D32T;  // tile-transposed FP32 factors (forward sweep of several right-hand sides)
+  // Hiptmair-Toselli decomposition (H(curl)): type-I edge-star patches on this
+  // handle, gradient potential problems on the CG vertex stars of `aux`, and the
+  // gradient map: CG interface DOF -> (Ned1 DOF, sign) and Ned1 interface DOF ->
+  // (CG DOF, sign) (Eq. (5.3))
+  bool ht = false;
+  riesz_handle* aux = nullptr;
+  std::vector<int64_t> ht_star_ptr;
+  std::vector<int32_t> ht_star_dofs;
+  std::vector<int64_t> gt_ptr, gg_ptr;
+  std::vector<int32_t> gt_idx, gg_idx;
+  std::vector<float> gt_sgn, gg_sgn;
+  DBuf<int64_t> d_gt_ptr, d_gg_ptr;
+  DBuf<int32_t> d_gt_idx, d_gg_idx;
+  DBuf<float> d_gt_sgn, d_gg_sgn;
+  DBuf<double> d_zcg, d_zg;  // potential corrections [nrhs][n_if(CG)], their gradients [nrhs][n_if]
   // homogeneous Dirichlet DOFs (all DOFs of boundary entities), flag per interface DOF
   std::vector<uint8_t> dir_mask;
   DBuf<uint8_t> d_dmask;
@@ -150,7 +165,9 @@ struct riesz_handle {
            d_pb_cell.bytes() + d_pb_ent.bytes() + d_cgdofs.bytes() + d_sc_ptr.bytes() + d_pdoff.bytes() +
            d_pfoff.bytes() + d_pdioff.bytes() + d_pmoff.bytes() + d_meta.bytes() + d_pz_ptr.bytes() + d_pb_ptr.bytes() + d_pb_off.bytes() + d_r.bytes() + d_z.bytes() +
            d_zold.bytes() + d_p.bytes() + d_Ap.bytes() + d_part.bytes() + d_scal.bytes() + d_tmp.bytes() + d_xh.bytes() +
-           d_xw.bytes() + d_ctl.bytes() + d_flags.bytes() + d_dmask.bytes() + d_cw.bytes() + d_cidx.bytes() + d_cJ.bytes() +
+           d_xw.bytes() + d_ctl.bytes() + d_flags.bytes() + d_dmask.bytes() + d_gt_ptr.bytes() + d_gg_ptr.bytes() +
+           d_gt_idx.bytes() + d_gg_idx.bytes() + d_gt_sgn.bytes() + d_gg_sgn.bytes() + d_zcg.bytes() + d_zg.bytes() +
+           (aux ? aux->device_bytes() : 0) + d_cw.bytes() + d_cidx.bytes() + d_cJ.bytes() +
            d_ccell.bytes() + d_cab.bytes() + d_cptr.bytes() + d_A0.bytes() + d_Dinv0.bytes() + d_Rb0.bytes() +
            d_r0.bytes() + d_zc.bytes();
   }
@@ -168,6 +185,14 @@ struct riesz_handle {
     d_ctl.free();
     d_flags.free();
     d_dmask.free();
+    d_gt_ptr.free();
+    d_gg_ptr.free();
+    d_gt_idx.free();
+    d_gg_idx.free();
+    d_gt_sgn.free();
+    d_gg_sgn.free();
+    d_zcg.free();
+    d_zg.free();
     for (auto* b : {&d_cw, &d_cidx, &d_cJ, &d_ccell, &d_cab}) b->free();
     d_cptr.free();
     d_A0.free();
@@ -200,6 +225,7 @@ struct riesz_handle {
     if (ev_join) cudaEventDestroy(ev_join);
     if (ev_pfork) cudaEventDestroy(ev_pfork);
     if (ev_pjoin) cudaEventDestroy(ev_pjoin);
+    delete aux;
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   }
 };
@@ -290,13 +316,14 @@ dev::Mat3 ref_edge_inverse() {
 // DOFs in bands and leaves most 32x32 tiles of the factor zero.  The tile
 // pattern of the factor is the symbolic tile-level Cholesky of the pattern of
 // A_V; only nonzero tiles are stored, in block-row order.
-void plan_patch(riesz_handle& h, int64_t v, int64_t& foff, int64_t& dioff) {
+// Plan one patch: its DOFs pd[0..np) (ascending interface DOFs) and the cells
+// of its star (cells whose interface DOFs may touch it); `center` is a point
+// of the star (the Fiedler ordering uses coordinates relative to it).
+void plan_patch(riesz_handle& h, const int32_t* pd, int np, const int32_t* star, int64_t nstar, const double* center,
+                int64_t& foff, int64_t& dioff) {
   const MeshMaps& M = h.mesh;
   const int n = M.nref;
-  const int64_t b = M.patch_ptr[v], e = M.patch_ptr[v + 1];
-  const int np = (int)(e - b);
-  const int32_t* pd = &M.patch_dofs[b];
-  // entities: contiguous runs of the sorted patch DOF list
+  // entities: contiguous runs of the sorted patch DOF list with the same entity
   std::vector<int> ent_start, ent_len, dof_ent(np);
   std::vector<std::array<double, 3>> mid;
   const double* X = h.verts.data();
@@ -305,6 +332,8 @@ void plan_patch(riesz_handle& h, int64_t v, int64_t& foff, int64_t& dioff) {
     int kind = (d < M.off[1]) ? 0 : (d < M.off[2] ? 1 : 2);
     const int per = M.per_entity[kind];
     const int64_t id = (d - M.off[kind]) / per;
+    int run = 1;
+    while (k + run < np && pd[k + run] < M.off[kind] + (id + 1) * per && pd[k + run] >= M.off[kind] + id * per) ++run;
     std::array<double, 3> m = {0.0, 0.0, 0.0};
     int nvx = 0;
     int32_t vv[3];
@@ -320,21 +349,21 @@ void plan_patch(riesz_handle& h, int64_t v, int64_t& foff, int64_t& dioff) {
       nvx = 3;
     }
     for (int q = 0; q < nvx; ++q)
-      for (int c = 0; c < 3; ++c) m[c] += (X[(size_t)vv[q] * 3 + c] - X[(size_t)v * 3 + c]) / nvx;
+      for (int c = 0; c < 3; ++c) m[c] += (X[(size_t)vv[q] * 3 + c] - center[c]) / nvx;
     const int ei = (int)ent_start.size();
     ent_start.push_back(k);
-    ent_len.push_back(per);
+    ent_len.push_back(run);
     mid.push_back(m);
-    for (int q = 0; q < per; ++q) dof_ent[k + q] = ei;
-    k += per;
+    for (int q = 0; q < run; ++q) dof_ent[k + q] = ei;
+    k += run;
   }
   const int ne = (int)ent_start.size();
   // star cells -> patch entities (and DOF positions)
   std::vector<std::vector<int>> cell_ents;
   std::vector<int32_t> cell_ids;
   std::vector<std::vector<std::pair<int, int>>> cell_locs;  // (local j, sorted patch index)
-  for (int64_t sidx = M.star_ptr[v]; sidx < M.star_ptr[v + 1]; ++sidx) {
-    const int32_t c = M.star_cells[sidx];
+  for (int64_t sidx = 0; sidx < nstar; ++sidx) {
+    const int32_t c = star[sidx];
     std::vector<int> ce;
     std::vector<std::pair<int, int>> loc;
     for (int j = 0; j < h.nif; ++j) {
@@ -452,6 +481,96 @@ void plan_patch(riesz_handle& h, int64_t v, int64_t& foff, int64_t& dioff) {
   h.pb_ptr.push_back((int64_t)h.pb_cell.size());
 }
 
+// Index of the sorted edge (a, b), a < b, in the lexicographic edge list.
+int64_t edge_index(const MeshMaps& M, int32_t a, int32_t b) {
+  int64_t lo = 0, hi = M.nedges;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    const int32_t* e = &M.edges[mid * 2];
+    if (e[0] < a || (e[0] == a && e[1] < b))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  if (lo >= M.nedges || M.edges[lo * 2] != a || M.edges[lo * 2 + 1] != b)
+    throw Err(RIESZ_ERR_INTERNAL, "edge not found");
+  return lo;
+}
+
+// Hiptmair-Toselli decomposition of Eq. (6.19) for H(curl): per edge L the
+// Whitney DOF of L and the type-I DOFs of every face containing L (the
+// interface DOFs of X^{1,I} on the star of L; inside a face the type-I DOFs
+// come first), and the gradient map between CG_p and Ned1_p interface DOFs:
+// the gradient of the CG vertex function v has Whitney coefficient +1 on edges
+// ending at v and -1 on edges starting at v; the gradient of the m-th CG edge
+// (face) function is the m-th type-II Ned1 function of that edge (face)
+// (Eq. (5.3), Lemma 4.3).
+void plan_ht(riesz_handle& h) {
+  const MeshMaps& M = h.mesh;
+  const MeshMaps& Mc = h.meshcg;
+  const int ne_d = M.per_entity[1], nf_d = M.per_entity[2];
+  const int ce = Mc.per_entity[1], cf = Mc.per_entity[2];
+  const int nfI = nf_d - cf;
+  if (ne_d != ce + 1 || nfI < 0 || Mc.per_entity[0] != 1)
+    throw Err(RIESZ_ERR_INTERNAL, "gradient map: unexpected DOF counts");
+  std::vector<std::vector<int32_t>> faces_of(M.nedges);
+  for (int64_t f = 0; f < M.nfaces; ++f) {
+    const int32_t* v = &M.faces[f * 3];
+    faces_of[edge_index(M, v[0], v[1])].push_back((int32_t)f);
+    faces_of[edge_index(M, v[0], v[2])].push_back((int32_t)f);
+    faces_of[edge_index(M, v[1], v[2])].push_back((int32_t)f);
+  }
+  h.ht_star_ptr.assign(1, 0);
+  h.ht_star_dofs.clear();
+  for (int64_t e = 0; e < M.nedges; ++e) {
+    std::vector<int32_t> d{(int32_t)(M.off[1] + (int64_t)ne_d * e)};
+    for (int32_t f : faces_of[e])
+      for (int m = 0; m < nfI; ++m) d.push_back((int32_t)(M.off[2] + (int64_t)nf_d * f + m));
+    std::sort(d.begin(), d.end());
+    h.ht_star_dofs.insert(h.ht_star_dofs.end(), d.begin(), d.end());
+    h.ht_star_ptr.push_back((int64_t)h.ht_star_dofs.size());
+  }
+  // G^T rows: CG interface DOF -> (Ned1 DOF, sign)
+  const int64_t ncif = Mc.n_interface;
+  std::vector<std::vector<std::pair<int32_t, float>>> gt(ncif);
+  std::vector<std::vector<std::pair<int32_t, float>>> gg(M.n_interface);
+  for (int64_t e = 0; e < M.nedges; ++e) {
+    const int32_t a = M.edges[e * 2], b = M.edges[e * 2 + 1];
+    const int32_t w = (int32_t)(M.off[1] + (int64_t)ne_d * e);
+    gt[Mc.off[0] + a].push_back({w, -1.f});
+    gt[Mc.off[0] + b].push_back({w, 1.f});
+    gg[w].push_back({(int32_t)(Mc.off[0] + a), -1.f});
+    gg[w].push_back({(int32_t)(Mc.off[0] + b), 1.f});
+    for (int m = 0; m < ce; ++m) {
+      const int32_t nd = w + 1 + m, cd = (int32_t)(Mc.off[1] + (int64_t)ce * e + m);
+      gt[cd].push_back({nd, 1.f});
+      gg[nd].push_back({cd, 1.f});
+    }
+  }
+  for (int64_t f = 0; f < M.nfaces; ++f)
+    for (int m = 0; m < cf; ++m) {
+      const int32_t nd = (int32_t)(M.off[2] + (int64_t)nf_d * f + nfI + m), cd = (int32_t)(Mc.off[2] + (int64_t)cf * f + m);
+      gt[cd].push_back({nd, 1.f});
+      gg[nd].push_back({cd, 1.f});
+    }
+  auto flatten = [](const std::vector<std::vector<std::pair<int32_t, float>>>& rows, std::vector<int64_t>& ptr,
+                    std::vector<int32_t>& idx, std::vector<float>& sgn) {
+    ptr.assign(1, 0);
+    idx.clear();
+    sgn.clear();
+    for (const auto& r : rows) {
+      for (const auto& q : r) {
+        idx.push_back(q.first);
+        sgn.push_back(q.second);
+      }
+      ptr.push_back((int64_t)idx.size());
+    }
+  };
+  flatten(gt, h.gt_ptr, h.gt_idx, h.gt_sgn);
+  flatten(gg, h.gg_ptr, h.gg_idx, h.gg_sgn);
+  h.ht = true;
+}
+
 // Homogeneous Dirichlet conditions on the whole boundary (X_{p,D} with
 // Gamma_D the boundary, Eq. (2.8)): a function has zero trace there exactly
 // when every DOF of every boundary vertex, edge and face is zero.  Marks those
@@ -462,20 +581,6 @@ void plan_dirichlet(riesz_handle& h) {
   std::vector<int> cnt(M.nfaces, 0);
   for (int64_t c = 0; c < M.ncells; ++c)
     for (int f = 0; f < 4; ++f) ++cnt[M.cell_faces[c * 4 + f]];
-  auto edge_index = [&](int32_t a, int32_t b) -> int64_t {  // edges: sorted pairs, lexicographic
-    int64_t lo = 0, hi = M.nedges;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) / 2;
-      const int32_t* e = &M.edges[mid * 2];
-      if (e[0] < a || (e[0] == a && e[1] < b))
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    if (lo >= M.nedges || M.edges[lo * 2] != a || M.edges[lo * 2 + 1] != b)
-      throw Err(RIESZ_ERR_INTERNAL, "boundary edge not found");
-    return lo;
-  };
   auto mark = [&](int k, int64_t ent) {
     const int nd = M.per_entity[k];
     for (int m = 0; m < nd; ++m) h.dir_mask[M.off[k] + (int64_t)nd * ent + m] = 1;
@@ -485,9 +590,9 @@ void plan_dirichlet(riesz_handle& h) {
     const int32_t* v = &M.faces[f * 3];
     mark(2, f);
     for (int a = 0; a < 3; ++a) mark(0, v[a]);
-    mark(1, edge_index(v[0], v[1]));
-    mark(1, edge_index(v[0], v[2]));
-    mark(1, edge_index(v[1], v[2]));
+    mark(1, edge_index(M, v[0], v[1]));
+    mark(1, edge_index(M, v[0], v[2]));
+    mark(1, edge_index(M, v[1], v[2]));
   }
   std::vector<int64_t> ptr(M.nverts + 1, 0);
   std::vector<int32_t> dofs;
@@ -624,12 +729,39 @@ void build_plans(riesz_handle& h) {
   h.tile_ops = 0;
   h.chol_flops = 0.0;
   int64_t foff = 0, dioff = 0;
-  for (int64_t v : order) {
-    const int64_t b = M.patch_ptr[v], e = M.patch_ptr[v + 1];
-    const int np = (int)(e - b);
-    if (np == 0) continue;
-    if (np > 32 * dev::MAXNB) throw Err(RIESZ_ERR_INVALID_ARG, "patch larger than 4096 DOFs");
-    plan_patch(h, v, foff, dioff);
+  if (h.ht) {  // Hiptmair-Toselli: type-I edge stars instead of vertex stars
+    std::vector<int64_t> eorder(h.ht_star_ptr.size() - 1);
+    for (size_t e = 0; e < eorder.size(); ++e) eorder[e] = (int64_t)e;
+    std::stable_sort(eorder.begin(), eorder.end(), [&](int64_t a, int64_t b) {
+      return (h.ht_star_ptr[a + 1] - h.ht_star_ptr[a]) > (h.ht_star_ptr[b + 1] - h.ht_star_ptr[b]);
+    });
+    for (int64_t e : eorder) {
+      const int np = (int)(h.ht_star_ptr[e + 1] - h.ht_star_ptr[e]);
+      if (np == 0) continue;
+      if (np > 32 * dev::MAXNB) throw Err(RIESZ_ERR_INVALID_ARG, "patch larger than 4096 DOFs");
+      const int32_t a = M.edges[e * 2], b = M.edges[e * 2 + 1];
+      std::vector<int32_t> cells;  // cells containing both endpoints
+      for (int64_t k = M.star_ptr[a]; k < M.star_ptr[a + 1]; ++k) {
+        const int32_t c = M.star_cells[k];
+        for (int q = 0; q < 4; ++q)
+          if (M.cells[(int64_t)c * 4 + q] == b) {
+            cells.push_back(c);
+            break;
+          }
+      }
+      double center[3];
+      for (int q = 0; q < 3; ++q) center[q] = 0.5 * (h.verts[(size_t)a * 3 + q] + h.verts[(size_t)b * 3 + q]);
+      plan_patch(h, &h.ht_star_dofs[h.ht_star_ptr[e]], np, cells.data(), (int64_t)cells.size(), center, foff, dioff);
+    }
+  } else {
+    for (int64_t v : order) {
+      const int64_t b = M.patch_ptr[v], e = M.patch_ptr[v + 1];
+      const int np = (int)(e - b);
+      if (np == 0) continue;
+      if (np > 32 * dev::MAXNB) throw Err(RIESZ_ERR_INVALID_ARG, "patch larger than 4096 DOFs");
+      plan_patch(h, &M.patch_dofs[b], np, &M.star_cells[M.star_ptr[v]], M.star_ptr[v + 1] - M.star_ptr[v],
+                 &h.verts[(size_t)v * 3], foff, dioff);
+    }
   }
   h.factor_entries = foff;
   h.dinv_entries = dioff;
@@ -788,15 +920,38 @@ void coarse_join(riesz_handle& h, cudaStream_t s) {
   if (h.coarse_on) CK(cudaStreamWaitEvent(s, h.ev_pjoin, 0));
 }
 
+// Gradient part of the Hiptmair-Toselli preconditioner: zg = G sum_J R_J^T
+// K_J^{-1} R_J G^T r with the potential problems K_J factored in the CG handle.
+void ht_potential(riesz_handle& h, const double* r, int nrhs, cudaStream_t s) {
+  if (!h.ht) return;
+  riesz_handle& a = *h.aux;
+  const int64_t ncif = a.mesh.n_interface, nif = h.mesh.n_interface;
+  launch(h, RIESZ_K_HT, s, [&] {
+    dev::k_ht_map<<<nblk(ncif, 256), 256, 0, s>>>(ncif, h.d_gt_ptr.p, h.d_gt_idx.p, h.d_gt_sgn.p, r, h.N(), a.d_r.p,
+                                                 a.N(), nrhs);
+  });
+  op_patch_solves(a, a.d_r.p, nrhs, s);
+  launch(h, RIESZ_K_HT, s, [&] {
+    dev::k_ht_gather<<<nblk(ncif, 256), 256, 0, s>>>(ncif, a.d_pz_ptr.p, a.d_pz_pos.p, a.d_zpatch.p,
+                                                    (int64_t)a.p_dofs.size(), h.d_zcg.p, ncif, nrhs);
+  });
+  launch(h, RIESZ_K_HT, s, [&] {
+    dev::k_ht_map<<<nblk(nif, 256), 256, 0, s>>>(nif, h.d_gg_ptr.p, h.d_gg_idx.p, h.d_gg_sgn.p, h.d_zcg.p, ncif,
+                                                h.d_zg.p, nif, nrhs);
+  });
+}
+
 void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStream_t s) {
   const int64_t N = h.N();
+  ht_potential(h, r, nrhs, s);
   coarse_fork(h, r, nrhs, s);
   op_patch_solves(h, r, nrhs, s);
   coarse_join(h, s);
   launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
     dev::k_precond_gather<<<nblk(N, 256), 256, 0, s>>>(N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p,
                                                       (int64_t)h.p_dofs.size(), h.d_dinv.p, r, z, nrhs,
-                                                      h.coarse_on ? h.d_cidx.p : nullptr, h.d_zc.p, h.N0, h.dmask());
+                                                      h.coarse_on ? h.d_cidx.p : nullptr, h.d_zc.p, h.N0, h.dmask(),
+                                                      h.ht ? h.d_zg.p : nullptr);
   });
 }
 
@@ -804,6 +959,7 @@ void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStrea
 void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* zold, int op, double* scal, int nrhs,
                     cudaStream_t s) {
   const int64_t N = h.N();
+  ht_potential(h, r, nrhs, s);
   coarse_fork(h, r, nrhs, s);
   op_patch_solves(h, r, nrhs, s);
   coarse_join(h, s);
@@ -811,7 +967,7 @@ void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* z
     dev::k_precond_gather_dot<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(
         N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p, h.d_dinv.p, r, z, zold, h.d_part.p,
         h.d_ticket.p, op, scal, (int64_t)h.p_dofs.size(), h.coarse_on ? h.d_cidx.p : nullptr, h.d_zc.p, h.N0,
-        h.dmask());
+        h.dmask(), h.ht ? h.d_zg.p : nullptr);
   });
 }
 
@@ -980,7 +1136,8 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
 
 constexpr unsigned LOOP_KINDS = (1u << RIESZ_K_APPLY) | (1u << RIESZ_K_APPLY32) | (1u << RIESZ_K_GATHER) |
                                 (1u << RIESZ_K_PATCH_SOLVE) | (1u << RIESZ_K_PRECOND_GATHER) | (1u << RIESZ_K_DOT) |
-                                (1u << RIESZ_K_SCALAR) | (1u << RIESZ_K_UPDATE) | (1u << RIESZ_K_COARSE_APPLY);
+                                (1u << RIESZ_K_SCALAR) | (1u << RIESZ_K_UPDATE) | (1u << RIESZ_K_COARSE_APPLY) |
+                                (1u << RIESZ_K_HT);
 
 bool profiling_loop(const riesz_handle& h) { return h.prof && (h.prof_mask & LOOP_KINDS) != 0u; }
 
@@ -1011,6 +1168,7 @@ void iter_head(riesz_handle& h, int nrhs, cudaStream_t s) {
 std::pair<int64_t, int64_t> add_loop(riesz_handle& h, cudaGraph_t G, int nrhs, bool entry) {
   cudaStream_t cs = h.cap_stream;
   const int64_t l0 = h.launches;
+  const int64_t la0 = h.aux ? h.aux->launches : 0;  // launches of the potential problems count here too
   int64_t pro = 0, body = 0;
   cudaGraphConditionalHandle hc;
   CK(cudaGraphConditionalHandleCreate(&hc, G, entry ? 0u : 1u, cudaGraphCondAssignDefault));
@@ -1057,6 +1215,11 @@ std::pair<int64_t, int64_t> add_loop(riesz_handle& h, cudaGraph_t G, int nrhs, b
   captured(cp.conditional.phGraph_out[0], [&] { iter_head(h, nrhs, cs); iter_tail(h, h.d_xw.p, nrhs, cs); control(); },
            nullptr);
   body = h.launches - l1;
+  if (h.aux) {
+    const int64_t la = h.aux->launches - la0;  // prologue has none: the potential step is in the body only
+    body += la;
+    h.aux->launches = la0;
+  }
   h.launches = l0;  // captured, not launched: counted per executed pass instead
   return {pro, body};
 }
@@ -1418,6 +1581,10 @@ void device_compute(riesz_handle& h, cudaStream_t s) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, s));
+  if (h.aux) {  // the potential problems follow the same vertices
+    CK(cudaMemcpyAsync(h.aux->d_verts.p, h.d_verts.p, h.d_verts.bytes(), cudaMemcpyDeviceToDevice, s));
+    device_compute(*h.aux, s);
+  }
   launch(h, RIESZ_K_GEOM, s, [&] {
     dev::k_geom<<<nblk(C, 128), 128, 0, s>>>(h.space, C, h.d_verts.p, h.d_cells.p, ref_edge_inverse(),
                                               h.opts.alpha, h.opts.beta, h.d_g.p, h.d_jac.p);
@@ -1637,6 +1804,17 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   h.d_pmoff.upload(h.p_moff, s);
   h.d_meta.upload(h.p_meta, s);
   if (h.opts.dirichlet) h.d_dmask.upload(h.dir_mask, s);
+  if (h.ht) {
+    setup_device_impl(*h.aux, s);
+    h.d_gt_ptr.upload(h.gt_ptr, s);
+    h.d_gt_idx.upload(h.gt_idx, s);
+    h.d_gt_sgn.upload(h.gt_sgn, s);
+    h.d_gg_ptr.upload(h.gg_ptr, s);
+    h.d_gg_idx.upload(h.gg_idx, s);
+    h.d_gg_sgn.upload(h.gg_sgn, s);
+    h.d_zcg.alloc((size_t)nrhs * h.aux->mesh.n_interface);
+    h.d_zg.alloc((size_t)nrhs * M.n_interface);
+  }
   if (h.coarse_on) {
     h.d_cw.upload(h.c_w, s);
     h.d_cidx.upload(h.c_idx, s);
@@ -1686,6 +1864,66 @@ void check_dev(const riesz_handle* h) {
   need(h->on_device, "handle has no device state (call riesz_setup_device)", RIESZ_ERR_NO_DEVICE);
 }
 
+// Host part of a handle: reference element, mesh maps and plans.  `internal`
+// handles (the potential problems of the Hiptmair-Toselli decomposition) may
+// have beta = 0.
+riesz_handle* create_handle(int space, int p, int64_t nverts, const double* verts, int64_t ncells,
+                            const int64_t* cells, const riesz_opts& opts, bool internal) {
+  need(space >= 0 && space <= 2, "space must be RIESZ_H1, RIESZ_HCURL or RIESZ_HDIV");
+  need(p >= 1 && p <= 10, "degree p must be in 1..10");
+  need(verts && cells && nverts > 0 && ncells > 0, "empty mesh", RIESZ_ERR_BAD_MESH);
+  auto t0 = std::chrono::steady_clock::now();
+  auto h = std::make_unique<riesz_handle>();
+  h->space = space;
+  h->p = p;
+  h->opts = opts;
+  need(h->opts.rtol > 0 && h->opts.maxit >= 0 && h->opts.nrhs_max >= 1 && h->opts.nrhs_max <= 64, "bad options");
+  need(h->opts.precond_precision == 0 || h->opts.precond_precision == 1, "bad precond_precision");
+  need(h->opts.apply_mode == 0 || h->opts.apply_mode == 1, "bad apply_mode");
+  need(h->opts.alpha > 0 && (h->opts.beta > 0 || (internal && h->opts.beta == 0)) && std::isfinite(h->opts.alpha) &&
+           std::isfinite(h->opts.beta),
+       "alpha and beta must be positive and finite");
+  need(h->opts.apply_precision == 0 || h->opts.apply_precision == 1, "bad apply_precision");
+  need(h->opts.loop == RIESZ_LOOP_HOST || h->opts.loop == RIESZ_LOOP_GRAPH, "bad loop");
+  need(h->opts.autotune >= 0 && h->opts.autotune <= 2, "bad autotune");
+  need(h->opts.coarse == 0 || h->opts.coarse == 1, "bad coarse");
+  need(h->opts.dirichlet == 0 || h->opts.dirichlet == 1, "bad dirichlet");
+  need(h->opts.decomposition == RIESZ_DECOMP_VERTEX_STAR || h->opts.decomposition == RIESZ_DECOMP_HT,
+       "bad decomposition");
+  need(h->opts.decomposition != RIESZ_DECOMP_HT || (space == RIESZ_HCURL && !h->opts.dirichlet),
+       "the Hiptmair-Toselli decomposition is for H(curl) without Dirichlet conditions");
+  for (int64_t i = 0; i < nverts * 3; ++i)
+    need(std::isfinite(verts[i]), "non-finite vertex coordinate", RIESZ_ERR_BAD_MESH);
+  h->verts.assign(verts, verts + nverts * 3);
+  try {
+    h->ref = &reference_element(space, p);
+    h->refcg = &reference_element(RIESZ_H1, p);
+    h->mesh = build_mesh(*h->ref, nverts, ncells, cells);
+    h->meshcg = (space == RIESZ_H1) ? h->mesh : build_mesh(*h->refcg, nverts, ncells, cells);
+  } catch (const Err&) {
+    throw;
+  } catch (const std::exception& e) {
+    throw Err(RIESZ_ERR_BAD_MESH, e.what());
+  }
+  if (h->opts.dirichlet) plan_dirichlet(*h);
+  if (h->opts.decomposition == RIESZ_DECOMP_HT) plan_ht(*h);
+  build_plans(*h);
+  plan_coarse(*h);
+  if (h->ht) {  // potential problems: CG_p on the same mesh with a = beta (grad, grad), vertex stars
+    riesz_opts ao = h->opts;
+    ao.alpha = h->opts.beta;
+    ao.beta = 0.0;
+    ao.coarse = 0;
+    ao.dirichlet = 0;
+    ao.decomposition = RIESZ_DECOMP_VERTEX_STAR;
+    ao.apply_precision = RIESZ_PREC_FP64;
+    ao.apply_mode = RIESZ_APPLY_ELEMENT;
+    h->aux = create_handle(RIESZ_H1, p, nverts, verts, ncells, cells, ao, true);
+  }
+  h->setup_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return h.release();
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1731,6 +1969,7 @@ void riesz_default_opts(riesz_opts* o) {
   o->autotune = 1;
   o->coarse = 1;
   o->dirichlet = 0;
+  o->decomposition = RIESZ_DECOMP_VERTEX_STAR;
 }
 
 const char* riesz_last_error(void) { return g_err.c_str(); }
@@ -1740,43 +1979,10 @@ int riesz_create(int space, int p, int64_t nverts, const double* verts, int64_t 
   return guarded([&] {
     need(out != nullptr, "out is NULL");
     *out = nullptr;
-    need(space >= 0 && space <= 2, "space must be RIESZ_H1, RIESZ_HCURL or RIESZ_HDIV");
-    need(p >= 1 && p <= 10, "degree p must be in 1..10");
-    need(verts && cells && nverts > 0 && ncells > 0, "empty mesh", RIESZ_ERR_BAD_MESH);
-    auto t0 = std::chrono::steady_clock::now();
-    auto h = std::make_unique<riesz_handle>();
-    h->space = space;
-    h->p = p;
-    riesz_default_opts(&h->opts);
-    if (opts) h->opts = *opts;
-    need(h->opts.rtol > 0 && h->opts.maxit >= 0 && h->opts.nrhs_max >= 1 && h->opts.nrhs_max <= 64, "bad options");
-    need(h->opts.precond_precision == 0 || h->opts.precond_precision == 1, "bad precond_precision");
-    need(h->opts.apply_mode == 0 || h->opts.apply_mode == 1, "bad apply_mode");
-    need(h->opts.alpha > 0 && h->opts.beta > 0 && std::isfinite(h->opts.alpha) && std::isfinite(h->opts.beta),
-         "alpha and beta must be positive and finite");
-    need(h->opts.apply_precision == 0 || h->opts.apply_precision == 1, "bad apply_precision");
-    need(h->opts.loop == RIESZ_LOOP_HOST || h->opts.loop == RIESZ_LOOP_GRAPH, "bad loop");
-    need(h->opts.autotune >= 0 && h->opts.autotune <= 2, "bad autotune");
-    need(h->opts.coarse == 0 || h->opts.coarse == 1, "bad coarse");
-    need(h->opts.dirichlet == 0 || h->opts.dirichlet == 1, "bad dirichlet");
-    for (int64_t i = 0; i < nverts * 3; ++i)
-      need(std::isfinite(verts[i]), "non-finite vertex coordinate", RIESZ_ERR_BAD_MESH);
-    h->verts.assign(verts, verts + nverts * 3);
-    try {
-      h->ref = &reference_element(space, p);
-      h->refcg = &reference_element(RIESZ_H1, p);
-      h->mesh = build_mesh(*h->ref, nverts, ncells, cells);
-      h->meshcg = (space == RIESZ_H1) ? h->mesh : build_mesh(*h->refcg, nverts, ncells, cells);
-    } catch (const Err&) {
-      throw;
-    } catch (const std::exception& e) {
-      throw Err(RIESZ_ERR_BAD_MESH, e.what());
-    }
-    if (h->opts.dirichlet) plan_dirichlet(*h);
-    build_plans(*h);
-    plan_coarse(*h);
-    h->setup_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    *out = h.release();
+    riesz_opts o;
+    riesz_default_opts(&o);
+    if (opts) o = *opts;
+    *out = create_handle(space, p, nverts, verts, ncells, cells, o, false);
   });
 }
 
@@ -2029,12 +2235,15 @@ int riesz_tuning(const riesz_handle* h, int* out) {
 int riesz_profile(riesz_handle* h, int enable) {
   return guarded([&] {
     need(h != nullptr, "null handle");
-    if (!h->prof_pending.empty()) prof_collect(*h);
-    h->prof = enable != 0;
-    h->prof_mask = (unsigned)enable;
-    for (int k = 0; k < RIESZ_NKIND; ++k) {
-      h->prof_ms[k] = 0.0;
-      h->prof_cnt[k] = 0;
+    for (riesz_handle* x : {h, h->aux}) {  // the potential problems' kernels are reported with the handle's
+      if (!x) continue;
+      if (!x->prof_pending.empty()) prof_collect(*x);
+      x->prof = enable != 0;
+      x->prof_mask = (unsigned)enable;
+      for (int k = 0; k < RIESZ_NKIND; ++k) {
+        x->prof_ms[k] = 0.0;
+        x->prof_cnt[k] = 0;
+      }
     }
   });
 }
@@ -2043,9 +2252,10 @@ int riesz_profile_read(riesz_handle* h, double* ms, int64_t* counts) {
   return guarded([&] {
     need(h != nullptr, "null handle");
     prof_collect(*h);
+    if (h->aux) prof_collect(*h->aux);
     for (int k = 0; k < RIESZ_NKIND; ++k) {
-      if (ms) ms[k] = h->prof_ms[k];
-      if (counts) counts[k] = h->prof_cnt[k];
+      if (ms) ms[k] = h->prof_ms[k] + (h->aux ? h->aux->prof_ms[k] : 0.0);
+      if (counts) counts[k] = h->prof_cnt[k] + (h->aux ? h->aux->prof_cnt[k] : 0);
     }
   });
 }
@@ -2058,8 +2268,8 @@ int riesz_stats(const riesz_handle* h, double* out) {
     out[2] = (double)h->device_bytes();
     out[3] = (double)(h->factor_entries + h->dinv_entries) * (h->opts.precond_precision == RIESZ_PREC_FP32 ? 4.0 : 8.0);
     out[4] = h->last_iters;
-    out[5] = (double)h->launches;
-    out[6] = h->chol_flops;
+    out[5] = (double)(h->launches + (h->aux ? h->aux->launches : 0));
+    out[6] = h->chol_flops + (h->aux ? h->aux->chol_flops : 0.0);
     const double fb = h->opts.precond_precision == RIESZ_PREC_FP32 ? 4.0 : 8.0;
     out[7] = 2.0 * (double)(h->factor_entries + h->dinv_entries) * fb + (double)h->p_dofs.size() * 20.0;
   });

@@ -18,9 +18,10 @@ SPACES = {"CG": H1, "H1": H1, "N1curl": HCURL, "HCURL": HCURL, "RT": HDIV, "HDIV
 PREC_FP64, PREC_FP32 = 0, 1
 APPLY_MATRIX_FREE, APPLY_ELEMENT = 0, 1
 LOOP_HOST, LOOP_GRAPH = 0, 1
+DECOMP_VERTEX_STAR, DECOMP_HT = 0, 1
 
 KINDS = ["geom", "elem", "diag", "assemble", "cholesky", "to_f32", "apply", "gather", "patch_solve",
-         "precond_gather", "dot", "scalar", "update", "load", "apply32", "coarse", "coarse_apply"]
+         "precond_gather", "dot", "scalar", "update", "load", "apply32", "coarse", "coarse_apply", "ht"]
 
 ERRORS = {1: "INVALID_ARG", 2: "BAD_MESH", 3: "OOM", 4: "NOT_CONVERGED", 5: "NONFINITE", 6: "CUDA",
           7: "INTERNAL", 8: "NO_DEVICE"}
@@ -36,7 +37,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precond_precision", ctypes.c_int), ("apply_mode", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("nrhs_max", ctypes.c_int), ("alpha", ctypes.c_double),
                 ("beta", ctypes.c_double), ("apply_precision", ctypes.c_int), ("loop", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("coarse", ctypes.c_int), ("dirichlet", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("coarse", ctypes.c_int), ("dirichlet", ctypes.c_int),
+                ("decomposition", ctypes.c_int)]
 
 
 _lib = None

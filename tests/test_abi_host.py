@@ -148,3 +148,12 @@ def test_dirichlet_map_bit_exact(lib, space, p):
         assert np.array_equal(dofs[off[vv]:off[vv + 1]], exp[~fixed[exp]])
     s0 = rz.Riesz(space, p, v, c, device=False)
     assert s0.dirichlet_map().sum() == 0
+
+
+def test_ht_validation(lib):
+    v, c = kuhn_mesh(2)
+    rz.Riesz("N1curl", 2, v, c, device=False, decomposition=rz.DECOMP_HT)
+    for space, kw in [("RT", {}), ("CG", {}), ("N1curl", dict(dirichlet=1))]:
+        with pytest.raises(rz.RieszError) as e:
+            rz.Riesz(space, 2, v, c, device=False, decomposition=rz.DECOMP_HT, **kw)
+        assert e.value.code == 1

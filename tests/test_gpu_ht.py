@@ -1,0 +1,78 @@
+"""Hiptmair-Toselli decomposition for H(curl) (Eq. (6.19)) against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import assemble as asm
+from oracle.mesh import MeshDofs
+from oracle.refelem import reference_element
+from paper_2506_17406_gb300 import riesz as rz
+from paper_2506_17406_gb300.inputs import kuhn_mesh, normal_coeffs, normal_vector
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def setup(p, n, amp=0.1, seed=3, alpha=1.0, beta=1.0):
+    verts, cells = kuhn_mesh(n, amp, seed)
+    rn, rc = reference_element("N1curl", p), reference_element("CG", p)
+    mn, mc = MeshDofs(verts, cells, rn), MeshDofs(verts, cells, rc)
+    A = asm.assemble(mn, asm.element_matrices(rn, verts, cells, alpha=alpha, beta=beta))
+    return verts, cells, mn, mc, A
+
+
+@pytest.mark.parametrize("p,n,alpha,beta", [(2, 3, 1.0, 1.0), (3, 3, 1.0, 1.0), (4, 2, 1.0, 1.0),
+                                             (3, 3, 2.0, 0.5), (3, 3, 1e3, 1.0)])
+def test_ht_precond_matches_oracle(p, n, alpha, beta):
+    """The potential problems carry beta (G^T A G = beta times the CG stiffness), the edge stars
+    and W^1 both coefficients."""
+    verts, cells, mn, mc, A = setup(p, n, alpha=alpha, beta=beta)
+    s = rz.Riesz("N1curl", p, verts, cells, decomposition=rz.DECOMP_HT, alpha=alpha, beta=beta)
+    P = asm.HTPreconditioner(A, mn, mc)
+    r = normal_vector(s.N, 5)
+    z = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    s.precond(dev(r), z)
+    ze = P.apply(r)
+    A0 = A.tocsr()[P.W][:, P.W].toarray()
+    tol = max(1e-10 * max(1.0, alpha), 64.0 * np.linalg.cond(A0) * 2.0 ** -24)
+    assert np.abs(host(z) - ze).max() <= tol * np.abs(ze).max()
+
+
+@pytest.mark.parametrize("prec", [rz.PREC_FP64, rz.PREC_FP32])
+@pytest.mark.parametrize("p,n", [(3, 3), (2, 4)])
+def test_ht_solve_matches_direct_solve(p, n, prec):
+    verts, cells, mn, mc, A = setup(p, n)
+    s = rz.Riesz("N1curl", p, verts, cells, decomposition=rz.DECOMP_HT, precond_precision=prec, rtol=1e-10,
+                 maxit=3000)
+    b = normal_vector(s.N, 8)
+    x = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    it, rr, rc = s.solve(dev(b), x)
+    assert rc == 0
+    xh = host(x)
+    assert np.linalg.norm(b - A @ xh) <= 1.001e-10 * np.linalg.norm(b)
+    xe = asm.direct_solve(A, b)
+    assert np.linalg.norm(xh - xe) <= 1e-7 * np.linalg.norm(xe)
+    _, it_o, _ = asm.pcg(A, b, asm.HTPreconditioner(A, mn, mc).apply, rtol=1e-10)
+    assert int(it[0]) <= it_o + 3
+
+
+def test_ht_graph_loop_equals_host_loop_and_lockstep():
+    verts, cells, mn, mc, A = setup(3, 3)
+    out = []
+    for loop in (rz.LOOP_GRAPH, rz.LOOP_HOST):
+        s = rz.Riesz("N1curl", 3, verts, cells, decomposition=rz.DECOMP_HT, loop=loop, nrhs_max=3,
+                     precond_precision=rz.PREC_FP32, rtol=1e-10)
+        B = normal_coeffs((3, s.N), 4)
+        X = torch.zeros((3, s.N), dtype=torch.float64, device="cuda")
+        it, rr, rc = s.solve(dev(B), X, nrhs=3)
+        assert rc == 0 and np.all(rr <= 1e-10)
+        out.append((host(X), it))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
