@@ -55,6 +55,9 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, the profiling recipe's nominal f
 CPU_SAMPLE_N = 3
 
 
+DECOMPOSITIONS = {"vertex_star": 0, "ht": 1, "edge_star": 2}  # riesz_opts.decomposition
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -73,9 +76,10 @@ def parse():
                     help="batched run: seeded mixed systems solved in one graph launch per HBM wave")
     ap.add_argument("--systems", type=int, default=64)
     ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
-    ap.add_argument("--decomposition", default="vertex_star", choices=["vertex_star", "ht"],
-                    help="H(curl) subspace decomposition: vertex stars (Eq. 6.11) or Hiptmair-Toselli "
-                         "edge stars + gradient potential problems (Eq. 6.19)")
+    ap.add_argument("--decomposition", default="vertex_star", choices=sorted(DECOMPOSITIONS),
+                    help="subspace decomposition: vertex stars (Eq. 6.11), Hiptmair-Toselli edge stars + "
+                         "gradient potential problems for H(curl) (Eq. 6.19), or PAFW_1 edge stars for "
+                         "H(div) (Eq. 6.24)")
     ap.add_argument("--pcg-loop", default="graph", choices=["graph", "host"],
                     help="device-driven (CUDA graph) or host-driven PCG iterations; same kernels, same results")
     ap.add_argument("--p-sweep", action="store_true",
@@ -468,7 +472,7 @@ def main():
         """A solver handle for the workload and its step closure (device setup + load + solve)."""
         s = rz.Riesz(wl["space"], wl["p"], verts, cells, precond_precision=prec, nrhs_max=nrhs,
                      apply_precision=a32, loop=rz.LOOP_HOST if args.pcg_loop == "host" else rz.LOOP_GRAPH,
-                     decomposition=rz.DECOMP_HT if args.decomposition == "ht" else rz.DECOMP_VERTEX_STAR)
+                     decomposition=DECOMPOSITIONS[args.decomposition])
         if nrhs == 1:  # f with N(0,1) CG_p coefficients per Cartesian component, b = (f, phi)
             fcg_h = normal_coeffs((ncomp, s.n_cg), 2 + rank)
         else:  # the paper's random right-hand side vectors (Section 7.1), one per RHS

@@ -66,7 +66,7 @@ enum {
 enum { RIESZ_PREC_FP64 = 0, RIESZ_PREC_FP32 = 1 };
 enum { RIESZ_APPLY_MATRIX_FREE = 0, RIESZ_APPLY_ELEMENT = 1 };
 enum { RIESZ_LOOP_HOST = 0, RIESZ_LOOP_GRAPH = 1 };
-enum { RIESZ_DECOMP_VERTEX_STAR = 0, RIESZ_DECOMP_HT = 1 };
+enum { RIESZ_DECOMP_VERTEX_STAR = 0, RIESZ_DECOMP_HT = 1, RIESZ_DECOMP_EDGE_STAR = 2 };
 
 typedef struct {
   /* Precision of the stored patch Cholesky factors and of the triangular
@@ -151,7 +151,12 @@ typedef struct {
      Eq. (5.3).  Interior Jacobi and W^k as for the vertex stars.  The
      patches are much smaller (Ned1_6: 431-DOF potential and 121-DOF edge
      problems instead of 1164-DOF vertex stars), so the FP64 factorisation
-     is far cheaper; PCG takes somewhat more iterations. */
+     is far cheaper; PCG takes somewhat more iterations.
+     RIESZ_DECOMP_EDGE_STAR (H(div) only): PAFW_1 of Eq. (6.24), exact solves
+     on the interface DOFs of every edge star (the DOFs of the faces
+     containing the edge; with Dirichlet conditions the free ones), interior
+     Jacobi and W^k as above.  RT_8: 216-DOF edge problems instead of
+     1296-DOF vertex stars. */
   int decomposition;
 } riesz_opts;
 
@@ -185,10 +190,17 @@ int riesz_dof_map(const riesz_handle* h, int32_t* cell_dofs);
    (opts.dirichlet), 0 otherwise. */
 int riesz_dirichlet_map(const riesz_handle* h, uint8_t* mask);
 
-/* offsets: host [nverts + 1]; dofs: host [offsets[nverts]] (query the size by
-   passing dofs == NULL).  Patch of vertex v = dofs[offsets[v] .. offsets[v+1]),
-   increasing global DOF indices (without the Dirichlet DOFs when
-   opts.dirichlet is set). */
+/* *npatches = the number of stars the patches are taken over: the mesh
+   vertices for RIESZ_DECOMP_VERTEX_STAR, the mesh edges (in the order of
+   increasing vertex pairs) for RIESZ_DECOMP_HT and RIESZ_DECOMP_EDGE_STAR. */
+int riesz_patch_count(const riesz_handle* h, int64_t* npatches);
+
+/* offsets: host [npatches + 1]; dofs: host [offsets[npatches]] (query the
+   size by passing dofs == NULL).  Patch of star s (vertex or edge, see
+   riesz_patch_count) = dofs[offsets[s] .. offsets[s+1]), increasing global
+   DOF indices (without the Dirichlet DOFs when opts.dirichlet is set).  For
+   RIESZ_DECOMP_HT these are the edge-star patches of this handle; the
+   potential problems live on the CG_p vertex stars. */
 int riesz_patch_map(const riesz_handle* h, int64_t* offsets, int32_t* dofs);
 
 /* Tabulate the reference basis of (space, p) at npts points of the reference

@@ -227,11 +227,11 @@ class DirichletPreconditioner:
     """The one- or two-level preconditioner of the free DOFs (patches and W^k without the fixed DOFs)
     with the identity on the fixed DOFs."""
 
-    def __init__(self, A, md, D, two_level=True, weight=0.5):
+    def __init__(self, A, md, D, two_level=True, weight=0.5, patches=None):
         self.D = np.asarray(D)
         fixed = np.zeros(md.ndofs, dtype=bool)
         fixed[self.D] = True
-        patches = [p[~fixed[p]] for p in md.patches()]
+        patches = [p[~fixed[p]] for p in (md.patches() if patches is None else patches)]
         Ac = constrained(A, self.D)
         if two_level:
             self.P = TwoLevelPreconditioner(Ac, md, patches, weight, W=coarse_dofs(md)[~fixed[coarse_dofs(md)]])
@@ -286,6 +286,27 @@ def edge_star_type1_dofs(md_ned, md_cg):
         for f in faces_of.get((a, b), []):
             d += [off_f + nf_d * f + m for m in range(nfI)]
         out.append(np.array(sorted(d), dtype=np.int64))
+    return out
+
+
+def edge_star_dofs(md, exclude=None):
+    """Per edge E: the interface DOFs of E and of every face containing E, i.e. the interface functions
+    supported in the star of E (the edge-star subspaces X^k_Gamma|_{star E} of the PAFW_1 decomposition,
+    Eq. (6.24) for H(div), where only the face DOFs are present), sorted.  DOFs in `exclude` (fixed
+    Dirichlet DOFs) are left out."""
+    ne_d, nf_d = md.per_entity[1], md.per_entity[2]
+    off_e, off_f = md._offsets[1], md._offsets[2]
+    drop = set() if exclude is None else set(int(d) for d in exclude)
+    faces_of = {}
+    for f, tri in enumerate(md.faces.tolist()):
+        for a, b in ((tri[0], tri[1]), (tri[0], tri[2]), (tri[1], tri[2])):
+            faces_of.setdefault((a, b), []).append(f)
+    out = []
+    for e, (a, b) in enumerate(md.edges.tolist()):
+        d = [off_e + ne_d * e + m for m in range(ne_d)]
+        for f in faces_of.get((a, b), []):
+            d += [off_f + nf_d * f + m for m in range(nf_d)]
+        out.append(np.array(sorted(x for x in d if x not in drop), dtype=np.int64))
     return out
 
 

@@ -99,8 +99,10 @@ struct riesz_handle {
   // (CG DOF, sign) (Eq. (5.3))
   bool ht = false;
   riesz_handle* aux = nullptr;
-  std::vector<int64_t> ht_star_ptr;
-  std::vector<int32_t> ht_star_dofs;
+  // edge-star patches (Hiptmair-Toselli for H(curl), PAFW_1 for H(div)): CSR edge -> sorted DOFs
+  bool edge_star = false;
+  std::vector<int64_t> es_ptr;
+  std::vector<int32_t> es_dofs;
   std::vector<int64_t> gt_ptr, gg_ptr;
   std::vector<int32_t> gt_idx, gg_idx;
   std::vector<float> gt_sgn, gg_sgn;
@@ -497,6 +499,38 @@ int64_t edge_index(const MeshMaps& M, int32_t a, int32_t b) {
   return lo;
 }
 
+// Edge-star patches: per edge E the first `take_e` DOFs of E and the first
+// `take_f` DOFs of every face containing E, without fixed Dirichlet DOFs,
+// sorted.  All DOFs of both (take_e = 0 edge DOFs of RT_p, all face DOFs) give
+// the interface functions supported in the star of E: the PAFW_1 subspaces of
+// Eq. (6.24) for H(div).
+void plan_edge_stars(riesz_handle& h, int take_e, int take_f) {
+  const MeshMaps& M = h.mesh;
+  const int ne_d = M.per_entity[1], nf_d = M.per_entity[2];
+  std::vector<std::vector<int32_t>> faces_of(M.nedges);
+  for (int64_t f = 0; f < M.nfaces; ++f) {
+    const int32_t* v = &M.faces[f * 3];
+    faces_of[edge_index(M, v[0], v[1])].push_back((int32_t)f);
+    faces_of[edge_index(M, v[0], v[2])].push_back((int32_t)f);
+    faces_of[edge_index(M, v[1], v[2])].push_back((int32_t)f);
+  }
+  auto keep = [&](int64_t d) { return h.dir_mask.empty() || !h.dir_mask[d]; };
+  h.es_ptr.assign(1, 0);
+  h.es_dofs.clear();
+  for (int64_t e = 0; e < M.nedges; ++e) {
+    std::vector<int32_t> d;
+    for (int m = 0; m < take_e; ++m)
+      if (keep(M.off[1] + (int64_t)ne_d * e + m)) d.push_back((int32_t)(M.off[1] + (int64_t)ne_d * e + m));
+    for (int32_t f : faces_of[e])
+      for (int m = 0; m < take_f; ++m)
+        if (keep(M.off[2] + (int64_t)nf_d * f + m)) d.push_back((int32_t)(M.off[2] + (int64_t)nf_d * f + m));
+    std::sort(d.begin(), d.end());
+    h.es_dofs.insert(h.es_dofs.end(), d.begin(), d.end());
+    h.es_ptr.push_back((int64_t)h.es_dofs.size());
+  }
+  h.edge_star = true;
+}
+
 // Hiptmair-Toselli decomposition of Eq. (6.19) for H(curl): per edge L the
 // Whitney DOF of L and the type-I DOFs of every face containing L (the
 // interface DOFs of X^{1,I} on the star of L; inside a face the type-I DOFs
@@ -513,23 +547,7 @@ void plan_ht(riesz_handle& h) {
   const int nfI = nf_d - cf;
   if (ne_d != ce + 1 || nfI < 0 || Mc.per_entity[0] != 1)
     throw Err(RIESZ_ERR_INTERNAL, "gradient map: unexpected DOF counts");
-  std::vector<std::vector<int32_t>> faces_of(M.nedges);
-  for (int64_t f = 0; f < M.nfaces; ++f) {
-    const int32_t* v = &M.faces[f * 3];
-    faces_of[edge_index(M, v[0], v[1])].push_back((int32_t)f);
-    faces_of[edge_index(M, v[0], v[2])].push_back((int32_t)f);
-    faces_of[edge_index(M, v[1], v[2])].push_back((int32_t)f);
-  }
-  h.ht_star_ptr.assign(1, 0);
-  h.ht_star_dofs.clear();
-  for (int64_t e = 0; e < M.nedges; ++e) {
-    std::vector<int32_t> d{(int32_t)(M.off[1] + (int64_t)ne_d * e)};
-    for (int32_t f : faces_of[e])
-      for (int m = 0; m < nfI; ++m) d.push_back((int32_t)(M.off[2] + (int64_t)nf_d * f + m));
-    std::sort(d.begin(), d.end());
-    h.ht_star_dofs.insert(h.ht_star_dofs.end(), d.begin(), d.end());
-    h.ht_star_ptr.push_back((int64_t)h.ht_star_dofs.size());
-  }
+  plan_edge_stars(h, 1, nfI);
   // G^T rows: CG interface DOF -> (Ned1 DOF, sign)
   const int64_t ncif = Mc.n_interface;
   std::vector<std::vector<std::pair<int32_t, float>>> gt(ncif);
@@ -729,14 +747,14 @@ void build_plans(riesz_handle& h) {
   h.tile_ops = 0;
   h.chol_flops = 0.0;
   int64_t foff = 0, dioff = 0;
-  if (h.ht) {  // Hiptmair-Toselli: type-I edge stars instead of vertex stars
-    std::vector<int64_t> eorder(h.ht_star_ptr.size() - 1);
+  if (h.edge_star) {  // edge stars instead of vertex stars
+    std::vector<int64_t> eorder(h.es_ptr.size() - 1);
     for (size_t e = 0; e < eorder.size(); ++e) eorder[e] = (int64_t)e;
     std::stable_sort(eorder.begin(), eorder.end(), [&](int64_t a, int64_t b) {
-      return (h.ht_star_ptr[a + 1] - h.ht_star_ptr[a]) > (h.ht_star_ptr[b + 1] - h.ht_star_ptr[b]);
+      return (h.es_ptr[a + 1] - h.es_ptr[a]) > (h.es_ptr[b + 1] - h.es_ptr[b]);
     });
     for (int64_t e : eorder) {
-      const int np = (int)(h.ht_star_ptr[e + 1] - h.ht_star_ptr[e]);
+      const int np = (int)(h.es_ptr[e + 1] - h.es_ptr[e]);
       if (np == 0) continue;
       if (np > 32 * dev::MAXNB) throw Err(RIESZ_ERR_INVALID_ARG, "patch larger than 4096 DOFs");
       const int32_t a = M.edges[e * 2], b = M.edges[e * 2 + 1];
@@ -751,7 +769,7 @@ void build_plans(riesz_handle& h) {
       }
       double center[3];
       for (int q = 0; q < 3; ++q) center[q] = 0.5 * (h.verts[(size_t)a * 3 + q] + h.verts[(size_t)b * 3 + q]);
-      plan_patch(h, &h.ht_star_dofs[h.ht_star_ptr[e]], np, cells.data(), (int64_t)cells.size(), center, foff, dioff);
+      plan_patch(h, &h.es_dofs[h.es_ptr[e]], np, cells.data(), (int64_t)cells.size(), center, foff, dioff);
     }
   } else {
     for (int64_t v : order) {
@@ -1888,10 +1906,12 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
   need(h->opts.autotune >= 0 && h->opts.autotune <= 2, "bad autotune");
   need(h->opts.coarse == 0 || h->opts.coarse == 1, "bad coarse");
   need(h->opts.dirichlet == 0 || h->opts.dirichlet == 1, "bad dirichlet");
-  need(h->opts.decomposition == RIESZ_DECOMP_VERTEX_STAR || h->opts.decomposition == RIESZ_DECOMP_HT,
+  need(h->opts.decomposition >= RIESZ_DECOMP_VERTEX_STAR && h->opts.decomposition <= RIESZ_DECOMP_EDGE_STAR,
        "bad decomposition");
   need(h->opts.decomposition != RIESZ_DECOMP_HT || (space == RIESZ_HCURL && !h->opts.dirichlet),
        "the Hiptmair-Toselli decomposition is for H(curl) without Dirichlet conditions");
+  need(h->opts.decomposition != RIESZ_DECOMP_EDGE_STAR || space == RIESZ_HDIV,
+       "the edge-star decomposition (PAFW_1) is for H(div)");
   for (int64_t i = 0; i < nverts * 3; ++i)
     need(std::isfinite(verts[i]), "non-finite vertex coordinate", RIESZ_ERR_BAD_MESH);
   h->verts.assign(verts, verts + nverts * 3);
@@ -1907,6 +1927,7 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
   }
   if (h->opts.dirichlet) plan_dirichlet(*h);
   if (h->opts.decomposition == RIESZ_DECOMP_HT) plan_ht(*h);
+  if (h->opts.decomposition == RIESZ_DECOMP_EDGE_STAR) plan_edge_stars(*h, 0, h->mesh.per_entity[2]);
   build_plans(*h);
   plan_coarse(*h);
   if (h->ht) {  // potential problems: CG_p on the same mesh with a = beta (grad, grad), vertex stars
@@ -2020,11 +2041,20 @@ int riesz_dof_map(const riesz_handle* h, int32_t* cell_dofs) {
   });
 }
 
+int riesz_patch_count(const riesz_handle* h, int64_t* npatches) {
+  return guarded([&] {
+    need(h != nullptr && npatches != nullptr, "null argument");
+    *npatches = h->edge_star ? (int64_t)h->es_ptr.size() - 1 : (int64_t)h->mesh.patch_ptr.size() - 1;
+  });
+}
+
 int riesz_patch_map(const riesz_handle* h, int64_t* offsets, int32_t* dofs) {
   return guarded([&] {
     need(h != nullptr && offsets != nullptr, "null argument");
-    std::memcpy(offsets, h->mesh.patch_ptr.data(), h->mesh.patch_ptr.size() * sizeof(int64_t));
-    if (dofs) std::memcpy(dofs, h->mesh.patch_dofs.data(), h->mesh.patch_dofs.size() * sizeof(int32_t));
+    const std::vector<int64_t>& ptr = h->edge_star ? h->es_ptr : h->mesh.patch_ptr;
+    const std::vector<int32_t>& d = h->edge_star ? h->es_dofs : h->mesh.patch_dofs;
+    std::memcpy(offsets, ptr.data(), ptr.size() * sizeof(int64_t));
+    if (dofs) std::memcpy(dofs, d.data(), d.size() * sizeof(int32_t));
   });
 }
 

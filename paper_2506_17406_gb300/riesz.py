@@ -18,7 +18,7 @@ SPACES = {"CG": H1, "H1": H1, "N1curl": HCURL, "HCURL": HCURL, "RT": HDIV, "HDIV
 PREC_FP64, PREC_FP32 = 0, 1
 APPLY_MATRIX_FREE, APPLY_ELEMENT = 0, 1
 LOOP_HOST, LOOP_GRAPH = 0, 1
-DECOMP_VERTEX_STAR, DECOMP_HT = 0, 1
+DECOMP_VERTEX_STAR, DECOMP_HT, DECOMP_EDGE_STAR = 0, 1, 2
 
 KINDS = ["geom", "elem", "diag", "assemble", "cholesky", "to_f32", "apply", "gather", "patch_solve",
          "precond_gather", "dot", "scalar", "update", "load", "apply32", "coarse", "coarse_apply", "ht"]
@@ -55,6 +55,7 @@ _SIGS = {
     "riesz_num_cg_dofs": (_I, [_P, ctypes.POINTER(_I64)]),
     "riesz_ref_info": (_I, [_P, _P]),
     "riesz_dof_map": (_I, [_P, _P]),
+    "riesz_patch_count": (_I, [_P, _P]),
     "riesz_patch_map": (_I, [_P, _P, _P]),
     "riesz_ref_tabulate": (_I, [_I, _I, _I64, _P, _P, _P]),
     "riesz_setup_device": (_I, [_P, _P]),
@@ -204,7 +205,10 @@ class Riesz:
         return out
 
     def patch_map(self):
-        off = np.zeros(self.nverts + 1, dtype=np.int64)
+        """(offsets, dofs) of the patches: one per vertex (vertex stars) or per edge (edge stars)."""
+        cnt = np.zeros(1, dtype=np.int64)
+        _check(self.lib.riesz_patch_count(self.h, _ptr(cnt)))
+        off = np.zeros(int(cnt[0]) + 1, dtype=np.int64)
         _check(self.lib.riesz_patch_map(self.h, _ptr(off), None))
         dofs = np.zeros(int(off[-1]), dtype=np.int32)
         _check(self.lib.riesz_patch_map(self.h, _ptr(off), _ptr(dofs)))

@@ -157,3 +157,30 @@ def test_ht_validation(lib):
         with pytest.raises(rz.RieszError) as e:
             rz.Riesz(space, 2, v, c, device=False, decomposition=rz.DECOMP_HT, **kw)
         assert e.value.code == 1
+    rz.Riesz("RT", 2, v, c, device=False, decomposition=rz.DECOMP_EDGE_STAR)
+    rz.Riesz("RT", 2, v, c, device=False, decomposition=rz.DECOMP_EDGE_STAR, dirichlet=1)
+    for space in ("CG", "N1curl"):
+        with pytest.raises(rz.RieszError) as e:
+            rz.Riesz(space, 2, v, c, device=False, decomposition=rz.DECOMP_EDGE_STAR)
+        assert e.value.code == 1
+    with pytest.raises(rz.RieszError):
+        rz.Riesz("RT", 2, v, c, device=False, decomposition=3)
+
+
+@pytest.mark.parametrize("dirichlet", [0, 1])
+def test_edge_star_patches_match_oracle(lib, dirichlet):
+    """The library's H(div) edge-star patches (Eq. (6.24)) are the oracle's edge-star DOF sets, bit-exact,
+    with the fixed Dirichlet DOFs left out."""
+    from oracle import assemble as asm
+    from oracle.mesh import MeshDofs
+    from oracle.refelem import reference_element
+    v, c = kuhn_mesh(2, 0.1, 3)
+    h = rz.Riesz("RT", 3, v, c, device=False, decomposition=rz.DECOMP_EDGE_STAR, dirichlet=dirichlet)
+    off, dofs = h.patch_map()
+    md = MeshDofs(v, c, reference_element("RT", 3))
+    D = asm.dirichlet_dofs(md) if dirichlet else None
+    exp = asm.edge_star_dofs(md, exclude=D)
+    assert len(off) == len(md.edges) + 1 == len(exp) + 1
+    for e, q in enumerate(exp):
+        assert np.array_equal(dofs[off[e]:off[e + 1]], q)
+    assert dirichlet == int(any(len(q) == 0 for q in exp))

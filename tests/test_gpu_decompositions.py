@@ -1,4 +1,5 @@
-"""Hiptmair-Toselli decomposition for H(curl) (Eq. (6.19)) against the oracle."""
+"""The finer space decompositions against the oracle: Hiptmair-Toselli for H(curl) (Eq. (6.19)) and
+PAFW_1 edge stars for H(div) (Eq. (6.24))."""
 import numpy as np
 import pytest
 
@@ -76,3 +77,56 @@ def test_ht_graph_loop_equals_host_loop_and_lockstep():
         assert rc == 0 and np.all(rr <= 1e-10)
         out.append((host(X), it))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def setup_rt(p, n, amp=0.1, seed=3, alpha=1.0, beta=1.0):
+    verts, cells = kuhn_mesh(n, amp, seed)
+    ref = reference_element("RT", p)
+    md = MeshDofs(verts, cells, ref)
+    A = asm.assemble(md, asm.element_matrices(ref, verts, cells, alpha=alpha, beta=beta))
+    return verts, cells, md, A
+
+
+@pytest.mark.parametrize("p,n,alpha", [(1, 3, 1.0), (3, 3, 1.0), (5, 2, 1.0), (3, 3, 1e3)])
+@pytest.mark.parametrize("prec,tol", [(rz.PREC_FP64, 1e-10), (rz.PREC_FP32, 1e-4)])
+def test_edge_star_precond_matches_oracle(p, n, alpha, prec, tol):
+    verts, cells, md, A = setup_rt(p, n, alpha=alpha)
+    s = rz.Riesz("RT", p, verts, cells, decomposition=rz.DECOMP_EDGE_STAR, precond_precision=prec, alpha=alpha)
+    P = asm.TwoLevelPreconditioner(A, md, asm.edge_star_dofs(md))
+    r = normal_vector(s.N, 5)
+    z = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    s.precond(dev(r), z)
+    ze = P.apply(r)
+    tol = max(tol * max(1.0, alpha if prec == rz.PREC_FP64 else 1.0), 64.0 * np.linalg.cond(P.A0) * 2.0 ** -24)
+    assert np.abs(host(z) - ze).max() <= tol * np.abs(ze).max()
+
+
+def test_edge_star_dirichlet_precond_matches_oracle():
+    verts, cells, md, A = setup_rt(3, 3)
+    s = rz.Riesz("RT", 3, verts, cells, decomposition=rz.DECOMP_EDGE_STAR, dirichlet=1)
+    D = asm.dirichlet_dofs(md)
+    P = asm.DirichletPreconditioner(A, md, D, patches=asm.edge_star_dofs(md))
+    r = normal_vector(s.N, 6)
+    z = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    s.precond(dev(r), z)
+    ze = P.apply(r)
+    tol = max(1e-10, 64.0 * np.linalg.cond(P.P.A0) * 2.0 ** -24)
+    assert np.abs(host(z) - ze).max() <= tol * np.abs(ze).max()
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_edge_star_solve_matches_direct_solve(nrhs):
+    verts, cells, md, A = setup_rt(3, 3)
+    s = rz.Riesz("RT", 3, verts, cells, decomposition=rz.DECOMP_EDGE_STAR, precond_precision=rz.PREC_FP32,
+                 nrhs_max=nrhs, rtol=1e-10)
+    B = normal_coeffs((nrhs, s.N), 8)
+    X = torch.zeros((nrhs, s.N), dtype=torch.float64, device="cuda")
+    it, rr, rc = s.solve(dev(B), X, nrhs=nrhs)
+    assert rc == 0
+    Xh = host(X)
+    _, it_o, _ = asm.pcg(A, B[0], asm.TwoLevelPreconditioner(A, md, asm.edge_star_dofs(md)).apply, rtol=1e-10)
+    for k in range(nrhs):
+        assert np.linalg.norm(B[k] - A @ Xh[k]) <= 1.001e-10 * np.linalg.norm(B[k])
+        xe = asm.direct_solve(A, B[k])
+        assert np.linalg.norm(Xh[k] - xe) <= 1e-7 * np.linalg.norm(xe)
+    assert int(it[0]) <= it_o + 3

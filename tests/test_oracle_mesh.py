@@ -100,3 +100,22 @@ def test_numbering_layout():
             exp = md.n_interface + np.arange(len(c))[:, None] * len(I) + np.arange(len(I))[None, :]
             assert np.array_equal(md.cell_dofs[:, I], exp)
         assert np.all(used[md.n_interface:] == 1)
+
+
+@pytest.mark.parametrize("space,p,edge,vert", [tuple(r[:1]) + (int(r[1]), int(r[2]), r[3])
+                                               for r in _rows("paper_edge_patch_sizes.txt")])
+def test_edge_patch_sizes_match_paper(space, p, edge, vert):
+    """Tables 1-2: largest edge-star patches of the HT decomposition (type-I DOFs, Eq. (6.19)) and of
+    PAFW_1 for H(div) (Eq. (6.24)); the HT potential problem on the largest vertex star."""
+    from oracle import assemble as asm
+    v, c = kuhn_mesh(2)
+    ref = reference_element(space, p) if p <= 4 else _CountsOnly(space, p)
+    md = MeshDofs(v, c, ref)
+    if space == "N1curl":
+        rc = reference_element("CG", p) if p <= 4 else _CountsOnly("CG", p)
+        mc = MeshDofs(v, c, rc)
+        stars = asm.edge_star_type1_dofs(md, mc)
+        assert max(len(q) for q in mc.patches()) == int(vert)
+    else:
+        stars = asm.edge_star_dofs(md)
+    assert max(len(q) for q in stars) == edge

@@ -442,3 +442,43 @@ def test_ht_preconditioner_spd_and_refinement_robust():
         b = normal_vector(mn.ndofs, 3)
         its.append(asm.pcg(A, b, asm.HTPreconditioner(A, mn, mc).apply)[1])
     assert its[1] <= 1.2 * its[0] + 2
+
+
+def test_hdiv_edge_stars_cover_faces():
+    """PAFW_1 edge stars for RT_p (Eq. (6.24)): exactly the DOFs of the faces containing the edge, so
+    every interface (face) DOF lies in the stars of its face's three edges and nowhere else."""
+    p = 3
+    v, c = kuhn_mesh(2, 0.1, 4)
+    md = MeshDofs(v, c, reference_element("RT", p))
+    stars = asm.edge_star_dofs(md)
+    nf_d = md.per_entity[2]
+    cnt = np.zeros(md.n_interface, dtype=int)
+    for e, (a, b) in enumerate(md.edges):
+        nf = int(np.sum(np.isin(md.faces, [a, b]).sum(1) == 2))
+        assert len(stars[e]) == nf * nf_d
+        np.add.at(cnt, stars[e], 1)
+    assert np.all(cnt == 3)
+    # every edge star lies inside the vertex stars of both endpoints
+    vp = md.patches()
+    for e, (a, b) in enumerate(md.edges):
+        assert set(stars[e]) <= set(vp[a]) and set(stars[e]) <= set(vp[b])
+
+
+def test_hdiv_edge_star_preconditioner_spd_and_refinement_robust():
+    """PAFW_1(X^2_Gamma)+J(X^2_I) with W^2 (Eq. (6.24)): SPD on A and a PCG count that stays flat from
+    2^3 to 4^3 cubes (h-robust with the coarse space, alpha = beta = 1)."""
+    ref = reference_element("RT", 2)
+    v, c = kuhn_mesh(2, 0.1, 6)
+    md = MeshDofs(v, c, ref)
+    A = asm.assemble(md, asm.element_matrices(ref, v, c))
+    P = asm.TwoLevelPreconditioner(A, md, asm.edge_star_dofs(md))
+    ev = np.linalg.eigvals(P.dense() @ A.toarray())
+    assert np.abs(ev.imag).max() < 1e-8 and ev.real.min() > 0
+    its = []
+    for n in (2, 4):
+        v, c = kuhn_mesh(n, 0.1, 1)
+        md = MeshDofs(v, c, ref)
+        A = asm.assemble(md, asm.element_matrices(ref, v, c))
+        b = normal_vector(md.ndofs, 3)
+        its.append(asm.pcg(A, b, asm.TwoLevelPreconditioner(A, md, asm.edge_star_dofs(md)).apply)[1])
+    assert its[1] <= 1.2 * its[0] + 2
