@@ -86,6 +86,8 @@ def parse():
                     help="iteration counts against the degree p on a fixed mesh (p-robustness table)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the run with the paper's finer decomposition (HT / edge stars)")
     ap.add_argument("--no-fp64-plain", action="store_true",
                     help="skip the comparison run of the plain FP64 solver on the same workload")
     return ap.parse_args()
@@ -468,11 +470,11 @@ def main():
     verts_d = torch.tensor(verts, device="cuda")
     ncomp = 1 if wl["space"] == "CG" else 3
 
-    def make(prec, a32):
+    def make(prec, a32, decomposition=args.decomposition):
         """A solver handle for the workload and its step closure (device setup + load + solve)."""
         s = rz.Riesz(wl["space"], wl["p"], verts, cells, precond_precision=prec, nrhs_max=nrhs,
                      apply_precision=a32, loop=rz.LOOP_HOST if args.pcg_loop == "host" else rz.LOOP_GRAPH,
-                     decomposition=DECOMPOSITIONS[args.decomposition])
+                     decomposition=DECOMPOSITIONS[decomposition])
         if nrhs == 1:  # f with N(0,1) CG_p coefficients per Cartesian component, b = (f, phi)
             fcg_h = normal_coeffs((ncomp, s.n_cg), 2 + rank)
         else:  # the paper's random right-hand side vectors (Section 7.1), one per RHS
@@ -577,12 +579,22 @@ def main():
     else:
         esize = 4.0 if dom == "apply32" else 8.0
         byt = C * n * n * esize + nrhs * (C * n * 12.0 + s.N * 16.0)
+        flops = 2.0 * C * n * n * nrhs
         achieved = byt / (dom_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
                 "frac": achieved / peak_hbm, "traffic": measured_traffic(args.workload, "k_" + dom),
                 "kernel": dom,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                 "algorithmic": "element matrices + gathered vectors = %.3e B per launch" % byt}
+        if dom == "apply" and flops / (FP64_NOMINAL_TFLOPS * 1e12) > byt / (peak_hbm * 1e9):
+            # FP64 element products: one DFMA per 8-byte matrix entry and right-hand side, so the FP64
+            # pipe, not HBM, bounds the launch (2 C n^2 nrhs flop)
+            tf = flops / (dom_ms / 1e3) / 1e12
+            roof.update({"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tf / FP64_NOMINAL_TFLOPS, "hbm_gbs": achieved, "hbm_frac": achieved / peak_hbm,
+                         "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s)",
+                         "algorithmic": "2 C n^2 nrhs = %.3e flop per launch (element matrices + gathered "
+                                        "vectors = %.3e B)" % (flops, byt)})
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -626,6 +638,33 @@ def main():
                  "config": "same mesh, right-hand side and rtol; FP64 operator and FP64 patch solves"}
         s64.close()
 
+    # the same workload with the paper's finer decomposition for the space (Hiptmair-Toselli for H(curl),
+    # PAFW_1 edge stars for H(div)): same mesh, right-hand side, precisions and rtol
+    variants = {}
+    alt = {"N1curl": "ht", "RT": "edge_star"}.get(wl["space"])
+    if alt and alt != args.decomposition and not args.no_variants:
+        sv, stepv, itv, rrv, *_ = make(wl["prec"], wl.get("a32", 0), alt)
+        for _ in range(args.warmup):
+            stepv()
+        sv.profile(True)
+        stepv()
+        torch.cuda.synchronize()
+        profv = sv.profile_read()
+        sv.profile(False)
+        perv = timed(stepv, args.steps)
+        msv, _ = combine_ranks(sum(perv), sv.N, dist, device="cuda")
+        kv = {k: v[0] for k, v in profv.items()}
+        variants[alt] = {"value": ntot * nrhs * args.steps / (msv / 1e3), "unit": "DOFs/s",
+                         "ms_per_step": msv / args.steps,
+                         "latency_p50_ms": float(np.percentile(perv, 50)),
+                         "latency_p99_ms": float(np.percentile(perv, 99)),
+                         "iterations": statistics.median(itv[-args.steps:]), "max_relres": max(rrv[-args.steps:]),
+                         "largest_patch": int(np.diff(sv.patch_map()[0]).max()),
+                         "kernel_ms_per_step": {k: round(v, 4) for k, v in kv.items() if v > 0},
+                         "pcg_loop": args.pcg_loop,
+                         "config": "same mesh, right-hand side, precisions and rtol; decomposition " + alt}
+        sv.close()
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(wl)
@@ -649,6 +688,7 @@ def main():
             "latency_p99_ms": float(np.percentile(per_step, 99)),
             "fp64_plain": plain,
             "speedup_vs_fp64_plain": (value / plain["value"]) if plain else None,
+            "decomposition_variants": variants,
             "setup_kernel_ms": sum(k_ms[k] for k in setup_kinds if k not in SIDE_STREAM_KINDS),
             "solve_kernel_ms": sum(v for k, v in k_ms.items() if k not in setup_kinds and k not in SIDE_STREAM_KINDS),
             "kernel_ms_per_step": {k: round(v, 4) for k, v in k_ms.items() if v > 0},

@@ -144,6 +144,8 @@ struct riesz_handle {
   cudaStream_t cap_stream = nullptr;
   cudaStream_t side_stream = nullptr;  // setup work that runs beside the patch factorisation
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_pfork = nullptr, ev_pjoin = nullptr;
+  cudaStream_t ht_stream = nullptr;  // the potential problems (setup and per application) beside the edge stars
+  cudaEvent_t ev_hfork = nullptr, ev_hjoin = nullptr;
   cudaGraphExec_t g_entry = nullptr, g_resume = nullptr;
   int g_nrhs = 0;
   int64_t g_pro_launches = 0, g_body_launches = 0;
@@ -227,6 +229,9 @@ struct riesz_handle {
     if (ev_join) cudaEventDestroy(ev_join);
     if (ev_pfork) cudaEventDestroy(ev_pfork);
     if (ev_pjoin) cudaEventDestroy(ev_pjoin);
+    if (ht_stream) cudaStreamDestroy(ht_stream);
+    if (ev_hfork) cudaEventDestroy(ev_hfork);
+    if (ev_hjoin) cudaEventDestroy(ev_hjoin);
     delete aux;
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   }
@@ -959,12 +964,26 @@ void ht_potential(riesz_handle& h, const double* r, int nrhs, cudaStream_t s) {
   });
 }
 
+// The potential step reads only r: it runs on its own stream beside the
+// edge-star sweeps and the coarse correction and joins before the gather.
+void ht_fork(riesz_handle& h, const double* r, int nrhs, cudaStream_t s) {
+  if (!h.ht) return;
+  CK(cudaEventRecord(h.ev_hfork, s));
+  CK(cudaStreamWaitEvent(h.ht_stream, h.ev_hfork, 0));
+  ht_potential(h, r, nrhs, h.ht_stream);
+  CK(cudaEventRecord(h.ev_hjoin, h.ht_stream));
+}
+void ht_join(riesz_handle& h, cudaStream_t s) {
+  if (h.ht) CK(cudaStreamWaitEvent(s, h.ev_hjoin, 0));
+}
+
 void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStream_t s) {
   const int64_t N = h.N();
-  ht_potential(h, r, nrhs, s);
+  ht_fork(h, r, nrhs, s);
   coarse_fork(h, r, nrhs, s);
   op_patch_solves(h, r, nrhs, s);
   coarse_join(h, s);
+  ht_join(h, s);
   launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
     dev::k_precond_gather<<<nblk(N, 256), 256, 0, s>>>(N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p,
                                                       (int64_t)h.p_dofs.size(), h.d_dinv.p, r, z, nrhs,
@@ -977,10 +996,11 @@ void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStrea
 void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* zold, int op, double* scal, int nrhs,
                     cudaStream_t s) {
   const int64_t N = h.N();
-  ht_potential(h, r, nrhs, s);
+  ht_fork(h, r, nrhs, s);
   coarse_fork(h, r, nrhs, s);
   op_patch_solves(h, r, nrhs, s);
   coarse_join(h, s);
+  ht_join(h, s);
   launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
     dev::k_precond_gather_dot<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(
         N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p, h.d_dinv.p, r, z, zold, h.d_part.p,
@@ -1587,21 +1607,41 @@ void coarse_setup(riesz_handle& h, cudaStream_t s) {
     launch(h, RIESZ_K_COARSE, s, [&] { dev::k_coarse_mirror<<<nbk * (nbk - 1) / 2, 256, 0, s>>>(h.N0p, h.d_A0.p); });
 }
 
+// Patch factorisations that met a non-positive pivot (after the stream is synchronised).
+void check_factor_info(riesz_handle& h, cudaStream_t s) {
+  const int npatch = (int)h.p_n.size();
+  if (!npatch) return;
+  std::vector<int> info(npatch);
+  CK(cudaMemcpyAsync(info.data(), h.d_info.p, sizeof(int) * npatch, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int P = 0; P < npatch; ++P)
+    if (info[P]) throw Err(RIESZ_ERR_INTERNAL, "patch matrix not positive definite");
+}
+
 // Device setup from resident maps and vertex coordinates: a1 geometry,
 // element matrices, a6 interior diagonal, a8 patch assembly + Cholesky.
-void device_compute(riesz_handle& h, cudaStream_t s) {
+// with_aux: also recompute the potential problems of a Hiptmair-Toselli
+// handle (on their own stream, beside this handle's factorisation).  sync:
+// wait for the result, record the device setup time and check the pivots.
+void device_compute(riesz_handle& h, cudaStream_t s, bool with_aux = true, bool sync = true) {
   const RefElement& R = *h.ref;
   const MeshMaps& M = h.mesh;
   const int n = M.nref;
   const int64_t C = M.ncells;
   const int npatch = (int)h.p_n.size();
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  CK(cudaEventRecord(e0, s));
-  if (h.aux) {  // the potential problems follow the same vertices
-    CK(cudaMemcpyAsync(h.aux->d_verts.p, h.d_verts.p, h.d_verts.bytes(), cudaMemcpyDeviceToDevice, s));
-    device_compute(*h.aux, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (sync) {
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+  }
+  const bool aux_now = h.aux && with_aux;
+  if (aux_now) {  // the potential problems follow the same vertices
+    CK(cudaEventRecord(h.ev_hfork, s));
+    CK(cudaStreamWaitEvent(h.ht_stream, h.ev_hfork, 0));
+    CK(cudaMemcpyAsync(h.aux->d_verts.p, h.d_verts.p, h.d_verts.bytes(), cudaMemcpyDeviceToDevice, h.ht_stream));
+    device_compute(*h.aux, h.ht_stream, false, false);
+    CK(cudaEventRecord(h.ev_hjoin, h.ht_stream));
   }
   launch(h, RIESZ_K_GEOM, s, [&] {
     dev::k_geom<<<nblk(C, 128), 128, 0, s>>>(h.space, C, h.d_verts.p, h.d_cells.p, ref_edge_inverse(),
@@ -1657,6 +1697,8 @@ void device_compute(riesz_handle& h, cudaStream_t s) {
     }
   }
   if (h.coarse_on) CK(cudaStreamWaitEvent(s, h.ev_join, 0));
+  if (aux_now) CK(cudaStreamWaitEvent(s, h.ev_hjoin, 0));
+  if (!sync) return;
   CK(cudaEventRecord(e1, s));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;
@@ -1664,13 +1706,8 @@ void device_compute(riesz_handle& h, cudaStream_t s) {
   h.setup_dev_ms = ms;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (npatch) {
-    std::vector<int> info(npatch);
-    CK(cudaMemcpyAsync(info.data(), h.d_info.p, sizeof(int) * npatch, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    for (int P = 0; P < npatch; ++P)
-      if (info[P]) throw Err(RIESZ_ERR_INTERNAL, "patch matrix not positive definite");
-  }
+  check_factor_info(h, s);
+  if (aux_now) check_factor_info(*h.aux, s);
 }
 
 // Autotuner of the patch factorisation's residency: with between one and 24
@@ -1688,7 +1725,7 @@ void tune_cholesky(riesz_handle& h, cudaStream_t s) {
   h.chol_split = h.opts.autotune == 2 ? 2 : 1;
   h.chol_tuned = 0;
   if (h.opts.autotune == 2) {  // fixed: 2-CTA clusters, maximum residency
-    device_compute(h, s);
+    device_compute(h, s, false);
     return;
   }
   if (!h.opts.autotune || npatch <= nsm || npatch > 24 * nsm) return;
@@ -1703,7 +1740,7 @@ void tune_cholesky(riesz_handle& h, cudaStream_t s) {
       h.chol_split = it->second[0];
       h.chol_ctas = it->second[1];
       h.chol_tuned = it->second[2];
-      if (h.chol_split != 1 || h.chol_ctas != 0) device_compute(h, s);
+      if (h.chol_split != 1 || h.chol_ctas != 0) device_compute(h, s, false);
       return;
     }
   }
@@ -1741,7 +1778,7 @@ void tune_cholesky(riesz_handle& h, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(mu);
     done[key] = {best_split, best_c, h.chol_tuned};
   }
-  device_compute(h, s);  // factors (and their FP32 copies) with the chosen residency
+  device_compute(h, s, false);  // factors (and their FP32 copies) with the chosen residency
 }
 
 void setup_device_impl(riesz_handle& h, cudaStream_t s) {
@@ -1823,6 +1860,9 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   h.d_meta.upload(h.p_meta, s);
   if (h.opts.dirichlet) h.d_dmask.upload(h.dir_mask, s);
   if (h.ht) {
+    if (!h.ht_stream) CK(cudaStreamCreateWithFlags(&h.ht_stream, cudaStreamNonBlocking));
+    if (!h.ev_hfork) CK(cudaEventCreateWithFlags(&h.ev_hfork, cudaEventDisableTiming));
+    if (!h.ev_hjoin) CK(cudaEventCreateWithFlags(&h.ev_hjoin, cudaEventDisableTiming));
     setup_device_impl(*h.aux, s);
     h.d_gt_ptr.upload(h.gt_ptr, s);
     h.d_gt_idx.upload(h.gt_idx, s);
@@ -1872,7 +1912,7 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
                           (int)cudaSharedmemCarveoutMaxShared));
   CK(cudaFuncSetAttribute(dev::k_cholesky<2>, cudaFuncAttributePreferredSharedMemoryCarveout,
                           (int)cudaSharedmemCarveoutMaxShared));
-  device_compute(h, s);
+  device_compute(h, s, false);  // the potential problems were factored by their own setup above
   tune_cholesky(h, s);
   h.on_device = true;
 }
