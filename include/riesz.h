@@ -48,6 +48,7 @@ extern "C" {
 #endif
 
 typedef struct riesz_handle riesz_handle;
+typedef struct riesz_hodge riesz_hodge;
 
 enum { RIESZ_H1 = 0, RIESZ_HCURL = 1, RIESZ_HDIV = 2 };
 
@@ -346,6 +347,54 @@ int riesz_stats(const riesz_handle* h, double* out);
 int riesz_destroy(riesz_handle* h);
 
 const char* riesz_last_error(void);
+
+/* ---- Hodge-Laplace problems (Section 7.2) ----------------------------- */
+
+/* The mixed Hodge-Laplace problem of Eq. (7.5) for k = 1 (sigma in CG_p,
+   u in Ned1_p) or k = 2 (sigma in Ned1_p, u in RT_p) on one mesh, pure
+   Neumann (the paper's Fichera corner has Gamma_N = the whole boundary):
+     -(sigma, tau) + (u, d tau) = 0,   (d sigma, v) + (d u, d v) = (f, v).
+   Block vectors are device [sigma (n0) | u (n1)] FP64 (riesz_hodge_sizes),
+   each block in the numbering of riesz_dof_map of its space.
+   Preconditioner: block diagonal, the weighted Riesz maps of Eq. (7.6),
+   (sigma, tau) + gamma (d sigma, d tau) on X^{k-1} and
+   gamma^{-1} (u, v) + (d u, d v) on X^k, each replaced by one application
+   of its Schwarz preconditioner (interior Jacobi, patches, W^k as
+   configured by opts).  opts->decomposition = RIESZ_DECOMP_VERTEX_STAR:
+   vertex stars in both blocks; any other value: the paper's choice of
+   Section 7.2 (vertex stars for CG_p, Hiptmair-Toselli for Ned1_p, edge
+   stars for RT_p).  opts->precond_precision, coarse, autotune, rtol and
+   maxit apply; alpha, beta, nrhs_max, loop, apply_mode and apply_precision
+   are set internally; dirichlet must be 0.  gamma > 0.
+   Setup builds both blocks' maps on the host and runs the device setup on
+   the current device (stream may be NULL); the handle owns all its memory. */
+int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t ncells, const int64_t* cells,
+                      double gamma, const riesz_opts* opts, void* stream, riesz_hodge** out);
+/* *n0 = dim X^{k-1}, *n1 = dim X^k, *ncg (may be NULL) = dim CG_p (the
+   source coefficients of riesz_hodge_load). */
+int riesz_hodge_sizes(const riesz_hodge* h, int64_t* n0, int64_t* n1, int64_t* ncg);
+/* y = A x with A = [-M_{k-1} B^T; B K_k], B_ij = (d phi^{k-1}_j, phi^k_i).
+   x, y: device [n0 + n1], distinct. */
+int riesz_hodge_apply(riesz_hodge* h, const double* x, double* y, void* stream);
+/* z = P^{-1} r, the block-diagonal preconditioner above.  r, z: device [n0 + n1]. */
+int riesz_hodge_precond(riesz_hodge* h, const double* r, double* z, void* stream);
+/* b = [0 | (f, v)_{v in X^k}] for f with CG_p coefficients per Cartesian
+   component (device [3][n_cg], as riesz_load on X^k).  b: device [n0 + n1]. */
+int riesz_hodge_load(riesz_hodge* h, const double* fcg, double* b, void* stream);
+/* New vertex coordinates (device [nverts][3], same connectivity): recompute
+   every block's element matrices, patch factors and the coupling. */
+int riesz_hodge_update_geometry(riesz_hodge* h, const double* verts, void* stream);
+/* Preconditioned MINRES (Paige-Saunders) from the initial guess in x
+   (device [n0 + n1], overwritten by the iterate).  Stops when the
+   P^{-1}-norm of the residual has dropped by rtol; *iters and *relres (host,
+   may be NULL) receive the iteration count and the true relative residual
+   ||b - A x||_2 / ||b||_2.  RIESZ_ERR_NOT_CONVERGED at maxit (x holds the
+   last iterate).  The host synchronises with the stream once per iteration. */
+int riesz_hodge_solve(riesz_hodge* h, const double* b, double* x, void* stream, int* iters, double* relres);
+/* out (host [6]): kernel launches so far (all blocks), last iteration count,
+   last true relative residual, last P^{-1}-norm residual ratio, n0, n1. */
+int riesz_hodge_stats(const riesz_hodge* h, double* out);
+int riesz_hodge_destroy(riesz_hodge* h);
 
 #ifdef __cplusplus
 }

@@ -60,22 +60,25 @@ class HodgeSystem:
 
         return apply
 
-    def schwarz_blocks(self, recommended=True):
+    def schwarz_blocks(self, recommended=True, coarse=True):
         """The two Schwarz preconditioners (the paper's per-space decompositions when recommended,
-        else vertex stars for both), each with interior Jacobi and the weighted W^k summand."""
+        else vertex stars for both), each with interior Jacobi and, when coarse, the weighted W^k
+        summand (one-level otherwise)."""
         out = []
         for sp, P, md in ((SPACES[self.k][0], self.P0, self.md0), (SPACES[self.k][1], self.P1, self.md1)):
             if recommended and sp == "N1curl":
                 mc = self.md0 if self.k == 1 else MeshDofs(md.verts, md.cells, reference_element("CG", self.p))
-                out.append(asm.HTPreconditioner(P, md, mc))
-            elif recommended and sp == "RT":
-                out.append(asm.TwoLevelPreconditioner(P, md, asm.edge_star_dofs(md)))
+                out.append(asm.HTPreconditioner(P, md, mc, weight=0.5 if coarse else 0.0))
             else:
-                out.append(asm.TwoLevelPreconditioner(P, md))
+                patches = asm.edge_star_dofs(md) if (recommended and sp == "RT") else None
+                if coarse:
+                    out.append(asm.TwoLevelPreconditioner(P, md, patches))
+                else:
+                    out.append(asm.Preconditioner(P, md, patches))
         return out
 
-    def schwarz_preconditioner(self, recommended=True):
-        b0, b1 = self.schwarz_blocks(recommended)
+    def schwarz_preconditioner(self, recommended=True, coarse=True):
+        b0, b1 = self.schwarz_blocks(recommended, coarse)
 
         def apply(r):
             return np.concatenate([b0.apply(r[:self.n0]), b1.apply(r[self.n0:])])

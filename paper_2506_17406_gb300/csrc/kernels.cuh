@@ -1271,15 +1271,17 @@ constexpr int CB = 64;  // block size of the coarse sweeps
 
 // A0 [N0p][N0p] (zeroed before): row I of the coarse matrix from its contribution list
 // (ptr, J, cell, local a | b << 16), entries sum_q g_q(cell) R_q[a][b] in list order;
-// the padding rows get 1 on the diagonal.
+// the padding rows get 1 on the diagonal.  T = float (default) or double (ill-
+// conditioned coarse matrices, inverted by the Cholesky route below).
+template <typename T>
 __global__ void k_coarse_assemble(int N0, int N0p, const int64_t* __restrict__ ptr, const int32_t* __restrict__ cJ,
                                   const int32_t* __restrict__ ccell, const int32_t* __restrict__ cab, int64_t C, int n,
                                   int Q, const double* __restrict__ g, const double* __restrict__ R,
-                                  float* __restrict__ A0) {
+                                  T* __restrict__ A0) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= N0p) return;
   if (I >= N0) {
-    A0[(int64_t)I * N0p + I] = 1.f;
+    A0[(int64_t)I * N0p + I] = (T)1;
     return;
   }
   const int64_t nn = (int64_t)n * n;
@@ -1293,63 +1295,78 @@ __global__ void k_coarse_assemble(int N0, int N0p, const int64_t* __restrict__ p
       const int a = cab[e] & 0xffff, b = cab[e] >> 16;
       for (int q = 0; q < Q; ++q) s += g[q * C + c] * R[q * nn + (int64_t)a * n + b];
     }
-    A0[(int64_t)I * N0p + J] = (float)s;
+    A0[(int64_t)I * N0p + J] = (T)s;
   }
 }
 
-constexpr int CBP = CB + 4;  // shared row stride of a 64x64 FP32 tile (16-byte rows, few bank conflicts)
+constexpr int CBP = CB + 4;  // shared row stride of a 64x64 tile (16-byte rows, few bank conflicts)
+
+// 16-byte vector of T
+template <typename T> struct V16;
+template <> struct V16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct V16<double> { using type = double2; static constexpr int n = 2; };
 
 // 64x64 tile, row-major with leading dimension ld, into shared memory; with
 // transpose the tile's transpose is stored.  16-byte global loads.
-__device__ __forceinline__ void load_tile64(float (*S)[CBP], const float* __restrict__ src, int64_t ld,
-                                            bool transpose) {
-  for (int t = threadIdx.x; t < CB * CB / 4; t += blockDim.x) {
-    const int r = t / (CB / 4), c = 4 * (t % (CB / 4));
-    const float4 v = *reinterpret_cast<const float4*>(src + r * ld + c);
+template <typename T>
+__device__ __forceinline__ void load_tile64(T (*S)[CBP], const T* __restrict__ src, int64_t ld, bool transpose) {
+  using V = typename V16<T>::type;
+  constexpr int NV = V16<T>::n;
+  for (int t = threadIdx.x; t < CB * CB / NV; t += blockDim.x) {
+    const int r = t / (CB / NV), c = NV * (t % (CB / NV));
+    const V v = *reinterpret_cast<const V*>(src + r * ld + c);
     if (transpose) {
-      S[c][r] = v.x;
-      S[c + 1][r] = v.y;
-      S[c + 2][r] = v.z;
-      S[c + 3][r] = v.w;
+      const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) S[c + q][r] = e[q];
     } else {
-      *reinterpret_cast<float4*>(&S[r][c]) = v;
+      *reinterpret_cast<V*>(&S[r][c]) = v;
     }
   }
 }
 
+// four consecutive entries of a shared tile row (one 16-byte load in FP32, two in FP64)
+__device__ __forceinline__ void row4(const float* p, float b[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  b[0] = v.x, b[1] = v.y, b[2] = v.z, b[3] = v.w;
+}
+__device__ __forceinline__ void row4(const double* p, double b[4]) {
+  const double2 v = reinterpret_cast<const double2*>(p)[0], w = reinterpret_cast<const double2*>(p)[1];
+  b[0] = v.x, b[1] = v.y, b[2] = w.x, b[3] = w.y;
+}
+
 // acc[a][b] = sum_k As[ty + 16 a][k] Bs[k][4 tx + b]  (ty = tid / 16, tx = tid % 16)
-__device__ __forceinline__ void tile64_mma(const float (*As)[CBP], const float (*Bs)[CBP], int ty, int tx,
-                                           float acc[4][4]) {
+template <typename T>
+__device__ __forceinline__ void tile64_mma(const T (*As)[CBP], const T (*Bs)[CBP], int ty, int tx, T acc[4][4]) {
 #pragma unroll 8
   for (int k = 0; k < CB; ++k) {
-    float av[4];
+    T av[4], b[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) av[a] = As[ty + 16 * a][k];
-    const float4 b = *reinterpret_cast<const float4*>(&Bs[k][4 * tx]);
+    row4(&Bs[k][4 * tx], b);
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      acc[a][0] = fmaf(av[a], b.x, acc[a][0]);
-      acc[a][1] = fmaf(av[a], b.y, acc[a][1]);
-      acc[a][2] = fmaf(av[a], b.z, acc[a][2]);
-      acc[a][3] = fmaf(av[a], b.w, acc[a][3]);
-    }
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[a][q] = fma(av[a], b[q], acc[a][q]);
   }
 }
 
 // The sweeps keep only the block lower triangle (tiles i >= j; diagonal tiles
 // full).  Tile (i, j) of the symmetric matrix: stored, or the transpose of (j, i).
-__device__ __forceinline__ const float* tile_ptr(const float* A, int N0p, int i, int j) {
+template <typename T>
+__device__ __forceinline__ const T* tile_ptr(const T* A, int N0p, int i, int j) {
   return A + (int64_t)i * CB * N0p + (int64_t)j * CB;
 }
 
 // Sweep of block k, step 1 (one CTA): Dinv = A_kk^{-1} by Gauss-Jordan in shared memory.
-__global__ void __launch_bounds__(256) k_gj_pivot(int N0p, int k, const float* __restrict__ A, float* __restrict__ Dinv) {
-  __shared__ __align__(16) float D[CB][CBP];
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_pivot(int N0p, int k, const T* __restrict__ A, T* __restrict__ Dinv) {
+  __shared__ __align__(16) T D[CB][CBP];
   load_tile64(D, tile_ptr(A, N0p, k, k), N0p, false);
   for (int p = 0; p < CB; ++p) {
     __syncthreads();
-    const float pv = D[p][p];
-    float old[16], fi[16], pr[16];
+    const T pv = D[p][p];
+    T old[16], fi[16], pr[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int e = threadIdx.x + 256 * m, i = e / CB, j = e % CB;
@@ -1358,11 +1375,11 @@ __global__ void __launch_bounds__(256) k_gj_pivot(int N0p, int k, const float* _
       pr[m] = D[p][j];
     }
     __syncthreads();
-    const float ipv = 1.f / pv;
+    const T ipv = (T)1 / pv;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int e = threadIdx.x + 256 * m, i = e / CB, j = e % CB;
-      float v;
+      T v;
       if (i == p)
         v = (j == p) ? ipv : pr[m] * ipv;
       else
@@ -1374,12 +1391,21 @@ __global__ void __launch_bounds__(256) k_gj_pivot(int N0p, int k, const float* _
   for (int t = threadIdx.x; t < CB * CB; t += blockDim.x) Dinv[t] = D[t / CB][t % CB];
 }
 
+// Dynamic shared memory of the two-tile sweep kernels.
+template <typename T>
+constexpr size_t gj_smem() {
+  return (size_t)2 * CB * CBP * sizeof(T);
+}
+
 // step 2 (a CTA per column block j != k): Rb[:, j] = Dinv A_kj
-__global__ void __launch_bounds__(256) k_gj_row(int N0p, int k, const float* __restrict__ A,
-                                               const float* __restrict__ Dinv, float* __restrict__ Rb) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_row(int N0p, int k, const T* __restrict__ A, const T* __restrict__ Dinv,
+                                               T* __restrict__ Rb) {
   const int j = blockIdx.x;
   if (j == k) return;
-  __shared__ __align__(16) float As[CB][CBP], Bs[CB][CBP];
+  extern __shared__ __align__(16) unsigned char gj_sm[];
+  T (*As)[CBP] = reinterpret_cast<T (*)[CBP]>(gj_sm);
+  T (*Bs)[CBP] = As + CB;
   load_tile64(As, Dinv, CB, false);
   if (j < k)
     load_tile64(Bs, tile_ptr(A, N0p, k, j), N0p, false);
@@ -1387,23 +1413,26 @@ __global__ void __launch_bounds__(256) k_gj_row(int N0p, int k, const float* __r
     load_tile64(Bs, tile_ptr(A, N0p, j, k), N0p, true);
   __syncthreads();
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  float acc[4][4] = {};
-  tile64_mma(As, Bs, ty, tx, acc);
+  T acc[4][4] = {};
+  tile64_mma<T>(As, Bs, ty, tx, acc);
 #pragma unroll
   for (int a = 0; a < 4; ++a)
-    *reinterpret_cast<float4*>(Rb + (int64_t)(ty + 16 * a) * N0p + j * CB + 4 * tx) =
-        make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Rb[(int64_t)(ty + 16 * a) * N0p + j * CB + 4 * tx + q] = acc[a][q];
 }
 
 // step 3 (a CTA per lower tile (i, j), i >= j, i, j != k): A_ij -= A_ik Rb[:, j]
-__global__ void __launch_bounds__(256) k_gj_update(int N0p, int k, float* __restrict__ A, const float* __restrict__ Rb) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_update(int N0p, int k, T* __restrict__ A, const T* __restrict__ Rb) {
   const int t = blockIdx.x;  // lower-triangle tile index: t = i (i + 1) / 2 + j
   int i = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
   while ((i + 1) * (i + 2) / 2 <= t) ++i;
   while (i * (i + 1) / 2 > t) --i;
   const int j = t - i * (i + 1) / 2;
   if (i == k || j == k) return;
-  __shared__ __align__(16) float As[CB][CBP], Bs[CB][CBP];
+  extern __shared__ __align__(16) unsigned char gj_sm[];
+  T (*As)[CBP] = reinterpret_cast<T (*)[CBP]>(gj_sm);
+  T (*Bs)[CBP] = As + CB;
   if (i > k)
     load_tile64(As, tile_ptr(A, N0p, i, k), N0p, false);
   else
@@ -1411,32 +1440,27 @@ __global__ void __launch_bounds__(256) k_gj_update(int N0p, int k, float* __rest
   load_tile64(Bs, Rb + (int64_t)j * CB, N0p, false);
   __syncthreads();
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  float acc[4][4] = {};
-  tile64_mma(As, Bs, ty, tx, acc);
-  float* Aij = A + (int64_t)i * CB * N0p + (int64_t)j * CB;
+  T acc[4][4] = {};
+  tile64_mma<T>(As, Bs, ty, tx, acc);
+  T* Aij = A + (int64_t)i * CB * N0p + (int64_t)j * CB;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    float4* q = reinterpret_cast<float4*>(Aij + (int64_t)(ty + 16 * a) * N0p + 4 * tx);
-    float4 v = *q;
-    v.x -= acc[a][0];
-    v.y -= acc[a][1];
-    v.z -= acc[a][2];
-    v.w -= acc[a][3];
-    *q = v;
-  }
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Aij[(int64_t)(ty + 16 * a) * N0p + 4 * tx + q] -= acc[a][q];
 }
 
 // step 4 (a CTA per block j): A_kj = Rb[:, j] (j < k), A_jk = Rb[:, j]^T (j > k),
 // A_kk = -Dinv.  After every block has been swept, the lower triangle holds -A_0^{-1}.
-__global__ void __launch_bounds__(256) k_gj_finish(int N0p, int k, float* __restrict__ A, const float* __restrict__ Dinv,
-                                                  const float* __restrict__ Rb) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_finish(int N0p, int k, T* __restrict__ A, const T* __restrict__ Dinv,
+                                                  const T* __restrict__ Rb) {
   const int j = blockIdx.x;
   for (int t = threadIdx.x; t < CB * CB; t += blockDim.x) {
     const int r = t / CB, c = t % CB;
     if (j == k) {
       A[(int64_t)(k * CB + r) * N0p + k * CB + c] = -Dinv[t];
     } else {
-      const float v = Rb[(int64_t)r * N0p + j * CB + c];
+      const T v = Rb[(int64_t)r * N0p + j * CB + c];
       if (j < k)
         A[(int64_t)(k * CB + r) * N0p + j * CB + c] = v;
       else
@@ -1446,7 +1470,8 @@ __global__ void __launch_bounds__(256) k_gj_finish(int N0p, int k, float* __rest
 }
 
 // Fill the upper tiles from the lower ones (full rows for the coarse product).
-__global__ void __launch_bounds__(256) k_coarse_mirror(int N0p, float* __restrict__ A) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_mirror(int N0p, T* __restrict__ A) {
   const int t = blockIdx.x;  // strictly lower tile index
   int i = (int)((sqrtf(8.f * t + 1.f) + 1.f) * 0.5f);
   while (i * (i - 1) / 2 > t) --i;
@@ -1458,44 +1483,245 @@ __global__ void __launch_bounds__(256) k_coarse_mirror(int N0p, float* __restric
   }
 }
 
-// r0[rh][j] = r[rh][cw[j]] in FP32 (zero padding up to N0p)
+// ---------------------------------------------------------------------------
+// Positive definite FP64 coarse inverse X = L^{-T} L^{-1} for ill-conditioned
+// A_0 (an explicit Gauss-Jordan inverse loses definiteness once kappa(A_0)
+// exceeds ~5e6): blocked Cholesky A_0 = L L^T, blocked inversion of L in place,
+// then the product L^{-T} L^{-1}, every step on 64x64 tiles of the lower
+// triangle.  X is stored negated, as the swept Gauss-Jordan matrix.
+// ---------------------------------------------------------------------------
+// Cholesky of the diagonal tile k (one CTA): L_kk into A (upper part zeroed),
+// L_kk^{-1} into Dall[k]; a non-positive pivot sets *bad.
+__global__ void __launch_bounds__(256) k_cc_pivot(int N0p, int k, double* __restrict__ A, double* __restrict__ Dall,
+                                                 int* __restrict__ bad) {
+  __shared__ double D[CB][CB + 1];
+  double* T = A + (int64_t)k * CB * N0p + (int64_t)k * CB;
+  double* Dk = Dall + (int64_t)k * CB * CB;
+  for (int t = threadIdx.x; t < CB * CB; t += blockDim.x) D[t / CB][t % CB] = T[(int64_t)(t / CB) * N0p + t % CB];
+  for (int p = 0; p < CB; ++p) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double d = D[p][p];
+      if (!(d > 0.0)) {
+        *bad = 1;
+        d = 1.0;
+      }
+      D[p][p] = sqrt(d);
+    }
+    __syncthreads();
+    const double dp = D[p][p];
+    for (int i = p + 1 + threadIdx.x; i < CB; i += blockDim.x) D[i][p] /= dp;
+    __syncthreads();
+    for (int t = threadIdx.x; t < (CB - p - 1) * (CB - p - 1); t += blockDim.x) {
+      const int i = p + 1 + t / (CB - p - 1), j = p + 1 + t % (CB - p - 1);
+      if (j <= i) D[i][j] -= D[i][p] * D[j][p];
+    }
+  }
+  __syncthreads();
+  // inverse of the lower-triangular tile into Dk: one thread per column j, rows in
+  // order (each thread reads back only the entries of its own column it wrote)
+  if (threadIdx.x < CB) {
+    const int j = threadIdx.x;
+    for (int i = 0; i < CB; ++i) {
+      if (i < j) {
+        Dk[i * CB + j] = 0.0;
+      } else if (i == j) {
+        Dk[i * CB + j] = 1.0 / D[i][i];
+      } else {
+        double acc = 0.0;
+        for (int m = j; m < i; ++m) acc += D[i][m] * Dk[m * CB + j];
+        Dk[i * CB + j] = -acc / D[i][i];
+      }
+    }
+  }
+  for (int t = threadIdx.x; t < CB * CB; t += blockDim.x) {
+    const int i = t / CB, j = t % CB;
+    T[(int64_t)i * N0p + j] = j <= i ? D[i][j] : 0.0;
+  }
+}
+
+// panel (a CTA per block row i > k): L_ik = A_ik L_kk^{-T}
+__global__ void __launch_bounds__(256) k_cc_panel(int N0p, int k, double* __restrict__ A,
+                                                 const double* __restrict__ Dall) {
+  const int i = k + 1 + blockIdx.x;
+  extern __shared__ __align__(16) unsigned char gj_sm[];
+  double (*As)[CBP] = reinterpret_cast<double (*)[CBP]>(gj_sm);
+  double (*Bs)[CBP] = As + CB;
+  double* Aik = A + (int64_t)i * CB * N0p + (int64_t)k * CB;
+  load_tile64(As, Aik, N0p, false);
+  load_tile64(Bs, Dall + (int64_t)k * CB * CB, CB, true);
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  double acc[4][4] = {};
+  tile64_mma<double>(As, Bs, ty, tx, acc);
+  for (int a = 0; a < 4; ++a)
+    for (int q = 0; q < 4; ++q) Aik[(int64_t)(ty + 16 * a) * N0p + 4 * tx + q] = acc[a][q];
+}
+
+// lower tile (i, j) of the trailing block, i >= j > k, from t = i'(i'+1)/2 + j'
+__device__ __forceinline__ void trailing_tile(int t, int k, int& i, int& j) {
+  int a = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+  while ((a + 1) * (a + 2) / 2 <= t) ++a;
+  while (a * (a + 1) / 2 > t) --a;
+  i = k + 1 + a;
+  j = k + 1 + (t - a * (a + 1) / 2);
+}
+
+// trailing update (a CTA per lower tile i >= j > k): A_ij -= L_ik L_jk^T
+__global__ void __launch_bounds__(256) k_cc_update(int N0p, int k, double* __restrict__ A) {
+  int i, j;
+  trailing_tile(blockIdx.x, k, i, j);
+  extern __shared__ __align__(16) unsigned char gj_sm[];
+  double (*As)[CBP] = reinterpret_cast<double (*)[CBP]>(gj_sm);
+  double (*Bs)[CBP] = As + CB;
+  load_tile64(As, A + (int64_t)i * CB * N0p + (int64_t)k * CB, N0p, false);
+  load_tile64(Bs, A + (int64_t)j * CB * N0p + (int64_t)k * CB, N0p, true);
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  double acc[4][4] = {};
+  tile64_mma<double>(As, Bs, ty, tx, acc);
+  double* Aij = A + (int64_t)i * CB * N0p + (int64_t)j * CB;
+  for (int a = 0; a < 4; ++a)
+    for (int q = 0; q < 4; ++q) Aij[(int64_t)(ty + 16 * a) * N0p + 4 * tx + q] -= acc[a][q];
+}
+
+// Inversion of the lower-triangular L in place, sweep k (Gauss-Jordan on a
+// triangular matrix keeps it lower triangular).  Row step (a CTA per j < k):
+// Rb[:, j] = L_kk^{-1} M_kj.
+__global__ void __launch_bounds__(256) k_ct_row(int N0p, int k, const double* __restrict__ M,
+                                               const double* __restrict__ Dall, double* __restrict__ Rb) {
+  const int j = blockIdx.x;
+  extern __shared__ __align__(16) unsigned char gj_sm[];
+  double (*As)[CBP] = reinterpret_cast<double (*)[CBP]>(gj_sm);
+  double (*Bs)[CBP] = As + CB;
+  load_tile64(As, Dall + (int64_t)k * CB * CB, CB, false);
+  load_tile64(Bs, M + (int64_t)k * CB * N0p + (int64_t)j * CB, N0p, false);
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  double acc[4][4] = {};
+  tile64_mma<double>(As, Bs, ty, tx, acc);
+  for (int a = 0; a < 4; ++a)
+    for (int q = 0; q < 4; ++q) Rb[(int64_t)(ty + 16 * a) * N0p + j * CB + 4 * tx + q] = acc[a][q];
+}
+
+// update step (a CTA per (i, j), i > k, j < k): M_ij -= M_ik Rb[:, j]
+__global__ void __launch_bounds__(256) k_ct_update(int N0p, int k, double* __restrict__ M,
+                                                  const double* __restrict__ Rb) {
+  const int i = k + 1 + blockIdx.x / k, j = blockIdx.x % k;
+  extern __shared__ __align__(16) unsigned char gj_sm[];
+  double (*As)[CBP] = reinterpret_cast<double (*)[CBP]>(gj_sm);
+  double (*Bs)[CBP] = As + CB;
+  load_tile64(As, M + (int64_t)i * CB * N0p + (int64_t)k * CB, N0p, false);
+  load_tile64(Bs, Rb + (int64_t)j * CB, N0p, false);
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  double acc[4][4] = {};
+  tile64_mma<double>(As, Bs, ty, tx, acc);
+  double* Mij = M + (int64_t)i * CB * N0p + (int64_t)j * CB;
+  for (int a = 0; a < 4; ++a)
+    for (int q = 0; q < 4; ++q) Mij[(int64_t)(ty + 16 * a) * N0p + 4 * tx + q] -= acc[a][q];
+}
+
+// finish step (a CTA per block b): M_kb = Rb[:, b] (b < k), M_bk = -M_bk L_kk^{-1}
+// (b > k), M_kk = L_kk^{-1}.
+__global__ void __launch_bounds__(256) k_ct_finish(int N0p, int k, double* __restrict__ M,
+                                                  const double* __restrict__ Dall, const double* __restrict__ Rb) {
+  const int b = blockIdx.x;
+  const double* Dk = Dall + (int64_t)k * CB * CB;
+  if (b < k) {
+    for (int t = threadIdx.x; t < CB * CB; t += blockDim.x)
+      M[(int64_t)(k * CB + t / CB) * N0p + b * CB + t % CB] = Rb[(int64_t)(t / CB) * N0p + b * CB + t % CB];
+    return;
+  }
+  if (b == k) {
+    for (int t = threadIdx.x; t < CB * CB; t += blockDim.x) M[(int64_t)(k * CB + t / CB) * N0p + k * CB + t % CB] = Dk[t];
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char gj_sm[];
+  double (*As)[CBP] = reinterpret_cast<double (*)[CBP]>(gj_sm);
+  double (*Bs)[CBP] = As + CB;
+  double* Mbk = M + (int64_t)b * CB * N0p + (int64_t)k * CB;
+  load_tile64(As, Mbk, N0p, false);
+  load_tile64(Bs, Dk, CB, false);
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  double acc[4][4] = {};
+  tile64_mma<double>(As, Bs, ty, tx, acc);
+  for (int a = 0; a < 4; ++a)
+    for (int q = 0; q < 4; ++q) Mbk[(int64_t)(ty + 16 * a) * N0p + 4 * tx + q] = -acc[a][q];
+}
+
+// X_ij = -sum_{m >= i} (L^{-1})_mi^T (L^{-1})_mj for the lower tiles i >= j (a CTA
+// each, t = i(i+1)/2 + j); the upper tiles follow by k_coarse_mirror.
+__global__ void __launch_bounds__(256) k_ct_lauum(int N0p, int nb, const double* __restrict__ M,
+                                                 double* __restrict__ X) {
+  int i, j;
+  trailing_tile(blockIdx.x, -1, i, j);
+  extern __shared__ __align__(16) unsigned char gj_sm[];
+  double (*As)[CBP] = reinterpret_cast<double (*)[CBP]>(gj_sm);
+  double (*Bs)[CBP] = As + CB;
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  double acc[4][4] = {};
+  for (int m = i; m < nb; ++m) {
+    __syncthreads();
+    load_tile64(As, M + (int64_t)m * CB * N0p + (int64_t)i * CB, N0p, true);
+    load_tile64(Bs, M + (int64_t)m * CB * N0p + (int64_t)j * CB, N0p, false);
+    __syncthreads();
+    tile64_mma<double>(As, Bs, ty, tx, acc);
+  }
+  double* Xij = X + (int64_t)i * CB * N0p + (int64_t)j * CB;
+  for (int a = 0; a < 4; ++a)
+    for (int q = 0; q < 4; ++q) Xij[(int64_t)(ty + 16 * a) * N0p + 4 * tx + q] = -acc[a][q];
+}
+
+// r0[rh][j] = r[rh][cw[j]] (zero padding up to N0p)
+template <typename T>
 __global__ void k_coarse_gather(int N0, int N0p, const int32_t* __restrict__ cw, const double* __restrict__ r,
-                                int64_t N, int nrhs, float* __restrict__ r0) {
+                                int64_t N, int nrhs, T* __restrict__ r0) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nrhs * N0p) return;
   const int rh = t / N0p, j = t % N0p;
-  r0[t] = j < N0 ? (float)r[rh * N + cw[j]] : 0.f;
+  r0[t] = j < N0 ? (T)r[rh * N + cw[j]] : (T)0;
 }
 
 // zc[rh][i] = w sum_j A0inv[i][j] r0[rh][j] with A0inv = -A (the swept, mirrored
 // matrix) and w the coarse weight: r0 staged in shared memory, one warp per
 // row, every matrix row read once for all right-hand sides.
-__global__ void __launch_bounds__(256) k_coarse_apply(int N0, int N0p, const float* __restrict__ A,
-                                                     const float* __restrict__ r0g, int nrhs, double weight,
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_apply(int N0, int N0p, const T* __restrict__ A,
+                                                     const T* __restrict__ r0g, int nrhs, double weight,
                                                      double* __restrict__ zc) {
-  extern __shared__ __align__(16) float r0[];  // [nrhs][N0p]
-  for (int t = threadIdx.x; t < nrhs * N0p / 4; t += blockDim.x)
-    reinterpret_cast<float4*>(r0)[t] = reinterpret_cast<const float4*>(r0g)[t];
+  using V = typename V16<T>::type;
+  constexpr int NV = V16<T>::n;
+  extern __shared__ __align__(16) unsigned char ca_sm[];
+  T* r0 = reinterpret_cast<T*>(ca_sm);  // [nrhs][N0p]
+  for (int t = threadIdx.x; t < nrhs * N0p / NV; t += blockDim.x)
+    reinterpret_cast<V*>(r0)[t] = reinterpret_cast<const V*>(r0g)[t];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int wg = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), nw = gridDim.x * (blockDim.x / 32);
   for (int i = wg; i < N0; i += nw) {
-    const float4* row = reinterpret_cast<const float4*>(A + (int64_t)i * N0p);
-    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int q = lane; q < N0p / 4; q += 32) {
-      const float4 a = row[q];
+    const V* row = reinterpret_cast<const V*>(A + (int64_t)i * N0p);
+    T s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q = lane; q < N0p / NV; q += 32) {
+      const V a = row[q];
+      const T* ae = reinterpret_cast<const T*>(&a);
 #pragma unroll
       for (int rh = 0; rh < 8; ++rh) {
         if (rh < nrhs) {
-          const float4 x = reinterpret_cast<const float4*>(r0 + rh * N0p)[q];
-          s[rh] += a.x * x.x + a.y * x.y + a.z * x.z + a.w * x.w;
+          const V x = reinterpret_cast<const V*>(r0 + rh * N0p)[q];
+          const T* xe = reinterpret_cast<const T*>(&x);
+          T d = 0;
+#pragma unroll
+          for (int e = 0; e < NV; ++e) d += ae[e] * xe[e];
+          s[rh] += d;
         }
       }
     }
 #pragma unroll
     for (int rh = 0; rh < 8; ++rh) {
       if (rh < nrhs) {
-        float v = s[rh];
+        T v = s[rh];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) zc[(int64_t)rh * N0 + i] = -weight * (double)v;
       }
@@ -1823,6 +2049,213 @@ __global__ void k_load(int space, int64_t C, int n, int nif, int ncg, const doub
     else
       Ycell[(int64_t)i * C + c] = s;
   }
+}
+
+
+// ---------------------------------------------------------------------------
+// Hodge-Laplace problem of Section 7.2 (Eq. (7.5)): the block operator
+//   [ -M_{k-1}  B^T ] [sigma]
+//   [  B        K_k ] [u    ],   B_ij = (d phi^{k-1}_j, phi^k_i).
+// ---------------------------------------------------------------------------
+// Coupling element matrices Be[c][j][i] = sum_q g_q(c) R_q[j][i] over the six
+// metric entries of the X^k mass factors (j < n0 in X^{k-1}, i < n1 in X^k).
+__global__ void k_mixed_elem(int64_t C, int n0, int n1, const double* __restrict__ g, const double* __restrict__ R,
+                             double* __restrict__ Be) {
+  const int64_t c = blockIdx.x;
+  const int64_t nn = (int64_t)n0 * n1;
+  double gq[6];
+  for (int q = 0; q < 6; ++q) gq[q] = g[q * C + c];
+  for (int64_t t = threadIdx.x; t < nn; t += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < 6; ++q) s += gq[q] * R[q * nn + t];
+    Be[c * nn + t] = s;
+  }
+}
+
+// One CTA per cell: gather sigma_T and u_T, then
+//   X^k rows i:      y1_i = sum_j K_T[j][i] u_j + sum_j Be_T[j][i] sigma_j   (threads over i)
+//   X^{k-1} rows j:  y0_j = -sum_l M_T[l][j] sigma_l + sum_i Be_T[j][i] u_i  (threads over j, then a
+//                    warp per j for the transposed coupling, lanes over i, fixed shuffle tree)
+// Interface rows go to the cell slots Ycell (summed per DOF by k_gather_iface),
+// interior rows straight to y (each interior DOF belongs to one cell).
+__global__ void __launch_bounds__(NT) k_hodge_apply(int64_t C, int n0, int n1, int nif0, int nif1,
+                                                    const double* __restrict__ Me, const double* __restrict__ Ke,
+                                                    const double* __restrict__ Be, const int32_t* __restrict__ cd0,
+                                                    const int32_t* __restrict__ cd1, const double* __restrict__ x0,
+                                                    const double* __restrict__ x1, double* __restrict__ y0,
+                                                    double* __restrict__ y1, double* __restrict__ Yc0,
+                                                    double* __restrict__ Yc1) {
+  extern __shared__ double smh[];
+  double* xs0 = smh;        // [n0]
+  double* xs1 = smh + n0;   // [n1]
+  double* ys0 = xs1 + n1;   // [n0]
+  const int64_t c = blockIdx.x;
+  for (int t = threadIdx.x; t < n0; t += blockDim.x) xs0[t] = x0[cd0[(int64_t)t * C + c]];
+  for (int t = threadIdx.x; t < n1; t += blockDim.x) xs1[t] = x1[cd1[(int64_t)t * C + c]];
+  __syncthreads();
+  const double* K = Ke + c * (int64_t)n1 * n1;
+  const double* M = Me + c * (int64_t)n0 * n0;
+  const double* B = Be + c * (int64_t)n0 * n1;
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+    double a = 0.0;
+    for (int j = 0; j < n1; ++j) a = fma(K[(int64_t)j * n1 + i], xs1[j], a);
+    for (int j = 0; j < n0; ++j) a = fma(B[(int64_t)j * n1 + i], xs0[j], a);
+    if (i >= nif1)
+      y1[cd1[(int64_t)i * C + c]] = a;
+    else
+      Yc1[(int64_t)i * C + c] = a;
+  }
+  for (int j = threadIdx.x; j < n0; j += blockDim.x) {
+    double a = 0.0;
+    for (int l = 0; l < n0; ++l) a = fma(M[(int64_t)l * n0 + j], xs0[l], a);
+    ys0[j] = -a;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < n0; j += nw) {
+    double a = 0.0;
+    for (int i = lane; i < n1; i += 32) a = fma(B[(int64_t)j * n1 + i], xs1[i], a);
+    a = warp_sum(a);
+    if (lane == 0) ys0[j] += a;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n0; j += blockDim.x) {
+    if (j >= nif0)
+      y0[cd0[(int64_t)j * C + c]] = ys0[j];
+    else
+      Yc0[(int64_t)j * C + c] = ys0[j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Preconditioned MINRES (Paige-Saunders) for the Hodge-Laplace system: the
+// Lanczos vectors and the Givens recurrences run on the device; the scalars
+// live in a MinresSlot array (slot 6 is the shared non-finite flag).
+// ---------------------------------------------------------------------------
+enum MinresSlot { M_BETA = 0, M_ALPHA = 1, M_BNEXT = 2, M_C1 = 3, M_S1 = 4, M_C2 = 5, M_S2 = 7, M_PHIBAR = 8,
+                  M_BETA1 = 9, M_TAU = 10, M_DELTA = 11, M_EPS = 12, M_GAM = 13, M_INVB = 14, M_RAW = 15 };
+
+// op 0: (r, z) of the initial residual -> beta_1, phibar, rotations reset.
+// op 1: (u, w) -> alpha_k.  op 2: (w, z) -> beta_{k+1} and the rotation step:
+// the two previous rotations applied to column k of T (beta_k, alpha_k), the
+// new one chosen to eliminate beta_{k+1}, the step tau_k = c_k phibar.
+__device__ __forceinline__ void minres_op(int op, double s0, double* __restrict__ m) {
+  if (!isfinite(s0)) m[6] = 1.0;
+  if (op != 1) m[M_RAW] = s0;  // (r, P^{-1} r) < 0 means the preconditioner is not positive definite
+  if (op == 0) {
+    const double b = sqrt(fmax(s0, 0.0));
+    m[M_BETA] = b;
+    m[M_BETA1] = b;
+    m[M_PHIBAR] = b;
+    m[M_C1] = m[M_C2] = 1.0;
+    m[M_S1] = m[M_S2] = 0.0;
+    m[M_INVB] = b > 0.0 ? 1.0 / b : 0.0;
+  } else if (op == 1) {
+    m[M_ALPHA] = s0;
+  } else {
+    const double bn = sqrt(fmax(s0, 0.0));
+    const double beta = m[M_BETA], alpha = m[M_ALPHA];
+    const double eps = m[M_S2] * beta, dlt = m[M_C2] * beta;
+    const double delta = m[M_C1] * dlt + m[M_S1] * alpha;
+    const double gbar = -m[M_S1] * dlt + m[M_C1] * alpha;
+    const double gam = hypot(gbar, bn);
+    const double cs = gam > 0.0 ? gbar / gam : 1.0, sn = gam > 0.0 ? bn / gam : 0.0;
+    m[M_EPS] = eps;
+    m[M_DELTA] = delta;
+    m[M_GAM] = gam;
+    m[M_TAU] = cs * m[M_PHIBAR];
+    m[M_PHIBAR] = -sn * m[M_PHIBAR];
+    m[M_C2] = m[M_C1];
+    m[M_S2] = m[M_S1];
+    m[M_C1] = cs;
+    m[M_S1] = sn;
+    m[M_BNEXT] = bn;
+    m[M_BETA] = bn;
+    m[M_INVB] = bn > 0.0 ? 1.0 / bn : 0.0;
+  }
+}
+
+// Deterministic a.b (fixed-order two-stage reduction, last block finishes) -> minres_op.
+__global__ void __launch_bounds__(NT) k_mr_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                                              double* __restrict__ part, unsigned* __restrict__ ticket, int op,
+                                              double* __restrict__ m) {
+  double v = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * NT)
+    v = fma(a[i], b[i], v);
+  __shared__ double sh[NT / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += sh[w];
+    part[blockIdx.x] = t;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == (unsigned)(gridDim.x - 1));
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int i = threadIdx.x; i < RED_BLOCKS; i += NT) t += __ldcg(part + i);
+  t = warp_sum(t);
+  __syncthreads();
+  if (lane == 0) sh[warp] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s0 += sh[w];
+    minres_op(op, s0, m);
+    *ticket = 0u;
+  }
+}
+
+// w -= beta_k v_prev (when v_prev != nullptr)
+__global__ void k_mr_sub_beta(int64_t n, const double* __restrict__ m, double* __restrict__ w,
+                              const double* __restrict__ vprev) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) w[i] -= m[M_BETA] * vprev[i];
+}
+
+// w -= alpha_k v
+__global__ void k_mr_sub_alpha(int64_t n, const double* __restrict__ m, double* __restrict__ w,
+                               const double* __restrict__ v) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) w[i] -= m[M_ALPHA] * v[i];
+}
+
+// r = b - r (r holds A x on entry)
+__global__ void k_mr_residual(int64_t n, const double* __restrict__ b, double* __restrict__ r) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) r[i] = b[i] - r[i];
+}
+
+// v = r / beta, u = z / beta (the first Lanczos vectors)
+__global__ void k_mr_scale(int64_t n, const double* __restrict__ m, const double* __restrict__ r,
+                           const double* __restrict__ z, double* __restrict__ v, double* __restrict__ u) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double s = m[M_INVB];
+  v[i] = r[i] * s;
+  u[i] = z[i] * s;
+}
+
+// d_k = (u_k - delta d_{k-1} - eps d_{k-2}) / gamma (written over d_{k-2}),
+// x += tau d_k, and the next Lanczos vectors v_{k+1} = w / beta_{k+1} (into vnew),
+// u_{k+1} = z / beta_{k+1} (over u_k).
+__global__ void k_mr_update(int64_t n, const double* __restrict__ m, double* __restrict__ x, double* __restrict__ u,
+                            const double* __restrict__ d1, double* __restrict__ d2, double* __restrict__ vnew,
+                            const double* __restrict__ w, const double* __restrict__ z) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double g = m[M_GAM];
+  const double d = g != 0.0 ? (u[i] - m[M_DELTA] * d1[i] - m[M_EPS] * d2[i]) / g : 0.0;
+  d2[i] = d;
+  x[i] += m[M_TAU] * d;
+  vnew[i] = w[i] * m[M_INVB];
+  u[i] = z[i] * m[M_INVB];
 }
 
 }  // namespace dev

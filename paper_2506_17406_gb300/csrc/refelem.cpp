@@ -1051,4 +1051,36 @@ const RefElement& reference_element(int space, int p) {
   });
 }
 
+const std::vector<double>& mixed_reference_tables(int k, int p) {
+  static OnceCache<std::pair<int, int>, std::vector<double>> cache;
+  if (k < 1 || k > 2) throw std::runtime_error("mixed_reference_tables: k must be 1 or 2");
+  return cache.get(std::make_pair(k, p), [&] {
+    const RefElement& R0 = reference_element(k - 1, p);  // X^{k-1}: CG_p or Ned1_p
+    const RefElement& R1 = reference_element(k, p);      // X^k: Ned1_p or RT_p
+    const int n0 = R0.nref, n1 = R1.nref;
+    Rule Q = simplex_rule(3, p + 2);
+    const int np = Q.npt();
+    std::vector<double> v1((size_t)np * n1 * 3), d0((size_t)np * n0 * 3);
+    R1.tabulate(np, Q.x.data(), v1.data(), nullptr);
+    R0.tabulate(np, Q.x.data(), nullptr, d0.data());
+    auto comp = [&](const std::vector<double>& t, int n, int a) {  // [q][i] = t_i^a(x_q)
+      Mat T(np, n);
+      for (int q = 0; q < np; ++q)
+        for (int i = 0; i < n; ++i) T(q, i) = t[((size_t)q * n + i) * 3 + a];
+      return T;
+    };
+    const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    auto out = std::make_shared<std::vector<double>>((size_t)6 * n0 * n1, 0.0);
+    for (int q = 0; q < 6; ++q) {
+      const int a = pairs[q][0], b = pairs[q][1];
+      const Mat G = gram_tn(comp(d0, n0, b), Q.w, comp(v1, n1, a));  // [j][i] = sum w (d phi0_j)_b (phi1_i)_a
+      const Mat H = (a == b) ? Mat() : gram_tn(comp(d0, n0, a), Q.w, comp(v1, n1, b));
+      double* o = out->data() + (size_t)q * n0 * n1;
+      for (int j = 0; j < n0; ++j)
+        for (int i = 0; i < n1; ++i) o[(size_t)j * n1 + i] = G(j, i) + (a == b ? 0.0 : H(j, i));
+    }
+    return out;
+  });
+}
+
 }  // namespace riesz

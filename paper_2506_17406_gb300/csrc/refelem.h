@@ -51,4 +51,11 @@ struct RefElement {
 // Cached per (space, p).  Throws std::runtime_error on failure.
 const RefElement& reference_element(int space, int p);
 
+// Reference tables of the coupling (d phi^{k-1}_j, phi^k_i) of the Hodge-Laplace
+// problem (k = 1: CG_p -> Ned1_p, k = 2: Ned1_p -> RT_p): 6 matrices [j][i]
+// (n_{k-1} x n_k), one per symmetric metric entry (00, 11, 22, 01, 02, 12), the
+// off-diagonal ones holding both orderings; contracted against the X^k mass
+// factors of a cell (|det J| J^{-1}J^{-T} for k = 1, J^T J / |det J| for k = 2).
+const std::vector<double>& mixed_reference_tables(int k, int p);
+
 }  // namespace riesz

@@ -101,6 +101,7 @@ struct riesz_handle {
   riesz_handle* aux = nullptr;
   // edge-star patches (Hiptmair-Toselli for H(curl), PAFW_1 for H(div)): CSR edge -> sorted DOFs
   bool edge_star = false;
+  bool apply_only = false;  // internal operator handles (Hodge-Laplace blocks): no patches, no coarse space
   std::vector<int64_t> es_ptr;
   std::vector<int32_t> es_dofs;
   std::vector<int64_t> gt_ptr, gg_ptr;
@@ -124,6 +125,12 @@ struct riesz_handle {
   DBuf<int64_t> d_cptr;
   DBuf<float> d_A0, d_Dinv0, d_Rb0;  // swept coarse matrix (-A_0^{-1} when done), pivot inverse, sweep row
   DBuf<float> d_r0;                   // R_0 r in FP32 [nrhs][N0p]
+  // the same in FP64 for ill-conditioned coarse matrices (beta/alpha far from 1, and the blocks of
+  // the Hodge-Laplace preconditioner), where the FP32 inverse stops being positive definite
+  bool coarse64 = false;
+  DBuf<double> d_A0d, d_Dinv0d, d_Rb0d, d_r0d;
+  DBuf<double> d_X0d;   // FP64 path: X = -(L^{-T} L^{-1}) (the factor and its inverse are built in d_A0d)
+  DBuf<int> d_cbad;     // non-positive pivot in the coarse Cholesky
   DBuf<double> d_zc;                  // coarse corrections [nrhs][N0]
   int multi_group = 8;  // right-hand sides per k_patch_solve_multi launch
   int chol_ctas = 0;    // resident k_cholesky CTAs per SM picked by the autotuner (0: no limit)
@@ -173,7 +180,7 @@ struct riesz_handle {
            d_gt_idx.bytes() + d_gg_idx.bytes() + d_gt_sgn.bytes() + d_gg_sgn.bytes() + d_zcg.bytes() + d_zg.bytes() +
            (aux ? aux->device_bytes() : 0) + d_cw.bytes() + d_cidx.bytes() + d_cJ.bytes() +
            d_ccell.bytes() + d_cab.bytes() + d_cptr.bytes() + d_A0.bytes() + d_Dinv0.bytes() + d_Rb0.bytes() +
-           d_r0.bytes() + d_zc.bytes();
+           d_r0.bytes() + d_zc.bytes() + d_A0d.bytes() + d_X0d.bytes() + d_Dinv0d.bytes() + d_Rb0d.bytes() + d_r0d.bytes();
   }
   void drop_graphs() {
     if (g_entry) cudaGraphExecDestroy(g_entry);
@@ -203,6 +210,12 @@ struct riesz_handle {
     d_Dinv0.free();
     d_Rb0.free();
     d_r0.free();
+    d_A0d.free();
+    d_X0d.free();
+    d_cbad.free();
+    d_Dinv0d.free();
+    d_Rb0d.free();
+    d_r0d.free();
     d_zc.free();
     if (h_ctl) cudaFreeHost(h_ctl);
     h_ctl = nullptr;
@@ -691,6 +704,11 @@ void plan_coarse(riesz_handle& h) {
   }
   for (int i = 0; i < N0; ++i) h.c_ptr[i + 1] += h.c_ptr[i];
   h.coarse_on = true;
+  // FP64 Cholesky-route coarse inverse when the weights are unbalanced: kappa(A_0) grows like
+  // (alpha / beta) h^-2 (or beta / alpha), and beyond ~1e4 the FP32 Gauss-Jordan inverse is no longer
+  // positive definite
+  if (h.opts.beta > 0 && h.opts.alpha > 0)
+    h.coarse64 = h.coarse64 || std::max(h.opts.alpha / h.opts.beta, h.opts.beta / h.opts.alpha) > 10.0;
 }
 
 void build_plans(riesz_handle& h) {
@@ -776,7 +794,7 @@ void build_plans(riesz_handle& h) {
       for (int q = 0; q < 3; ++q) center[q] = 0.5 * (h.verts[(size_t)a * 3 + q] + h.verts[(size_t)b * 3 + q]);
       plan_patch(h, &h.es_dofs[h.es_ptr[e]], np, cells.data(), (int64_t)cells.size(), center, foff, dioff);
     }
-  } else {
+  } else if (!h.apply_only) {
     for (int64_t v : order) {
       const int64_t b = M.patch_ptr[v], e = M.patch_ptr[v + 1];
       const int np = (int)(e - b);
@@ -913,21 +931,28 @@ void op_patch_solves(riesz_handle& h, const double* r, int nrhs, cudaStream_t s)
 }
 
 // Coarse corrections zc = A_0^{-1} R_0 r (W^k), when the handle has a coarse space.
-void op_coarse(riesz_handle& h, const double* r, int nrhs, cudaStream_t s) {
-  if (!h.coarse_on) return;
+template <typename T>
+void op_coarse_t(riesz_handle& h, const double* r, int nrhs, cudaStream_t s, T* A0, T* r0) {
   const int64_t N = h.N();
   const unsigned grid = (unsigned)std::min<int64_t>((h.N0 + 7) / 8, 608);
   launch(h, RIESZ_K_COARSE_APPLY, s, [&] {
-    dev::k_coarse_gather<<<nblk((int64_t)nrhs * h.N0p, 256), 256, 0, s>>>(h.N0, h.N0p, h.d_cw.p, r, N, nrhs,
-                                                                          h.d_r0.p);
+    dev::k_coarse_gather<T><<<nblk((int64_t)nrhs * h.N0p, 256), 256, 0, s>>>(h.N0, h.N0p, h.d_cw.p, r, N, nrhs, r0);
   });
-  for (int r0 = 0; r0 < nrhs; r0 += h.coarse_group) {
-    const int nr = std::min(h.coarse_group, nrhs - r0);
+  for (int k0 = 0; k0 < nrhs; k0 += h.coarse_group) {
+    const int nr = std::min(h.coarse_group, nrhs - k0);
     launch(h, RIESZ_K_COARSE_APPLY, s, [&] {
-      dev::k_coarse_apply<<<grid, 256, (size_t)nr * h.N0p * sizeof(float), s>>>(
-          h.N0, h.N0p, h.d_A0.p, h.d_r0.p + (int64_t)r0 * h.N0p, nr, COARSE_WEIGHT, h.d_zc.p + (int64_t)r0 * h.N0);
+      dev::k_coarse_apply<T><<<grid, 256, (size_t)nr * h.N0p * sizeof(T), s>>>(
+          h.N0, h.N0p, A0, r0 + (int64_t)k0 * h.N0p, nr, COARSE_WEIGHT, h.d_zc.p + (int64_t)k0 * h.N0);
     });
   }
+}
+
+void op_coarse(riesz_handle& h, const double* r, int nrhs, cudaStream_t s) {
+  if (!h.coarse_on) return;
+  if (h.coarse64)
+    op_coarse_t<double>(h, r, nrhs, s, h.d_X0d.p, h.d_r0d.p);
+  else
+    op_coarse_t<float>(h, r, nrhs, s, h.d_A0.p, h.d_r0.p);
 }
 
 // The coarse correction reads only r: it runs on the side stream beside the
@@ -1586,29 +1611,81 @@ void launch_cholesky(riesz_handle& h, int split, int ctas, cudaStream_t s) {
 }
 
 // A_0 from the geometric factors, then -A_0^{-1} in place by block sweeps.
-void coarse_setup(riesz_handle& h, cudaStream_t s) {
+template <typename T>
+void coarse_setup_t(riesz_handle& h, cudaStream_t s, DBuf<T>& A0, DBuf<T>& Dinv, DBuf<T>& Rb) {
   const int nbk = h.N0p / dev::CB;
   const RefElement& R = *h.ref;
-  CK(cudaMemsetAsync(h.d_A0.p, 0, h.d_A0.bytes(), s));
+  const size_t sm = dev::gj_smem<T>();
+  CK(cudaMemsetAsync(A0.p, 0, A0.bytes(), s));
   launch(h, RIESZ_K_COARSE, s, [&] {
-    dev::k_coarse_assemble<<<nblk(h.N0p, 128), 128, 0, s>>>(h.N0, h.N0p, h.d_cptr.p, h.d_cJ.p, h.d_ccell.p, h.d_cab.p,
-                                                            h.C(), h.mesh.nref, R.Q, h.d_g.p, h.d_R.p, h.d_A0.p);
+    dev::k_coarse_assemble<T><<<nblk(h.N0p, 128), 128, 0, s>>>(h.N0, h.N0p, h.d_cptr.p, h.d_cJ.p, h.d_ccell.p,
+                                                               h.d_cab.p, h.C(), h.mesh.nref, R.Q, h.d_g.p, h.d_R.p,
+                                                               A0.p);
   });
   for (int k = 0; k < nbk; ++k) {
-    launch(h, RIESZ_K_COARSE, s, [&] { dev::k_gj_pivot<<<1, 256, 0, s>>>(h.N0p, k, h.d_A0.p, h.d_Dinv0.p); });
+    launch(h, RIESZ_K_COARSE, s, [&] { dev::k_gj_pivot<T><<<1, 256, 0, s>>>(h.N0p, k, A0.p, Dinv.p); });
+    launch(h, RIESZ_K_COARSE, s, [&] { dev::k_gj_row<T><<<nbk, 256, sm, s>>>(h.N0p, k, A0.p, Dinv.p, Rb.p); });
     launch(h, RIESZ_K_COARSE, s,
-           [&] { dev::k_gj_row<<<nbk, 256, 0, s>>>(h.N0p, k, h.d_A0.p, h.d_Dinv0.p, h.d_Rb0.p); });
-    launch(h, RIESZ_K_COARSE, s,
-           [&] { dev::k_gj_update<<<nbk * (nbk + 1) / 2, 256, 0, s>>>(h.N0p, k, h.d_A0.p, h.d_Rb0.p); });
-    launch(h, RIESZ_K_COARSE, s,
-           [&] { dev::k_gj_finish<<<nbk, 256, 0, s>>>(h.N0p, k, h.d_A0.p, h.d_Dinv0.p, h.d_Rb0.p); });
+           [&] { dev::k_gj_update<T><<<nbk * (nbk + 1) / 2, 256, sm, s>>>(h.N0p, k, A0.p, Rb.p); });
+    launch(h, RIESZ_K_COARSE, s, [&] { dev::k_gj_finish<T><<<nbk, 256, 0, s>>>(h.N0p, k, A0.p, Dinv.p, Rb.p); });
   }
   if (nbk > 1)
-    launch(h, RIESZ_K_COARSE, s, [&] { dev::k_coarse_mirror<<<nbk * (nbk - 1) / 2, 256, 0, s>>>(h.N0p, h.d_A0.p); });
+    launch(h, RIESZ_K_COARSE, s, [&] { dev::k_coarse_mirror<T><<<nbk * (nbk - 1) / 2, 256, 0, s>>>(h.N0p, A0.p); });
+}
+
+// FP64: positive definite inverse X = L^{-T} L^{-1} from the blocked Cholesky factor
+// (stored negated in d_X0d, the convention of the swept Gauss-Jordan matrix).
+void coarse_setup_chol(riesz_handle& h, cudaStream_t s) {
+  const int nb = h.N0p / dev::CB;
+  const RefElement& R = *h.ref;
+  const size_t sm = dev::gj_smem<double>();
+  double* A = h.d_A0d.p;
+  CK(cudaMemsetAsync(A, 0, h.d_A0d.bytes(), s));
+  launch(h, RIESZ_K_COARSE, s, [&] {
+    dev::k_coarse_assemble<double><<<nblk(h.N0p, 128), 128, 0, s>>>(h.N0, h.N0p, h.d_cptr.p, h.d_cJ.p, h.d_ccell.p,
+                                                                    h.d_cab.p, h.C(), h.mesh.nref, R.Q, h.d_g.p,
+                                                                    h.d_R.p, A);
+  });
+  for (int k = 0; k < nb; ++k) {
+    launch(h, RIESZ_K_COARSE, s, [&] { dev::k_cc_pivot<<<1, 256, 0, s>>>(h.N0p, k, A, h.d_Dinv0d.p, h.d_cbad.p); });
+    const int m = nb - 1 - k;
+    if (m > 0) {
+      launch(h, RIESZ_K_COARSE, s, [&] { dev::k_cc_panel<<<m, 256, sm, s>>>(h.N0p, k, A, h.d_Dinv0d.p); });
+      launch(h, RIESZ_K_COARSE, s, [&] { dev::k_cc_update<<<m * (m + 1) / 2, 256, sm, s>>>(h.N0p, k, A); });
+    }
+  }
+  for (int k = 0; k < nb; ++k) {
+    if (k > 0)
+      launch(h, RIESZ_K_COARSE, s,
+             [&] { dev::k_ct_row<<<k, 256, sm, s>>>(h.N0p, k, A, h.d_Dinv0d.p, h.d_Rb0d.p); });
+    if (k > 0 && nb - 1 - k > 0)
+      launch(h, RIESZ_K_COARSE, s,
+             [&] { dev::k_ct_update<<<(nb - 1 - k) * k, 256, sm, s>>>(h.N0p, k, A, h.d_Rb0d.p); });
+    launch(h, RIESZ_K_COARSE, s,
+           [&] { dev::k_ct_finish<<<nb, 256, sm, s>>>(h.N0p, k, A, h.d_Dinv0d.p, h.d_Rb0d.p); });
+  }
+  launch(h, RIESZ_K_COARSE, s,
+         [&] { dev::k_ct_lauum<<<nb * (nb + 1) / 2, 256, sm, s>>>(h.N0p, nb, A, h.d_X0d.p); });
+  if (nb > 1)
+    launch(h, RIESZ_K_COARSE, s,
+           [&] { dev::k_coarse_mirror<double><<<nb * (nb - 1) / 2, 256, 0, s>>>(h.N0p, h.d_X0d.p); });
+}
+
+void coarse_setup(riesz_handle& h, cudaStream_t s) {
+  if (h.coarse64)
+    coarse_setup_chol(h, s);
+  else
+    coarse_setup_t<float>(h, s, h.d_A0, h.d_Dinv0, h.d_Rb0);
 }
 
 // Patch factorisations that met a non-positive pivot (after the stream is synchronised).
 void check_factor_info(riesz_handle& h, cudaStream_t s) {
+  if (h.coarse_on && h.coarse64) {
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, h.d_cbad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (bad) throw Err(RIESZ_ERR_INTERNAL, "coarse matrix not positive definite");
+  }
   const int npatch = (int)h.p_n.size();
   if (!npatch) return;
   std::vector<int> info(npatch);
@@ -1880,14 +1957,37 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     h.d_cJ.upload(h.c_J, s);
     h.d_ccell.upload(h.c_cell, s);
     h.d_cab.upload(h.c_ab, s);
-    h.d_A0.alloc((size_t)h.N0p * h.N0p);
-    h.d_Dinv0.alloc((size_t)dev::CB * dev::CB);
-    h.d_Rb0.alloc((size_t)dev::CB * h.N0p);
+    if (h.coarse64) {
+      h.d_A0d.alloc((size_t)h.N0p * h.N0p);
+      h.d_X0d.alloc((size_t)h.N0p * h.N0p);
+      h.d_Dinv0d.alloc((size_t)h.N0p * dev::CB);  // the inverse of every diagonal tile of L
+      h.d_Rb0d.alloc((size_t)dev::CB * h.N0p);
+      h.d_r0d.alloc((size_t)nrhs * h.N0p);
+      h.d_cbad.alloc(1);
+      CK(cudaMemsetAsync(h.d_cbad.p, 0, sizeof(int), s));
+      raise_smem_limit(dev::k_cc_panel, dev::gj_smem<double>());
+      raise_smem_limit(dev::k_cc_update, dev::gj_smem<double>());
+      raise_smem_limit(dev::k_ct_row, dev::gj_smem<double>());
+      raise_smem_limit(dev::k_ct_update, dev::gj_smem<double>());
+      raise_smem_limit(dev::k_ct_finish, dev::gj_smem<double>());
+      raise_smem_limit(dev::k_ct_lauum, dev::gj_smem<double>());
+    } else {
+      h.d_A0.alloc((size_t)h.N0p * h.N0p);
+      h.d_Dinv0.alloc((size_t)dev::CB * dev::CB);
+      h.d_Rb0.alloc((size_t)dev::CB * h.N0p);
+      h.d_r0.alloc((size_t)nrhs * h.N0p);
+    }
+    raise_smem_limit(dev::k_gj_row<float>, dev::gj_smem<float>());
+    raise_smem_limit(dev::k_gj_update<float>, dev::gj_smem<float>());
+    raise_smem_limit(dev::k_gj_row<double>, dev::gj_smem<double>());
+    raise_smem_limit(dev::k_gj_update<double>, dev::gj_smem<double>());
     h.d_zc.alloc((size_t)nrhs * h.N0);
-    h.d_r0.alloc((size_t)nrhs * h.N0p);
-    const size_t per = (size_t)h.N0p * sizeof(float);
+    const size_t per = (size_t)h.N0p * (h.coarse64 ? sizeof(double) : sizeof(float));
     h.coarse_group = (int)std::max<size_t>(1, std::min<size_t>(8, (160 * 1024) / per));
-    raise_smem_limit(dev::k_coarse_apply, per * h.coarse_group);
+    if (h.coarse64)
+      raise_smem_limit(dev::k_coarse_apply<double>, per * h.coarse_group);
+    else
+      raise_smem_limit(dev::k_coarse_apply<float>, per * h.coarse_group);
   }
   if (npatch) {
     h.d_L64.alloc((size_t)h.factor_entries);
@@ -1926,7 +2026,7 @@ void check_dev(const riesz_handle* h) {
 // handles (the potential problems of the Hiptmair-Toselli decomposition) may
 // have beta = 0.
 riesz_handle* create_handle(int space, int p, int64_t nverts, const double* verts, int64_t ncells,
-                            const int64_t* cells, const riesz_opts& opts, bool internal) {
+                            const int64_t* cells, const riesz_opts& opts, bool internal, bool apply_only = false) {
   need(space >= 0 && space <= 2, "space must be RIESZ_H1, RIESZ_HCURL or RIESZ_HDIV");
   need(p >= 1 && p <= 10, "degree p must be in 1..10");
   need(verts && cells && nverts > 0 && ncells > 0, "empty mesh", RIESZ_ERR_BAD_MESH);
@@ -1938,9 +2038,12 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
   need(h->opts.rtol > 0 && h->opts.maxit >= 0 && h->opts.nrhs_max >= 1 && h->opts.nrhs_max <= 64, "bad options");
   need(h->opts.precond_precision == 0 || h->opts.precond_precision == 1, "bad precond_precision");
   need(h->opts.apply_mode == 0 || h->opts.apply_mode == 1, "bad apply_mode");
-  need(h->opts.alpha > 0 && (h->opts.beta > 0 || (internal && h->opts.beta == 0)) && std::isfinite(h->opts.alpha) &&
-           std::isfinite(h->opts.beta),
+  h->apply_only = internal && apply_only;
+  need((h->opts.alpha > 0 || (h->apply_only && h->opts.alpha == 0)) &&
+           (h->opts.beta > 0 || (internal && h->opts.beta == 0)) && (h->opts.alpha > 0 || h->opts.beta > 0) &&
+           std::isfinite(h->opts.alpha) && std::isfinite(h->opts.beta),
        "alpha and beta must be positive and finite");
+  if (h->apply_only) h->opts.coarse = 0;
   need(h->opts.apply_precision == 0 || h->opts.apply_precision == 1, "bad apply_precision");
   need(h->opts.loop == RIESZ_LOOP_HOST || h->opts.loop == RIESZ_LOOP_GRAPH, "bad loop");
   need(h->opts.autotune >= 0 && h->opts.autotune <= 2, "bad autotune");
@@ -2346,6 +2449,324 @@ int riesz_stats(const riesz_handle* h, double* out) {
 }
 
 int riesz_destroy(riesz_handle* h) {
+  return guarded([&] { delete h; });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Hodge-Laplace problems of Section 7.2 (Eq. (7.5)) for k = 1 (CG_p x Ned1_p)
+// and k = 2 (Ned1_p x RT_p): block vectors [sigma (n0) | u (n1)], the block
+// operator [-M_{k-1} B^T; B K_k], the block-diagonal augmented-Lagrangian
+// preconditioner of Eq. (7.6) with each weighted Riesz map replaced by its
+// Schwarz preconditioner, and preconditioned MINRES on the device.
+// ---------------------------------------------------------------------------
+struct riesz_hodge {
+  int k = 0, p = 0;
+  double gamma = 1.0, rtol = 1e-8;
+  int maxit = 1000;
+  riesz_handle* P0 = nullptr;  // X^{k-1}: (sigma, tau) + gamma (d sigma, d tau), preconditioner block
+  riesz_handle* P1 = nullptr;  // X^k: gamma^{-1} (u, v) + (d u, d v), preconditioner block
+  riesz_handle* Mh = nullptr;  // X^{k-1} mass (operator only)
+  riesz_handle* Kh = nullptr;  // X^k d-stiffness (operator only)
+  int64_t n0 = 0, n1 = 0;
+  int64_t launches = 0;
+  int last_iters = 0;
+  double last_relres = 0.0, last_phi = 0.0;
+  DBuf<double> d_R, d_gB, d_jacB, d_Be;                   // coupling tables, factors, element matrices
+  DBuf<double> v, vp, u, w, z, d1, d2, d_m, d_part;       // MINRES vectors and scalars
+  DBuf<unsigned> d_ticket;
+  double* h_m = nullptr;
+  ~riesz_hodge() {
+    if (h_m) cudaFreeHost(h_m);
+    for (auto* b : {&d_R, &d_gB, &d_jacB, &d_Be, &v, &vp, &u, &w, &z, &d1, &d2, &d_m, &d_part}) b->free();
+    d_ticket.free();
+    delete P0;
+    delete P1;
+    delete Mh;
+    delete Kh;
+  }
+  int64_t N() const { return n0 + n1; }
+  int64_t sub_launches() const {
+    int64_t l = 0;
+    for (riesz_handle* x : {P0, P1, Mh, Kh})
+      if (x) l += x->launches + (x->aux ? x->aux->launches : 0);
+    return l;
+  }
+};
+
+namespace {
+
+void hodge_geometry(riesz_hodge& H, cudaStream_t s) {
+  riesz_handle& K = *H.Kh;
+  const int64_t C = K.C();
+  // the X^k mass factors (beta = 1, alpha = 0) are the metric of the coupling
+  dev::k_geom<<<nblk(C, 128), 128, 0, s>>>(H.k, C, K.d_verts.p, K.d_cells.p, ref_edge_inverse(), 0.0, 1.0, H.d_gB.p,
+                                          H.d_jacB.p);
+  CK(cudaGetLastError());
+  dev::k_mixed_elem<<<(unsigned)C, 256, 0, s>>>(C, H.Mh->mesh.nref, K.mesh.nref, H.d_gB.p, H.d_R.p, H.d_Be.p);
+  CK(cudaGetLastError());
+  H.launches += 2;
+}
+
+void hodge_apply(riesz_hodge& H, const double* x, double* y, cudaStream_t s) {
+  riesz_handle& M = *H.Mh;
+  riesz_handle& K = *H.Kh;
+  const int64_t C = K.C();
+  const int n0 = M.mesh.nref, n1 = K.mesh.nref;
+  const size_t sm = (size_t)(2 * n0 + n1) * sizeof(double);
+  dev::k_hodge_apply<<<(unsigned)C, dev::NT, sm, s>>>(C, n0, n1, M.nif, K.nif, M.d_Ae.p, K.d_Ae.p, H.d_Be.p,
+                                                     M.d_cdofs.p, K.d_cdofs.p, x, x + H.n0, y, y + H.n0, M.d_Ycell.p,
+                                                     K.d_Ycell.p);
+  CK(cudaGetLastError());
+  const int64_t nI0 = M.mesh.n_interface, nI1 = K.mesh.n_interface;
+  dev::k_gather_iface<<<nblk(nI0, 256), 256, 0, s>>>(nI0, M.d_sc_ptr.p, M.d_sc_pos.p, M.d_Ycell.p,
+                                                     (int64_t)M.nif * C, y, H.n0, 1, nullptr, nullptr);
+  CK(cudaGetLastError());
+  dev::k_gather_iface<<<nblk(nI1, 256), 256, 0, s>>>(nI1, K.d_sc_ptr.p, K.d_sc_pos.p, K.d_Ycell.p,
+                                                     (int64_t)K.nif * C, y + H.n0, H.n1, 1, nullptr, nullptr);
+  CK(cudaGetLastError());
+  H.launches += 3;
+}
+
+void hodge_precond(riesz_hodge& H, const double* r, double* z, cudaStream_t s) {
+  op_precond(*H.P0, r, z, 1, s);
+  op_precond(*H.P1, r + H.n0, z + H.n0, 1, s);
+}
+
+void hodge_dot(riesz_hodge& H, const double* a, const double* b, int op, cudaStream_t s) {
+  dev::k_mr_dot<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(H.N(), a, b, H.d_part.p, H.d_ticket.p, op, H.d_m.p);
+  CK(cudaGetLastError());
+  ++H.launches;
+}
+
+void hodge_read(riesz_hodge& H, cudaStream_t s) {
+  CK(cudaMemcpyAsync(H.h_m, H.d_m.p, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+// Preconditioned MINRES (Paige-Saunders): Lanczos on P^{-1} A in the P-inner
+// product, the tridiagonal reduced by Givens rotations as it grows; stops when
+// the P^{-1}-norm of the residual, |phibar|, drops below rtol times its initial
+// value, then reports the true relative residual ||b - A x|| / ||b||.
+int hodge_minres(riesz_hodge& H, const double* b, double* x, cudaStream_t s, int* iters, double* relres) {
+  const int64_t N = H.N();
+  const unsigned nb = nblk(N, 256);
+  double* vcur = H.v.p;
+  double* vprev = H.vp.p;
+  double* dd1 = H.d1.p;
+  double* dd2 = H.d2.p;
+  hodge_apply(H, x, H.w.p, s);
+  dev::k_mr_residual<<<nb, 256, 0, s>>>(N, b, H.w.p);
+  hodge_precond(H, H.w.p, H.z.p, s);
+  hodge_dot(H, H.w.p, H.z.p, 0, s);
+  dev::k_mr_scale<<<nb, 256, 0, s>>>(N, H.d_m.p, H.w.p, H.z.p, vcur, H.u.p);
+  CK(cudaMemsetAsync(dd1, 0, N * sizeof(double), s));
+  CK(cudaMemsetAsync(dd2, 0, N * sizeof(double), s));
+  H.launches += 2;
+  hodge_read(H, s);
+  if (H.h_m[6] != 0.0) throw Err(RIESZ_ERR_NONFINITE, "non-finite right-hand side or preconditioner");
+  if (H.h_m[dev::M_RAW] < 0.0) throw Err(RIESZ_ERR_INTERNAL, "block preconditioner is not positive definite");
+  const double beta1 = H.h_m[dev::M_BETA1];
+  int it = 0;
+  int rc = RIESZ_OK;
+  double phi = beta1;
+  while (beta1 > 0.0) {
+    if (it >= H.maxit) {
+      rc = RIESZ_ERR_NOT_CONVERGED;
+      break;
+    }
+    ++it;
+    hodge_apply(H, H.u.p, H.w.p, s);
+    if (it > 1) {
+      dev::k_mr_sub_beta<<<nb, 256, 0, s>>>(N, H.d_m.p, H.w.p, vprev);
+      ++H.launches;
+    }
+    hodge_dot(H, H.u.p, H.w.p, 1, s);
+    dev::k_mr_sub_alpha<<<nb, 256, 0, s>>>(N, H.d_m.p, H.w.p, vcur);
+    hodge_precond(H, H.w.p, H.z.p, s);
+    hodge_dot(H, H.w.p, H.z.p, 2, s);
+    dev::k_mr_update<<<nb, 256, 0, s>>>(N, H.d_m.p, x, H.u.p, dd1, dd2, vprev, H.w.p, H.z.p);
+    CK(cudaGetLastError());
+    H.launches += 2;
+    std::swap(dd1, dd2);      // d_k is now in dd1, d_{k-1} in dd2
+    std::swap(vprev, vcur);   // v_{k+1} was written over v_{k-1}
+    hodge_read(H, s);
+    if (H.h_m[6] != 0.0) throw Err(RIESZ_ERR_NONFINITE, "non-finite value in the MINRES recurrence");
+    if (H.h_m[dev::M_RAW] < 0.0) throw Err(RIESZ_ERR_INTERNAL, "block preconditioner is not positive definite");
+    phi = std::fabs(H.h_m[dev::M_PHIBAR]);
+    if (phi <= H.rtol * beta1 || H.h_m[dev::M_BNEXT] == 0.0) break;
+  }
+  // true residual
+  hodge_apply(H, x, H.w.p, s);
+  dev::k_mr_residual<<<nb, 256, 0, s>>>(N, b, H.w.p);
+  ++H.launches;
+  hodge_dot(H, H.w.p, H.w.p, 1, s);
+  hodge_read(H, s);
+  const double rr = H.h_m[dev::M_ALPHA];
+  hodge_dot(H, b, b, 1, s);
+  hodge_read(H, s);
+  const double bb = H.h_m[dev::M_ALPHA];
+  H.last_iters = it;
+  H.last_relres = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+  H.last_phi = beta1 > 0.0 ? phi / beta1 : 0.0;
+  if (iters) *iters = it;
+  if (relres) *relres = H.last_relres;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t ncells, const int64_t* cells,
+                      double gamma, const riesz_opts* opts, void* stream, riesz_hodge** out) {
+  return guarded([&] {
+    need(out != nullptr, "null output");
+    *out = nullptr;
+    need(k == 1 || k == 2, "k must be 1 (CG_p x Ned1_p) or 2 (Ned1_p x RT_p)");
+    need(gamma > 0 && std::isfinite(gamma), "gamma must be positive and finite");
+    riesz_opts o;
+    riesz_default_opts(&o);
+    if (opts) o = *opts;
+    need(!o.dirichlet, "the Hodge-Laplace problems are pure Neumann");
+    need(o.rtol > 0 && o.maxit >= 0, "bad rtol or maxit");
+    const bool paper = o.decomposition != RIESZ_DECOMP_VERTEX_STAR;
+    auto H = std::make_unique<riesz_hodge>();
+    H->k = k;
+    H->p = p;
+    H->gamma = gamma;
+    H->rtol = o.rtol;
+    H->maxit = o.maxit;
+    riesz_opts b = o;
+    b.nrhs_max = 1;
+    b.loop = RIESZ_LOOP_HOST;
+    b.apply_mode = RIESZ_APPLY_ELEMENT;
+    b.apply_precision = RIESZ_PREC_FP64;
+    // preconditioner blocks: the weighted Riesz maps of Eq. (7.6)
+    riesz_opts o0 = b, o1 = b;
+    o0.alpha = gamma;
+    o0.beta = 1.0;
+    o0.decomposition = (paper && k == 2) ? RIESZ_DECOMP_HT : RIESZ_DECOMP_VERTEX_STAR;
+    o1.alpha = 1.0;
+    o1.beta = 1.0 / gamma;
+    o1.decomposition = !paper ? RIESZ_DECOMP_VERTEX_STAR : (k == 1 ? RIESZ_DECOMP_HT : RIESZ_DECOMP_EDGE_STAR);
+    H->P0 = create_handle(k - 1, p, nverts, verts, ncells, cells, o0, true);
+    H->P1 = create_handle(k, p, nverts, verts, ncells, cells, o1, true);
+    // MINRES needs a positive definite preconditioner: the W^k inverses of both blocks by the FP64
+    // Cholesky route (A_0 = R_0 (M + gamma K) R_0^T and gamma^{-1} M + K reach kappa ~ 1e7 for gamma
+    // far from 1, where an explicit Gauss-Jordan inverse, even in FP64, is no longer definite)
+    H->P0->coarse64 = H->P1->coarse64 = true;
+    // operator blocks
+    riesz_opts om = b, ok = b;
+    om.alpha = 0.0;
+    om.beta = 1.0;
+    om.decomposition = RIESZ_DECOMP_VERTEX_STAR;
+    ok.alpha = 1.0;
+    ok.beta = 0.0;
+    ok.decomposition = RIESZ_DECOMP_VERTEX_STAR;
+    H->Mh = create_handle(k - 1, p, nverts, verts, ncells, cells, om, true, true);
+    H->Kh = create_handle(k, p, nverts, verts, ncells, cells, ok, true, true);
+    H->n0 = H->Mh->N();
+    H->n1 = H->Kh->N();
+    cudaStream_t s = S(stream);
+    for (riesz_handle* x : {H->P0, H->P1, H->Mh, H->Kh}) setup_device_impl(*x, s);
+    const int64_t C = H->Kh->C();
+    const int n0 = H->Mh->mesh.nref, n1 = H->Kh->mesh.nref;
+    std::vector<double> R;
+    try {
+      R = mixed_reference_tables(k, p);
+    } catch (const std::exception& e) {
+      throw Err(RIESZ_ERR_INTERNAL, e.what());
+    }
+    H->d_R.upload(R, s);
+    H->d_gB.alloc((size_t)12 * C);  // k_geom writes all Q factors of X^k (12 for Ned1_p)
+    H->d_jacB.alloc((size_t)C * 10);
+    H->d_Be.alloc((size_t)C * n0 * n1);
+    const size_t sm = (size_t)(2 * n0 + n1) * sizeof(double);
+    if (sm > 48 * 1024) raise_smem_limit(dev::k_hodge_apply, sm);
+    for (auto* v : {&H->v, &H->vp, &H->u, &H->w, &H->z, &H->d1, &H->d2}) v->alloc((size_t)H->N());
+    H->d_m.alloc(16);
+    CK(cudaMemsetAsync(H->d_m.p, 0, 16 * sizeof(double), s));
+    H->d_part.alloc(dev::RED_BLOCKS);
+    H->d_ticket.alloc(1);
+    CK(cudaMemsetAsync(H->d_ticket.p, 0, sizeof(unsigned), s));
+    CK(cudaMallocHost((void**)&H->h_m, 16 * sizeof(double)));
+    hodge_geometry(*H, s);
+    CK(cudaStreamSynchronize(s));
+    *out = H.release();
+  });
+}
+
+int riesz_hodge_sizes(const riesz_hodge* h, int64_t* n0, int64_t* n1, int64_t* ncg) {
+  return guarded([&] {
+    need(h && n0 && n1, "null argument");
+    *n0 = h->n0;
+    *n1 = h->n1;
+    if (ncg) *ncg = h->Kh->meshcg.ndofs;
+  });
+}
+
+int riesz_hodge_apply(riesz_hodge* h, const double* x, double* y, void* stream) {
+  return guarded([&] {
+    need(h && x && y, "null argument");
+    hodge_apply(*h, x, y, S(stream));
+  });
+}
+
+int riesz_hodge_precond(riesz_hodge* h, const double* r, double* z, void* stream) {
+  return guarded([&] {
+    need(h && r && z, "null argument");
+    hodge_precond(*h, r, z, S(stream));
+  });
+}
+
+int riesz_hodge_load(riesz_hodge* h, const double* fcg, double* b, void* stream) {
+  return guarded([&] {
+    need(h && fcg && b, "null argument");
+    cudaStream_t s = S(stream);
+    CK(cudaMemsetAsync(b, 0, h->n0 * sizeof(double), s));
+    const int rc = riesz_load(h->Kh, fcg, b + h->n0, stream);
+    if (rc != RIESZ_OK) throw Err(rc, "load on X^k failed");
+  });
+}
+
+int riesz_hodge_update_geometry(riesz_hodge* h, const double* verts, void* stream) {
+  return guarded([&] {
+    need(h && verts, "null argument");
+    cudaStream_t s = S(stream);
+    for (riesz_handle* x : {h->P0, h->P1, h->Mh, h->Kh}) {
+      CK(cudaMemcpyAsync(x->d_verts.p, verts, x->d_verts.bytes(), cudaMemcpyDeviceToDevice, s));
+      device_compute(*x, s);
+    }
+    hodge_geometry(*h, s);
+  });
+}
+
+int riesz_hodge_solve(riesz_hodge* h, const double* b, double* x, void* stream, int* iters, double* relres) {
+  int rc = RIESZ_OK;
+  const int g = guarded([&] {
+    need(h && b && x, "null argument");
+    rc = hodge_minres(*h, b, x, S(stream), iters, relres);
+  });
+  if (g != RIESZ_OK) return g;
+  if (rc != RIESZ_OK) g_err = "MINRES did not reach rtol within maxit";
+  return rc;
+}
+
+int riesz_hodge_stats(const riesz_hodge* h, double* out) {
+  return guarded([&] {
+    need(h && out, "null argument");
+    out[0] = (double)(h->launches + h->sub_launches());
+    out[1] = h->last_iters;
+    out[2] = h->last_relres;
+    out[3] = h->last_phi;
+    out[4] = (double)h->n0;
+    out[5] = (double)h->n1;
+  });
+}
+
+int riesz_hodge_destroy(riesz_hodge* h) {
   return guarded([&] { delete h; });
 }
 

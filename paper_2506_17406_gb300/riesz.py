@@ -74,6 +74,16 @@ _SIGS = {
     "riesz_profile": (_I, [_P, _I]),
     "riesz_profile_read": (_I, [_P, _P, _P]),
     "riesz_destroy": (_I, [_P]),
+    "riesz_hodge_setup": (_I, [_I, _I, _I64, _P, _I64, _P, ctypes.c_double, ctypes.POINTER(Opts), _P,
+                               ctypes.POINTER(_P)]),
+    "riesz_hodge_sizes": (_I, [_P, _P, _P, _P]),
+    "riesz_hodge_apply": (_I, [_P, _P, _P, _P]),
+    "riesz_hodge_precond": (_I, [_P, _P, _P, _P]),
+    "riesz_hodge_load": (_I, [_P, _P, _P, _P]),
+    "riesz_hodge_update_geometry": (_I, [_P, _P, _P]),
+    "riesz_hodge_solve": (_I, [_P, _P, _P, _P, _P, _P]),
+    "riesz_hodge_stats": (_I, [_P, _P]),
+    "riesz_hodge_destroy": (_I, [_P]),
 }
 
 
@@ -288,6 +298,67 @@ class Riesz:
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             self.lib.riesz_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hodge:
+    """The mixed Hodge-Laplace problem of Section 7.2 for k = 1 (CG_p x Ned1_p) or k = 2
+    (Ned1_p x RT_p): ``Hodge(k, p, verts, cells, gamma, **opts)`` builds and sets up on the
+    device; block vectors are [sigma (n0) | u (n1)]."""
+
+    def __init__(self, k, p, verts, cells, gamma=1.0, stream=None, **opts):
+        self.lib = load_library()
+        self.k, self.p, self.gamma = k, p, gamma
+        verts = np.ascontiguousarray(verts, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        self.opts = default_opts(**opts)
+        h = ctypes.c_void_p()
+        _check(self.lib.riesz_hodge_setup(k, p, verts.shape[0], _ptr(verts), cells.shape[0], _ptr(cells),
+                                          float(gamma), ctypes.byref(self.opts), _stream(stream), ctypes.byref(h)))
+        self.h = h
+        sz = np.zeros(3, dtype=np.int64)
+        _check(self.lib.riesz_hodge_sizes(self.h, _ptr(sz[0:1]), _ptr(sz[1:2]), _ptr(sz[2:3])))
+        self.n0, self.n1, self.n_cg = (int(x) for x in sz)
+        self.N = self.n0 + self.n1
+
+    def apply(self, x, y, stream=None):
+        _check(self.lib.riesz_hodge_apply(self.h, _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def precond(self, r, z, stream=None):
+        _check(self.lib.riesz_hodge_precond(self.h, _ptr(r), _ptr(z), _stream(stream)))
+        return z
+
+    def load(self, fcg, b, stream=None):
+        _check(self.lib.riesz_hodge_load(self.h, _ptr(fcg), _ptr(b), _stream(stream)))
+        return b
+
+    def update_geometry(self, verts_dev, stream=None):
+        _check(self.lib.riesz_hodge_update_geometry(self.h, _ptr(verts_dev), _stream(stream)))
+
+    def solve(self, b, x, stream=None, check=True):
+        it = np.zeros(1, dtype=np.int32)
+        rr = np.zeros(1)
+        rc = self.lib.riesz_hodge_solve(self.h, _ptr(b), _ptr(x), _stream(stream), _ptr(it), _ptr(rr))
+        if check:
+            _check(rc)
+        return int(it[0]), float(rr[0]), rc
+
+    def stats(self):
+        out = np.zeros(6)
+        _check(self.lib.riesz_hodge_stats(self.h, _ptr(out)))
+        return {"launches": int(out[0]), "last_iters": int(out[1]), "last_relres": out[2],
+                "last_precond_residual_ratio": out[3], "n0": int(out[4]), "n1": int(out[5])}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.riesz_hodge_destroy(self.h)
             self.h = None
 
     def __del__(self):

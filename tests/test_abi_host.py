@@ -184,3 +184,19 @@ def test_edge_star_patches_match_oracle(lib, dirichlet):
     for e, q in enumerate(exp):
         assert np.array_equal(dofs[off[e]:off[e + 1]], q)
     assert dirichlet == int(any(len(q) == 0 for q in exp))
+
+
+def test_hodge_validation(lib):
+    """Arguments are checked before any device work: k, gamma, Dirichlet; without a GPU the setup
+    reports the missing device instead of falling back."""
+    from paper_2506_17406_gb300.inputs import fichera_mesh
+    v, c = fichera_mesh(2)
+    for k, gamma, kw in [(0, 1.0, {}), (3, 1.0, {}), (1, 0.0, {}), (2, -1.0, {}), (1, 1.0, dict(dirichlet=1))]:
+        with pytest.raises(rz.RieszError) as e:
+            rz.Hodge(k, 2, v, c, gamma, stream=0, **kw)
+        assert e.value.code == 1
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(rz.RieszError) as e:
+            rz.Hodge(1, 2, v, c, 1.0, stream=0)
+        assert e.value.code == 6
