@@ -1306,6 +1306,23 @@ template <typename T> struct V16;
 template <> struct V16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct V16<double> { using type = double2; static constexpr int n = 2; };
 
+// the components of a 16-byte vector down a tile column (transposed store)
+__device__ __forceinline__ void store_col(float (*S)[CBP], int c, int r, const float4& v) {
+  S[c][r] = v.x;
+  S[c + 1][r] = v.y;
+  S[c + 2][r] = v.z;
+  S[c + 3][r] = v.w;
+}
+__device__ __forceinline__ void store_col(double (*S)[CBP], int c, int r, const double2& v) {
+  S[c][r] = v.x;
+  S[c + 1][r] = v.y;
+}
+// dot product of two 16-byte vectors
+__device__ __forceinline__ float vdot(const float4& a, const float4& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
+__device__ __forceinline__ double vdot(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
+
 // 64x64 tile, row-major with leading dimension ld, into shared memory; with
 // transpose the tile's transpose is stored.  16-byte global loads.
 template <typename T>
@@ -1315,13 +1332,10 @@ __device__ __forceinline__ void load_tile64(T (*S)[CBP], const T* __restrict__ s
   for (int t = threadIdx.x; t < CB * CB / NV; t += blockDim.x) {
     const int r = t / (CB / NV), c = NV * (t % (CB / NV));
     const V v = *reinterpret_cast<const V*>(src + r * ld + c);
-    if (transpose) {
-      const T* e = reinterpret_cast<const T*>(&v);
-#pragma unroll
-      for (int q = 0; q < NV; ++q) S[c + q][r] = e[q];
-    } else {
+    if (transpose)
+      store_col(S, c, r, v);
+    else
       *reinterpret_cast<V*>(&S[r][c]) = v;
-    }
   }
 }
 
@@ -1703,20 +1717,23 @@ __global__ void __launch_bounds__(256) k_coarse_apply(int N0, int N0p, const T* 
   for (int i = wg; i < N0; i += nw) {
     const V* row = reinterpret_cast<const V*>(A + (int64_t)i * N0p);
     T s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int q = lane; q < N0p / NV; q += 32) {
-      const V a = row[q];
-      const T* ae = reinterpret_cast<const T*>(&a);
+    const int nq = N0p / NV;
+    int q = lane;
+    for (; q + 96 < nq; q += 128) {  // four independent 16-byte loads in flight per lane
+      const V a0 = row[q], a1 = row[q + 32], a2 = row[q + 64], a3 = row[q + 96];
 #pragma unroll
       for (int rh = 0; rh < 8; ++rh) {
         if (rh < nrhs) {
-          const V x = reinterpret_cast<const V*>(r0 + rh * N0p)[q];
-          const T* xe = reinterpret_cast<const T*>(&x);
-          T d = 0;
-#pragma unroll
-          for (int e = 0; e < NV; ++e) d += ae[e] * xe[e];
-          s[rh] += d;
+          const V* x = reinterpret_cast<const V*>(r0 + rh * N0p);
+          s[rh] += (vdot(a0, x[q]) + vdot(a1, x[q + 32])) + (vdot(a2, x[q + 64]) + vdot(a3, x[q + 96]));
         }
       }
+    }
+    for (; q < nq; q += 32) {
+      const V a = row[q];
+#pragma unroll
+      for (int rh = 0; rh < 8; ++rh)
+        if (rh < nrhs) s[rh] += vdot(a, reinterpret_cast<const V*>(r0 + rh * N0p)[q]);
     }
 #pragma unroll
     for (int rh = 0; rh < 8; ++rh) {
