@@ -1641,6 +1641,7 @@ void coarse_setup_chol(riesz_handle& h, cudaStream_t s) {
   const size_t sm = dev::gj_smem<double>();
   double* A = h.d_A0d.p;
   CK(cudaMemsetAsync(A, 0, h.d_A0d.bytes(), s));
+  CK(cudaMemsetAsync(h.d_cbad.p, 0, sizeof(int), s));
   launch(h, RIESZ_K_COARSE, s, [&] {
     dev::k_coarse_assemble<double><<<nblk(h.N0p, 128), 128, 0, s>>>(h.N0, h.N0p, h.d_cptr.p, h.d_cJ.p, h.d_ccell.p,
                                                                     h.d_cab.p, h.C(), h.mesh.nref, R.Q, h.d_g.p,
