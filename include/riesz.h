@@ -211,6 +211,15 @@ int riesz_patch_map(const riesz_handle* h, int64_t* offsets, int32_t* dofs);
    curl or div); either may be NULL. */
 int riesz_ref_tabulate(int space, int p, int64_t npts, const double* pts, double* vals, double* dvals);
 
+/* Reference coupling tables of the Hodge-Laplace problem (k = 1: CG_p -> Ned1_p,
+   k = 2: Ned1_p -> RT_p): out host [6][n_{k-1}][n_k], entry [q][j][i] =
+   integral over the reference tetrahedron of (d phi^{k-1}_j)_b (phi^k_i)_a
+   (+ the same with a and b exchanged when a != b) for the metric entry
+   q = (a, b) in the order 00, 11, 22, 01, 02, 12.  On a cell,
+   (d phi^{k-1}_j, phi^k_i) = sum_q G_q R_q[j][i] with G the symmetric metric
+   |det J| J^{-1} J^{-T} (k = 1) or J^T J / |det J| (k = 2). */
+int riesz_ref_mixed_tables(int k, int p, double* out);
+
 /* ---- device calls ---------------------------------------------------- */
 
 /* Upload the maps and tables to the current CUDA device and run the device

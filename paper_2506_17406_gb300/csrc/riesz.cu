@@ -2210,6 +2210,16 @@ int riesz_ref_tabulate(int space, int p, int64_t npts, const double* pts, double
   });
 }
 
+int riesz_ref_mixed_tables(int k, int p, double* out) {
+  return guarded([&] {
+    need(k == 1 || k == 2, "k must be 1 or 2");
+    need(p >= 1 && p <= 10, "degree p must be in 1..10");
+    need(out != nullptr, "null output");
+    const std::vector<double>& R = mixed_reference_tables(k, p);
+    std::copy(R.begin(), R.end(), out);
+  });
+}
+
 int riesz_setup_device(riesz_handle* h, void* stream) {
   return guarded([&] {
     need(h != nullptr, "null handle");

@@ -58,6 +58,7 @@ _SIGS = {
     "riesz_patch_count": (_I, [_P, _P]),
     "riesz_patch_map": (_I, [_P, _P, _P]),
     "riesz_ref_tabulate": (_I, [_I, _I, _I64, _P, _P, _P]),
+    "riesz_ref_mixed_tables": (_I, [_I, _I, _P]),
     "riesz_setup_device": (_I, [_P, _P]),
     "riesz_setup": (_I, [_I, _I, _I64, _P, _I64, _P, ctypes.POINTER(Opts), _P, ctypes.POINTER(_P)]),
     "riesz_apply": (_I, [_P, _P, _P, _I, _P]),
@@ -155,6 +156,15 @@ def riesz_ref_tabulate(space, p, pts):
     dvals = np.zeros((pts.shape[0], nref, dcomp))
     _check(lib.riesz_ref_tabulate(space, p, pts.shape[0], _ptr(pts), _ptr(vals), _ptr(dvals)))
     return vals, dvals
+
+
+def riesz_ref_mixed_tables(k, p):
+    """Reference coupling tables [6][n_{k-1}][n_k] of the Hodge-Laplace problem (host)."""
+    lib = load_library()
+    nref = {0: (p + 1) * (p + 2) * (p + 3) // 6, 1: p * (p + 2) * (p + 3) // 2, 2: p * (p + 1) * (p + 3) // 2}
+    out = np.zeros((6, nref[k - 1], nref[k]))
+    _check(lib.riesz_ref_mixed_tables(k, p, _ptr(out)))
+    return out
 
 
 def solve_batch(solvers, bs, xs, nrhs=None, stream=None):

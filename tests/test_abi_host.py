@@ -200,3 +200,26 @@ def test_hodge_validation(lib):
         with pytest.raises(rz.RieszError) as e:
             rz.Hodge(1, 2, v, c, 1.0, stream=0)
         assert e.value.code == 6
+
+
+@pytest.mark.parametrize("k,p", [(1, 1), (1, 3), (2, 2), (2, 4)])
+def test_hodge_coupling_tables_match_oracle(lib, k, p):
+    """The library's reference coupling tables, contracted with one cell's metric, give the oracle's
+    (d phi^{k-1}_j, phi^k_i) on that cell (oracle: quadrature of the pulled-back functions)."""
+    from oracle import assemble as asm
+    from oracle.mesh import MeshDofs
+    from oracle.refelem import reference_element
+    rng = np.random.default_rng(k * 10 + p)
+    verts = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=float) + 0.2 * rng.standard_normal((4, 3))
+    cells = np.array([[0, 1, 2, 3]])
+    sp = {1: ("CG", "N1curl"), 2: ("N1curl", "RT")}[k]
+    r0, r1 = reference_element(sp[0], p), reference_element(sp[1], p)
+    B = asm.mixed_matrix(r1, MeshDofs(verts, cells, r1), r0, MeshDofs(verts, cells, r0)).toarray()
+    J, _ = asm.jacobians(verts, cells)
+    J = J[0]
+    d = abs(np.linalg.det(J))
+    G = d * np.linalg.inv(J) @ np.linalg.inv(J).T if k == 1 else J.T @ J / d
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    R = rz.riesz_ref_mixed_tables(k, p)
+    Bl = sum(G[a, b] * R[q] for q, (a, b) in enumerate(pairs))  # [j][i]
+    assert np.abs(Bl.T - B).max() <= 1e-12 * np.abs(B).max()
