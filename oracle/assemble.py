@@ -47,9 +47,12 @@ def physical_tabulation(ref, J, vhat, dhat):
         JiT = np.linalg.inv(J).transpose(0, 2, 1)
         v = np.einsum("cab,pnb->cpna", JiT, vhat)
         d = np.einsum("cab,pnb->cpna", J, dhat) / det[:, None, None, None]
-    else:
+    elif ref.k == 2:
         v = np.einsum("cab,pnb->cpna", J, vhat) / det[:, None, None, None]
         d = dhat[None] / det[:, None, None, None]
+    else:  # 3-forms (DG): v = v_hat / det J, d = 0
+        v = vhat[None] / det[:, None, None, None]
+        d = np.zeros((J.shape[0],) + dhat.shape)
     return v, d, det
 
 

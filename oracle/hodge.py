@@ -2,7 +2,7 @@
 
 Test infrastructure only: the library never imports this module.
 
-For k in {1, 2} find (sigma, u) in X^{k-1} x X^k with
+For k in {1, 2, 3} find (sigma, u) in X^{k-1} x X^k with
     -(sigma, tau) + (u, d tau)         = 0       for all tau in X^{k-1}
      (d sigma, v) + (d u, d v)         = (f, v)  for all v in X^k,
 i.e. the symmetric indefinite block system
@@ -14,7 +14,8 @@ or replaced by the paper's Schwarz preconditioners for each block (Section 7.2: 
 for CG_p, Hiptmair-Toselli for Ned1_p, PAFW_1 edge stars for RT_p, each with W^k).  MINRES (Paige
 and Saunders, 1975) is written out below from the Lanczos recurrence and Givens rotations.
 
-k = 3 (RT_p x DG_{p-1}) needs the DG space, which this project does not build.
+k = 3 is the mixed Poisson problem in RT_p x DG_{p-1} (d^3 = 0, so K_3 = 0); the DG block of the
+preconditioner is its diagonal mass matrix, inverted exactly (point-Jacobi, Section 7.2).
 """
 import numpy as np
 import scipy.linalg
@@ -25,11 +26,11 @@ from . import assemble as asm
 from .mesh import MeshDofs
 from .refelem import reference_element
 
-SPACES = {1: ("CG", "N1curl"), 2: ("N1curl", "RT")}
+SPACES = {1: ("CG", "N1curl"), 2: ("N1curl", "RT"), 3: ("RT", "DG")}
 
 
 class HodgeSystem:
-    """Blocks of the Hodge-Laplace problem of Section 7.2 for k in {1, 2} on one mesh."""
+    """Blocks of the Hodge-Laplace problem of Section 7.2 for k in {1, 2, 3} on one mesh."""
 
     def __init__(self, k, p, verts, cells, gamma=1.0):
         self.k, self.p, self.gamma = k, p, gamma
@@ -66,7 +67,9 @@ class HodgeSystem:
         summand (one-level otherwise)."""
         out = []
         for sp, P, md in ((SPACES[self.k][0], self.P0, self.md0), (SPACES[self.k][1], self.P1, self.md1)):
-            if recommended and sp == "N1curl":
+            if sp == "DG":  # diagonal mass (orthogonal basis): Jacobi is the exact inverse
+                out.append(asm.Preconditioner(P, md, patches=[]))
+            elif recommended and sp == "N1curl":
                 mc = self.md0 if self.k == 1 else MeshDofs(md.verts, md.cells, reference_element("CG", self.p))
                 out.append(asm.HTPreconditioner(P, md, mc, weight=0.5 if coarse else 0.0))
             else:

@@ -151,6 +151,9 @@ def space(family, p, dim):
     if family == "CG":
         E = Expansion(dim, p, 1)
         return E, np.eye(E.n)
+    if family == "DG":  # the last space of the complex whose X^{d-1} is RT_p: P_{p-1}
+        E = Expansion(dim, p - 1, 1)
+        return E, np.eye(E.n)
     E = Expansion(dim, p, dim)
     if family == "N2":
         return E, np.eye(E.n)
@@ -356,10 +359,14 @@ def eigenbasis(family, p, dim):
 # degrees of freedom (Eqs. (3.14), (3.16), (3.18)) and the dual basis
 # ---------------------------------------------------------------------------
 class RefElement:
-    """Reference element of the paper for space in {'CG', 'N1curl', 'N2curl', 'RT'}, degree p.
+    """Reference element of the paper for space in {'CG', 'N1curl', 'N2curl', 'RT', 'DG'}, degree p.
 
     'N2curl' (second-kind Nedelec) is built only because the H(div) degrees of
-    freedom use its bubbles; the solver spaces are CG, N1curl and RT.
+    freedom use its bubbles; the Riesz-map spaces are CG, N1curl and RT.  'DG' is
+    X^3 = DG_{p-1} of the complex ending in RT_p (the k = 3 Hodge-Laplace problem):
+    the cell DOFs of the abstract definition with k = d, i.e. the mean (1, v)_T and
+    the moments (div Phi_{C,j}, v)_T against the divergences of the RT_p interior
+    eigenbasis; v pulls back as a 3-form, v = v_hat / det J.
 
     Attributes
     ----------
@@ -372,8 +379,8 @@ class RefElement:
 
     def __init__(self, space_name, p):
         self.space, self.p = space_name, p
-        fam = {"CG": "CG", "N1curl": "N1", "N2curl": "N2", "RT": "RT"}[space_name]
-        self.k = {"CG": 0, "N1curl": 1, "N2curl": 1, "RT": 2}[space_name]
+        fam = {"CG": "CG", "N1curl": "N1", "N2curl": "N2", "RT": "RT", "DG": "DG"}[space_name]
+        self.k = {"CG": 0, "N1curl": 1, "N2curl": 1, "RT": 2, "DG": 3}[space_name]
         self.fam = fam
         # the H(grad) degree of the complex X^0 -> X^1 used by the H(curl) DOFs
         self.p0 = p + 1 if fam == "N2" else p
@@ -398,6 +405,17 @@ class RefElement:
             start = sum(r.shape[0] for r in rows)
             rows.append(R)
             ent.setdefault(key, []).extend(range(start, start + R.shape[0]))
+
+        if k == 3:  # DG_{p-1}: only cell DOFs
+            Xc, wc = quadrature(3, p + 2)
+            val, _ = E.tab(Xc)
+            add((3, 0), (wc[:, None] * val[:, :, 0]).sum(0)[None, :])  # Whitney (1, v)_T
+            ER, YR, _ = eigenbasis("RT", p, 3)
+            if YR.shape[1]:
+                _, jR = ER.tab(Xc)
+                dphi = np.einsum("pn,nj->pj", ddiv(jR), YR)
+                add((3, 0), np.einsum("pj,pn,p->jn", dphi, val[:, :, 0], wc))  # type II
+            return np.concatenate(rows, 0), ent
 
         V3 = REF_VERTS[3]
         # edge and face rules (intrinsic coordinates)
@@ -500,8 +518,10 @@ class RefElement:
             d = J[:, :, 0, :]
         elif self.k == 1:
             d = dcurl3(J)
-        else:
+        elif self.k == 2:
             d = ddiv(J)[..., None]
+        else:  # d^3 = 0
+            d = np.zeros(v.shape[:2] + (1,))
         return v, d
 
     def ref_matrices(self):

@@ -6,6 +6,7 @@ import scipy.sparse.linalg
 
 from oracle import assemble as asm
 from oracle import hodge
+from oracle.refelem import reference_element
 from paper_2506_17406_gb300.inputs import fichera_mesh, kuhn_mesh, normal_vector
 
 
@@ -115,3 +116,62 @@ def test_schwarz_block_preconditioner(k):
         assert np.linalg.norm(x - xe) <= 1e-7 * np.linalg.norm(xe)
         its.append(it)
     assert its[1] <= 1.1 * its[0] + 2
+
+
+def test_dg_basis_orthogonal_and_div_map():
+    """X^3 = DG_{p-1} (the abstract DOFs with k = d): its reference mass matrix is diagonal (the paper's
+    reason for point-Jacobi on DG in Section 7.2), and div maps RT_p onto DG_{p-1} with an exact
+    coefficient map -- the signed face-cell incidence on the Whitney functions and the identity from
+    the RT interior type-I functions onto the DG type-II functions (Lemma 4.3 at k = 2) -- so the
+    coupling of the k = 3 problem is B = M_3 D."""
+    for p in (1, 3):
+        M, _ = reference_element("DG", p).ref_matrices()
+        assert np.abs(M - np.diag(np.diag(M))).max() <= 1e-13 * np.abs(M).max()
+    v, c = fichera_mesh(2, 0.1, 5)
+    h = hodge.HodgeSystem(3, 3, v, c)
+    assert abs(h.K1).max() == 0.0
+    # D = M_3^{-1} B must be the structured map: integer entries, identity on the interior type-I DOFs
+    D = scipy.sparse.diags(1.0 / h.M1.diagonal()) @ h.B
+    Dd = D.toarray()
+    assert np.abs(Dd - np.round(Dd)).max() <= 1e-9
+    rt, dg = h.md0, h.md1
+    nI = dg.per_entity[3] - 1  # RT interior type-I (div-type) DOFs = DG type-II DOFs
+    for cell in range(len(c)):
+        # the DG Whitney row: the Whitney DOFs of the cell's four faces with +-1, nothing else
+        row = Dd[dg.cell_dofs[cell, 0]]
+        nz = np.nonzero(np.abs(row) > 1e-9)[0]
+        assert len(nz) == 4 and np.all(np.abs(np.abs(row[nz]) - 1.0) <= 1e-9)
+        assert set(nz) <= set(rt._offsets[2] + rt.per_entity[2] * rt.cell_faces[cell])
+        # the DG type-II rows: the identity onto the cell's RT interior type-I DOFs
+        for m in range(nI):
+            row = Dd[dg.cell_dofs[cell, 1 + m]]
+            nz = np.nonzero(np.abs(row) > 1e-9)[0]
+            assert list(nz) == [rt.n_interface + rt.per_entity[3] * cell + m]
+            assert abs(row[nz[0]] - 1.0) <= 1e-9
+
+
+@pytest.mark.parametrize("p,gamma", [(1, 1.0), (2, 1e3)])
+def test_theorem_c1_spectrum_k3(p, gamma):
+    """Theorem C.1 for the mixed Poisson problem (k = 3): -1 with multiplicity dim RT_p and
+    nu gamma / (nu gamma + 1) for the nonzero div-div/mass eigenvalues nu of RT_p (one per DG DOF)."""
+    v, c = fichera_mesh(2, 0.1, 2)
+    h = hodge.HodgeSystem(3, p, v, c, gamma)
+    P = scipy.sparse.block_diag([h.P0, h.P1]).toarray()
+    lam = np.sort(scipy.linalg.eigh(h.A.toarray(), P, eigvals_only=True))
+    exp = hodge.predicted_spectrum(h)
+    assert len(exp) == h.n0 + h.n1
+    assert np.abs(lam - exp).max() <= 1e-8
+
+
+def test_minres_k3():
+    """Mixed Poisson: MINRES reaches the direct solution with the exact preconditioner in a handful of
+    iterations at gamma = 1e3 (the paper: 3 at p = 1) and with the Schwarz/Jacobi blocks."""
+    v, c = fichera_mesh(2, 0.1, 1)
+    for gamma, bound in ((1.0, 12), (1e3, 6)):
+        h = hodge.HodgeSystem(3, 2, v, c, gamma)
+        b = h.rhs(normal_vector(h.n1, 4))
+        xe = scipy.sparse.linalg.splu(h.A.tocsc()).solve(b)
+        x, it, _ = hodge.minres(h.A, b, h.exact_preconditioner(), rtol=1e-10)
+        assert np.linalg.norm(x - xe) <= 1e-7 * np.linalg.norm(xe) and it <= bound
+        x, it, _ = hodge.minres(h.A, b, h.schwarz_preconditioner(True), rtol=1e-10, maxit=1000)
+        assert np.linalg.norm(x - xe) <= 1e-7 * np.linalg.norm(xe)
