@@ -223,3 +223,21 @@ def test_hodge_coupling_tables_match_oracle(lib, k, p):
     R = rz.riesz_ref_mixed_tables(k, p)
     Bl = sum(G[a, b] * R[q] for q, (a, b) in enumerate(pairs))  # [j][i]
     assert np.abs(Bl.T - B).max() <= 1e-12 * np.abs(B).max()
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_ht_edge_star_patches_match_oracle(lib, p):
+    """The library's Hiptmair-Toselli edge stars (Eq. (6.19): the edge's Whitney DOF and the type-I DOFs of
+    every face containing it) are the oracle's, bit-exact, edge by edge."""
+    from oracle import assemble as asm
+    from oracle.mesh import MeshDofs
+    from oracle.refelem import reference_element
+    v, c = kuhn_mesh(2, 0.1, 3)
+    h = rz.Riesz("N1curl", p, v, c, device=False, decomposition=rz.DECOMP_HT)
+    off, dofs = h.patch_map()
+    mn = MeshDofs(v, c, reference_element("N1curl", p))
+    mc = MeshDofs(v, c, reference_element("CG", p))
+    exp = asm.edge_star_type1_dofs(mn, mc)
+    assert len(off) == len(exp) + 1
+    for e, q in enumerate(exp):
+        assert np.array_equal(dofs[off[e]:off[e + 1]], q)
