@@ -204,6 +204,13 @@ int riesz_patch_count(const riesz_handle* h, int64_t* npatches);
    potential problems live on the CG_p vertex stars. */
 int riesz_patch_map(const riesz_handle* h, int64_t* offsets, int32_t* dofs);
 
+/* The gradient map of a RIESZ_DECOMP_HT handle (Eq. (5.3)) as a signed CSR
+   list over the Ned1_p interface DOFs: row d lists the CG_p interface DOFs c
+   with the coefficient (+1 or -1) of grad phi^CG_c in Ned1_p DOF d.
+   ptr: host [n_interface + 1]; idx, sgn: host [ptr[n_interface]] (query the
+   size with idx == NULL).  RIESZ_ERR_INVALID_ARG for other handles. */
+int riesz_ht_gradient_map(const riesz_handle* h, int64_t* ptr, int32_t* idx, float* sgn);
+
 /* Tabulate the reference basis of (space, p) at npts points of the reference
    tetrahedron (edge length 2, centroid 0, vertices (-1,-1/sqrt3,-1/sqrt6),
    (1,-1/sqrt3,-1/sqrt6), (0,2/sqrt3,-1/sqrt6), (0,0,3/sqrt6)).

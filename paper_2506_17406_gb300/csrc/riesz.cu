@@ -2202,6 +2202,16 @@ int riesz_patch_map(const riesz_handle* h, int64_t* offsets, int32_t* dofs) {
   });
 }
 
+int riesz_ht_gradient_map(const riesz_handle* h, int64_t* ptr, int32_t* idx, float* sgn) {
+  return guarded([&] {
+    need(h != nullptr && ptr != nullptr, "null argument");
+    need(h->ht, "not a Hiptmair-Toselli handle");
+    std::copy(h->gg_ptr.begin(), h->gg_ptr.end(), ptr);
+    if (idx) std::copy(h->gg_idx.begin(), h->gg_idx.end(), idx);
+    if (sgn) std::copy(h->gg_sgn.begin(), h->gg_sgn.end(), sgn);
+  });
+}
+
 int riesz_ref_tabulate(int space, int p, int64_t npts, const double* pts, double* vals, double* dvals) {
   return guarded([&] {
     need(space >= 0 && space <= 2 && p >= 1 && p <= 10, "bad space or degree");

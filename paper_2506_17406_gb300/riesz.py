@@ -57,6 +57,7 @@ _SIGS = {
     "riesz_dof_map": (_I, [_P, _P]),
     "riesz_patch_count": (_I, [_P, _P]),
     "riesz_patch_map": (_I, [_P, _P, _P]),
+    "riesz_ht_gradient_map": (_I, [_P, _P, _P, _P]),
     "riesz_ref_tabulate": (_I, [_I, _I, _I64, _P, _P, _P]),
     "riesz_ref_mixed_tables": (_I, [_I, _I, _P]),
     "riesz_setup_device": (_I, [_P, _P]),
@@ -233,6 +234,16 @@ class Riesz:
         dofs = np.zeros(int(off[-1]), dtype=np.int32)
         _check(self.lib.riesz_patch_map(self.h, _ptr(off), _ptr(dofs)))
         return off, dofs
+
+    def ht_gradient_map(self, n_interface):
+        """(ptr, idx, sgn): the gradient map of a Hiptmair-Toselli handle as a signed CSR list over the
+        Ned1_p interface DOFs (columns: CG_p interface DOFs)."""
+        ptr = np.zeros(n_interface + 1, dtype=np.int64)
+        _check(self.lib.riesz_ht_gradient_map(self.h, _ptr(ptr), None, None))
+        idx = np.zeros(int(ptr[-1]), dtype=np.int32)
+        sgn = np.zeros(int(ptr[-1]), dtype=np.float32)
+        _check(self.lib.riesz_ht_gradient_map(self.h, _ptr(ptr), _ptr(idx), _ptr(sgn)))
+        return ptr, idx, sgn
 
     def stats(self):
         out = np.zeros(8)

@@ -241,3 +241,25 @@ def test_ht_edge_star_patches_match_oracle(lib, p):
     assert len(off) == len(exp) + 1
     for e, q in enumerate(exp):
         assert np.array_equal(dofs[off[e]:off[e + 1]], q)
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_ht_gradient_map_matches_oracle(lib, p):
+    """The library's gradient map (Eq. (5.3): signed vertex-edge incidence on the Whitney DOFs, identity from CG
+    edge/face DOFs onto the Ned1 type-II DOFs) equals the oracle's gradient_matrix on the interface, bit-exact."""
+    from oracle import assemble as asm
+    from oracle.mesh import MeshDofs
+    from oracle.refelem import reference_element
+    v, c = kuhn_mesh(2, 0.1, 3)
+    h = rz.Riesz("N1curl", p, v, c, device=False, decomposition=rz.DECOMP_HT)
+    mn = MeshDofs(v, c, reference_element("N1curl", p))
+    mc = MeshDofs(v, c, reference_element("CG", p))
+    ptr, idx, sgn = h.ht_gradient_map(mn.n_interface)
+    G = asm.gradient_matrix(mn, mc).tocsr()[:mn.n_interface, :mc.n_interface].toarray()
+    Gl = np.zeros_like(G)
+    for d in range(mn.n_interface):
+        for k in range(ptr[d], ptr[d + 1]):
+            Gl[d, idx[k]] += sgn[k]
+    assert np.array_equal(Gl, G)
+    with pytest.raises(rz.RieszError):
+        rz.Riesz("N1curl", p, v, c, device=False).ht_gradient_map(mn.n_interface)
