@@ -51,6 +51,10 @@ typedef struct riesz_handle riesz_handle;
 typedef struct riesz_hodge riesz_hodge;
 
 enum { RIESZ_H1 = 0, RIESZ_HCURL = 1, RIESZ_HDIV = 2 };
+/* X^3 = DG_{p-1}, the last space of the complex ending in RT_p: only for
+   riesz_ref_tabulate (no Riesz-map handle: its Riesz map is the diagonal
+   mass matrix). */
+enum { RIESZ_L2 = 3 };
 
 enum {
   RIESZ_OK = 0,
@@ -215,11 +219,17 @@ int riesz_ht_gradient_map(const riesz_handle* h, int64_t* ptr, int32_t* idx, flo
    tetrahedron (edge length 2, centroid 0, vertices (-1,-1/sqrt3,-1/sqrt6),
    (1,-1/sqrt3,-1/sqrt6), (0,2/sqrt3,-1/sqrt6), (0,0,3/sqrt6)).
    vals: host [npts][n_ref][ncomp]; dvals: host [npts][n_ref][dcomp] (grad,
-   curl or div); either may be NULL. */
+   curl or div); either may be NULL.  space = RIESZ_L2: DG_{p-1}, n_ref =
+   p(p+1)(p+2)/6, ncomp = dcomp = 1, the basis dual to the mean and the
+   moments against the divergences of the RT_p interior eigenbasis (values
+   1/|T| and div Phi_{C,j}); dvals are zero (d^3 = 0). */
 int riesz_ref_tabulate(int space, int p, int64_t npts, const double* pts, double* vals, double* dvals);
 
 /* Reference coupling tables of the Hodge-Laplace problem (k = 1: CG_p -> Ned1_p,
-   k = 2: Ned1_p -> RT_p): out host [6][n_{k-1}][n_k], entry [q][j][i] =
+   k = 2: Ned1_p -> RT_p, k = 3: RT_p -> DG_{p-1}): for k = 3, out host
+   [1][n_RT][n_DG], entry [j][i] = (div phi^RT_j, psi^DG_i) on the reference
+   cell, scaled on a cell by 1 / |det J|; for k = 1, 2, out host
+   [6][n_{k-1}][n_k], entry [q][j][i] =
    integral over the reference tetrahedron of (d phi^{k-1}_j)_b (phi^k_i)_a
    (+ the same with a and b exchanged when a != b) for the metric entry
    q = (a, b) in the order 00, 11, 22, 01, 02, 12.  On a cell,

@@ -1051,9 +1051,47 @@ const RefElement& reference_element(int space, int p) {
   });
 }
 
+int dg_dim(int p) { return p * (p + 1) * (p + 2) / 6; }
+
+void dg_tabulate(int p, int npt, const double* x, double* vals) {
+  const EigenBasis& A = eig_cached(RT, p, 3);
+  const int n1 = A.Y.n, n = 1 + n1;
+  if (n != dg_dim(p)) throw std::runtime_error("DG basis: dimension mismatch");
+  double E[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) E[r][c] = vert(3, r + 1, c) - vert(3, 0, c);
+  const double det = E[0][0] * (E[1][1] * E[2][2] - E[1][2] * E[2][1]) - E[0][1] * (E[1][0] * E[2][2] - E[1][2] * E[2][0]) +
+                     E[0][2] * (E[1][0] * E[2][1] - E[1][1] * E[2][0]);
+  const double vol = std::fabs(det) / 6.0;
+  std::vector<double> v1, d1;
+  int nd1 = 0;
+  if (n1) eig_tab(A, 2, npt, x, v1, d1, nd1);
+  for (int i = 0; i < npt; ++i) {
+    vals[(size_t)i * n] = 1.0 / vol;  // dual to the mean (1, v)_T
+    for (int j = 0; j < n1; ++j) vals[(size_t)i * n + 1 + j] = d1[(size_t)i * n1 + j];  // div Phi_{C,j}
+  }
+}
+
 const std::vector<double>& mixed_reference_tables(int k, int p) {
   static OnceCache<std::pair<int, int>, std::vector<double>> cache;
-  if (k < 1 || k > 2) throw std::runtime_error("mixed_reference_tables: k must be 1 or 2");
+  if (k < 1 || k > 3) throw std::runtime_error("mixed_reference_tables: k must be 1, 2 or 3");
+  if (k == 3)
+    return cache.get(std::make_pair(k, p), [&] {
+      const RefElement& R0 = reference_element(HDIV, p);
+      const int n0 = R0.nref, n1 = dg_dim(p);
+      Rule Q = simplex_rule(3, p + 2);
+      const int np = Q.npt();
+      std::vector<double> d0((size_t)np * n0), v1((size_t)np * n1);
+      R0.tabulate(np, Q.x.data(), nullptr, d0.data());
+      dg_tabulate(p, np, Q.x.data(), v1.data());
+      Mat D(np, n0), V(np, n1);
+      for (int q = 0; q < np; ++q) {
+        for (int j = 0; j < n0; ++j) D(q, j) = d0[(size_t)q * n0 + j];
+        for (int i = 0; i < n1; ++i) V(q, i) = v1[(size_t)q * n1 + i];
+      }
+      const Mat G = gram_tn(D, Q.w, V);  // [j][i] = sum w div phi^RT_j psi^DG_i
+      return std::make_shared<std::vector<double>>(G.a);
+    });
   return cache.get(std::make_pair(k, p), [&] {
     const RefElement& R0 = reference_element(k - 1, p);  // X^{k-1}: CG_p or Ned1_p
     const RefElement& R1 = reference_element(k, p);      // X^k: Ned1_p or RT_p

@@ -56,6 +56,15 @@ const RefElement& reference_element(int space, int p);
 // (n_{k-1} x n_k), one per symmetric metric entry (00, 11, 22, 01, 02, 12), the
 // off-diagonal ones holding both orderings; contracted against the X^k mass
 // factors of a cell (|det J| J^{-1}J^{-T} for k = 1, J^T J / |det J| for k = 2).
+// k = 3 (RT_p -> DG_{p-1}): one matrix [j][i] (n_RT x n_DG) of
+// (div phi^RT_j, psi^DG_i), contracted with the single factor 1 / |det J|.
 const std::vector<double>& mixed_reference_tables(int k, int p);
+
+// X^3 = DG_{p-1} of the complex ending in RT_p: the dual basis of the paper's
+// cell DOFs at k = d, (1, v)_T and (div Phi_{C,j}, v)_T with Phi the RT_p
+// interior type-I eigenbasis normalised by (div Phi_i, div Phi_j) = delta_ij;
+// it is {1 / |T|} followed by {div Phi_{C,j}}, L2-orthogonal.
+int dg_dim(int p);
+void dg_tabulate(int p, int npt, const double* x, double* vals);  // vals [npt][dg_dim(p)]
 
 }  // namespace riesz

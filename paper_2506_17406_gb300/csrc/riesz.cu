@@ -2214,15 +2214,21 @@ int riesz_ht_gradient_map(const riesz_handle* h, int64_t* ptr, int32_t* idx, flo
 
 int riesz_ref_tabulate(int space, int p, int64_t npts, const double* pts, double* vals, double* dvals) {
   return guarded([&] {
-    need(space >= 0 && space <= 2 && p >= 1 && p <= 10, "bad space or degree");
+    need(space >= 0 && space <= 3 && p >= 1 && p <= 10, "bad space or degree");
     need(npts >= 0 && (npts == 0 || pts != nullptr), "bad points");
+    if (space == RIESZ_L2) {  // DG_{p-1}: values only, d = 0
+      const int n = dg_dim(p);
+      if (vals) dg_tabulate(p, (int)npts, pts, vals);
+      if (dvals) std::fill(dvals, dvals + (size_t)npts * n, 0.0);
+      return;
+    }
     reference_element(space, p).tabulate((int)npts, pts, vals, dvals);
   });
 }
 
 int riesz_ref_mixed_tables(int k, int p, double* out) {
   return guarded([&] {
-    need(k == 1 || k == 2, "k must be 1 or 2");
+    need(k >= 1 && k <= 3, "k must be 1, 2 or 3");
     need(p >= 1 && p <= 10, "degree p must be in 1..10");
     need(out != nullptr, "null output");
     const std::vector<double>& R = mixed_reference_tables(k, p);

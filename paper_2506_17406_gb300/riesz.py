@@ -13,8 +13,8 @@ import numpy as np
 
 from . import build as _build
 
-H1, HCURL, HDIV = 0, 1, 2
-SPACES = {"CG": H1, "H1": H1, "N1curl": HCURL, "HCURL": HCURL, "RT": HDIV, "HDIV": HDIV}
+H1, HCURL, HDIV, L2 = 0, 1, 2, 3
+SPACES = {"CG": H1, "H1": H1, "N1curl": HCURL, "HCURL": HCURL, "RT": HDIV, "HDIV": HDIV, "DG": L2, "L2": L2}
 PREC_FP64, PREC_FP32 = 0, 1
 APPLY_MATRIX_FREE, APPLY_ELEMENT = 0, 1
 LOOP_HOST, LOOP_GRAPH = 0, 1
@@ -149,10 +149,10 @@ def riesz_ref_tabulate(space, p, pts):
     lib = load_library()
     space = SPACES.get(space, space)
     pts = np.ascontiguousarray(pts, dtype=np.float64)
-    ncomp = 1 if space == H1 else 3
-    dcomp = 1 if space == HDIV else 3
+    ncomp = 1 if space in (H1, L2) else 3
+    dcomp = 1 if space in (HDIV, L2) else 3
     nref = {H1: (p + 1) * (p + 2) * (p + 3) // 6, HCURL: p * (p + 2) * (p + 3) // 2,
-            HDIV: p * (p + 1) * (p + 3) // 2}[space]
+            HDIV: p * (p + 1) * (p + 3) // 2, L2: p * (p + 1) * (p + 2) // 6}[space]
     vals = np.zeros((pts.shape[0], nref, ncomp))
     dvals = np.zeros((pts.shape[0], nref, dcomp))
     _check(lib.riesz_ref_tabulate(space, p, pts.shape[0], _ptr(pts), _ptr(vals), _ptr(dvals)))
@@ -162,8 +162,9 @@ def riesz_ref_tabulate(space, p, pts):
 def riesz_ref_mixed_tables(k, p):
     """Reference coupling tables [6][n_{k-1}][n_k] of the Hodge-Laplace problem (host)."""
     lib = load_library()
-    nref = {0: (p + 1) * (p + 2) * (p + 3) // 6, 1: p * (p + 2) * (p + 3) // 2, 2: p * (p + 1) * (p + 3) // 2}
-    out = np.zeros((6, nref[k - 1], nref[k]))
+    nref = {0: (p + 1) * (p + 2) * (p + 3) // 6, 1: p * (p + 2) * (p + 3) // 2, 2: p * (p + 1) * (p + 3) // 2,
+            3: p * (p + 1) * (p + 2) // 6}
+    out = np.zeros((1 if k == 3 else 6, nref[k - 1], nref[k]))
     _check(lib.riesz_ref_mixed_tables(k, p, _ptr(out)))
     return out
 

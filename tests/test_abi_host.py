@@ -263,3 +263,41 @@ def test_ht_gradient_map_matches_oracle(lib, p):
     assert np.array_equal(Gl, G)
     with pytest.raises(rz.RieszError):
         rz.Riesz("N1curl", p, v, c, device=False).ht_gradient_map(mn.n_interface)
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_dg_reference_basis_matches_oracle(lib, p):
+    """DG_{p-1} (X^3): the library's basis (1/|T| and the divergences of its RT_p interior eigenbasis) equals
+    the oracle's dual basis of the cell DOFs at random reference points; d = 0."""
+    from oracle.refelem import reference_element
+    rng = np.random.default_rng(p)
+    lam = rng.dirichlet(np.ones(4), size=40)
+    V = np.array([[-1, -1 / np.sqrt(3), -1 / np.sqrt(6)], [1, -1 / np.sqrt(3), -1 / np.sqrt(6)],
+                  [0, 2 / np.sqrt(3), -1 / np.sqrt(6)], [0, 0, 3 / np.sqrt(6)]])
+    X = lam @ V
+    vals, dvals = rz.riesz_ref_tabulate("DG", p, X)
+    ve, _ = reference_element("DG", p).tabulate(X)
+    assert vals.shape == ve.shape
+    assert np.abs(vals - ve).max() <= 1e-11 * np.abs(ve).max()
+    assert np.all(dvals == 0.0)
+    with pytest.raises(rz.RieszError):
+        rz.Riesz("DG", p, *kuhn_mesh(1), device=False)
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_hodge_coupling_tables_k3_match_oracle(lib, p):
+    """k = 3: (div phi^RT_j, psi^DG_i) on a random cell is the library's reference table over |det J| (the
+    3-form and contravariant pullbacks leave a single metric factor)."""
+    from oracle import assemble as asm
+    from oracle.mesh import MeshDofs
+    from oracle.refelem import reference_element
+    rng = np.random.default_rng(30 + p)
+    verts = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=float) + 0.2 * rng.standard_normal((4, 3))
+    cells = np.array([[0, 1, 2, 3]])
+    r0, r1 = reference_element("RT", p), reference_element("DG", p)
+    B = asm.mixed_matrix(r1, MeshDofs(verts, cells, r1), r0, MeshDofs(verts, cells, r0)).toarray()
+    J, _ = asm.jacobians(verts, cells)
+    R = rz.riesz_ref_mixed_tables(3, p)
+    assert R.shape[0] == 1
+    Bl = R[0] / abs(np.linalg.det(J[0]))
+    assert np.abs(Bl.T - B).max() <= 1e-12 * np.abs(B).max()
