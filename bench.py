@@ -84,9 +84,10 @@ def parse():
                     help="device-driven (CUDA graph) or host-driven PCG iterations; same kernels, same results")
     ap.add_argument("--p-sweep", action="store_true",
                     help="iteration counts against the degree p on a fixed mesh (p-robustness table)")
-    ap.add_argument("--hodge", type=int, default=0, choices=[0, 1, 2],
-                    help="Hodge-Laplace problem of Section 7.2 (k = 1: CG_p x Ned1_p, k = 2: Ned1_p x RT_p) on "
-                         "a Kuhn Fichera corner, MINRES with the augmented-Lagrangian preconditioner")
+    ap.add_argument("--hodge", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="Hodge-Laplace problem of Section 7.2 (k = 1: CG_p x Ned1_p, k = 2: Ned1_p x RT_p, "
+                         "k = 3: RT_p x DG_{p-1}) on a Kuhn Fichera corner, MINRES with the augmented-Lagrangian "
+                         "preconditioner")
     ap.add_argument("--hodge-p", type=int, default=4)
     ap.add_argument("--hodge-n", type=int, default=8)
     ap.add_argument("--gamma", type=float, default=1e3)
@@ -453,8 +454,8 @@ def run_hodge(args):
     h = rz.Hodge(k, p, verts, cells, gamma, decomposition=rz.DECOMP_HT, precond_precision=prec,
                  rtol=1e-8, maxit=5000)
     stream = torch.cuda.current_stream()
-    fcg_h = np.zeros((3, h.n_cg))
-    fcg_h[:, :len(verts)] = 1.0  # f = (1,1,1): the vertex (Whitney) functions sum to one
+    fcg_h = np.zeros((3 if k < 3 else 1, h.n_cg))
+    fcg_h[:, :len(verts)] = 1.0  # f = (1,1,1) (f = 1 for k = 3): the vertex (Whitney) functions sum to one
     fcg = torch.tensor(fcg_h, device="cuda")
     verts_d = torch.tensor(verts, device="cuda")
     b = torch.zeros(h.N, dtype=torch.float64, device="cuda")
@@ -497,12 +498,12 @@ def run_hodge(args):
     e1.record(stream)
     torch.cuda.synchronize()
     apply_ms = e0.elapsed_time(e1) / 20
-    sp = {1: ("CG", "N1curl"), 2: ("N1curl", "RT")}[k]
+    sp = {1: ("CG", "N1curl"), 2: ("N1curl", "RT"), 3: ("RT", "DG")}[k]
     nref = {"CG": (p + 1) * (p + 2) * (p + 3) // 6, "N1curl": p * (p + 2) * (p + 3) // 2,
-            "RT": p * (p + 1) * (p + 3) // 2}
+            "RT": p * (p + 1) * (p + 3) // 2, "DG": p * (p + 1) * (p + 2) // 6}
     n0, n1 = nref[sp[0]], nref[sp[1]]
     C = len(cells)
-    flops = 2.0 * C * (n1 * n1 + 2 * n0 * n1 + n0 * n0)
+    flops = 2.0 * C * ((n1 * n1 if k < 3 else 0) + 2 * n0 * n1 + n0 * n0)
     tf = flops / (apply_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
             "frac": tf / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": "k_hodge_apply (+2 k_gather_iface)",

@@ -377,8 +377,10 @@ const char* riesz_last_error(void);
 /* ---- Hodge-Laplace problems (Section 7.2) ----------------------------- */
 
 /* The mixed Hodge-Laplace problem of Eq. (7.5) for k = 1 (sigma in CG_p,
-   u in Ned1_p) or k = 2 (sigma in Ned1_p, u in RT_p) on one mesh, pure
-   Neumann (the paper's Fichera corner has Gamma_N = the whole boundary):
+   u in Ned1_p), k = 2 (sigma in Ned1_p, u in RT_p) or k = 3 (sigma in RT_p,
+   u in DG_{p-1}: mixed Poisson, d^3 = 0; DG DOFs cell-major, dg_dim(p) =
+   p(p+1)(p+2)/6 per cell) on one mesh, pure Neumann (the paper's Fichera
+   corner has Gamma_N = the whole boundary):
      -(sigma, tau) + (u, d tau) = 0,   (d sigma, v) + (d u, d v) = (f, v).
    Block vectors are device [sigma (n0) | u (n1)] FP64 (riesz_hodge_sizes),
    each block in the numbering of riesz_dof_map of its space.
@@ -391,7 +393,9 @@ const char* riesz_last_error(void);
    Section 7.2 (vertex stars for CG_p, Hiptmair-Toselli for Ned1_p, edge
    stars for RT_p).  opts->precond_precision, coarse, autotune, rtol and
    maxit apply; alpha, beta, nrhs_max, loop, apply_mode and apply_precision
-   are set internally; dirichlet must be 0.  gamma > 0.
+   are set internally; dirichlet must be 0.  gamma > 0.  For k = 3 the DG
+   block gamma^{-1} M_DG is diagonal (the DG basis is L2-orthogonal) and is
+   inverted exactly.
    Setup builds both blocks' maps on the host and runs the device setup on
    the current device (stream may be NULL); the handle owns all its memory. */
 int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t ncells, const int64_t* cells,
@@ -405,7 +409,8 @@ int riesz_hodge_apply(riesz_hodge* h, const double* x, double* y, void* stream);
 /* z = P^{-1} r, the block-diagonal preconditioner above.  r, z: device [n0 + n1]. */
 int riesz_hodge_precond(riesz_hodge* h, const double* r, double* z, void* stream);
 /* b = [0 | (f, v)_{v in X^k}] for f with CG_p coefficients per Cartesian
-   component (device [3][n_cg], as riesz_load on X^k).  b: device [n0 + n1]. */
+   component (device [3][n_cg], as riesz_load on X^k; for k = 3 a scalar f,
+   device [n_cg]).  b: device [n0 + n1]. */
 int riesz_hodge_load(riesz_hodge* h, const double* fcg, double* b, void* stream);
 /* New vertex coordinates (device [nverts][3], same connectivity): recompute
    every block's element matrices, patch factors and the coupling. */

@@ -2074,17 +2074,18 @@ __global__ void k_load(int space, int64_t C, int n, int nif, int ncg, const doub
 //   [ -M_{k-1}  B^T ] [sigma]
 //   [  B        K_k ] [u    ],   B_ij = (d phi^{k-1}_j, phi^k_i).
 // ---------------------------------------------------------------------------
-// Coupling element matrices Be[c][j][i] = sum_q g_q(c) R_q[j][i] over the six
-// metric entries of the X^k mass factors (j < n0 in X^{k-1}, i < n1 in X^k).
-__global__ void k_mixed_elem(int64_t C, int n0, int n1, const double* __restrict__ g, const double* __restrict__ R,
-                             double* __restrict__ Be) {
+// Coupling element matrices Be[c][j][i] = sum_q g_q(c) R_q[j][i] (j < n0 in X^{k-1},
+// i < n1 in X^k): Q = 6 metric entries of the X^k mass factors for k = 1, 2; Q = 1,
+// the factor 1 / |det J|, for k = 3.
+__global__ void k_mixed_elem(int64_t C, int n0, int n1, int Q, const double* __restrict__ g,
+                             const double* __restrict__ R, double* __restrict__ Be) {
   const int64_t c = blockIdx.x;
   const int64_t nn = (int64_t)n0 * n1;
   double gq[6];
-  for (int q = 0; q < 6; ++q) gq[q] = g[q * C + c];
+  for (int q = 0; q < Q; ++q) gq[q] = g[q * C + c];
   for (int64_t t = threadIdx.x; t < nn; t += blockDim.x) {
     double s = 0.0;
-    for (int q = 0; q < 6; ++q) s += gq[q] * R[q * nn + t];
+    for (int q = 0; q < Q; ++q) s += gq[q] * R[q * nn + t];
     Be[c * nn + t] = s;
   }
 }
@@ -2110,12 +2111,13 @@ __global__ void __launch_bounds__(NT) k_hodge_apply(int64_t C, int n0, int n1, i
   for (int t = threadIdx.x; t < n0; t += blockDim.x) xs0[t] = x0[cd0[(int64_t)t * C + c]];
   for (int t = threadIdx.x; t < n1; t += blockDim.x) xs1[t] = x1[cd1[(int64_t)t * C + c]];
   __syncthreads();
-  const double* K = Ke + c * (int64_t)n1 * n1;
+  const double* K = Ke ? Ke + c * (int64_t)n1 * n1 : nullptr;
   const double* M = Me + c * (int64_t)n0 * n0;
   const double* B = Be + c * (int64_t)n0 * n1;
   for (int i = threadIdx.x; i < n1; i += blockDim.x) {
     double a = 0.0;
-    for (int j = 0; j < n1; ++j) a = fma(K[(int64_t)j * n1 + i], xs1[j], a);
+    if (Ke)  // K_3 = 0 (k = 3): no d-stiffness block
+      for (int j = 0; j < n1; ++j) a = fma(K[(int64_t)j * n1 + i], xs1[j], a);
     for (int j = 0; j < n0; ++j) a = fma(B[(int64_t)j * n1 + i], xs0[j], a);
     if (i >= nif1)
       y1[cd1[(int64_t)i * C + c]] = a;
@@ -2141,6 +2143,38 @@ __global__ void __launch_bounds__(NT) k_hodge_apply(int64_t C, int n0, int n1, i
       y0[cd0[(int64_t)j * C + c]] = ys0[j];
     else
       Yc0[(int64_t)j * C + c] = ys0[j];
+  }
+}
+
+// k = 3: X^3 = DG_{p-1} with cell-major DOFs (cell c owns c n .. c n + n - 1).
+// Its weighted Riesz map gamma^{-1} M_DG is diagonal, (1 / |det J|) mhat_i per
+// DOF, so the block preconditioner is dinv = gamma |det J| / mhat_i exactly.
+__global__ void k_dg_diag(int64_t C, int n, const double* __restrict__ jac, const double* __restrict__ mhat,
+                          double gamma, double* __restrict__ dinv) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= C * n) return;
+  const int64_t c = t / n;
+  dinv[t] = gamma * fabs(jac[c * 10 + 9]) / mhat[t % n];
+}
+
+// z = d r elementwise
+__global__ void k_dg_scale(int64_t N, const double* __restrict__ d, const double* __restrict__ r,
+                           double* __restrict__ z) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < N) z[i] = d[i] * r[i];
+}
+
+// b[c n + i] = (f, psi_i)_T = sign(det J) sum_a f_a X[a][i] for a scalar source f
+// with CG_p coefficients (the 3-form pullback psi = psi_hat / det J against dx = |det J| dx_hat).
+__global__ void k_dg_load(int64_t C, int n, int ncg, const double* __restrict__ jac,
+                          const int32_t* __restrict__ cg_cdofs, const double* __restrict__ fcg,
+                          const double* __restrict__ X, double* __restrict__ b) {
+  const int64_t c = blockIdx.x;
+  const double sg = jac[c * 10 + 9] > 0.0 ? 1.0 : -1.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int a = 0; a < ncg; ++a) s += fcg[cg_cdofs[(int64_t)a * C + c]] * X[(int64_t)a * n + i];
+    b[c * n + i] = sg * s;
   }
 }
 

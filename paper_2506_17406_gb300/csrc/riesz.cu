@@ -2495,8 +2495,13 @@ struct riesz_hodge {
   riesz_handle* P0 = nullptr;  // X^{k-1}: (sigma, tau) + gamma (d sigma, d tau), preconditioner block
   riesz_handle* P1 = nullptr;  // X^k: gamma^{-1} (u, v) + (d u, d v), preconditioner block
   riesz_handle* Mh = nullptr;  // X^{k-1} mass (operator only)
-  riesz_handle* Kh = nullptr;  // X^k d-stiffness (operator only)
+  riesz_handle* Kh = nullptr;  // X^k d-stiffness (operator only; none for k = 3, where d^3 = 0)
   int64_t n0 = 0, n1 = 0;
+  // k = 3: X^3 = DG_{p-1}, cell-major DOFs; no handle: its cell map, reference mass diagonal, load
+  // cross table (CG_p -> DG) and the exact inverse of the block gamma^{-1} M_DG
+  int n_dg = 0;
+  DBuf<int32_t> d_dg_cd;
+  DBuf<double> d_dg_mhat, d_dg_X, d_dg_dinv;
   int64_t launches = 0;
   int last_iters = 0;
   double last_relres = 0.0, last_phi = 0.0;
@@ -2506,8 +2511,11 @@ struct riesz_hodge {
   double* h_m = nullptr;
   ~riesz_hodge() {
     if (h_m) cudaFreeHost(h_m);
-    for (auto* b : {&d_R, &d_gB, &d_jacB, &d_Be, &v, &vp, &u, &w, &z, &d1, &d2, &d_m, &d_part}) b->free();
+    for (auto* b : {&d_R, &d_gB, &d_jacB, &d_Be, &v, &vp, &u, &w, &z, &d1, &d2, &d_m, &d_part, &d_dg_mhat, &d_dg_X,
+                    &d_dg_dinv})
+      b->free();
     d_ticket.free();
+    d_dg_cd.free();
     delete P0;
     delete P1;
     delete Mh;
@@ -2525,40 +2533,63 @@ struct riesz_hodge {
 namespace {
 
 void hodge_geometry(riesz_hodge& H, cudaStream_t s) {
-  riesz_handle& K = *H.Kh;
-  const int64_t C = K.C();
+  riesz_handle& M = *H.Mh;
+  const int64_t C = M.C();
+  if (H.k == 3) {
+    // RT_p factors with alpha = 1, beta = 0: g[6] = 1 / |det J|, the single coupling factor
+    dev::k_geom<<<nblk(C, 128), 128, 0, s>>>(2, C, M.d_verts.p, M.d_cells.p, ref_edge_inverse(), 1.0, 0.0,
+                                            H.d_gB.p, H.d_jacB.p);
+    CK(cudaGetLastError());
+    dev::k_mixed_elem<<<(unsigned)C, 256, 0, s>>>(C, M.mesh.nref, H.n_dg, 1, H.d_gB.p + 6 * C, H.d_R.p, H.d_Be.p);
+    CK(cudaGetLastError());
+    dev::k_dg_diag<<<nblk(C * H.n_dg, 256), 256, 0, s>>>(C, H.n_dg, H.d_jacB.p, H.d_dg_mhat.p, H.gamma,
+                                                        H.d_dg_dinv.p);
+    CK(cudaGetLastError());
+    H.launches += 3;
+    return;
+  }
   // the X^k mass factors (beta = 1, alpha = 0) are the metric of the coupling
-  dev::k_geom<<<nblk(C, 128), 128, 0, s>>>(H.k, C, K.d_verts.p, K.d_cells.p, ref_edge_inverse(), 0.0, 1.0, H.d_gB.p,
+  dev::k_geom<<<nblk(C, 128), 128, 0, s>>>(H.k, C, M.d_verts.p, M.d_cells.p, ref_edge_inverse(), 0.0, 1.0, H.d_gB.p,
                                           H.d_jacB.p);
   CK(cudaGetLastError());
-  dev::k_mixed_elem<<<(unsigned)C, 256, 0, s>>>(C, H.Mh->mesh.nref, K.mesh.nref, H.d_gB.p, H.d_R.p, H.d_Be.p);
+  dev::k_mixed_elem<<<(unsigned)C, 256, 0, s>>>(C, M.mesh.nref, H.Kh->mesh.nref, 6, H.d_gB.p, H.d_R.p, H.d_Be.p);
   CK(cudaGetLastError());
   H.launches += 2;
 }
 
 void hodge_apply(riesz_hodge& H, const double* x, double* y, cudaStream_t s) {
   riesz_handle& M = *H.Mh;
-  riesz_handle& K = *H.Kh;
-  const int64_t C = K.C();
-  const int n0 = M.mesh.nref, n1 = K.mesh.nref;
+  riesz_handle* K = H.Kh;  // null for k = 3
+  const int64_t C = M.C();
+  const int n0 = M.mesh.nref, n1 = K ? K->mesh.nref : H.n_dg;
   const size_t sm = (size_t)(2 * n0 + n1) * sizeof(double);
-  dev::k_hodge_apply<<<(unsigned)C, dev::NT, sm, s>>>(C, n0, n1, M.nif, K.nif, M.d_Ae.p, K.d_Ae.p, H.d_Be.p,
-                                                     M.d_cdofs.p, K.d_cdofs.p, x, x + H.n0, y, y + H.n0, M.d_Ycell.p,
-                                                     K.d_Ycell.p);
+  dev::k_hodge_apply<<<(unsigned)C, dev::NT, sm, s>>>(
+      C, n0, n1, M.nif, K ? K->nif : 0, M.d_Ae.p, K ? K->d_Ae.p : nullptr, H.d_Be.p, M.d_cdofs.p,
+      K ? K->d_cdofs.p : H.d_dg_cd.p, x, x + H.n0, y, y + H.n0, M.d_Ycell.p, K ? K->d_Ycell.p : nullptr);
   CK(cudaGetLastError());
-  const int64_t nI0 = M.mesh.n_interface, nI1 = K.mesh.n_interface;
+  const int64_t nI0 = M.mesh.n_interface;
   dev::k_gather_iface<<<nblk(nI0, 256), 256, 0, s>>>(nI0, M.d_sc_ptr.p, M.d_sc_pos.p, M.d_Ycell.p,
                                                      (int64_t)M.nif * C, y, H.n0, 1, nullptr, nullptr);
   CK(cudaGetLastError());
-  dev::k_gather_iface<<<nblk(nI1, 256), 256, 0, s>>>(nI1, K.d_sc_ptr.p, K.d_sc_pos.p, K.d_Ycell.p,
-                                                     (int64_t)K.nif * C, y + H.n0, H.n1, 1, nullptr, nullptr);
-  CK(cudaGetLastError());
-  H.launches += 3;
+  H.launches += 2;
+  if (K && K->mesh.n_interface > 0) {
+    const int64_t nI1 = K->mesh.n_interface;
+    dev::k_gather_iface<<<nblk(nI1, 256), 256, 0, s>>>(nI1, K->d_sc_ptr.p, K->d_sc_pos.p, K->d_Ycell.p,
+                                                       (int64_t)K->nif * C, y + H.n0, H.n1, 1, nullptr, nullptr);
+    CK(cudaGetLastError());
+    ++H.launches;
+  }
 }
 
 void hodge_precond(riesz_hodge& H, const double* r, double* z, cudaStream_t s) {
   op_precond(*H.P0, r, z, 1, s);
-  op_precond(*H.P1, r + H.n0, z + H.n0, 1, s);
+  if (H.P1) {
+    op_precond(*H.P1, r + H.n0, z + H.n0, 1, s);
+  } else {  // k = 3: the diagonal DG block, inverted exactly
+    dev::k_dg_scale<<<nblk(H.n1, 256), 256, 0, s>>>(H.n1, H.d_dg_dinv.p, r + H.n0, z + H.n0);
+    CK(cudaGetLastError());
+    ++H.launches;
+  }
 }
 
 void hodge_dot(riesz_hodge& H, const double* a, const double* b, int op, cudaStream_t s) {
@@ -2651,7 +2682,7 @@ int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t
   return guarded([&] {
     need(out != nullptr, "null output");
     *out = nullptr;
-    need(k == 1 || k == 2, "k must be 1 (CG_p x Ned1_p) or 2 (Ned1_p x RT_p)");
+    need(k >= 1 && k <= 3, "k must be 1 (CG_p x Ned1_p), 2 (Ned1_p x RT_p) or 3 (RT_p x DG_{p-1})");
     need(gamma > 0 && std::isfinite(gamma), "gamma must be positive and finite");
     riesz_opts o;
     riesz_default_opts(&o);
@@ -2670,20 +2701,29 @@ int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t
     b.loop = RIESZ_LOOP_HOST;
     b.apply_mode = RIESZ_APPLY_ELEMENT;
     b.apply_precision = RIESZ_PREC_FP64;
-    // preconditioner blocks: the weighted Riesz maps of Eq. (7.6)
+    // preconditioner blocks: the weighted Riesz maps of Eq. (7.6), with the paper's decomposition of
+    // each space (vertex stars for CG_p, Hiptmair-Toselli for Ned1_p, edge stars for RT_p) or vertex stars
+    auto decomp = [&](int space) {
+      if (!paper) return (int)RIESZ_DECOMP_VERTEX_STAR;
+      return space == RIESZ_HCURL ? (int)RIESZ_DECOMP_HT
+                                  : (space == RIESZ_HDIV ? (int)RIESZ_DECOMP_EDGE_STAR : (int)RIESZ_DECOMP_VERTEX_STAR);
+    };
     riesz_opts o0 = b, o1 = b;
     o0.alpha = gamma;
     o0.beta = 1.0;
-    o0.decomposition = (paper && k == 2) ? RIESZ_DECOMP_HT : RIESZ_DECOMP_VERTEX_STAR;
-    o1.alpha = 1.0;
-    o1.beta = 1.0 / gamma;
-    o1.decomposition = !paper ? RIESZ_DECOMP_VERTEX_STAR : (k == 1 ? RIESZ_DECOMP_HT : RIESZ_DECOMP_EDGE_STAR);
+    o0.decomposition = decomp(k - 1);
     H->P0 = create_handle(k - 1, p, nverts, verts, ncells, cells, o0, true);
-    H->P1 = create_handle(k, p, nverts, verts, ncells, cells, o1, true);
-    // MINRES needs a positive definite preconditioner: the W^k inverses of both blocks by the FP64
+    // MINRES needs a positive definite preconditioner: the W^k inverses of the blocks by the FP64
     // Cholesky route (A_0 = R_0 (M + gamma K) R_0^T and gamma^{-1} M + K reach kappa ~ 1e7 for gamma
     // far from 1, where an explicit Gauss-Jordan inverse, even in FP64, is no longer definite)
-    H->P0->coarse64 = H->P1->coarse64 = true;
+    H->P0->coarse64 = true;
+    if (k < 3) {
+      o1.alpha = 1.0;
+      o1.beta = 1.0 / gamma;
+      o1.decomposition = decomp(k);
+      H->P1 = create_handle(k, p, nverts, verts, ncells, cells, o1, true);
+      H->P1->coarse64 = true;
+    }
     // operator blocks
     riesz_opts om = b, ok = b;
     om.alpha = 0.0;
@@ -2693,13 +2733,20 @@ int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t
     ok.beta = 0.0;
     ok.decomposition = RIESZ_DECOMP_VERTEX_STAR;
     H->Mh = create_handle(k - 1, p, nverts, verts, ncells, cells, om, true, true);
-    H->Kh = create_handle(k, p, nverts, verts, ncells, cells, ok, true, true);
+    if (k < 3) H->Kh = create_handle(k, p, nverts, verts, ncells, cells, ok, true, true);
+    const int64_t C = H->Mh->C();
     H->n0 = H->Mh->N();
-    H->n1 = H->Kh->N();
+    if (k < 3) {
+      H->n1 = H->Kh->N();
+    } else {
+      H->n_dg = dg_dim(p);
+      H->n1 = C * H->n_dg;
+      need(H->n1 < ((int64_t)1 << 31), "too many DG DOFs for 32-bit indices");
+    }
     cudaStream_t s = S(stream);
-    for (riesz_handle* x : {H->P0, H->P1, H->Mh, H->Kh}) setup_device_impl(*x, s);
-    const int64_t C = H->Kh->C();
-    const int n0 = H->Mh->mesh.nref, n1 = H->Kh->mesh.nref;
+    for (riesz_handle* x : {H->P0, H->P1, H->Mh, H->Kh})
+      if (x) setup_device_impl(*x, s);
+    const int n0 = H->Mh->mesh.nref, n1 = H->Kh ? H->Kh->mesh.nref : H->n_dg;
     std::vector<double> R;
     try {
       R = mixed_reference_tables(k, p);
@@ -2707,9 +2754,32 @@ int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t
       throw Err(RIESZ_ERR_INTERNAL, e.what());
     }
     H->d_R.upload(R, s);
-    H->d_gB.alloc((size_t)12 * C);  // k_geom writes all Q factors of X^k (12 for Ned1_p)
+    H->d_gB.alloc((size_t)12 * C);  // k_geom writes all Q factors of its space (12 for Ned1_p)
     H->d_jacB.alloc((size_t)C * 10);
     H->d_Be.alloc((size_t)C * n0 * n1);
+    if (k == 3) {  // DG_{p-1}: cell-major map, reference mass diagonal, load cross table
+      const int nd = H->n_dg;
+      std::vector<int32_t> cd((size_t)nd * C);
+      for (int i = 0; i < nd; ++i)
+        for (int64_t c = 0; c < C; ++c) cd[(size_t)i * C + c] = (int32_t)(c * nd + i);
+      H->d_dg_cd.upload(cd, s);
+      Rule Q = simplex_rule(3, p + 2);
+      const int np = Q.npt();
+      const RefElement& cg = *H->Mh->refcg;
+      std::vector<double> v((size_t)np * nd), vc((size_t)np * cg.nref);
+      dg_tabulate(p, np, Q.x.data(), v.data());
+      cg.tabulate(np, Q.x.data(), vc.data(), nullptr);
+      std::vector<double> mhat(nd, 0.0), X((size_t)cg.nref * nd, 0.0);
+      for (int q = 0; q < np; ++q)
+        for (int i = 0; i < nd; ++i) {
+          const double wv = Q.w[q] * v[(size_t)q * nd + i];
+          mhat[i] += wv * v[(size_t)q * nd + i];
+          for (int a = 0; a < cg.nref; ++a) X[(size_t)a * nd + i] += wv * vc[(size_t)q * cg.nref + a];
+        }
+      H->d_dg_mhat.upload(mhat, s);
+      H->d_dg_X.upload(X, s);
+      H->d_dg_dinv.alloc((size_t)H->n1);
+    }
     const size_t sm = (size_t)(2 * n0 + n1) * sizeof(double);
     if (sm > 48 * 1024) raise_smem_limit(dev::k_hodge_apply, sm);
     for (auto* v : {&H->v, &H->vp, &H->u, &H->w, &H->z, &H->d1, &H->d2}) v->alloc((size_t)H->N());
@@ -2730,7 +2800,7 @@ int riesz_hodge_sizes(const riesz_hodge* h, int64_t* n0, int64_t* n1, int64_t* n
     need(h && n0 && n1, "null argument");
     *n0 = h->n0;
     *n1 = h->n1;
-    if (ncg) *ncg = h->Kh->meshcg.ndofs;
+    if (ncg) *ncg = h->Mh->meshcg.ndofs;
   });
 }
 
@@ -2753,6 +2823,14 @@ int riesz_hodge_load(riesz_hodge* h, const double* fcg, double* b, void* stream)
     need(h && fcg && b, "null argument");
     cudaStream_t s = S(stream);
     CK(cudaMemsetAsync(b, 0, h->n0 * sizeof(double), s));
+    if (h->k == 3) {  // scalar source f in CG_p against the DG functions
+      riesz_handle& M = *h->Mh;
+      dev::k_dg_load<<<(unsigned)M.C(), 128, 0, s>>>(M.C(), h->n_dg, M.refcg->nref, M.d_jac.p, M.d_cgdofs.p, fcg,
+                                                     h->d_dg_X.p, b + h->n0);
+      CK(cudaGetLastError());
+      ++h->launches;
+      return;
+    }
     const int rc = riesz_load(h->Kh, fcg, b + h->n0, stream);
     if (rc != RIESZ_OK) throw Err(rc, "load on X^k failed");
   });
@@ -2763,6 +2841,7 @@ int riesz_hodge_update_geometry(riesz_hodge* h, const double* verts, void* strea
     need(h && verts, "null argument");
     cudaStream_t s = S(stream);
     for (riesz_handle* x : {h->P0, h->P1, h->Mh, h->Kh}) {
+      if (!x) continue;
       CK(cudaMemcpyAsync(x->d_verts.p, verts, x->d_verts.bytes(), cudaMemcpyDeviceToDevice, s));
       device_compute(*x, s);
     }

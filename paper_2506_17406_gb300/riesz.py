@@ -330,9 +330,10 @@ class Riesz:
 
 
 class Hodge:
-    """The mixed Hodge-Laplace problem of Section 7.2 for k = 1 (CG_p x Ned1_p) or k = 2
-    (Ned1_p x RT_p): ``Hodge(k, p, verts, cells, gamma, **opts)`` builds and sets up on the
-    device; block vectors are [sigma (n0) | u (n1)]."""
+    """The mixed Hodge-Laplace problem of Section 7.2 for k = 1 (CG_p x Ned1_p), k = 2
+    (Ned1_p x RT_p) or k = 3 (RT_p x DG_{p-1}): ``Hodge(k, p, verts, cells, gamma, **opts)``
+    builds and sets up on the device; block vectors are [sigma (n0) | u (n1)]; the source of
+    ``load`` is [3][n_cg] CG_p coefficients (k = 1, 2) or [n_cg] (k = 3)."""
 
     def __init__(self, k, p, verts, cells, gamma=1.0, stream=None, **opts):
         self.lib = load_library()

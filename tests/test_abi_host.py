@@ -191,7 +191,7 @@ def test_hodge_validation(lib):
     reports the missing device instead of falling back."""
     from paper_2506_17406_gb300.inputs import fichera_mesh
     v, c = fichera_mesh(2)
-    for k, gamma, kw in [(0, 1.0, {}), (3, 1.0, {}), (1, 0.0, {}), (2, -1.0, {}), (1, 1.0, dict(dirichlet=1))]:
+    for k, gamma, kw in [(0, 1.0, {}), (4, 1.0, {}), (1, 0.0, {}), (2, -1.0, {}), (3, 1.0, dict(dirichlet=1))]:
         with pytest.raises(rz.RieszError) as e:
             rz.Hodge(k, 2, v, c, gamma, stream=0, **kw)
         assert e.value.code == 1

@@ -36,7 +36,8 @@ def host(t):
     return t.cpu().numpy()
 
 
-@pytest.mark.parametrize("k,p,n", [(1, 1, 2), (1, 3, 2), (2, 2, 2), (2, 3, 2), (1, 2, 4), (2, 1, 4)])
+@pytest.mark.parametrize("k,p,n", [(1, 1, 2), (1, 3, 2), (2, 2, 2), (2, 3, 2), (1, 2, 4), (2, 1, 4), (3, 1, 2),
+                                   (3, 3, 2), (3, 2, 4)])
 def test_hodge_apply_matches_oracle(k, p, n):
     v, c, hs = system(k, p, n)
     h = rz.Hodge(k, p, v, c)
@@ -49,7 +50,7 @@ def test_hodge_apply_matches_oracle(k, p, n):
 
 
 @pytest.mark.parametrize("decomp", [rz.DECOMP_VERTEX_STAR, rz.DECOMP_HT])
-@pytest.mark.parametrize("k,p,gamma", [(1, 2, 1.0), (1, 3, 1e3), (2, 2, 1.0), (2, 3, 1e3)])
+@pytest.mark.parametrize("k,p,gamma", [(1, 2, 1.0), (1, 3, 1e3), (2, 2, 1.0), (2, 3, 1e3), (3, 2, 1.0), (3, 3, 1e3)])
 def test_hodge_precond_matches_oracle(k, p, gamma, decomp):
     """Each block: the library's Schwarz preconditioner of the weighted Riesz map against the oracle's
     (vertex stars, or the paper's per-space choice: HT for Ned1_p, edge stars for RT_p)."""
@@ -66,10 +67,12 @@ def test_hodge_precond_matches_oracle(k, p, gamma, decomp):
         assert np.abs(zh[sl] - ze).max() <= tol * np.abs(ze).max()
 
 
-def test_hodge_load_matches_oracle():
-    v, c, hs = system(2, 3, 2)
-    h = rz.Hodge(2, 3, v, c)
-    F = normal_coeffs((3, h.n_cg), 2)
+@pytest.mark.parametrize("k", [2, 3])
+def test_hodge_load_matches_oracle(k):
+    """b = [0 | (f, v)]: a vector source for k = 2, a scalar one against the DG functions for k = 3."""
+    v, c, hs = system(k, 3, 2)
+    h = rz.Hodge(k, 3, v, c)
+    F = normal_coeffs((3 if k < 3 else 1, h.n_cg), 2)
     b = torch.zeros(h.N, dtype=torch.float64, device="cuda")
     h.load(dev(F), b)
     rc = reference_element("CG", 3)
@@ -80,7 +83,7 @@ def test_hodge_load_matches_oracle():
 
 
 @pytest.mark.parametrize("prec", [rz.PREC_FP64, rz.PREC_FP32])
-@pytest.mark.parametrize("k,p,gamma", [(1, 2, 1.0), (1, 2, 1e3), (2, 2, 1.0), (2, 2, 1e3)])
+@pytest.mark.parametrize("k,p,gamma", [(1, 2, 1.0), (1, 2, 1e3), (2, 2, 1.0), (2, 2, 1e3), (3, 2, 1.0), (3, 2, 1e3)])
 def test_hodge_minres_matches_direct_and_oracle_counts(k, p, gamma, prec):
     """MINRES reaches the direct solution; its count stays within 10% (FP64 sweeps) or 25% (FP32 sweeps,
     which perturb the preconditioner by about kappa(A_V) 2^-24 and, over 100+ Lanczos steps at rtol
@@ -116,11 +119,12 @@ def test_hodge_exact_first_iterate_and_restart():
     assert (it3, rr3, rc3) == (0, 0.0, 0) and float(z.abs().max()) == 0.0
 
 
-def test_hodge_update_geometry():
-    v0, c, _ = system(2, 2, 2, 1.0, 3)
-    v1, c1, hs1 = system(2, 2, 2, 1.0, 9)
+@pytest.mark.parametrize("k", [2, 3])
+def test_hodge_update_geometry(k):
+    v0, c, _ = system(k, 2, 2, 1.0, 3)
+    v1, c1, hs1 = system(k, 2, 2, 1.0, 9)
     assert np.array_equal(c, c1)
-    h = rz.Hodge(2, 2, v0, c)
+    h = rz.Hodge(k, 2, v0, c)
     h.update_geometry(dev(v1))
     x = normal_vector(h.N, 12)
     y = torch.zeros(h.N, dtype=torch.float64, device="cuda")
