@@ -384,6 +384,102 @@ class TwoLevelPreconditioner:
         return np.stack([self.apply(I[:, j]) for j in range(self.N)], 1)
 
 
+def lanczos_extremes(A_apply, Binv_apply, n, iters=10, seed=0):
+    """Estimates of the extreme eigenvalues of B^{-1} A (A and B SPD on R^n) from `iters` steps of
+    preconditioned CG with a random right-hand side: the eigenvalues of the Lanczos tridiagonal
+    assembled from the CG step lengths alpha_j and ratios beta_j (diagonal 1/alpha_j +
+    beta_{j-1}/alpha_{j-1}, off-diagonal sqrt(beta_j)/alpha_j)."""
+    rng = np.random.default_rng(seed)
+    r = rng.standard_normal(n)
+    z = Binv_apply(r)
+    p = z.copy()
+    rz = r @ z
+    al, be = [], []
+    for _ in range(min(iters, n)):
+        Ap = A_apply(p)
+        a = rz / (p @ Ap)
+        r = r - a * Ap
+        z = Binv_apply(r)
+        rz_new = r @ z
+        al.append(a)
+        be.append(rz_new / rz)
+        if rz_new <= 0.0 or not np.isfinite(rz_new):
+            break
+        p = z + be[-1] * p
+        rz = rz_new
+    m = len(al)
+    T = np.zeros((m, m))
+    for j in range(m):
+        T[j, j] = 1.0 / al[j] + (be[j - 1] / al[j - 1] if j > 0 else 0.0)
+        if j + 1 < m:
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(be[j]) / al[j]
+    ev = np.linalg.eigvalsh(T)
+    return ev[0], ev[-1]
+
+
+class HybridPreconditioner:
+    """The paper's symmetric hybrid Schwarz preconditioner (Section 7.1, Eq. (7.2)): the spaces
+    X_1 = interior DOFs (point-Jacobi), X_2 = interface DOFs (additive patches with exact solvers),
+    X_3 = W^k (exact solve here; the paper uses a geometric-multigrid V-cycle), each inexact solver
+    weighted by rho_m = (lambda_min + 3 lambda_max) / 4 from 10 Lanczos/CG steps of
+    a(u, v) = lambda a~_m(u, v) on X_m (Eq. (7.3)), and combined multiplicatively in the sweep
+    X_1, X_2, X_3, X_2, X_1 (X_1, X_2, X_1 without the coarse space)."""
+
+    def __init__(self, A, md, patches=None, coarse=True, iters=10, seed=0):
+        A = A.tocsr()
+        self.A = A
+        self.N = A.shape[0]
+        nI = md.n_interface
+        self.I = np.arange(nI, self.N)
+        self.G = np.arange(nI)
+        self.one = Preconditioner(A, md, patches)
+        AII, AGG = A[self.I][:, self.I], A[self.G][:, self.G]
+        self.dinv = 1.0 / AII.diagonal() if len(self.I) else np.zeros(0)
+
+        def patch_apply(rg):
+            r = np.zeros(self.N)
+            r[self.G] = rg
+            return self.one.apply(r)[self.G]
+
+        self.rho = {}
+        if len(self.I):
+            lo, hi = lanczos_extremes(lambda x: AII @ x, lambda x: self.dinv * x, len(self.I), iters, seed)
+            self.rho[1] = (lo + 3.0 * hi) / 4.0
+        lo, hi = lanczos_extremes(lambda x: AGG @ x, patch_apply, nI, iters, seed + 1)
+        self.rho[2] = (lo + 3.0 * hi) / 4.0
+        self.patch_apply = patch_apply
+        self.sweep = [1, 2, 3, 2, 1] if coarse else [1, 2, 1]
+        if not len(self.I):
+            self.sweep = [m for m in self.sweep if m != 1]
+        if coarse:
+            self.W = coarse_dofs(md)
+            A0 = A[self.W][:, self.W].toarray()
+            self.fac0 = scipy.linalg.cho_factor(A0, lower=True)
+            lo, hi = lanczos_extremes(lambda x: A0 @ x, lambda x: scipy.linalg.cho_solve(self.fac0, x),
+                                      len(self.W), iters, seed + 2)
+            self.rho[3] = (lo + 3.0 * hi) / 4.0
+
+    def correction(self, m, res):
+        z = np.zeros(self.N)
+        if m == 1:
+            z[self.I] = self.dinv * res[self.I] / self.rho[1]
+        elif m == 2:
+            z[self.G] = self.patch_apply(res[self.G]) / self.rho[2]
+        else:
+            z[self.W] = scipy.linalg.cho_solve(self.fac0, res[self.W]) / self.rho[3]
+        return z
+
+    def apply(self, r):
+        z = np.zeros_like(r)
+        for m in self.sweep:
+            z = z + self.correction(m, r - self.A @ z)
+        return z
+
+    def dense(self):
+        I = np.eye(self.N)
+        return np.stack([self.apply(I[:, j]) for j in range(self.N)], 1)
+
+
 def pcg(A, b, M=None, rtol=1e-8, maxit=1000):
     """PCG from x0 = 0; stops on the true relative residual.  Returns (x, iters, relres)."""
     nb = np.linalg.norm(b)
