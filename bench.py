@@ -541,11 +541,12 @@ def run_hodge(args):
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64+f32" if prec == rz.PREC_FP32 else "f64", "data": "synthetic",
            "config": {"workload": "Hodge-Laplace k=%d (%s x %s), p=%d, Kuhn Fichera corner %d^3 cubes minus "
-                                  "the (1/2,1)^3 octant (%d tets), perturbed 0.1h, f=(1,1,1), gamma=%g"
-                                  % (k, sp[0], sp[1], p, n, C, gamma),
+                                  "the (1/2,1)^3 octant (%d tets), perturbed 0.1h, f=%s, gamma=%g"
+                                  % (k, sp[0], sp[1], p, n, C, "(1,1,1)" if k < 3 else "1", gamma),
                       "n0": h.n0, "n1": h.n1, "dofs": h.N,
                       "preconditioner": "block diagonal weighted Riesz maps (Eq. 7.6), each one application "
                                         "of its Schwarz preconditioner (CG: vertex stars, Ned1: Hiptmair-Toselli, "
+                                        "DG: exact diagonal, "
                                         "RT: edge stars; W^k with FP64 coarse inverse)",
                       "sweeps": "fp32" if prec == rz.PREC_FP32 else "fp64",
                       "step": "device setup of all blocks + load + MINRES", "l2": "element matrices and patch "
