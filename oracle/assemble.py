@@ -425,14 +425,17 @@ class HybridPreconditioner:
     a(u, v) = lambda a~_m(u, v) on X_m (Eq. (7.3)), and combined multiplicatively in the sweep
     X_1, X_2, X_3, X_2, X_1 (X_1, X_2, X_1 without the coarse space)."""
 
-    def __init__(self, A, md, patches=None, coarse=True, iters=10, seed=0):
+    def __init__(self, A, md, patches=None, coarse=True, iters=10, seed=0, interface=None):
+        """interface: an additive preconditioner whose restriction to the interface DOFs is the X_2
+        solver (default: exact solves on `patches`, vertex stars if None); e.g. an HTPreconditioner
+        with weight 0 for the Hiptmair-Toselli splitting."""
         A = A.tocsr()
         self.A = A
         self.N = A.shape[0]
         nI = md.n_interface
         self.I = np.arange(nI, self.N)
         self.G = np.arange(nI)
-        self.one = Preconditioner(A, md, patches)
+        self.one = Preconditioner(A, md, patches) if interface is None else interface
         AII, AGG = A[self.I][:, self.I], A[self.G][:, self.G]
         self.dinv = 1.0 / AII.diagonal() if len(self.I) else np.zeros(0)
 

@@ -61,14 +61,24 @@ class HodgeSystem:
 
         return apply
 
-    def schwarz_blocks(self, recommended=True, coarse=True):
+    def schwarz_blocks(self, recommended=True, coarse=True, form="additive"):
         """The two Schwarz preconditioners (the paper's per-space decompositions when recommended,
         else vertex stars for both), each with interior Jacobi and, when coarse, the weighted W^k
-        summand (one-level otherwise)."""
+        summand (one-level otherwise).  form = "hybrid": the paper's symmetric hybrid sweep with
+        Lanczos-estimated weights (Eqs. (7.2)-(7.3)) in each Riesz block instead."""
         out = []
         for sp, P, md in ((SPACES[self.k][0], self.P0, self.md0), (SPACES[self.k][1], self.P1, self.md1)):
             if sp == "DG":  # diagonal mass (orthogonal basis): Jacobi is the exact inverse
                 out.append(asm.Preconditioner(P, md, patches=[]))
+            elif form == "hybrid":
+                iface = None
+                patches = None
+                if recommended and sp == "N1curl":
+                    mc = self.md0 if self.k == 1 else MeshDofs(md.verts, md.cells, reference_element("CG", self.p))
+                    iface = asm.HTPreconditioner(P, md, mc, weight=0.0)
+                elif recommended and sp == "RT":
+                    patches = asm.edge_star_dofs(md)
+                out.append(asm.HybridPreconditioner(P, md, patches, coarse=coarse, interface=iface))
             elif recommended and sp == "N1curl":
                 mc = self.md0 if self.k == 1 else MeshDofs(md.verts, md.cells, reference_element("CG", self.p))
                 out.append(asm.HTPreconditioner(P, md, mc, weight=0.5 if coarse else 0.0))
@@ -80,8 +90,8 @@ class HodgeSystem:
                     out.append(asm.Preconditioner(P, md, patches))
         return out
 
-    def schwarz_preconditioner(self, recommended=True, coarse=True):
-        b0, b1 = self.schwarz_blocks(recommended, coarse)
+    def schwarz_preconditioner(self, recommended=True, coarse=True, form="additive"):
+        b0, b1 = self.schwarz_blocks(recommended, coarse, form)
 
         def apply(r):
             return np.concatenate([b0.apply(r[:self.n0]), b1.apply(r[self.n0:])])
