@@ -97,7 +97,7 @@ class Expansion:
     def project(self, F, X, w):
         """L2 projection coefficients of fields with values F (npt, nf, ncomp) at rule (X, w)."""
         val, _ = self.tab(X)
-        return np.einsum("pnc,pfc,p->nf", val, F, w)
+        return np.einsum("pnc,pfc,p->nf", val, F, w, optimize=True)
 
 
 def dcurl3(jac):
@@ -247,7 +247,7 @@ def bubbles(family, p, dim):
             if family == "CG":
                 rows.append(val[:, :, 0])
             else:
-                rows.append(np.einsum("pnc,c->pn", val, t))
+                rows.append(np.einsum("pnc,c->pn", val, t, optimize=True))
         C = np.concatenate(rows, 0)
         bdim = {"CG": (p - 1) * (p - 2) // 2, "N1": p * (p - 1), "N2": (p + 1) * (p - 1)}[family]
     else:
@@ -260,11 +260,11 @@ def bubbles(family, p, dim):
             if family == "CG":
                 rows.append(val[:, :, 0])
             elif family in ("N1", "N2"):
-                tv = np.einsum("pnc,cd->pnd", val, B)
+                tv = np.einsum("pnc,cd->pnd", val, B, optimize=True)
                 rows.append(tv[:, :, 0])
                 rows.append(tv[:, :, 1])
             else:
-                rows.append(np.einsum("pnc,c->pn", val, n))
+                rows.append(np.einsum("pnc,c->pn", val, n, optimize=True))
         C = np.concatenate(rows, 0)
         nsp = U.shape[1]
         bdim = {"CG": (p - 1) * (p - 2) * (p - 3) // 6,
@@ -287,7 +287,7 @@ def d_gram(E, family, dim):
         D = dcurl3(jac) if dim == 3 else dcurl2(jac)[..., None]
     else:
         D = ddiv(jac)[..., None]
-    return np.einsum("pnc,pmc,p->nm", D, D, w)
+    return np.einsum("pnc,pmc,p->nm", D, D, w, optimize=True)
 
 
 def kernel_dim(family, p, dim):
@@ -322,7 +322,7 @@ def canonicalize(E, Y, mu, dim):
         if E.ncomp == 1:
             Pm = val[:, :, 0]
         else:
-            Pm = np.einsum("pnc,pc->pn", val, probe_dirs(dim, m))
+            Pm = np.einsum("pnc,pc->pn", val, probe_dirs(dim, m), optimize=True)
         G = Pm @ Y[:, i:j]  # (m, m)
         Q, R = np.linalg.qr(G.T)
         s = np.sign(np.diag(R))
@@ -413,8 +413,8 @@ class RefElement:
             ER, YR, _ = eigenbasis("RT", p, 3)
             if YR.shape[1]:
                 _, jR = ER.tab(Xc)
-                dphi = np.einsum("pn,nj->pj", ddiv(jR), YR)
-                add((3, 0), np.einsum("pj,pn,p->jn", dphi, val[:, :, 0], wc))  # type II
+                dphi = np.einsum("pn,nj->pj", ddiv(jR), YR, optimize=True)
+                add((3, 0), np.einsum("pj,pn,p->jn", dphi, val[:, :, 0], wc, optimize=True))  # type II
             return np.concatenate(rows, 0), ent
 
         V3 = REF_VERTS[3]
@@ -430,80 +430,80 @@ class RefElement:
         if k in (0, 1):
             Eb, Y, _ = eigenbasis("CG", self.p0, 1)
             vb, gb = Eb.tab(s[:, None])
-            dpsi = np.einsum("pn,nj->pj", gb[:, :, 0, 0], Y)  # d psi / ds
+            dpsi = np.einsum("pn,nj->pj", gb[:, :, 0, 0], Y, optimize=True)  # d psi / ds
             for e, (mid, t) in enumerate(edge_frames()):
                 X = mid[None, :] + s[:, None] * t[None, :]
                 val, jac = E.tab(X)
                 if k == 0:  # (grad_E psi, grad_E v)_E
-                    tg = np.einsum("pnd,d->pn", jac[:, :, 0, :], t)
-                    add((1, e), np.einsum("pj,pn,p->jn", dpsi, tg, ws))
+                    tg = np.einsum("pnd,d->pn", jac[:, :, 0, :], t, optimize=True)
+                    add((1, e), np.einsum("pj,pn,p->jn", dpsi, tg, ws, optimize=True))
                 else:
-                    tv = np.einsum("pnc,c->pn", val, t)
+                    tv = np.einsum("pnc,c->pn", val, t, optimize=True)
                     add((1, e), (ws[:, None] * tv).sum(0)[None, :])  # Whitney (1, t.v)_E
-                    add((1, e), np.einsum("pj,pn,p->jn", dpsi, tv, ws))  # type II
+                    add((1, e), np.einsum("pj,pn,p->jn", dpsi, tv, ws, optimize=True))  # type II
         if k == 0:
             Ef, Y, _ = eigenbasis("CG", p, 2)
             _, gf = Ef.tab(xi)
-            gpsi = np.einsum("pnd,nj->pjd", gf[:, :, 0, :], Y)
+            gpsi = np.einsum("pnd,nj->pjd", gf[:, :, 0, :], Y, optimize=True)
             for f, fr in enumerate(face_frames()):
                 val, jac = E.tab(to_face(xi, fr))
                 _, B, _ = fr
-                tg = np.einsum("pnd,de->pne", jac[:, :, 0, :], B)
-                add((2, f), np.einsum("pjd,pnd,p->jn", gpsi, tg, wf))
+                tg = np.einsum("pnd,de->pne", jac[:, :, 0, :], B, optimize=True)
+                add((2, f), np.einsum("pjd,pnd,p->jn", gpsi, tg, wf, optimize=True))
         elif k == 1:
             EN, YN, _ = eigenbasis(self.fam, p, 2)
             _, jN = EN.tab(xi)
-            cpsi = np.einsum("pn,nj->pj", dcurl2(jN), YN)
+            cpsi = np.einsum("pn,nj->pj", dcurl2(jN), YN, optimize=True)
             Ef, Y, _ = eigenbasis("CG", self.p0, 2)
             _, gf = Ef.tab(xi)
-            gpsi = np.einsum("pnd,nj->pjd", gf[:, :, 0, :], Y)
+            gpsi = np.einsum("pnd,nj->pjd", gf[:, :, 0, :], Y, optimize=True)
             for f, fr in enumerate(face_frames()):
                 val, jac = E.tab(to_face(xi, fr))
                 _, B, n = fr
-                nc = np.einsum("pnc,c->pn", dcurl3(jac), n)
-                add((2, f), np.einsum("pj,pn,p->jn", cpsi, nc, wf))  # type I
-                tv = np.einsum("pnc,cd->pnd", val, B)
-                add((2, f), np.einsum("pjd,pnd,p->jn", gpsi, tv, wf))  # type II
+                nc = np.einsum("pnc,c->pn", dcurl3(jac), n, optimize=True)
+                add((2, f), np.einsum("pj,pn,p->jn", cpsi, nc, wf, optimize=True))  # type I
+                tv = np.einsum("pnc,cd->pnd", val, B, optimize=True)
+                add((2, f), np.einsum("pjd,pnd,p->jn", gpsi, tv, wf, optimize=True))  # type II
         else:
             EN, YN, _ = eigenbasis("N2", p, 2)
             _, jN = EN.tab(xi)
-            cpsi = np.einsum("pn,nj->pj", dcurl2(jN), YN)
+            cpsi = np.einsum("pn,nj->pj", dcurl2(jN), YN, optimize=True)
             for f, fr in enumerate(face_frames()):
                 val, _ = E.tab(to_face(xi, fr))
                 _, B, n = fr
-                nv = np.einsum("pnc,c->pn", val, n)
+                nv = np.einsum("pnc,c->pn", val, n, optimize=True)
                 add((2, f), (wf[:, None] * nv).sum(0)[None, :])  # Whitney (1, n.v)_F
-                add((2, f), np.einsum("pj,pn,p->jn", cpsi, nv, wf))  # type II
+                add((2, f), np.einsum("pj,pn,p->jn", cpsi, nv, wf, optimize=True))  # type II
         # interior
         val, jac = E.tab(Xc)
         if k == 0:
             Ec, Y, _ = eigenbasis("CG", p, 3)
             if Y.shape[1]:
                 _, gc = Ec.tab(Xc)
-                gpsi = np.einsum("pnd,nj->pjd", gc[:, :, 0, :], Y)
-                add((3, 0), np.einsum("pjd,pnd,p->jn", gpsi, jac[:, :, 0, :], wc))
+                gpsi = np.einsum("pnd,nj->pjd", gc[:, :, 0, :], Y, optimize=True)
+                add((3, 0), np.einsum("pjd,pnd,p->jn", gpsi, jac[:, :, 0, :], wc, optimize=True))
         elif k == 1:
             EN, YN, _ = eigenbasis(self.fam, p, 3)
             if YN.shape[1]:
                 _, jN = EN.tab(Xc)
-                cpsi = np.einsum("pnc,nj->pjc", dcurl3(jN), YN)
-                add((3, 0), np.einsum("pjc,pnc,p->jn", cpsi, dcurl3(jac), wc))
+                cpsi = np.einsum("pnc,nj->pjc", dcurl3(jN), YN, optimize=True)
+                add((3, 0), np.einsum("pjc,pnc,p->jn", cpsi, dcurl3(jac), wc, optimize=True))
             Ec, Y, _ = eigenbasis("CG", self.p0, 3)
             if Y.shape[1]:
                 _, gc = Ec.tab(Xc)
-                gpsi = np.einsum("pnd,nj->pjd", gc[:, :, 0, :], Y)
-                add((3, 0), np.einsum("pjd,pnd,p->jn", gpsi, val, wc))
+                gpsi = np.einsum("pnd,nj->pjd", gc[:, :, 0, :], Y, optimize=True)
+                add((3, 0), np.einsum("pjd,pnd,p->jn", gpsi, val, wc, optimize=True))
         else:
             ER, YR, _ = eigenbasis("RT", p, 3)
             if YR.shape[1]:
                 _, jR = ER.tab(Xc)
-                dphi = np.einsum("pn,nj->pj", ddiv(jR), YR)
-                add((3, 0), np.einsum("pj,pn,p->jn", dphi, ddiv(jac), wc))
+                dphi = np.einsum("pn,nj->pj", ddiv(jR), YR, optimize=True)
+                add((3, 0), np.einsum("pj,pn,p->jn", dphi, ddiv(jac), wc, optimize=True))
             EN, YN, _ = eigenbasis("N2", p, 3)
             if YN.shape[1]:
                 _, jN = EN.tab(Xc)
-                cpsi = np.einsum("pnc,nj->pjc", dcurl3(jN), YN)
-                add((3, 0), np.einsum("pjc,pnc,p->jn", cpsi, val, wc))
+                cpsi = np.einsum("pnc,nj->pjc", dcurl3(jN), YN, optimize=True)
+                add((3, 0), np.einsum("pjc,pnc,p->jn", cpsi, val, wc, optimize=True))
         ent.setdefault((3, 0), [])
         return np.concatenate(rows, 0), ent
 
@@ -512,8 +512,8 @@ class RefElement:
         """Reference basis at points X (npt, 3): values (npt, n_ref, ncomp) and
         d (npt, n_ref, dcomp): gradient (3), curl (3) or div (1)."""
         val, jac = self.E.tab(X)
-        v = np.einsum("pnc,nj->pjc", val, self.Phi)
-        J = np.einsum("pncd,nj->pjcd", jac, self.Phi)
+        v = np.einsum("pnc,nj->pjc", val, self.Phi, optimize=True)
+        J = np.einsum("pncd,nj->pjcd", jac, self.Phi, optimize=True)
         if self.k == 0:
             d = J[:, :, 0, :]
         elif self.k == 1:
@@ -528,8 +528,8 @@ class RefElement:
         """Reference mass and d-stiffness matrices on the reference tetrahedron."""
         X, w = quadrature(3, self.p + 2)
         v, d = self.tabulate(X)
-        M = np.einsum("pic,pjc,p->ij", v, v, w)
-        K = np.einsum("pic,pjc,p->ij", d, d, w)
+        M = np.einsum("pic,pjc,p->ij", v, v, w, optimize=True)
+        K = np.einsum("pic,pjc,p->ij", d, d, w, optimize=True)
         return M, K
 
 
