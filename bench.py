@@ -7,10 +7,13 @@ element matrices, interior diagonal, patch assembly, batched FP64 Cholesky),
 right-hand-side assembly, and PCG to ||b - A x|| <= 1e-8 ||b|| (true residual).
 The host-side reference element and mesh maps are built once before timing.
 
-Default workload: H(curl) Riesz map, first-kind Nedelec p = 6 on the unit cube
-split into 8^3 cubes x 6 tets (3072 tets), interior vertices perturbed by up
-to 0.1 h (seeded), f with N(0,1) CG_6 coefficients per Cartesian component,
-FP64 operator with FP32 patch solves, rtol 1e-8.
+Default workload (the largest single-GPU configuration): H(div) Riesz map,
+Raviart-Thomas p = 8 on the unit cube split into 16^3 cubes x 6 tets (24576
+tets, 8 017 920 DOFs), interior vertices perturbed by up to 0.1 h (seeded),
+8 seeded N(0,1) right-hand sides solved in lockstep, FP64 outer PCG (residuals,
+inner products, refinement) with FP32 products and FP32 patch sweeps inside,
+rtol 1e-8.  --workload hcurl_ned1_p6_n8 gives the Ned1_6 8^3 line (FP64
+operator, FP32 patch solves), --workload hgrad_cg3_n4 the CG_3 4^3 one.
 
 Prints one JSON line (rank 0) with per-step latency (p50/p99 over the timed
 steps) and, for the mixed-precision workloads, the same workload timed with the
@@ -44,15 +47,19 @@ WORKLOADS = {
                               "solves (small case for kernel profiles)"),
     "hgrad_cg3_n4": dict(space="CG", p=3, n=4, amp=0.0, prec=0, nrhs=1,
                          label="H(grad) CG_3 on 4^3 x 6 tets, FP64"),
-    "hdiv_rt8_n16": dict(space="RT", p=8, n=16, amp=0.1, prec=1, nrhs=8, a32=1,
+    "hdiv_rt8_n16": dict(space="RT", p=8, n=16, amp=0.1, prec=1, nrhs=8, a32=1, plain_steps=3,
                          label="H(div) RT_8 on 16^3 x 6 tets, perturbed 0.1h, 8 RHS in lockstep, FP32 inner "
                                "products and patch solves, FP64 residuals"),
 }
-DEFAULT = "hcurl_ned1_p6_n8"
+DEFAULT = "hdiv_rt8_n16"
 METRIC = "DOFs/s solved to 1e-8 rel. residual"
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, the profiling recipe's nominal figure
-# CPU sample for the oracle: same space, degree, perturbation and RHS recipe on 3^3 x 6 tets
-CPU_SAMPLE_N = 3
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, the profiling recipe's nominal figure (context only)
+# CPU sample for the oracle: same space, degree, perturbation and RHS recipe on a small Kuhn mesh
+# (cubes per edge, right-hand sides), sized for 10-30 s of CPU work per pass
+CPU_SAMPLE = {"hdiv_rt8_n16": (2, 2), "hdiv_rt8_n4": (2, 2)}
+CPU_SAMPLE_DEFAULT = (3, 1)
+# mesh of the error check against the oracle's direct solve (same recipe, small mesh)
+ERR_SAMPLE_N = 2
 
 
 DECOMPOSITIONS = {"vertex_star": 0, "ht": 1, "edge_star": 2}  # riesz_opts.decomposition
@@ -156,8 +163,10 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample)
 # ---------------------------------------------------------------------------
-def oracle_pass(space, p, n, amp, seed=1):
-    """One pass of the oracle (assembly, load, preconditioner setup, PCG); returns (N, seconds, iters)."""
+def oracle_pass(space, p, n, amp, nrhs=1, seed=1):
+    """One pass of the oracle (assembly, load, preconditioner setup, PCG per right-hand side); returns
+    (N, seconds, iters).  One right-hand side: f with N(0,1) CG_p coefficients per component (b = (f, phi));
+    several: N(0,1) vectors (the paper's random right-hand side), as the GPU workload draws them."""
     import numpy as np
     from oracle import assemble as asm
     from oracle.mesh import MeshDofs
@@ -168,46 +177,109 @@ def oracle_pass(space, p, n, amp, seed=1):
     verts, cells = kuhn_mesh(n, amp, seed)
     t0 = time.perf_counter()
     md = MeshDofs(verts, cells, ref)
-    mcg = MeshDofs(verts, cells, cg)
     A = asm.assemble(md, asm.element_matrices(ref, verts, cells))
-    f = normal_coeffs((1 if space == "CG" else 3, mcg.ndofs), 2)
-    b = asm.load_cg_field(ref, md, cg, mcg, f)
+    if nrhs == 1:
+        mcg = MeshDofs(verts, cells, cg)
+        f = normal_coeffs((1 if space == "CG" else 3, mcg.ndofs), 2)
+        B = asm.load_cg_field(ref, md, cg, mcg, f)[None, :]
+    else:
+        B = normal_coeffs((nrhs, md.ndofs), 2)
     P = asm.Preconditioner(A, md)
-    x, it, rr = asm.pcg(A, b, P.apply, rtol=1e-8)
+    its = []
+    for k in range(nrhs):
+        x, it, rr = asm.pcg(A, B[k], P.apply, rtol=1e-8)
+        assert rr <= 1e-8 * 1.001, rr
+        its.append(it)
     dt = time.perf_counter() - t0
-    assert rr <= 1e-8 * 1.001, rr
-    return md.ndofs, dt, it
+    return md.ndofs, dt, max(its)
 
 
-def cpu_baseline(wl):
-    N, dt, it = oracle_pass(wl["space"], wl["p"], CPU_SAMPLE_N, wl["amp"])
-    return {"value": N / dt, "unit": "DOFs/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%s p=%d on %d^3 x 6 tets (N=%d, same perturbation and RHS recipe), one full oracle pass "
-                      "(numbering, quadrature assembly, load, patch Cholesky, PCG to 1e-8): %.1f s, %d iterations; "
-                      "BLAS threads at library default" % (wl["space"], wl["p"], CPU_SAMPLE_N, N, dt, it)}
+def cpu_sample(args):
+    return CPU_SAMPLE.get(args.workload, CPU_SAMPLE_DEFAULT)
+
+
+def cpu_baseline(wl, args):
+    n, nr = cpu_sample(args)
+    N, dt, it = oracle_pass(wl["space"], wl["p"], n, wl["amp"], nrhs=nr)
+    return {"value": N * nr / dt, "unit": "DOFs/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%s p=%d on %d^3 x 6 tets (N=%d, same perturbation and RHS recipe), %d right-hand side(s), "
+                      "one full oracle pass (numbering, quadrature assembly, load, patch Cholesky, PCG to 1e-8 per "
+                      "right-hand side): %.1f s, %d iterations; BLAS threads at library default"
+                      % (wl["space"], wl["p"], n, N, nr, dt, it)}
+
+
+def err_vs_oracle(wl, args, make_solver):
+    """The GPU path of the workload (same space, degree, precisions, right-hand-side recipe, number of
+    right-hand sides and rtol) on the ERR_SAMPLE_N^3 mesh of the same recipe, against the oracle's FP64
+    sparse direct solve: max over right-hand sides of ||x - x_oracle|| / ||x_oracle||."""
+    import numpy as np
+    import torch
+    from oracle import assemble as asm
+    from oracle.mesh import MeshDofs
+    from oracle.refelem import reference_element
+    from paper_2506_17406_gb300.inputs import kuhn_mesh, normal_coeffs
+    n = ERR_SAMPLE_N
+    nrhs = wl.get("nrhs", 1)
+    verts, cells = kuhn_mesh(n, wl["amp"], 1)
+    s = make_solver(verts, cells)
+    ref = reference_element(wl["space"], wl["p"])
+    md = MeshDofs(verts, cells, ref)
+    A = asm.assemble(md, asm.element_matrices(ref, verts, cells))
+    if nrhs == 1:
+        cg = reference_element("CG", wl["p"])
+        mcg = MeshDofs(verts, cells, cg)
+        f = normal_coeffs((1 if wl["space"] == "CG" else 3, mcg.ndofs), 2)
+        B = asm.load_cg_field(ref, md, cg, mcg, f)[None, :]
+    else:
+        B = normal_coeffs((nrhs, md.ndofs), 2)
+    b = torch.tensor(B, device="cuda")
+    x = torch.zeros_like(b)
+    it, rr, rc = s.solve(b, x, nrhs=nrhs, check=False)
+    X = x.cpu().numpy()
+    errs = []
+    for k in range(nrhs):
+        xe = asm.direct_solve(A, B[k])
+        errs.append(float(np.linalg.norm(X[k] - xe) / np.linalg.norm(xe)))
+    s.close()
+    return {"max_rel_l2": max(errs), "rtol": 1e-8, "status": int(rc), "iterations": int(it[0]),
+            "sample": "same recipe on %d^3 x 6 tets (N=%d, %d right-hand side(s)), oracle FP64 sparse direct solve"
+                      % (n, md.ndofs, nrhs)}
 
 
 # ---------------------------------------------------------------------------
 def run_reference(args, wl, rank, world):
     if rank != 0:
         return
+    n, nr = cpu_sample(args)
     for _ in range(args.warmup):
-        oracle_pass(wl["space"], wl["p"], CPU_SAMPLE_N, wl["amp"])
+        oracle_pass(wl["space"], wl["p"], n, wl["amp"], nrhs=nr)
     tot, N = 0.0, 0
     for _ in range(args.steps):
-        N, dt, _ = oracle_pass(wl["space"], wl["p"], CPU_SAMPLE_N, wl["amp"])
+        N, dt, _ = oracle_pass(wl["space"], wl["p"], n, wl["amp"], nrhs=nr)
         tot += dt
-    value = N * args.steps / tot
+    value = N * nr * args.steps / tot
     cb = {"value": value, "unit": "DOFs/s", "cores": os.cpu_count(), "kind": "oracle",
-          "sample": "%s p=%d on %d^3 x 6 tets (N=%d): full oracle pass per step" % (wl["space"], wl["p"],
-                                                                                 CPU_SAMPLE_N, N)}
+          "sample": "%s p=%d on %d^3 x 6 tets (N=%d), %d right-hand side(s): full oracle pass per step"
+                    % (wl["space"], wl["p"], n, N, nr)}
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOFs/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": wl["label"], "cpu_sample_cubes_per_edge": CPU_SAMPLE_N},
+           "data": "synthetic", "config": {"workload": wl["label"], "cpu_sample_cubes_per_edge": n,
+                                           "cpu_sample_rhs": nr},
            "cpu_baseline": cb,
            "e2e": {"value": value, "unit": "DOFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def measured_fp64_peak():
+    """FP64 FMA rate of this GPU (riesz_probe_fp64, best of three bounded launches), TFLOP/s."""
+    from paper_2506_17406_gb300 import riesz as rz
+    return max(rz.probe_fp64(16384) for _ in range(3))
+
+
+def fp64_peak_source(tf):
+    return ("measured in this run: riesz_probe_fp64, a bounded FP64 FMA loop on this GPU (best of 3), "
+            "%.3f TFLOP/s; nominal %.2f" % (tf, FP64_NOMINAL_TFLOPS))
 
 
 def combine_ranks(ms, n_local, dist=None, device=None):
@@ -505,9 +577,10 @@ def run_hodge(args):
     C = len(cells)
     flops = 2.0 * C * ((n1 * n1 if k < 3 else 0) + 2 * n0 * n1 + n0 * n0)
     tf = flops / (apply_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-            "frac": tf / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": "k_hodge_apply (+2 k_gather_iface)",
-            "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s)",
+    pk = measured_fp64_peak()
+    roof = {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s",
+            "frac": tf / pk, "traffic": None, "kernel": "k_hodge_apply (+2 k_gather_iface)",
+            "peak_source": fp64_peak_source(pk),
             "algorithmic": "2 C (n_k^2 + 2 n_{k-1} n_k + n_{k-1}^2) = %.3e flop per block product (element "
                            "matrices of K_k, M_{k-1} and the coupling read once: %.3e B)"
                            % (flops, 8.0 * C * (n1 * n1 + n0 * n1 + n0 * n0))}
@@ -691,12 +764,13 @@ def main():
         peak_hbm = float(peaks.get("hbm_gbs", peak_hbm))
     except Exception:
         pass
+    fp64_pk = measured_fp64_peak()
     if dom == "cholesky":
         achieved = chol_flops / (dom_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": measured_traffic(args.workload, "k_cholesky"),
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_pk, "unit": "TFLOP/s",
+                "frac": achieved / fp64_pk, "traffic": measured_traffic(args.workload, "k_cholesky"),
                 "kernel": "k_cholesky",
-                "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s)",
+                "peak_source": fp64_peak_source(fp64_pk),
                 "algorithmic": "tile-sparse Cholesky of all patches = %.3e flop per launch (dense "
                                "sum n_V^3/3 would be %.3e)" % (chol_flops, dense_flops)}
     elif dom == "patch_solve":
@@ -718,13 +792,13 @@ def main():
                 "kernel": dom,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                 "algorithmic": "element matrices + gathered vectors = %.3e B per launch" % byt}
-        if dom == "apply" and flops / (FP64_NOMINAL_TFLOPS * 1e12) > byt / (peak_hbm * 1e9):
+        if dom == "apply" and flops / (fp64_pk * 1e12) > byt / (peak_hbm * 1e9):
             # FP64 element products: one DFMA per 8-byte matrix entry and right-hand side, so the FP64
             # pipe, not HBM, bounds the launch (2 C n^2 nrhs flop)
             tf = flops / (dom_ms / 1e3) / 1e12
-            roof.update({"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                         "frac": tf / FP64_NOMINAL_TFLOPS, "hbm_gbs": achieved, "hbm_frac": achieved / peak_hbm,
-                         "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s)",
+            roof.update({"bound": "alu", "achieved": tf, "peak": fp64_pk, "unit": "TFLOP/s",
+                         "frac": tf / fp64_pk, "hbm_gbs": achieved, "hbm_frac": achieved / peak_hbm,
+                         "peak_source": fp64_peak_source(fp64_pk),
                          "algorithmic": "2 C n^2 nrhs = %.3e flop per launch (element matrices + gathered "
                                         "vectors = %.3e B)" % (flops, byt)})
 
@@ -755,18 +829,23 @@ def main():
                "d2h_bytes_per_step": d2h}
 
     # the same workload with the plain FP64 solver (FP64 operator and FP64 patch solves)
+    x_mixed = x.clone()  # the last step's solution, for the comparison with the plain FP64 solver
     plain = None
     if (wl["prec"] != 0 or wl.get("a32", 0)) and not args.no_fp64_plain:
-        s64, step64, it64, rr64, *_ = make(0, 0)
-        for _ in range(args.warmup):
+        s64, step64, it64, rr64, _, _, _, x64 = make(0, 0)
+        # the plain solver is several times slower: fewer steps keep the run within minutes
+        psteps = min(args.steps, wl.get("plain_steps", args.steps))
+        for _ in range(min(args.warmup, 1 if psteps < args.steps else args.warmup)):
             step64()
-        per64 = timed(step64, args.steps)
+        per64 = timed(step64, psteps)
         ms64, _ = combine_ranks(sum(per64), s64.N, dist, device="cuda")
-        plain = {"value": ntot * nrhs * args.steps / (ms64 / 1e3), "unit": "DOFs/s",
-                 "ms_per_step": ms64 / args.steps,
+        dx = [float(torch.linalg.norm(x_mixed[k] - x64[k]) / torch.linalg.norm(x64[k])) for k in range(nrhs)]
+        plain = {"value": ntot * nrhs * psteps / (ms64 / 1e3), "unit": "DOFs/s",
+                 "steps": psteps, "ms_per_step": ms64 / psteps,
                  "latency_p50_ms": float(np.percentile(per64, 50)),
                  "latency_p99_ms": float(np.percentile(per64, 99)),
-                 "iterations": statistics.median(it64[-args.steps:]), "max_relres": max(rr64[-args.steps:]),
+                 "iterations": statistics.median(it64[-psteps:]), "max_relres": max(rr64[-psteps:]),
+                 "max_rel_l2_diff_of_solutions": max(dx),
                  "config": "same mesh, right-hand side and rtol; FP64 operator and FP64 patch solves"}
         s64.close()
 
@@ -797,9 +876,14 @@ def main():
                          "config": "same mesh, right-hand side, precisions and rtol; decomposition " + alt}
         sv.close()
 
-    cb = None
+    cb = err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(wl)
+        cb = cpu_baseline(wl, args)
+
+        def small_solver(v, c):
+            return rz.Riesz(wl["space"], wl["p"], v, c, precond_precision=wl["prec"], nrhs_max=nrhs,
+                            apply_precision=wl.get("a32", 0), decomposition=DECOMPOSITIONS[args.decomposition])
+        err = err_vs_oracle(wl, args, small_solver)
 
     if rank == 0:
         out = {
@@ -818,6 +902,7 @@ def main():
             "iterations": statistics.median(iters[-args.steps:]), "max_relres": relres,
             "latency_p50_ms": float(np.percentile(per_step, 50)),
             "latency_p99_ms": float(np.percentile(per_step, 99)),
+            "err_vs_oracle": err,
             "fp64_plain": plain,
             "speedup_vs_fp64_plain": (value / plain["value"]) if plain else None,
             "decomposition_variants": variants,

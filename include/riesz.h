@@ -265,7 +265,11 @@ int riesz_apply(riesz_handle* h, const double* x, double* y, int nrhs, void* str
    Limits: n_interface_per_cell * ncells <= 2^21 (RIESZ_ERR_INVALID_ARG
    otherwise, nothing launched).  The first call on a device looks up the
    array's device address (cudaGetSymbolAddress), so make that first call
-   before any stream capture.  All calls share the one array, which keeps the
+   before any stream capture.  The address is kept per device ordinal for the
+   life of the process: after cudaDeviceReset (or any teardown of the
+   device's primary context) the library's module is loaded afresh and the
+   kept address no longer names the array, so do not call this entry point
+   on a device after resetting it.  All calls share the one array, which keeps the
    last call's contents; calls that overlap on the GPU (other streams, other
    handles on the same device) race on it and must be serialised by the
    caller.  Every scratch entry a call reads is written earlier in the same
@@ -369,6 +373,24 @@ int riesz_tuning(const riesz_handle* h, int* out);
    out[7] bytes one riesz_precond call reads and writes for the patch sweeps
           (stored factor tiles and diagonal inverses twice, patch vectors). */
 int riesz_stats(const riesz_handle* h, double* out);
+
+/* Device bytes riesz_setup_device will allocate for this handle (host-only,
+   no GPU needed): *bytes = the sum of the handle's device buffers (those of
+   its internal potential-problem handle included), equal to riesz_stats'
+   out[2] once the setup has run; *nalloc (may be NULL) = the number of
+   device allocations, so that a caller can add the allocator's rounding
+   (at most one 2 MiB page per allocation).  Lets a scheduler budget HBM
+   before a request touches the device. */
+int riesz_plan_bytes(const riesz_handle* h, double* bytes, int64_t* nalloc);
+
+/* Measurement helper (no counterpart in the paper): the FP64 fused
+   multiply-add rate of the current device, in TFLOP/s, from one timed launch
+   (CUDA events on stream) of a kernel with eight independent dependent-FMA
+   chains per thread, iters steps each, four CTAs of 256 threads per SM, after
+   one shorter warm-up launch.  iters in 1..2^24 (about 2^14 gives tens of
+   milliseconds on one GPU).  Synchronises the stream.  Used as the measured
+   FP64 peak for the roofline of the FP64 kernels; changes no GPU setting. */
+int riesz_probe_fp64(int iters, void* stream, double* tflops);
 
 int riesz_destroy(riesz_handle* h);
 

@@ -428,7 +428,11 @@ class HybridPreconditioner:
     def __init__(self, A, md, patches=None, coarse=True, iters=10, seed=0, interface=None):
         """interface: an additive preconditioner whose restriction to the interface DOFs is the X_2
         solver (default: exact solves on `patches`, vertex stars if None); e.g. an HTPreconditioner
-        with weight 0 for the Hiptmair-Toselli splitting."""
+        with weight 0 for the Hiptmair-Toselli splitting.  The X_2 correction is that solver's
+        output on the interface DOFs for a residual restricted to the interface DOFs (interior
+        entries zeroed on input, dropped on output): for Hiptmair-Toselli this is the interface
+        restriction of the HT operator, so the interior Ned1 components of its gradient corrections
+        G (potential solves) are not part of X_2; the interior DOFs belong to X_1 alone."""
         A = A.tocsr()
         self.A = A
         self.N = A.shape[0]

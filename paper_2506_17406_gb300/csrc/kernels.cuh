@@ -2309,5 +2309,26 @@ __global__ void k_mr_update(int64_t n, const double* __restrict__ m, double* __r
   u[i] = z[i] * m[M_INVB];
 }
 
+// Measurement helper: eight independent chains of dependent FP64 fused
+// multiply-adds per thread, `iters` steps each (2 flop per step and chain), so
+// the FP64 pipe, not latency, bounds the launch.  The chains contract towards
+// c / (1 - m) and never overflow; their sum is stored so no step is dead code.
+__global__ void __launch_bounds__(256) k_fp64_probe(int iters, double m, double c, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double a0 = t * 1e-9, a1 = a0 + 0.1, a2 = a0 + 0.2, a3 = a0 + 0.3;
+  double a4 = a0 + 0.4, a5 = a0 + 0.5, a6 = a0 + 0.6, a7 = a0 + 0.7;
+  for (int i = 0; i < iters; ++i) {
+    a0 = fma(a0, m, c);
+    a1 = fma(a1, m, c);
+    a2 = fma(a2, m, c);
+    a3 = fma(a3, m, c);
+    a4 = fma(a4, m, c);
+    a5 = fma(a5, m, c);
+    a6 = fma(a6, m, c);
+    a7 = fma(a7, m, c);
+  }
+  out[t] = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+}
+
 }  // namespace dev
 }  // namespace riesz

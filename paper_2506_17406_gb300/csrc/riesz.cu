@@ -180,7 +180,8 @@ struct riesz_handle {
            d_gt_idx.bytes() + d_gg_idx.bytes() + d_gt_sgn.bytes() + d_gg_sgn.bytes() + d_zcg.bytes() + d_zg.bytes() +
            (aux ? aux->device_bytes() : 0) + d_cw.bytes() + d_cidx.bytes() + d_cJ.bytes() +
            d_ccell.bytes() + d_cab.bytes() + d_cptr.bytes() + d_A0.bytes() + d_Dinv0.bytes() + d_Rb0.bytes() +
-           d_r0.bytes() + d_zc.bytes() + d_A0d.bytes() + d_X0d.bytes() + d_Dinv0d.bytes() + d_Rb0d.bytes() + d_r0d.bytes();
+           d_r0.bytes() + d_zc.bytes() + d_A0d.bytes() + d_X0d.bytes() + d_Dinv0d.bytes() + d_Rb0d.bytes() + d_r0d.bytes() +
+           d_info.bytes() + d_ticket.bytes() + d_cbad.bytes();
   }
   void drop_graphs() {
     if (g_entry) cudaGraphExecDestroy(g_entry);
@@ -2018,6 +2019,117 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   h.on_device = true;
 }
 
+// Device bytes riesz_setup_device will allocate for this handle (the sum of
+// its device buffers, the internal potential-problem handle included), from
+// the host plans alone: the same sizes as setup_device_impl, buffer by buffer,
+// so that admission control can budget a request before it touches the GPU.
+// *nalloc receives the number of device allocations (for the allocator's
+// per-allocation rounding).
+double plan_device_bytes(const riesz_handle& h, int64_t* nalloc) {
+  const RefElement& R = *h.ref;
+  const MeshMaps& M = h.mesh;
+  const double n = M.nref, C = (double)M.ncells, N = (double)M.ndofs;
+  const double nrhs = std::max(1, h.opts.nrhs_max);
+  const double npatch = (double)h.p_n.size();
+  double b = 0.0;
+  int64_t na = 0;
+  auto add = [&](double count, double size) {
+    if (count > 0) {
+      b += count * size;
+      ++na;
+    }
+  };
+  add((double)h.verts.size(), 8);
+  add((double)M.cells.size(), 4);
+  add(C * n, 4);                                   // cell_dofs
+  add((double)R.R.size(), 8);
+  add((double)R.Q * C, 8);                         // g
+  add(C * 10, 8);                                  // jac
+  add(nrhs * h.nif * C, 8);                        // Ycell
+  add(std::max<double>(1, (double)M.n_interior), 8);
+  add((double)h.sc_ptr.size(), 8);
+  add((double)h.sc_pos.size(), 4);
+  add((double)h.p_n.size(), 4);
+  add((double)h.p_doff.size(), 8);
+  add((double)h.p_foff.size(), 8);
+  add((double)h.p_dofs.size(), 4);
+  add((double)h.pz_ptr.size(), 8);
+  add((double)h.pz_pos.size(), 4);
+  add((double)h.pb_ptr.size(), 8);
+  add((double)h.pb_off.size(), 8);
+  add((double)h.pb_cell.size(), 4);
+  add((double)h.pb_ent.size(), 4);
+  add(std::max<double>(1, (double)h.p_dofs.size() * nrhs), 8);  // zpatch
+  add((double)R.Xcross.size(), 8);
+  add(C * h.refcg->nref, 4);                       // CG cell_dofs (load)
+  for (int k = 0; k < 8; ++k) add(N * nrhs, 8);    // r, z, zold, p, Ap, tmp, xh, xw
+  add(4, 4);                                       // ctl
+  add(4, 4);                                       // flags
+  add(2.0 * dev::RED_BLOCKS * nrhs, 8);            // part
+  add(16 * nrhs, 8);                               // scal
+  add(std::max<double>(1, npatch), 4);             // info
+  if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
+    add(C * n * n, 8);
+    if (h.opts.apply_precision == RIESZ_PREC_FP32) add(C * n * n, 4);
+  }
+  add((double)h.p_dioff.size(), 8);
+  add((double)h.p_moff.size(), 8);
+  add((double)h.p_meta.size(), 4);
+  if (h.opts.dirichlet) add((double)h.dir_mask.size(), 1);
+  if (h.ht) {
+    int64_t na_aux = 0;
+    b += plan_device_bytes(*h.aux, &na_aux);
+    na += na_aux;
+    add((double)h.gt_ptr.size(), 8);
+    add((double)h.gt_idx.size(), 4);
+    add((double)h.gt_sgn.size(), 4);
+    add((double)h.gg_ptr.size(), 8);
+    add((double)h.gg_idx.size(), 4);
+    add((double)h.gg_sgn.size(), 4);
+    add(nrhs * (double)h.aux->mesh.n_interface, 8);
+    add(nrhs * (double)M.n_interface, 8);
+  }
+  if (h.coarse_on) {
+    const double N0p = h.N0p, CB = dev::CB;
+    add((double)h.c_w.size(), 4);
+    add((double)h.c_idx.size(), 4);
+    add((double)h.c_ptr.size(), 8);
+    add((double)h.c_J.size(), 4);
+    add((double)h.c_cell.size(), 4);
+    add((double)h.c_ab.size(), 4);
+    if (h.coarse64) {
+      add(N0p * N0p, 8);
+      add(N0p * N0p, 8);
+      add(N0p * CB, 8);
+      add(CB * N0p, 8);
+      add(nrhs * N0p, 8);
+      add(1, 4);
+    } else {
+      add(N0p * N0p, 4);
+      add(CB * CB, 4);
+      add(CB * N0p, 4);
+      add(nrhs * N0p, 4);
+    }
+    add(nrhs * h.N0, 8);
+  }
+  if (npatch > 0) {
+    const double fe = (double)h.factor_entries, de = (double)h.dinv_entries;
+    add(fe, 8);
+    add(de, 8);
+    if (h.opts.precond_precision == RIESZ_PREC_FP32) {
+      add(fe, 4);
+      if (nrhs > 1) {
+        add(fe, 4);
+        add(de, 4);
+      }
+      add(de, 4);
+    }
+  }
+  add(nrhs, 4);  // ticket
+  if (nalloc) *nalloc = na;
+  return b;
+}
+
 void check_dev(const riesz_handle* h) {
   need(h != nullptr, "null handle");
   need(h->on_device, "handle has no device state (call riesz_setup_device)", RIESZ_ERR_NO_DEVICE);
@@ -2472,6 +2584,45 @@ int riesz_stats(const riesz_handle* h, double* out) {
     out[6] = h->chol_flops + (h->aux ? h->aux->chol_flops : 0.0);
     const double fb = h->opts.precond_precision == RIESZ_PREC_FP32 ? 4.0 : 8.0;
     out[7] = 2.0 * (double)(h->factor_entries + h->dinv_entries) * fb + (double)h->p_dofs.size() * 20.0;
+  });
+}
+
+int riesz_probe_fp64(int iters, void* stream, double* tflops) {
+  return guarded([&] {
+    need(tflops != nullptr && iters >= 1 && iters <= (1 << 24), "iters must be in 1..2^24");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = 4 * nsm, threads = 256;
+    DBuf<double> out;
+    out.alloc((size_t)blocks * threads);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float ms = 0.f;
+    cudaError_t rc = cudaSuccess;
+    dev::k_fp64_probe<<<blocks, threads, 0, s>>>(std::min(iters, 1024), 0.999999, 1e-7, out.p);  // warm-up
+    rc = cudaEventRecord(e0, s);
+    if (rc == cudaSuccess) {
+      dev::k_fp64_probe<<<blocks, threads, 0, s>>>(iters, 0.999999, 1e-7, out.p);
+      rc = cudaGetLastError();
+    }
+    if (rc == cudaSuccess) rc = cudaEventRecord(e1, s);
+    if (rc == cudaSuccess) rc = cudaEventSynchronize(e1);
+    if (rc == cudaSuccess) rc = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(rc);
+    const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+    *tflops = flops / (ms * 1e-3) / 1e12;
+  });
+}
+
+int riesz_plan_bytes(const riesz_handle* h, double* bytes, int64_t* nalloc) {
+  return guarded([&] {
+    need(h != nullptr && bytes != nullptr, "null argument");
+    *bytes = plan_device_bytes(*h, nalloc);
   });
 }
 

@@ -76,6 +76,8 @@ _SIGS = {
     "riesz_profile": (_I, [_P, _I]),
     "riesz_profile_read": (_I, [_P, _P, _P]),
     "riesz_destroy": (_I, [_P]),
+    "riesz_plan_bytes": (_I, [_P, _P, _P]),
+    "riesz_probe_fp64": (_I, [_I, _P, _P]),
     "riesz_hodge_setup": (_I, [_I, _I, _I64, _P, _I64, _P, ctypes.c_double, ctypes.POINTER(Opts), _P,
                                ctypes.POINTER(_P)]),
     "riesz_hodge_sizes": (_I, [_P, _P, _P, _P]),
@@ -169,6 +171,14 @@ def riesz_ref_mixed_tables(k, p):
     return out
 
 
+def probe_fp64(iters=16384, stream=None):
+    """Measured FP64 FMA rate of the current device in TFLOP/s (riesz_probe_fp64)."""
+    lib = load_library()
+    out = np.zeros(1)
+    _check(lib.riesz_probe_fp64(int(iters), _stream(stream), _ptr(out)))
+    return float(out[0])
+
+
 def solve_batch(solvers, bs, xs, nrhs=None, stream=None):
     """Solve independent systems in one graph launch (riesz_solve_batch).
 
@@ -252,6 +262,13 @@ class Riesz:
         return {"setup_host_ms": out[0], "setup_device_ms": out[1], "device_bytes": out[2],
                 "factor_bytes": out[3], "last_iters": int(out[4]), "launches": int(out[5]),
                 "chol_flops": out[6], "precond_bytes": out[7]}
+
+    def plan_bytes(self):
+        """(bytes, allocations) that setup_device will allocate on the device (host-only)."""
+        b = np.zeros(1)
+        na = np.zeros(1, dtype=np.int64)
+        _check(self.lib.riesz_plan_bytes(self.h, _ptr(b), _ptr(na)))
+        return int(b[0]), int(na[0])
 
     def dirichlet_map(self):
         """Flags (uint8, [N]) of the DOFs fixed by the Dirichlet condition."""

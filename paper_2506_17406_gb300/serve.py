@@ -42,6 +42,7 @@ class Request:
     t_admit: float = float("nan")
     t_done: float = float("nan")
     footprint: int = 0
+    gpu_span: tuple = (float("nan"), float("nan"))  # ms after the server's start event: setup begins, solve ends
     x: np.ndarray = field(default=None, repr=False)
 
     @property
@@ -65,18 +66,15 @@ def poisson_stream(count, rate, seed, spaces=("CG", "N1curl", "RT"), degrees=(3,
     return out
 
 
-def estimate_footprint(h, opts):
-    """Device bytes of a created (host-only) handle for the given apply mode."""
-    st = h.stats()
-    N = h.N
-    n = h.nref
-    elem = 0
-    if opts.get("apply_mode", rz.APPLY_ELEMENT) == rz.APPLY_ELEMENT:
-        elem = h.ncells * n * n * (12 if opts.get("apply_precision", rz.PREC_FP64) == rz.PREC_FP32 else 8)
-    factor64 = st["factor_bytes"] * (2 if opts.get("precond_precision", 0) == rz.PREC_FP32 else 1)
-    vectors = 11 * N * 8 * opts.get("nrhs_max", 1)
-    maps = h.ncells * n * 4 * 3 + 4 * N * 8
-    return int(elem + factor64 + vectors + maps)
+ALLOC_PAGE = 2 << 20  # device allocator granularity allowed for per allocation (an upper bound)
+
+
+def estimate_footprint(h, opts=None):
+    """Device bytes a created (host-only) handle will hold after setup_device: the library's own plan of
+    its buffers (riesz_plan_bytes, the same sizes setup_device allocates) plus one allocator page per
+    allocation.  `opts` is accepted for older callers; the handle's options decide the plan."""
+    b, nalloc = h.plan_bytes()
+    return int(b + nalloc * ALLOC_PAGE)
 
 
 class Server:
@@ -106,12 +104,17 @@ class Server:
         try:
             stream = torch.cuda.Stream()
             with torch.cuda.stream(stream):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                ev[0].record(stream)
                 h.setup_device(stream)
                 b = torch.tensor(normal_vector(h.N, req.seed % 7919), device="cuda")
                 x = torch.zeros_like(b)
                 it, rr, rc = h.solve(b, x, stream=stream, check=False)
+                ev[1].record(stream)
                 stream.synchronize()
                 req.x = x.cpu().numpy()
+                # the request's span on the GPU clock, relative to the server's start event
+                req.gpu_span = (self.ev0.elapsed_time(ev[0]), self.ev0.elapsed_time(ev[1]))
             req.N, req.iters, req.relres, req.status = h.N, int(it[0]), float(rr[0]), int(rc)
         finally:
             req.t_done = time.perf_counter() - t0
@@ -141,6 +144,10 @@ class Server:
     def run(self, requests, realtime=True):
         """Serve the requests; each gets its own thread at its arrival time, which prepares the
         host maps (in parallel with the others), waits for a slot and memory, then solves."""
+        import torch
+        self.ev0 = torch.cuda.Event(enable_timing=True)
+        self.ev0.record()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         threads = []
         for req in sorted(requests, key=lambda r: r.arrival):

@@ -31,15 +31,24 @@ def test_exports_every_declared_symbol(lib):
 
 
 @pytest.mark.parametrize("space", ["CG", "N1curl", "RT"])
-@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 def test_reference_basis_matches_oracle(lib, space, p):
     """The library's basis (Dubiner expansion, own eigen/null-space code) equals the
-    oracle's (Gram-Schmidt expansion, LAPACK) at points of the reference cell."""
+    oracle's (Gram-Schmidt expansion, LAPACK) at points of the reference cell, for every
+    degree the configurations draw (1..10).
+
+    Both sides solve the eigenproblems of Eq. (3.9) independently; inside an eigenvalue
+    cluster the probe rule fixes the basis, but an eigenvector still moves by about
+    eps / (relative gap to the nearest other cluster) under rounding.  Those gaps shrink
+    with p (down to 2.6e-5 at p = 10 for Ned1 and RT), so the agreement is 1e-11 up to
+    p = 5, a few 1e-11 up to p = 8 and at most 1.5e-9 at p = 9, 10 (measured); a wrong
+    cluster, order or sign would differ by O(1)."""
+    tol = 1e-11 if p <= 5 else (1e-10 if p <= 8 else 1e-8)
     X, _ = quadrature(3, 4)
     v, d = rz.riesz_ref_tabulate(space, p, X)
     vo, do = reference_element(space, p).tabulate(X)
-    assert np.abs(v - vo).max() <= 1e-11 * np.abs(vo).max()
-    assert np.abs(d - do).max() <= 1e-11 * np.abs(do).max()
+    assert np.abs(v - vo).max() <= tol * np.abs(vo).max()
+    assert np.abs(d - do).max() <= tol * np.abs(do).max()
 
 
 @pytest.mark.parametrize("space,p,n", [("CG", 3, 4), ("CG", 4, 2), ("N1curl", 3, 3), ("N1curl", 1, 2),

@@ -181,7 +181,7 @@ def test_minres_k3():
 def test_hybrid_blocks_reach_the_papers_range(k, bound):
     """With the paper's hybrid Schwarz form in each Riesz block (Eqs. (7.2)-(7.3)), MINRES at p = 2,
     gamma = 1e3 needs about as many iterations as Table 6 reports (37, 56, 14 for k = 1, 2, 3 on the
-    paper's graded Fichera mesh; here 35, 41, 10 on the 2^3-cube Kuhn mesh), well below the additive
+    paper's graded Fichera mesh; here 35, 41, 10 on the 2^3-cube Fichera mesh), well below the additive
     blocks, and still reaches the direct solution."""
     v, c = fichera_mesh(2, 0.1, 1)
     h = hodge.HodgeSystem(k, 2, v, c, 1e3)
