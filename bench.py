@@ -74,8 +74,9 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
                     help="patch solves in FP64, or FP32 (mixed)")
-    ap.add_argument("--apply-precision", default=None, choices=["fp64", "fp32"],
-                    help="precision of the operator products inside PCG (FP64 residuals either way)")
+    ap.add_argument("--apply-precision", default=None, choices=["fp64", "fp32", "bf16x3"],
+                    help="precision of the operator products inside PCG (FP64 residuals either way): FP64 or "
+                         "FP32 element matrices, or the BF16x3 tensor-core matrix-free contraction")
     ap.add_argument("--serve", action="store_true",
                     help="serving run: Poisson stream of mixed solves, reports DOFs/s and p50/p99 latency")
     ap.add_argument("--requests", type=int, default=48)
@@ -83,10 +84,18 @@ def parse():
                     help="batched run: seeded mixed systems solved in one graph launch per HBM wave")
     ap.add_argument("--systems", type=int, default=64)
     ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
-    ap.add_argument("--decomposition", default="vertex_star", choices=sorted(DECOMPOSITIONS),
+    ap.add_argument("--decomposition", default=None, choices=sorted(DECOMPOSITIONS),
                     help="subspace decomposition: vertex stars (Eq. 6.11), Hiptmair-Toselli edge stars + "
                          "gradient potential problems for H(curl) (Eq. 6.19), or PAFW_1 edge stars for "
                          "H(div) (Eq. 6.24)")
+    ap.add_argument("--form", default=None, choices=["additive", "hybrid"],
+                    help="combination of the subspace corrections: additive, or the paper's symmetric "
+                         "multiplicative hybrid sweep (Section 7.1, Eqs. 7.2-7.3)")
+    ap.add_argument("--coarse", type=int, default=None, choices=[0, 1, 2],
+                    help="W^k coarse space: 0 off, 1 dense inverse up to 6144 DOFs and lowest-order PCG steps above, "
+                         "2 lowest-order PCG steps")
+    ap.add_argument("--coarse-its", type=int, default=None,
+                    help="PCG steps of the lowest-order coarse route (W^k above the dense limit)")
     ap.add_argument("--pcg-loop", default="graph", choices=["graph", "host"],
                     help="device-driven (CUDA graph) or host-driven PCG iterations; same kernels, same results")
     ap.add_argument("--p-sweep", action="store_true",
@@ -194,6 +203,23 @@ def oracle_pass(space, p, n, amp, nrhs=1, seed=1):
     return md.ndofs, dt, max(its)
 
 
+FORMS = {"additive": 0, "hybrid": 1}  # riesz_opts.form
+
+
+def solver_opts(wl, args, decomposition=None, form=None):
+    """Decomposition, form and coarse-space options of the workload (command-line overrides first)."""
+    o = {"decomposition": DECOMPOSITIONS[decomposition or args.decomposition or wl.get("decomposition",
+                                                                                       "vertex_star")],
+         "form": FORMS[form or args.form or wl.get("form", "additive")]}
+    coarse = args.coarse if args.coarse is not None else wl.get("coarse")
+    if coarse is not None:
+        o["coarse"] = coarse
+    cits = args.coarse_its if args.coarse_its is not None else wl.get("coarse_its")
+    if cits is not None:
+        o["coarse_its"] = cits
+    return o
+
+
 def cpu_sample(args):
     return CPU_SAMPLE.get(args.workload, CPU_SAMPLE_DEFAULT)
 
@@ -297,8 +323,8 @@ def combine_ranks(ms, n_local, dist=None, device=None):
 
 SIDE_STREAM_KINDS = {"coarse", "coarse_apply"}
 # kernel kinds launched inside the PCG loop (timing one per launch needs the host-driven loop)
-LOOP_KIND_NAMES = {"apply", "apply32", "gather", "patch_solve", "precond_gather", "dot", "scalar", "update",
-                   "coarse_apply"}
+LOOP_KIND_NAMES = {"apply", "apply32", "apply_tc", "gather", "patch_solve", "precond_gather", "dot", "scalar",
+                   "update", "coarse_apply", "ht"}
 
 
 def kernel_source_hash(name):
@@ -653,6 +679,8 @@ def main():
         wl["a32"] = 0
     elif args.apply_precision == "fp32":
         wl["a32"] = 1
+    elif args.apply_precision == "bf16x3":
+        wl["a32"] = 2
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -675,11 +703,11 @@ def main():
     verts_d = torch.tensor(verts, device="cuda")
     ncomp = 1 if wl["space"] == "CG" else 3
 
-    def make(prec, a32, decomposition=args.decomposition):
+    def make(prec, a32, decomposition=None, form=None):
         """A solver handle for the workload and its step closure (device setup + load + solve)."""
         s = rz.Riesz(wl["space"], wl["p"], verts, cells, precond_precision=prec, nrhs_max=nrhs,
                      apply_precision=a32, loop=rz.LOOP_HOST if args.pcg_loop == "host" else rz.LOOP_GRAPH,
-                     decomposition=DECOMPOSITIONS[decomposition])
+                     **solver_opts(wl, args, decomposition, form))
         if nrhs == 1:  # f with N(0,1) CG_p coefficients per Cartesian component, b = (f, phi)
             fcg_h = normal_coeffs((ncomp, s.n_cg), 2 + rank)
         else:  # the paper's random right-hand side vectors (Section 7.1), one per RHS
@@ -782,6 +810,29 @@ def main():
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                 "algorithmic": "2 sweeps over the stored factor tiles and diagonal inverses + patch "
                                "vectors = %.3e B per launch" % byt}
+    elif dom == "apply_tc":
+        # BF16x3 contraction: algorithmic 2 Q n^2 C nrhs flop per launch (the operator); the tensor pipe
+        # executes three BF16 products per term over the padded tile (rows 128 per tile, N = n padded to
+        # 16, K = Q x n padded to 32)
+        Q = {"CG": 7, "N1curl": 12, "RT": 7}[wl["space"]]
+        algo = 2.0 * Q * n * n * C * nrhs
+        rt = 8 if nrhs >= 8 else (4 if nrhs >= 4 else (2 if nrhs >= 2 else 1))
+        tiles = -(-C // (128 // rt)) * -(-nrhs // rt)
+        np_, kpad = -(-n // 16) * 16, -(-n // 32) * 32 * Q
+        executed = 3 * 2.0 * 128 * np_ * kpad * tiles
+        peak_bf16 = 1704.7
+        try:
+            peak_bf16 = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops_sustained",
+                                                                                             peak_bf16))
+        except Exception:
+            pass
+        tf = executed / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": tf, "peak": peak_bf16, "unit": "TFLOP/s", "frac": tf / peak_bf16,
+                "traffic": measured_traffic(args.workload, "k_apply_tc"), "kernel": "k_apply_tc",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16 GEMM, seconds-long loop)",
+                "algorithmic_tflops": algo / (dom_ms / 1e3) / 1e12,
+                "algorithmic": "operator 2 Q n^2 C nrhs = %.3e flop per launch; executed BF16 MMA work (3 split "
+                               "products, padded tiles) %.3e flop" % (algo, executed)}
     else:
         esize = 4.0 if dom == "apply32" else 8.0
         byt = C * n * n * esize + nrhs * (C * n * 12.0 + s.N * 16.0)
@@ -853,7 +904,8 @@ def main():
     # PAFW_1 edge stars for H(div)): same mesh, right-hand side, precisions and rtol
     variants = {}
     alt = {"N1curl": "ht", "RT": "edge_star"}.get(wl["space"])
-    if alt and alt != args.decomposition and not args.no_variants:
+    main_decomp = args.decomposition or wl.get("decomposition", "vertex_star")
+    if alt and alt != main_decomp and not args.no_variants:
         sv, stepv, itv, rrv, *_ = make(wl["prec"], wl.get("a32", 0), alt)
         for _ in range(args.warmup):
             stepv()
@@ -882,20 +934,26 @@ def main():
 
         def small_solver(v, c):
             return rz.Riesz(wl["space"], wl["p"], v, c, precond_precision=wl["prec"], nrhs_max=nrhs,
-                            apply_precision=wl.get("a32", 0), decomposition=DECOMPOSITIONS[args.decomposition])
+                            apply_precision=wl.get("a32", 0), **solver_opts(wl, args))
         err = err_vs_oracle(wl, args, small_solver)
 
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "DOFs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl["prec"] == 0 else "f64+f32",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32+bf16" if wl.get("a32", 0) == 2 else ("f64" if wl["prec"] == 0 and not wl.get("a32", 0)
+                                                                   else "f64+f32"),
             "data": "synthetic",
             "config": {"workload": wl["label"], "space": wl["space"], "p": wl["p"], "cells": C, "dofs": s.N,
-                       "nrhs": nrhs, "apply_precision": "fp32" if wl.get("a32", 0) else "fp64",
+                       "nrhs": nrhs, "apply_precision": {0: "fp64", 1: "fp32", 2: "bf16x3 tensor cores"}[
+                           wl.get("a32", 0)],
                        "precond_precision": "fp32" if wl["prec"] == 1 else "fp64",
                        "rtol": 1e-8, "step": "device setup + load + PCG solve",
-                       "pcg_loop": loop_driver, "decomposition": args.decomposition,
+                       "pcg_loop": loop_driver, "decomposition": main_decomp,
+                       "form": args.form or wl.get("form", "additive"),
+                       "coarse_solve": {0: "none", 1: "dense inverse", 2: "lowest-order PCG"}[
+                           s.tuning()["coarse_mode"]] if "coarse_mode" in s.tuning() else None,
                        "autotuned": s.tuning(),
                        "l2": "inputs larger than L2 (element matrices and patch factors)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

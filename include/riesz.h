@@ -68,10 +68,11 @@ enum {
   RIESZ_ERR_NO_DEVICE = 8      /* a device call on a handle without device state */
 };
 
-enum { RIESZ_PREC_FP64 = 0, RIESZ_PREC_FP32 = 1 };
+enum { RIESZ_PREC_FP64 = 0, RIESZ_PREC_FP32 = 1, RIESZ_PREC_BF16X3 = 2 };
 enum { RIESZ_APPLY_MATRIX_FREE = 0, RIESZ_APPLY_ELEMENT = 1 };
 enum { RIESZ_LOOP_HOST = 0, RIESZ_LOOP_GRAPH = 1 };
 enum { RIESZ_DECOMP_VERTEX_STAR = 0, RIESZ_DECOMP_HT = 1, RIESZ_DECOMP_EDGE_STAR = 2 };
+enum { RIESZ_FORM_ADDITIVE = 0, RIESZ_FORM_HYBRID = 1 };
 
 typedef struct {
   /* Precision of the stored patch Cholesky factors and of the triangular
@@ -97,7 +98,15 @@ typedef struct {
      b - A x whenever a right-hand side gains four digits
      and at convergence (the stopping test is always on the FP64 residual);
      the first residual needs no product when x = 0.  riesz_apply is always
-     FP64.  Default RIESZ_PREC_FP64. */
+     FP64.  RIESZ_PREC_BF16X3 (any apply_mode, n_ref <= 512): the same
+     products, and the residual updates of the hybrid sweep, matrix-free on
+     the tensor cores (tcgen05): Y_T = sum_q g_q(T) R_q X_T as a GEMM over
+     tiles of 128 (cell, right-hand side) rows with every operand split into
+     two BF16 parts (hi + lo) and the three leading products accumulated in
+     FP32 in tensor memory (relative error ~1e-5 per product); no FP32
+     element matrices are stored.  With the hybrid form and FP32 patch
+     sweeps, RIESZ_PREC_FP32 also moves the sweep's residual updates to the
+     FP32 element matrices.  Default RIESZ_PREC_FP64. */
   int apply_precision;
   /* Who drives the PCG iterations of riesz_solve.  RIESZ_LOOP_GRAPH (default):
      the iterations run as a CUDA graph whose WHILE node repeats the body
@@ -131,10 +140,17 @@ typedef struct {
      with weight w = 1/2 (every W^k function also lies in the vertex-star
      spaces, so the unweighted sum over-corrects).  A_0 is assembled densely and inverted in FP32 at device
      setup (block Gauss-Jordan) and applied as a dense product, so it is used
-     only when W^k has at most 6144 DOFs (otherwise the preconditioner stays
-     one-level; riesz_tuning reports the coarse size).  Its FP32 rounding only
-     perturbs the preconditioner: solves run flexible PCG and stop on the FP64
-     true residual.  0: one-level preconditioner. */
+     only when W^k has at most 6144 DOFs.  Above that the coarse problem,
+     which is the lowest-order Riesz map on the same mesh (Lemma 4.1), is
+     held by an internal p = 1 handle and solved approximately by coarse_its
+     PCG steps from zero preconditioned by that handle's own vertex-star
+     patches (on the lowest-order H(curl)/H(div) problems these are robust
+     in h: 3 steps reduce the residual 10x on 8^3 and 16^3 Kuhn meshes), all
+     on the device with the main loop's PCG kernels.  Either way the coarse
+     solve only perturbs the preconditioner: solves run flexible PCG and stop
+     on the FP64 true residual.  riesz_tuning reports the coarse size and
+     route.  0: one-level preconditioner.  2: the lowest-order PCG route
+     whatever the size. */
   int coarse;
   /* 0 (default): pure Neumann (the paper's benchmarks).  1: homogeneous
      Dirichlet conditions on the whole boundary (X_{p,D} of Eq. (2.8) with
@@ -163,6 +179,20 @@ typedef struct {
      Jacobi and W^k as above.  RT_8: 216-DOF edge problems instead of
      1296-DOF vertex stars. */
   int decomposition;
+  /* How the subspace corrections combine.  RIESZ_FORM_ADDITIVE (default):
+     the sum above.  RIESZ_FORM_HYBRID: the paper's symmetric multiplicative
+     sweep over X_1 = interior DOFs (point-Jacobi), X_2 = interface DOFs (the
+     patch solves of the decomposition) and X_3 = W^k (when coarse is on),
+     in the order X_1, X_2, X_3, X_2, X_1 with the residual updated by an
+     operator product between steps, each correction divided by its weight
+     rho_m = (lambda_min + 3 lambda_max) / 4 of the extreme eigenvalues of the
+     subspace operator against its solver, estimated at device setup by 10
+     Lanczos (CG) steps (Section 7.1, Eqs. (7.2)-(7.3)); riesz_hybrid_weights
+     reads or sets them. */
+  int form;
+  /* PCG steps of the lowest-order coarse route (see coarse; 1..1000,
+     default 4). */
+  int coarse_its;
 } riesz_opts;
 
 /* Fill *o with the defaults: FP64 preconditioner, element-matrix apply,
@@ -346,7 +376,8 @@ enum {
   RIESZ_K_COARSE = 15,      /* W^k: A_0 assembly and block inversion     */
   RIESZ_K_COARSE_APPLY = 16,/* W^k: coarse correction A_0^{-1} R_0 r     */
   RIESZ_K_HT = 17,          /* HT: gradient map and potential gather     */
-  RIESZ_NKIND = 18
+  RIESZ_K_APPLY_TC = 18,    /* a3-a4 BF16x3 contraction on tensor cores  */
+  RIESZ_NKIND = 19
 };
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around
@@ -362,7 +393,8 @@ int riesz_profile_read(riesz_handle* h, double* ms, int64_t* counts);
    the autotuner (0: no limit), out[1] = candidates timed for this shape (by
    this handle or an earlier one; 0 when tuning does not apply), out[2] = DOFs of the W^k coarse space (0 when it is off),
    out[3] = CTAs per patch in the factorisation (1, or 2 for a 2-CTA cluster
-   that shares each patch). */
+   that shares each patch), out[4] = the W^k solve: 0 none, 1 dense inverse,
+   2 lowest-order PCG steps.  out: host [5]. */
 int riesz_tuning(const riesz_handle* h, int* out);
 
 /* Timings (ms) and sizes of the last setup / solve:
@@ -382,6 +414,25 @@ int riesz_stats(const riesz_handle* h, double* out);
    (at most one 2 MiB page per allocation).  Lets a scheduler budget HBM
    before a request touches the device. */
 int riesz_plan_bytes(const riesz_handle* h, double* bytes, int64_t* nalloc);
+
+/* y = A x with the products of the given precision, as riesz_solve runs them
+   inside its iterations: RIESZ_PREC_FP64 (= riesz_apply), RIESZ_PREC_FP32
+   (the FP32 element matrices; handles that keep them) or RIESZ_PREC_BF16X3
+   (the tensor-core contraction; handles with apply_precision BF16X3).
+   x, y: device [nrhs][N], distinct.  RIESZ_ERR_INVALID_ARG when the handle
+   does not hold that precision. */
+int riesz_apply_prec(riesz_handle* h, const double* x, double* y, int nrhs, int prec, void* stream);
+
+/* Weights rho_1, rho_2, rho_3 of the hybrid form (opts.form =
+   RIESZ_FORM_HYBRID; Section 7.1, Eq. (7.3)) for X_1 = interior DOFs,
+   X_2 = interface DOFs, X_3 = W^k.  set = 0: rho (host [3]) receives the
+   weights estimated at the last device setup (10 Lanczos steps from a fixed
+   start vector; rho_3 = 1 for the W^k solve, which is exact or the
+   lowest-order PCG steps);
+   set = 1: the handle uses rho from now on and keeps them through later
+   setups (riesz_update_geometry).  RIESZ_ERR_INVALID_ARG for other handles
+   or non-positive weights. */
+int riesz_hybrid_weights(riesz_handle* h, double* rho, int set);
 
 /* Measurement helper (no counterpart in the paper): the FP64 fused
    multiply-add rate of the current device, in TFLOP/s, from one timed launch

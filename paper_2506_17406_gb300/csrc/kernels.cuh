@@ -1688,6 +1688,113 @@ __global__ void __launch_bounds__(256) k_ct_lauum(int N0p, int nb, const double*
     for (int q = 0; q < 4; ++q) Xij[(int64_t)(ty + 16 * a) * N0p + 4 * tx + q] = -acc[a][q];
 }
 
+// ---------------------------------------------------------------------------
+// Hybrid (symmetric multiplicative) form of the preconditioner (Section 7.1,
+// Eqs. (7.2)-(7.3)): one subspace correction c from the current residual, c
+// zero outside the subspace, added to z (z = c on the first step of a sweep).
+// ---------------------------------------------------------------------------
+// X_1: interior DOFs, c_I = w D_II^{-1} res_I
+__global__ void k_hyb_interior(int64_t N, int64_t nifd, const double* __restrict__ dinv,
+                               const double* __restrict__ res, double w, double* __restrict__ c,
+                               double* __restrict__ z, int nrhs, int first) {
+  const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (d >= N) return;
+  for (int rh = 0; rh < nrhs; ++rh) {
+    const int64_t o = rh * N + d;
+    const double v = d < nifd ? 0.0 : w * dinv[d - nifd] * res[o];
+    c[o] = v;
+    z[o] = first ? v : z[o] + v;
+  }
+}
+
+// X_2: interface DOFs, c = w (sum of the patch solutions [+ the gradient corrections]);
+// Dirichlet DOFs carry the identity block unweighted (c_d = res_d)
+__global__ void k_hyb_interface(int64_t N, int64_t nifd, const int64_t* __restrict__ ptr,
+                                const int32_t* __restrict__ pos, const double* __restrict__ zpatch, int64_t zstride,
+                                const double* __restrict__ zg, const uint8_t* __restrict__ dmask,
+                                const double* __restrict__ res, double w, double* __restrict__ c,
+                                double* __restrict__ z, int nrhs, int first) {
+  const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (d >= N) return;
+  for (int rh = 0; rh < nrhs; ++rh) {
+    const int64_t o = rh * N + d;
+    double v = 0.0;
+    if (d < nifd) {
+      if (dmask && dmask[d]) {
+        v = res[o];
+      } else {
+        double t = 0.0;
+        for (int64_t k = ptr[d]; k < ptr[d + 1]; ++k) t += zpatch[rh * zstride + pos[k]];
+        if (zg) t += zg[rh * nifd + d];
+        v = w * t;
+      }
+    }
+    c[o] = v;
+    z[o] = first ? v : z[o] + v;
+  }
+}
+
+// X_3: W^k, c = w zc at the coarse DOFs (cidx: interface DOF -> coarse index or -1)
+__global__ void k_hyb_coarse(int64_t N, int64_t nifd, const int32_t* __restrict__ cidx,
+                             const double* __restrict__ zc, int64_t n0, double w, double* __restrict__ c,
+                             double* __restrict__ z, int nrhs) {
+  const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (d >= N) return;
+  const int ci = d < nifd ? cidx[d] : -1;
+  for (int rh = 0; rh < nrhs; ++rh) {
+    const int64_t o = rh * N + d;
+    const double v = ci >= 0 ? w * zc[rh * n0 + ci] : 0.0;
+    c[o] = v;
+    z[o] += v;
+  }
+}
+
+// out = in - Ac (the residual after a correction; out may alias in)
+__global__ void k_hyb_residual(int64_t n, const double* in, const double* __restrict__ Ac, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i] - Ac[i];
+}
+
+// v = 0 outside one subspace: keep = 1 the interface DOFs (without the Dirichlet ones), keep = 2 the
+// interior DOFs
+__global__ void k_restrict(int64_t N, int64_t nifd, const uint8_t* __restrict__ dmask, int keep,
+                           double* __restrict__ v) {
+  const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (d >= N) return;
+  const bool iface = d < nifd && !(dmask && dmask[d]);
+  const bool in = keep == 1 ? iface : d >= nifd;
+  if (!in) v[d] = 0.0;
+}
+
+// y = a x + b y
+__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+// ---------------------------------------------------------------------------
+// W^k coarse solve above the dense limit: the coarse problem is the lowest-order
+// Riesz map on the same mesh (Lemma 4.1), held by an internal p = 1 handle; its
+// vector is indexed by entity, the coarse vector by coarse index.
+// ---------------------------------------------------------------------------
+// out[rh][map[j]] = r[rh][cw[j]] (out zeroed before: entities without a coarse DOF stay 0)
+__global__ void k_coarse_to_aux(int N0, const int32_t* __restrict__ cw, const int32_t* __restrict__ map,
+                                const double* __restrict__ r, int64_t N, int nrhs, double* __restrict__ out,
+                                int64_t Na) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nrhs * N0) return;
+  const int rh = (int)(t / N0), j = (int)(t % N0);
+  out[rh * Na + map[j]] = r[rh * N + cw[j]];
+}
+// zc[rh][j] = w xa[rh][map[j]]
+__global__ void k_coarse_from_aux(int N0, const int32_t* __restrict__ map, const double* __restrict__ xa, int64_t Na,
+                                  int nrhs, double w, double* __restrict__ zc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nrhs * N0) return;
+  const int rh = (int)(t / N0), j = (int)(t % N0);
+  zc[(int64_t)rh * N0 + j] = w * xa[rh * Na + map[j]];
+}
+
 // r0[rh][j] = r[rh][cw[j]] (zero padding up to N0p)
 template <typename T>
 __global__ void k_coarse_gather(int N0, int N0p, const int32_t* __restrict__ cw, const double* __restrict__ r,

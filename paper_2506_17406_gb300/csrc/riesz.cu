@@ -17,6 +17,7 @@
 
 #include "../../include/riesz.h"
 #include "kernels.cuh"
+#include "tc_apply.cuh"
 #include "mesh.h"
 #include "refelem.h"
 
@@ -132,6 +133,23 @@ struct riesz_handle {
   DBuf<double> d_X0d;   // FP64 path: X = -(L^{-T} L^{-1}) (the factor and its inverse are built in d_A0d)
   DBuf<int> d_cbad;     // non-positive pivot in the coarse Cholesky
   DBuf<double> d_zc;                  // coarse corrections [nrhs][N0]
+  // hybrid form (opts.form): the subspace weights rho_1..3 (index 0 unused), fixed once set by
+  // the caller, and the sweep's residual, correction and product vectors [nrhs][N]
+  double rho[4] = {0.0, 1.0, 1.0, 1.0};
+  bool rho_fixed = false;
+  DBuf<double> d_hres, d_hc, d_hAc;
+  // BF16x3 tensor-core contraction (apply_precision = RIESZ_PREC_BF16X3): the split reference
+  // matrices in the kernel's stage layout, n padded to 16 (tc_np) and the number of 32-wide K chunks
+  DBuf<uint16_t> d_Btc;
+  int tc_np = 0, tc_kc = 0;
+  // coarse solve above the dense limit (or opts.coarse = 2): A_0 is the lowest-order Riesz map
+  // on the same mesh (Lemma 4.1), held by an internal p = 1 handle with its own vertex-star
+  // patches; a coarse application runs opts.coarse_its PCG steps on it.  c_aux maps coarse index
+  // -> that handle's DOF (its entity index)
+  bool coarse_sparse = false;
+  riesz_handle* caux = nullptr;
+  std::vector<int32_t> c_aux;
+  DBuf<int32_t> d_caux;
   int multi_group = 8;  // right-hand sides per k_patch_solve_multi launch
   int chol_ctas = 0;    // resident k_cholesky CTAs per SM picked by the autotuner (0: no limit)
   int chol_tuned = 0;   // candidates the autotuner timed
@@ -181,7 +199,8 @@ struct riesz_handle {
            (aux ? aux->device_bytes() : 0) + d_cw.bytes() + d_cidx.bytes() + d_cJ.bytes() +
            d_ccell.bytes() + d_cab.bytes() + d_cptr.bytes() + d_A0.bytes() + d_Dinv0.bytes() + d_Rb0.bytes() +
            d_r0.bytes() + d_zc.bytes() + d_A0d.bytes() + d_X0d.bytes() + d_Dinv0d.bytes() + d_Rb0d.bytes() + d_r0d.bytes() +
-           d_info.bytes() + d_ticket.bytes() + d_cbad.bytes();
+           d_info.bytes() + d_ticket.bytes() + d_cbad.bytes() + d_caux.bytes() + (caux ? caux->device_bytes() : 0) +
+           d_hres.bytes() + d_hc.bytes() + d_hAc.bytes() + d_Btc.bytes();
   }
   void drop_graphs() {
     if (g_entry) cudaGraphExecDestroy(g_entry);
@@ -218,6 +237,12 @@ struct riesz_handle {
     d_Rb0d.free();
     d_r0d.free();
     d_zc.free();
+    d_caux.free();
+    if (caux) caux->free_device();
+    d_hres.free();
+    d_hc.free();
+    d_hAc.free();
+    d_Btc.free();
     if (h_ctl) cudaFreeHost(h_ctl);
     h_ctl = nullptr;
     d_L32.free();
@@ -247,6 +272,7 @@ struct riesz_handle {
     if (ev_hfork) cudaEventDestroy(ev_hfork);
     if (ev_hjoin) cudaEventDestroy(ev_hjoin);
     delete aux;
+    delete caux;
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   }
 };
@@ -663,7 +689,8 @@ void plan_coarse(riesz_handle& h) {
     const int64_t gd = M.off[k] + (int64_t)nd * e;
     if (h.dir_mask.empty() || !h.dir_mask[gd]) w.push_back((int32_t)gd);
   }
-  if (w.empty() || (int64_t)w.size() > COARSE_MAX) return;
+  if (w.empty()) return;
+  h.coarse_sparse = h.opts.coarse == 2 || (int64_t)w.size() > COARSE_MAX;
   const int N0 = (int)w.size();
   const int nloc = k == 1 ? 6 : 4;
   const int loc0 = k == 0 ? 0 : (k == 1 ? 4 * M.per_entity[0] : 4 * M.per_entity[0] + 6 * M.per_entity[1]);
@@ -705,6 +732,11 @@ void plan_coarse(riesz_handle& h) {
   }
   for (int i = 0; i < N0; ++i) h.c_ptr[i + 1] += h.c_ptr[i];
   h.coarse_on = true;
+  if (h.coarse_sparse) {  // coarse index -> entity (the DOF of the p = 1 handle)
+    h.c_aux.resize(N0);
+    for (int j = 0; j < N0; ++j) h.c_aux[j] = (int32_t)((h.c_w[j] - M.off[k]) / nd);
+    return;
+  }
   // FP64 Cholesky-route coarse inverse when the weights are unbalanced: kappa(A_0) grows like
   // (alpha / beta) h^-2 (or beta / alpha), and beyond ~1e4 the FP32 Gauss-Jordan inverse is no longer
   // positive definite
@@ -832,10 +864,21 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 // ---- operator pieces ------------------------------------------------------
 // y = A x for nrhs right-hand sides; fp32 selects the FP32 copy of the element
 // matrices (inner applies of the mixed-precision solver).
-void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_t s, bool fp32 = false) {
+void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_t s, int prec = RIESZ_PREC_FP64) {
   const int n = h.mesh.nref;
   const int64_t C = h.C(), N = h.N();
-  if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
+  const bool fp32 = prec == RIESZ_PREC_FP32;
+  if (prec == RIESZ_PREC_BF16X3) {
+    const int RT = nrhs >= 8 ? 8 : (nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1));
+    const int cells = dev::TC_ROWS / RT;
+    dim3 grid((unsigned)((C + cells - 1) / cells), (unsigned)((nrhs + RT - 1) / RT));
+    launch(h, RIESZ_K_APPLY_TC, s, [&] {
+      const int ns = dev::tc_stages(h.tc_np);
+      dev::k_apply_tc<<<grid, dev::TC_NT, dev::tc_smem_bytes(h.tc_np, ns), s>>>(
+          C, n, h.nif, h.ref->Q, h.tc_np, h.tc_kc, RT, ns, h.d_Btc.p, h.d_g.p, h.d_cdofs.p, x, y, h.d_Ycell.p, nrhs, N,
+          h.dmask(), h.d_flags.p + 2);
+    });
+  } else if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     const int rows = (n % 2 == 0) ? n / 2 : n;
     const int nt = std::min(1024, (rows + 31) / 32 * 32);
     if (fp32) {
@@ -933,7 +976,7 @@ void op_patch_solves(riesz_handle& h, const double* r, int nrhs, cudaStream_t s)
 
 // Coarse corrections zc = A_0^{-1} R_0 r (W^k), when the handle has a coarse space.
 template <typename T>
-void op_coarse_t(riesz_handle& h, const double* r, int nrhs, cudaStream_t s, T* A0, T* r0) {
+void op_coarse_t(riesz_handle& h, const double* r, int nrhs, cudaStream_t s, T* A0, T* r0, double w) {
   const int64_t N = h.N();
   const unsigned grid = (unsigned)std::min<int64_t>((h.N0 + 7) / 8, 608);
   launch(h, RIESZ_K_COARSE_APPLY, s, [&] {
@@ -943,17 +986,52 @@ void op_coarse_t(riesz_handle& h, const double* r, int nrhs, cudaStream_t s, T* 
     const int nr = std::min(h.coarse_group, nrhs - k0);
     launch(h, RIESZ_K_COARSE_APPLY, s, [&] {
       dev::k_coarse_apply<T><<<grid, 256, (size_t)nr * h.N0p * sizeof(T), s>>>(
-          h.N0, h.N0p, A0, r0 + (int64_t)k0 * h.N0p, nr, COARSE_WEIGHT, h.d_zc.p + (int64_t)k0 * h.N0);
+          h.N0, h.N0p, A0, r0 + (int64_t)k0 * h.N0p, nr, w, h.d_zc.p + (int64_t)k0 * h.N0);
     });
   }
 }
 
-void op_coarse(riesz_handle& h, const double* r, int nrhs, cudaStream_t s) {
+void iter_tail(riesz_handle& h, double* x, int nrhs, cudaStream_t s);
+void iter_head(riesz_handle& h, int nrhs, cudaStream_t s);
+void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* zold, int op, double* scal, int nrhs,
+                    cudaStream_t s);
+// Sparse route: zc = w * (opts.coarse_its PCG steps from zero on the p = 1 handle, its vertex-star
+// patches as the preconditioner), all on the device with the PCG kernels of the main loop (device-side
+// scalars, no host round trip), so it is captured into the loop graphs like any other step.
+void op_coarse_sparse(riesz_handle& h, const double* r, int nrhs, cudaStream_t s, double w) {
+  riesz_handle& a = *h.caux;
+  const int64_t N = h.N(), Na = a.N();
+  const size_t vb = (size_t)nrhs * Na * sizeof(double);
+  CK(cudaMemsetAsync(a.d_r.p, 0, vb, s));
+  CK(cudaMemsetAsync(a.d_xw.p, 0, vb, s));
+  CK(cudaMemsetAsync(a.d_scal.p, 0, (size_t)nrhs * dev::SCAL_STRIDE * sizeof(double), s));
+  launch(h, RIESZ_K_COARSE_APPLY, s, [&] {
+    dev::k_coarse_to_aux<<<nblk((int64_t)nrhs * h.N0, 256), 256, 0, s>>>(h.N0, h.d_cw.p, h.d_caux.p, r, N, nrhs,
+                                                                         a.d_r.p, Na);
+  });
+  // z = P r, p = z, (r, z)
+  op_precond_dot(a, a.d_r.p, a.d_z.p, nullptr, 5, a.d_scal.p, nrhs, s);
+  CK(cudaMemcpyAsync(a.d_p.p, a.d_z.p, vb, cudaMemcpyDeviceToDevice, s));
+  for (int k = 0; k < h.opts.coarse_its; ++k) {
+    if (k > 0) iter_head(a, nrhs, s);
+    iter_tail(a, a.d_xw.p, nrhs, s);
+  }
+  launch(h, RIESZ_K_COARSE_APPLY, s, [&] {
+    dev::k_coarse_from_aux<<<nblk((int64_t)nrhs * h.N0, 256), 256, 0, s>>>(h.N0, h.d_caux.p, a.d_xw.p, Na, nrhs, w,
+                                                                           h.d_zc.p);
+  });
+}
+
+// zc = w A_0^{-1} R_0 r (dense inverse, or the sparse CG's approximation); the additive form uses
+// w = COARSE_WEIGHT.
+void op_coarse(riesz_handle& h, const double* r, int nrhs, cudaStream_t s, double w = COARSE_WEIGHT) {
   if (!h.coarse_on) return;
-  if (h.coarse64)
-    op_coarse_t<double>(h, r, nrhs, s, h.d_X0d.p, h.d_r0d.p);
+  if (h.coarse_sparse)
+    op_coarse_sparse(h, r, nrhs, s, w);
+  else if (h.coarse64)
+    op_coarse_t<double>(h, r, nrhs, s, h.d_X0d.p, h.d_r0d.p, w);
   else
-    op_coarse_t<float>(h, r, nrhs, s, h.d_A0.p, h.d_r0.p);
+    op_coarse_t<float>(h, r, nrhs, s, h.d_A0.p, h.d_r0.p, w);
 }
 
 // The coarse correction reads only r: it runs on the side stream beside the
@@ -1003,8 +1081,70 @@ void ht_join(riesz_handle& h, cudaStream_t s) {
   if (h.ht) CK(cudaStreamWaitEvent(s, h.ev_hjoin, 0));
 }
 
+// The hybrid form (Section 7.1, Eq. (7.2)): the subspace corrections applied one after the other,
+// X_1, X_2, X_3, X_2, X_1 (X_3 = W^k only with the coarse space, X_1 only with interior DOFs), each
+// divided by its weight rho_m, the residual updated by an operator product after every step but the
+// last.  The products use the FP32 element matrices when the patch sweeps are FP32.
+bool hyb_fp32(const riesz_handle& h);
+int sweep_prec(const riesz_handle& h);
+void hybrid_sweep(const riesz_handle& h, std::vector<int>& steps) {
+  steps.clear();
+  const bool interior = h.mesh.n_interior > 0;
+  if (interior) steps.push_back(1);
+  steps.push_back(2);
+  if (h.coarse_on) {
+    steps.push_back(3);
+    steps.push_back(2);
+  }
+  if (interior) steps.push_back(1);
+}
+
+void op_precond_hybrid(riesz_handle& h, const double* r, double* z, int nrhs, cudaStream_t s) {
+  const int64_t N = h.N(), nI = h.mesh.n_interface;
+  std::vector<int> steps;
+  hybrid_sweep(h, steps);
+  const int sp = sweep_prec(h);
+  const double* res = r;
+  double* c = h.d_hc.p;
+  for (size_t i = 0; i < steps.size(); ++i) {
+    const int m = steps[i];
+    const int first = i == 0 ? 1 : 0;
+    if (m == 1) {
+      launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
+        dev::k_hyb_interior<<<nblk(N, 256), 256, 0, s>>>(N, nI, h.d_dinv.p, res, 1.0 / h.rho[1], c, z, nrhs, first);
+      });
+    } else if (m == 2) {
+      ht_fork(h, res, nrhs, s);
+      op_patch_solves(h, res, nrhs, s);
+      ht_join(h, s);
+      launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
+        dev::k_hyb_interface<<<nblk(N, 256), 256, 0, s>>>(N, nI, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p,
+                                                         (int64_t)h.p_dofs.size(), h.ht ? h.d_zg.p : nullptr,
+                                                         h.dmask(), res, 1.0 / h.rho[2], c, z, nrhs, first);
+      });
+    } else {
+      op_coarse(h, res, nrhs, s, 1.0);
+      launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
+        dev::k_hyb_coarse<<<nblk(N, 256), 256, 0, s>>>(N, nI, h.d_cidx.p, h.d_zc.p, h.N0, 1.0 / h.rho[3], c, z,
+                                                      nrhs);
+      });
+    }
+    if (i + 1 < steps.size()) {
+      op_apply(h, c, h.d_hAc.p, nrhs, s, sp);
+      launch(h, RIESZ_K_UPDATE, s, [&] {
+        dev::k_hyb_residual<<<1184, 256, 0, s>>>((int64_t)nrhs * N, res, h.d_hAc.p, h.d_hres.p);
+      });
+      res = h.d_hres.p;
+    }
+  }
+}
+
 void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStream_t s) {
   const int64_t N = h.N();
+  if (h.opts.form == RIESZ_FORM_HYBRID) {
+    op_precond_hybrid(h, r, z, nrhs, s);
+    return;
+  }
   ht_fork(h, r, nrhs, s);
   coarse_fork(h, r, nrhs, s);
   op_patch_solves(h, r, nrhs, s);
@@ -1019,9 +1159,16 @@ void op_precond(riesz_handle& h, const double* r, double* z, int nrhs, cudaStrea
 }
 
 // z = P^{-1} r followed by (r, z) [and (r, zold)] -> scalar op, per right-hand side.
+void dot(riesz_handle& h, const double* a, const double* b, const double* c, int op, double* scal, int nrhs,
+         cudaStream_t s);
 void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* zold, int op, double* scal, int nrhs,
                     cudaStream_t s) {
   const int64_t N = h.N();
+  if (h.opts.form == RIESZ_FORM_HYBRID) {
+    op_precond_hybrid(h, r, z, nrhs, s);
+    dot(h, r, z, zold, op, scal, nrhs, s);
+    return;
+  }
   ht_fork(h, r, nrhs, s);
   coarse_fork(h, r, nrhs, s);
   op_patch_solves(h, r, nrhs, s);
@@ -1047,13 +1194,124 @@ void read_scal(riesz_handle& h, const double* scal, int nrhs, cudaStream_t s) {
   CK(cudaStreamSynchronize(s));
 }
 
-bool use_a32(const riesz_handle& h) {
-  return h.opts.apply_precision == RIESZ_PREC_FP32 && h.opts.apply_mode == RIESZ_APPLY_ELEMENT;
+// The FP32 copy of the element matrices serves the search-direction products (apply_precision FP32)
+// and the residual updates inside the hybrid sweep (precond_precision FP32).
+bool hyb_fp32(const riesz_handle& h) {
+  return h.opts.form == RIESZ_FORM_HYBRID && h.opts.precond_precision == RIESZ_PREC_FP32 &&
+         h.opts.apply_mode == RIESZ_APPLY_ELEMENT;
 }
+
+// Precision of the search-direction products inside riesz_solve: FP64, the FP32 element matrices, or
+// the BF16x3 tensor-core contraction (matrix-free).
+int inner_prec(const riesz_handle& h) {
+  if (h.opts.apply_precision == RIESZ_PREC_BF16X3) return RIESZ_PREC_BF16X3;
+  if (h.opts.apply_precision == RIESZ_PREC_FP32 && h.opts.apply_mode == RIESZ_APPLY_ELEMENT) return RIESZ_PREC_FP32;
+  return RIESZ_PREC_FP64;
+}
+bool use_a32(const riesz_handle& h) { return inner_prec(h) != RIESZ_PREC_FP64; }
+// Precision of the residual updates inside the hybrid sweep.
+int sweep_prec(const riesz_handle& h) {
+  if (h.opts.apply_precision == RIESZ_PREC_BF16X3) return RIESZ_PREC_BF16X3;
+  return hyb_fp32(h) ? RIESZ_PREC_FP32 : RIESZ_PREC_FP64;
+}
+bool needs_ae32(const riesz_handle& h) {
+  return inner_prec(h) == RIESZ_PREC_FP32 || (h.opts.form == RIESZ_FORM_HYBRID && sweep_prec(h) == RIESZ_PREC_FP32);
+}
+bool needs_tc(const riesz_handle& h) { return h.opts.apply_precision == RIESZ_PREC_BF16X3; }
 // Flexible (Polak-Ribiere) beta whenever an FP32 piece enters the preconditioner
 // or the search-direction product.
 bool use_flex(const riesz_handle& h) {
   return h.opts.precond_precision == RIESZ_PREC_FP32 || use_a32(h) || h.coarse_on;
+}
+
+// Weights of the hybrid form (Section 7.1, Eq. (7.3)): rho_m = (lambda_min + 3 lambda_max) / 4 of the
+// generalized eigenproblem a(u, v) = lambda a~_m(u, v) on X_m, the extremes estimated by `iters` steps
+// of CG on X_m preconditioned by the subspace solver (the Lanczos tridiagonal from the CG coefficients,
+// its eigenvalues by Jacobi rotations), from a fixed pseudo-random start vector.  X_1 (interior,
+// point-Jacobi) and X_2 (interface, the patch solves); the W^k solve is exact (dense inverse) or
+// a few PCG steps on the lowest-order problem (sparse route), so rho_3 = 1.
+uint64_t splitmix64(uint64_t& x) {
+  uint64_t z = (x += 0x9e3779b97f4a7c15ull);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+double lanczos_weight(riesz_handle& h, int m, int iters, cudaStream_t s) {
+  const int64_t N = h.N(), nI = h.mesh.n_interface;
+  double *r = h.d_r.p, *z = h.d_z.p, *p = h.d_p.p, *Ap = h.d_Ap.p;
+  std::vector<double> r0(N);
+  uint64_t st = 0x5eed0000ull + (uint64_t)m;
+  for (int64_t i = 0; i < N; ++i) r0[i] = (double)(splitmix64(st) >> 11) * 0x1.0p-52 - 1.0;
+  CK(cudaMemcpyAsync(r, r0.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
+  const int keep = m == 1 ? 2 : 1;
+  auto restrict_ = [&](double* v) {
+    dev::k_restrict<<<nblk(N, 256), 256, 0, s>>>(N, nI, h.dmask(), keep, v);
+    KCHECK();
+  };
+  auto solver = [&]() {  // z = B_m r
+    if (m == 1) {
+      dev::k_hyb_interior<<<nblk(N, 256), 256, 0, s>>>(N, nI, h.d_dinv.p, r, 1.0, z, z, 1, 1);
+      KCHECK();
+    } else {
+      ht_fork(h, r, 1, s);
+      op_patch_solves(h, r, 1, s);
+      ht_join(h, s);
+      dev::k_hyb_interface<<<nblk(N, 256), 256, 0, s>>>(N, nI, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p,
+                                                       (int64_t)h.p_dofs.size(), h.ht ? h.d_zg.p : nullptr,
+                                                       h.dmask(), r, 1.0, z, z, 1, 1);
+      KCHECK();
+    }
+    restrict_(z);
+  };
+  auto dotv = [&](const double* a, const double* b) {
+    dot(h, a, b, nullptr, 6, h.d_scal.p, 1, s);
+    read_scal(h, h.d_scal.p, 1, s);
+    return h.h_scal[dev::S_XX];
+  };
+  restrict_(r);
+  solver();
+  CK(cudaMemcpyAsync(p, z, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double rz = dotv(r, z);
+  std::vector<double> al, be;
+  for (int j = 0; j < iters && rz > 0.0 && std::isfinite(rz); ++j) {
+    op_apply(h, p, Ap, 1, s, sweep_prec(h));
+    restrict_(Ap);
+    const double pap = dotv(p, Ap);
+    if (!(pap > 0.0)) break;
+    const double a = rz / pap;
+    dev::k_axpby<<<1184, 256, 0, s>>>(N, -a, Ap, 1.0, r);
+    KCHECK();
+    solver();
+    const double rzn = dotv(r, z);
+    al.push_back(a);
+    be.push_back(rzn / rz);
+    if (!(rzn > 0.0) || !std::isfinite(rzn)) break;
+    dev::k_axpby<<<1184, 256, 0, s>>>(N, 1.0, z, be.back(), p);
+    KCHECK();
+    rz = rzn;
+  }
+  const int k = (int)al.size();
+  if (k == 0) return 1.0;
+  Mat T(k, k);
+  for (int j = 0; j < k; ++j) {
+    T(j, j) = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+    if (j + 1 < k) T(j, j + 1) = T(j + 1, j) = std::sqrt(be[j]) / al[j];
+  }
+  std::vector<double> w;
+  Mat V;
+  sym_eig(T, w, V);
+  return (w.front() + 3.0 * w.back()) / 4.0;
+}
+
+void hybrid_weights(riesz_handle& h, cudaStream_t s) {
+  if (h.opts.form != RIESZ_FORM_HYBRID || h.rho_fixed) return;
+  const double r1 = h.mesh.n_interior > 0 ? lanczos_weight(h, 1, 10, s) : 1.0;
+  const double r2 = lanczos_weight(h, 2, 10, s);
+  if (r1 != h.rho[1] || r2 != h.rho[2]) h.drop_graphs();  // the loop graphs hold the weights as arguments
+  h.rho[1] = r1;
+  h.rho[2] = r2;
+  h.rho[3] = 1.0;
 }
 
 // PCG for nrhs right-hand sides in lockstep (Section 7.1): one apply and one
@@ -1123,7 +1381,7 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
   } else {
     restart();
     while (it < h.opts.maxit) {
-      op_apply(h, p, Ap, nrhs, s, a32);
+      op_apply(h, p, Ap, nrhs, s, inner_prec(h));
       dot(h, p, Ap, nullptr, 0, scal, nrhs, s);
       launch(h, RIESZ_K_UPDATE, s, [&] {
         dev::k_update_xr<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(N, scal, x, r, p, Ap, h.d_part.p,
@@ -1198,7 +1456,8 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
 // handle-owned buffers (x is the handle's working copy d_xw), so they are
 // built once per handle and nrhs and relaunched.
 
-constexpr unsigned LOOP_KINDS = (1u << RIESZ_K_APPLY) | (1u << RIESZ_K_APPLY32) | (1u << RIESZ_K_GATHER) |
+constexpr unsigned LOOP_KINDS = (1u << RIESZ_K_APPLY) | (1u << RIESZ_K_APPLY32) | (1u << RIESZ_K_APPLY_TC) |
+                                (1u << RIESZ_K_GATHER) |
                                 (1u << RIESZ_K_PATCH_SOLVE) | (1u << RIESZ_K_PRECOND_GATHER) | (1u << RIESZ_K_DOT) |
                                 (1u << RIESZ_K_SCALAR) | (1u << RIESZ_K_UPDATE) | (1u << RIESZ_K_COARSE_APPLY) |
                                 (1u << RIESZ_K_HT);
@@ -1208,7 +1467,7 @@ bool profiling_loop(const riesz_handle& h) { return h.prof && (h.prof_mask & LOO
 // Ap = A p; (p, Ap) -> alpha; x += alpha p, r -= alpha Ap; (r, r) -> RR
 void iter_tail(riesz_handle& h, double* x, int nrhs, cudaStream_t s) {
   const int64_t N = h.N();
-  op_apply(h, h.d_p.p, h.d_Ap.p, nrhs, s, use_a32(h));
+  op_apply(h, h.d_p.p, h.d_Ap.p, nrhs, s, inner_prec(h));
   dot(h, h.d_p.p, h.d_Ap.p, nullptr, 0, h.d_scal.p, nrhs, s);
   launch(h, RIESZ_K_UPDATE, s, [&] {
     dev::k_update_xr<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(N, h.d_scal.p, x, h.d_r.p, h.d_p.p, h.d_Ap.p,
@@ -1233,6 +1492,7 @@ std::pair<int64_t, int64_t> add_loop(riesz_handle& h, cudaGraph_t G, int nrhs, b
   cudaStream_t cs = h.cap_stream;
   const int64_t l0 = h.launches;
   const int64_t la0 = h.aux ? h.aux->launches : 0;  // launches of the potential problems count here too
+  const int64_t lc0 = h.caux ? h.caux->launches : 0;  // and those of the lowest-order coarse handle
   int64_t pro = 0, body = 0;
   cudaGraphConditionalHandle hc;
   CK(cudaGraphConditionalHandleCreate(&hc, G, entry ? 0u : 1u, cudaGraphCondAssignDefault));
@@ -1279,6 +1539,10 @@ std::pair<int64_t, int64_t> add_loop(riesz_handle& h, cudaGraph_t G, int nrhs, b
   captured(cp.conditional.phGraph_out[0], [&] { iter_head(h, nrhs, cs); iter_tail(h, h.d_xw.p, nrhs, cs); control(); },
            nullptr);
   body = h.launches - l1;
+  if (h.caux) {  // the coarse steps run in the body (and in the entry graph's prologue only via the head)
+    body += h.caux->launches - lc0;
+    h.caux->launches = lc0;
+  }
   if (h.aux) {
     const int64_t la = h.aux->launches - la0;  // prologue has none: the potential step is in the body only
     body += la;
@@ -1673,8 +1937,18 @@ void coarse_setup_chol(riesz_handle& h, cudaStream_t s) {
            [&] { dev::k_coarse_mirror<double><<<nb * (nb - 1) / 2, 256, 0, s>>>(h.N0p, h.d_X0d.p); });
 }
 
+void device_compute(riesz_handle& h, cudaStream_t s, bool with_aux, bool sync);
+// Sparse route: the p = 1 handle's geometry, element matrices and patch factors for the same vertices.
+void coarse_setup_sparse(riesz_handle& h, cudaStream_t s) {
+  riesz_handle& a = *h.caux;
+  CK(cudaMemcpyAsync(a.d_verts.p, h.d_verts.p, h.d_verts.bytes(), cudaMemcpyDeviceToDevice, s));
+  device_compute(a, s, false, false);
+}
+
 void coarse_setup(riesz_handle& h, cudaStream_t s) {
-  if (h.coarse64)
+  if (h.coarse_sparse)
+    coarse_setup_sparse(h, s);
+  else if (h.coarse64)
     coarse_setup_chol(h, s);
   else
     coarse_setup_t<float>(h, s, h.d_A0, h.d_Dinv0, h.d_Rb0);
@@ -1682,7 +1956,7 @@ void coarse_setup(riesz_handle& h, cudaStream_t s) {
 
 // Patch factorisations that met a non-positive pivot (after the stream is synchronised).
 void check_factor_info(riesz_handle& h, cudaStream_t s) {
-  if (h.coarse_on && h.coarse64) {
+  if (h.coarse_on && h.coarse64 && !h.coarse_sparse) {
     int bad = 0;
     CK(cudaMemcpyAsync(&bad, h.d_cbad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1787,6 +2061,8 @@ void device_compute(riesz_handle& h, cudaStream_t s, bool with_aux = true, bool 
   cudaEventDestroy(e1);
   check_factor_info(h, s);
   if (aux_now) check_factor_info(*h.aux, s);
+  if (h.caux && h.coarse_on) check_factor_info(*h.caux, s);
+  hybrid_weights(h, s);
 }
 
 // Autotuner of the patch factorisation's residency: with between one and 24
@@ -1860,6 +2136,44 @@ void tune_cholesky(riesz_handle& h, cudaStream_t s) {
   device_compute(h, s, false);  // factors (and their FP32 copies) with the chosen residency
 }
 
+// Round-to-nearest-even BF16 bits of an FP32 value (finite inputs).
+uint16_t bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+float bf16_value(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// The B operand of k_apply_tc: for each stage (32-wide chunk jc of j, then q) the split
+// R_q[i][jc*32 + kk] = hi + lo (hi = bf16(R), lo = bf16(R - hi)), hi block then lo block, each
+// [NP/8 row groups][4 K core matrices][8 rows][8 values] (the K-major layout without swizzle).
+void build_tc_table(riesz_handle& h, std::vector<uint16_t>& t) {
+  const int n = h.mesh.nref, Q = h.ref->Q, NP = h.tc_np, KC = h.tc_kc;
+  const std::vector<double>& R = h.ref->R;
+  const size_t blk = (size_t)NP * dev::TC_KC;
+  t.assign((size_t)KC * Q * 2 * blk, 0);
+  for (int jc = 0; jc < KC; ++jc)
+    for (int q = 0; q < Q; ++q) {
+      const size_t base = ((size_t)jc * Q + q) * 2 * blk;
+      for (int i = 0; i < n; ++i)
+        for (int kk = 0; kk < dev::TC_KC; ++kk) {
+          const int k = jc * dev::TC_KC + kk;
+          if (k >= n) break;
+          const double v = R[(size_t)q * n * n + (size_t)i * n + k];
+          const uint16_t hi = bf16_bits((float)v);
+          const uint16_t lo = bf16_bits((float)(v - (double)bf16_value(hi)));
+          const size_t idx = ((size_t)(i / 8) * 4 + kk / 8) * 64 + (size_t)(i % 8) * 8 + kk % 8;
+          t[base + idx] = hi;
+          t[base + blk + idx] = lo;
+        }
+    }
+}
+
 void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) throw Err(RIESZ_ERR_CUDA, "no CUDA device");
@@ -1912,7 +2226,7 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   h.d_info.alloc(std::max(1, npatch));
   if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     h.d_Ae.alloc((size_t)C * n * n);
-    if (h.opts.apply_precision == RIESZ_PREC_FP32) h.d_Ae32.alloc((size_t)C * n * n);
+    if (needs_ae32(h)) h.d_Ae32.alloc((size_t)C * n * n);
   } else {
     const size_t sm = ((size_t)n + R.Q) * dev::TC * sizeof(double);
     raise_smem_limit(dev::k_apply_mf, (size_t)sm);
@@ -1952,7 +2266,13 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     h.d_zcg.alloc((size_t)nrhs * h.aux->mesh.n_interface);
     h.d_zg.alloc((size_t)nrhs * M.n_interface);
   }
-  if (h.coarse_on) {
+  if (h.coarse_on && h.coarse_sparse) {
+    h.d_cw.upload(h.c_w, s);
+    h.d_cidx.upload(h.c_idx, s);
+    h.d_caux.upload(h.c_aux, s);
+    h.d_zc.alloc((size_t)nrhs * h.N0);
+    setup_device_impl(*h.caux, s);
+  } else if (h.coarse_on) {
     h.d_cw.upload(h.c_w, s);
     h.d_cidx.upload(h.c_idx, s);
     h.d_cptr.upload(h.c_ptr, s);
@@ -2007,6 +2327,16 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     const int nbm = h.p_n.empty() ? 1 : (h.p_n[0] + 31) / 32;
     raise_smem_limit(dev::k_patch_sweep<float, SWEEP_SLOTS_F32>, sweep_smem<float>(SWEEP_SLOTS_F32, nbm));
     raise_smem_limit(dev::k_patch_sweep<double, SWEEP_SLOTS_F64>, sweep_smem<double>(SWEEP_SLOTS_F64, nbm));
+  }
+  if (h.opts.form == RIESZ_FORM_HYBRID)
+    for (auto* b : {&h.d_hres, &h.d_hc, &h.d_hAc}) b->alloc((size_t)N * nrhs);
+  if (needs_tc(h)) {
+    h.tc_np = (n + 15) / 16 * 16;
+    h.tc_kc = (n + dev::TC_KC - 1) / dev::TC_KC;
+    std::vector<uint16_t> t;
+    build_tc_table(h, t);
+    h.d_Btc.upload(t, s);
+    raise_smem_limit(dev::k_apply_tc, dev::tc_smem_bytes(h.tc_np, dev::tc_stages(h.tc_np)));
   }
   h.d_ticket.alloc(nrhs);
   CK(cudaMemsetAsync(h.d_ticket.p, 0, sizeof(unsigned) * nrhs, s));
@@ -2070,7 +2400,7 @@ double plan_device_bytes(const riesz_handle& h, int64_t* nalloc) {
   add(std::max<double>(1, npatch), 4);             // info
   if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     add(C * n * n, 8);
-    if (h.opts.apply_precision == RIESZ_PREC_FP32) add(C * n * n, 4);
+    if (needs_ae32(h)) add(C * n * n, 4);
   }
   add((double)h.p_dioff.size(), 8);
   add((double)h.p_moff.size(), 8);
@@ -2089,7 +2419,15 @@ double plan_device_bytes(const riesz_handle& h, int64_t* nalloc) {
     add(nrhs * (double)h.aux->mesh.n_interface, 8);
     add(nrhs * (double)M.n_interface, 8);
   }
-  if (h.coarse_on) {
+  if (h.coarse_on && h.coarse_sparse) {
+    add((double)h.c_w.size(), 4);
+    add((double)h.c_idx.size(), 4);
+    add((double)h.c_aux.size(), 4);
+    add(nrhs * h.N0, 8);  // zc
+    int64_t na_c = 0;
+    b += plan_device_bytes(*h.caux, &na_c);
+    na += na_c;
+  } else if (h.coarse_on) {
     const double N0p = h.N0p, CB = dev::CB;
     add((double)h.c_w.size(), 4);
     add((double)h.c_idx.size(), 4);
@@ -2125,6 +2463,12 @@ double plan_device_bytes(const riesz_handle& h, int64_t* nalloc) {
       add(de, 4);
     }
   }
+  if (h.opts.form == RIESZ_FORM_HYBRID)
+    for (int k = 0; k < 3; ++k) add(N * nrhs, 8);  // sweep residual, correction, product
+  if (needs_tc(h)) {  // split reference matrices in the tensor-core stage layout
+    const double NP = (M.nref + 15) / 16 * 16, KC = (M.nref + dev::TC_KC - 1) / dev::TC_KC;
+    add(KC * R.Q * 2 * NP * dev::TC_KC, 2);
+  }
   add(nrhs, 4);  // ticket
   if (nalloc) *nalloc = na;
   return b;
@@ -2157,10 +2501,13 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
            std::isfinite(h->opts.alpha) && std::isfinite(h->opts.beta),
        "alpha and beta must be positive and finite");
   if (h->apply_only) h->opts.coarse = 0;
-  need(h->opts.apply_precision == 0 || h->opts.apply_precision == 1, "bad apply_precision");
+  need(h->opts.apply_precision >= RIESZ_PREC_FP64 && h->opts.apply_precision <= RIESZ_PREC_BF16X3,
+       "bad apply_precision");
   need(h->opts.loop == RIESZ_LOOP_HOST || h->opts.loop == RIESZ_LOOP_GRAPH, "bad loop");
   need(h->opts.autotune >= 0 && h->opts.autotune <= 2, "bad autotune");
-  need(h->opts.coarse == 0 || h->opts.coarse == 1, "bad coarse");
+  need(h->opts.coarse >= 0 && h->opts.coarse <= 2, "bad coarse");
+  need(h->opts.coarse_its >= 1 && h->opts.coarse_its <= 1000, "coarse_its must be in 1..1000");
+  need(h->opts.form == RIESZ_FORM_ADDITIVE || h->opts.form == RIESZ_FORM_HYBRID, "bad form");
   need(h->opts.dirichlet == 0 || h->opts.dirichlet == 1, "bad dirichlet");
   need(h->opts.decomposition >= RIESZ_DECOMP_VERTEX_STAR && h->opts.decomposition <= RIESZ_DECOMP_EDGE_STAR,
        "bad decomposition");
@@ -2181,11 +2528,25 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
   } catch (const std::exception& e) {
     throw Err(RIESZ_ERR_BAD_MESH, e.what());
   }
+  need(h->opts.apply_precision != RIESZ_PREC_BF16X3 || h->mesh.nref <= dev::TC_MAXNP,
+       "the BF16x3 tensor-core products hold n_ref <= 512 accumulators per row (degree too high)");
   if (h->opts.dirichlet) plan_dirichlet(*h);
   if (h->opts.decomposition == RIESZ_DECOMP_HT) plan_ht(*h);
   if (h->opts.decomposition == RIESZ_DECOMP_EDGE_STAR) plan_edge_stars(*h, 0, h->mesh.per_entity[2]);
   build_plans(*h);
   plan_coarse(*h);
+  if (h->coarse_on && h->coarse_sparse) {  // W^k = the lowest-order space: its own p = 1 handle
+    riesz_opts co = h->opts;
+    co.coarse = 0;
+    co.form = RIESZ_FORM_ADDITIVE;
+    co.decomposition = RIESZ_DECOMP_VERTEX_STAR;
+    co.precond_precision = RIESZ_PREC_FP64;
+    co.apply_precision = RIESZ_PREC_FP64;
+    co.apply_mode = RIESZ_APPLY_ELEMENT;
+    co.autotune = 0;
+    h->caux = create_handle(space, 1, nverts, verts, ncells, cells, co, true);
+    if (h->caux->N() < (int64_t)h->c_w.size()) throw Err(RIESZ_ERR_INTERNAL, "lowest-order handle too small");
+  }
   if (h->ht) {  // potential problems: CG_p on the same mesh with a = beta (grad, grad), vertex stars
     riesz_opts ao = h->opts;
     ao.alpha = h->opts.beta;
@@ -2247,6 +2608,8 @@ void riesz_default_opts(riesz_opts* o) {
   o->coarse = 1;
   o->dirichlet = 0;
   o->decomposition = RIESZ_DECOMP_VERTEX_STAR;
+  o->form = RIESZ_FORM_ADDITIVE;
+  o->coarse_its = 4;
 }
 
 const char* riesz_last_error(void) { return g_err.c_str(); }
@@ -2541,17 +2904,25 @@ int riesz_tuning(const riesz_handle* h, int* out) {
     out[1] = h->chol_tuned;
     out[2] = h->coarse_on ? h->N0 : 0;
     out[3] = h->chol_split;
+    out[4] = !h->coarse_on ? 0 : (h->coarse_sparse ? 2 : 1);
   });
 }
 
 int riesz_profile(riesz_handle* h, int enable) {
   return guarded([&] {
     need(h != nullptr, "null handle");
-    for (riesz_handle* x : {h, h->aux}) {  // the potential problems' kernels are reported with the handle's
+    // the potential problems' kernels are reported with the handle's own kinds; the kernels of the
+    // lowest-order coarse handle as RIESZ_K_COARSE (its setup) and RIESZ_K_COARSE_APPLY (its PCG steps)
+    const unsigned mask = (unsigned)enable;
+    unsigned cmask = 0;
+    if (mask & (1u << RIESZ_K_COARSE)) cmask |= ~LOOP_KINDS;
+    if (mask & (1u << RIESZ_K_COARSE_APPLY)) cmask |= LOOP_KINDS;
+    for (riesz_handle* x : {h, h->aux, h->caux}) {
       if (!x) continue;
       if (!x->prof_pending.empty()) prof_collect(*x);
-      x->prof = enable != 0;
-      x->prof_mask = (unsigned)enable;
+      const unsigned m = x == h->caux ? cmask : mask;
+      x->prof = m != 0;
+      x->prof_mask = m;
       for (int k = 0; k < RIESZ_NKIND; ++k) {
         x->prof_ms[k] = 0.0;
         x->prof_cnt[k] = 0;
@@ -2565,9 +2936,17 @@ int riesz_profile_read(riesz_handle* h, double* ms, int64_t* counts) {
     need(h != nullptr, "null handle");
     prof_collect(*h);
     if (h->aux) prof_collect(*h->aux);
+    if (h->caux) prof_collect(*h->caux);
     for (int k = 0; k < RIESZ_NKIND; ++k) {
       if (ms) ms[k] = h->prof_ms[k] + (h->aux ? h->aux->prof_ms[k] : 0.0);
       if (counts) counts[k] = h->prof_cnt[k] + (h->aux ? h->aux->prof_cnt[k] : 0);
+    }
+    if (h->caux) {
+      for (int k = 0; k < RIESZ_NKIND; ++k) {
+        const int to = ((LOOP_KINDS >> k) & 1u) ? RIESZ_K_COARSE_APPLY : RIESZ_K_COARSE;
+        if (ms) ms[to] += h->caux->prof_ms[k];
+        if (counts) counts[to] += h->caux->prof_cnt[k];
+      }
     }
   });
 }
@@ -2580,7 +2959,7 @@ int riesz_stats(const riesz_handle* h, double* out) {
     out[2] = (double)h->device_bytes();
     out[3] = (double)(h->factor_entries + h->dinv_entries) * (h->opts.precond_precision == RIESZ_PREC_FP32 ? 4.0 : 8.0);
     out[4] = h->last_iters;
-    out[5] = (double)(h->launches + (h->aux ? h->aux->launches : 0));
+    out[5] = (double)(h->launches + (h->aux ? h->aux->launches : 0) + (h->caux ? h->caux->launches : 0));
     out[6] = h->chol_flops + (h->aux ? h->aux->chol_flops : 0.0);
     const double fb = h->opts.precond_precision == RIESZ_PREC_FP32 ? 4.0 : 8.0;
     out[7] = 2.0 * (double)(h->factor_entries + h->dinv_entries) * fb + (double)h->p_dofs.size() * 20.0;
@@ -2616,6 +2995,33 @@ int riesz_probe_fp64(int iters, void* stream, double* tflops) {
     CK(rc);
     const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
     *tflops = flops / (ms * 1e-3) / 1e12;
+  });
+}
+
+int riesz_apply_prec(riesz_handle* h, const double* x, double* y, int nrhs, int prec, void* stream) {
+  return guarded([&] {
+    check_dev(h);
+    need(x && y && x != y, "x and y must be distinct device arrays");
+    need(nrhs >= 1 && nrhs <= h->opts.nrhs_max, "nrhs out of range");
+    need(prec == RIESZ_PREC_FP64 || (prec == RIESZ_PREC_FP32 && h->d_Ae32.p) || (prec == RIESZ_PREC_BF16X3 && h->d_Btc.p),
+         "precision not held by this handle (FP32: FP32 element matrices; BF16X3: apply_precision BF16X3)");
+    op_apply(*h, x, y, nrhs, S(stream), prec);
+    KCHECK();
+  });
+}
+
+int riesz_hybrid_weights(riesz_handle* h, double* rho, int set) {
+  return guarded([&] {
+    need(h != nullptr && rho != nullptr, "null argument");
+    need(h->opts.form == RIESZ_FORM_HYBRID, "the handle does not use the hybrid form");
+    if (set) {
+      for (int m = 0; m < 3; ++m) need(rho[m] > 0.0 && std::isfinite(rho[m]), "weights must be positive");
+      for (int m = 0; m < 3; ++m) h->rho[m + 1] = rho[m];
+      h->rho_fixed = true;
+      h->drop_graphs();
+    } else {
+      for (int m = 0; m < 3; ++m) rho[m] = h->rho[m + 1];
+    }
   });
 }
 
@@ -2867,13 +3273,19 @@ int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t
     // MINRES needs a positive definite preconditioner: the W^k inverses of the blocks by the FP64
     // Cholesky route (A_0 = R_0 (M + gamma K) R_0^T and gamma^{-1} M + K reach kappa ~ 1e7 for gamma
     // far from 1, where an explicit Gauss-Jordan inverse, even in FP64, is no longer definite)
-    H->P0->coarse64 = true;
+    // MINRES also needs a fixed (linear) preconditioner, which the sparse coarse CG is not: blocks whose
+    // W^k is above the dense limit stay one-level
+    auto dense_coarse_only = [](riesz_handle* P) {
+      P->coarse64 = true;
+      if (P->coarse_sparse) P->coarse_on = P->coarse_sparse = false;
+    };
+    dense_coarse_only(H->P0);
     if (k < 3) {
       o1.alpha = 1.0;
       o1.beta = 1.0 / gamma;
       o1.decomposition = decomp(k);
       H->P1 = create_handle(k, p, nverts, verts, ncells, cells, o1, true);
-      H->P1->coarse64 = true;
+      dense_coarse_only(H->P1);
     }
     // operator blocks
     riesz_opts om = b, ok = b;

@@ -1,0 +1,294 @@
+// Matrix-free operator on the 5th-generation tensor cores (sm_103a tcgen05):
+//   Y_c = sum_q g_q(c) R_q X_c           (Section 6.4; the Q reference matrices R_q
+// of the pullbacks of Eq. (2.7) against per-cell geometric factors g_q) as one
+// GEMM per tile of 128 (cell, right-hand side) rows:
+//   D[m][i] = sum_{(q, j)} A[m][(q, j)] B[(q, j)][i],
+//   A[m][(q, j)] = g_q(c_m) X_{c_m}[j],   B[(q, j)][i] = R_q[i][j]  (R_q symmetric),
+// in split BF16 with FP32 accumulation: every operand value v is v_hi + v_lo with
+// v_hi = bf16(v), v_lo = bf16(v - v_hi), and D accumulates A_hi B_hi + A_hi B_lo +
+// A_lo B_hi (the A_lo B_lo term is below the FP32 accumulation error).
+//
+// Layout.  The accumulator D (128 lanes x NP FP32 columns, NP = n padded to a
+// multiple of 16, at most 512) lives in tensor memory for the whole K loop.  K
+// runs over stages (j-chunk of 32, q): the B stage (hi and lo, NP rows x 32 K)
+// is a precomputed table in the canonical K-major layout without swizzle (core
+// matrices of 8 rows x 16 bytes, K-adjacent core matrices 128 B apart, 8-row
+// groups 512 B apart), so one bulk copy (cp.async.bulk) moves a stage into
+// shared memory; the A stage (hi and lo, 128 rows x 32 K, same layout) is built
+// by the four producer warps from the gathered X and g.  Ring of NSTAGE slots,
+// mbarriers with bounded waits.
+//
+// Warp roles (192 threads): warp 0 allocates tensor memory and issues the B
+// bulk copies (one lane); warps 1-4 gather X, build the A stages and run the
+// epilogue (warp w reads tensor-memory lanes 32 (w % 4) .. + 31, so row
+// m = 32 (w % 4) + lane); warp 5 (one lane) issues the MMAs and commits them
+// to the slot's "empty" barrier and, after the last stage, to "done".
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace riesz {
+namespace dev {
+
+constexpr int TC_NT = 192;
+constexpr int TC_ROWS = 128;   // M of one MMA (cta_group::1)
+constexpr int TC_KC = 32;      // K per stage (BF16 elements)
+constexpr int TC_NSTAGE = 3;   // most ring slots (fewer when shared memory does not hold three)
+constexpr int TC_MAXNP = 512;  // tensor-memory columns
+
+// bytes of one A stage (hi + lo) and of one B stage (hi + lo) for NP rows
+__host__ __device__ constexpr uint32_t tc_a_bytes() { return 2u * TC_ROWS * TC_KC * 2u; }
+__host__ __device__ constexpr uint32_t tc_b_bytes(int NP) { return 2u * (uint32_t)NP * TC_KC * 2u; }
+inline size_t tc_smem_bytes(int NP, int nstage) {
+  return (size_t)nstage * (tc_a_bytes() + tc_b_bytes(NP)) + 256;
+}
+// ring slots that fit in the 227 KB of shared memory a CTA may hold
+inline int tc_stages(int NP) { return tc_smem_bytes(NP, 3) <= 232448 ? 3 : 2; }
+
+// Shared-memory matrix descriptor (K-major, no swizzle): start address, leading
+// byte offset (between K-adjacent core matrices), stride byte offset (between
+// 8-row groups), descriptor version 1.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N x M tile.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this warp's 32 tensor-memory lanes
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// round-to-nearest-even BF16 of an FP32 value (finite inputs)
+__device__ __forceinline__ uint16_t tc_bf16(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+__device__ __forceinline__ float tc_bf16_to_f32(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+// y = A x (interior rows) and Ycell (interface rows, scattered by k_gather_iface)
+// for tiles of CELLS = 128 / RT cells and RT right-hand sides: row m = r * CELLS + c.
+// Bst: the B stages [KC][Q][hi | lo][NP / 8][4][8][8] BF16 (see the file comment).
+__global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif, int Q, int NP, int KC, int RT, int NS,
+                                                      const uint16_t* __restrict__ Bst, const double* __restrict__ g,
+                                                      const int32_t* __restrict__ cdofs, const double* __restrict__ x,
+                                                      double* __restrict__ y, double* __restrict__ Ycell, int nrhs,
+                                                      int64_t N, const uint8_t* __restrict__ dmask,
+                                                      int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tc_sm[];
+  const uint32_t abytes = tc_a_bytes(), bbytes = tc_b_bytes(NP);
+  unsigned char* sA = tc_sm;                           // [NS][abytes]
+  unsigned char* sB = tc_sm + (size_t)NS * abytes;     // [NS][bbytes]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)NS * bbytes);
+  uint64_t* full_a = bars;                   // [NS], 128 producer arrivals
+  uint64_t* full_b = bars + TC_NSTAGE;       // [NS], expect_tx
+  uint64_t* empty = bars + 2 * TC_NSTAGE;    // [NS], MMA commit
+  uint64_t* done = bars + 3 * TC_NSTAGE;     // accumulator complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * TC_NSTAGE + 1);
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int CELLS = TC_ROWS / RT;
+  const int64_t c0 = (int64_t)blockIdx.x * CELLS;
+  const int r0 = blockIdx.y * RT;
+  const int nst = KC * Q;
+  uint32_t ncols = 32;
+  while ((int)ncols < NP) ncols <<= 1;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full_a[s], 128);
+      mbar_init(&full_b[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // B stages: one bulk copy each into the ring
+    if (lane == 0) {
+      int issued = 0;
+      for (int s = 0; s < nst; ++s) {
+        const int slot = s % NS, use = s / NS;
+        if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1, err)) {
+          abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(&full_b[slot], bbytes);
+        bulk_g2s(sB + (size_t)slot * bbytes, Bst + (size_t)s * (bbytes / 2), bbytes, &full_b[slot]);
+        issued = s + 1;
+      }
+      // no copy may still be landing when the CTA exits (they have all landed in a complete run)
+      for (int s = issued > NS ? issued - NS : 0; s < issued; ++s) mbar_wait(&full_b[s % NS], (s / NS) & 1, err);
+    }
+  } else if (warp <= 4) {
+    // A producers: row m of the tile
+    const int m = 32 * (warp & 3) + lane;
+    const int cl = m % CELLS, rl = m / CELLS;
+    const int64_t c = c0 + cl;
+    const int r = r0 + rl;
+    const bool valid = c < C && r < nrhs;
+    const uint32_t rowoff = (uint32_t)(m >> 3) * 512u + (uint32_t)(m & 7) * 16u;
+    bool ok = true;
+    for (int jc = 0; jc < KC && ok; ++jc) {
+      float xf[TC_KC];
+#pragma unroll
+      for (int e = 0; e < TC_KC; ++e) {
+        const int j = jc * TC_KC + e;
+        float v = 0.f;
+        if (valid && j < n) {
+          const int64_t dof = cdofs[(int64_t)j * C + c];
+          if (!(dmask && j < nif && dmask[dof])) v = (float)x[(int64_t)r * N + dof];
+        }
+        xf[e] = v;
+      }
+      for (int q = 0; q < Q; ++q) {
+        const int s = jc * Q + q, slot = s % NS, use = s / NS;
+        if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1, err)) {
+          ok = false;
+          abort_flag = 1;
+          break;
+        }
+        unsigned char* hi = sA + (size_t)slot * abytes;
+        unsigned char* lo = hi + abytes / 2;
+        const float gv = valid ? (float)g[q * C + c] : 0.f;
+#pragma unroll
+        for (int kc = 0; kc < 4; ++kc) {
+          uint32_t ph[4], pl[4];
+#pragma unroll
+          for (int e2 = 0; e2 < 4; ++e2) {
+            const float a0 = gv * xf[kc * 8 + 2 * e2], a1 = gv * xf[kc * 8 + 2 * e2 + 1];
+            const uint16_t h0 = tc_bf16(a0), h1 = tc_bf16(a1);
+            const uint16_t l0 = tc_bf16(a0 - tc_bf16_to_f32(h0)), l1 = tc_bf16(a1 - tc_bf16_to_f32(h1));
+            ph[e2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+            pl[e2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+          }
+          const uint32_t off = rowoff + (uint32_t)kc * 128u;
+          *reinterpret_cast<uint4*>(hi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+          *reinterpret_cast<uint4*>(lo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        }
+        fence_async_smem();
+        mbar_arrive(&full_a[slot]);
+      }
+    }
+  } else {
+    // MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc0 = tc_idesc(TC_ROWS, NP <= 256 ? NP : (NP / 2 + 15) / 16 * 16);
+      const int np0 = NP <= 256 ? NP : (NP / 2 + 15) / 16 * 16;  // first N piece
+      const int np1 = NP - np0;                                 // second piece (0 if NP <= 256)
+      const uint32_t idesc1 = np1 > 0 ? tc_idesc(TC_ROWS, np1) : 0u;
+      bool ok = true;
+      for (int s = 0; s < nst && ok; ++s) {
+        const int slot = s % NS, use = s / NS;
+        if (!mbar_wait(&full_a[slot], use & 1, err) || !mbar_wait(&full_b[slot], use & 1, err)) {
+          ok = false;
+          abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_hi = smem_addr(sA + (size_t)slot * abytes), a_lo = a_hi + abytes / 2;
+        const uint32_t b_hi = smem_addr(sB + (size_t)slot * bbytes), b_lo = b_hi + bbytes / 2;
+#pragma unroll
+        for (int ks = 0; ks < TC_KC / 16; ++ks) {
+          const uint32_t ko = (uint32_t)ks * 256u;
+          const uint64_t ah = tc_desc(a_hi + ko, 128, 512), al = tc_desc(a_lo + ko, 128, 512);
+          const uint64_t bh0 = tc_desc(b_hi + ko, 128, 512), bl0 = tc_desc(b_lo + ko, 128, 512);
+          const int acc0 = (s > 0 || ks > 0) ? 1 : 0;
+          tc_mma(tmem, ah, bh0, idesc0, acc0);
+          tc_mma(tmem, ah, bl0, idesc0, 1);
+          tc_mma(tmem, al, bh0, idesc0, 1);
+          if (np1 > 0) {
+            const uint32_t bo = (uint32_t)(np0 / 8) * 512u;
+            const uint64_t bh1 = tc_desc(b_hi + bo + ko, 128, 512), bl1 = tc_desc(b_lo + bo + ko, 128, 512);
+            const uint32_t d1 = tmem + (uint32_t)np0;
+            tc_mma(d1, ah, bh1, idesc1, acc0);
+            tc_mma(d1, ah, bl1, idesc1, 1);
+            tc_mma(d1, al, bh1, idesc1, 1);
+          }
+        }
+        tc_commit(&empty[slot]);
+      }
+      tc_commit(done);
+    }
+  }
+
+  // epilogue: warps 1-4 read their lanes of the accumulator
+  if (warp >= 1 && warp <= 4) {
+    const bool ok = mbar_wait(done, 0, err) && !abort_flag;
+    tc_fence_after();
+    const int q4 = warp & 3;
+    const int m = 32 * q4 + lane;
+    const int cl = m % CELLS, rl = m / CELLS;
+    const int64_t c = c0 + cl;
+    const int r = r0 + rl;
+    const bool valid = c < C && r < nrhs;
+    const double bad = __longlong_as_double(0x7ff8000000000000ll);
+    for (int i0 = 0; i0 < NP; i0 += 16) {
+      float v[16];
+      tc_ld16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)i0, v);
+      if (!valid) continue;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int i = i0 + k;
+        if (i >= n) break;
+        const double val = ok ? (double)v[k] : bad;
+        if (i >= nif)
+          y[(int64_t)r * N + cdofs[(int64_t)i * C + c]] = val;
+        else
+          Ycell[((int64_t)r * nif + i) * C + c] = val;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
+}  // namespace dev
+}  // namespace riesz

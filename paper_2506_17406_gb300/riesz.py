@@ -15,13 +15,14 @@ from . import build as _build
 
 H1, HCURL, HDIV, L2 = 0, 1, 2, 3
 SPACES = {"CG": H1, "H1": H1, "N1curl": HCURL, "HCURL": HCURL, "RT": HDIV, "HDIV": HDIV, "DG": L2, "L2": L2}
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_BF16X3 = 0, 1, 2
 APPLY_MATRIX_FREE, APPLY_ELEMENT = 0, 1
 LOOP_HOST, LOOP_GRAPH = 0, 1
 DECOMP_VERTEX_STAR, DECOMP_HT, DECOMP_EDGE_STAR = 0, 1, 2
+FORM_ADDITIVE, FORM_HYBRID = 0, 1
 
 KINDS = ["geom", "elem", "diag", "assemble", "cholesky", "to_f32", "apply", "gather", "patch_solve",
-         "precond_gather", "dot", "scalar", "update", "load", "apply32", "coarse", "coarse_apply", "ht"]
+         "precond_gather", "dot", "scalar", "update", "load", "apply32", "coarse", "coarse_apply", "ht", "apply_tc"]
 
 ERRORS = {1: "INVALID_ARG", 2: "BAD_MESH", 3: "OOM", 4: "NOT_CONVERGED", 5: "NONFINITE", 6: "CUDA",
           7: "INTERNAL", 8: "NO_DEVICE"}
@@ -38,7 +39,7 @@ class Opts(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("nrhs_max", ctypes.c_int), ("alpha", ctypes.c_double),
                 ("beta", ctypes.c_double), ("apply_precision", ctypes.c_int), ("loop", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("coarse", ctypes.c_int), ("dirichlet", ctypes.c_int),
-                ("decomposition", ctypes.c_int)]
+                ("decomposition", ctypes.c_int), ("form", ctypes.c_int), ("coarse_its", ctypes.c_int)]
 
 
 _lib = None
@@ -77,6 +78,8 @@ _SIGS = {
     "riesz_profile_read": (_I, [_P, _P, _P]),
     "riesz_destroy": (_I, [_P]),
     "riesz_plan_bytes": (_I, [_P, _P, _P]),
+    "riesz_hybrid_weights": (_I, [_P, _P, _I]),
+    "riesz_apply_prec": (_I, [_P, _P, _P, _I, _I, _P]),
     "riesz_probe_fp64": (_I, [_I, _P, _P]),
     "riesz_hodge_setup": (_I, [_I, _I, _I64, _P, _I64, _P, ctypes.c_double, ctypes.POINTER(Opts), _P,
                                ctypes.POINTER(_P)]),
@@ -270,6 +273,12 @@ class Riesz:
         _check(self.lib.riesz_plan_bytes(self.h, _ptr(b), _ptr(na)))
         return int(b[0]), int(na[0])
 
+    def hybrid_weights(self, rho=None):
+        """The hybrid form's weights (rho_1, rho_2, rho_3); with rho given, set them (kept from then on)."""
+        out = np.zeros(3) if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+        _check(self.lib.riesz_hybrid_weights(self.h, _ptr(out), 0 if rho is None else 1))
+        return out
+
     def dirichlet_map(self):
         """Flags (uint8, [N]) of the DOFs fixed by the Dirichlet condition."""
         out = np.zeros(self.N, dtype=np.uint8)
@@ -277,10 +286,10 @@ class Riesz:
         return out
 
     def tuning(self):
-        out = np.zeros(4, dtype=np.int32)
+        out = np.zeros(5, dtype=np.int32)
         _check(self.lib.riesz_tuning(self.h, _ptr(out)))
         return {"cholesky_ctas_per_sm": int(out[0]), "candidates_timed": int(out[1]), "coarse_dofs": int(out[2]),
-                "cholesky_ctas_per_patch": int(out[3])}
+                "cholesky_ctas_per_patch": int(out[3]), "coarse_mode": int(out[4])}
 
     # ----- device calls -----
     def setup_device(self, stream=None):
@@ -288,6 +297,11 @@ class Riesz:
 
     def apply(self, x, y, nrhs=1, stream=None):
         _check(self.lib.riesz_apply(self.h, _ptr(x), _ptr(y), nrhs, _stream(stream)))
+        return y
+
+    def apply_prec(self, x, y, prec, nrhs=1, stream=None):
+        """y = A x in the inner-product precision prec (PREC_FP64, PREC_FP32, PREC_BF16X3)."""
+        _check(self.lib.riesz_apply_prec(self.h, _ptr(x), _ptr(y), nrhs, prec, _stream(stream)))
         return y
 
     def apply_noalloc(self, x, y, stream=None):

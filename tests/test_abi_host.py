@@ -118,13 +118,30 @@ def test_device_calls_fail_loudly_without_device_state(lib):
 
 def test_option_validation(lib):
     v, c = kuhn_mesh(1)
-    for kw in [dict(loop=2), dict(loop=-1), dict(autotune=3), dict(coarse=2), dict(apply_precision=3), dict(alpha=0.0), dict(beta=-1.0),
-               dict(nrhs_max=0), dict(rtol=0.0)]:
+    for kw in [dict(loop=2), dict(loop=-1), dict(autotune=3), dict(apply_precision=3), dict(alpha=0.0), dict(beta=-1.0),
+               dict(nrhs_max=0), dict(rtol=0.0), dict(coarse=3), dict(form=2), dict(coarse_its=0),
+               dict(coarse_its=1001)]:
         with pytest.raises(rz.RieszError) as e:
             rz.Riesz("CG", 2, v, c, device=False, **kw)
         assert e.value.code == 1, kw
     o = rz.default_opts()
     assert o.loop == rz.LOOP_GRAPH and o.apply_precision == rz.PREC_FP64
+    assert o.form == rz.FORM_ADDITIVE and o.coarse_its == 4
+
+
+def test_planned_bytes_count_the_options(lib):
+    """riesz_plan_bytes (host-only) grows by the buffers each option adds: a second right-hand side adds
+    its Krylov vectors, the hybrid form its three sweep vectors, the sparse coarse route its CSR."""
+    v, c = kuhn_mesh(3, 0.1, 1)
+    base, na = rz.Riesz("RT", 3, v, c, device=False).plan_bytes()
+    assert base > 0 and na > 20
+    N = rz.Riesz("RT", 3, v, c, device=False).N
+    hyb, _ = rz.Riesz("RT", 3, v, c, device=False, form=rz.FORM_HYBRID).plan_bytes()
+    assert hyb - base == 3 * 8 * N
+    two, _ = rz.Riesz("RT", 3, v, c, device=False, nrhs_max=2).plan_bytes()
+    assert two - base >= 8 * 8 * N
+    sp, _ = rz.Riesz("RT", 3, v, c, device=False, coarse=2).plan_bytes()
+    assert sp != base
 
 
 def test_batch_without_device_state(lib):

@@ -529,3 +529,44 @@ def test_hybrid_preconditioner_iterations():
     it_add = asm.pcg(A, b, asm.TwoLevelPreconditioner(A, md).apply)[1]
     it_hyb = asm.pcg(A, b, asm.HybridPreconditioner(A, md).apply)[1]
     assert it_hyb <= 15 and 2 * it_hyb <= it_add
+
+
+@pytest.mark.parametrize("space,p,ht", [("CG", 2, False), ("CG", 4, False), ("RT", 2, False), ("N1curl", 2, True),
+                                        ("N1curl", 3, True)])
+def test_hybrid_sweep_equals_error_propagation_product(space, p, ht):
+    """The residual-update sweep of HybridPreconditioner equals the closed form of a multiplicative
+    Schwarz method (Section 7.1, Eq. (7.2)): P^{-1} = (I - E) A^{-1} with the error propagation
+    E = (I - T_1)(I - T_2)(I - T_3)(I - T_2)(I - T_1), T_m = rho_m^{-1} B_m A and B_m the subspace solver
+    extended by zero (X_1: interior point-Jacobi; X_2: the interface solver on interface residuals,
+    interface output only, also for the Hiptmair-Toselli splitting; X_3: the exact W^k solve)."""
+    v, c = kuhn_mesh(2, 0.1, 1)
+    ref = reference_element(space, p)
+    md = MeshDofs(v, c, ref)
+    A = asm.assemble(md, asm.element_matrices(ref, v, c)).tocsr()
+    iface = None
+    if ht:
+        mc = MeshDofs(v, c, reference_element("CG", p))
+        iface = asm.HTPreconditioner(A, md, mc, weight=0.0)
+    H = asm.HybridPreconditioner(A, md, interface=iface)
+    N = A.shape[0]
+    nI = md.n_interface
+    Ad = A.toarray()
+    I = np.eye(N)
+    B1 = np.zeros((N, N))
+    B1[nI:, nI:] = np.diag(1.0 / np.diag(Ad)[nI:])
+    solver = asm.Preconditioner(A, md) if iface is None else iface
+    B2 = np.zeros((N, N))
+    for j in range(nI):
+        e = np.zeros(N)
+        e[j] = 1.0
+        B2[:nI, j] = solver.apply(e)[:nI]
+    W = asm.coarse_dofs(md)
+    B3 = np.zeros((N, N))
+    B3[np.ix_(W, W)] = np.linalg.inv(Ad[np.ix_(W, W)])
+    T = {m: B @ Ad / H.rho[m] for m, B in ((1, B1), (2, B2), (3, B3)) if m in H.rho}
+    assert H.sweep == [m for m in [1, 2, 3, 2, 1] if m in T]  # X_1 only where there are interior DOFs
+    E = I
+    for m in H.sweep:
+        E = (I - T[m]) @ E
+    P = (I - E) @ np.linalg.inv(Ad)
+    assert np.abs(H.dense() - P).max() <= 1e-9 * np.abs(P).max()
