@@ -45,6 +45,9 @@ WORKLOADS = {
     "hdiv_rt8_n4": dict(space="RT", p=8, n=4, amp=0.1, prec=1, nrhs=8, a32=1,
                         label="H(div) RT_8 on 4^3 x 6 tets, perturbed 0.1h, 8 RHS, FP32 inner products and patch "
                               "solves (small case for kernel profiles)"),
+    "hdiv_rt8_n8": dict(space="RT", p=8, n=8, amp=0.1, prec=1, nrhs=8, a32=1,
+                        label="H(div) RT_8 on 8^3 x 6 tets, perturbed 0.1h, 8 RHS, FP32 inner products and patch "
+                              "solves (medium case for kernel profiles)"),
     "hgrad_cg3_n4": dict(space="CG", p=3, n=4, amp=0.0, prec=0, nrhs=1,
                          label="H(grad) CG_3 on 4^3 x 6 tets, FP64"),
     "hdiv_rt8_n16": dict(space="RT", p=8, n=16, amp=0.1, prec=1, nrhs=8, a32=1, plain_steps=3,
@@ -79,7 +82,7 @@ def parse():
                          "FP32 element matrices, or the BF16x3 tensor-core matrix-free contraction")
     ap.add_argument("--serve", action="store_true",
                     help="serving run: Poisson stream of mixed solves, reports DOFs/s and p50/p99 latency")
-    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--batch", action="store_true",
                     help="batched run: seeded mixed systems solved in one graph launch per HBM wave")
     ap.add_argument("--systems", type=int, default=64)
@@ -368,28 +371,44 @@ def patch_flops_bytes(s):
 
 
 def run_serving(args):
-    """Poisson arrivals (mean 200 requests/s, seeded) of Riesz-map solves mixing CG, Ned1 and RT
-    with p in 3..6 and Kuhn meshes of 4..8 cubes per edge (384..3072 tets), perturbed by 0.1h,
-    admitted by a 150 GB HBM budget with up to 8 requests in flight."""
+    """Poisson arrivals (mean 200 requests/s, seeded) of Riesz-map solves mixing CG, Ned1 and RT with p in
+    3..10 and Kuhn meshes of 4..20 cubes per edge (384..48 000 tets), perturbed by 0.1h, admitted by a 150 GB
+    HBM budget with up to 8 requests in flight, each solved with the paper's decomposition for its space
+    (vertex stars, Hiptmair-Toselli, edge stars) and W^k.  The mixed server (FP32 patch sweeps and FP32
+    products) and the plain FP64 server serve the same stream one after the other."""
+    import numpy as np
     import torch
+    from paper_2506_17406_gb300 import riesz as rz
     from paper_2506_17406_gb300 import serve
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    warm = serve.poisson_stream(6, rate=200.0, seed=100, degrees=(3, 4, 5, 6), sizes=(4,))
-    serve.Server(max_slots=8).run(warm, realtime=False)  # builds and caches the reference elements
-    reqs = serve.poisson_stream(args.requests, rate=200.0, seed=7, degrees=(3, 4, 5, 6), sizes=(4, 5, 6, 8))
+    degrees, sizes = tuple(range(3, 11)), tuple(range(4, 21))
+    warm = serve.poisson_stream(6, rate=200.0, seed=100, degrees=(3, 4), sizes=(4,))
+    serve.Server(max_slots=8, recommended=True).run(warm, realtime=False)
+    out = {"metric": "serving: DOFs/s and p50/p99 latency of solves to 1e-8", "unit": "DOFs/s", "n_gpus": 1,
+           "higher_is_better": True, "data": "synthetic",
+           "config": {"workload": "Poisson stream, mean 200 req/s, CG/Ned1/RT, p 3..10, 4..20 cubes per edge "
+                                  "(384..48000 tets), perturbed 0.1h, 150 GB budget, 8 slots, recommended "
+                                  "decompositions + W^k", "requests": args.requests}}
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    srv = serve.Server(hbm_budget_bytes=150 << 30, max_slots=8)
-    done = srv.run(reqs, realtime=True)
-    clk = clocks.stop()
-    st = serve.summary(done, srv.wall)
-    out = {"metric": "serving: DOFs/s and p50/p99 latency of solves to 1e-8", "value": st["dofs_per_s"],
-           "unit": "DOFs/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-           "config": {"workload": "Poisson stream, mean 200 req/s, CG/Ned1/RT, p 3..6, 4..8 cubes per edge, "
-                                  "perturbed 0.1h, 150 GB budget, 8 slots", "requests": args.requests},
-           "latency_p50_s": st["latency_p50_s"], "latency_p99_s": st["latency_p99_s"],
-           "queue_p50_s": st["queue_p50_s"], "completed": st["completed"], "wall_s": st["wall_s"],
-           "max_relres": max(r.relres for r in done if r.status == 0), "clocks": clk}
+    for name, kw in (("mixed", dict(precond_precision=rz.PREC_FP32, apply_precision=rz.PREC_FP32)),
+                     ("fp64_plain", dict(precond_precision=rz.PREC_FP64, apply_precision=rz.PREC_FP64))):
+        reqs = serve.poisson_stream(args.requests, rate=200.0, seed=7, degrees=degrees, sizes=sizes)
+        srv = serve.Server(hbm_budget_bytes=150 << 30, max_slots=8, recommended=True, **kw)
+        done = srv.run(reqs, realtime=True)
+        st = serve.summary(done, srv.wall)
+        ok = [r for r in done if r.status == 0]
+        res = {"value": st["dofs_per_s"], "latency_p50_s": st["latency_p50_s"],
+               "latency_p99_s": st["latency_p99_s"], "queue_p50_s": st["queue_p50_s"], "completed": st["completed"],
+               "wall_s": st["wall_s"], "max_relres": max(r.relres for r in ok) if ok else None,
+               "dofs_total": int(sum(r.N for r in ok)),
+               "largest_request": max(((r.space, r.p, r.n, r.N) for r in ok), key=lambda t: t[3]) if ok else None}
+        if name == "mixed":
+            out.update(res)
+        else:
+            out["fp64_plain"] = res
+    out["clocks"] = clocks.stop()
+    out["speedup_vs_fp64_plain"] = out["value"] / out["fp64_plain"]["value"] if out["fp64_plain"]["value"] else None
     print(json.dumps(out), flush=True)
 
 
@@ -549,8 +568,9 @@ def run_hodge(args):
     k, p, n, gamma = args.hodge, args.hodge_p, args.hodge_n, args.gamma
     verts, cells = fichera_mesh(n, 0.1, 1)
     prec = rz.PREC_FP32 if args.precision == "mixed" else rz.PREC_FP64
+    form = args.form or "additive"
     h = rz.Hodge(k, p, verts, cells, gamma, decomposition=rz.DECOMP_HT, precond_precision=prec,
-                 rtol=1e-8, maxit=5000)
+                 rtol=1e-8, maxit=5000, form=FORMS[form])
     stream = torch.cuda.current_stream()
     fcg_h = np.zeros((3 if k < 3 else 1, h.n_cg))
     fcg_h[:, :len(verts)] = 1.0  # f = (1,1,1) (f = 1 for k = 3): the vertex (Whitney) functions sum to one
@@ -630,7 +650,7 @@ def run_hodge(args):
         t1 = time.perf_counter()
         hs = ohodge.HodgeSystem(k, p, vs, cs, gamma)
         bs = hs.rhs(np.ones(hs.n1))
-        _, ito, _ = ohodge.minres(hs.A, bs, hs.schwarz_preconditioner(True), rtol=1e-8, maxit=5000)
+        _, ito, _ = ohodge.minres(hs.A, bs, hs.schwarz_preconditioner(True, form=form), rtol=1e-8, maxit=5000)
         dt = time.perf_counter() - t1
         cb = {"value": (hs.n0 + hs.n1) / dt, "unit": "DOFs/s", "cores": os.cpu_count(), "kind": "oracle",
               "sample": "same k, p, gamma on the 2^3-cube Fichera mesh (N=%d): assembly, Schwarz blocks and "
@@ -647,7 +667,7 @@ def run_hodge(args):
                                         "of its Schwarz preconditioner (CG: vertex stars, Ned1: Hiptmair-Toselli, "
                                         "DG: exact diagonal, "
                                         "RT: edge stars; W^k with FP64 coarse inverse)",
-                      "sweeps": "fp32" if prec == rz.PREC_FP32 else "fp64",
+                      "sweeps": "fp32" if prec == rz.PREC_FP32 else "fp64", "form": form,
                       "step": "device setup of all blocks + load + MINRES", "l2": "element matrices and patch "
                                                                                "factors larger than L2"},
            "iterations": float(np.median(iters[-args.steps:])), "max_relres": max(rels[-args.steps:]),

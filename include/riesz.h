@@ -153,9 +153,10 @@ typedef struct {
      whatever the size. */
   int coarse;
   /* 0 (default): pure Neumann (the paper's benchmarks).  1: homogeneous
-     Dirichlet conditions on the whole boundary (X_{p,D} of Eq. (2.8) with
-     Gamma_D the boundary): every DOF of a boundary vertex, edge or face is
-     fixed (riesz_dirichlet_map lists them).  The system becomes
+     Dirichlet conditions on Gamma_D (X_{p,D} of Eq. (2.8); Gamma_D the whole
+     boundary, or the part chosen by dirichlet_vertices): every DOF of a
+     vertex, edge or face of Gamma_D is fixed (riesz_dirichlet_map lists
+     them).  The system becomes
      [A_ff 0; 0 I]: riesz_apply gives y_f = A_ff x_f, y_d = x_d;
      riesz_precond gives z_d = r_d and leaves the fixed DOFs out of every
      patch and of W^k; riesz_load writes b_d = 0; a solve returns x_d = b_d. */
@@ -193,6 +194,12 @@ typedef struct {
   /* PCG steps of the lowest-order coarse route (see coarse; 1..1000,
      default 4). */
   int coarse_its;
+  /* With dirichlet = 1: NULL (default) fixes the whole boundary; otherwise
+     a host array of one flag per mesh vertex, and Gamma_D of Eq. (2.8) is
+     the boundary faces whose three vertices are all flagged (a part of the
+     boundary with its closure: those faces, their edges and vertices carry
+     the fixed DOFs).  Read during riesz_create only. */
+  const uint8_t* dirichlet_vertices;
 } riesz_opts;
 
 /* Fill *o with the defaults: FP64 preconditioner, element-matrix apply,
@@ -466,7 +473,10 @@ const char* riesz_last_error(void);
    Section 7.2 (vertex stars for CG_p, Hiptmair-Toselli for Ned1_p, edge
    stars for RT_p).  opts->precond_precision, coarse, autotune, rtol and
    maxit apply; alpha, beta, nrhs_max, loop, apply_mode and apply_precision
-   are set internally; dirichlet must be 0.  gamma > 0.  For k = 3 the DG
+   are set internally; dirichlet must be 0.  opts->form = RIESZ_FORM_HYBRID
+   makes every Riesz block the paper's multiplicative hybrid (Section 7.1)
+   instead of the additive sum (a fixed symmetric positive definite
+   operator with FP64 sweeps, as MINRES needs).  gamma > 0.  For k = 3 the DG
    block gamma^{-1} M_DG is diagonal (the DG basis is L2-orthogonal) and is
    inverted exactly.
    Setup builds both blocks' maps on the host and runs the device setup on

@@ -198,11 +198,16 @@ def coarse_matrix(ref, md, alpha=1.0, beta=1.0):
     return scipy.sparse.coo_matrix((Ae.ravel(), (rows, cols)), shape=(len(W), len(W))).tocsr()
 
 
-def dirichlet_dofs(md):
-    """DOFs fixed by a homogeneous Dirichlet condition on the whole boundary (X_{p,D} of Eq. (2.8)):
-    every DOF of a vertex, edge or face of a boundary face (a face of exactly one cell)."""
+def dirichlet_dofs(md, vertex_mask=None):
+    """DOFs fixed by a homogeneous Dirichlet condition (X_{p,D} of Eq. (2.8)): every DOF of a vertex, edge
+    or face of a face of Gamma_D.  Gamma_D is the whole boundary (the faces of exactly one cell), or, with
+    vertex_mask (one flag per mesh vertex), the boundary faces whose three vertices are all flagged: a part
+    of the boundary together with its closure."""
     _, cnt = np.unique(md.cell_faces.ravel(), return_counts=True)
     bfaces = np.nonzero(cnt == 1)[0]
+    if vertex_mask is not None:
+        vm = np.asarray(vertex_mask).astype(bool)
+        bfaces = bfaces[np.all(vm[md.faces[bfaces]], axis=1)]
     nv_d, ne_d, nf_d, _ = md.per_entity
     off_v, off_e, off_f = md._offsets
     tri = md.faces[bfaces]

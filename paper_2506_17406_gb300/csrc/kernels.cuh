@@ -1236,6 +1236,124 @@ __global__ void __launch_bounds__(NT) k_patch_solve_multi(
   }
 }
 
+// Small patches (at most SMALL_NB tiles of 32 DOFs, e.g. the vertex stars of the lowest-order spaces):
+// one warp per patch, lane = row inside a tile, nr <= 8 right-hand sides in a per-warp shared-memory
+// vector, no CTA-wide barrier.  Same tile storage and the same two sweeps as k_patch_solve_multi:
+// forward y_I = Dinv_I (b_I - sum_{J<I} L_IJ y_J), backward x_I = Dinv_I^T (y_I - sum_{J>I} L_JI^T x_J).
+constexpr int SMALL_NB = 2;
+constexpr int SMALL_WARPS = 4;
+// per-warp shared memory: a staged tile (rows padded to 33) and the patch vectors
+template <typename T>
+__host__ __device__ constexpr size_t small_warp_smem() {
+  return sizeof(T) * (32 * 33 + 8 * SMALL_NB * 32 + 8 * 32);
+}
+// a 32x32 tile into shared memory with coalesced loads (row r, column lane), rows padded to 33
+template <typename T>
+__device__ __forceinline__ void small_stage(T (*ts)[33], const T* __restrict__ tile, int lane) {
+#pragma unroll 8
+  for (int r = 0; r < 32; ++r) ts[r][lane] = tile[r * 32 + lane];
+  __syncwarp();
+}
+template <typename T>
+__global__ void __launch_bounds__(SMALL_WARPS * 32) k_patch_solve_small(
+    int npatch, const int32_t* __restrict__ pn, const int64_t* __restrict__ pdoff, const int64_t* __restrict__ pfoff,
+    const int64_t* __restrict__ pdoff_inv, const int64_t* __restrict__ pmoff, const int32_t* __restrict__ meta,
+    const int32_t* __restrict__ pdofs, const T* __restrict__ Lall, const T* __restrict__ Dall,
+    const double* __restrict__ r, double* __restrict__ zpatch, int64_t N, int64_t zstride, int nr) {
+  constexpr int RM = 8;
+  extern __shared__ __align__(16) unsigned char small_sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* base = reinterpret_cast<T*>(small_sm + warp * small_warp_smem<T>());
+  T (*ts)[33] = reinterpret_cast<T (*)[33]>(base);
+  T (*y)[SMALL_NB * 32] = reinterpret_cast<T (*)[SMALL_NB * 32]>(base + 32 * 33);
+  T (*t)[32] = reinterpret_cast<T (*)[32]>(base + 32 * 33 + 8 * SMALL_NB * 32);
+  const int P = blockIdx.x * SMALL_WARPS + warp;
+  if (P >= npatch) return;
+  const int n = pn[P];
+  const int nb = (n + 31) / 32;
+  const int32_t* tix = meta + pmoff[P];
+  const T* L = Lall + pfoff[P];
+  const T* Dv = Dall + pdoff_inv[P];
+  const int32_t* dofs = pdofs + pdoff[P];
+  for (int i = lane; i < nb * 32; i += 32) {
+    const int d = i < n ? dofs[i] : -1;
+    for (int k = 0; k < nr; ++k) y[k][i] = d >= 0 ? (T)r[k * N + d] : (T)0;
+  }
+  __syncwarp();
+  for (int I = 0; I < nb; ++I) {  // forward: row access of staged tiles
+    T acc[RM];
+#pragma unroll
+    for (int k = 0; k < RM; ++k) acc[k] = (T)0;
+    for (int J = 0; J < I; ++J) {
+      const int ti = tix[I * nb + J];
+      if (ti < 0) continue;
+      small_stage(ts, L + (int64_t)ti * 1024, lane);
+#pragma unroll 4
+      for (int c = 0; c < 32; ++c) {
+        const T a = ts[lane][c];
+#pragma unroll
+        for (int k = 0; k < RM; ++k)
+          if (k < nr) acc[k] += a * y[k][J * 32 + c];
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int k = 0; k < RM; ++k)
+      if (k < nr) t[k][lane] = y[k][I * 32 + lane] - acc[k];
+    small_stage(ts, Dv + I * 1024, lane);
+#pragma unroll
+    for (int k = 0; k < RM; ++k) acc[k] = (T)0;
+#pragma unroll 4
+    for (int c = 0; c < 32; ++c) {
+      const T a = ts[lane][c];
+#pragma unroll
+      for (int k = 0; k < RM; ++k)
+        if (k < nr) acc[k] += a * t[k][c];
+    }
+#pragma unroll
+    for (int k = 0; k < RM; ++k)
+      if (k < nr) y[k][I * 32 + lane] = acc[k];
+    __syncwarp();
+  }
+  for (int I = nb - 1; I >= 0; --I) {  // backward: column access, coalesced from global memory
+    T acc[RM];
+#pragma unroll
+    for (int k = 0; k < RM; ++k) acc[k] = (T)0;
+    for (int J = I + 1; J < nb; ++J) {
+      const int ti = tix[J * nb + I];
+      if (ti < 0) continue;
+      const T* tile = L + (int64_t)ti * 1024;
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr) {
+        const T a = tile[rr * 32 + lane];
+#pragma unroll
+        for (int k = 0; k < RM; ++k)
+          if (k < nr) acc[k] += a * y[k][J * 32 + rr];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < RM; ++k)
+      if (k < nr) t[k][lane] = y[k][I * 32 + lane] - acc[k];
+    __syncwarp();
+    const T* dt = Dv + I * 1024;
+#pragma unroll
+    for (int k = 0; k < RM; ++k) acc[k] = (T)0;
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr) {
+      const T a = dt[rr * 32 + lane];
+#pragma unroll
+      for (int k = 0; k < RM; ++k)
+        if (k < nr) acc[k] += a * t[k][rr];
+    }
+#pragma unroll
+    for (int k = 0; k < RM; ++k)
+      if (k < nr) y[k][I * 32 + lane] = acc[k];
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32)
+    for (int k = 0; k < nr; ++k) zpatch[k * zstride + pdoff[P] + i] = (double)y[k][i];
+}
+
 // z = diag(A_II)^{-1} r on the interior, sum of patch results on the interface.
 __global__ void k_precond_gather(int64_t N, int64_t nifd, const int64_t* __restrict__ ptr,
                                  const int32_t* __restrict__ pos, const double* __restrict__ zpatch, int64_t zstride,
@@ -2044,8 +2162,10 @@ __global__ void k_update_p(int64_t n, double* __restrict__ scal, const double* _
 // the last true residual), 4 iteration limit.  The loop body runs again only
 // for reason 0, and ctl[0] grows by one per pass, so the loop ends after at
 // most ctl[1] passes whatever the scalars hold.
+// reliable: replace the recursive residual once a right-hand side's (r, r) has fallen by this factor
+// since the last true residual (0: never).
 __global__ void k_pcg_control(cudaGraphConditionalHandle cond, const double* __restrict__ scal, int nrhs,
-                              double rtol2, int reliable, int* __restrict__ ctl) {
+                              double rtol2, double reliable, int* __restrict__ ctl) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int it = ctl[0] + 1;
   ctl[0] = it;
@@ -2056,7 +2176,7 @@ __global__ void k_pcg_control(cudaGraphConditionalHandle cond, const double* __r
     if (sk[S_NONFINITE] != 0.0 || !isfinite(rr)) nonfinite = true;
     const bool below = rr <= tol2;
     if (!below) all = false;
-    if (reliable && !below && rr <= 1e-8 * sk[S_RRLAST]) replace = true;
+    if (reliable > 0.0 && !below && rr <= reliable * sk[S_RRLAST]) replace = true;
   }
   const int reason = nonfinite ? 1 : all ? 2 : replace ? 3 : (it >= ctl[1]) ? 4 : 0;
   ctl[2] = reason;

@@ -648,9 +648,11 @@ void plan_dirichlet(riesz_handle& h) {
     const int nd = M.per_entity[k];
     for (int m = 0; m < nd; ++m) h.dir_mask[M.off[k] + (int64_t)nd * ent + m] = 1;
   };
+  const uint8_t* vm = h.opts.dirichlet_vertices;  // Gamma_D: the boundary faces with all three vertices flagged
   for (int64_t f = 0; f < M.nfaces; ++f) {
     if (cnt[f] != 1) continue;
     const int32_t* v = &M.faces[f * 3];
+    if (vm && !(vm[v[0]] && vm[v[1]] && vm[v[2]])) continue;
     mark(2, f);
     for (int a = 0; a < 3; ++a) mark(0, v[a]);
     mark(1, edge_index(M, v[0], v[1]));
@@ -874,9 +876,15 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
     dim3 grid((unsigned)((C + cells - 1) / cells), (unsigned)((nrhs + RT - 1) / RT));
     launch(h, RIESZ_K_APPLY_TC, s, [&] {
       const int ns = dev::tc_stages(h.tc_np);
-      dev::k_apply_tc<<<grid, dev::TC_NT, dev::tc_smem_bytes(h.tc_np, ns), s>>>(
-          C, n, h.nif, h.ref->Q, h.tc_np, h.tc_kc, RT, ns, h.d_Btc.p, h.d_g.p, h.d_cdofs.p, x, y, h.d_Ycell.p, nrhs, N,
-          h.dmask(), h.d_flags.p + 2);
+      const size_t sm = dev::tc_smem_bytes(h.tc_np, ns);
+      if (h.ref->Q == 12)
+        dev::k_apply_tc<12><<<grid, dev::TC_NT, sm, s>>>(C, n, h.nif, h.tc_np, h.tc_kc, RT, ns, h.d_Btc.p, h.d_g.p,
+                                                         h.d_cdofs.p, x, y, h.d_Ycell.p, nrhs, N, h.dmask(),
+                                                         h.d_flags.p + 2);
+      else
+        dev::k_apply_tc<7><<<grid, dev::TC_NT, sm, s>>>(C, n, h.nif, h.tc_np, h.tc_kc, RT, ns, h.d_Btc.p, h.d_g.p,
+                                                        h.d_cdofs.p, x, y, h.d_Ycell.p, nrhs, N, h.dmask(),
+                                                        h.d_flags.p + 2);
     });
   } else if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     const int rows = (n % 2 == 0) ? n / 2 : n;
@@ -935,6 +943,25 @@ void op_patch_solves(riesz_handle& h, const double* r, int nrhs, cudaStream_t s)
   const int nbmax = (h.p_n[0] + 31) / 32;
   const int64_t zstride = (int64_t)h.p_dofs.size();
   const bool f32 = h.opts.precond_precision == RIESZ_PREC_FP32;
+  if (nbmax <= dev::SMALL_NB) {  // small patches: one warp per patch
+    const unsigned grid = (unsigned)((npatch + dev::SMALL_WARPS - 1) / dev::SMALL_WARPS);
+    for (int r0 = 0; r0 < nrhs; r0 += 8) {
+      const int nr = std::min(8, nrhs - r0);
+      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
+        if (f32)
+          dev::k_patch_solve_small<float><<<grid, dev::SMALL_WARPS * 32,
+                                            dev::SMALL_WARPS * dev::small_warp_smem<float>(), s>>>(
+              npatch, h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p,
+              h.d_L32.p, h.d_D32.p, r + (int64_t)r0 * N, h.d_zpatch.p + (int64_t)r0 * zstride, N, zstride, nr);
+        else
+          dev::k_patch_solve_small<double><<<grid, dev::SMALL_WARPS * 32,
+                                             dev::SMALL_WARPS * dev::small_warp_smem<double>(), s>>>(
+              npatch, h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p,
+              h.d_L64.p, h.d_D64.p, r + (int64_t)r0 * N, h.d_zpatch.p + (int64_t)r0 * zstride, N, zstride, nr);
+      });
+    }
+    return;
+  }
   if (nrhs == 1) {  // factor tiles streamed through shared memory by bulk copies
     if (f32)
       launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
@@ -1209,6 +1236,13 @@ int inner_prec(const riesz_handle& h) {
   return RIESZ_PREC_FP64;
 }
 bool use_a32(const riesz_handle& h) { return inner_prec(h) != RIESZ_PREC_FP64; }
+// Residual replacement (reliable updates) once (r, r) has fallen by this factor since the last true
+// residual: four digits of the residual norm with FP32 products, two with BF16x3 products (their
+// ~1e-5 relative error would otherwise build up a larger gap between the recursive and true residuals).
+double reliable_gain(const riesz_handle& h) {
+  const int ip = inner_prec(h);
+  return ip == RIESZ_PREC_FP64 ? 0.0 : (ip == RIESZ_PREC_BF16X3 ? 1e-4 : 1e-8);
+}
 // Precision of the residual updates inside the hybrid sweep.
 int sweep_prec(const riesz_handle& h) {
   if (h.opts.apply_precision == RIESZ_PREC_BF16X3) return RIESZ_PREC_BF16X3;
@@ -1416,7 +1450,7 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
       } else if (a32) {  // reliable update: four more digits on some right-hand side
         for (int k = 0; k < nrhs; ++k) {
           const double rrk = h.h_scal[k * SS + dev::S_RR];
-          if (rrk > tol2[k] && rrk <= 1e-8 * rr_last[k]) replace = true;
+          if (rrk > tol2[k] && rrk <= reliable_gain(h) * rr_last[k]) replace = true;
         }
         if (replace) {
           residual();
@@ -1497,7 +1531,7 @@ std::pair<int64_t, int64_t> add_loop(riesz_handle& h, cudaGraph_t G, int nrhs, b
   cudaGraphConditionalHandle hc;
   CK(cudaGraphConditionalHandleCreate(&hc, G, entry ? 0u : 1u, cudaGraphCondAssignDefault));
   const double rtol2 = h.opts.rtol * h.opts.rtol;
-  const int reliable = use_a32(h) ? 1 : 0;
+  const double reliable = reliable_gain(h);
   auto control = [&] {
     launch(h, RIESZ_K_SCALAR, cs, [&] {
       dev::k_pcg_control<<<1, 32, 0, cs>>>(hc, h.d_scal.p, nrhs, rtol2, reliable, h.d_ctl.p);
@@ -2247,6 +2281,8 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     raise_smem_limit(dev::k_patch_solve_multi<double>, (size_t)smm);
     const int nbm = h.p_n.empty() ? 1 : (h.p_n[0] + 31) / 32;
     raise_smem_limit(dev::k_patch_sweep8<SWEEP_SLOTS_F32>, sweep8_smem(nbm));
+    raise_smem_limit(dev::k_patch_solve_small<double>, dev::SMALL_WARPS * dev::small_warp_smem<double>());
+    raise_smem_limit(dev::k_patch_solve_small<float>, dev::SMALL_WARPS * dev::small_warp_smem<float>());
   }
   h.d_pdioff.upload(h.p_dioff, s);
   h.d_pmoff.upload(h.p_moff, s);
@@ -2336,7 +2372,13 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     std::vector<uint16_t> t;
     build_tc_table(h, t);
     h.d_Btc.upload(t, s);
-    raise_smem_limit(dev::k_apply_tc, dev::tc_smem_bytes(h.tc_np, dev::tc_stages(h.tc_np)));
+    if (h.ref->Q != 7 && h.ref->Q != 12) throw Err(RIESZ_ERR_INTERNAL, "tensor-core products: Q must be 7 or 12");
+    for (int c = 0; c < C; ++c)  // interior DOFs of a cell are contiguous (the kernel writes them from the first)
+      for (int t = h.nif + 1; t < n; ++t)
+        if (M.cell_dofs[(size_t)c * n + t] != M.cell_dofs[(size_t)c * n + h.nif] + (t - h.nif))
+          throw Err(RIESZ_ERR_INTERNAL, "interior DOFs of a cell are not contiguous");
+    raise_smem_limit(dev::k_apply_tc<7>, dev::tc_smem_bytes(h.tc_np, dev::tc_stages(h.tc_np)));
+    raise_smem_limit(dev::k_apply_tc<12>, dev::tc_smem_bytes(h.tc_np, dev::tc_stages(h.tc_np)));
   }
   h.d_ticket.alloc(nrhs);
   CK(cudaMemsetAsync(h.d_ticket.p, 0, sizeof(unsigned) * nrhs, s));
@@ -2507,6 +2549,7 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
   need(h->opts.autotune >= 0 && h->opts.autotune <= 2, "bad autotune");
   need(h->opts.coarse >= 0 && h->opts.coarse <= 2, "bad coarse");
   need(h->opts.coarse_its >= 1 && h->opts.coarse_its <= 1000, "coarse_its must be in 1..1000");
+  need(!h->opts.dirichlet_vertices || h->opts.dirichlet, "dirichlet_vertices needs dirichlet = 1");
   need(h->opts.form == RIESZ_FORM_ADDITIVE || h->opts.form == RIESZ_FORM_HYBRID, "bad form");
   need(h->opts.dirichlet == 0 || h->opts.dirichlet == 1, "bad dirichlet");
   need(h->opts.decomposition >= RIESZ_DECOMP_VERTEX_STAR && h->opts.decomposition <= RIESZ_DECOMP_EDGE_STAR,
@@ -2558,6 +2601,7 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
     ao.apply_mode = RIESZ_APPLY_ELEMENT;
     h->aux = create_handle(RIESZ_H1, p, nverts, verts, ncells, cells, ao, true);
   }
+  h->opts.dirichlet_vertices = nullptr;  // the caller's array is read during creation only
   h->setup_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return h.release();
 }
@@ -2610,6 +2654,7 @@ void riesz_default_opts(riesz_opts* o) {
   o->decomposition = RIESZ_DECOMP_VERTEX_STAR;
   o->form = RIESZ_FORM_ADDITIVE;
   o->coarse_its = 4;
+  o->dirichlet_vertices = nullptr;
 }
 
 const char* riesz_last_error(void) { return g_err.c_str(); }
@@ -3272,9 +3317,9 @@ int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t
     H->P0 = create_handle(k - 1, p, nverts, verts, ncells, cells, o0, true);
     // MINRES needs a positive definite preconditioner: the W^k inverses of the blocks by the FP64
     // Cholesky route (A_0 = R_0 (M + gamma K) R_0^T and gamma^{-1} M + K reach kappa ~ 1e7 for gamma
-    // far from 1, where an explicit Gauss-Jordan inverse, even in FP64, is no longer definite)
-    // MINRES also needs a fixed (linear) preconditioner, which the sparse coarse CG is not: blocks whose
-    // W^k is above the dense limit stay one-level
+    // far from 1, where an explicit Gauss-Jordan inverse, even in FP64, is no longer definite).  It also
+    // needs a fixed (linear) preconditioner, which the few lowest-order PCG steps of the coarse route
+    // above the dense limit are not: such blocks stay one-level.
     auto dense_coarse_only = [](riesz_handle* P) {
       P->coarse64 = true;
       if (P->coarse_sparse) P->coarse_on = P->coarse_sparse = false;

@@ -18,11 +18,14 @@
 // by the four producer warps from the gathered X and g.  Ring of NSTAGE slots,
 // mbarriers with bounded waits.
 //
-// Warp roles (192 threads): warp 0 allocates tensor memory and issues the B
-// bulk copies (one lane); warps 1-4 gather X, build the A stages and run the
-// epilogue (warp w reads tensor-memory lanes 32 (w % 4) .. + 31, so row
-// m = 32 (w % 4) + lane); warp 5 (one lane) issues the MMAs and commits them
-// to the slot's "empty" barrier and, after the last stage, to "done".
+// Warp roles (320 threads): warp 0 allocates tensor memory and issues the B
+// bulk copies (one lane); warps 1-8 gather X, build the A stages and run the
+// epilogue: warp w serves row m = 32 (w % 4) + lane (tensor-memory lanes of
+// its quarter) and the K half (w - 1) / 4 of every stage (the two halves of a
+// row in different warps, two producer warps per scheduler); in the epilogue
+// the two warps of a quarter take alternate 16-column chunks.  Warp 9 (one
+// lane) issues the MMAs and commits them to the slot's "empty" barrier and,
+// after the last stage, to "done".
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -30,7 +33,8 @@
 namespace riesz {
 namespace dev {
 
-constexpr int TC_NT = 192;
+constexpr int TC_NT = 320;
+constexpr int TC_PRODUCERS = 256;  // threads of warps 1-8
 constexpr int TC_ROWS = 128;   // M of one MMA (cta_group::1)
 constexpr int TC_KC = 32;      // K per stage (BF16 elements)
 constexpr int TC_NSTAGE = 3;   // most ring slots (fewer when shared memory does not hold three)
@@ -89,17 +93,44 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// round-to-nearest-even BF16 of an FP32 value (finite inputs)
-__device__ __forceinline__ uint16_t tc_bf16(float f) {
-  const uint32_t u = __float_as_uint(f);
-  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+// Two FP32 values to packed BF16 (round to nearest even; a0 in the low half, a1 in the high half)
+__device__ __forceinline__ uint32_t tc_bf16x2(float a0, float a1) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(a1), "f"(a0));
+  return d;
 }
-__device__ __forceinline__ float tc_bf16_to_f32(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+// hi/lo split of a pair: hi = bf16(a), lo = bf16(a - hi) (the subtraction is exact in FP32)
+__device__ __forceinline__ void tc_split2(float a0, float a1, uint32_t& hi, uint32_t& lo) {
+  hi = tc_bf16x2(a0, a1);
+  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
+  lo = tc_bf16x2(a0 - h0, a1 - h1);
+}
+
+// X_c[j0 .. j0 + 15] of row (c, r) as FP32 (zero outside the cell's n DOFs, and at Dirichlet DOFs)
+constexpr int TC_KH = TC_KC / 2;  // K values of a stage per producer thread
+__device__ __forceinline__ void tc_load_x(float (&xf)[TC_KH], bool valid, int j0, int n, int nif, int64_t C,
+                                          int64_t c, int r, int64_t N, const int32_t* __restrict__ cdofs,
+                                          const double* __restrict__ x, const uint8_t* __restrict__ dmask) {
+#pragma unroll
+  for (int e = 0; e < TC_KH; ++e) {
+    const int j = j0 + e;
+    float v = 0.f;
+    if (valid && j < n) {
+      const int64_t dof = cdofs[(int64_t)j * C + c];
+      if (!(dmask && j < nif && dmask[dof])) v = (float)x[(int64_t)r * N + dof];
+    }
+    xf[e] = v;
+  }
+}
 
 // y = A x (interior rows) and Ycell (interface rows, scattered by k_gather_iface)
 // for tiles of CELLS = 128 / RT cells and RT right-hand sides: row m = r * CELLS + c.
 // Bst: the B stages [KC][Q][hi | lo][NP / 8][4][8][8] BF16 (see the file comment).
-__global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif, int Q, int NP, int KC, int RT, int NS,
+// The interior DOFs of a cell are numbered contiguously (cell-major), so row m writes its interior
+// outputs from the cell's first interior DOF on.  Q (the number of reference matrices) is a template
+// parameter so that the producers keep the Q factors of their cell in registers.
+template <int Q>
+__global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif, int NP, int KC, int RT, int NS,
                                                       const uint16_t* __restrict__ Bst, const double* __restrict__ g,
                                                       const int32_t* __restrict__ cdofs, const double* __restrict__ x,
                                                       double* __restrict__ y, double* __restrict__ Ycell, int nrhs,
@@ -110,7 +141,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
   unsigned char* sA = tc_sm;                           // [NS][abytes]
   unsigned char* sB = tc_sm + (size_t)NS * abytes;     // [NS][bbytes]
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)NS * bbytes);
-  uint64_t* full_a = bars;                   // [NS], 128 producer arrivals
+  uint64_t* full_a = bars;                   // [NS], 256 producer arrivals
   uint64_t* full_b = bars + TC_NSTAGE;       // [NS], expect_tx
   uint64_t* empty = bars + 2 * TC_NSTAGE;    // [NS], MMA commit
   uint64_t* done = bars + 3 * TC_NSTAGE;     // accumulator complete
@@ -128,7 +159,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < NS; ++s) {
-      mbar_init(&full_a[s], 128);
+      mbar_init(&full_a[s], TC_PRODUCERS);
       mbar_init(&full_b[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -163,27 +194,24 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
       // no copy may still be landing when the CTA exits (they have all landed in a complete run)
       for (int s = issued > NS ? issued - NS : 0; s < issued; ++s) mbar_wait(&full_b[s % NS], (s / NS) & 1, err);
     }
-  } else if (warp <= 4) {
-    // A producers: row m of the tile
-    const int m = 32 * (warp & 3) + lane;
+  } else if (warp <= 8) {
+    // A producers: row m of the tile, K half kh of each stage; the next chunk of X is gathered while
+    // this one is used
+    const int m = 32 * (warp & 3) + lane, kh = (warp - 1) >> 2;
     const int cl = m % CELLS, rl = m / CELLS;
     const int64_t c = c0 + cl;
     const int r = r0 + rl;
     const bool valid = c < C && r < nrhs;
-    const uint32_t rowoff = (uint32_t)(m >> 3) * 512u + (uint32_t)(m & 7) * 16u;
+    float gq[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) gq[q] = valid ? (float)g[q * C + c] : 0.f;
+    const uint32_t rowoff = (uint32_t)(m >> 3) * 512u + (uint32_t)(m & 7) * 16u + (uint32_t)kh * 256u;
+    float xf[TC_KH], xn[TC_KH];
+    tc_load_x(xf, valid, kh * TC_KH, n, nif, C, c, r, N, cdofs, x, dmask);
     bool ok = true;
     for (int jc = 0; jc < KC && ok; ++jc) {
-      float xf[TC_KC];
+      if (jc + 1 < KC) tc_load_x(xn, valid, (jc + 1) * TC_KC + kh * TC_KH, n, nif, C, c, r, N, cdofs, x, dmask);
 #pragma unroll
-      for (int e = 0; e < TC_KC; ++e) {
-        const int j = jc * TC_KC + e;
-        float v = 0.f;
-        if (valid && j < n) {
-          const int64_t dof = cdofs[(int64_t)j * C + c];
-          if (!(dmask && j < nif && dmask[dof])) v = (float)x[(int64_t)r * N + dof];
-        }
-        xf[e] = v;
-      }
       for (int q = 0; q < Q; ++q) {
         const int s = jc * Q + q, slot = s % NS, use = s / NS;
         if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1, err)) {
@@ -193,18 +221,13 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
         }
         unsigned char* hi = sA + (size_t)slot * abytes;
         unsigned char* lo = hi + abytes / 2;
-        const float gv = valid ? (float)g[q * C + c] : 0.f;
+        const float gv = gq[q];
 #pragma unroll
-        for (int kc = 0; kc < 4; ++kc) {
+        for (int kc = 0; kc < 2; ++kc) {  // the two core matrices of this K half
           uint32_t ph[4], pl[4];
 #pragma unroll
-          for (int e2 = 0; e2 < 4; ++e2) {
-            const float a0 = gv * xf[kc * 8 + 2 * e2], a1 = gv * xf[kc * 8 + 2 * e2 + 1];
-            const uint16_t h0 = tc_bf16(a0), h1 = tc_bf16(a1);
-            const uint16_t l0 = tc_bf16(a0 - tc_bf16_to_f32(h0)), l1 = tc_bf16(a1 - tc_bf16_to_f32(h1));
-            ph[e2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-            pl[e2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-          }
+          for (int e2 = 0; e2 < 4; ++e2)
+            tc_split2(gv * xf[kc * 8 + 2 * e2], gv * xf[kc * 8 + 2 * e2 + 1], ph[e2], pl[e2]);
           const uint32_t off = rowoff + (uint32_t)kc * 128u;
           *reinterpret_cast<uint4*>(hi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
           *reinterpret_cast<uint4*>(lo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
@@ -212,6 +235,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
         fence_async_smem();
         mbar_arrive(&full_a[slot]);
       }
+#pragma unroll
+      for (int e = 0; e < TC_KH; ++e) xf[e] = xn[e];
     }
   } else {
     // MMA issuer
@@ -255,8 +280,10 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
     }
   }
 
-  // epilogue: warps 1-4 read their lanes of the accumulator
-  if (warp >= 1 && warp <= 4) {
+  // epilogue: warps 1-8 read their quarter's lanes of the accumulator, the two warps of a quarter
+  // alternate 16-column chunks
+  if (warp >= 1 && warp <= 8) {
+    const int kh = (warp - 1) >> 2;
     const bool ok = mbar_wait(done, 0, err) && !abort_flag;
     tc_fence_after();
     const int q4 = warp & 3;
@@ -266,7 +293,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
     const int r = r0 + rl;
     const bool valid = c < C && r < nrhs;
     const double bad = __longlong_as_double(0x7ff8000000000000ll);
-    for (int i0 = 0; i0 < NP; i0 += 16) {
+    double* yint = (valid && nif < n) ? y + (int64_t)r * N + cdofs[(int64_t)nif * C + c] - nif : nullptr;
+    for (int i0 = 16 * kh; i0 < NP; i0 += 32) {
       float v[16];
       tc_ld16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)i0, v);
       if (!valid) continue;
@@ -276,7 +304,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
         if (i >= n) break;
         const double val = ok ? (double)v[k] : bad;
         if (i >= nif)
-          y[(int64_t)r * N + cdofs[(int64_t)i * C + c]] = val;
+          yint[i] = val;
         else
           Ycell[((int64_t)r * nif + i) * C + c] = val;
       }

@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("nrhs_max", ctypes.c_int), ("alpha", ctypes.c_double),
                 ("beta", ctypes.c_double), ("apply_precision", ctypes.c_int), ("loop", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("coarse", ctypes.c_int), ("dirichlet", ctypes.c_int),
-                ("decomposition", ctypes.c_int), ("form", ctypes.c_int), ("coarse_its", ctypes.c_int)]
+                ("decomposition", ctypes.c_int), ("form", ctypes.c_int), ("coarse_its", ctypes.c_int),
+                ("dirichlet_vertices", ctypes.c_void_p)]
 
 
 _lib = None
@@ -209,8 +210,12 @@ class Riesz:
     """A solver handle: ``Riesz(space, p, verts, cells, **opts)`` builds the host
     maps; ``setup_device()`` runs the device setup."""
 
-    def __init__(self, space, p, verts, cells, device=True, stream=None, **opts):
+    def __init__(self, space, p, verts, cells, device=True, stream=None, dirichlet_vertices=None, **opts):
+        """dirichlet_vertices: optional flags (one per vertex) choosing Gamma_D with dirichlet=1."""
         self.lib = load_library()
+        if dirichlet_vertices is not None:
+            dv = np.ascontiguousarray(dirichlet_vertices, dtype=np.uint8)
+            opts["dirichlet_vertices"] = dv.ctypes.data
         self.space = SPACES.get(space, space)
         self.p = p
         verts = np.ascontiguousarray(verts, dtype=np.float64)

@@ -77,11 +77,22 @@ def estimate_footprint(h, opts=None):
     return int(b + nalloc * ALLOC_PAGE)
 
 
+# the paper's recommended decomposition per space: vertex stars (H1), Hiptmair-Toselli (H(curl), Eq. (6.19)),
+# edge stars (H(div), Eq. (6.24))
+RECOMMENDED = {"CG": rz.DECOMP_VERTEX_STAR, "N1curl": rz.DECOMP_HT, "RT": rz.DECOMP_EDGE_STAR}
+
+
 class Server:
-    def __init__(self, hbm_budget_bytes=150 << 30, max_slots=4, precond_precision=rz.PREC_FP32):
+    def __init__(self, hbm_budget_bytes=150 << 30, max_slots=4, precond_precision=rz.PREC_FP32, recommended=False,
+                 apply_precision=rz.PREC_FP64):
+        """recommended: solve each request with the paper's decomposition for its space (else vertex stars);
+        apply_precision: precision of the search-direction products (FP32 element matrices need
+        RIESZ_APPLY_ELEMENT, which every request that fits uses)."""
         self.budget = hbm_budget_bytes
         self.max_slots = max_slots
         self.prec = precond_precision
+        self.recommended = recommended
+        self.aprec = apply_precision
         self.lock = threading.Condition()
         self.in_use = 0
         self.active = 0
@@ -89,12 +100,18 @@ class Server:
     def _prepare(self, req):
         verts, cells = kuhn_mesh(req.n, req.amp, req.seed % 1000)
         # no setup-time autotuning: its timing runs would add latency and compete with the other requests
-        opts = dict(precond_precision=self.prec, rtol=req.rtol, maxit=5000, autotune=0)
+        opts = dict(precond_precision=self.prec, apply_precision=self.aprec, rtol=req.rtol, maxit=5000, autotune=0)
+        if self.recommended:
+            opts["decomposition"] = RECOMMENDED[req.space]
         h = rz.Riesz(req.space, req.p, verts, cells, device=False, **opts)
         fp = estimate_footprint(h, opts)
         if fp > self.budget // 2:  # element matrices too large: matrix-free operator
             h.close()
             opts["apply_mode"] = rz.APPLY_MATRIX_FREE
+            if opts["apply_precision"] == rz.PREC_FP32:
+                opts["apply_precision"] = rz.PREC_FP64  # FP32 products need the element matrices
+            if self.recommended:
+                opts["decomposition"] = RECOMMENDED[req.space]
             h = rz.Riesz(req.space, req.p, verts, cells, device=False, **opts)
             fp = estimate_footprint(h, opts)
         return h, fp

@@ -327,3 +327,33 @@ def test_hodge_coupling_tables_k3_match_oracle(lib, p):
     assert R.shape[0] == 1
     Bl = R[0] / abs(np.linalg.det(J[0]))
     assert np.abs(Bl.T - B).max() <= 1e-12 * np.abs(B).max()
+
+
+@pytest.mark.parametrize("space,p", [("CG", 3), ("N1curl", 2), ("RT", 3)])
+def test_partial_dirichlet_map_bit_exact(lib, space, p):
+    """Dirichlet conditions on a part of the boundary (Eq. (2.8) with Gamma_D a proper part of the
+    boundary): Gamma_D = the two faces x = 0 and y = 0 of the cube, chosen by flagging their vertices.
+    The library's fixed DOFs equal the oracle's bit for bit, and their count is the closed form over the
+    closure of Gamma_D (two n x n squares of 2n^2 triangles each sharing the edge x = y = 0)."""
+    n = 3
+    v, c = kuhn_mesh(n, 0.1, 2)
+    x0 = np.isclose(v[:, 0], 0.0)
+    y0 = np.isclose(v[:, 1], 0.0)
+    mask = (x0 | y0).astype(np.uint8)
+    s = rz.Riesz(space, p, v, c, device=False, dirichlet=1, dirichlet_vertices=mask)
+    md = MeshDofs(v, c, reference_element(space, p))
+    from oracle import assemble as asm
+    D = asm.dirichlet_dofs(md, vertex_mask=mask)
+    got = np.nonzero(s.dirichlet_map())[0]
+    assert np.array_equal(got, D)
+    # closure of two squares glued along an edge: vertices, edges and faces of Gamma_D
+    nv_g = 2 * (n + 1) ** 2 - (n + 1)
+    ne_g = 2 * (3 * n * n + 2 * n) - n
+    nf_g = 2 * (2 * n * n)
+    pv, pe, pf, _ = s.per_entity
+    assert len(D) == pv * nv_g + pe * ne_g + pf * nf_g
+    # a mask that flags no boundary face fixes nothing; the whole-boundary default is unchanged
+    none = rz.Riesz(space, p, v, c, device=False, dirichlet=1, dirichlet_vertices=np.zeros(len(v), np.uint8))
+    assert none.dirichlet_map().sum() == 0
+    full = rz.Riesz(space, p, v, c, device=False, dirichlet=1)
+    assert np.array_equal(np.nonzero(full.dirichlet_map())[0], asm.dirichlet_dofs(md))

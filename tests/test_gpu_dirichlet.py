@@ -103,3 +103,42 @@ def test_dirichlet_manufactured_bubble_cg6():
     xq, val = asm.evaluate(ref, md, host(x), X)
     ue = u(xq.reshape(-1, 3)).reshape(val.shape)
     assert np.abs(val - ue).max() <= 1e-9 * np.abs(ue).max()
+
+
+@pytest.mark.parametrize("space,p", [("CG", 3), ("N1curl", 3), ("RT", 3)])
+def test_partial_dirichlet_apply_precond_solve(space, p):
+    """Gamma_D = the faces x = 0 and y = 0 (a proper part of the boundary, Eq. (2.8)), the rest Neumann:
+    apply, preconditioner (one- and two-level) and solve against the oracle's constrained system."""
+    verts, cells = kuhn_mesh(3, 0.1, 3)
+    mask = (np.isclose(verts[:, 0], 0.0) | np.isclose(verts[:, 1], 0.0)).astype(np.uint8)
+    ref = reference_element(space, p)
+    md = MeshDofs(verts, cells, ref)
+    A = asm.assemble(md, asm.element_matrices(ref, verts, cells))
+    D = asm.dirichlet_dofs(md, vertex_mask=mask)
+    Ac = asm.constrained(A, D)
+    for coarse in (0, 1):
+        s = rz.Riesz(space, p, verts, cells, dirichlet=1, dirichlet_vertices=mask, coarse=coarse, rtol=1e-13,
+                     maxit=3000)
+        assert np.array_equal(np.nonzero(s.dirichlet_map())[0], D)
+        x = normal_vector(s.N, 5)
+        y = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+        s.apply(dev(x), y)
+        ye = Ac @ x
+        assert np.abs(host(y) - ye).max() <= 1e-11 * np.abs(ye).max()
+        z = torch.zeros_like(y)
+        s.precond(dev(x), z)
+        P = asm.DirichletPreconditioner(A, md, D, two_level=bool(coarse))
+        ze = P.apply(x)
+        tol = 1e-10
+        if coarse:
+            tol = max(tol, 64.0 * np.linalg.cond(P.P.A0) * 2.0 ** -24)
+        assert np.abs(host(z) - ze).max() <= tol * np.abs(ze).max()
+        b = normal_vector(s.N, 6)
+        b[D] = 0.0
+        xs = torch.zeros_like(y)
+        it, rr, rc = s.solve(dev(b), xs)
+        assert rc == 0
+        xh = host(xs)
+        assert np.all(xh[D] == 0.0)
+        xe = asm.direct_solve(Ac, b)
+        assert np.linalg.norm(xh - xe) <= 1e-10 * np.linalg.norm(xe)
