@@ -50,9 +50,15 @@ WORKLOADS = {
                               "solves (medium case for kernel profiles)"),
     "hgrad_cg3_n4": dict(space="CG", p=3, n=4, amp=0.0, prec=0, nrhs=1,
                          label="H(grad) CG_3 on 4^3 x 6 tets, FP64"),
-    "hdiv_rt8_n16": dict(space="RT", p=8, n=16, amp=0.1, prec=1, nrhs=8, a32=1, plain_steps=3,
-                         label="H(div) RT_8 on 16^3 x 6 tets, perturbed 0.1h, 8 RHS in lockstep, FP32 inner "
-                               "products and patch solves, FP64 residuals"),
+    "hdiv_rt8_n16": dict(space="RT", p=8, n=16, amp=0.1, prec=1, nrhs=8, a32=2, plain_steps=3,
+                         decomposition="edge_star", coarse=1,
+                         variants=[("hybrid", dict(form="hybrid")),
+                                   ("vertex_star_fp32_products", dict(decomposition="vertex_star", a32=1,
+                                                                      steps=3))],
+                         label="H(div) RT_8 on 16^3 x 6 tets, perturbed 0.1h, 8 RHS in lockstep, FP64 outer PCG "
+                               "(residuals, inner products, replacement) with BF16x3 tensor-core contraction "
+                               "(FP32 accumulation) for the inner products and FP32 patch solves; PAFW_1 edge "
+                               "stars + interior Jacobi + W^2 by lowest-order PCG steps"),
 }
 DEFAULT = "hdiv_rt8_n16"
 METRIC = "DOFs/s solved to 1e-8 rel. residual"
@@ -97,6 +103,8 @@ def parse():
     ap.add_argument("--coarse", type=int, default=None, choices=[0, 1, 2],
                     help="W^k coarse space: 0 off, 1 dense inverse up to 6144 DOFs and lowest-order PCG steps above, "
                          "2 lowest-order PCG steps")
+    ap.add_argument("--replace-digits", type=int, default=None,
+                    help="FP64 residual replacement every this many digits (inexact inner products)")
     ap.add_argument("--coarse-its", type=int, default=None,
                     help="PCG steps of the lowest-order coarse route (W^k above the dense limit)")
     ap.add_argument("--pcg-loop", default="graph", choices=["graph", "host"],
@@ -217,6 +225,9 @@ def solver_opts(wl, args, decomposition=None, form=None):
     coarse = args.coarse if args.coarse is not None else wl.get("coarse")
     if coarse is not None:
         o["coarse"] = coarse
+    rd = args.replace_digits if args.replace_digits is not None else wl.get("replace_digits")
+    if rd is not None:
+        o["replace_digits"] = rd
     cits = args.coarse_its if args.coarse_its is not None else wl.get("coarse_its")
     if cits is not None:
         o["coarse_its"] = cits
@@ -434,13 +445,19 @@ def run_batch(args):
     from paper_2506_17406_gb300.inputs import kuhn_mesh, normal_vector
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     draws = batch_draws(args.systems)
-    opts = dict(precond_precision=rz.PREC_FP32, apply_precision=rz.PREC_FP32, rtol=1e-8, maxit=5000)
+    opts = dict(precond_precision=rz.PREC_FP32, rtol=1e-8, maxit=5000)
+    nref = {"CG": lambda p: (p + 1) * (p + 2) * (p + 3) // 6, "N1curl": lambda p: p * (p + 2) * (p + 3) // 2,
+            "RT": lambda p: p * (p + 1) * (p + 3) // 2}
 
     def prep(i):
         space, p, n = draws[i]
         verts, cells = kuhn_mesh(n, 0.1, 1000 + i)
-        h = rz.Riesz(space, p, verts, cells, device=False, **opts)
-        return h, verts, serve.estimate_footprint(h, opts)
+        # the paper's decomposition per space; BF16x3 tensor-core products where the accumulator fits
+        # (n_ref <= 512), FP32 element matrices otherwise
+        o = dict(opts, decomposition=serve.RECOMMENDED[space],
+                 apply_precision=rz.PREC_BF16X3 if nref[space](p) <= 512 else rz.PREC_FP32)
+        h = rz.Riesz(space, p, verts, cells, device=False, **o)
+        return h, verts, serve.estimate_footprint(h)
 
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
@@ -510,8 +527,9 @@ def run_batch(args):
            "value": ntot / ((setup_ms + solve_ms) / 1e3), "unit": "DOFs/s", "n_gpus": 1, "higher_is_better": True,
            "data": "synthetic", "dtype": "f64+f32",
            "config": {"workload": "%d seeded draws: space in {CG, Ned1, RT}, p in 2..10, n^3 x 6 tets with n in "
-                                  "4..12, perturbed 0.1h, random RHS, FP32 products and patch sweeps, FP64 "
-                                  "residuals, rtol 1e-8" % len(draws),
+                                  "4..12, perturbed 0.1h, random RHS, the paper's decomposition per space + W^k, "
+                                  "BF16x3 tensor-core products (FP32 element matrices where n_ref > 512) and "
+                                  "FP32 patch sweeps, FP64 residuals, rtol 1e-8" % len(draws),
                       "hbm_budget_gb": args.hbm_budget_gb, "waves": [len(w) for w in waves]},
            "dofs": int(ntot), "setup_ms": setup_ms, "solve_ms": solve_ms,
            "solve_dofs_per_s": ntot / (solve_ms / 1e3),
@@ -538,7 +556,10 @@ def run_p_sweep(args):
             for p in range(1, 11):
                 row = {}
                 for name, kw in (("one_level", dict(coarse=0)), ("two_level", dict(coarse=1)),
-                                 ("two_level_mixed", dict(coarse=1, precond_precision=rz.PREC_FP32))):
+                                 ("two_level_mixed", dict(coarse=1, precond_precision=rz.PREC_FP32)),
+                                 ("hybrid", dict(coarse=1, form=rz.FORM_HYBRID)),
+                                 ("hybrid_recommended", dict(coarse=1, form=rz.FORM_HYBRID,
+                                                             decomposition={"CG": 0, "N1curl": 1, "RT": 2}[space]))):
                     s = rz.Riesz(space, p, verts, cells, maxit=5000, **kw)
                     b = torch.tensor(normal_vector(s.N, 7), device="cuda")
                     x = torch.zeros_like(b)
@@ -551,7 +572,10 @@ def run_p_sweep(args):
                       "config": {"meshes": "n^3 x 6 Kuhn tets, perturbed 0.1h", "rhs": "N(0,1) vector",
                                  "preconditioner": "interior Jacobi + vertex-star patches (one_level), "
                                                    "+ W^k coarse space (two_level), additive; two_level_mixed "
-                                                   "with FP32 patch sweeps"},
+                                                   "with FP32 patch sweeps; hybrid: the paper's multiplicative "
+                                                   "sweep with Lanczos weights (vertex stars), "
+                                                   "hybrid_recommended: the same with the paper's decomposition "
+                                                   "per space (Hiptmair-Toselli for Ned1, edge stars for RT)"},
                       "iterations": table}), flush=True)
 
 
@@ -922,11 +946,19 @@ def main():
 
     # the same workload with the paper's finer decomposition for the space (Hiptmair-Toselli for H(curl),
     # PAFW_1 edge stars for H(div)): same mesh, right-hand side, precisions and rtol
+    # other configurations of the same workload: the paper's finer decomposition for the space when the main
+    # line uses vertex stars (Hiptmair-Toselli for H(curl), PAFW_1 edge stars for H(div)), the hybrid form, and
+    # whatever the workload lists (e.g. the previous default); same mesh, right-hand sides, precisions and rtol
     variants = {}
-    alt = {"N1curl": "ht", "RT": "edge_star"}.get(wl["space"])
     main_decomp = args.decomposition or wl.get("decomposition", "vertex_star")
-    if alt and alt != main_decomp and not args.no_variants:
-        sv, stepv, itv, rrv, *_ = make(wl["prec"], wl.get("a32", 0), alt)
+    vlist = []
+    alt = {"N1curl": "ht", "RT": "edge_star"}.get(wl["space"])
+    if alt and alt != main_decomp:
+        vlist.append((alt, dict(decomposition=alt)))
+    vlist += wl.get("variants", [])
+    for vname, vkw in ([] if args.no_variants else vlist):
+        sv, stepv, itv, rrv, *_ = make(vkw.get("prec", wl["prec"]), vkw.get("a32", wl.get("a32", 0)),
+                                       vkw.get("decomposition"), vkw.get("form"))
         for _ in range(args.warmup):
             stepv()
         sv.profile(True)
@@ -934,18 +966,20 @@ def main():
         torch.cuda.synchronize()
         profv = sv.profile_read()
         sv.profile(False)
-        perv = timed(stepv, args.steps)
+        vsteps = min(args.steps, vkw.get("steps", args.steps))
+        perv = timed(stepv, vsteps)
         msv, _ = combine_ranks(sum(perv), sv.N, dist, device="cuda")
         kv = {k: v[0] for k, v in profv.items()}
-        variants[alt] = {"value": ntot * nrhs * args.steps / (msv / 1e3), "unit": "DOFs/s",
-                         "ms_per_step": msv / args.steps,
-                         "latency_p50_ms": float(np.percentile(perv, 50)),
-                         "latency_p99_ms": float(np.percentile(perv, 99)),
-                         "iterations": statistics.median(itv[-args.steps:]), "max_relres": max(rrv[-args.steps:]),
-                         "largest_patch": int(np.diff(sv.patch_map()[0]).max()),
-                         "kernel_ms_per_step": {k: round(v, 4) for k, v in kv.items() if v > 0},
-                         "pcg_loop": args.pcg_loop,
-                         "config": "same mesh, right-hand side, precisions and rtol; decomposition " + alt}
+        variants[vname] = {"value": ntot * nrhs * vsteps / (msv / 1e3), "unit": "DOFs/s",
+                           "steps": vsteps, "ms_per_step": msv / vsteps,
+                           "latency_p50_ms": float(np.percentile(perv, 50)),
+                           "latency_p99_ms": float(np.percentile(perv, 99)),
+                           "iterations": statistics.median(itv[-vsteps:]), "max_relres": max(rrv[-vsteps:]),
+                           "largest_patch": int(np.diff(sv.patch_map()[0]).max()),
+                           "kernel_ms_per_step": {k: round(v, 4) for k, v in kv.items() if v > 0},
+                           "pcg_loop": args.pcg_loop,
+                           "config": "same mesh, right-hand sides and rtol; " + ", ".join(
+                               "%s %s" % kv_ for kv_ in sorted(vkw.items()))}
         sv.close()
 
     cb = err = None

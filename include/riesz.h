@@ -200,6 +200,13 @@ typedef struct {
      boundary with its closure: those faces, their edges and vertices carry
      the fixed DOFs).  Read during riesz_create only. */
   const uint8_t* dirichlet_vertices;
+  /* With inexact inner products (apply_precision FP32 or BF16X3): replace the
+     recursive residual by the FP64 true residual whenever a right-hand side's
+     residual norm has fallen by this many digits since the last replacement.
+     0 (default): 4 with FP32 products, 2 with BF16x3 products; 1..12 sets
+     it.  Each replacement costs one FP64 operator product; fewer of them let
+     the recursive residual drift further from the true one. */
+  int replace_digits;
 } riesz_opts;
 
 /* Fill *o with the defaults: FP64 preconditioner, element-matrix apply,

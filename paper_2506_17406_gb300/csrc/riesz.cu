@@ -1241,7 +1241,9 @@ bool use_a32(const riesz_handle& h) { return inner_prec(h) != RIESZ_PREC_FP64; }
 // ~1e-5 relative error would otherwise build up a larger gap between the recursive and true residuals).
 double reliable_gain(const riesz_handle& h) {
   const int ip = inner_prec(h);
-  return ip == RIESZ_PREC_FP64 ? 0.0 : (ip == RIESZ_PREC_BF16X3 ? 1e-4 : 1e-8);
+  if (ip == RIESZ_PREC_FP64) return 0.0;
+  const int d = h.opts.replace_digits > 0 ? h.opts.replace_digits : (ip == RIESZ_PREC_BF16X3 ? 2 : 4);
+  return std::pow(10.0, -2.0 * d);  // (r, r) falls by the square of the norm's factor
 }
 // Precision of the residual updates inside the hybrid sweep.
 int sweep_prec(const riesz_handle& h) {
@@ -2550,6 +2552,7 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
   need(h->opts.coarse >= 0 && h->opts.coarse <= 2, "bad coarse");
   need(h->opts.coarse_its >= 1 && h->opts.coarse_its <= 1000, "coarse_its must be in 1..1000");
   need(!h->opts.dirichlet_vertices || h->opts.dirichlet, "dirichlet_vertices needs dirichlet = 1");
+  need(h->opts.replace_digits >= 0 && h->opts.replace_digits <= 12, "replace_digits must be in 0..12");
   need(h->opts.form == RIESZ_FORM_ADDITIVE || h->opts.form == RIESZ_FORM_HYBRID, "bad form");
   need(h->opts.dirichlet == 0 || h->opts.dirichlet == 1, "bad dirichlet");
   need(h->opts.decomposition >= RIESZ_DECOMP_VERTEX_STAR && h->opts.decomposition <= RIESZ_DECOMP_EDGE_STAR,
@@ -2583,7 +2586,9 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
     co.coarse = 0;
     co.form = RIESZ_FORM_ADDITIVE;
     co.decomposition = RIESZ_DECOMP_VERTEX_STAR;
-    co.precond_precision = RIESZ_PREC_FP64;
+    // FP32 patch sweeps (the coarse steps are approximate anyway, and FP64 arithmetic runs at ~1/40 of
+    // the FP32 rate on GB300), FP64 products, residuals and inner products
+    co.precond_precision = RIESZ_PREC_FP32;
     co.apply_precision = RIESZ_PREC_FP64;
     co.apply_mode = RIESZ_APPLY_ELEMENT;
     co.autotune = 0;
@@ -2655,6 +2660,7 @@ void riesz_default_opts(riesz_opts* o) {
   o->form = RIESZ_FORM_ADDITIVE;
   o->coarse_its = 4;
   o->dirichlet_vertices = nullptr;
+  o->replace_digits = 0;
 }
 
 const char* riesz_last_error(void) { return g_err.c_str(); }

@@ -40,7 +40,7 @@ class Opts(ctypes.Structure):
                 ("beta", ctypes.c_double), ("apply_precision", ctypes.c_int), ("loop", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("coarse", ctypes.c_int), ("dirichlet", ctypes.c_int),
                 ("decomposition", ctypes.c_int), ("form", ctypes.c_int), ("coarse_its", ctypes.c_int),
-                ("dirichlet_vertices", ctypes.c_void_p)]
+                ("dirichlet_vertices", ctypes.c_void_p), ("replace_digits", ctypes.c_int)]
 
 
 _lib = None
