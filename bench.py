@@ -385,8 +385,8 @@ def run_serving(args):
     """Poisson arrivals (mean 200 requests/s, seeded) of Riesz-map solves mixing CG, Ned1 and RT with p in
     3..10 and Kuhn meshes of 4..20 cubes per edge (384..48 000 tets), perturbed by 0.1h, admitted by a 150 GB
     HBM budget with up to 8 requests in flight, each solved with the paper's decomposition for its space
-    (vertex stars, Hiptmair-Toselli, edge stars) and W^k.  The mixed server (FP32 patch sweeps and FP32
-    products) and the plain FP64 server serve the same stream one after the other."""
+    (vertex stars, Hiptmair-Toselli, edge stars) and W^k.  The mixed server (FP32 patch sweeps, BF16x3
+    tensor-core products) and the plain FP64 server serve the same stream one after the other."""
     import numpy as np
     import torch
     from paper_2506_17406_gb300 import riesz as rz
@@ -402,7 +402,7 @@ def run_serving(args):
                                   "decompositions + W^k", "requests": args.requests}}
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    for name, kw in (("mixed", dict(precond_precision=rz.PREC_FP32, apply_precision=rz.PREC_FP32)),
+    for name, kw in (("mixed", dict(precond_precision=rz.PREC_FP32, apply_precision=rz.PREC_BF16X3)),
                      ("fp64_plain", dict(precond_precision=rz.PREC_FP64, apply_precision=rz.PREC_FP64))):
         reqs = serve.poisson_stream(args.requests, rate=200.0, seed=7, degrees=degrees, sizes=sizes)
         srv = serve.Server(hbm_budget_bytes=150 << 30, max_slots=8, recommended=True, **kw)
@@ -446,16 +446,12 @@ def run_batch(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     draws = batch_draws(args.systems)
     opts = dict(precond_precision=rz.PREC_FP32, rtol=1e-8, maxit=5000)
-    nref = {"CG": lambda p: (p + 1) * (p + 2) * (p + 3) // 6, "N1curl": lambda p: p * (p + 2) * (p + 3) // 2,
-            "RT": lambda p: p * (p + 1) * (p + 3) // 2}
 
     def prep(i):
         space, p, n = draws[i]
         verts, cells = kuhn_mesh(n, 0.1, 1000 + i)
-        # the paper's decomposition per space; BF16x3 tensor-core products where the accumulator fits
-        # (n_ref <= 512), FP32 element matrices otherwise
-        o = dict(opts, decomposition=serve.RECOMMENDED[space],
-                 apply_precision=rz.PREC_BF16X3 if nref[space](p) <= 512 else rz.PREC_FP32)
+        # the paper's decomposition per space, BF16x3 tensor-core products
+        o = dict(opts, decomposition=serve.RECOMMENDED[space], apply_precision=rz.PREC_BF16X3)
         h = rz.Riesz(space, p, verts, cells, device=False, **o)
         return h, verts, serve.estimate_footprint(h)
 
@@ -528,8 +524,8 @@ def run_batch(args):
            "data": "synthetic", "dtype": "f64+f32",
            "config": {"workload": "%d seeded draws: space in {CG, Ned1, RT}, p in 2..10, n^3 x 6 tets with n in "
                                   "4..12, perturbed 0.1h, random RHS, the paper's decomposition per space + W^k, "
-                                  "BF16x3 tensor-core products (FP32 element matrices where n_ref > 512) and "
-                                  "FP32 patch sweeps, FP64 residuals, rtol 1e-8" % len(draws),
+                                  "BF16x3 tensor-core products and FP32 patch sweeps, FP64 residuals, rtol 1e-8"
+                                  % len(draws),
                       "hbm_budget_gb": args.hbm_budget_gb, "waves": [len(w) for w in waves]},
            "dofs": int(ntot), "setup_ms": setup_ms, "solve_ms": solve_ms,
            "solve_dofs_per_s": ntot / (solve_ms / 1e3),

@@ -98,7 +98,7 @@ typedef struct {
      b - A x whenever a right-hand side gains four digits
      and at convergence (the stopping test is always on the FP64 residual);
      the first residual needs no product when x = 0.  riesz_apply is always
-     FP64.  RIESZ_PREC_BF16X3 (any apply_mode, n_ref <= 512): the same
+     FP64.  RIESZ_PREC_BF16X3 (any apply_mode, every degree up to 10): the same
      products, and the residual updates of the hybrid sweep, matrix-free on
      the tensor cores (tcgen05): Y_T = sum_q g_q(T) R_q X_T as a GEMM over
      tiles of 128 (cell, right-hand side) rows with every operand split into

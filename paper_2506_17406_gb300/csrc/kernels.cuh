@@ -99,17 +99,24 @@ __global__ void k_geom(int space, int64_t C, const double* __restrict__ verts, c
   jac[c * 10 + 9] = det;
 }
 
-// A_T = sum_q g_q(T) R_q, stored [C][n][n] (setup of the element-matrix apply).
+// A_T = sum_q g_q(T) R_q, stored [C][n][n] (setup of the element-matrix apply).  The R_q are
+// symmetric, so A_T is: the upper triangle is formed (row by row, coalesced) and mirrored, half the
+// FP64 work of forming every entry.
 __global__ void k_elem_matrices(int64_t C, int n, int Q, const double* __restrict__ g, const double* __restrict__ R,
                                 double* __restrict__ Ae) {
   const int64_t c = blockIdx.x;
   const int64_t nn = (int64_t)n * n;
   double gq[16];
   for (int q = 0; q < Q; ++q) gq[q] = g[q * C + c];
-  for (int64_t t = threadIdx.x; t < nn; t += blockDim.x) {
-    double s = 0.0;
-    for (int q = 0; q < Q; ++q) s += gq[q] * R[q * nn + t];
-    Ae[c * nn + t] = s;
+  double* A = Ae + c * nn;
+  for (int i = 0; i < n; ++i) {
+    for (int j = i + threadIdx.x; j < n; j += blockDim.x) {
+      const int64_t t = (int64_t)i * n + j;
+      double s = 0.0;
+      for (int q = 0; q < Q; ++q) s += gq[q] * R[q * nn + t];
+      A[t] = s;
+      if (j != i) A[(int64_t)j * n + i] = s;
+    }
   }
 }
 

@@ -873,10 +873,11 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
   if (prec == RIESZ_PREC_BF16X3) {
     const int RT = nrhs >= 8 ? 8 : (nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1));
     const int cells = dev::TC_ROWS / RT;
-    dim3 grid((unsigned)((C + cells - 1) / cells), (unsigned)((nrhs + RT - 1) / RT));
+    dim3 grid((unsigned)((C + cells - 1) / cells), (unsigned)((nrhs + RT - 1) / RT), (unsigned)dev::tc_parts(h.tc_np));
     launch(h, RIESZ_K_APPLY_TC, s, [&] {
-      const int ns = dev::tc_stages(h.tc_np);
-      const size_t sm = dev::tc_smem_bytes(h.tc_np, ns);
+      const int npc = dev::tc_part_cols(h.tc_np, 0);
+      const int ns = dev::tc_stages(npc);
+      const size_t sm = dev::tc_smem_bytes(npc, ns);
       if (h.ref->Q == 12)
         dev::k_apply_tc<12><<<grid, dev::TC_NT, sm, s>>>(C, n, h.nif, h.tc_np, h.tc_kc, RT, ns, h.d_Btc.p, h.d_g.p,
                                                          h.d_cdofs.p, x, y, h.d_Ycell.p, nrhs, N, h.dmask(),
@@ -2185,9 +2186,9 @@ float bf16_value(uint16_t b) {
   return f;
 }
 
-// The B operand of k_apply_tc: for each stage (32-wide chunk jc of j, then q) the split
-// R_q[i][jc*32 + kk] = hi + lo (hi = bf16(R), lo = bf16(R - hi)), hi block then lo block, each
-// [NP/8 row groups][4 K core matrices][8 rows][8 values] (the K-major layout without swizzle).
+// The B operand of k_apply_tc: for each stage (TC_KC-wide chunk jc of j, then q) the split
+// R_q[i][jc*TC_KC + kk] = hi + lo (hi = bf16(R), lo = bf16(R - hi)), hi block then lo block, each
+// [NP/8 row groups][TC_KCORE K core matrices][8 rows][8 values] (the K-major layout without swizzle).
 void build_tc_table(riesz_handle& h, std::vector<uint16_t>& t) {
   const int n = h.mesh.nref, Q = h.ref->Q, NP = h.tc_np, KC = h.tc_kc;
   const std::vector<double>& R = h.ref->R;
@@ -2203,7 +2204,7 @@ void build_tc_table(riesz_handle& h, std::vector<uint16_t>& t) {
           const double v = R[(size_t)q * n * n + (size_t)i * n + k];
           const uint16_t hi = bf16_bits((float)v);
           const uint16_t lo = bf16_bits((float)(v - (double)bf16_value(hi)));
-          const size_t idx = ((size_t)(i / 8) * 4 + kk / 8) * 64 + (size_t)(i % 8) * 8 + kk % 8;
+          const size_t idx = ((size_t)(i / 8) * dev::TC_KCORE + kk / 8) * 64 + (size_t)(i % 8) * 8 + kk % 8;
           t[base + idx] = hi;
           t[base + blk + idx] = lo;
         }
@@ -2379,8 +2380,9 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
       for (int t = h.nif + 1; t < n; ++t)
         if (M.cell_dofs[(size_t)c * n + t] != M.cell_dofs[(size_t)c * n + h.nif] + (t - h.nif))
           throw Err(RIESZ_ERR_INTERNAL, "interior DOFs of a cell are not contiguous");
-    raise_smem_limit(dev::k_apply_tc<7>, dev::tc_smem_bytes(h.tc_np, dev::tc_stages(h.tc_np)));
-    raise_smem_limit(dev::k_apply_tc<12>, dev::tc_smem_bytes(h.tc_np, dev::tc_stages(h.tc_np)));
+    const int npc = dev::tc_part_cols(h.tc_np, 0);
+    raise_smem_limit(dev::k_apply_tc<7>, dev::tc_smem_bytes(npc, dev::tc_stages(npc)));
+    raise_smem_limit(dev::k_apply_tc<12>, dev::tc_smem_bytes(npc, dev::tc_stages(npc)));
   }
   h.d_ticket.alloc(nrhs);
   CK(cudaMemsetAsync(h.d_ticket.p, 0, sizeof(unsigned) * nrhs, s));
@@ -2574,8 +2576,8 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
   } catch (const std::exception& e) {
     throw Err(RIESZ_ERR_BAD_MESH, e.what());
   }
-  need(h->opts.apply_precision != RIESZ_PREC_BF16X3 || h->mesh.nref <= dev::TC_MAXNP,
-       "the BF16x3 tensor-core products hold n_ref <= 512 accumulators per row (degree too high)");
+  need(h->opts.apply_precision != RIESZ_PREC_BF16X3 || h->mesh.nref <= dev::TC_MAXN,
+       "the BF16x3 tensor-core products hold n_ref <= 1024 accumulators per row (degree too high)");
   if (h->opts.dirichlet) plan_dirichlet(*h);
   if (h->opts.decomposition == RIESZ_DECOMP_HT) plan_ht(*h);
   if (h->opts.decomposition == RIESZ_DECOMP_EDGE_STAR) plan_edge_stars(*h, 0, h->mesh.per_entity[2]);
@@ -3117,8 +3119,14 @@ struct riesz_hodge {
   DBuf<double> v, vp, u, w, z, d1, d2, d_m, d_part;       // MINRES vectors and scalars
   DBuf<unsigned> d_ticket;
   double* h_m = nullptr;
+  // the second block preconditioner runs on its own stream beside the first
+  cudaStream_t s1 = nullptr;
+  cudaEvent_t ev_f = nullptr, ev_j = nullptr;
   ~riesz_hodge() {
     if (h_m) cudaFreeHost(h_m);
+    if (s1) cudaStreamDestroy(s1);
+    if (ev_f) cudaEventDestroy(ev_f);
+    if (ev_j) cudaEventDestroy(ev_j);
     for (auto* b : {&d_R, &d_gB, &d_jacB, &d_Be, &v, &vp, &u, &w, &z, &d1, &d2, &d_m, &d_part, &d_dg_mhat, &d_dg_X,
                     &d_dg_dinv})
       b->free();
@@ -3189,15 +3197,21 @@ void hodge_apply(riesz_hodge& H, const double* x, double* y, cudaStream_t s) {
   }
 }
 
+// The two blocks of Eq. (7.6) are independent: the X^k block runs on the handle's second stream
+// beside the X^{k-1} block and joins before the caller's next step.
 void hodge_precond(riesz_hodge& H, const double* r, double* z, cudaStream_t s) {
-  op_precond(*H.P0, r, z, 1, s);
+  CK(cudaEventRecord(H.ev_f, s));
+  CK(cudaStreamWaitEvent(H.s1, H.ev_f, 0));
   if (H.P1) {
-    op_precond(*H.P1, r + H.n0, z + H.n0, 1, s);
+    op_precond(*H.P1, r + H.n0, z + H.n0, 1, H.s1);
   } else {  // k = 3: the diagonal DG block, inverted exactly
-    dev::k_dg_scale<<<nblk(H.n1, 256), 256, 0, s>>>(H.n1, H.d_dg_dinv.p, r + H.n0, z + H.n0);
+    dev::k_dg_scale<<<nblk(H.n1, 256), 256, 0, H.s1>>>(H.n1, H.d_dg_dinv.p, r + H.n0, z + H.n0);
     CK(cudaGetLastError());
     ++H.launches;
   }
+  op_precond(*H.P0, r, z, 1, s);
+  CK(cudaEventRecord(H.ev_j, H.s1));
+  CK(cudaStreamWaitEvent(s, H.ev_j, 0));
 }
 
 void hodge_dot(riesz_hodge& H, const double* a, const double* b, int op, cudaStream_t s) {
@@ -3358,6 +3372,9 @@ int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t
       need(H->n1 < ((int64_t)1 << 31), "too many DG DOFs for 32-bit indices");
     }
     cudaStream_t s = S(stream);
+    CK(cudaStreamCreateWithFlags(&H->s1, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&H->ev_f, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&H->ev_j, cudaEventDisableTiming));
     for (riesz_handle* x : {H->P0, H->P1, H->Mh, H->Kh})
       if (x) setup_device_impl(*x, s);
     const int n0 = H->Mh->mesh.nref, n1 = H->Kh ? H->Kh->mesh.nref : H->n_dg;

@@ -10,11 +10,11 @@
 //
 // Layout.  The accumulator D (128 lanes x NP FP32 columns, NP = n padded to a
 // multiple of 16, at most 512) lives in tensor memory for the whole K loop.  K
-// runs over stages (j-chunk of 32, q): the B stage (hi and lo, NP rows x 32 K)
+// runs over stages (j-chunk of TC_KC, q): the B stage (hi and lo, NP rows x TC_KC K)
 // is a precomputed table in the canonical K-major layout without swizzle (core
 // matrices of 8 rows x 16 bytes, K-adjacent core matrices 128 B apart, 8-row
-// groups 512 B apart), so one bulk copy (cp.async.bulk) moves a stage into
-// shared memory; the A stage (hi and lo, 128 rows x 32 K, same layout) is built
+// groups TC_SBO bytes apart), so one bulk copy (cp.async.bulk) moves a stage into
+// shared memory; the A stage (hi and lo, 128 rows x TC_KC K, same layout) is built
 // by the four producer warps from the gathered X and g.  Ring of NSTAGE slots,
 // mbarriers with bounded waits.
 //
@@ -36,9 +36,19 @@ namespace dev {
 constexpr int TC_NT = 320;
 constexpr int TC_PRODUCERS = 256;  // threads of warps 1-8
 constexpr int TC_ROWS = 128;   // M of one MMA (cta_group::1)
-constexpr int TC_KC = 32;      // K per stage (BF16 elements)
-constexpr int TC_NSTAGE = 3;   // most ring slots (fewer when shared memory does not hold three)
-constexpr int TC_MAXNP = 512;  // tensor-memory columns
+constexpr int TC_KC = 16;      // K per stage (BF16 elements): one MMA K step
+constexpr int TC_KCORE = TC_KC / 8;        // core matrices along K per stage
+constexpr int TC_SBO = TC_KCORE * 128;     // bytes between 8-row groups (stride byte offset)
+constexpr int TC_NSTAGE = 8;   // most ring slots (as many as shared memory holds, at least 2)
+constexpr int TC_MAXNP = 512;  // tensor-memory columns of one CTA
+constexpr int TC_MAXN = 1024;  // largest n_ref: above 512 outputs the columns are split over two CTAs (grid z)
+// columns of part z (0 or 1) of NP padded outputs: one part up to 512, else two halves rounded to 16
+__host__ __device__ inline int tc_part_cols(int NP, int z) {
+  if (NP <= TC_MAXNP) return z == 0 ? NP : 0;
+  const int h = (NP / 2 + 15) / 16 * 16;
+  return z == 0 ? h : NP - h;
+}
+__host__ __device__ inline int tc_parts(int NP) { return NP <= TC_MAXNP ? 1 : 2; }
 
 // bytes of one A stage (hi + lo) and of one B stage (hi + lo) for NP rows
 __host__ __device__ constexpr uint32_t tc_a_bytes() { return 2u * TC_ROWS * TC_KC * 2u; }
@@ -47,7 +57,11 @@ inline size_t tc_smem_bytes(int NP, int nstage) {
   return (size_t)nstage * (tc_a_bytes() + tc_b_bytes(NP)) + 256;
 }
 // ring slots that fit in the 227 KB of shared memory a CTA may hold
-inline int tc_stages(int NP) { return tc_smem_bytes(NP, 3) <= 232448 ? 3 : 2; }
+inline int tc_stages(int NP) {
+  int ns = TC_NSTAGE;
+  while (ns > 2 && tc_smem_bytes(NP, ns) > 232448) --ns;
+  return ns;
+}
 
 // Shared-memory matrix descriptor (K-major, no swizzle): start address, leading
 // byte offset (between K-adjacent core matrices), stride byte offset (between
@@ -125,22 +139,25 @@ __device__ __forceinline__ void tc_load_x(float (&xf)[TC_KH], bool valid, int j0
 
 // y = A x (interior rows) and Ycell (interface rows, scattered by k_gather_iface)
 // for tiles of CELLS = 128 / RT cells and RT right-hand sides: row m = r * CELLS + c.
-// Bst: the B stages [KC][Q][hi | lo][NP / 8][4][8][8] BF16 (see the file comment).
+// Bst: the B stages [KC][Q][hi | lo][NP / 8][TC_KCORE][8][8] BF16 (see the file comment).
 // The interior DOFs of a cell are numbered contiguously (cell-major), so row m writes its interior
 // outputs from the cell's first interior DOF on.  Q (the number of reference matrices) is a template
 // parameter so that the producers keep the Q factors of their cell in registers.
 template <int Q>
-__global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif, int NP, int KC, int RT, int NS,
+__global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif, int NPt, int KC, int RT, int NS,
                                                       const uint16_t* __restrict__ Bst, const double* __restrict__ g,
                                                       const int32_t* __restrict__ cdofs, const double* __restrict__ x,
                                                       double* __restrict__ y, double* __restrict__ Ycell, int nrhs,
                                                       int64_t N, const uint8_t* __restrict__ dmask,
                                                       int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tc_sm[];
-  const uint32_t abytes = tc_a_bytes(), bbytes = tc_b_bytes(NP);
+  // this CTA's output columns [col0, col0 + NP) of the NPt padded ones (grid z: the column part)
+  const int NP = tc_part_cols(NPt, blockIdx.z), col0 = blockIdx.z == 0 ? 0 : tc_part_cols(NPt, 0);
+  const int NPs = tc_part_cols(NPt, 0);  // the ring is sized for the widest part
+  const uint32_t abytes = tc_a_bytes(), bbytes = tc_b_bytes(NP), bstride = tc_b_bytes(NPs);
   unsigned char* sA = tc_sm;                           // [NS][abytes]
-  unsigned char* sB = tc_sm + (size_t)NS * abytes;     // [NS][bbytes]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)NS * bbytes);
+  unsigned char* sB = tc_sm + (size_t)NS * abytes;     // [NS][bstride], this part's rows of each B stage
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)NS * bstride);
   uint64_t* full_a = bars;                   // [NS], 256 producer arrivals
   uint64_t* full_b = bars + TC_NSTAGE;       // [NS], expect_tx
   uint64_t* empty = bars + 2 * TC_NSTAGE;    // [NS], MMA commit
@@ -187,8 +204,12 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
           abort_flag = 1;
           break;
         }
+        // hi rows then lo rows of this part: contiguous row-group ranges of the stage's hi and lo blocks
+        const uint16_t* src = Bst + (size_t)s * 2 * NPt * TC_KC + (size_t)col0 * TC_KC;
+        unsigned char* dst = sB + (size_t)slot * bstride;
         mbar_expect_tx(&full_b[slot], bbytes);
-        bulk_g2s(sB + (size_t)slot * bbytes, Bst + (size_t)s * (bbytes / 2), bbytes, &full_b[slot]);
+        bulk_g2s(dst, src, bbytes / 2, &full_b[slot]);
+        bulk_g2s(dst + bbytes / 2, src + (size_t)NPt * TC_KC, bbytes / 2, &full_b[slot]);
         issued = s + 1;
       }
       // no copy may still be landing when the CTA exits (they have all landed in a complete run)
@@ -205,7 +226,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
     float gq[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) gq[q] = valid ? (float)g[q * C + c] : 0.f;
-    const uint32_t rowoff = (uint32_t)(m >> 3) * 512u + (uint32_t)(m & 7) * 16u + (uint32_t)kh * 256u;
+    const uint32_t rowoff =
+        (uint32_t)(m >> 3) * TC_SBO + (uint32_t)(m & 7) * 16u + (uint32_t)kh * (TC_KCORE / 2) * 128u;
     float xf[TC_KH], xn[TC_KH];
     tc_load_x(xf, valid, kh * TC_KH, n, nif, C, c, r, N, cdofs, x, dmask);
     bool ok = true;
@@ -223,7 +245,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
         unsigned char* lo = hi + abytes / 2;
         const float gv = gq[q];
 #pragma unroll
-        for (int kc = 0; kc < 2; ++kc) {  // the two core matrices of this K half
+        for (int kc = 0; kc < TC_KCORE / 2; ++kc) {  // the core matrices of this K half
           uint32_t ph[4], pl[4];
 #pragma unroll
           for (int e2 = 0; e2 < 4; ++e2)
@@ -255,19 +277,19 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
         }
         tc_fence_after();
         const uint32_t a_hi = smem_addr(sA + (size_t)slot * abytes), a_lo = a_hi + abytes / 2;
-        const uint32_t b_hi = smem_addr(sB + (size_t)slot * bbytes), b_lo = b_hi + bbytes / 2;
+        const uint32_t b_hi = smem_addr(sB + (size_t)slot * bstride), b_lo = b_hi + bbytes / 2;
 #pragma unroll
         for (int ks = 0; ks < TC_KC / 16; ++ks) {
-          const uint32_t ko = (uint32_t)ks * 256u;
-          const uint64_t ah = tc_desc(a_hi + ko, 128, 512), al = tc_desc(a_lo + ko, 128, 512);
-          const uint64_t bh0 = tc_desc(b_hi + ko, 128, 512), bl0 = tc_desc(b_lo + ko, 128, 512);
+          const uint32_t ko = (uint32_t)ks * 256u;  // two core matrices per K step of 16
+          const uint64_t ah = tc_desc(a_hi + ko, 128, TC_SBO), al = tc_desc(a_lo + ko, 128, TC_SBO);
+          const uint64_t bh0 = tc_desc(b_hi + ko, 128, TC_SBO), bl0 = tc_desc(b_lo + ko, 128, TC_SBO);
           const int acc0 = (s > 0 || ks > 0) ? 1 : 0;
           tc_mma(tmem, ah, bh0, idesc0, acc0);
           tc_mma(tmem, ah, bl0, idesc0, 1);
           tc_mma(tmem, al, bh0, idesc0, 1);
           if (np1 > 0) {
-            const uint32_t bo = (uint32_t)(np0 / 8) * 512u;
-            const uint64_t bh1 = tc_desc(b_hi + bo + ko, 128, 512), bl1 = tc_desc(b_lo + bo + ko, 128, 512);
+            const uint32_t bo = (uint32_t)(np0 / 8) * TC_SBO;
+            const uint64_t bh1 = tc_desc(b_hi + bo + ko, 128, TC_SBO), bl1 = tc_desc(b_lo + bo + ko, 128, TC_SBO);
             const uint32_t d1 = tmem + (uint32_t)np0;
             tc_mma(d1, ah, bh1, idesc1, acc0);
             tc_mma(d1, ah, bl1, idesc1, 1);
@@ -300,7 +322,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
       if (!valid) continue;
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        const int i = i0 + k;
+        const int i = col0 + i0 + k;
         if (i >= n) break;
         const double val = ok ? (double)v[k] : bad;
         if (i >= nif)

@@ -26,10 +26,12 @@ def dev(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-# (space, p, cubes per edge, right-hand sides): n_ref from 4 to 440 (one and two N pieces of the MMA),
-# tiles of 128 cells (1 RHS) down to 16 cells x 8 RHS, ragged last tiles, Dirichlet masks
+# (space, p, cubes per edge, right-hand sides): n_ref from 4 to 715 (one and two N pieces of the MMA, and
+# above 512 outputs the columns split over two CTAs), tiles of 128 cells (1 RHS) down to 16 cells x 8 RHS,
+# ragged last tiles
 CASES = [("CG", 1, 3, 1), ("CG", 3, 4, 2), ("N1curl", 3, 3, 3), ("RT", 3, 3, 8), ("N1curl", 6, 2, 8),
-         ("RT", 8, 2, 8), ("RT", 8, 1, 1), ("CG", 8, 2, 4), ("N1curl", 8, 1, 5)]
+         ("RT", 8, 2, 8), ("RT", 8, 1, 1), ("CG", 8, 2, 4), ("N1curl", 8, 1, 5), ("N1curl", 9, 1, 3),
+         ("RT", 10, 1, 2)]
 
 
 @pytest.mark.parametrize("space,p,n,nr", CASES)
@@ -48,7 +50,7 @@ def test_tensor_apply_matches_oracle(space, p, n, nr):
     y64 = torch.zeros_like(y)
     s.apply(dev(X), y64, nrhs=nr)
     Y64 = y64.cpu().numpy()
-    tol64 = 1e-11 if p <= 5 else 1e-10  # the two bases agree to a few 1e-11 at p = 6..8
+    tol64 = 1e-11 if p <= 5 else (1e-10 if p <= 8 else 1e-8)  # basis agreement by degree
     for r in range(nr):
         ye = A @ X[r]
         assert np.abs(Y64[r] - ye).max() <= tol64 * np.abs(ye).max()
