@@ -889,7 +889,9 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
     });
   } else if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     const int rows = (n % 2 == 0) ? n / 2 : n;
-    const int nt = std::min(1024, (rows + 31) / 32 * 32);
+    // the rows loop strides by the block size; the multi-RHS variants hold up to 92 registers per
+    // thread, so their blocks stay at 512 threads (odd n_ref, e.g. RT_10: 715 rows)
+    const int nt = std::min(nrhs == 1 ? 1024 : 512, (rows + 31) / 32 * 32);
     if (fp32) {
       const size_t sm = (size_t)n * nrhs * sizeof(float);
       launch(h, RIESZ_K_APPLY32, s, [&] {
