@@ -18,12 +18,12 @@
 // by the four producer warps from the gathered X and g.  Ring of NSTAGE slots,
 // mbarriers with bounded waits.
 //
-// Warp roles (320 threads): warp 0 allocates tensor memory and issues the B
-// bulk copies (one lane); warps 1-8 gather X, build the A stages and run the
+// Warp roles (576 threads): warp 0 allocates tensor memory and issues the B
+// bulk copies (one lane); warps 1-16 gather X, build the A stages and run the
 // epilogue: warp w serves row m = 32 (w % 4) + lane (tensor-memory lanes of
-// its quarter) and the K half (w - 1) / 4 of every stage (the two halves of a
-// row in different warps, two producer warps per scheduler); in the epilogue
-// the two warps of a quarter take alternate 16-column chunks.  Warp 9 (one
+// its quarter) and the K part (w - 1) / 4 (4 values) of every stage, four
+// producer warps per scheduler to hide the gathers' latency; in the epilogue
+// the four warps of a quarter take alternate 16-column chunks.  Warp 17 (one
 // lane) issues the MMAs and commits them to the slot's "empty" barrier and,
 // after the last stage, to "done".
 #pragma once
@@ -33,8 +33,9 @@
 namespace riesz {
 namespace dev {
 
-constexpr int TC_NT = 320;
-constexpr int TC_PRODUCERS = 256;  // threads of warps 1-8
+constexpr int TC_PWARPS = 16;                  // producer warps (warps 1..16), four per scheduler
+constexpr int TC_NT = (TC_PWARPS + 2) * 32;    // + the copy warp (0) and the MMA warp (TC_PWARPS + 1)
+constexpr int TC_PRODUCERS = TC_PWARPS * 32;
 constexpr int TC_ROWS = 128;   // M of one MMA (cta_group::1)
 constexpr int TC_KC = 16;      // K per stage (BF16 elements): one MMA K step
 constexpr int TC_KCORE = TC_KC / 8;        // core matrices along K per stage
@@ -121,7 +122,9 @@ __device__ __forceinline__ void tc_split2(float a0, float a1, uint32_t& hi, uint
 }
 
 // X_c[j0 .. j0 + 15] of row (c, r) as FP32 (zero outside the cell's n DOFs, and at Dirichlet DOFs)
-constexpr int TC_KH = TC_KC / 2;  // K values of a stage per producer thread
+constexpr int TC_KQ = TC_PWARPS / 4;  // K parts of a stage (one per producer warp of a lane quarter)
+constexpr int TC_KH = TC_KC / TC_KQ;  // K values of a stage per producer thread
+static_assert(TC_KH == 4, "a producer thread writes 4 BF16 values (8 bytes) of each row per stage");
 __device__ __forceinline__ void tc_load_x(float (&xf)[TC_KH], bool valid, int j0, int n, int nif, int64_t C,
                                           int64_t c, int r, int64_t N, const int32_t* __restrict__ cdofs,
                                           const double* __restrict__ x, const uint8_t* __restrict__ dmask) {
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
   unsigned char* sA = tc_sm;                           // [NS][abytes]
   unsigned char* sB = tc_sm + (size_t)NS * abytes;     // [NS][bstride], this part's rows of each B stage
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)NS * bstride);
-  uint64_t* full_a = bars;                   // [NS], 256 producer arrivals
+  uint64_t* full_a = bars;                   // [NS], TC_PRODUCERS producer arrivals
   uint64_t* full_b = bars + TC_NSTAGE;       // [NS], expect_tx
   uint64_t* empty = bars + 2 * TC_NSTAGE;    // [NS], MMA commit
   uint64_t* done = bars + 3 * TC_NSTAGE;     // accumulator complete
@@ -215,9 +218,9 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
       // no copy may still be landing when the CTA exits (they have all landed in a complete run)
       for (int s = issued > NS ? issued - NS : 0; s < issued; ++s) mbar_wait(&full_b[s % NS], (s / NS) & 1, err);
     }
-  } else if (warp <= 8) {
-    // A producers: row m of the tile, K half kh of each stage; the next chunk of X is gathered while
-    // this one is used
+  } else if (warp <= TC_PWARPS) {
+    // A producers: row m of the tile, K part kh (TC_KH values) of each stage; the next chunk of X is
+    // gathered while this one is used
     const int m = 32 * (warp & 3) + lane, kh = (warp - 1) >> 2;
     const int cl = m % CELLS, rl = m / CELLS;
     const int64_t c = c0 + cl;
@@ -226,8 +229,9 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
     float gq[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) gq[q] = valid ? (float)g[q * C + c] : 0.f;
-    const uint32_t rowoff =
-        (uint32_t)(m >> 3) * TC_SBO + (uint32_t)(m & 7) * 16u + (uint32_t)kh * (TC_KCORE / 2) * 128u;
+    // part kh covers K values kh*4 .. kh*4+3: core matrix kh/2, bytes (kh%2)*8 of the 16-byte core row
+    const uint32_t rowoff = (uint32_t)(m >> 3) * TC_SBO + (uint32_t)(kh >> 1) * 128u + (uint32_t)(m & 7) * 16u +
+                            (uint32_t)(kh & 1) * 8u;
     float xf[TC_KH], xn[TC_KH];
     tc_load_x(xf, valid, kh * TC_KH, n, nif, C, c, r, N, cdofs, x, dmask);
     bool ok = true;
@@ -244,16 +248,11 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
         unsigned char* hi = sA + (size_t)slot * abytes;
         unsigned char* lo = hi + abytes / 2;
         const float gv = gq[q];
-#pragma unroll
-        for (int kc = 0; kc < TC_KCORE / 2; ++kc) {  // the core matrices of this K half
-          uint32_t ph[4], pl[4];
-#pragma unroll
-          for (int e2 = 0; e2 < 4; ++e2)
-            tc_split2(gv * xf[kc * 8 + 2 * e2], gv * xf[kc * 8 + 2 * e2 + 1], ph[e2], pl[e2]);
-          const uint32_t off = rowoff + (uint32_t)kc * 128u;
-          *reinterpret_cast<uint4*>(hi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-          *reinterpret_cast<uint4*>(lo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-        }
+        uint32_t ph[2], pl[2];
+        tc_split2(gv * xf[0], gv * xf[1], ph[0], pl[0]);
+        tc_split2(gv * xf[2], gv * xf[3], ph[1], pl[1]);
+        *reinterpret_cast<uint2*>(hi + rowoff) = make_uint2(ph[0], ph[1]);
+        *reinterpret_cast<uint2*>(lo + rowoff) = make_uint2(pl[0], pl[1]);
         fence_async_smem();
         mbar_arrive(&full_a[slot]);
       }
@@ -304,7 +303,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
 
   // epilogue: warps 1-8 read their quarter's lanes of the accumulator, the two warps of a quarter
   // alternate 16-column chunks
-  if (warp >= 1 && warp <= 8) {
+  if (warp >= 1 && warp <= TC_PWARPS) {
     const int kh = (warp - 1) >> 2;
     const bool ok = mbar_wait(done, 0, err) && !abort_flag;
     tc_fence_after();
@@ -316,7 +315,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
     const bool valid = c < C && r < nrhs;
     const double bad = __longlong_as_double(0x7ff8000000000000ll);
     double* yint = (valid && nif < n) ? y + (int64_t)r * N + cdofs[(int64_t)nif * C + c] - nif : nullptr;
-    for (int i0 = 16 * kh; i0 < NP; i0 += 32) {
+    for (int i0 = 16 * kh; i0 < NP; i0 += 16 * TC_KQ) {
       float v[16];
       tc_ld16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)i0, v);
       if (!valid) continue;
