@@ -4,9 +4,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 Follows Section 3 in the paper's order:
 
-1. the local spaces of Eq. (2.5) (first kind) and Eq. (2.6) (second kind,
-   needed because the H(div) degrees of freedom use the second-kind H(curl)
-   bubbles, Section 3.4.3);
+1. the local spaces of Eq. (2.5) (first kind) and Eq. (2.6) (second kind:
+   NedTwo_p and BDM_p as solution spaces, and NedTwo bubbles inside the
+   H(div) degrees of freedom, Section 3.4.3);
 2. the bubble spaces of Section 3.1 on every subsimplex;
 3. the augmented eigenproblem Eq. (3.10) on the bubble space, dropping the
    kernel of d (the type-II part, Eq. (3.5)) and rescaling the rest so that
@@ -146,7 +146,7 @@ def space(family, p, dim):
 
     family: 'CG' (P_p), 'N1' (first-kind Nedelec, P_{p-1}^d + P_{p-1}^d x x,
     in 2D P_{p-1}^2 + P_{p-1} x^perp), 'N2' (second kind, P_p^d),
-    'RT' (P_{p-1}^3 + P_{p-1} x, 3D only).
+    'RT' (P_{p-1}^3 + P_{p-1} x, 3D only), 'BDM' (second kind, P_p^3, Eq. (2.6)).
     """
     if family == "CG":
         E = Expansion(dim, p, 1)
@@ -155,7 +155,7 @@ def space(family, p, dim):
         E = Expansion(dim, p - 1, 1)
         return E, np.eye(E.n)
     E = Expansion(dim, p, dim)
-    if family == "N2":
+    if family in ("N2", "BDM"):
         return E, np.eye(E.n)
     X, w = quadrature(dim, p + 2)
     Elow = Expansion(dim, p - 1, 1)
@@ -270,7 +270,8 @@ def bubbles(family, p, dim):
         bdim = {"CG": (p - 1) * (p - 2) * (p - 3) // 6,
                 "N1": nsp - 6 * p - 4 * p * (p - 1),
                 "N2": nsp - 6 * (p + 1) - 4 * (p + 1) * (p - 1),
-                "RT": nsp - 4 * p * (p + 1) // 2}[family]
+                "RT": nsp - 4 * p * (p + 1) // 2,
+                "BDM": nsp - 4 * (p + 1) * (p + 2) // 2}[family]
     if bdim == 0:
         return E, np.zeros((E.n, 0))
     Zs = null_basis(C @ U, bdim, ("bubbles", family, p, dim))
@@ -300,6 +301,9 @@ def kernel_dim(family, p, dim):
         return {2: p * (p - 1) // 2, 3: p * (p - 1) * (p - 2) // 6}[dim]
     if family == "RT":  # RT bubbles minus div range (mean-free P_{p-1})
         nb = p * (p + 1) * (p - 1) // 2
+        return nb - (dim_P(3, p - 1) - 1)
+    if family == "BDM":  # BDM bubbles minus div range (mean-free P_{p-1}, as for RT_p)
+        nb = (p + 1) * (p + 2) * (p - 1) // 2
         return nb - (dim_P(3, p - 1) - 1)
     raise ValueError(family)
 
@@ -359,10 +363,13 @@ def eigenbasis(family, p, dim):
 # degrees of freedom (Eqs. (3.14), (3.16), (3.18)) and the dual basis
 # ---------------------------------------------------------------------------
 class RefElement:
-    """Reference element of the paper for space in {'CG', 'N1curl', 'N2curl', 'RT', 'DG'}, degree p.
+    """Reference element of the paper for space in {'CG', 'N1curl', 'N2curl', 'RT', 'BDM', 'DG'}, degree p.
 
-    'N2curl' (second-kind Nedelec) is built only because the H(div) degrees of
-    freedom use its bubbles; the Riesz-map spaces are CG, N1curl and RT.  'DG' is
+    First kind (Eq. (2.5)): CG_p, Ned1_p ('N1curl'), RT_p.  Second kind (Eq. (2.6)): NedTwo_p = P_p^3
+    ('N2curl'), whose gradient moments use the CG_{p+1} eigenbasis (Section 3.4.2), and BDM_p = P_p^3
+    ('BDM'), whose face and curl moments use the NedTwo_{p+1} eigenbasis and whose divergence moments use
+    the eigenbasis of its own interior bubbles (Section 3.4.3).  RT_p's face and curl moments use the
+    NedTwo_p eigenbasis (the second-kind choice of Section 3.4.3).  'DG' is
     X^3 = DG_{p-1} of the complex ending in RT_p (the k = 3 Hodge-Laplace problem):
     the cell DOFs of the abstract definition with k = d, i.e. the mean (1, v)_T and
     the moments (div Phi_{C,j}, v)_T against the divergences of the RT_p interior
@@ -379,11 +386,13 @@ class RefElement:
 
     def __init__(self, space_name, p):
         self.space, self.p = space_name, p
-        fam = {"CG": "CG", "N1curl": "N1", "N2curl": "N2", "RT": "RT", "DG": "DG"}[space_name]
-        self.k = {"CG": 0, "N1curl": 1, "N2curl": 1, "RT": 2, "DG": 3}[space_name]
+        fam = {"CG": "CG", "N1curl": "N1", "N2curl": "N2", "RT": "RT", "BDM": "BDM", "DG": "DG"}[space_name]
+        self.k = {"CG": 0, "N1curl": 1, "N2curl": 1, "RT": 2, "BDM": 2, "DG": 3}[space_name]
         self.fam = fam
         # the H(grad) degree of the complex X^0 -> X^1 used by the H(curl) DOFs
         self.p0 = p + 1 if fam == "N2" else p
+        # the degree of the second-kind H(curl) space X^1 -> X^2 used by the H(div) DOFs
+        self.p1 = p + 1 if fam == "BDM" else p
         E, U = space(fam, p, 3)
         self.E = E
         L, ent = self._functionals(E)
@@ -465,7 +474,7 @@ class RefElement:
                 tv = np.einsum("pnc,cd->pnd", val, B, optimize=True)
                 add((2, f), np.einsum("pjd,pnd,p->jn", gpsi, tv, wf, optimize=True))  # type II
         else:
-            EN, YN, _ = eigenbasis("N2", p, 2)
+            EN, YN, _ = eigenbasis("N2", self.p1, 2)
             _, jN = EN.tab(xi)
             cpsi = np.einsum("pn,nj->pj", dcurl2(jN), YN, optimize=True)
             for f, fr in enumerate(face_frames()):
@@ -494,12 +503,12 @@ class RefElement:
                 gpsi = np.einsum("pnd,nj->pjd", gc[:, :, 0, :], Y, optimize=True)
                 add((3, 0), np.einsum("pjd,pnd,p->jn", gpsi, val, wc, optimize=True))
         else:
-            ER, YR, _ = eigenbasis("RT", p, 3)
+            ER, YR, _ = eigenbasis(self.fam, p, 3)
             if YR.shape[1]:
                 _, jR = ER.tab(Xc)
                 dphi = np.einsum("pn,nj->pj", ddiv(jR), YR, optimize=True)
                 add((3, 0), np.einsum("pj,pn,p->jn", dphi, ddiv(jac), wc, optimize=True))
-            EN, YN, _ = eigenbasis("N2", p, 3)
+            EN, YN, _ = eigenbasis("N2", self.p1, 3)
             if YN.shape[1]:
                 _, jN = EN.tab(Xc)
                 cpsi = np.einsum("pnc,nj->pjc", dcurl3(jN), YN, optimize=True)
