@@ -6,9 +6,11 @@
  * Problem (Eq. (2.8), pure Neumann, Section 7.1): find u in V with
  * beta (u, v) + alpha (d u, d v) = (f, v) for all v in V (alpha = beta = 1 by
  * default: the Riesz map), V one of
- *   RIESZ_H1    CG_p     (d = grad),  Eq. (2.5), k = 0
- *   RIESZ_HCURL Ned1_p   (d = curl),  Eq. (2.5), k = 1
- *   RIESZ_HDIV  RT_p     (d = div),   Eq. (2.5), k = 2
+ *   RIESZ_H1     CG_p     (d = grad),  Eq. (2.5), k = 0
+ *   RIESZ_HCURL  Ned1_p   (d = curl),  Eq. (2.5), k = 1
+ *   RIESZ_HDIV   RT_p     (d = div),   Eq. (2.5), k = 2
+ *   RIESZ_HCURL2 NedTwo_p = P_p^3 (d = curl), Eq. (2.6), k = 1
+ *   RIESZ_HDIV2  BDM_p    = P_p^3 (d = div),  Eq. (2.6), k = 2
  * on an affine tetrahedral mesh, in the paper's orthogonality-promoting basis
  * (Sections 3-4: the dual basis of the DOFs of Eqs. (3.14), (3.16), (3.18)).
  *
@@ -55,6 +57,13 @@ enum { RIESZ_H1 = 0, RIESZ_HCURL = 1, RIESZ_HDIV = 2 };
    riesz_ref_tabulate (no Riesz-map handle: its Riesz map is the diagonal
    mass matrix). */
 enum { RIESZ_L2 = 3 };
+/* The second-kind spaces of Eq. (2.6) (Section 3.4: NedTwo_p's gradient
+   moments use the CG_{p+1} eigenbasis; BDM_p's face and curl moments use the
+   NedTwo_{p+1} eigenbasis).  Everything that depends only on k (pullbacks,
+   geometric factors, patches, W^k) is shared with the first kind; W^k is the
+   same Whitney space (Lemma 4.1), so the lowest-order coarse route uses
+   Ned1_1 / RT_1.  The Hiptmair-Toselli potentials of NedTwo_p are CG_{p+1}. */
+enum { RIESZ_HCURL2 = 4, RIESZ_HDIV2 = 5 };
 
 enum {
   RIESZ_OK = 0,
@@ -219,6 +228,7 @@ void riesz_default_opts(riesz_opts* o);
 
 /* Build the reference element (Sections 3-4, host FP64, cached per (space,p))
    and the mesh maps (entities, DOF numbering, vertex-star patches) of a mesh.
+   space: RIESZ_H1, RIESZ_HCURL, RIESZ_HDIV, RIESZ_HCURL2 or RIESZ_HDIV2.
    verts: host [nverts][3] FP64 coordinates; cells: host [ncells][4] vertex
    indices (any order; each cell's vertices are sorted internally).
    p: 1..10.  opts may be NULL (defaults).  *out receives a new handle. */
@@ -253,8 +263,9 @@ int riesz_patch_count(const riesz_handle* h, int64_t* npatches);
 int riesz_patch_map(const riesz_handle* h, int64_t* offsets, int32_t* dofs);
 
 /* The gradient map of a RIESZ_DECOMP_HT handle (Eq. (5.3)) as a signed CSR
-   list over the Ned1_p interface DOFs: row d lists the CG_p interface DOFs c
-   with the coefficient (+1 or -1) of grad phi^CG_c in Ned1_p DOF d.
+   list over the Ned1_p (NedTwo_p) interface DOFs: row d lists the CG_p
+   (CG_{p+1}) interface DOFs c with the coefficient (+1 or -1) of grad phi^CG_c
+   in DOF d.
    ptr: host [n_interface + 1]; idx, sgn: host [ptr[n_interface]] (query the
    size with idx == NULL).  RIESZ_ERR_INVALID_ARG for other handles. */
 int riesz_ht_gradient_map(const riesz_handle* h, int64_t* ptr, int32_t* idx, float* sgn);
@@ -263,7 +274,8 @@ int riesz_ht_gradient_map(const riesz_handle* h, int64_t* ptr, int32_t* idx, flo
    tetrahedron (edge length 2, centroid 0, vertices (-1,-1/sqrt3,-1/sqrt6),
    (1,-1/sqrt3,-1/sqrt6), (0,2/sqrt3,-1/sqrt6), (0,0,3/sqrt6)).
    vals: host [npts][n_ref][ncomp]; dvals: host [npts][n_ref][dcomp] (grad,
-   curl or div); either may be NULL.  space = RIESZ_L2: DG_{p-1}, n_ref =
+   curl or div); either may be NULL.  space: any of the five Riesz-map spaces
+   (RIESZ_HCURL2 / RIESZ_HDIV2 give NedTwo_p / BDM_p), or RIESZ_L2: DG_{p-1}, n_ref =
    p(p+1)(p+2)/6, ncomp = dcomp = 1, the basis dual to the mean and the
    moments against the divergences of the RT_p interior eigenbasis (values
    1/|T| and div Phi_{C,j}); dvals are zero (d^3 = 0). */

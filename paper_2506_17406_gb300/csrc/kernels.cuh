@@ -1361,6 +1361,113 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_patch_solve_small(
     for (int k = 0; k < nr; ++k) zpatch[k * zstride + pdoff[P] + i] = (double)y[k][i];
 }
 
+// Patches of at most WARP_NB tiles (the edge stars of PAFW_1 and Hiptmair-Toselli, Eqs. (6.19), (6.24)),
+// FP32 factors, up to 8 right-hand sides: one warp per patch, no block-level synchronisation.  The
+// right-hand sides are interleaved in shared memory (y[i][8], two 16-byte broadcasts per factor entry);
+// each 32x32 tile is read straight from global memory into registers (32 coalesced 128-byte loads in
+// flight per warp), the forward sweep from the tile-transposed copies LT / DT, the backward sweep from
+// the tiles as stored, so every read is a row of 32 consecutive floats.
+//   forward:  t_I = b_I - sum_{J<I} L_IJ y_J,  y_I = Dinv_I t_I
+//   backward: x_I = Dinv_I^T y_I,  y_J -= L_IJ^T x_I  (J < I)
+constexpr int WARP_NB = 8;
+constexpr int WARP_SWEEP_WARPS = 8;
+__host__ __device__ constexpr size_t warp_sweep_smem() { return sizeof(float) * (WARP_NB * 32 * 8 + 32 * 8); }
+
+__device__ __forceinline__ void warp_tile_fma(const float (&a)[32], const float* __restrict__ v, float (&acc)[8]) {
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    const float4 v0 = *reinterpret_cast<const float4*>(v + c * 8);
+    const float4 v1 = *reinterpret_cast<const float4*>(v + c * 8 + 4);
+    acc[0] = fmaf(a[c], v0.x, acc[0]);
+    acc[1] = fmaf(a[c], v0.y, acc[1]);
+    acc[2] = fmaf(a[c], v0.z, acc[2]);
+    acc[3] = fmaf(a[c], v0.w, acc[3]);
+    acc[4] = fmaf(a[c], v1.x, acc[4]);
+    acc[5] = fmaf(a[c], v1.y, acc[5]);
+    acc[6] = fmaf(a[c], v1.z, acc[6]);
+    acc[7] = fmaf(a[c], v1.w, acc[7]);
+  }
+}
+
+__global__ void __launch_bounds__(WARP_SWEEP_WARPS * 32) k_patch_sweep_warp8(
+    int npatch, const int32_t* __restrict__ pn, const int64_t* __restrict__ pdoff, const int64_t* __restrict__ pfoff,
+    const int64_t* __restrict__ pdoff_inv, const int64_t* __restrict__ pmoff, const int32_t* __restrict__ meta,
+    const int32_t* __restrict__ pdofs, const float* __restrict__ Lall, const float* __restrict__ Dall,
+    const float* __restrict__ LTall, const float* __restrict__ DTall, const double* __restrict__ r,
+    double* __restrict__ zpatch, int64_t N, int64_t zstride, int nr) {
+  extern __shared__ __align__(16) unsigned char warp_sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* y = reinterpret_cast<float*>(warp_sm + warp * warp_sweep_smem());  // [nb * 32][8]
+  float* tv = y + WARP_NB * 32 * 8;                                          // [32][8]
+  const int P = blockIdx.x * WARP_SWEEP_WARPS + warp;
+  if (P >= npatch) return;
+  const int n = pn[P];
+  const int nb = (n + 31) / 32;
+  const int32_t* tix = meta + pmoff[P];
+  const float* L = Lall + pfoff[P];
+  const float* LT = LTall + pfoff[P];
+  const float* Dv = Dall + pdoff_inv[P];
+  const float* DT = DTall + pdoff_inv[P];
+  const int32_t* dofs = pdofs + pdoff[P];
+  for (int i = lane; i < nb * 32; i += 32) {
+    const int d = i < n ? dofs[i] : -1;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) y[i * 8 + k] = (d >= 0 && k < nr) ? (float)r[k * N + d] : 0.f;
+  }
+  __syncwarp();
+  float a[32];
+  for (int I = 0; I < nb; ++I) {
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int J = 0; J < I; ++J) {
+      const int ti = tix[I * nb + J];
+      if (ti < 0) continue;
+      const float* At = LT + (int64_t)ti * 1024;  // At[c][r] = L_IJ[r][c]
+#pragma unroll
+      for (int c = 0; c < 32; ++c) a[c] = At[c * 32 + lane];
+      warp_tile_fma(a, y + J * 32 * 8, acc);
+    }
+    float* yI = y + (I * 32 + lane) * 8;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tv[lane * 8 + k] = yI[k] - acc[k];
+    const float* Dt = DT + (int64_t)I * 1024;  // Dt[c][r] = Dinv_I[r][c]
+#pragma unroll
+    for (int c = 0; c < 32; ++c) a[c] = Dt[c * 32 + lane];
+    __syncwarp();
+    float s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    warp_tile_fma(a, tv, s8);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) yI[k] = s8[k];
+    __syncwarp();
+  }
+  for (int I = nb - 1; I >= 0; --I) {
+    const float* Dd = Dv + (int64_t)I * 1024;  // Dinv_I[r][c]
+#pragma unroll
+    for (int rr = 0; rr < 32; ++rr) a[rr] = Dd[rr * 32 + lane];
+    float x8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    warp_tile_fma(a, y + I * 32 * 8, x8);
+    __syncwarp();
+    float* yI = y + (I * 32 + lane) * 8;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) yI[k] = x8[k];
+    __syncwarp();
+    for (int J = 0; J < I; ++J) {
+      const int ti = tix[I * nb + J];
+      if (ti < 0) continue;
+      const float* At = L + (int64_t)ti * 1024;  // L_IJ[r][c], lane = c
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) a[rr] = At[rr * 32 + lane];
+      float s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      warp_tile_fma(a, y + I * 32 * 8, s8);
+      float* yJ = y + (J * 32 + lane) * 8;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) yJ[k] -= s8[k];
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32)
+    for (int k = 0; k < nr; ++k) zpatch[k * zstride + pdoff[P] + i] = (double)y[i * 8 + k];
+}
+
 // z = diag(A_II)^{-1} r on the interior, sum of patch results on the interface.
 __global__ void k_precond_gather(int64_t N, int64_t nifd, const int64_t* __restrict__ ptr,
                                  const int32_t* __restrict__ pos, const double* __restrict__ zpatch, int64_t zstride,

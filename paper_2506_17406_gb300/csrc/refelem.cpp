@@ -387,7 +387,7 @@ Mat d_gram(const Expansion& E, int ncomp, int family) {
 }
 
 // --- local spaces ----------------------------------------------------------
-enum Family { CG = 0, N1 = 1, N2 = 2, RT = 3 };
+enum Family { CG = 0, N1 = 1, N2 = 2, RT = 3, BDM = 4 };  // BDM: P_p^3 with normal-trace bubbles
 
 struct FieldSpace {
   Expansion E;
@@ -400,7 +400,7 @@ FieldSpace make_space(int fam, int p, int dim) {
   S.E = Expansion(dim, p);
   S.ncomp = (fam == CG) ? 1 : dim;
   const int N = S.ncomp * S.E.n;
-  if (fam == CG || fam == N2) {
+  if (fam == CG || fam == N2 || fam == BDM) {  // the full P_p (P_p^dim) of Eq. (2.6)
     S.U = Mat::eye(N);
     return S;
   }
@@ -467,6 +467,7 @@ int bubble_dim(int fam, int p, int dim) {
     const int n = 3 * dimP(3, p);
     return dim == 2 ? (p + 1) * (p - 1) : n - 6 * (p + 1) - 4 * (p + 1) * (p - 1);
   }
+  if (fam == BDM) return 3 * dimP(3, p) - 4 * dimP(2, p);  // P_p^3 minus the degree-p normal traces
   return p * (p + 1) * (p - 1) / 2;  // RT, 3D
 }
 
@@ -474,7 +475,8 @@ int kernel_dim(int fam, int p, int dim) {
   if (fam == CG) return 0;
   if (fam == N1) return dimP(dim, p - dim - 1);  // grad of CG_p bubbles
   if (fam == N2) return dimP(dim, p + 1 - dim - 1);  // grad of CG_{p+1} bubbles
-  return bubble_dim(RT, p, 3) - (dimP(3, p - 1) - 1);  // RT minus mean-free P_{p-1}
+  // RT / BDM bubbles minus their divergences, the mean-free P_{p-1}
+  return bubble_dim(fam, p, 3) - (dimP(3, p - 1) - 1);
 }
 
 // Columns: L2-orthonormal bubble basis in the space's coefficients.
@@ -554,14 +556,15 @@ Mat bubble_basis(const FieldSpace& S, int fam, int p, int dim) {
         for (int c = 0; c < 3; ++c) X.push_back(TET[a][c] + B[c][0] * xi0 + B[c][1] * xi1);
       }
       Tab T = tabulate_expansion(S.E, 3, F.npt(), X.data());
-      const int nproj = (fam == RT) ? 1 : 2;
+      const bool normal = fam == RT || fam == BDM;
+      const int nproj = normal ? 1 : 2;
       for (int m = 0; m < nproj; ++m)
         for (int j = 0; j < E2.n; ++j) {
           std::vector<double> row(N, 0.0);
           for (int i = 0; i < F.npt(); ++i) {
             const double f2 = F.w[i] * fv[(size_t)i * E2.n + j];
             for (int c = 0; c < 3; ++c) {
-              const double dirc = (fam == RT) ? nrm[c] : B[c][m];
+              const double dirc = normal ? nrm[c] : B[c][m];
               for (int k = 0; k < S.E.n; ++k) row[c * S.E.n + k] += f2 * dirc * T.v[(size_t)i * S.E.n + k];
             }
           }
@@ -614,7 +617,7 @@ EigenBasis eigenbasis(int fam, int p, int dim) {
     EB.Y = Mat(N, 0);
     return EB;
   }
-  const int dfam = (fam == CG) ? 0 : (fam == RT ? 2 : 1);
+  const int dfam = (fam == CG) ? 0 : ((fam == RT || fam == BDM) ? 2 : 1);
   Mat G = d_gram(EB.S.E, EB.S.ncomp, dfam);
   Mat K = matmul_tn(Z, matmul(G, Z));
   for (int i = 0; i < nb; ++i)
@@ -741,10 +744,17 @@ void eig_tab(const EigenBasis& EB, int dfam, int npt, const double* x, std::vect
 // ---------------------------------------------------------------------------
 // the reference element
 // ---------------------------------------------------------------------------
-static void build_element(RefElement& R, int space, int p) {
+// kind 1: CG_p, Ned1_p, RT_p (Eq. (2.5)); kind 2: NedTwo_p, BDM_p (Eq. (2.6)).  The H(curl) gradient
+// moments use the CG eigenbasis of degree p0 (p, or p + 1 for NedTwo_p: its X^0 is CG_{p+1}); the H(div)
+// face and curl moments use the NedTwo eigenbasis of degree p1 (p, or p + 1 for BDM_p), Section 3.4.
+static void build_element(RefElement& R, int space, int p, int kind) {
   R.space = space;
   R.p = p;
-  const int fam = space == H1 ? CG : (space == HCURL ? N1 : RT);
+  R.kind = kind;
+  const bool second = kind == 2 && space != H1;
+  const int fam = space == H1 ? CG : (space == HCURL ? (second ? N2 : N1) : (second ? BDM : RT));
+  const int p0 = (space == HCURL && second) ? p + 1 : p;
+  const int p1 = (space == HDIV && second) ? p + 1 : p;
   FieldSpace S = make_space(fam, p, 3);
   R.E = S.E;
   R.ncomp = S.ncomp;
@@ -772,7 +782,7 @@ static void build_element(RefElement& R, int space, int p) {
   }
   // ----- edges
   if (space != HDIV) {
-    const EigenBasis& EE = eig_cached(CG, p, 1);
+    const EigenBasis& EE = eig_cached(CG, space == HCURL ? p0 : p, 1);
     std::vector<double> ev, ed;
     int nd;
     eig_tab(EE, 0, G.npt(), G.x.data(), ev, ed, nd);
@@ -824,14 +834,14 @@ static void build_element(RefElement& R, int space, int p) {
       eig_tab(A, 0, F.npt(), F.x.data(), av, ad, nda);
       na = A.Y.n;
     } else if (space == HCURL) {
-      const EigenBasis& A = eig_cached(N1, p, 2);
+      const EigenBasis& A = eig_cached(fam, p, 2);
       eig_tab(A, 1, F.npt(), F.x.data(), av, ad, nda);
       na = A.Y.n;
-      const EigenBasis& B = eig_cached(CG, p, 2);
+      const EigenBasis& B = eig_cached(CG, p0, 2);
       eig_tab(B, 0, F.npt(), F.x.data(), bv, bd, ndb);
       nb = B.Y.n;
     } else {
-      const EigenBasis& A = eig_cached(N2, p, 2);
+      const EigenBasis& A = eig_cached(N2, p1, 2);
       eig_tab(A, 1, F.npt(), F.x.data(), av, ad, nda);
       na = A.Y.n;
     }
@@ -906,17 +916,17 @@ static void build_element(RefElement& R, int space, int p) {
       n1 = A.Y.n;
       if (n1) eig_tab(A, 0, C.npt(), C.x.data(), v1, d1, nd1);
     } else if (space == HCURL) {
-      const EigenBasis& A = eig_cached(N1, p, 3);
+      const EigenBasis& A = eig_cached(fam, p, 3);
       n1 = A.Y.n;
       if (n1) eig_tab(A, 1, C.npt(), C.x.data(), v1, d1, nd1);
-      const EigenBasis& B = eig_cached(CG, p, 3);
+      const EigenBasis& B = eig_cached(CG, p0, 3);
       n2 = B.Y.n;
       if (n2) eig_tab(B, 0, C.npt(), C.x.data(), v2, d2, nd2);
     } else {
-      const EigenBasis& A = eig_cached(RT, p, 3);
+      const EigenBasis& A = eig_cached(fam, p, 3);
       n1 = A.Y.n;
       if (n1) eig_tab(A, 2, C.npt(), C.x.data(), v1, d1, nd1);
-      const EigenBasis& B = eig_cached(N2, p, 3);
+      const EigenBasis& B = eig_cached(N2, p1, 3);
       n2 = B.Y.n;
       if (n2) eig_tab(B, 1, C.npt(), C.x.data(), v2, d2, nd2);
     }
@@ -1039,12 +1049,14 @@ static void build_cross(RefElement& R, const RefElement& cg) {
   }
 }
 
-const RefElement& reference_element(int space, int p) {
-  static OnceCache<std::pair<int, int>, RefElement> cache;
-  if (p < 1 || p > 12 || space < 0 || space > 2) throw std::runtime_error("reference_element: unsupported (space, p)");
-  return cache.get(std::make_pair(space, p), [&] {
+const RefElement& reference_element(int space, int p, int kind) {
+  static OnceCache<std::tuple<int, int, int>, RefElement> cache;
+  if (p < 1 || p > 12 || space < 0 || space > 2 || kind < 1 || kind > 2)
+    throw std::runtime_error("reference_element: unsupported (space, p, kind)");
+  if (space == H1) kind = 1;  // CG_p is both kinds
+  return cache.get(std::make_tuple(space, p, kind), [&] {
     auto R = std::make_shared<RefElement>();
-    build_element(*R, space, p);
+    build_element(*R, space, p, kind);
     const RefElement& cg = (space == H1) ? *R : reference_element(H1, p);
     build_cross(*R, cg);
     return R;

@@ -32,6 +32,7 @@ Rule simplex_rule(int dim, int npts_per_dir);
 // A reference element: the dual basis of the paper's DOFs and its tables.
 struct RefElement {
   int space = 0, p = 0, nref = 0, ninterior = 0;
+  int kind = 1;                      // 1: first kind (Eq. (2.5)), 2: second kind (Eq. (2.6))
   int ncomp = 1, dcomp = 3;  // value / exterior-derivative components
   int per_entity[4] = {0, 0, 0, 0};  // DOFs per vertex, edge, face, interior
   Expansion E;                       // expansion (scalar for H1, vector otherwise)
@@ -48,8 +49,9 @@ struct RefElement {
   void tabulate(int npt, const double* x, double* vals, double* dvals) const;
 };
 
-// Cached per (space, p).  Throws std::runtime_error on failure.
-const RefElement& reference_element(int space, int p);
+// Cached per (space, p, kind).  space H1, HCURL or HDIV; kind 1 gives CG_p, Ned1_p, RT_p
+// (Eq. (2.5)), kind 2 NedTwo_p and BDM_p (Eq. (2.6); CG_p for H1).  Throws std::runtime_error on failure.
+const RefElement& reference_element(int space, int p, int kind = 1);
 
 // Reference tables of the coupling (d phi^{k-1}_j, phi^k_i) of the Hodge-Laplace
 // problem (k = 1: CG_p -> Ned1_p, k = 2: Ned1_p -> RT_p): 6 matrices [j][i]

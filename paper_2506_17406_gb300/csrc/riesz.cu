@@ -66,12 +66,14 @@ struct DBuf {  // device buffer owned by the handle
 }  // namespace
 
 struct riesz_handle {
-  int space = 0, p = 0;
+  int space = 0, p = 0;  // space: k (0, 1, 2)
+  int kind = 1;          // 1: CG_p / Ned1_p / RT_p (Eq. (2.5)), 2: NedTwo_p / BDM_p (Eq. (2.6))
   riesz_opts opts;
   const RefElement* ref = nullptr;
-  const RefElement* refcg = nullptr;
+  const RefElement* refcg = nullptr;  // CG_p: the load's source field
   std::vector<double> verts;
   MeshMaps mesh, meshcg;
+  MeshMaps meshpot;  // CG_{p+1}: the Hiptmair-Toselli potentials of NedTwo_p (kind 2 only)
   int nif = 0;  // interface DOFs per cell
   // host-side plans
   std::vector<int64_t> sc_ptr;   // interface DOF -> positions in Ycell
@@ -579,14 +581,15 @@ void plan_edge_stars(riesz_handle& h, int take_e, int take_f) {
 // Hiptmair-Toselli decomposition of Eq. (6.19) for H(curl): per edge L the
 // Whitney DOF of L and the type-I DOFs of every face containing L (the
 // interface DOFs of X^{1,I} on the star of L; inside a face the type-I DOFs
-// come first), and the gradient map between CG_p and Ned1_p interface DOFs:
+// come first), and the gradient map between CG_p and Ned1_p interface DOFs
+// (CG_{p+1} and NedTwo_p for the second kind, whose X^0 is CG_{p+1}):
 // the gradient of the CG vertex function v has Whitney coefficient +1 on edges
 // ending at v and -1 on edges starting at v; the gradient of the m-th CG edge
 // (face) function is the m-th type-II Ned1 function of that edge (face)
 // (Eq. (5.3), Lemma 4.3).
 void plan_ht(riesz_handle& h) {
   const MeshMaps& M = h.mesh;
-  const MeshMaps& Mc = h.meshcg;
+  const MeshMaps& Mc = h.kind == 2 ? h.meshpot : h.meshcg;
   const int ne_d = M.per_entity[1], nf_d = M.per_entity[2];
   const int ce = Mc.per_entity[1], cf = Mc.per_entity[2];
   const int nfI = nf_d - cf;
@@ -978,6 +981,19 @@ void op_patch_solves(riesz_handle& h, const double* r, int nrhs, cudaStream_t s)
             h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p, h.d_L64.p,
             h.d_D64.p, r, h.d_zpatch.p, h.d_flags.p);
       });
+    return;
+  }
+  if (f32 && nbmax <= dev::WARP_NB) {  // patches of at most 8 tiles (edge stars): one warp per patch
+    const unsigned grid = (unsigned)((npatch + dev::WARP_SWEEP_WARPS - 1) / dev::WARP_SWEEP_WARPS);
+    for (int r0 = 0; r0 < nrhs; r0 += 8) {
+      const int nr = std::min(8, nrhs - r0);
+      launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
+        dev::k_patch_sweep_warp8<<<grid, dev::WARP_SWEEP_WARPS * 32, dev::WARP_SWEEP_WARPS * dev::warp_sweep_smem(),
+                                   s>>>(npatch, h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p,
+                                        h.d_meta.p, h.d_pdofs.p, h.d_L32.p, h.d_D32.p, h.d_L32T.p, h.d_D32T.p,
+                                        r + (int64_t)r0 * N, h.d_zpatch.p + (int64_t)r0 * zstride, N, zstride, nr);
+      });
+    }
     return;
   }
   if (f32) {  // up to 8 right-hand sides per launch on the bulk-copy pipeline
@@ -2287,6 +2303,7 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     const int nbm = h.p_n.empty() ? 1 : (h.p_n[0] + 31) / 32;
     raise_smem_limit(dev::k_patch_sweep8<SWEEP_SLOTS_F32>, sweep8_smem(nbm));
     raise_smem_limit(dev::k_patch_solve_small<double>, dev::SMALL_WARPS * dev::small_warp_smem<double>());
+    raise_smem_limit(dev::k_patch_sweep_warp8, dev::WARP_SWEEP_WARPS * dev::warp_sweep_smem());
     raise_smem_limit(dev::k_patch_solve_small<float>, dev::SMALL_WARPS * dev::small_warp_smem<float>());
   }
   h.d_pdioff.upload(h.p_dioff, s);
@@ -2532,12 +2549,17 @@ void check_dev(const riesz_handle* h) {
 // have beta = 0.
 riesz_handle* create_handle(int space, int p, int64_t nverts, const double* verts, int64_t ncells,
                             const int64_t* cells, const riesz_opts& opts, bool internal, bool apply_only = false) {
-  need(space >= 0 && space <= 2, "space must be RIESZ_H1, RIESZ_HCURL or RIESZ_HDIV");
-  need(p >= 1 && p <= 10, "degree p must be in 1..10");
+  need(space >= RIESZ_H1 && space <= RIESZ_HDIV2 && space != RIESZ_L2,
+       "space must be RIESZ_H1, RIESZ_HCURL, RIESZ_HDIV, RIESZ_HCURL2 or RIESZ_HDIV2");
+  const int kind = space >= RIESZ_HCURL2 ? 2 : 1;
+  if (kind == 2) space -= RIESZ_HCURL2 - RIESZ_HCURL;  // k of the second-kind space
+  // internal handles: the CG_{p+1} potentials of NedTwo_p reach degree 11
+  need(p >= 1 && p <= (internal ? 11 : 10), "degree p must be in 1..10");
   need(verts && cells && nverts > 0 && ncells > 0, "empty mesh", RIESZ_ERR_BAD_MESH);
   auto t0 = std::chrono::steady_clock::now();
   auto h = std::make_unique<riesz_handle>();
   h->space = space;
+  h->kind = kind;
   h->p = p;
   h->opts = opts;
   need(h->opts.rtol > 0 && h->opts.maxit >= 0 && h->opts.nrhs_max >= 1 && h->opts.nrhs_max <= 64, "bad options");
@@ -2569,10 +2591,12 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
     need(std::isfinite(verts[i]), "non-finite vertex coordinate", RIESZ_ERR_BAD_MESH);
   h->verts.assign(verts, verts + nverts * 3);
   try {
-    h->ref = &reference_element(space, p);
+    h->ref = &reference_element(space, p, kind);
     h->refcg = &reference_element(RIESZ_H1, p);
     h->mesh = build_mesh(*h->ref, nverts, ncells, cells);
     h->meshcg = (space == RIESZ_H1) ? h->mesh : build_mesh(*h->refcg, nverts, ncells, cells);
+    if (kind == 2 && h->opts.decomposition == RIESZ_DECOMP_HT)
+      h->meshpot = build_mesh(reference_element(RIESZ_H1, p + 1), nverts, ncells, cells);
   } catch (const Err&) {
     throw;
   } catch (const std::exception& e) {
@@ -2585,7 +2609,7 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
   if (h->opts.decomposition == RIESZ_DECOMP_EDGE_STAR) plan_edge_stars(*h, 0, h->mesh.per_entity[2]);
   build_plans(*h);
   plan_coarse(*h);
-  if (h->coarse_on && h->coarse_sparse) {  // W^k = the lowest-order space: its own p = 1 handle
+  if (h->coarse_on && h->coarse_sparse) {  // W^k = the lowest-order space (Whitney forms, Lemma 4.1, for either kind): its own p = 1 handle
     riesz_opts co = h->opts;
     co.coarse = 0;
     co.form = RIESZ_FORM_ADDITIVE;
@@ -2599,7 +2623,7 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
     h->caux = create_handle(space, 1, nverts, verts, ncells, cells, co, true);
     if (h->caux->N() < (int64_t)h->c_w.size()) throw Err(RIESZ_ERR_INTERNAL, "lowest-order handle too small");
   }
-  if (h->ht) {  // potential problems: CG_p on the same mesh with a = beta (grad, grad), vertex stars
+  if (h->ht) {  // potential problems: CG_p (CG_{p+1} for NedTwo_p) on the same mesh, a = beta (grad, grad), vertex stars
     riesz_opts ao = h->opts;
     ao.alpha = h->opts.beta;
     ao.beta = 0.0;
@@ -2608,7 +2632,7 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
     ao.decomposition = RIESZ_DECOMP_VERTEX_STAR;
     ao.apply_precision = RIESZ_PREC_FP64;
     ao.apply_mode = RIESZ_APPLY_ELEMENT;
-    h->aux = create_handle(RIESZ_H1, p, nverts, verts, ncells, cells, ao, true);
+    h->aux = create_handle(RIESZ_H1, kind == 2 ? p + 1 : p, nverts, verts, ncells, cells, ao, true);
   }
   h->opts.dirichlet_vertices = nullptr;  // the caller's array is read during creation only
   h->setup_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -2744,7 +2768,7 @@ int riesz_ht_gradient_map(const riesz_handle* h, int64_t* ptr, int32_t* idx, flo
 
 int riesz_ref_tabulate(int space, int p, int64_t npts, const double* pts, double* vals, double* dvals) {
   return guarded([&] {
-    need(space >= 0 && space <= 3 && p >= 1 && p <= 10, "bad space or degree");
+    need(space >= 0 && space <= RIESZ_HDIV2 && p >= 1 && p <= 10, "bad space or degree");
     need(npts >= 0 && (npts == 0 || pts != nullptr), "bad points");
     if (space == RIESZ_L2) {  // DG_{p-1}: values only, d = 0
       const int n = dg_dim(p);
@@ -2752,7 +2776,10 @@ int riesz_ref_tabulate(int space, int p, int64_t npts, const double* pts, double
       if (dvals) std::fill(dvals, dvals + (size_t)npts * n, 0.0);
       return;
     }
-    reference_element(space, p).tabulate((int)npts, pts, vals, dvals);
+    if (space >= RIESZ_HCURL2)
+      reference_element(space - (RIESZ_HCURL2 - RIESZ_HCURL), p, 2).tabulate((int)npts, pts, vals, dvals);
+    else
+      reference_element(space, p).tabulate((int)npts, pts, vals, dvals);
   });
 }
 

@@ -13,8 +13,10 @@ import numpy as np
 
 from . import build as _build
 
-H1, HCURL, HDIV, L2 = 0, 1, 2, 3
-SPACES = {"CG": H1, "H1": H1, "N1curl": HCURL, "HCURL": HCURL, "RT": HDIV, "HDIV": HDIV, "DG": L2, "L2": L2}
+H1, HCURL, HDIV, L2, HCURL2, HDIV2 = 0, 1, 2, 3, 4, 5
+# first kind (Eq. (2.5)): CG_p, Ned1_p, RT_p; second kind (Eq. (2.6)): NedTwo_p, BDM_p
+SPACES = {"CG": H1, "H1": H1, "N1curl": HCURL, "HCURL": HCURL, "RT": HDIV, "HDIV": HDIV, "DG": L2, "L2": L2,
+          "N2curl": HCURL2, "HCURL2": HCURL2, "BDM": HDIV2, "HDIV2": HDIV2}
 PREC_FP64, PREC_FP32, PREC_BF16X3 = 0, 1, 2
 APPLY_MATRIX_FREE, APPLY_ELEMENT = 0, 1
 LOOP_HOST, LOOP_GRAPH = 0, 1
@@ -156,9 +158,10 @@ def riesz_ref_tabulate(space, p, pts):
     space = SPACES.get(space, space)
     pts = np.ascontiguousarray(pts, dtype=np.float64)
     ncomp = 1 if space in (H1, L2) else 3
-    dcomp = 1 if space in (HDIV, L2) else 3
+    dcomp = 1 if space in (HDIV, HDIV2, L2) else 3
     nref = {H1: (p + 1) * (p + 2) * (p + 3) // 6, HCURL: p * (p + 2) * (p + 3) // 2,
-            HDIV: p * (p + 1) * (p + 3) // 2, L2: p * (p + 1) * (p + 2) // 6}[space]
+            HDIV: p * (p + 1) * (p + 3) // 2, L2: p * (p + 1) * (p + 2) // 6,
+            HCURL2: (p + 1) * (p + 2) * (p + 3) // 2, HDIV2: (p + 1) * (p + 2) * (p + 3) // 2}[space]
     vals = np.zeros((pts.shape[0], nref, ncomp))
     dvals = np.zeros((pts.shape[0], nref, dcomp))
     _check(lib.riesz_ref_tabulate(space, p, pts.shape[0], _ptr(pts), _ptr(vals), _ptr(dvals)))

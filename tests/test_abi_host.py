@@ -51,8 +51,25 @@ def test_reference_basis_matches_oracle(lib, space, p):
     assert np.abs(d - do).max() <= tol * np.abs(do).max()
 
 
+@pytest.mark.parametrize("space,p", [(s, p) for s in ("N2curl", "BDM") for p in range(1, 9)] +
+                         [("N2curl", 9), ("N2curl", 10)])
+def test_second_kind_basis_matches_oracle(lib, space, p):
+    """NedTwo_p and BDM_p (Eq. (2.6)) from the library equal the oracle's at points of the reference cell;
+    same tolerance argument as for the first kind (measured: at most 2e-11 up to p = 8, 6e-10 at p = 9, 10).
+    BDM_9 and BDM_10 (about a minute of host eigensolves on each side) are checked through the GPU apply
+    against the oracle's assembled matrix (tests/test_gpu_second_kind.py)."""
+    tol = 1e-10 if p <= 8 else 1e-8
+    X, _ = quadrature(3, 4)
+    v, d = rz.riesz_ref_tabulate(space, p, X)
+    vo, do = reference_element(space, p).tabulate(X)
+    assert v.shape == vo.shape == (X.shape[0], (p + 1) * (p + 2) * (p + 3) // 2, 3)
+    assert np.abs(v - vo).max() <= tol * np.abs(vo).max()
+    assert np.abs(d - do).max() <= tol * np.abs(do).max()
+
+
 @pytest.mark.parametrize("space,p,n", [("CG", 3, 4), ("CG", 4, 2), ("N1curl", 3, 3), ("N1curl", 1, 2),
-                                       ("RT", 2, 3), ("RT", 4, 2)])
+                                       ("RT", 2, 3), ("RT", 4, 2), ("N2curl", 2, 3), ("N2curl", 3, 2),
+                                       ("BDM", 1, 3), ("BDM", 3, 2)])
 def test_dof_and_patch_maps_bit_exact(lib, space, p, n):
     verts, cells = kuhn_mesh(n, 0.1, 5)
     # present the cells with scrambled vertex order: both sides must sort them
