@@ -20,15 +20,12 @@
 //
 // Warp roles (576 threads): warp 0 allocates tensor memory and issues the B
 // bulk copies (one lane); warps 1-16 gather X, build the A stages and run the
-// epilogue.  As producers, warp w builds the 8-row group w - 1 of every stage:
-// lane l serves row 8 (w - 1) + (l % 8) and the K part l / 8 (4 values), so a
-// warp's 8-byte stores cover 256 contiguous bytes (no bank conflicts); after
-// every TC_GROUP stages each warp fences its stores for the async proxy and one
-// lane arrives on the stages' "full" barriers.  In the epilogue warp w serves
-// row m = 32 (w % 4) + lane (the tensor-memory lanes of its quarter) and the
-// four warps of a quarter take alternate 16-column chunks.  Warp 17 (one lane)
-// issues the MMAs and commits them to the slot's "empty" barrier and, after
-// the last stage, to "done".
+// epilogue: warp w serves row m = 32 (w % 4) + lane (tensor-memory lanes of
+// its quarter) and the K part (w - 1) / 4 (4 values) of every stage, four
+// producer warps per scheduler to hide the gathers' latency; in the epilogue
+// the four warps of a quarter take alternate 16-column chunks.  Warp 17 (one
+// lane) issues the MMAs and commits them to the slot's "empty" barrier and,
+// after the last stage, to "done".
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -39,10 +36,6 @@ namespace dev {
 constexpr int TC_PWARPS = 16;                  // producer warps (warps 1..16), four per scheduler
 constexpr int TC_NT = (TC_PWARPS + 2) * 32;    // + the copy warp (0) and the MMA warp (TC_PWARPS + 1)
 constexpr int TC_PRODUCERS = TC_PWARPS * 32;
-constexpr int TC_GROUP = 2;    // stages written between two fences / arrivals of a producer warp
-// a producer waits for slot s - NS to drain before writing stage s; that stage's group is complete
-// (published) as long as a group is no longer than the ring, whose smallest size is 2
-static_assert(TC_GROUP >= 1 && TC_GROUP <= 2, "a producer group must fit in the smallest ring");
 constexpr int TC_ROWS = 128;   // M of one MMA (cta_group::1)
 constexpr int TC_KC = 16;      // K per stage (BF16 elements): one MMA K step
 constexpr int TC_KCORE = TC_KC / 8;        // core matrices along K per stage
@@ -168,7 +161,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
   unsigned char* sA = tc_sm;                           // [NS][abytes]
   unsigned char* sB = tc_sm + (size_t)NS * abytes;     // [NS][bstride], this part's rows of each B stage
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)NS * bstride);
-  uint64_t* full_a = bars;                   // [NS], one arrival per producer warp
+  uint64_t* full_a = bars;                   // [NS], TC_PRODUCERS producer arrivals
   uint64_t* full_b = bars + TC_NSTAGE;       // [NS], expect_tx
   uint64_t* empty = bars + 2 * TC_NSTAGE;    // [NS], MMA commit
   uint64_t* done = bars + 3 * TC_NSTAGE;     // accumulator complete
@@ -186,7 +179,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < NS; ++s) {
-      mbar_init(&full_a[s], TC_PWARPS);
+      mbar_init(&full_a[s], TC_PRODUCERS);
       mbar_init(&full_b[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -228,7 +221,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
   } else if (warp <= TC_PWARPS) {
     // A producers: row m of the tile, K part kh (TC_KH values) of each stage; the next chunk of X is
     // gathered while this one is used
-    const int m = 8 * (warp - 1) + (lane & 7), kh = lane >> 3;
+    const int m = 32 * (warp & 3) + lane, kh = (warp - 1) >> 2;
     const int cl = m % CELLS, rl = m / CELLS;
     const int64_t c = c0 + cl;
     const int r = r0 + rl;
@@ -247,9 +240,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         const int s = jc * Q + q, slot = s % NS, use = s / NS;
-        // every lane waits; the warp goes on only if all of them saw the slot free
-        const bool free_slot = use == 0 || mbar_wait(&empty[slot], (use - 1) & 1, err);
-        if (!__all_sync(0xffffffffu, free_slot)) {
+        if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1, err)) {
           ok = false;
           abort_flag = 1;
           break;
@@ -262,12 +253,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
         tc_split2(gv * xf[2], gv * xf[3], ph[1], pl[1]);
         *reinterpret_cast<uint2*>(hi + rowoff) = make_uint2(ph[0], ph[1]);
         *reinterpret_cast<uint2*>(lo + rowoff) = make_uint2(pl[0], pl[1]);
-        if ((s + 1) % TC_GROUP == 0 || s + 1 == nst) {  // publish the group's stages
-          fence_async_smem();
-          __syncwarp();
-          if (lane == 0)
-            for (int t = s - s % TC_GROUP; t <= s; ++t) mbar_arrive(&full_a[t % NS]);
-        }
+        fence_async_smem();
+        mbar_arrive(&full_a[slot]);
       }
 #pragma unroll
       for (int e = 0; e < TC_KH; ++e) xf[e] = xn[e];
