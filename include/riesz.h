@@ -423,6 +423,16 @@ int riesz_profile_read(riesz_handle* h, double* ms, int64_t* counts);
    2 lowest-order PCG steps.  out: host [5]. */
 int riesz_tuning(const riesz_handle* h, int* out);
 
+/* The shape of the FP32 patch sweeps for several right-hand sides over
+   patches of 33..256 DOFs (the edge stars of Eqs. (6.19) and (6.24)), picked
+   at riesz_setup_device by timing each candidate on the handle's own factors
+   (autotune = 1; kept per device and patch structure for the life of the
+   process): *shape = 0 one CTA per patch streaming the factor tiles through a
+   bulk-copy ring, 4 or 8 one warp per patch with that many warps per block,
+   -1 when the choice does not apply (FP64 factors, one right-hand side,
+   larger or smaller patches).  *timed (may be NULL) = candidates timed. */
+int riesz_sweep_shape(const riesz_handle* h, int* shape, int* timed);
+
 /* Timings (ms) and sizes of the last setup / solve:
    out[0] setup host ms, out[1] setup device ms, out[2] device bytes held,
    out[3] patch factor bytes, out[4] last solve iterations (rhs 0),

@@ -1370,7 +1370,7 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_patch_solve_small(
 //   forward:  t_I = b_I - sum_{J<I} L_IJ y_J,  y_I = Dinv_I t_I
 //   backward: x_I = Dinv_I^T y_I,  y_J -= L_IJ^T x_I  (J < I)
 constexpr int WARP_NB = 8;
-constexpr int WARP_SWEEP_WARPS = 8;
+constexpr int WARP_SWEEP_WARPS = 8;  // most warps (patches) per block; the launch picks 4 or 8
 __host__ __device__ constexpr size_t warp_sweep_smem() { return sizeof(float) * (WARP_NB * 32 * 8 + 32 * 8); }
 
 __device__ __forceinline__ void warp_tile_fma(const float (&a)[32], const float* __restrict__ v, float (&acc)[8]) {
@@ -1399,7 +1399,7 @@ __global__ void __launch_bounds__(WARP_SWEEP_WARPS * 32) k_patch_sweep_warp8(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* y = reinterpret_cast<float*>(warp_sm + warp * warp_sweep_smem());  // [nb * 32][8]
   float* tv = y + WARP_NB * 32 * 8;                                          // [32][8]
-  const int P = blockIdx.x * WARP_SWEEP_WARPS + warp;
+  const int P = blockIdx.x * (int)(blockDim.x >> 5) + warp;
   if (P >= npatch) return;
   const int n = pn[P];
   const int nb = (n + 31) / 32;
@@ -2432,11 +2432,18 @@ __global__ void k_mixed_elem(int64_t C, int n0, int n1, int Q, const double* __r
 }
 
 // One CTA per cell: gather sigma_T and u_T, then
-//   X^k rows i:      y1_i = sum_j K_T[j][i] u_j + sum_j Be_T[j][i] sigma_j   (threads over i)
-//   X^{k-1} rows j:  y0_j = -sum_l M_T[l][j] sigma_l + sum_i Be_T[j][i] u_i  (threads over j, then a
-//                    warp per j for the transposed coupling, lanes over i, fixed shuffle tree)
+//   X^k rows i:      y1_i = sum_j K_T[j][i] u_j + sum_j Be_T[j][i] sigma_j
+//   X^{k-1} rows j:  y0_j = -sum_l M_T[l][j] sigma_l + sum_i Be_T[j][i] u_i
+// The first two sums run with every thread busy: each row's j (l) range is cut into a fixed number of
+// equal parts (threads / rows), one thread per (row, part), the partial sums added in part order; the
+// transposed coupling runs a warp per j, lanes over i, fixed shuffle tree.  Deterministic.
 // Interface rows go to the cell slots Ycell (summed per DOF by k_gather_iface),
 // interior rows straight to y (each interior DOF belongs to one cell).
+__host__ __device__ inline int hodge_split(int nt, int n) { return n >= nt ? 1 : nt / n; }
+inline size_t hodge_apply_smem(int nt, int n0, int n1) {
+  return (size_t)(2 * n0 + n1 + hodge_split(nt, n1) * n1 + hodge_split(nt, n0) * n0) * sizeof(double);
+}
+
 __global__ void __launch_bounds__(NT) k_hodge_apply(int64_t C, int n0, int n1, int nif0, int nif1,
                                                     const double* __restrict__ Me, const double* __restrict__ Ke,
                                                     const double* __restrict__ Be, const int32_t* __restrict__ cd0,
@@ -2445,33 +2452,54 @@ __global__ void __launch_bounds__(NT) k_hodge_apply(int64_t C, int n0, int n1, i
                                                     double* __restrict__ y1, double* __restrict__ Yc0,
                                                     double* __restrict__ Yc1) {
   extern __shared__ double smh[];
-  double* xs0 = smh;        // [n0]
-  double* xs1 = smh + n0;   // [n1]
-  double* ys0 = xs1 + n1;   // [n0]
+  const int nt = blockDim.x;
+  const int S1 = hodge_split(nt, n1), S0 = hodge_split(nt, n0);  // threads per output row (fixed split)
+  double* xs0 = smh;           // [n0]
+  double* xs1 = smh + n0;      // [n1]
+  double* ys0 = xs1 + n1;      // [n0]
+  double* p1 = ys0 + n0;       // [S1][n1] partial sums of the X^k rows
+  double* p0 = p1 + S1 * n1;   // [S0][n0] partial sums of the mass rows
   const int64_t c = blockIdx.x;
-  for (int t = threadIdx.x; t < n0; t += blockDim.x) xs0[t] = x0[cd0[(int64_t)t * C + c]];
-  for (int t = threadIdx.x; t < n1; t += blockDim.x) xs1[t] = x1[cd1[(int64_t)t * C + c]];
+  for (int t = threadIdx.x; t < n0; t += nt) xs0[t] = x0[cd0[(int64_t)t * C + c]];
+  for (int t = threadIdx.x; t < n1; t += nt) xs1[t] = x1[cd1[(int64_t)t * C + c]];
   __syncthreads();
   const double* K = Ke ? Ke + c * (int64_t)n1 * n1 : nullptr;
   const double* M = Me + c * (int64_t)n0 * n0;
   const double* B = Be + c * (int64_t)n0 * n1;
-  for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+  // y1_i = sum_j K_ji x1_j + sum_j B_ji x0_j: the concatenated j range split into S1 equal parts
+  const int nK = Ke ? n1 : 0, L1 = nK + n0;
+  for (int t = threadIdx.x; t < S1 * n1; t += nt) {
+    const int i = t % n1, part = t / n1;
+    const int j0 = (int)((int64_t)L1 * part / S1), j1 = (int)((int64_t)L1 * (part + 1) / S1);
     double a = 0.0;
-    if (Ke)  // K_3 = 0 (k = 3): no d-stiffness block
-      for (int j = 0; j < n1; ++j) a = fma(K[(int64_t)j * n1 + i], xs1[j], a);
-    for (int j = 0; j < n0; ++j) a = fma(B[(int64_t)j * n1 + i], xs0[j], a);
+    for (int j = j0; j < min(j1, nK); ++j) a = fma(K[(int64_t)j * n1 + i], xs1[j], a);
+    for (int j = max(j0, nK); j < j1; ++j) a = fma(B[(int64_t)(j - nK) * n1 + i], xs0[j - nK], a);
+    p1[part * n1 + i] = a;
+  }
+  // -(M x0)_j, the l range split into S0 parts
+  for (int t = threadIdx.x; t < S0 * n0; t += nt) {
+    const int j = t % n0, part = t / n0;
+    const int l0 = (int)((int64_t)n0 * part / S0), l1 = (int)((int64_t)n0 * (part + 1) / S0);
+    double a = 0.0;
+    for (int l = l0; l < l1; ++l) a = fma(M[(int64_t)l * n0 + j], xs0[l], a);
+    p0[part * n0 + j] = a;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n1; i += nt) {
+    double a = 0.0;
+    for (int part = 0; part < S1; ++part) a += p1[part * n1 + i];
     if (i >= nif1)
       y1[cd1[(int64_t)i * C + c]] = a;
     else
       Yc1[(int64_t)i * C + c] = a;
   }
-  for (int j = threadIdx.x; j < n0; j += blockDim.x) {
+  for (int j = threadIdx.x; j < n0; j += nt) {
     double a = 0.0;
-    for (int l = 0; l < n0; ++l) a = fma(M[(int64_t)l * n0 + j], xs0[l], a);
+    for (int part = 0; part < S0; ++part) a += p0[part * n0 + j];
     ys0[j] = -a;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nt >> 5;
   for (int j = warp; j < n0; j += nw) {
     double a = 0.0;
     for (int i = lane; i < n1; i += 32) a = fma(B[(int64_t)j * n1 + i], xs1[i], a);
@@ -2479,7 +2507,7 @@ __global__ void __launch_bounds__(NT) k_hodge_apply(int64_t C, int n0, int n1, i
     if (lane == 0) ys0[j] += a;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n0; j += blockDim.x) {
+  for (int j = threadIdx.x; j < n0; j += nt) {
     if (j >= nif0)
       y0[cd0[(int64_t)j * C + c]] = ys0[j];
     else
@@ -2602,6 +2630,24 @@ __global__ void __launch_bounds__(NT) k_mr_dot(int64_t n, const double* __restri
     minres_op(op, s0, m);
     *ticket = 0u;
   }
+}
+
+// Control step of the device-driven MINRES loop (after the (w, z) reduction of an iteration):
+// ctl[0] iterations so far, ctl[1] the iteration limit, ctl[2] the reason to stop (0 go on,
+// 1 non-finite value, 2 converged: |phibar| <= rtol beta_1 or beta_{k+1} = 0, 4 iteration limit,
+// 5 preconditioner not positive definite).  Sets the WHILE condition, and the IF condition of the
+// second iteration of the loop body when `gate` is set.
+__global__ void k_mr_control(cudaGraphConditionalHandle loop_cond, cudaGraphConditionalHandle gate_cond, int gate,
+                             const double* __restrict__ m, double rtol, int* __restrict__ ctl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int it = ctl[0] + 1;
+  ctl[0] = it;
+  const bool nonfinite = m[6] != 0.0 || !isfinite(m[M_PHIBAR]);
+  const bool conv = fabs(m[M_PHIBAR]) <= rtol * m[M_BETA1] || m[M_BNEXT] == 0.0;
+  const int reason = nonfinite ? 1 : (m[M_RAW] < 0.0 ? 5 : (conv ? 2 : (it >= ctl[1] ? 4 : 0)));
+  ctl[2] = reason;
+  if (gate) cudaGraphSetConditional(gate_cond, reason == 0 ? 1u : 0u);
+  cudaGraphSetConditional(loop_cond, reason == 0 ? 1u : 0u);
 }
 
 // w -= beta_k v_prev (when v_prev != nullptr)

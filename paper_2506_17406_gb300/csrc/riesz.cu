@@ -154,6 +154,10 @@ struct riesz_handle {
   DBuf<int32_t> d_caux;
   int multi_group = 8;  // right-hand sides per k_patch_solve_multi launch
   int chol_ctas = 0;    // resident k_cholesky CTAs per SM picked by the autotuner (0: no limit)
+  // FP32 sweeps of several right-hand sides over patches of at most 8 tiles: 0 one CTA per patch
+  // (bulk-copy ring, k_patch_sweep8), 4 or 8: one warp per patch with that many warps per block
+  int sweep_shape = 8;
+  int sweep_tuned = 0;  // candidates the autotuner timed
   int chol_tuned = 0;   // candidates the autotuner timed
   int chol_split = 1;   // CTAs per patch in the factorisation (1, or a 2-CTA cluster)
   DBuf<int32_t> d_cells, d_cdofs, d_sc_pos, d_pn, d_pdofs, d_pz_pos, d_pb_cell, d_pb_ent, d_cgdofs, d_meta;
@@ -983,15 +987,16 @@ void op_patch_solves(riesz_handle& h, const double* r, int nrhs, cudaStream_t s)
       });
     return;
   }
-  if (f32 && nbmax <= dev::WARP_NB) {  // patches of at most 8 tiles (edge stars): one warp per patch
-    const unsigned grid = (unsigned)((npatch + dev::WARP_SWEEP_WARPS - 1) / dev::WARP_SWEEP_WARPS);
+  if (f32 && nbmax <= dev::WARP_NB && h.sweep_shape > 0) {  // patches of at most 8 tiles: one warp per patch
+    const int wpb = h.sweep_shape;
+    const unsigned grid = (unsigned)((npatch + wpb - 1) / wpb);
     for (int r0 = 0; r0 < nrhs; r0 += 8) {
       const int nr = std::min(8, nrhs - r0);
       launch(h, RIESZ_K_PATCH_SOLVE, s, [&] {
-        dev::k_patch_sweep_warp8<<<grid, dev::WARP_SWEEP_WARPS * 32, dev::WARP_SWEEP_WARPS * dev::warp_sweep_smem(),
-                                   s>>>(npatch, h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p,
-                                        h.d_meta.p, h.d_pdofs.p, h.d_L32.p, h.d_D32.p, h.d_L32T.p, h.d_D32T.p,
-                                        r + (int64_t)r0 * N, h.d_zpatch.p + (int64_t)r0 * zstride, N, zstride, nr);
+        dev::k_patch_sweep_warp8<<<grid, wpb * 32, wpb * dev::warp_sweep_smem(), s>>>(
+            npatch, h.d_pn.p, h.d_pdoff.p, h.d_pfoff.p, h.d_pdioff.p, h.d_pmoff.p, h.d_meta.p, h.d_pdofs.p,
+            h.d_L32.p, h.d_D32.p, h.d_L32T.p, h.d_D32T.p, r + (int64_t)r0 * N, h.d_zpatch.p + (int64_t)r0 * zstride,
+            N, zstride, nr);
       });
     }
     return;
@@ -2191,6 +2196,60 @@ void tune_cholesky(riesz_handle& h, cudaStream_t s) {
   device_compute(h, s, false);  // factors (and their FP32 copies) with the chosen residency
 }
 
+// Autotuner of the multi-RHS FP32 sweep shape for patches of at most 8 tiles (the edge stars of
+// PAFW_1 and Hiptmair-Toselli): one CTA per patch with the bulk-copy ring (k_patch_sweep8), or one
+// warp per patch with 4 or 8 warps per block (k_patch_sweep_warp8).  Each candidate sweeps 8
+// right-hand sides (the residual workspace, zeroed) over the handle's own factors, once untimed and
+// twice between CUDA events; the fastest is kept per device and patch structure.  Every candidate
+// computes the same patch solutions up to the FP32 summation order within a tile row.
+void tune_sweeps(riesz_handle& h, cudaStream_t s) {
+  const int npatch = (int)h.p_n.size();
+  h.sweep_tuned = 0;
+  h.sweep_shape = 8;
+  const int nr = std::min(8, h.opts.nrhs_max);
+  if (h.opts.autotune != 1 || !npatch || nr < 2 || h.opts.precond_precision != RIESZ_PREC_FP32 ||
+      (h.p_n[0] + 31) / 32 > dev::WARP_NB || (h.p_n[0] + 31) / 32 <= dev::SMALL_NB)
+    return;
+  static std::mutex mu;
+  static std::map<std::array<int64_t, 5>, std::array<int, 2>> done;  // shape, candidates timed
+  const std::array<int64_t, 5> key{h.device, npatch, (int64_t)h.factor_entries, (int64_t)h.p_dofs.size(), nr};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find(key);
+    if (it != done.end()) {
+      h.sweep_shape = it->second[0];
+      h.sweep_tuned = it->second[1];
+      return;
+    }
+  }
+  CK(cudaMemsetAsync(h.d_r.p, 0, (size_t)nr * h.N() * sizeof(double), s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 0.f;
+  int best_shape = 8;
+  for (int shape : {8, 4, 0}) {
+    h.sweep_shape = shape;
+    op_patch_solves(h, h.d_r.p, nr, s);
+    CK(cudaEventRecord(e0, s));
+    for (int rep = 0; rep < 2; ++rep) op_patch_solves(h, h.d_r.p, nr, s);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    ++h.sweep_tuned;
+    if (h.sweep_tuned == 1 || ms < best) {
+      best = ms;
+      best_shape = shape;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h.sweep_shape = best_shape;
+  std::lock_guard<std::mutex> lk(mu);
+  done[key] = {best_shape, h.sweep_tuned};
+}
+
 // Round-to-nearest-even BF16 bits of an FP32 value (finite inputs).
 uint16_t bf16_bits(float f) {
   uint32_t u;
@@ -2411,6 +2470,7 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
                           (int)cudaSharedmemCarveoutMaxShared));
   device_compute(h, s, false);  // the potential problems were factored by their own setup above
   tune_cholesky(h, s);
+  tune_sweeps(h, s);
   h.on_device = true;
 }
 
@@ -2990,6 +3050,17 @@ int riesz_tuning(const riesz_handle* h, int* out) {
   });
 }
 
+int riesz_sweep_shape(const riesz_handle* h, int* shape, int* timed) {
+  return guarded([&] {
+    check_dev(h);
+    need(shape != nullptr, "null argument");
+    const bool applies = h->opts.precond_precision == RIESZ_PREC_FP32 && h->opts.nrhs_max > 1 && !h->p_n.empty() &&
+                         (h->p_n[0] + 31) / 32 <= dev::WARP_NB && (h->p_n[0] + 31) / 32 > dev::SMALL_NB;
+    *shape = applies ? h->sweep_shape : -1;
+    if (timed) *timed = h->sweep_tuned;
+  });
+}
+
 int riesz_profile(riesz_handle* h, int enable) {
   return guarded([&] {
     need(h != nullptr, "null handle");
@@ -3146,20 +3217,34 @@ struct riesz_hodge {
   double last_relres = 0.0, last_phi = 0.0;
   DBuf<double> d_R, d_gB, d_jacB, d_Be;                   // coupling tables, factors, element matrices
   DBuf<double> v, vp, u, w, z, d1, d2, d_m, d_part;       // MINRES vectors and scalars
+  DBuf<double> xw;                                          // working copy of x (device-driven loop)
   DBuf<unsigned> d_ticket;
+  DBuf<int> d_ctl;                                          // loop control: iterations, limit, reason
   double* h_m = nullptr;
+  int* h_ctl = nullptr;
+  int loop = RIESZ_LOOP_GRAPH;
+  // device-driven loop: a CUDA graph WHILE { iteration, control, IF { iteration, control } } (two
+  // iterations per pass so that the Lanczos and direction buffers return to their roles), its
+  // capture stream, and the kernels one iteration launches
+  cudaGraphExec_t g_loop = nullptr;
+  cudaStream_t cap = nullptr;
+  int64_t g_iter_launches = 0;
   // the second block preconditioner runs on its own stream beside the first
   cudaStream_t s1 = nullptr;
   cudaEvent_t ev_f = nullptr, ev_j = nullptr;
   ~riesz_hodge() {
+    if (g_loop) cudaGraphExecDestroy(g_loop);
+    if (cap) cudaStreamDestroy(cap);
+    if (h_ctl) cudaFreeHost(h_ctl);
     if (h_m) cudaFreeHost(h_m);
     if (s1) cudaStreamDestroy(s1);
     if (ev_f) cudaEventDestroy(ev_f);
     if (ev_j) cudaEventDestroy(ev_j);
     for (auto* b : {&d_R, &d_gB, &d_jacB, &d_Be, &v, &vp, &u, &w, &z, &d1, &d2, &d_m, &d_part, &d_dg_mhat, &d_dg_X,
-                    &d_dg_dinv})
+                    &d_dg_dinv, &xw})
       b->free();
     d_ticket.free();
+    d_ctl.free();
     d_dg_cd.free();
     delete P0;
     delete P1;
@@ -3207,7 +3292,7 @@ void hodge_apply(riesz_hodge& H, const double* x, double* y, cudaStream_t s) {
   riesz_handle* K = H.Kh;  // null for k = 3
   const int64_t C = M.C();
   const int n0 = M.mesh.nref, n1 = K ? K->mesh.nref : H.n_dg;
-  const size_t sm = (size_t)(2 * n0 + n1) * sizeof(double);
+  const size_t sm = dev::hodge_apply_smem(dev::NT, n0, n1);
   dev::k_hodge_apply<<<(unsigned)C, dev::NT, sm, s>>>(
       C, n0, n1, M.nif, K ? K->nif : 0, M.d_Ae.p, K ? K->d_Ae.p : nullptr, H.d_Be.p, M.d_cdofs.p,
       K ? K->d_cdofs.p : H.d_dg_cd.p, x, x + H.n0, y, y + H.n0, M.d_Ycell.p, K ? K->d_Ycell.p : nullptr);
@@ -3254,24 +3339,147 @@ void hodge_read(riesz_hodge& H, cudaStream_t s) {
   CK(cudaStreamSynchronize(s));
 }
 
+// One MINRES iteration k: w = A u_k - beta_k v_{k-1} - alpha_k v_k (v_0 = 0), z = P^{-1} w,
+// beta_{k+1} and the Givens step, then d_k, x and the next Lanczos vectors (v_{k+1} written over
+// v_{k-1}, d_k over d_{k-2}).
+void hodge_iteration(riesz_hodge& H, double* x, double* vcur, double* vprev, double* dd1, double* dd2,
+                     cudaStream_t s) {
+  const int64_t N = H.N();
+  const unsigned nb = nblk(N, 256);
+  hodge_apply(H, H.u.p, H.w.p, s);
+  dev::k_mr_sub_beta<<<nb, 256, 0, s>>>(N, H.d_m.p, H.w.p, vprev);
+  ++H.launches;
+  hodge_dot(H, H.u.p, H.w.p, 1, s);
+  dev::k_mr_sub_alpha<<<nb, 256, 0, s>>>(N, H.d_m.p, H.w.p, vcur);
+  hodge_precond(H, H.w.p, H.z.p, s);
+  hodge_dot(H, H.w.p, H.z.p, 2, s);
+  dev::k_mr_update<<<nb, 256, 0, s>>>(N, H.d_m.p, x, H.u.p, dd1, dd2, vprev, H.w.p, H.z.p);
+  CK(cudaGetLastError());
+  H.launches += 2;
+}
+
+// launch counters of the Hodge handle and of every block handle (captured work is counted per pass)
+struct HodgeCounters {
+  std::vector<std::pair<int64_t*, int64_t>> c;
+  explicit HodgeCounters(riesz_hodge& H) {
+    c.push_back({&H.launches, H.launches});
+    for (riesz_handle* x : {H.P0, H.P1, H.Mh, H.Kh})
+      if (x)
+        for (riesz_handle* y : {x, x->aux, x->caux})
+          if (y) c.push_back({&y->launches, y->launches});
+  }
+  int64_t delta() const {
+    int64_t d = 0;
+    for (auto& e : c) d += *e.first - e.second;
+    return d;
+  }
+  void restore() {
+    for (auto& e : c) *e.first = e.second;
+  }
+};
+
+bool hodge_profiling(const riesz_hodge& H) {
+  for (riesz_handle* x : {H.P0, H.P1, H.Mh, H.Kh})
+    if (x && (x->prof || (x->aux && x->aux->prof))) return true;
+  return false;
+}
+
+// The device-driven loop's graph, built once per handle (every buffer it touches is handle-owned).
+void hodge_ensure_graph(riesz_hodge& H) {
+  if (H.g_loop) return;
+  if (!H.cap) CK(cudaStreamCreateWithFlags(&H.cap, cudaStreamNonBlocking));
+  cudaStream_t cs = H.cap;
+  HodgeCounters cnt(H);
+  cudaGraph_t G;
+  CK(cudaGraphCreate(&G, 0));
+  auto captured = [&](cudaGraph_t target, auto&& fn, std::vector<cudaGraphNode_t>* leaves) {
+    CK(cudaStreamBeginCaptureToGraph(cs, target, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+      fn();
+      if (leaves) {
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t* d = nullptr;
+        size_t nd = 0;
+        CK(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &d, nullptr, &nd));
+        leaves->assign(d, d + nd);
+      }
+    } catch (...) {
+      cudaGraph_t g;
+      cudaStreamEndCapture(cs, &g);
+      cudaGetLastError();
+      throw;
+    }
+    cudaGraph_t g;
+    CK(cudaStreamEndCapture(cs, &g));
+  };
+  try {
+    cudaGraphConditionalHandle hw;
+    CK(cudaGraphConditionalHandleCreate(&hw, G, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    CK(cudaGraphAddNode(&wn, G, nullptr, nullptr, 0, &wp));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    cudaGraphConditionalHandle hi;
+    CK(cudaGraphConditionalHandleCreate(&hi, body, 0u, cudaGraphCondAssignDefault));
+    std::vector<cudaGraphNode_t> deps;
+    captured(body, [&] {
+      hodge_iteration(H, H.xw.p, H.v.p, H.vp.p, H.d1.p, H.d2.p, cs);
+      dev::k_mr_control<<<1, 32, 0, cs>>>(hw, hi, 1, H.d_m.p, H.rtol, H.d_ctl.p);
+      CK(cudaGetLastError());
+      ++H.launches;
+    }, &deps);
+    H.g_iter_launches = cnt.delta();
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hi;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t in;
+    CK(cudaGraphAddNode(&in, body, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &ip));
+    captured(ip.conditional.phGraph_out[0], [&] {
+      hodge_iteration(H, H.xw.p, H.vp.p, H.v.p, H.d2.p, H.d1.p, cs);
+      dev::k_mr_control<<<1, 32, 0, cs>>>(hw, hi, 0, H.d_m.p, H.rtol, H.d_ctl.p);
+      CK(cudaGetLastError());
+      ++H.launches;
+    }, nullptr);
+  } catch (...) {
+    cnt.restore();
+    cudaGraphDestroy(G);
+    throw;
+  }
+  cnt.restore();  // captured, not launched
+  H.g_loop = instantiate(G);
+}
+
 // Preconditioned MINRES (Paige-Saunders): Lanczos on P^{-1} A in the P-inner
 // product, the tridiagonal reduced by Givens rotations as it grows; stops when
 // the P^{-1}-norm of the residual, |phibar|, drops below rtol times its initial
-// value, then reports the true relative residual ||b - A x|| / ||b||.
+// value, then reports the true relative residual ||b - A x|| / ||b||.  The
+// iterations run either from the host (one synchronisation per iteration) or
+// in the device-driven graph loop; both enqueue the same kernels in the same
+// order and give bitwise the same iterates.
 int hodge_minres(riesz_hodge& H, const double* b, double* x, cudaStream_t s, int* iters, double* relres) {
   const int64_t N = H.N();
   const unsigned nb = nblk(N, 256);
-  double* vcur = H.v.p;
-  double* vprev = H.vp.p;
-  double* dd1 = H.d1.p;
-  double* dd2 = H.d2.p;
-  hodge_apply(H, x, H.w.p, s);
+  const bool graph = H.loop == RIESZ_LOOP_GRAPH && !hodge_profiling(H);
+  double* xs = x;  // the iterate: the caller's x, or the handle's working copy for the graph loop
+  if (graph) {
+    if (!H.xw.p) H.xw.alloc((size_t)N);
+    CK(cudaMemcpyAsync(H.xw.p, x, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    xs = H.xw.p;
+  }
+  hodge_apply(H, xs, H.w.p, s);
   dev::k_mr_residual<<<nb, 256, 0, s>>>(N, b, H.w.p);
   hodge_precond(H, H.w.p, H.z.p, s);
   hodge_dot(H, H.w.p, H.z.p, 0, s);
-  dev::k_mr_scale<<<nb, 256, 0, s>>>(N, H.d_m.p, H.w.p, H.z.p, vcur, H.u.p);
-  CK(cudaMemsetAsync(dd1, 0, N * sizeof(double), s));
-  CK(cudaMemsetAsync(dd2, 0, N * sizeof(double), s));
+  dev::k_mr_scale<<<nb, 256, 0, s>>>(N, H.d_m.p, H.w.p, H.z.p, H.v.p, H.u.p);
+  CK(cudaMemsetAsync(H.d1.p, 0, N * sizeof(double), s));
+  CK(cudaMemsetAsync(H.d2.p, 0, N * sizeof(double), s));
+  CK(cudaMemsetAsync(H.vp.p, 0, N * sizeof(double), s));  // v_0 = 0
   H.launches += 2;
   hodge_read(H, s);
   if (H.h_m[6] != 0.0) throw Err(RIESZ_ERR_NONFINITE, "non-finite right-hand side or preconditioner");
@@ -3280,31 +3488,48 @@ int hodge_minres(riesz_hodge& H, const double* b, double* x, cudaStream_t s, int
   int it = 0;
   int rc = RIESZ_OK;
   double phi = beta1;
-  while (beta1 > 0.0) {
-    if (it >= H.maxit) {
+  if (graph && beta1 > 0.0) {
+    if (H.maxit == 0) {
       rc = RIESZ_ERR_NOT_CONVERGED;
-      break;
+    } else {
+      hodge_ensure_graph(H);
+      H.h_ctl[0] = 0;
+      H.h_ctl[1] = H.maxit;
+      H.h_ctl[2] = 0;
+      CK(cudaMemcpyAsync(H.d_ctl.p, H.h_ctl, 4 * sizeof(int), cudaMemcpyHostToDevice, s));
+      CK(cudaGraphLaunch(H.g_loop, s));
+      CK(cudaMemcpyAsync(H.h_ctl, H.d_ctl.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      hodge_read(H, s);
+      it = H.h_ctl[0];
+      H.launches += (int64_t)it * H.g_iter_launches;
+      const int reason = H.h_ctl[2];
+      if (reason == 1) throw Err(RIESZ_ERR_NONFINITE, "non-finite value in the MINRES recurrence");
+      if (reason == 5) throw Err(RIESZ_ERR_INTERNAL, "block preconditioner is not positive definite");
+      if (reason == 4) rc = RIESZ_ERR_NOT_CONVERGED;
+      phi = std::fabs(H.h_m[dev::M_PHIBAR]);
     }
-    ++it;
-    hodge_apply(H, H.u.p, H.w.p, s);
-    if (it > 1) {
-      dev::k_mr_sub_beta<<<nb, 256, 0, s>>>(N, H.d_m.p, H.w.p, vprev);
-      ++H.launches;
+    // an odd number of iterations leaves the roles of the two buffer pairs swapped; x is unaffected
+    CK(cudaMemcpyAsync(x, H.xw.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    double* vcur = H.v.p;
+    double* vprev = H.vp.p;
+    double* dd1 = H.d1.p;
+    double* dd2 = H.d2.p;
+    while (beta1 > 0.0) {
+      if (it >= H.maxit) {
+        rc = RIESZ_ERR_NOT_CONVERGED;
+        break;
+      }
+      ++it;
+      hodge_iteration(H, x, vcur, vprev, dd1, dd2, s);
+      std::swap(dd1, dd2);      // d_k is now in dd1, d_{k-1} in dd2
+      std::swap(vprev, vcur);   // v_{k+1} was written over v_{k-1}
+      hodge_read(H, s);
+      if (H.h_m[6] != 0.0) throw Err(RIESZ_ERR_NONFINITE, "non-finite value in the MINRES recurrence");
+      if (H.h_m[dev::M_RAW] < 0.0) throw Err(RIESZ_ERR_INTERNAL, "block preconditioner is not positive definite");
+      phi = std::fabs(H.h_m[dev::M_PHIBAR]);
+      if (phi <= H.rtol * beta1 || H.h_m[dev::M_BNEXT] == 0.0) break;
     }
-    hodge_dot(H, H.u.p, H.w.p, 1, s);
-    dev::k_mr_sub_alpha<<<nb, 256, 0, s>>>(N, H.d_m.p, H.w.p, vcur);
-    hodge_precond(H, H.w.p, H.z.p, s);
-    hodge_dot(H, H.w.p, H.z.p, 2, s);
-    dev::k_mr_update<<<nb, 256, 0, s>>>(N, H.d_m.p, x, H.u.p, dd1, dd2, vprev, H.w.p, H.z.p);
-    CK(cudaGetLastError());
-    H.launches += 2;
-    std::swap(dd1, dd2);      // d_k is now in dd1, d_{k-1} in dd2
-    std::swap(vprev, vcur);   // v_{k+1} was written over v_{k-1}
-    hodge_read(H, s);
-    if (H.h_m[6] != 0.0) throw Err(RIESZ_ERR_NONFINITE, "non-finite value in the MINRES recurrence");
-    if (H.h_m[dev::M_RAW] < 0.0) throw Err(RIESZ_ERR_INTERNAL, "block preconditioner is not positive definite");
-    phi = std::fabs(H.h_m[dev::M_PHIBAR]);
-    if (phi <= H.rtol * beta1 || H.h_m[dev::M_BNEXT] == 0.0) break;
   }
   // true residual
   hodge_apply(H, x, H.w.p, s);
@@ -3347,6 +3572,8 @@ int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t
     H->gamma = gamma;
     H->rtol = o.rtol;
     H->maxit = o.maxit;
+    need(o.loop == RIESZ_LOOP_HOST || o.loop == RIESZ_LOOP_GRAPH, "bad loop");
+    H->loop = o.loop;
     riesz_opts b = o;
     b.nrhs_max = 1;
     b.loop = RIESZ_LOOP_HOST;
@@ -3440,7 +3667,7 @@ int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t
       H->d_dg_X.upload(X, s);
       H->d_dg_dinv.alloc((size_t)H->n1);
     }
-    const size_t sm = (size_t)(2 * n0 + n1) * sizeof(double);
+    const size_t sm = dev::hodge_apply_smem(dev::NT, n0, n1);
     if (sm > 48 * 1024) raise_smem_limit(dev::k_hodge_apply, sm);
     for (auto* v : {&H->v, &H->vp, &H->u, &H->w, &H->z, &H->d1, &H->d2}) v->alloc((size_t)H->N());
     H->d_m.alloc(16);
@@ -3448,7 +3675,9 @@ int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t
     H->d_part.alloc(dev::RED_BLOCKS);
     H->d_ticket.alloc(1);
     CK(cudaMemsetAsync(H->d_ticket.p, 0, sizeof(unsigned), s));
+    H->d_ctl.alloc(4);
     CK(cudaMallocHost((void**)&H->h_m, 16 * sizeof(double)));
+    CK(cudaMallocHost((void**)&H->h_ctl, 4 * sizeof(int)));
     hodge_geometry(*H, s);
     CK(cudaStreamSynchronize(s));
     *out = H.release();

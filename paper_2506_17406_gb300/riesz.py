@@ -296,8 +296,11 @@ class Riesz:
     def tuning(self):
         out = np.zeros(5, dtype=np.int32)
         _check(self.lib.riesz_tuning(self.h, _ptr(out)))
+        shape, timed = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.riesz_sweep_shape(self.h, ctypes.byref(shape), ctypes.byref(timed)))
         return {"cholesky_ctas_per_sm": int(out[0]), "candidates_timed": int(out[1]), "coarse_dofs": int(out[2]),
-                "cholesky_ctas_per_patch": int(out[3]), "coarse_mode": int(out[4])}
+                "cholesky_ctas_per_patch": int(out[3]), "coarse_mode": int(out[4]),
+                "sweep_shape": shape.value, "sweep_candidates_timed": timed.value}
 
     # ----- device calls -----
     def setup_device(self, stream=None):

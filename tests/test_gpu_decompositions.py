@@ -119,6 +119,32 @@ def test_edge_star_precond_several_rhs_matches_oracle(p, n, nr):
         assert np.abs(Zh[k] - ze).max() <= tol * np.abs(ze).max(), k
 
 
+def test_sweep_shape_autotuner():
+    """The multi-RHS FP32 sweep shape for edge stars is picked by timing the candidates on the handle's own
+    factors (one CTA per patch, or one warp per patch with 4 or 8 warps per block); without tuning the
+    8-warp shape runs.  Both handles' preconditioners match the oracle's."""
+    verts, cells, md, A = setup_rt(5, 2)
+    P = asm.TwoLevelPreconditioner(A, md, asm.edge_star_dofs(md))
+    R = normal_coeffs((8, md.ndofs), 3)
+    for autotune in (1, 0):
+        s = rz.Riesz("RT", 5, verts, cells, decomposition=rz.DECOMP_EDGE_STAR, precond_precision=rz.PREC_FP32,
+                     nrhs_max=8, autotune=autotune)
+        t = s.tuning()
+        if autotune:
+            assert t["sweep_shape"] in (0, 4, 8) and t["sweep_candidates_timed"] in (0, 3)
+        else:
+            assert t["sweep_shape"] == 8 and t["sweep_candidates_timed"] == 0
+        Z = torch.zeros((8, s.N), dtype=torch.float64, device="cuda")
+        s.precond(dev(R), Z, nrhs=8)
+        Zh = host(Z)
+        tol = max(1e-4, 64.0 * np.linalg.cond(P.A0) * 2.0 ** -24)
+        for k in range(8):
+            ze = P.apply(R[k])
+            assert np.abs(Zh[k] - ze).max() <= tol * np.abs(ze).max(), (autotune, k)
+    s1 = rz.Riesz("RT", 5, verts, cells, precond_precision=rz.PREC_FP32, nrhs_max=8)  # vertex stars: n/a
+    assert s1.tuning()["sweep_shape"] == -1
+
+
 def test_edge_star_dirichlet_precond_matches_oracle():
     verts, cells, md, A = setup_rt(3, 3)
     s = rz.Riesz("RT", 3, verts, cells, decomposition=rz.DECOMP_EDGE_STAR, dirichlet=1)

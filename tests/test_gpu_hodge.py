@@ -104,6 +104,33 @@ def test_hodge_minres_matches_direct_and_oracle_counts(k, p, gamma, prec):
     assert abs(it - it_o) <= max(3, (0.1 if prec == rz.PREC_FP64 else 0.25) * it_o), (it, it_o)
 
 
+@pytest.mark.parametrize("k,p,gamma,decomp,form", [(1, 2, 1.0, rz.DECOMP_HT, rz.FORM_ADDITIVE),
+                                                  (2, 2, 1e3, rz.DECOMP_HT, rz.FORM_ADDITIVE),
+                                                  (2, 2, 1e3, rz.DECOMP_HT, rz.FORM_HYBRID),
+                                                  k3(3, 2, 1.0, rz.DECOMP_HT, rz.FORM_ADDITIVE)])
+def test_hodge_graph_loop_equals_host_loop(k, p, gamma, decomp, form):
+    """The device-driven MINRES (a CUDA graph WHILE loop, two iterations per pass with the second behind an
+    IF node) enqueues the host loop's kernels in the same order: bitwise the same iterate, count and
+    residual, for an odd and an even number of iterations."""
+    v, c, hs = system(k, p, 2, gamma)
+    b = hs.rhs(normal_vector(hs.n1, 4))
+    out = []
+    for loop in (rz.LOOP_GRAPH, rz.LOOP_HOST):
+        h = rz.Hodge(k, p, v, c, gamma, decomposition=decomp, form=form, rtol=1e-10, maxit=2000, loop=loop)
+        x = torch.zeros(h.N, dtype=torch.float64, device="cuda")
+        it, rr, rc = h.solve(dev(b), x)
+        assert rc == 0
+        out.append((host(x), it, rr))
+        h2 = rz.Hodge(k, p, v, c, gamma, decomposition=decomp, form=form, rtol=1e-10, maxit=out[0][1] - 1,
+                      loop=loop)
+        x2 = torch.zeros(h.N, dtype=torch.float64, device="cuda")
+        it2, _, rc2 = h2.solve(dev(b), x2, check=False)
+        assert rc2 == 4 and it2 == out[0][1] - 1
+        out.append((host(x2), it2, 0.0))
+    assert np.array_equal(out[0][0], out[2][0]) and out[0][1] == out[2][1] and out[0][2] == out[2][2]
+    assert np.array_equal(out[1][0], out[3][0])
+
+
 def test_hodge_exact_first_iterate_and_restart():
     """x already the solution: zero iterations; x from a partial solve: the restarted MINRES reaches
     the same tolerance."""
