@@ -22,10 +22,18 @@
 // bulk copies (one lane); warps 1-16 gather X, build the A stages and run the
 // epilogue: warp w serves row m = 32 (w % 4) + lane (tensor-memory lanes of
 // its quarter) and the K part (w - 1) / 4 (4 values) of every stage, four
-// producer warps per scheduler to hide the gathers' latency; in the epilogue
-// the four warps of a quarter take alternate 16-column chunks.  Warp 17 (one
+// producer warps per scheduler to hide the gathers' latency.  Warp 17 (one
 // lane) issues the MMAs and commits them to the slot's "empty" barrier and,
 // after the last stage, to "done".
+//
+// Epilogue: the accumulator leaves tensor memory in windows of up to 256
+// columns through a shared-memory staging tile (the operand ring, free once
+// "done" has fired): the four warps of a lane quarter read alternate 16-column
+// chunks (tcgen05.ld) into rows of the tile, then all 512 epilogue threads
+// write the window out in global order, consecutive threads on consecutive
+// addresses: interior rows of a cell are contiguous in y (row-major over the
+// window's interior columns), interface entries of one column are contiguous
+// over the tile's cells in Ycell.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -54,9 +62,19 @@ __host__ __device__ inline int tc_parts(int NP) { return NP <= TC_MAXNP ? 1 : 2;
 // bytes of one A stage (hi + lo) and of one B stage (hi + lo) for NP rows
 __host__ __device__ constexpr uint32_t tc_a_bytes() { return 2u * TC_ROWS * TC_KC * 2u; }
 __host__ __device__ constexpr uint32_t tc_b_bytes(int NP) { return 2u * (uint32_t)NP * TC_KC * 2u; }
-inline size_t tc_smem_bytes(int NP, int nstage) {
-  return (size_t)nstage * (tc_a_bytes() + tc_b_bytes(NP)) + 256;
+// epilogue staging: the accumulator passes through shared memory in windows of TC_SW columns, FP32,
+// rows padded by one word (conflict-free column writes and row reads)
+constexpr int TC_SW = 256;
+__host__ __device__ inline int tc_stage_cols(int NP) { return NP < TC_SW ? NP : TC_SW; }
+__host__ __device__ inline uint32_t tc_stage_bytes(int NP) {
+  return (uint32_t)TC_ROWS * (uint32_t)(tc_stage_cols(NP) + 1) * 4u;
 }
+// the operand ring, reused by the staging buffer once every MMA has completed; barriers behind both
+__host__ __device__ inline uint32_t tc_region_bytes(int NP, int nstage) {
+  const uint32_t ring = (uint32_t)nstage * (tc_a_bytes() + tc_b_bytes(NP)), st = tc_stage_bytes(NP);
+  return ring > st ? ring : st;
+}
+inline size_t tc_smem_bytes(int NP, int nstage) { return (size_t)tc_region_bytes(NP, nstage) + 256; }
 // ring slots that fit in the 227 KB of shared memory a CTA may hold
 inline int tc_stages(int NP) {
   int ns = TC_NSTAGE;
@@ -160,7 +178,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
   const uint32_t abytes = tc_a_bytes(), bbytes = tc_b_bytes(NP), bstride = tc_b_bytes(NPs);
   unsigned char* sA = tc_sm;                           // [NS][abytes]
   unsigned char* sB = tc_sm + (size_t)NS * abytes;     // [NS][bstride], this part's rows of each B stage
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)NS * bstride);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tc_sm + tc_region_bytes(NPs, NS));
   uint64_t* full_a = bars;                   // [NS], TC_PRODUCERS producer arrivals
   uint64_t* full_b = bars + TC_NSTAGE;       // [NS], expect_tx
   uint64_t* empty = bars + 2 * TC_NSTAGE;    // [NS], MMA commit
@@ -301,34 +319,51 @@ __global__ void __launch_bounds__(TC_NT, 1) k_apply_tc(int64_t C, int n, int nif
     }
   }
 
-  // epilogue: warps 1-8 read their quarter's lanes of the accumulator, the two warps of a quarter
-  // alternate 16-column chunks
+  // epilogue (see the file comment)
   if (warp >= 1 && warp <= TC_PWARPS) {
-    const int kh = (warp - 1) >> 2;
-    const bool ok = mbar_wait(done, 0, err) && !abort_flag;
+    const int et = threadIdx.x - 32;  // epilogue thread 0..511
+    if (!mbar_wait(done, 0, err)) abort_flag = 1;
     tc_fence_after();
-    const int q4 = warp & 3;
-    const int m = 32 * q4 + lane;
-    const int cl = m % CELLS, rl = m / CELLS;
-    const int64_t c = c0 + cl;
-    const int r = r0 + rl;
-    const bool valid = c < C && r < nrhs;
+    const int q4 = warp & 3, kh = (warp - 1) >> 2;
+    const int SW = tc_stage_cols(NPs), ld = SW + 1;
+    float* st = reinterpret_cast<float*>(tc_sm);  // [TC_ROWS][ld]
     const double bad = __longlong_as_double(0x7ff8000000000000ll);
-    double* yint = (valid && nif < n) ? y + (int64_t)r * N + cdofs[(int64_t)nif * C + c] - nif : nullptr;
-    for (int i0 = 16 * kh; i0 < NP; i0 += 16 * TC_KQ) {
-      float v[16];
-      tc_ld16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)i0, v);
-      if (!valid) continue;
+    const int nvalid = min(NP, n - col0);  // this CTA's real output columns
+    for (int w0 = 0; w0 < NP; w0 += SW) {
+      const int wc = min(SW, NP - w0);
+      for (int i0 = 16 * kh; i0 < wc; i0 += 16 * TC_KQ) {
+        float v[16];
+        tc_ld16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(w0 + i0), v);
+        float* row = st + (32 * q4 + lane) * ld + i0;
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int i = col0 + i0 + k;
-        if (i >= n) break;
-        const double val = ok ? (double)v[k] : bad;
-        if (i >= nif)
-          yint[i] = val;
-        else
-          Ycell[((int64_t)r * nif + i) * C + c] = val;
+        for (int k = 0; k < 16; ++k) row[k] = v[k];
       }
+      asm volatile("bar.sync 1, %0;" ::"r"(TC_PRODUCERS) : "memory");
+      const bool ok = !abort_flag;
+      // global columns [g0, g1) of this window; interface part [g0, gi), interior part [gi, g1)
+      const int g0 = col0 + w0, g1 = col0 + w0 + min(wc, nvalid - w0);
+      const int gi = min(max(g0, nif), g1);
+      const int nI = gi - g0, nJ = g1 - gi;
+      // interface entries: item = ((r_local * nI + column) * CELLS + cell), cells fastest
+      for (int it = et; it < RT * nI * CELLS; it += TC_PRODUCERS) {
+        const int cl = it % CELLS, rest = it / CELLS, col = rest % nI, rl = rest / nI;
+        const int64_t c = c0 + cl;
+        const int r = r0 + rl;
+        if (c >= C || r >= nrhs) continue;
+        const float v = st[(rl * CELLS + cl) * ld + col];
+        Ycell[((int64_t)r * nif + g0 + col) * C + c] = ok ? (double)v : bad;
+      }
+      // interior entries: item = (row m, column), columns fastest; a cell's interior DOFs are contiguous
+      for (int it = et; it < TC_ROWS * nJ; it += TC_PRODUCERS) {
+        const int col = it % nJ, m = it / nJ;
+        const int cl = m % CELLS, rl = m / CELLS;
+        const int64_t c = c0 + cl;
+        const int r = r0 + rl;
+        if (c >= C || r >= nrhs) continue;
+        const float v = st[m * ld + nI + col];
+        y[(int64_t)r * N + cdofs[(int64_t)nif * C + c] + (gi + col - nif)] = ok ? (double)v : bad;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(TC_PRODUCERS) : "memory");
     }
   }
   tc_fence_before();
