@@ -434,9 +434,9 @@ def batch_draws(count, seed=4, degrees=(2, 10), sizes=(4, 12)):
 def run_batch(args):
     """Batched solves: seeded draws over spaces {CG, Ned1, RT}, p in 2..10, n^3 x 6 tets with n in 4..12,
     perturbed 0.1h, one seeded random right-hand side each, FP32 inner products and patch sweeps with FP64
-    residuals.  The systems are packed into waves that fit the HBM budget; a wave's device setups run back to
-    back and its solves run as one graph launch (riesz_solve_batch).  The same systems are then solved one
-    after the other for comparison."""
+    residuals.  The systems are packed into waves that fit the HBM budget; a wave's device setups run
+    together (riesz_update_geometry_batch: one stream per system) and its solves run as one graph launch
+    (riesz_solve_batch).  The same systems are then set up and solved one after the other for comparison."""
     import numpy as np
     import torch
     from concurrent.futures import ThreadPoolExecutor
@@ -472,7 +472,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    setup_ms = solve_ms = seq_ms = 0.0
+    setup_ms = solve_ms = seq_ms = seq_setup_ms = 0.0
     iters, relres, status, ndofs = [], [], [], []
     launches = 0
     for wave in waves:
@@ -486,8 +486,7 @@ def run_batch(args):
         torch.cuda.synchronize()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         e[0].record(stream)
-        for h, v in zip(hs, verts_d):
-            h.update_geometry(v)
+        rz.update_geometry_batch(hs, verts_d)  # every system's setup on its own stream, joined once
         e[1].record(stream)
         it, rr, st = rz.solve_batch(hs, bs, xs)
         e[2].record(stream)
@@ -499,17 +498,21 @@ def run_batch(args):
         relres += [float(r) for r in rr]
         status += [int(k) for k in st]
         ndofs += [h.N for h in hs]
-        # the same systems solved one after the other
+        # the same systems set up and solved one after the other
         for x in xs:
             x.zero_()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
+        for h, v in zip(hs, verts_d):
+            h.update_geometry(v)
+        e1.record(stream)
         for h, b, x in zip(hs, bs, xs):
             h.solve(b, x, check=False)
-        e1.record(stream)
+        e2.record(stream)
         torch.cuda.synchronize()
-        seq_ms += e0.elapsed_time(e1)
+        seq_setup_ms += e0.elapsed_time(e1)
+        seq_ms += e1.elapsed_time(e2)
         for h in hs:
             h.close()
         del verts_d, bs, xs
@@ -530,6 +533,7 @@ def run_batch(args):
            "dofs": int(ntot), "setup_ms": setup_ms, "solve_ms": solve_ms,
            "solve_dofs_per_s": ntot / (solve_ms / 1e3),
            "sequential_solve_ms": seq_ms, "batch_speedup_vs_sequential_solves": seq_ms / solve_ms,
+           "sequential_setup_ms": seq_setup_ms, "batch_speedup_vs_sequential_setups": seq_setup_ms / setup_ms,
            "converged": sum(1 for k in status if k == 0), "max_relres": max(relres),
            "iterations_by_space_and_p": {sp: {str(p): sorted(v) for p, v in sorted(d.items())}
                                          for sp, d in by_space.items()},

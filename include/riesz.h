@@ -382,6 +382,16 @@ int riesz_load(riesz_handle* h, const double* fcg, double* b, void* stream);
    mesh moves, or to time the device setup from resident data. */
 int riesz_update_geometry(riesz_handle* h, const double* verts, void* stream);
 
+/* riesz_update_geometry for count independent systems at once (batched
+   device setup): each system's setup runs on a stream of its own, forked from
+   stream and joined back into it, so the setups of small systems share the
+   GPU instead of running one after the other; the host checks (factorisation
+   status, hybrid weights) follow once all have finished.  Each system gets
+   bitwise the same factors as from riesz_update_geometry.  hs, verts: host
+   arrays of count handles (distinct, on the current device) and device
+   vertex arrays [nverts_i][3] FP64. */
+int riesz_update_geometry_batch(riesz_handle* const* hs, int count, const double* const* verts, void* stream);
+
 /* Kernel kinds reported by the profiler. */
 enum {
   RIESZ_K_GEOM = 0,         /* a1 geometric factors                      */

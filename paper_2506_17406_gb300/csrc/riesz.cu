@@ -177,6 +177,8 @@ struct riesz_handle {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_pfork = nullptr, ev_pjoin = nullptr;
   cudaStream_t ht_stream = nullptr;  // the potential problems (setup and per application) beside the edge stars
   cudaEvent_t ev_hfork = nullptr, ev_hjoin = nullptr;
+  cudaStream_t batch_stream = nullptr;  // this handle's device setup inside a batched setup
+  cudaEvent_t ev_batch = nullptr;
   cudaGraphExec_t g_entry = nullptr, g_resume = nullptr;
   int g_nrhs = 0;
   int64_t g_pro_launches = 0, g_body_launches = 0;
@@ -277,6 +279,8 @@ struct riesz_handle {
     if (ht_stream) cudaStreamDestroy(ht_stream);
     if (ev_hfork) cudaEventDestroy(ev_hfork);
     if (ev_hjoin) cudaEventDestroy(ev_hjoin);
+    if (batch_stream) cudaStreamDestroy(batch_stream);
+    if (ev_batch) cudaEventDestroy(ev_batch);
     delete aux;
     delete caux;
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
@@ -1049,6 +1053,8 @@ void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* z
 // Sparse route: zc = w * (opts.coarse_its PCG steps from zero on the p = 1 handle, its vertex-star
 // patches as the preconditioner), all on the device with the PCG kernels of the main loop (device-side
 // scalars, no host round trip), so it is captured into the loop graphs like any other step.
+bool use_flex(const riesz_handle& h);
+
 void op_coarse_sparse(riesz_handle& h, const double* r, int nrhs, cudaStream_t s, double w) {
   riesz_handle& a = *h.caux;
   const int64_t N = h.N(), Na = a.N();
@@ -1060,9 +1066,10 @@ void op_coarse_sparse(riesz_handle& h, const double* r, int nrhs, cudaStream_t s
     dev::k_coarse_to_aux<<<nblk((int64_t)nrhs * h.N0, 256), 256, 0, s>>>(h.N0, h.d_cw.p, h.d_caux.p, r, N, nrhs,
                                                                          a.d_r.p, Na);
   });
-  // z = P r, p = z, (r, z)
+  // z = P r, p = z (and zold = z for the flexible step), (r, z): every application starts from r alone
   op_precond_dot(a, a.d_r.p, a.d_z.p, nullptr, 5, a.d_scal.p, nrhs, s);
   CK(cudaMemcpyAsync(a.d_p.p, a.d_z.p, vb, cudaMemcpyDeviceToDevice, s));
+  if (use_flex(a)) CK(cudaMemcpyAsync(a.d_zold.p, a.d_z.p, vb, cudaMemcpyDeviceToDevice, s));
   for (int k = 0; k < h.opts.coarse_its; ++k) {
     if (k > 0) iter_head(a, nrhs, s);
     iter_tail(a, a.d_xw.p, nrhs, s);
@@ -1614,7 +1621,8 @@ std::pair<int64_t, int64_t> add_loop(riesz_handle& h, cudaGraph_t G, int nrhs, b
 
 cudaGraphExec_t instantiate(cudaGraph_t G) {
   cudaGraphExec_t e = nullptr;
-  const cudaError_t rc = cudaGraphInstantiate(&e, G, 0);
+  // kernel nodes keep the priority of the stream they were captured from (the coarse side stream's)
+  const cudaError_t rc = cudaGraphInstantiate(&e, G, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(G);
   CK(rc);
   return e;
@@ -2327,7 +2335,13 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
   CK(cudaMemsetAsync(h.d_flags.p, 0, 4 * sizeof(int), s));
   CK(cudaMallocHost((void**)&h.h_ctl, 4 * sizeof(int)));
   if (!h.cap_stream) CK(cudaStreamCreateWithFlags(&h.cap_stream, cudaStreamNonBlocking));
-  if (!h.side_stream) CK(cudaStreamCreateWithFlags(&h.side_stream, cudaStreamNonBlocking));
+  if (!h.side_stream) {
+    // the coarse correction's small kernels run beside the patch sweeps; at the highest priority their
+    // blocks are scheduled as soon as SMs free up instead of queueing behind the sweep's blocks
+    int prio_low = 0, prio_high = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+    CK(cudaStreamCreateWithPriority(&h.side_stream, cudaStreamNonBlocking, prio_high));
+  }
   if (!h.ev_fork) CK(cudaEventCreateWithFlags(&h.ev_fork, cudaEventDisableTiming));
   if (!h.ev_join) CK(cudaEventCreateWithFlags(&h.ev_join, cudaEventDisableTiming));
   if (!h.ev_pfork) CK(cudaEventCreateWithFlags(&h.ev_pfork, cudaEventDisableTiming));
@@ -3026,6 +3040,44 @@ int riesz_update_geometry(riesz_handle* h, const double* verts, void* stream) {
     cudaStream_t s = S(stream);
     CK(cudaMemcpyAsync(h->d_verts.p, verts, h->d_verts.bytes(), cudaMemcpyDeviceToDevice, s));
     device_compute(*h, s);
+  });
+}
+
+int riesz_update_geometry_batch(riesz_handle* const* hs, int count, const double* const* verts, void* stream) {
+  return guarded([&] {
+    need(count >= 0 && (count == 0 || (hs && verts)), "bad batch arguments");
+    int dev_now = 0;
+    CK(cudaGetDevice(&dev_now));
+    for (int i = 0; i < count; ++i) {
+      check_dev(hs[i]);
+      need(hs[i]->device == dev_now, "a handle of the batch is not on the current CUDA device");
+      need(verts[i] != nullptr, "null vertex array in the batch");
+      for (int j = 0; j < i; ++j) need(hs[j] != hs[i], "a handle appears twice in the batch");
+    }
+    if (count == 0) return;
+    cudaStream_t s = S(stream);
+    cudaEvent_t fork;
+    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    CK(cudaEventRecord(fork, s));
+    for (int i = 0; i < count; ++i) {  // fork: every system's setup on its own stream
+      riesz_handle& h = *hs[i];
+      if (!h.batch_stream) CK(cudaStreamCreateWithFlags(&h.batch_stream, cudaStreamNonBlocking));
+      if (!h.ev_batch) CK(cudaEventCreateWithFlags(&h.ev_batch, cudaEventDisableTiming));
+      CK(cudaStreamWaitEvent(h.batch_stream, fork, 0));
+      CK(cudaMemcpyAsync(h.d_verts.p, verts[i], h.d_verts.bytes(), cudaMemcpyDeviceToDevice, h.batch_stream));
+      device_compute(h, h.batch_stream, true, false);
+      CK(cudaEventRecord(h.ev_batch, h.batch_stream));
+      CK(cudaStreamWaitEvent(s, h.ev_batch, 0));
+    }
+    cudaEventDestroy(fork);
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < count; ++i) {  // the host checks of a single setup, system by system
+      riesz_handle& h = *hs[i];
+      check_factor_info(h, s);
+      if (h.aux) check_factor_info(*h.aux, s);
+      if (h.caux && h.coarse_on) check_factor_info(*h.caux, s);
+      hybrid_weights(h, s);
+    }
   });
 }
 

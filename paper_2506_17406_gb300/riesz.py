@@ -186,6 +186,15 @@ def probe_fp64(iters=16384, stream=None):
     return float(out[0])
 
 
+def update_geometry_batch(solvers, verts, stream=None):
+    """Device setups of independent systems at once (riesz_update_geometry_batch); verts: device tensors."""
+    lib = load_library()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s.h.value for s in solvers])
+    vp = (ctypes.c_void_p * n)(*[v.data_ptr() for v in verts])
+    _check(lib.riesz_update_geometry_batch(ctypes.cast(hs, _P), n, ctypes.cast(vp, _P), _stream(stream)))
+
+
 def solve_batch(solvers, bs, xs, nrhs=None, stream=None):
     """Solve independent systems in one graph launch (riesz_solve_batch).
 

@@ -32,6 +32,8 @@ LOOP_CASES = [
     ("N1curl", 3, 3, 0.1, dict(precond_precision=rz.PREC_FP32), 1),
     ("RT", 3, 3, 0.1, dict(precond_precision=rz.PREC_FP32, apply_precision=rz.PREC_FP32), 3),
     ("N1curl", 2, 3, 0.1, dict(apply_mode=rz.APPLY_MATRIX_FREE), 2),
+    # the lowest-order coarse route (its PCG steps inside every preconditioner application)
+    ("RT", 2, 3, 0.1, dict(decomposition=rz.DECOMP_EDGE_STAR, coarse=2, precond_precision=rz.PREC_FP32), 2),
 ]
 
 
@@ -154,6 +156,50 @@ def test_batch_equals_individual_solves():
         assert torch.equal(x, xi)
         off += k
     assert np.all(relres <= 1e-10)
+
+
+def test_repeated_solves_are_bitwise_equal():
+    """A solve depends only on its inputs: two solves in a row give bitwise the same iterates, also with the
+    lowest-order coarse route, whose PCG steps start every application from the residual alone."""
+    for opts in (dict(decomposition=rz.DECOMP_EDGE_STAR, coarse=2, precond_precision=rz.PREC_FP32),
+                 dict(coarse=2), dict(decomposition=rz.DECOMP_EDGE_STAR, form=rz.FORM_HYBRID)):
+        verts, cells = kuhn_mesh(3, 0.1, 18)
+        s = rz.Riesz("RT", 2, verts, cells, rtol=1e-10, **opts)
+        b = dev(normal_vector(s.N, 800).reshape(1, -1))
+        out = []
+        for _ in range(2):
+            x = torch.zeros_like(b)
+            it, rr, rc = s.solve(b, x)
+            assert rc == 0
+            out.append((host(x), int(it[0]), float(rr[0])))
+        assert np.array_equal(out[0][0], out[1][0]) and out[0][1:] == out[1][1:], opts
+
+
+def test_batched_setup_equals_individual_setups():
+    """riesz_update_geometry_batch (every system's device setup on its own stream, joined once) gives every
+    system bitwise the factors of its own riesz_update_geometry: the solves after either setup are equal
+    bit for bit (mixed spaces, Hiptmair-Toselli, edge stars, hybrid form, the lowest-order coarse route)."""
+    cases = BATCH + [("N1curl", 3, 3, 0.1, dict(decomposition=rz.DECOMP_HT, precond_precision=rz.PREC_FP32), 1),
+                     ("RT", 3, 3, 0.1, dict(decomposition=rz.DECOMP_EDGE_STAR, form=rz.FORM_HYBRID), 2),
+                     ("RT", 2, 3, 0.1, dict(decomposition=rz.DECOMP_EDGE_STAR, coarse=2), 1)]
+    solvers, bs, xs, nr = make_batch(cases)
+    moved = [dev(kuhn_mesh(n, amp, 50 + i)[0]) for i, (_, _, n, amp, _, _) in enumerate(cases)]
+    out = []
+    for batched in (True, False):
+        if batched:
+            rz.update_geometry_batch(solvers, moved)
+        else:
+            for s, v in zip(solvers, moved):
+                s.update_geometry(v)
+        res = []
+        for s, b, k in zip(solvers, bs, nr):
+            x = torch.zeros((k, s.N), dtype=torch.float64, device="cuda")
+            it, rr, rc = s.solve(b, x, nrhs=k)
+            assert rc == 0
+            res.append((host(x), it.copy(), rr.copy()))
+        out.append(res)
+    for (x1, i1, r1), (x2, i2, r2) in zip(*out):
+        assert np.array_equal(x1, x2) and np.array_equal(i1, i2) and np.array_equal(r1, r2)
 
 
 def test_batch_matches_oracle():
