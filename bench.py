@@ -846,14 +846,14 @@ def main():
                 "algorithmic": "tile-sparse Cholesky of all patches = %.3e flop per launch (dense "
                                "sum n_V^3/3 would be %.3e)" % (chol_flops, dense_flops)}
     elif dom == "patch_solve":
-        byt = st["precond_bytes"]
+        byt = st["precond_bytes"] + psum * 16.0 * (nrhs - 1)  # every RHS gathers r and writes its patch copy
         achieved = byt / (dom_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
                 "frac": achieved / peak_hbm, "traffic": measured_traffic(args.workload, "k_patch_solve"),
                 "kernel": "k_patch_sweep" if nrhs == 1 else "k_patch_solve_multi",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                 "algorithmic": "2 sweeps over the stored factor tiles and diagonal inverses + patch "
-                               "vectors = %.3e B per launch" % byt}
+                               "vectors of every RHS = %.3e B per launch" % byt}
     elif dom == "apply_tc":
         # BF16x3 contraction: algorithmic 2 Q n^2 C nrhs flop per launch (the operator); the tensor pipe
         # executes three BF16 products per term over the padded tile (rows 128 per tile, N = n padded to
