@@ -382,8 +382,8 @@ def patch_flops_bytes(s):
 
 
 def run_serving(args):
-    """Poisson arrivals (mean 200 requests/s, seeded) of Riesz-map solves mixing CG, Ned1 and RT with p in
-    3..10 and Kuhn meshes of 4..20 cubes per edge (384..48 000 tets), perturbed by 0.1h, admitted by a 150 GB
+    """Poisson arrivals (mean 200 requests/s, seeded) of Riesz-map solves mixing CG, Ned1, RT, NedTwo and BDM
+    with p in 3..10 and Kuhn meshes of 4..20 cubes per edge (384..48 000 tets), perturbed by 0.1h, admitted by a 150 GB
     HBM budget with up to 8 requests in flight, each solved with the paper's decomposition for its space
     (vertex stars, Hiptmair-Toselli, edge stars) and W^k.  The mixed server (FP32 patch sweeps, BF16x3
     tensor-core products) and the plain FP64 server serve the same stream one after the other."""
@@ -393,18 +393,20 @@ def run_serving(args):
     from paper_2506_17406_gb300 import serve
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     degrees, sizes = tuple(range(3, 11)), tuple(range(4, 21))
+    spaces = ("CG", "N1curl", "RT", "N2curl", "BDM")
     warm = serve.poisson_stream(6, rate=200.0, seed=100, degrees=(3, 4), sizes=(4,))
     serve.Server(max_slots=8, recommended=True).run(warm, realtime=False)
     out = {"metric": "serving: DOFs/s and p50/p99 latency of solves to 1e-8", "unit": "DOFs/s", "n_gpus": 1,
            "higher_is_better": True, "data": "synthetic",
-           "config": {"workload": "Poisson stream, mean 200 req/s, CG/Ned1/RT, p 3..10, 4..20 cubes per edge "
+           "config": {"workload": "Poisson stream, mean 200 req/s, CG/Ned1/RT/NedTwo/BDM, p 3..10, "
+                                  "4..20 cubes per edge "
                                   "(384..48000 tets), perturbed 0.1h, 150 GB budget, 8 slots, recommended "
                                   "decompositions + W^k", "requests": args.requests}}
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
     for name, kw in (("mixed", dict(precond_precision=rz.PREC_FP32, apply_precision=rz.PREC_BF16X3)),
                      ("fp64_plain", dict(precond_precision=rz.PREC_FP64, apply_precision=rz.PREC_FP64))):
-        reqs = serve.poisson_stream(args.requests, rate=200.0, seed=7, degrees=degrees, sizes=sizes)
+        reqs = serve.poisson_stream(args.requests, rate=200.0, seed=7, spaces=spaces, degrees=degrees, sizes=sizes)
         srv = serve.Server(hbm_budget_bytes=150 << 30, max_slots=8, recommended=True, **kw)
         done = srv.run(reqs, realtime=True)
         st = serve.summary(done, srv.wall)
@@ -427,14 +429,14 @@ def batch_draws(count, seed=4, degrees=(2, 10), sizes=(4, 12)):
     """Seeded draws (space, p, cubes per edge) with p and n uniform in the given ranges."""
     import numpy as np
     rng = np.random.Generator(np.random.PCG64(seed))
-    return [(str(rng.choice(["CG", "N1curl", "RT"])), int(rng.integers(degrees[0], degrees[1] + 1)),
+    return [(str(rng.choice(["CG", "N1curl", "RT", "N2curl", "BDM"])), int(rng.integers(degrees[0], degrees[1] + 1)),
              int(rng.integers(sizes[0], sizes[1] + 1))) for _ in range(count)]
 
 
 def run_batch(args):
-    """Batched solves: seeded draws over spaces {CG, Ned1, RT}, p in 2..10, n^3 x 6 tets with n in 4..12,
-    perturbed 0.1h, one seeded random right-hand side each, FP32 inner products and patch sweeps with FP64
-    residuals.  The systems are packed into waves that fit the HBM budget; a wave's device setups run
+    """Batched solves: seeded draws over spaces {CG, Ned1, RT, NedTwo, BDM}, p in 2..10, n^3 x 6 tets with n
+    in 4..12, perturbed 0.1h, one seeded random right-hand side each, FP32 inner products and patch sweeps
+    with FP64 residuals.  The systems are packed into waves that fit the HBM budget; a wave's device setups run
     together (riesz_update_geometry_batch: one stream per system) and its solves run as one graph launch
     (riesz_solve_batch).  The same systems are then set up and solved one after the other for comparison."""
     import numpy as np
@@ -525,7 +527,8 @@ def run_batch(args):
     out = {"metric": "batched: DOFs/s solved to 1e-8 (device setup + one-launch solve per wave)",
            "value": ntot / ((setup_ms + solve_ms) / 1e3), "unit": "DOFs/s", "n_gpus": 1, "higher_is_better": True,
            "data": "synthetic", "dtype": "f64+f32",
-           "config": {"workload": "%d seeded draws: space in {CG, Ned1, RT}, p in 2..10, n^3 x 6 tets with n in "
+           "config": {"workload": "%d seeded draws: space in {CG, Ned1, RT, NedTwo, BDM}, p in 2..10, "
+                                  "n^3 x 6 tets with n in "
                                   "4..12, perturbed 0.1h, random RHS, the paper's decomposition per space + W^k, "
                                   "BF16x3 tensor-core products and FP32 patch sweeps, FP64 residuals, rtol 1e-8"
                                   % len(draws),
@@ -552,14 +555,15 @@ def run_p_sweep(args):
     table = {}
     for n in (2, 4):
         verts, cells = kuhn_mesh(n, 0.1, 1)
-        for space in ("CG", "N1curl", "RT"):
+        for space in ("CG", "N1curl", "RT", "N2curl", "BDM"):
             for p in range(1, 11):
                 row = {}
                 for name, kw in (("one_level", dict(coarse=0)), ("two_level", dict(coarse=1)),
                                  ("two_level_mixed", dict(coarse=1, precond_precision=rz.PREC_FP32)),
                                  ("hybrid", dict(coarse=1, form=rz.FORM_HYBRID)),
                                  ("hybrid_recommended", dict(coarse=1, form=rz.FORM_HYBRID,
-                                                             decomposition={"CG": 0, "N1curl": 1, "RT": 2}[space]))):
+                                                             decomposition={"CG": 0, "N1curl": 1, "RT": 2,
+                                                                            "N2curl": 1, "BDM": 2}[space]))):
                     s = rz.Riesz(space, p, verts, cells, maxit=5000, **kw)
                     b = torch.tensor(normal_vector(s.N, 7), device="cuda")
                     x = torch.zeros_like(b)

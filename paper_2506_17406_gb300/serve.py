@@ -78,8 +78,10 @@ def estimate_footprint(h, opts=None):
 
 
 # the paper's recommended decomposition per space: vertex stars (H1), Hiptmair-Toselli (H(curl), Eq. (6.19)),
-# edge stars (H(div), Eq. (6.24))
-RECOMMENDED = {"CG": rz.DECOMP_VERTEX_STAR, "N1curl": rz.DECOMP_HT, "RT": rz.DECOMP_EDGE_STAR}
+# edge stars (H(div), Eq. (6.24)); the same for the second-kind spaces (Hiptmair-Toselli with CG_{p+1}
+# potentials for NedTwo_p)
+RECOMMENDED = {"CG": rz.DECOMP_VERTEX_STAR, "N1curl": rz.DECOMP_HT, "RT": rz.DECOMP_EDGE_STAR,
+               "N2curl": rz.DECOMP_HT, "BDM": rz.DECOMP_EDGE_STAR}
 
 
 class Server:

@@ -35,13 +35,16 @@ def test_results_identical_alone_and_in_the_mix():
 
 
 def test_served_results_match_the_oracle():
-    """Requests of every space (FP32 patch sweeps, FP64 residuals) served concurrently, each solved to
-    rtol 1e-11, against the oracle's sparse direct solve of the same mesh and right-hand side: 1e-8
-    relative L2 (the mixed path's accuracy target)."""
+    """Requests of every space, first and second kind (FP32 patch sweeps, FP64 residuals, the paper's
+    decomposition per space), served concurrently, each solved to rtol 1e-11, against the oracle's sparse
+    direct solve of the same mesh and right-hand side: 1e-8 relative L2 (the mixed path's accuracy target)."""
     reqs = serve.poisson_stream(6, rate=1000.0, seed=11, degrees=(2, 3, 4), sizes=(2, 3))
-    for r in reqs:
+    # and the second-kind spaces, with the paper's decompositions
+    reqs += serve.poisson_stream(4, rate=1000.0, seed=12, spaces=("N2curl", "BDM"), degrees=(2, 3), sizes=(2,))
+    for i, r in enumerate(reqs):
         r.rtol = 1e-11
-    done = serve.Server(hbm_budget_bytes=8 << 30, max_slots=6).run(reqs, realtime=True)
+        r.rid = i
+    done = serve.Server(hbm_budget_bytes=8 << 30, max_slots=6, recommended=True).run(reqs, realtime=True)
     for r in done:
         assert r.status == 0, r
         verts, cells = kuhn_mesh(r.n, r.amp, r.seed % 1000)
