@@ -147,9 +147,13 @@ typedef struct {
      basis is the first DOF of every vertex (H1), edge (H(curl)) or face
      (H(div))): z += w R_0^T A_0^{-1} R_0 r with A_0 = R_0 A R_0^T, additive
      with weight w = 1/2 (every W^k function also lies in the vertex-star
-     spaces, so the unweighted sum over-corrects).  A_0 is assembled densely and inverted in FP32 at device
-     setup (block Gauss-Jordan) and applied as a dense product, so it is used
-     only when W^k has at most 6144 DOFs.  Above that the coarse problem,
+     spaces, so the unweighted sum over-corrects).  A_0 is assembled densely at
+     device setup, factored by a blocked FP64 Cholesky, its inverse
+     L^{-T} L^{-1} formed in FP64 (positive definite by construction, exact to
+     FP64 rounding) and applied as a dense FP64 product, so it is used only
+     when W^k has at most 2048 DOFs (3072 for H1, whose lowest-order route
+     below is point-Jacobi PCG; 6144 for the blocks of the Hodge-Laplace
+     preconditioner, which MINRES needs linear).  Above that the coarse problem,
      which is the lowest-order Riesz map on the same mesh (Lemma 4.1), is
      held by an internal p = 1 handle and solved approximately by coarse_its
      PCG steps from zero preconditioned by that handle's own vertex-star
@@ -383,11 +387,15 @@ int riesz_load(riesz_handle* h, const double* fcg, double* b, void* stream);
 int riesz_update_geometry(riesz_handle* h, const double* verts, void* stream);
 
 /* riesz_update_geometry for count independent systems at once (batched
-   device setup): each system's setup runs on a stream of its own, forked from
-   stream and joined back into it, so the setups of small systems share the
-   GPU instead of running one after the other; the host checks (factorisation
-   status, hybrid weights) follow once all have finished.  Each system gets
-   bitwise the same factors as from riesz_update_geometry.  hs, verts: host
+   device setup): each system's geometry, element matrices and patch assembly
+   run on a stream of its own, forked from stream; then the patch
+   factorisations of all systems run as one persistent launch over a single
+   work list, largest patches first (uneven patch sizes across systems balance
+   over the SMs); then each system's FP32 factor copies, joined back into
+   stream.  The host checks (factorisation status, hybrid weights) follow once
+   all have finished.  Each system gets bitwise the same factors as from
+   riesz_update_geometry.  Allocates the work list (a few bytes per patch)
+   for the duration of the call.  hs, verts: host
    arrays of count handles (distinct, on the current device) and device
    vertex arrays [nverts_i][3] FP64. */
 int riesz_update_geometry_batch(riesz_handle* const* hs, int count, const double* const* verts, void* stream);

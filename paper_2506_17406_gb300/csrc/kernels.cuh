@@ -419,19 +419,12 @@ __device__ __forceinline__ void patch_sync() {
   }
 }
 
+// One patch (n DOFs, tile map tix, factor tiles A, diagonal inverses Dinv, pivot report *info) by one
+// CTA (SPLIT = 1) or one CTA of a 2-CTA cluster (rank).
 template <int SPLIT>
-__global__ void __launch_bounds__(NT, 6) k_cholesky(const int32_t* __restrict__ pn, const int64_t* __restrict__ pfoff,
-                                                 const int64_t* __restrict__ pdoff_inv,
-                                                 const int64_t* __restrict__ pmoff, const int32_t* __restrict__ meta,
-                                                 double* __restrict__ Lall, double* __restrict__ Dall,
-                                                 int* __restrict__ info) {
-  const int P = blockIdx.x / SPLIT;
-  const int rank = blockIdx.x % SPLIT;  // cluster rank (clusters are consecutive CTAs along x)
-  const int n = pn[P];
+__device__ __forceinline__ void chol_patch(int n, const int32_t* __restrict__ tix, double* __restrict__ A,
+                                           double* __restrict__ Dinv, int* __restrict__ info, int rank) {
   const int nb = (n + 31) / 32;
-  const int32_t* tix = meta + pmoff[P];
-  double* A = Lall + pfoff[P];
-  double* Dinv = Dall + pdoff_inv[P];
   __shared__ double D[32][33], Di[32][33];
   __shared__ double Ta[32][33], Tb[32][33];
   __shared__ int colI[MAXNB];
@@ -458,7 +451,7 @@ __global__ void __launch_bounds__(NT, 6) k_cholesky(const int32_t* __restrict__ 
           if (lane == 0) {
             double d = D[j][j];
             if (!(d > 0.0)) {
-              if (info[P] == 0) info[P] = K * 32 + j + 1;
+              if (*info == 0) *info = K * 32 + j + 1;
               d = 1.0;
             }
             D[j][j] = sqrt(d);
@@ -540,6 +533,43 @@ __global__ void __launch_bounds__(NT, 6) k_cholesky(const int32_t* __restrict__ 
       __syncthreads();
     }
     if constexpr (SPLIT > 1) patch_sync<SPLIT>();  // trailing tiles done before the next diagonal
+  }
+}
+
+template <int SPLIT>
+__global__ void __launch_bounds__(NT, 6) k_cholesky(const int32_t* __restrict__ pn, const int64_t* __restrict__ pfoff,
+                                                 const int64_t* __restrict__ pdoff_inv,
+                                                 const int64_t* __restrict__ pmoff, const int32_t* __restrict__ meta,
+                                                 double* __restrict__ Lall, double* __restrict__ Dall,
+                                                 int* __restrict__ info) {
+  const int P = blockIdx.x / SPLIT;
+  const int rank = blockIdx.x % SPLIT;  // cluster rank (clusters are consecutive CTAs along x)
+  chol_patch<SPLIT>(pn[P], meta + pmoff[P], Lall + pfoff[P], Dall + pdoff_inv[P], info + P, rank);
+}
+
+// The patch factorisations of several systems in one persistent launch: the patches of every system,
+// largest first, form one work list; each CTA takes the next patch from a global counter until the list
+// is empty, so uneven patch sizes across systems balance over the SMs.  Per patch the arithmetic is that
+// of k_cholesky (bitwise the same factors).
+struct CholJob {
+  const int32_t* tix;
+  double* A;
+  double* Dinv;
+  int* info;
+  int n;
+  int pad;
+};
+__global__ void __launch_bounds__(NT, 6) k_cholesky_many(const CholJob* __restrict__ jobs, int njobs,
+                                                      int* __restrict__ next) {
+  __shared__ int job;
+  for (;;) {
+    if (threadIdx.x == 0) job = atomicAdd(next, 1);
+    __syncthreads();
+    const int j = job;
+    if (j >= njobs) return;
+    const CholJob J = jobs[j];
+    chol_patch<1>(J.n, J.tix, J.A, J.Dinv, J.info, 0);
+    __syncthreads();  // every thread is done with this job before `job` is overwritten
   }
 }
 
@@ -1604,115 +1634,10 @@ __device__ __forceinline__ const T* tile_ptr(const T* A, int N0p, int i, int j) 
   return A + (int64_t)i * CB * N0p + (int64_t)j * CB;
 }
 
-// Sweep of block k, step 1 (one CTA): Dinv = A_kk^{-1} by Gauss-Jordan in shared memory.
-template <typename T>
-__global__ void __launch_bounds__(256) k_gj_pivot(int N0p, int k, const T* __restrict__ A, T* __restrict__ Dinv) {
-  __shared__ __align__(16) T D[CB][CBP];
-  load_tile64(D, tile_ptr(A, N0p, k, k), N0p, false);
-  for (int p = 0; p < CB; ++p) {
-    __syncthreads();
-    const T pv = D[p][p];
-    T old[16], fi[16], pr[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int e = threadIdx.x + 256 * m, i = e / CB, j = e % CB;
-      old[m] = D[i][j];
-      fi[m] = D[i][p];
-      pr[m] = D[p][j];
-    }
-    __syncthreads();
-    const T ipv = (T)1 / pv;
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int e = threadIdx.x + 256 * m, i = e / CB, j = e % CB;
-      T v;
-      if (i == p)
-        v = (j == p) ? ipv : pr[m] * ipv;
-      else
-        v = (j == p) ? -fi[m] * ipv : old[m] - fi[m] * pr[m] * ipv;
-      D[i][j] = v;
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < CB * CB; t += blockDim.x) Dinv[t] = D[t / CB][t % CB];
-}
-
-// Dynamic shared memory of the two-tile sweep kernels.
+// Dynamic shared memory of the two-tile kernels of the coarse factorisation.
 template <typename T>
 constexpr size_t gj_smem() {
   return (size_t)2 * CB * CBP * sizeof(T);
-}
-
-// step 2 (a CTA per column block j != k): Rb[:, j] = Dinv A_kj
-template <typename T>
-__global__ void __launch_bounds__(256) k_gj_row(int N0p, int k, const T* __restrict__ A, const T* __restrict__ Dinv,
-                                               T* __restrict__ Rb) {
-  const int j = blockIdx.x;
-  if (j == k) return;
-  extern __shared__ __align__(16) unsigned char gj_sm[];
-  T (*As)[CBP] = reinterpret_cast<T (*)[CBP]>(gj_sm);
-  T (*Bs)[CBP] = As + CB;
-  load_tile64(As, Dinv, CB, false);
-  if (j < k)
-    load_tile64(Bs, tile_ptr(A, N0p, k, j), N0p, false);
-  else
-    load_tile64(Bs, tile_ptr(A, N0p, j, k), N0p, true);
-  __syncthreads();
-  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  T acc[4][4] = {};
-  tile64_mma<T>(As, Bs, ty, tx, acc);
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) Rb[(int64_t)(ty + 16 * a) * N0p + j * CB + 4 * tx + q] = acc[a][q];
-}
-
-// step 3 (a CTA per lower tile (i, j), i >= j, i, j != k): A_ij -= A_ik Rb[:, j]
-template <typename T>
-__global__ void __launch_bounds__(256) k_gj_update(int N0p, int k, T* __restrict__ A, const T* __restrict__ Rb) {
-  const int t = blockIdx.x;  // lower-triangle tile index: t = i (i + 1) / 2 + j
-  int i = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
-  while ((i + 1) * (i + 2) / 2 <= t) ++i;
-  while (i * (i + 1) / 2 > t) --i;
-  const int j = t - i * (i + 1) / 2;
-  if (i == k || j == k) return;
-  extern __shared__ __align__(16) unsigned char gj_sm[];
-  T (*As)[CBP] = reinterpret_cast<T (*)[CBP]>(gj_sm);
-  T (*Bs)[CBP] = As + CB;
-  if (i > k)
-    load_tile64(As, tile_ptr(A, N0p, i, k), N0p, false);
-  else
-    load_tile64(As, tile_ptr(A, N0p, k, i), N0p, true);
-  load_tile64(Bs, Rb + (int64_t)j * CB, N0p, false);
-  __syncthreads();
-  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  T acc[4][4] = {};
-  tile64_mma<T>(As, Bs, ty, tx, acc);
-  T* Aij = A + (int64_t)i * CB * N0p + (int64_t)j * CB;
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) Aij[(int64_t)(ty + 16 * a) * N0p + 4 * tx + q] -= acc[a][q];
-}
-
-// step 4 (a CTA per block j): A_kj = Rb[:, j] (j < k), A_jk = Rb[:, j]^T (j > k),
-// A_kk = -Dinv.  After every block has been swept, the lower triangle holds -A_0^{-1}.
-template <typename T>
-__global__ void __launch_bounds__(256) k_gj_finish(int N0p, int k, T* __restrict__ A, const T* __restrict__ Dinv,
-                                                  const T* __restrict__ Rb) {
-  const int j = blockIdx.x;
-  for (int t = threadIdx.x; t < CB * CB; t += blockDim.x) {
-    const int r = t / CB, c = t % CB;
-    if (j == k) {
-      A[(int64_t)(k * CB + r) * N0p + k * CB + c] = -Dinv[t];
-    } else {
-      const T v = Rb[(int64_t)r * N0p + j * CB + c];
-      if (j < k)
-        A[(int64_t)(k * CB + r) * N0p + j * CB + c] = v;
-      else
-        A[(int64_t)(j * CB + c) * N0p + k * CB + r] = v;
-    }
-  }
 }
 
 // Fill the upper tiles from the lower ones (full rows for the coarse product).

@@ -126,11 +126,8 @@ struct riesz_handle {
   std::vector<int64_t> c_ptr;
   DBuf<int32_t> d_cw, d_cidx, d_cJ, d_ccell, d_cab;
   DBuf<int64_t> d_cptr;
-  DBuf<float> d_A0, d_Dinv0, d_Rb0;  // swept coarse matrix (-A_0^{-1} when done), pivot inverse, sweep row
-  DBuf<float> d_r0;                   // R_0 r in FP32 [nrhs][N0p]
   // the same in FP64 for ill-conditioned coarse matrices (beta/alpha far from 1, and the blocks of
   // the Hodge-Laplace preconditioner), where the FP32 inverse stops being positive definite
-  bool coarse64 = false;
   DBuf<double> d_A0d, d_Dinv0d, d_Rb0d, d_r0d;
   DBuf<double> d_X0d;   // FP64 path: X = -(L^{-T} L^{-1}) (the factor and its inverse are built in d_A0d)
   DBuf<int> d_cbad;     // non-positive pivot in the coarse Cholesky
@@ -205,8 +202,8 @@ struct riesz_handle {
            d_xw.bytes() + d_ctl.bytes() + d_flags.bytes() + d_dmask.bytes() + d_gt_ptr.bytes() + d_gg_ptr.bytes() +
            d_gt_idx.bytes() + d_gg_idx.bytes() + d_gt_sgn.bytes() + d_gg_sgn.bytes() + d_zcg.bytes() + d_zg.bytes() +
            (aux ? aux->device_bytes() : 0) + d_cw.bytes() + d_cidx.bytes() + d_cJ.bytes() +
-           d_ccell.bytes() + d_cab.bytes() + d_cptr.bytes() + d_A0.bytes() + d_Dinv0.bytes() + d_Rb0.bytes() +
-           d_r0.bytes() + d_zc.bytes() + d_A0d.bytes() + d_X0d.bytes() + d_Dinv0d.bytes() + d_Rb0d.bytes() + d_r0d.bytes() +
+           d_ccell.bytes() + d_cab.bytes() + d_cptr.bytes() +
+           d_zc.bytes() + d_A0d.bytes() + d_X0d.bytes() + d_Dinv0d.bytes() + d_Rb0d.bytes() + d_r0d.bytes() +
            d_info.bytes() + d_ticket.bytes() + d_cbad.bytes() + d_caux.bytes() + (caux ? caux->device_bytes() : 0) +
            d_hres.bytes() + d_hc.bytes() + d_hAc.bytes() + d_Btc.bytes();
   }
@@ -234,10 +231,6 @@ struct riesz_handle {
     d_zg.free();
     for (auto* b : {&d_cw, &d_cidx, &d_cJ, &d_ccell, &d_cab}) b->free();
     d_cptr.free();
-    d_A0.free();
-    d_Dinv0.free();
-    d_Rb0.free();
-    d_r0.free();
     d_A0d.free();
     d_X0d.free();
     d_cbad.free();
@@ -684,12 +677,21 @@ void plan_dirichlet(riesz_handle& h) {
 
 // W^k (Lemma 4.1: the first type-I DOF of each vertex, edge or face carries
 // the Whitney form) and the contribution lists of A_0 = R_0 A R_0^T.
-constexpr int COARSE_MAX = 6144;  // largest dense coarse problem (FP32 inverse: 151 MB)
+// Dense coarse inverse (FP64 Cholesky route, 0.83 N0^3 FP64 flop at setup: 220 ms at 5832 DOFs): up to
+// COARSE_DENSE_MAX DOFs for H(curl) and H(div), above that the lowest-order PCG steps; up to
+// COARSE_DENSE_MAX_H1 for H1, whose lowest-order vertex stars are single vertices (those steps are
+// point-Jacobi PCG and converge slowly); the blocks of the Hodge-Laplace preconditioner (which MINRES needs
+// linear) keep the dense inverse up to COARSE_MAX.  An FP32 Gauss-Jordan inverse was
+// cheaper to form but its error grows with N0 (measured on RT_1: 2e-3 relative at 1650 DOFs, 6e-3 at
+// 4410, where PCG took 217 iterations against 36 with the exact coarse solve and 46 with the PCG steps).
+constexpr int COARSE_DENSE_MAX = 2048;
+constexpr int COARSE_DENSE_MAX_H1 = 3072;
+constexpr int COARSE_MAX = 6144;
 // Weight of the additive coarse correction: every W^k function also lies in the
 // vertex-star spaces, so the unweighted sum over-corrects (most for H(div)).
 constexpr double COARSE_WEIGHT = 0.5;
 
-void plan_coarse(riesz_handle& h) {
+void plan_coarse(riesz_handle& h, bool hodge_block) {
   const MeshMaps& M = h.mesh;
   const int k = h.space;  // entity dimension of the Whitney DOFs: 0, 1, 2
   const int nd = M.per_entity[k];
@@ -703,7 +705,8 @@ void plan_coarse(riesz_handle& h) {
     if (h.dir_mask.empty() || !h.dir_mask[gd]) w.push_back((int32_t)gd);
   }
   if (w.empty()) return;
-  h.coarse_sparse = h.opts.coarse == 2 || (int64_t)w.size() > COARSE_MAX;
+  const int dense_max = hodge_block ? COARSE_MAX : (k == 0 ? COARSE_DENSE_MAX_H1 : COARSE_DENSE_MAX);
+  h.coarse_sparse = h.opts.coarse == 2 || (int64_t)w.size() > dense_max;
   const int N0 = (int)w.size();
   const int nloc = k == 1 ? 6 : 4;
   const int loc0 = k == 0 ? 0 : (k == 1 ? 4 * M.per_entity[0] : 4 * M.per_entity[0] + 6 * M.per_entity[1]);
@@ -750,11 +753,6 @@ void plan_coarse(riesz_handle& h) {
     for (int j = 0; j < N0; ++j) h.c_aux[j] = (int32_t)((h.c_w[j] - M.off[k]) / nd);
     return;
   }
-  // FP64 Cholesky-route coarse inverse when the weights are unbalanced: kappa(A_0) grows like
-  // (alpha / beta) h^-2 (or beta / alpha), and beyond ~1e4 the FP32 Gauss-Jordan inverse is no longer
-  // positive definite
-  if (h.opts.beta > 0 && h.opts.alpha > 0)
-    h.coarse64 = h.coarse64 || std::max(h.opts.alpha / h.opts.beta, h.opts.beta / h.opts.alpha) > 10.0;
 }
 
 void build_plans(riesz_handle& h) {
@@ -1086,10 +1084,8 @@ void op_coarse(riesz_handle& h, const double* r, int nrhs, cudaStream_t s, doubl
   if (!h.coarse_on) return;
   if (h.coarse_sparse)
     op_coarse_sparse(h, r, nrhs, s, w);
-  else if (h.coarse64)
-    op_coarse_t<double>(h, r, nrhs, s, h.d_X0d.p, h.d_r0d.p, w);
   else
-    op_coarse_t<float>(h, r, nrhs, s, h.d_A0.p, h.d_r0.p, w);
+    op_coarse_t<double>(h, r, nrhs, s, h.d_X0d.p, h.d_r0d.p, w);
 }
 
 // The coarse correction reads only r: it runs on the side stream beside the
@@ -1943,29 +1939,6 @@ void launch_cholesky(riesz_handle& h, int split, int ctas, cudaStream_t s) {
                         h.d_L64.p, h.d_D64.p, h.d_info.p));
 }
 
-// A_0 from the geometric factors, then -A_0^{-1} in place by block sweeps.
-template <typename T>
-void coarse_setup_t(riesz_handle& h, cudaStream_t s, DBuf<T>& A0, DBuf<T>& Dinv, DBuf<T>& Rb) {
-  const int nbk = h.N0p / dev::CB;
-  const RefElement& R = *h.ref;
-  const size_t sm = dev::gj_smem<T>();
-  CK(cudaMemsetAsync(A0.p, 0, A0.bytes(), s));
-  launch(h, RIESZ_K_COARSE, s, [&] {
-    dev::k_coarse_assemble<T><<<nblk(h.N0p, 128), 128, 0, s>>>(h.N0, h.N0p, h.d_cptr.p, h.d_cJ.p, h.d_ccell.p,
-                                                               h.d_cab.p, h.C(), h.mesh.nref, R.Q, h.d_g.p, h.d_R.p,
-                                                               A0.p);
-  });
-  for (int k = 0; k < nbk; ++k) {
-    launch(h, RIESZ_K_COARSE, s, [&] { dev::k_gj_pivot<T><<<1, 256, 0, s>>>(h.N0p, k, A0.p, Dinv.p); });
-    launch(h, RIESZ_K_COARSE, s, [&] { dev::k_gj_row<T><<<nbk, 256, sm, s>>>(h.N0p, k, A0.p, Dinv.p, Rb.p); });
-    launch(h, RIESZ_K_COARSE, s,
-           [&] { dev::k_gj_update<T><<<nbk * (nbk + 1) / 2, 256, sm, s>>>(h.N0p, k, A0.p, Rb.p); });
-    launch(h, RIESZ_K_COARSE, s, [&] { dev::k_gj_finish<T><<<nbk, 256, 0, s>>>(h.N0p, k, A0.p, Dinv.p, Rb.p); });
-  }
-  if (nbk > 1)
-    launch(h, RIESZ_K_COARSE, s, [&] { dev::k_coarse_mirror<T><<<nbk * (nbk - 1) / 2, 256, 0, s>>>(h.N0p, A0.p); });
-}
-
 // FP64: positive definite inverse X = L^{-T} L^{-1} from the blocked Cholesky factor
 // (stored negated in d_X0d, the convention of the swept Gauss-Jordan matrix).
 void coarse_setup_chol(riesz_handle& h, cudaStream_t s) {
@@ -2016,15 +1989,13 @@ void coarse_setup_sparse(riesz_handle& h, cudaStream_t s) {
 void coarse_setup(riesz_handle& h, cudaStream_t s) {
   if (h.coarse_sparse)
     coarse_setup_sparse(h, s);
-  else if (h.coarse64)
-    coarse_setup_chol(h, s);
   else
-    coarse_setup_t<float>(h, s, h.d_A0, h.d_Dinv0, h.d_Rb0);
+    coarse_setup_chol(h, s);
 }
 
 // Patch factorisations that met a non-positive pivot (after the stream is synchronised).
 void check_factor_info(riesz_handle& h, cudaStream_t s) {
-  if (h.coarse_on && h.coarse64 && !h.coarse_sparse) {
+  if (h.coarse_on && !h.coarse_sparse) {
     int bad = 0;
     CK(cudaMemcpyAsync(&bad, h.d_cbad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -2044,19 +2015,14 @@ void check_factor_info(riesz_handle& h, cudaStream_t s) {
 // with_aux: also recompute the potential problems of a Hiptmair-Toselli
 // handle (on their own stream, beside this handle's factorisation).  sync:
 // wait for the result, record the device setup time and check the pivots.
-void device_compute(riesz_handle& h, cudaStream_t s, bool with_aux = true, bool sync = true) {
+// Device setup, first part: everything up to the assembled patch matrices (the potential problems and
+// the coarse setup forked onto their streams).
+void device_compute_pre(riesz_handle& h, cudaStream_t s, bool aux_now) {
   const RefElement& R = *h.ref;
   const MeshMaps& M = h.mesh;
   const int n = M.nref;
   const int64_t C = M.ncells;
   const int npatch = (int)h.p_n.size();
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (sync) {
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    CK(cudaEventRecord(e0, s));
-  }
-  const bool aux_now = h.aux && with_aux;
   if (aux_now) {  // the potential problems follow the same vertices
     CK(cudaEventRecord(h.ev_hfork, s));
     CK(cudaStreamWaitEvent(h.ht_stream, h.ev_hfork, 0));
@@ -2097,9 +2063,14 @@ void device_compute(riesz_handle& h, cudaStream_t s, bool with_aux = true, bool 
                                                    h.d_pb_cell.p, h.d_pb_off.p, h.d_pb_ent.p, C, n, R.Q, h.d_g.p,
                                                    h.d_R.p, h.d_Ae.p, h.d_L64.p);
     });
-    launch(h, RIESZ_K_CHOLESKY, s, [&] {
-      launch_cholesky(h, h.chol_split, h.chol_ctas, s);
-    });
+  }
+}
+
+// Device setup, last part (after the patch factorisation): the FP32 copies of the factors, then the
+// joins of the side streams.
+void device_compute_post(riesz_handle& h, cudaStream_t s, bool aux_now) {
+  const int npatch = (int)h.p_n.size();
+  if (npatch) {
     if (h.opts.precond_precision == RIESZ_PREC_FP32) {
       launch(h, RIESZ_K_TO_F32, s, [&] {
         dev::k_to_f32<<<1184, 256, 0, s>>>(h.factor_entries, h.d_L64.p, h.d_L32.p);
@@ -2119,6 +2090,22 @@ void device_compute(riesz_handle& h, cudaStream_t s, bool with_aux = true, bool 
   }
   if (h.coarse_on) CK(cudaStreamWaitEvent(s, h.ev_join, 0));
   if (aux_now) CK(cudaStreamWaitEvent(s, h.ev_hjoin, 0));
+}
+
+void device_compute(riesz_handle& h, cudaStream_t s, bool with_aux = true, bool sync = true) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (sync) {
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+  }
+  const bool aux_now = h.aux && with_aux;
+  device_compute_pre(h, s, aux_now);
+  if (!h.p_n.empty())
+    launch(h, RIESZ_K_CHOLESKY, s, [&] {
+      launch_cholesky(h, h.chol_split, h.chol_ctas, s);
+    });
+  device_compute_post(h, s, aux_now);
   if (!sync) return;
   CK(cudaEventRecord(e1, s));
   CK(cudaEventSynchronize(e1));
@@ -2410,7 +2397,7 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
     h.d_cJ.upload(h.c_J, s);
     h.d_ccell.upload(h.c_cell, s);
     h.d_cab.upload(h.c_ab, s);
-    if (h.coarse64) {
+    {  // FP64 Cholesky-route inverse (positive definite by construction)
       h.d_A0d.alloc((size_t)h.N0p * h.N0p);
       h.d_X0d.alloc((size_t)h.N0p * h.N0p);
       h.d_Dinv0d.alloc((size_t)h.N0p * dev::CB);  // the inverse of every diagonal tile of L
@@ -2424,23 +2411,11 @@ void setup_device_impl(riesz_handle& h, cudaStream_t s) {
       raise_smem_limit(dev::k_ct_update, dev::gj_smem<double>());
       raise_smem_limit(dev::k_ct_finish, dev::gj_smem<double>());
       raise_smem_limit(dev::k_ct_lauum, dev::gj_smem<double>());
-    } else {
-      h.d_A0.alloc((size_t)h.N0p * h.N0p);
-      h.d_Dinv0.alloc((size_t)dev::CB * dev::CB);
-      h.d_Rb0.alloc((size_t)dev::CB * h.N0p);
-      h.d_r0.alloc((size_t)nrhs * h.N0p);
     }
-    raise_smem_limit(dev::k_gj_row<float>, dev::gj_smem<float>());
-    raise_smem_limit(dev::k_gj_update<float>, dev::gj_smem<float>());
-    raise_smem_limit(dev::k_gj_row<double>, dev::gj_smem<double>());
-    raise_smem_limit(dev::k_gj_update<double>, dev::gj_smem<double>());
     h.d_zc.alloc((size_t)nrhs * h.N0);
-    const size_t per = (size_t)h.N0p * (h.coarse64 ? sizeof(double) : sizeof(float));
+    const size_t per = (size_t)h.N0p * sizeof(double);
     h.coarse_group = (int)std::max<size_t>(1, std::min<size_t>(8, (160 * 1024) / per));
-    if (h.coarse64)
-      raise_smem_limit(dev::k_coarse_apply<double>, per * h.coarse_group);
-    else
-      raise_smem_limit(dev::k_coarse_apply<float>, per * h.coarse_group);
+    raise_smem_limit(dev::k_coarse_apply<double>, per * h.coarse_group);
   }
   if (npatch) {
     h.d_L64.alloc((size_t)h.factor_entries);
@@ -2574,18 +2549,13 @@ double plan_device_bytes(const riesz_handle& h, int64_t* nalloc) {
     add((double)h.c_J.size(), 4);
     add((double)h.c_cell.size(), 4);
     add((double)h.c_ab.size(), 4);
-    if (h.coarse64) {
+    {
       add(N0p * N0p, 8);
       add(N0p * N0p, 8);
       add(N0p * CB, 8);
       add(CB * N0p, 8);
       add(nrhs * N0p, 8);
       add(1, 4);
-    } else {
-      add(N0p * N0p, 4);
-      add(CB * CB, 4);
-      add(CB * N0p, 4);
-      add(nrhs * N0p, 4);
     }
     add(nrhs * h.N0, 8);
   }
@@ -2682,7 +2652,7 @@ riesz_handle* create_handle(int space, int p, int64_t nverts, const double* vert
   if (h->opts.decomposition == RIESZ_DECOMP_HT) plan_ht(*h);
   if (h->opts.decomposition == RIESZ_DECOMP_EDGE_STAR) plan_edge_stars(*h, 0, h->mesh.per_entity[2]);
   build_plans(*h);
-  plan_coarse(*h);
+  plan_coarse(*h, internal);  // the internal handles with a coarse space are the Hodge-Laplace blocks
   if (h->coarse_on && h->coarse_sparse) {  // W^k = the lowest-order space (Whitney forms, Lemma 4.1, for either kind): its own p = 1 handle
     riesz_opts co = h->opts;
     co.coarse = 0;
@@ -3059,13 +3029,53 @@ int riesz_update_geometry_batch(riesz_handle* const* hs, int count, const double
     cudaEvent_t fork;
     CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     CK(cudaEventRecord(fork, s));
-    for (int i = 0; i < count; ++i) {  // fork: every system's setup on its own stream
+    // 1. every system's setup up to its assembled patch matrices, on a stream of its own
+    for (int i = 0; i < count; ++i) {
       riesz_handle& h = *hs[i];
       if (!h.batch_stream) CK(cudaStreamCreateWithFlags(&h.batch_stream, cudaStreamNonBlocking));
       if (!h.ev_batch) CK(cudaEventCreateWithFlags(&h.ev_batch, cudaEventDisableTiming));
       CK(cudaStreamWaitEvent(h.batch_stream, fork, 0));
       CK(cudaMemcpyAsync(h.d_verts.p, verts[i], h.d_verts.bytes(), cudaMemcpyDeviceToDevice, h.batch_stream));
-      device_compute(h, h.batch_stream, true, false);
+      device_compute_pre(h, h.batch_stream, h.aux != nullptr);
+      CK(cudaEventRecord(h.ev_batch, h.batch_stream));
+      CK(cudaStreamWaitEvent(s, h.ev_batch, 0));
+    }
+    // 2. all systems' patch factorisations in one persistent launch, largest patches first
+    std::vector<dev::CholJob> jobs;
+    for (int i = 0; i < count; ++i) {
+      const riesz_handle& h = *hs[i];
+      for (size_t P = 0; P < h.p_n.size(); ++P)
+        jobs.push_back({h.d_meta.p + h.p_moff[P], h.d_L64.p + h.p_foff[P], h.d_D64.p + h.p_dioff[P],
+                        h.d_info.p + P, h.p_n[P], 0});
+    }
+    std::stable_sort(jobs.begin(), jobs.end(), [](const dev::CholJob& a, const dev::CholJob& b) { return a.n > b.n; });
+    struct JobBuf {  // the work list; freed on every exit (after the synchronisation below on success)
+      unsigned char* p = nullptr;
+      ~JobBuf() {
+        if (p) cudaFree(p);
+      }
+    } jbuf;
+    if (!jobs.empty()) {
+      const size_t jb = jobs.size() * sizeof(dev::CholJob);
+      CK(cudaMalloc((void**)&jbuf.p, jb + sizeof(int)));
+      int* next = reinterpret_cast<int*>(jbuf.p + jb);
+      CK(cudaMemcpyAsync(jbuf.p, jobs.data(), jb, cudaMemcpyHostToDevice, s));
+      CK(cudaMemsetAsync(next, 0, sizeof(int), s));
+      int occ = 0, nsm = 0;
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::k_cholesky_many, dev::NT, 0));
+      CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_now));
+      const int grid = (int)std::min<size_t>(jobs.size(), (size_t)std::max(1, occ) * nsm);
+      dev::k_cholesky_many<<<grid, dev::NT, 0, s>>>(reinterpret_cast<const dev::CholJob*>(jbuf.p), (int)jobs.size(),
+                                                     next);
+      KCHECK();
+      ++hs[0]->launches;
+    }
+    CK(cudaEventRecord(fork, s));
+    // 3. each system's FP32 factor copies and joins, on its own stream again
+    for (int i = 0; i < count; ++i) {
+      riesz_handle& h = *hs[i];
+      CK(cudaStreamWaitEvent(h.batch_stream, fork, 0));
+      device_compute_post(h, h.batch_stream, h.aux != nullptr);
       CK(cudaEventRecord(h.ev_batch, h.batch_stream));
       CK(cudaStreamWaitEvent(s, h.ev_batch, 0));
     }
@@ -3649,7 +3659,6 @@ int riesz_hodge_setup(int k, int p, int64_t nverts, const double* verts, int64_t
     // needs a fixed (linear) preconditioner, which the few lowest-order PCG steps of the coarse route
     // above the dense limit are not: such blocks stay one-level.
     auto dense_coarse_only = [](riesz_handle* P) {
-      P->coarse64 = true;
       if (P->coarse_sparse) P->coarse_on = P->coarse_sparse = false;
     };
     dense_coarse_only(H->P0);

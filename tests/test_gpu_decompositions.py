@@ -42,8 +42,7 @@ def test_ht_precond_matches_oracle(p, n, alpha, beta):
     z = torch.zeros(s.N, dtype=torch.float64, device="cuda")
     s.precond(dev(r), z)
     ze = P.apply(r)
-    A0 = A.tocsr()[P.W][:, P.W].toarray()
-    tol = max(1e-10 * max(1.0, alpha), 64.0 * np.linalg.cond(A0) * 2.0 ** -24)
+    tol = 1e-10 * max(1.0, alpha)
     assert np.abs(host(z) - ze).max() <= tol * np.abs(ze).max()
 
 
@@ -97,7 +96,7 @@ def test_edge_star_precond_matches_oracle(p, n, alpha, prec, tol):
     z = torch.zeros(s.N, dtype=torch.float64, device="cuda")
     s.precond(dev(r), z)
     ze = P.apply(r)
-    tol = max(tol * max(1.0, alpha if prec == rz.PREC_FP64 else 1.0), 64.0 * np.linalg.cond(P.A0) * 2.0 ** -24)
+    tol = tol * max(1.0, alpha if prec == rz.PREC_FP64 else 1.0)
     assert np.abs(host(z) - ze).max() <= tol * np.abs(ze).max()
 
 
@@ -113,7 +112,7 @@ def test_edge_star_precond_several_rhs_matches_oracle(p, n, nr):
     Z = torch.zeros((nr, s.N), dtype=torch.float64, device="cuda")
     s.precond(dev(R), Z, nrhs=nr)
     Zh = host(Z)
-    tol = max(1e-4, 64.0 * np.linalg.cond(P.A0) * 2.0 ** -24)
+    tol = 1e-4
     for k in range(nr):
         ze = P.apply(R[k])
         assert np.abs(Zh[k] - ze).max() <= tol * np.abs(ze).max(), k
@@ -137,7 +136,7 @@ def test_sweep_shape_autotuner():
         Z = torch.zeros((8, s.N), dtype=torch.float64, device="cuda")
         s.precond(dev(R), Z, nrhs=8)
         Zh = host(Z)
-        tol = max(1e-4, 64.0 * np.linalg.cond(P.A0) * 2.0 ** -24)
+        tol = 1e-4
         for k in range(8):
             ze = P.apply(R[k])
             assert np.abs(Zh[k] - ze).max() <= tol * np.abs(ze).max(), (autotune, k)
@@ -154,7 +153,7 @@ def test_edge_star_dirichlet_precond_matches_oracle():
     z = torch.zeros(s.N, dtype=torch.float64, device="cuda")
     s.precond(dev(r), z)
     ze = P.apply(r)
-    tol = max(1e-10, 64.0 * np.linalg.cond(P.P.A0) * 2.0 ** -24)
+    tol = 1e-10
     assert np.abs(host(z) - ze).max() <= tol * np.abs(ze).max()
 
 

@@ -49,8 +49,6 @@ def test_dirichlet_apply_precond_solve(space, p, n, amp):
         P = asm.DirichletPreconditioner(A, md, D, two_level=bool(coarse))
         ze = P.apply(x)
         tol = 1e-10
-        if coarse:
-            tol = max(tol, 64.0 * np.linalg.cond(P.P.A0) * 2.0 ** -24)
         assert np.abs(host(z) - ze).max() <= tol * np.abs(ze).max()
         b = normal_vector(s.N, 6)
         b[D] = 0.0
@@ -130,8 +128,6 @@ def test_partial_dirichlet_apply_precond_solve(space, p):
         P = asm.DirichletPreconditioner(A, md, D, two_level=bool(coarse))
         ze = P.apply(x)
         tol = 1e-10
-        if coarse:
-            tol = max(tol, 64.0 * np.linalg.cond(P.P.A0) * 2.0 ** -24)
         assert np.abs(host(z) - ze).max() <= tol * np.abs(ze).max()
         b = normal_vector(s.N, 6)
         b[D] = 0.0

@@ -131,13 +131,16 @@ def test_fullsize_rt8_eight_rhs_mixed_solve():
 
 
 def test_fullsize_ned6_two_level(ned6):
-    """The benchmark's configuration with W^k (4184 lowest-order edge DOFs): the coarse correction against
-    the oracle's exact coarse solve at every coarse DOF, then load + PCG to 1e-8 checked on the oracle's
-    residual at sampled DOFs, in fewer iterations than the one-level preconditioner."""
+    """The benchmark's configuration with W^k (4184 lowest-order edge DOFs, above the dense limit: the
+    lowest-order PCG route): the coarse correction is supported on the coarse DOFs and its four PCG steps
+    leave at most a quarter of the A_0-norm error of the oracle's exact coarse solve (0.14 in an FP64 CPU
+    emulation of those steps); then load + PCG to 1e-8 checked on the oracle's residual at sampled DOFs, in
+    fewer iterations than the one-level preconditioner."""
     verts, cells, ref, md, s0 = ned6
     s = rz.Riesz("N1curl", 6, verts, cells, precond_precision=rz.PREC_FP32)
     W = asm.coarse_dofs(md)
-    assert s.tuning()["coarse_dofs"] == len(W) == 4184
+    t = s.tuning()
+    assert t["coarse_dofs"] == len(W) == 4184 and t["coarse_mode"] == 2
     A0 = asm.coarse_matrix(ref, md).toarray()
     r = normal_coeffs(s.N, 12)
     z1 = torch.zeros(s.N, dtype=torch.float64, device="cuda")
@@ -145,9 +148,11 @@ def test_fullsize_ned6_two_level(ned6):
     s.precond(torch.tensor(r, device="cuda"), z1)
     s0.precond(torch.tensor(r, device="cuda"), z0)
     dz = (z1 - z0).cpu().numpy()
-    ze = 0.5 * np.linalg.solve(A0, r[W])  # coarse weight 1/2
-    tol = 64.0 * np.linalg.cond(A0) * 2.0 ** -24
-    assert np.abs(dz[W] - ze).max() <= tol * np.abs(ze).max()
+    off = np.setdiff1d(np.arange(s.N), W)
+    assert np.abs(dz[off]).max() <= 1e-12 * np.abs(dz).max()  # FP32 sweeps: the one-level part is the same
+    u = 2.0 * dz[W]  # coarse weight 1/2
+    e = np.linalg.solve(A0, r[W])
+    assert np.sqrt((e - u) @ A0 @ (e - u)) <= 0.25 * np.sqrt(e @ A0 @ e)
     cg = reference_element("CG", 6)
     f = normal_coeffs((3, s.n_cg), 2)
     b = torch.zeros(s.N, dtype=torch.float64, device="cuda")

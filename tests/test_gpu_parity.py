@@ -262,9 +262,9 @@ def test_mixed_precision_apply_reaches_fp64_accuracy(space, p, n, amp):
 # ---------------------------------------------------------------------------
 # W^k coarse space (PAFW's first summand, Section 6.2)
 def coarse_tolerance(A0):
-    """FP32 block Gauss-Jordan inverse applied in FP32: relative error of the coarse correction
-    bounded by a small multiple of kappa(A_0) times the FP32 unit roundoff."""
-    return 64.0 * np.linalg.cond(A0) * 2.0 ** -24
+    """FP64 Cholesky-route inverse applied in FP64: relative error of the coarse correction bounded by a
+    small multiple of kappa(A_0) times the FP64 unit roundoff (and at most 1e-10)."""
+    return min(1e-10, 64.0 * np.linalg.cond(A0) * 2.0 ** -53)
 
 
 @pytest.mark.parametrize("space,p,n,amp", CASES)

@@ -80,7 +80,6 @@ def test_vertex_star_precond_matches_oracle(space, p, n, prec, tol):
     z = torch.zeros(s.N, dtype=torch.float64, device="cuda")
     s.precond(dev(r), z)
     ze = P.apply(r)
-    tol = max(tol, 64.0 * np.linalg.cond(P.A0) * 2.0 ** -24)
     assert np.abs(host(z) - ze).max() <= tol * np.abs(ze).max()
 
 
@@ -97,7 +96,6 @@ def test_ht_precond_matches_oracle(p, n, prec, tol):
     s.precond(dev(R), Z, nrhs=8)
     Zh = host(Z)
     A0 = A[P.W][:, P.W].toarray()
-    tol = max(tol, 64.0 * np.linalg.cond(A0) * 2.0 ** -24)
     for k in range(8):
         ze = P.apply(R[k])
         assert np.abs(Zh[k] - ze).max() <= tol * np.abs(ze).max(), k
@@ -113,7 +111,6 @@ def test_edge_star_precond_matches_oracle(p, n, nr, prec, tol):
     Z = torch.zeros((nr, s.N), dtype=torch.float64, device="cuda")
     s.precond(dev(R), Z, nrhs=nr)
     Zh = host(Z)
-    tol = max(tol, 64.0 * np.linalg.cond(P.A0) * 2.0 ** -24)
     for k in range(nr):
         ze = P.apply(R[k])
         assert np.abs(Zh[k] - ze).max() <= tol * np.abs(ze).max(), k
