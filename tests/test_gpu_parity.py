@@ -94,7 +94,7 @@ def test_solve_reaches_rtol_on_oracle_residual(space, p, n, amp, prec):
     assert np.linalg.norm(xh - xe) <= 1e-5 * np.linalg.norm(xe)
 
 
-def test_manufactured_solution_cfg1():
+def test_manufactured_cubic_cg3_on_4_cubed():
     """CG_3 on 4^3 x 6 tets, cubic u with N(0,1) coefficients: b from the oracle's quadrature,
     x from the GPU solve reproduces u (Section 7.1 setting, exact in V_h)."""
     verts, cells, ref, md, A = oracle("CG", 3, 4, 0.0)
