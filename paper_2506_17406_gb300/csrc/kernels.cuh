@@ -101,21 +101,39 @@ __global__ void k_geom(int space, int64_t C, const double* __restrict__ verts, c
 
 // A_T = sum_q g_q(T) R_q, stored [C][n][n] (setup of the element-matrix apply).  The R_q are
 // symmetric, so A_T is: the upper triangle is formed (row by row, coalesced) and mirrored, half the
-// FP64 work of forming every entry.
-__global__ void k_elem_matrices(int64_t C, int n, int Q, const double* __restrict__ g, const double* __restrict__ R,
-                                double* __restrict__ Ae) {
-  const int64_t c = blockIdx.x;
+// FP64 work of forming every entry.  A CTA forms ELEM_CELLS cells at once, so every R_q entry it reads
+// from L2 serves all of them (one cell per CTA read 8 B per FMA, more than L2 sustains at the FP64 rate).
+constexpr int ELEM_CELLS = 4;  // cells per CTA of k_elem_matrices: each R_q entry read once for all of them
+template <int Q>
+__global__ void __launch_bounds__(256) k_elem_matrices(int64_t C, int n, const double* __restrict__ g,
+                                                      const double* __restrict__ R, double* __restrict__ Ae) {
+  const int64_t c0 = (int64_t)blockIdx.x * ELEM_CELLS;
+  const int nc = (int)min((int64_t)ELEM_CELLS, C - c0);
   const int64_t nn = (int64_t)n * n;
-  double gq[16];
-  for (int q = 0; q < Q; ++q) gq[q] = g[q * C + c];
-  double* A = Ae + c * nn;
+  double gq[ELEM_CELLS][Q];
+#pragma unroll
+  for (int e = 0; e < ELEM_CELLS; ++e)
+#pragma unroll
+    for (int q = 0; q < Q; ++q) gq[e][q] = e < nc ? g[q * C + c0 + e] : 0.0;
   for (int i = 0; i < n; ++i) {
     for (int j = i + threadIdx.x; j < n; j += blockDim.x) {
       const int64_t t = (int64_t)i * n + j;
-      double s = 0.0;
-      for (int q = 0; q < Q; ++q) s += gq[q] * R[q * nn + t];
-      A[t] = s;
-      if (j != i) A[(int64_t)j * n + i] = s;
+      double s[ELEM_CELLS];
+#pragma unroll
+      for (int e = 0; e < ELEM_CELLS; ++e) s[e] = 0.0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const double r = R[q * nn + t];
+#pragma unroll
+        for (int e = 0; e < ELEM_CELLS; ++e) s[e] += gq[e][q] * r;
+      }
+#pragma unroll
+      for (int e = 0; e < ELEM_CELLS; ++e) {
+        if (e >= nc) break;
+        double* A = Ae + (c0 + e) * nn;
+        A[t] = s[e];
+        if (j != i) A[(int64_t)j * n + i] = s[e];
+      }
     }
   }
 }
@@ -427,6 +445,7 @@ __device__ __forceinline__ void chol_patch(int n, const int32_t* __restrict__ ti
   const int nb = (n + 31) / 32;
   __shared__ double D[32][33], Di[32][33];
   __shared__ double Ta[32][33], Tb[32][33];
+  __shared__ double Rd[32];  // reciprocals of the factor's diagonal
   __shared__ int colI[MAXNB];
   __shared__ int ncol;
   const int tid = threadIdx.x;
@@ -454,11 +473,13 @@ __device__ __forceinline__ void chol_patch(int n, const int32_t* __restrict__ ti
               if (*info == 0) *info = K * 32 + j + 1;
               d = 1.0;
             }
-            D[j][j] = sqrt(d);
+            const double sd = sqrt(d);
+            D[j][j] = sd;
+            Rd[j] = 1.0 / sd;
           }
           __syncwarp();
-          const double djj = D[j][j];
-          if (lane > j) D[lane][j] /= djj;
+          const double rdjj = Rd[j];
+          if (lane > j) D[lane][j] *= rdjj;
           __syncwarp();
           for (int k = j + 1; k < 32; ++k)
             if (lane >= k) D[lane][k] -= D[lane][j] * D[k][j];
@@ -468,7 +489,7 @@ __device__ __forceinline__ void chol_patch(int n, const int32_t* __restrict__ ti
         for (int r = lane; r < 32; ++r) {
           double s = (r == lane) ? 1.0 : 0.0;
           for (int k = lane; k < r; ++k) s -= D[r][k] * Di[k][lane];
-          Di[r][lane] = s / D[r][r];
+          Di[r][lane] = s * Rd[r];
         }
       }
       __syncthreads();
@@ -500,38 +521,36 @@ __device__ __forceinline__ void chol_patch(int n, const int32_t* __restrict__ ti
     }
     if constexpr (SPLIT > 1) patch_sync<SPLIT>();  // every panel tile is written
     // trailing update A_IJ -= L_IK L_JK^T over pairs of the column (I >= J)
-    const int npair = m * (m + 1) / 2;
-    for (int tt = rank; tt < npair; tt += SPLIT) {
-      int a = (int)((sqrt(8.0 * tt + 1.0) - 1.0) * 0.5);
-      while ((a + 1) * (a + 2) / 2 <= tt) ++a;
-      while (a * (a + 1) / 2 > tt) --a;
-      const int bb = tt - a * (a + 1) / 2;
-      const int I = colI[a], J = colI[bb];
-      const double* LI = A + (int64_t)tix[I * nb + K] * 1024;
-      const double* LJ = A + (int64_t)tix[J * nb + K] * 1024;
-      for (int t = tid; t < 1024; t += NT) {
-        Ta[t >> 5][t & 31] = ldt<SPLIT>(LI + t);
-        Tb[t >> 5][t & 31] = ldt<SPLIT>(LJ + t);
-      }
-      __syncthreads();
-      double* AIJ = A + (int64_t)tix[I * nb + J] * 1024;
-      const int r0 = tid >> 4, c0 = tid & 15;
-      double a00 = 0.0, a01 = 0.0, a10 = 0.0, a11 = 0.0;
+    // pairs (a, bb), bb <= a, in the order tt = a (a + 1) / 2 + bb, every SPLIT-th to this CTA
+    for (int a = 0, tt = 0; a < m; ++a)
+      for (int bb = 0; bb <= a; ++bb, ++tt) {
+        if (tt % SPLIT != rank) continue;
+        const int I = colI[a], J = colI[bb];
+        const double* LI = A + (int64_t)tix[I * nb + K] * 1024;
+        const double* LJ = A + (int64_t)tix[J * nb + K] * 1024;
+        for (int t = tid; t < 1024; t += NT) {
+          Ta[t >> 5][t & 31] = ldt<SPLIT>(LI + t);
+          Tb[t >> 5][t & 31] = ldt<SPLIT>(LJ + t);
+        }
+        __syncthreads();
+        double* AIJ = A + (int64_t)tix[I * nb + J] * 1024;
+        const int r0 = tid >> 4, c0 = tid & 15;
+        double a00 = 0.0, a01 = 0.0, a10 = 0.0, a11 = 0.0;
 #pragma unroll 8
-      for (int k = 0; k < 32; ++k) {
-        const double x0 = Ta[r0][k], x1 = Ta[r0 + 16][k];
-        const double y0 = Tb[c0][k], y1 = Tb[c0 + 16][k];
-        a00 = fma(x0, y0, a00);
-        a01 = fma(x0, y1, a01);
-        a10 = fma(x1, y0, a10);
-        a11 = fma(x1, y1, a11);
+        for (int k = 0; k < 32; ++k) {
+          const double x0 = Ta[r0][k], x1 = Ta[r0 + 16][k];
+          const double y0 = Tb[c0][k], y1 = Tb[c0 + 16][k];
+          a00 = fma(x0, y0, a00);
+          a01 = fma(x0, y1, a01);
+          a10 = fma(x1, y0, a10);
+          a11 = fma(x1, y1, a11);
+        }
+        AIJ[r0 * 32 + c0] = ldt<SPLIT>(AIJ + r0 * 32 + c0) - a00;
+        AIJ[r0 * 32 + c0 + 16] = ldt<SPLIT>(AIJ + r0 * 32 + c0 + 16) - a01;
+        AIJ[(r0 + 16) * 32 + c0] = ldt<SPLIT>(AIJ + (r0 + 16) * 32 + c0) - a10;
+        AIJ[(r0 + 16) * 32 + c0 + 16] = ldt<SPLIT>(AIJ + (r0 + 16) * 32 + c0 + 16) - a11;
+        __syncthreads();
       }
-      AIJ[r0 * 32 + c0] = ldt<SPLIT>(AIJ + r0 * 32 + c0) - a00;
-      AIJ[r0 * 32 + c0 + 16] = ldt<SPLIT>(AIJ + r0 * 32 + c0 + 16) - a01;
-      AIJ[(r0 + 16) * 32 + c0] = ldt<SPLIT>(AIJ + (r0 + 16) * 32 + c0) - a10;
-      AIJ[(r0 + 16) * 32 + c0 + 16] = ldt<SPLIT>(AIJ + (r0 + 16) * 32 + c0 + 16) - a11;
-      __syncthreads();
-    }
     if constexpr (SPLIT > 1) patch_sync<SPLIT>();  // trailing tiles done before the next diagonal
   }
 }

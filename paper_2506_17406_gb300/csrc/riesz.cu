@@ -2042,7 +2042,11 @@ void device_compute_pre(riesz_handle& h, cudaStream_t s, bool aux_now) {
   }
   if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     launch(h, RIESZ_K_ELEM, s, [&] {
-      dev::k_elem_matrices<<<(unsigned)C, 256, 0, s>>>(C, n, R.Q, h.d_g.p, h.d_R.p, h.d_Ae.p);
+      const unsigned grid = (unsigned)((C + dev::ELEM_CELLS - 1) / dev::ELEM_CELLS);
+      if (R.Q == 12)
+        dev::k_elem_matrices<12><<<grid, 256, 0, s>>>(C, n, h.d_g.p, h.d_R.p, h.d_Ae.p);
+      else
+        dev::k_elem_matrices<7><<<grid, 256, 0, s>>>(C, n, h.d_g.p, h.d_R.p, h.d_Ae.p);
     });
     if (h.d_Ae32.p)
       launch(h, RIESZ_K_TO_F32, s, [&] {
