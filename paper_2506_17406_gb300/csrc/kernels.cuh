@@ -511,14 +511,18 @@ __device__ __forceinline__ void chol_patch(int n, const int32_t* __restrict__ ti
       double* AIK = A + (int64_t)tix[colI[a] * nb + K] * 1024;
       for (int t = tid; t < 1024; t += NT) Ta[t >> 5][t & 31] = ldt<SPLIT>(AIK + t);
       __syncthreads();
+      // column c = t >> 5 is the same for the whole warp, so every lane runs the same
+      // c + 1 terms (row-per-warp would leave half the lanes idle on average)
       for (int t = tid; t < 1024; t += NT) {
-        const int r = t >> 5, c = t & 31;
+        const int c = t >> 5, r = t & 31;
         double acc = 0.0;
         for (int k = 0; k <= c; ++k) acc = fma(Ta[r][k], Di[c][k], acc);
-        AIK[t] = acc;
+        Tb[r][c] = acc;
       }
       __syncthreads();
+      for (int t = tid; t < 1024; t += NT) AIK[t] = Tb[t >> 5][t & 31];
     }
+    __syncthreads();
     if constexpr (SPLIT > 1) patch_sync<SPLIT>();  // every panel tile is written
     // trailing update A_IJ -= L_IK L_JK^T over pairs of the column (I >= J)
     // pairs (a, bb), bb <= a, in the order tt = a (a + 1) / 2 + bb, every SPLIT-th to this CTA
