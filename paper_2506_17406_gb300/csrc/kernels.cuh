@@ -247,6 +247,45 @@ __global__ void k_apply_elem(int64_t C, int n, int nif, const T* __restrict__ Ae
   }
 }
 
+// Element-matrix product for small elements (n_ref <= NMAX, e.g. the lowest-order spaces of a
+// coarse problem): one thread per (right-hand side, cell), cells fastest, so the cell-major Ycell
+// rows and the DOF map are read and written coalesced and a launch over many small cells is a few
+// hundred blocks rather than one block per cell.  Same sums in the same order as k_apply_elem.
+template <typename T, int NMAX>
+__global__ void __launch_bounds__(256) k_apply_elem_small(int64_t C, int n, int nif, const T* __restrict__ Ae,
+                                                         const int32_t* __restrict__ cdofs,
+                                                         const double* __restrict__ x, double* __restrict__ y,
+                                                         double* __restrict__ Ycell, int nrhs, int64_t N,
+                                                         const uint8_t* __restrict__ dmask) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nrhs * C) return;
+  const int r = (int)(t / C);
+  const int64_t c = t - (int64_t)r * C;
+  T xs[NMAX];
+#pragma unroll
+  for (int j = 0; j < NMAX; ++j) {
+    xs[j] = (T)0;
+    if (j < n) {
+      const int64_t dof = cdofs[(int64_t)j * C + c];
+      if (!(dmask && j < nif && dmask[dof])) xs[j] = (T)x[r * N + dof];
+    }
+  }
+  const T* A = Ae + c * (int64_t)n * n;
+#pragma unroll
+  for (int i = 0; i < NMAX; ++i) {
+    if (i >= n) break;
+    T acc = (T)0;
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j)
+      if (j < n) acc = fma(A[j * n + i], xs[j], acc);
+    if (i >= nif)
+      y[r * N + cdofs[(int64_t)i * C + c]] = (double)acc;
+    else
+      Ycell[((int64_t)r * nif + i) * C + c] = (double)acc;
+  }
+}
+constexpr int SMALL_ELEM = 16;  // n_ref up to which k_apply_elem_small is used
+
 // Matrix-free variant: y_T = sum_q g_q(T) R_q x_T for a tile of TC cells.
 // lane = cell of the tile, warps split the rows; R entries are warp-uniform
 // (broadcast loads), x_T and g_T live in shared memory.
@@ -2068,6 +2107,13 @@ __global__ void k_ht_gather(int64_t nrow, const int64_t* __restrict__ ptr, const
 // scal layout (per right-hand side, stride 16): see riesz.cu
 // ---------------------------------------------------------------------------
 constexpr int RED_BLOCKS = 608;  // 4 x 152 partials, reduced in a fixed order
+// Blocks of a two-stage reduction over n entries: 4 x 152 for large vectors, fewer for small ones
+// (about four entries per thread), so a short vector (a coarse problem) does not pay for thousands of
+// nearly empty blocks.  The partition, and with it the summation order, depends only on n.
+inline int red_blocks(int64_t n) {
+  const int64_t b = (n + 4 * NT - 1) / (4 * NT);
+  return (int)(b < 1 ? 1 : (b > RED_BLOCKS ? RED_BLOCKS : b));
+}
 
 // Scalar slots (per right-hand side, stride 16).
 // S_RZNEW holds (r, z) of a preconditioner step until k_update_p commits it to
@@ -2108,7 +2154,7 @@ __device__ __forceinline__ void scalar_op(int op, double s0, double s1, double* 
 
 // Two-stage deterministic reduction in one launch: every block stores its two
 // partial sums; the last block to finish (atomic ticket after a fence) adds
-// the RED_BLOCKS partials in a fixed order, applies the scalar step and resets
+// partials of the grid in a fixed order, applies the scalar step and resets
 // the ticket.  No block waits for another.
 __device__ __forceinline__ void reduce2_finish(double v0, double v1, double* __restrict__ part,
                                                unsigned* __restrict__ ticket, int op, double* __restrict__ scal) {
@@ -2141,7 +2187,7 @@ __device__ __forceinline__ void reduce2_finish(double v0, double v1, double* __r
   if (!last) return;
   __threadfence();
   double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < RED_BLOCKS; i += NT) {
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) {
     a += __ldcg(part + i);
     b += __ldcg(part + RED_BLOCKS + i);
   }
@@ -2172,7 +2218,7 @@ __global__ void __launch_bounds__(NT) k_dot2(int64_t n, const double* __restrict
   b += blockIdx.y * n;
   if (c) c += blockIdx.y * n;
   double v0 = 0.0, v1 = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * NT) {
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
     const double ai = a[i];
     v0 = fma(ai, b[i], v0);
     if (c) v1 = fma(ai, c[i], v1);
@@ -2192,7 +2238,7 @@ __global__ void __launch_bounds__(NT) k_update_xr(int64_t n, double* __restrict_
   Ap += o;
   const double alpha = scal[blockIdx.y * SCAL_STRIDE + S_ALPHA];
   double v0 = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * NT) {
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, Ap[i], r[i]);
     r[i] = ri;
@@ -2255,7 +2301,7 @@ __global__ void __launch_bounds__(NT) k_residual(int64_t n, const double* __rest
   if (Ax) Ax += o;
   r += o;
   double v0 = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * NT) {
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
     const double ri = Ax ? b[i] - Ax[i] : b[i];
     r[i] = ri;
     v0 = fma(ri, ri, v0);
@@ -2284,7 +2330,7 @@ __global__ void __launch_bounds__(NT) k_precond_gather_dot(int64_t N, int64_t ni
   z += o;
   if (zold) zold += o;
   double v0 = 0.0, v1 = 0.0;
-  for (int64_t d = blockIdx.x * (int64_t)NT + threadIdx.x; d < N; d += (int64_t)RED_BLOCKS * NT) {
+  for (int64_t d = blockIdx.x * (int64_t)NT + threadIdx.x; d < N; d += (int64_t)gridDim.x * NT) {
     double zi;
     if (d < nifd && dmask && dmask[d]) {
       zi = r[d];  // identity block of a Dirichlet DOF
@@ -2548,7 +2594,7 @@ __global__ void __launch_bounds__(NT) k_mr_dot(int64_t n, const double* __restri
                                               double* __restrict__ part, unsigned* __restrict__ ticket, int op,
                                               double* __restrict__ m) {
   double v = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)RED_BLOCKS * NT)
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT)
     v = fma(a[i], b[i], v);
   __shared__ double sh[NT / 32];
   __shared__ bool last;
@@ -2567,7 +2613,7 @@ __global__ void __launch_bounds__(NT) k_mr_dot(int64_t n, const double* __restri
   if (!last) return;
   __threadfence();
   double t = 0.0;
-  for (int i = threadIdx.x; i < RED_BLOCKS; i += NT) t += __ldcg(part + i);
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) t += __ldcg(part + i);
   t = warp_sum(t);
   __syncthreads();
   if (lane == 0) sh[warp] = t;

@@ -871,6 +871,9 @@ std::vector<int32_t> transpose_dofs(const std::vector<int32_t>& cd, int64_t C, i
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+// Blocks of 256 threads for the search-direction update: two per SM on large vectors, about four
+// entries per thread on short ones.
+inline unsigned update_blocks(int64_t n) { return (unsigned)std::min<int64_t>(296, std::max<int64_t>(1, (n + 1023) / 1024)); }
 
 // ---- operator pieces ------------------------------------------------------
 // y = A x for nrhs right-hand sides; fp32 selects the FP32 copy of the element
@@ -896,6 +899,18 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
                                                         h.d_cdofs.p, x, y, h.d_Ycell.p, nrhs, N, h.dmask(),
                                                         h.d_flags.p + 2);
     });
+  } else if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT && n <= dev::SMALL_ELEM) {
+    const unsigned grid = nblk((int64_t)nrhs * C, 256);
+    if (fp32)
+      launch(h, RIESZ_K_APPLY32, s, [&] {
+        dev::k_apply_elem_small<float, dev::SMALL_ELEM><<<grid, 256, 0, s>>>(C, n, h.nif, h.d_Ae32.p, h.d_cdofs.p, x,
+                                                                           y, h.d_Ycell.p, nrhs, N, h.dmask());
+      });
+    else
+      launch(h, RIESZ_K_APPLY, s, [&] {
+        dev::k_apply_elem_small<double, dev::SMALL_ELEM><<<grid, 256, 0, s>>>(C, n, h.nif, h.d_Ae.p, h.d_cdofs.p, x,
+                                                                            y, h.d_Ycell.p, nrhs, N, h.dmask());
+      });
   } else if (h.opts.apply_mode == RIESZ_APPLY_ELEMENT) {
     const int rows = (n % 2 == 0) ? n / 2 : n;
     // the rows loop strides by the block size; the multi-RHS variants hold up to 92 registers per
@@ -1229,7 +1244,7 @@ void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* z
   coarse_join(h, s);
   ht_join(h, s);
   launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
-    dev::k_precond_gather_dot<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(
+    dev::k_precond_gather_dot<<<dim3(dev::red_blocks(h.N()), nrhs), dev::NT, 0, s>>>(
         N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p, h.d_dinv.p, r, z, zold, h.d_part.p,
         h.d_ticket.p, op, scal, (int64_t)h.p_dofs.size(), h.coarse_on ? h.d_cidx.p : nullptr, h.d_zc.p, h.N0,
         h.dmask(), h.ht ? h.d_zg.p : nullptr);
@@ -1239,7 +1254,7 @@ void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* z
 void dot(riesz_handle& h, const double* a, const double* b, const double* c, int op, double* scal, int nrhs,
          cudaStream_t s) {
   launch(h, RIESZ_K_DOT, s, [&] {
-    dev::k_dot2<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(h.N(), a, b, c, h.d_part.p, h.d_ticket.p, op, scal);
+    dev::k_dot2<<<dim3(dev::red_blocks(h.N()), nrhs), dev::NT, 0, s>>>(h.N(), a, b, c, h.d_part.p, h.d_ticket.p, op, scal);
   });
 }
 
@@ -1401,7 +1416,7 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
   auto residual = [&](bool x_is_zero = false) {  // r = b - A x (FP64), RR
     if (!x_is_zero) op_apply(h, x, Ap, nrhs, s);
     launch(h, RIESZ_K_UPDATE, s, [&] {
-      dev::k_residual<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(N, b, x_is_zero ? nullptr : Ap, r, h.d_part.p,
+      dev::k_residual<<<dim3(dev::red_blocks(N), nrhs), dev::NT, 0, s>>>(N, b, x_is_zero ? nullptr : Ap, r, h.d_part.p,
                                                                       h.d_ticket.p, scal);
     });
   };
@@ -1447,7 +1462,7 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
       op_apply(h, p, Ap, nrhs, s, inner_prec(h));
       dot(h, p, Ap, nullptr, 0, scal, nrhs, s);
       launch(h, RIESZ_K_UPDATE, s, [&] {
-        dev::k_update_xr<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(N, scal, x, r, p, Ap, h.d_part.p,
+        dev::k_update_xr<<<dim3(dev::red_blocks(N), nrhs), dev::NT, 0, s>>>(N, scal, x, r, p, Ap, h.d_part.p,
                                                                           h.d_ticket.p);
       });
       ++it;
@@ -1491,7 +1506,7 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
         op_precond_dot(h, r, z, zold, 3, scal, nrhs, s);  // redo the step on the replaced residual
       }
       launch(h, RIESZ_K_UPDATE, s, [&] {
-        dev::k_update_p<<<dim3(296, nrhs), 256, 0, s>>>(N, scal, z, p, flex ? zold : nullptr);
+        dev::k_update_p<<<dim3(update_blocks(N), nrhs), 256, 0, s>>>(N, scal, z, p, flex ? zold : nullptr);
       });
     }
     if (status == RIESZ_ERR_NOT_CONVERGED) {
@@ -1533,7 +1548,7 @@ void iter_tail(riesz_handle& h, double* x, int nrhs, cudaStream_t s) {
   op_apply(h, h.d_p.p, h.d_Ap.p, nrhs, s, inner_prec(h));
   dot(h, h.d_p.p, h.d_Ap.p, nullptr, 0, h.d_scal.p, nrhs, s);
   launch(h, RIESZ_K_UPDATE, s, [&] {
-    dev::k_update_xr<<<dim3(dev::RED_BLOCKS, nrhs), dev::NT, 0, s>>>(N, h.d_scal.p, x, h.d_r.p, h.d_p.p, h.d_Ap.p,
+    dev::k_update_xr<<<dim3(dev::red_blocks(N), nrhs), dev::NT, 0, s>>>(N, h.d_scal.p, x, h.d_r.p, h.d_p.p, h.d_Ap.p,
                                                                       h.d_part.p, h.d_ticket.p);
   });
 }
@@ -1543,7 +1558,7 @@ void iter_head(riesz_handle& h, int nrhs, cudaStream_t s) {
   const bool flex = use_flex(h);
   op_precond_dot(h, h.d_r.p, h.d_z.p, flex ? h.d_zold.p : nullptr, flex ? 3 : 2, h.d_scal.p, nrhs, s);
   launch(h, RIESZ_K_UPDATE, s, [&] {
-    dev::k_update_p<<<dim3(296, nrhs), 256, 0, s>>>(h.N(), h.d_scal.p, h.d_z.p, h.d_p.p, flex ? h.d_zold.p : nullptr);
+    dev::k_update_p<<<dim3(update_blocks(h.N()), nrhs), 256, 0, s>>>(h.N(), h.d_scal.p, h.d_z.p, h.d_p.p, flex ? h.d_zold.p : nullptr);
   });
 }
 
@@ -1683,7 +1698,7 @@ void ls_residual(LoopSolve& L, cudaStream_t s, bool x_is_zero) {
   const int64_t N = h.N();
   if (!x_is_zero) op_apply(h, h.d_xw.p, h.d_Ap.p, L.nrhs, s);
   launch(h, RIESZ_K_UPDATE, s, [&] {
-    dev::k_residual<<<dim3(dev::RED_BLOCKS, L.nrhs), dev::NT, 0, s>>>(
+    dev::k_residual<<<dim3(dev::red_blocks(N), L.nrhs), dev::NT, 0, s>>>(
         N, L.b, x_is_zero ? nullptr : h.d_Ap.p, h.d_r.p, h.d_part.p, h.d_ticket.p, h.d_scal.p);
   });
 }
@@ -3395,7 +3410,7 @@ void hodge_precond(riesz_hodge& H, const double* r, double* z, cudaStream_t s) {
 }
 
 void hodge_dot(riesz_hodge& H, const double* a, const double* b, int op, cudaStream_t s) {
-  dev::k_mr_dot<<<dev::RED_BLOCKS, dev::NT, 0, s>>>(H.N(), a, b, H.d_part.p, H.d_ticket.p, op, H.d_m.p);
+  dev::k_mr_dot<<<dev::red_blocks(H.N()), dev::NT, 0, s>>>(H.N(), a, b, H.d_part.p, H.d_ticket.p, op, H.d_m.p);
   CK(cudaGetLastError());
   ++H.launches;
 }
