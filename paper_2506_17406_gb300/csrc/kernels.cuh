@@ -2226,6 +2226,42 @@ __global__ void __launch_bounds__(NT) k_dot2(int64_t n, const double* __restrict
   reduce2_finish(v0, v1, part, ticket, op, scal);
 }
 
+// k_gather_iface fused with the PCG reduction that follows every search-direction product:
+// one grid row per right-hand side walks all N rows in the partition of k_dot2, assembles the
+// interface rows (as k_gather_iface), reads the interior rows the cell kernel wrote, and
+// accumulates (x, y) -> scalar step op.  Same values and the same partial sums as the gather
+// followed by k_dot2, one launch fewer.
+__global__ void __launch_bounds__(NT) k_gather_iface_dot(int64_t nifd, const int64_t* __restrict__ ptr,
+                                                        const int32_t* __restrict__ pos,
+                                                        const double* __restrict__ Ycell, int64_t ystride,
+                                                        double* __restrict__ y, int64_t N,
+                                                        const uint8_t* __restrict__ dmask,
+                                                        const double* __restrict__ x, double* __restrict__ part,
+                                                        unsigned* __restrict__ ticket, int op,
+                                                        double* __restrict__ scal) {
+  const int r = blockIdx.y;
+  Ycell += r * ystride;
+  y += r * N;
+  x += r * N;
+  double v0 = 0.0;
+  for (int64_t d = blockIdx.x * (int64_t)NT + threadIdx.x; d < N; d += (int64_t)gridDim.x * NT) {
+    double yd;
+    if (d < nifd) {
+      if (dmask && dmask[d]) {
+        yd = x[d];
+      } else {
+        yd = 0.0;
+        for (int64_t k = ptr[d]; k < ptr[d + 1]; ++k) yd += Ycell[pos[k]];
+      }
+      y[d] = yd;
+    } else {
+      yd = y[d];
+    }
+    v0 = fma(x[d], yd, v0);
+  }
+  reduce2_finish(v0, 0.0, part, ticket, op, scal);
+}
+
 // x += alpha p ; r -= alpha Ap ; r.r -> RR
 __global__ void __launch_bounds__(NT) k_update_xr(int64_t n, double* __restrict__ scal, double* __restrict__ x,
                                                  double* __restrict__ r, const double* __restrict__ p,

@@ -878,7 +878,10 @@ inline unsigned update_blocks(int64_t n) { return (unsigned)std::min<int64_t>(29
 // ---- operator pieces ------------------------------------------------------
 // y = A x for nrhs right-hand sides; fp32 selects the FP32 copy of the element
 // matrices (inner applies of the mixed-precision solver).
-void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_t s, int prec = RIESZ_PREC_FP64) {
+// With scal non-null the interface gather is fused with the PCG reduction (x, y) -> scalar op
+// `op` (k_gather_iface_dot: the same values as the gather followed by dot()).
+void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_t s, int prec = RIESZ_PREC_FP64,
+              double* scal = nullptr, int op = 0) {
   const int n = h.mesh.nref;
   const int64_t C = h.C(), N = h.N();
   const bool fp32 = prec == RIESZ_PREC_FP32;
@@ -946,6 +949,14 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
     });
   }
   const int64_t nI = h.mesh.n_interface;
+  if (scal) {
+    launch(h, RIESZ_K_GATHER, s, [&] {
+      dev::k_gather_iface_dot<<<dim3(dev::red_blocks(N), nrhs), dev::NT, 0, s>>>(
+          nI, h.d_sc_ptr.p, h.d_sc_pos.p, h.d_Ycell.p, (int64_t)h.nif * C, y, N, h.dmask(), x, h.d_part.p,
+          h.d_ticket.p, op, scal);
+    });
+    return;
+  }
   launch(h, RIESZ_K_GATHER, s, [&] {
     dev::k_gather_iface<<<nblk(nI, 256), 256, 0, s>>>(nI, h.d_sc_ptr.p, h.d_sc_pos.p, h.d_Ycell.p, (int64_t)h.nif * C, y,
                                                      N, nrhs, h.dmask(), x);
@@ -1459,8 +1470,7 @@ int pcg_batch(riesz_handle& h, const double* b, double* x, int nrhs, cudaStream_
   } else {
     restart();
     while (it < h.opts.maxit) {
-      op_apply(h, p, Ap, nrhs, s, inner_prec(h));
-      dot(h, p, Ap, nullptr, 0, scal, nrhs, s);
+      op_apply(h, p, Ap, nrhs, s, inner_prec(h), scal, 0);  // and (p, Ap) -> alpha
       launch(h, RIESZ_K_UPDATE, s, [&] {
         dev::k_update_xr<<<dim3(dev::red_blocks(N), nrhs), dev::NT, 0, s>>>(N, scal, x, r, p, Ap, h.d_part.p,
                                                                           h.d_ticket.p);
@@ -1545,8 +1555,7 @@ bool profiling_loop(const riesz_handle& h) { return h.prof && (h.prof_mask & LOO
 // Ap = A p; (p, Ap) -> alpha; x += alpha p, r -= alpha Ap; (r, r) -> RR
 void iter_tail(riesz_handle& h, double* x, int nrhs, cudaStream_t s) {
   const int64_t N = h.N();
-  op_apply(h, h.d_p.p, h.d_Ap.p, nrhs, s, inner_prec(h));
-  dot(h, h.d_p.p, h.d_Ap.p, nullptr, 0, h.d_scal.p, nrhs, s);
+  op_apply(h, h.d_p.p, h.d_Ap.p, nrhs, s, inner_prec(h), h.d_scal.p, 0);  // and (p, Ap) -> alpha
   launch(h, RIESZ_K_UPDATE, s, [&] {
     dev::k_update_xr<<<dim3(dev::red_blocks(N), nrhs), dev::NT, 0, s>>>(N, h.d_scal.p, x, h.d_r.p, h.d_p.p, h.d_Ap.p,
                                                                       h.d_part.p, h.d_ticket.p);
