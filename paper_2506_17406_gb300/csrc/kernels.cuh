@@ -104,38 +104,73 @@ __global__ void k_geom(int space, int64_t C, const double* __restrict__ verts, c
 // FP64 work of forming every entry.  A CTA forms ELEM_CELLS cells at once, so every R_q entry it reads
 // from L2 serves all of them (one cell per CTA read 8 B per FMA, more than L2 sustains at the FP64 rate).
 constexpr int ELEM_CELLS = 4;  // cells per CTA of k_elem_matrices: each R_q entry read once for all of them
+// A_T = sum_q g_q(T) R_q for ELEM_CELLS cells per CTA, in 32x32 tiles (I, J), I <= J: warp w holds
+// rows w, w + 8, w + 16, w + 24 of the tile and lane = column, four cells at once.  The upper
+// triangle (j >= i) is stored as computed, row-contiguous; the strictly lower triangle is the
+// mirror of the upper one, staged through shared memory so that its stores are row-contiguous
+// too.  Same FMA order over q as a plain per-entry sum.
 template <int Q>
 __global__ void __launch_bounds__(256) k_elem_matrices(int64_t C, int n, const double* __restrict__ g,
                                                       const double* __restrict__ R, double* __restrict__ Ae) {
+  __shared__ double gs[Q][ELEM_CELLS];
+  __shared__ double T[ELEM_CELLS][32][33];
   const int64_t c0 = (int64_t)blockIdx.x * ELEM_CELLS;
   const int nc = (int)min((int64_t)ELEM_CELLS, C - c0);
   const int64_t nn = (int64_t)n * n;
-  double gq[ELEM_CELLS][Q];
+  for (int t = threadIdx.x; t < Q * ELEM_CELLS; t += blockDim.x) {
+    const int q = t / ELEM_CELLS, e = t % ELEM_CELLS;
+    gs[q][e] = e < nc ? g[q * C + c0 + e] : 0.0;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+  const int nt = (n + 31) >> 5;
+  for (int I = 0; I < nt; ++I)
+    for (int J = I; J < nt; ++J) {
+      const int j = J * 32 + tx;
+      double s[4][ELEM_CELLS];
 #pragma unroll
-  for (int e = 0; e < ELEM_CELLS; ++e)
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int q = 0; q < Q; ++q) gq[e][q] = e < nc ? g[q * C + c0 + e] : 0.0;
-  for (int i = 0; i < n; ++i) {
-    for (int j = i + threadIdx.x; j < n; j += blockDim.x) {
-      const int64_t t = (int64_t)i * n + j;
-      double s[ELEM_CELLS];
-#pragma unroll
-      for (int e = 0; e < ELEM_CELLS; ++e) s[e] = 0.0;
+        for (int e = 0; e < ELEM_CELLS; ++e) s[u][e] = 0.0;
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        const double r = R[q * nn + t];
+        double rv[4];
 #pragma unroll
-        for (int e = 0; e < ELEM_CELLS; ++e) s[e] += gq[e][q] * r;
+        for (int u = 0; u < 4; ++u) {
+          const int i = I * 32 + ty + 8 * u;
+          rv[u] = (i < n && j < n) ? R[q * nn + (int64_t)i * n + j] : 0.0;
+        }
+#pragma unroll
+        for (int e = 0; e < ELEM_CELLS; ++e) {
+          const double gv = gs[q][e];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) s[u][e] = fma(gv, rv[u], s[u][e]);
+        }
       }
 #pragma unroll
-      for (int e = 0; e < ELEM_CELLS; ++e) {
-        if (e >= nc) break;
-        double* A = Ae + (c0 + e) * nn;
-        A[t] = s[e];
-        if (j != i) A[(int64_t)j * n + i] = s[e];
+      for (int u = 0; u < 4; ++u) {
+        const int i = I * 32 + ty + 8 * u;
+        if (i < n && j < n && j >= i)
+#pragma unroll
+          for (int e = 0; e < ELEM_CELLS; ++e)
+            if (e < nc) Ae[(c0 + e) * nn + (int64_t)i * n + j] = s[u][e];
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int e = 0; e < ELEM_CELLS; ++e) T[e][ty + 8 * u][tx] = s[u][e];
+      __syncthreads();
+      // mirror: entry (jr, ic) with jr > ic is the computed entry (ic, jr) = T[e][ic - 32 I][jr - 32 J]
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int jr = J * 32 + ty + 8 * u, ic = I * 32 + tx;
+        if (jr < n && ic < n && jr > ic)
+#pragma unroll
+          for (int e = 0; e < ELEM_CELLS; ++e)
+            if (e < nc) Ae[(c0 + e) * nn + (int64_t)jr * n + ic] = T[e][tx][ty + 8 * u];
+      }
+      __syncthreads();
     }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1133,6 +1168,32 @@ __global__ void __launch_bounds__(SWEEP_NT) k_patch_sweep8(const int32_t* __rest
 }
 
 // FP64 factor tiles to FP32, each 32x32 tile transposed (the forward sweep of k_patch_sweep8)
+// FP32 copies of tile-packed FP64 factors in one pass over them: b = (float)a, and, when bt is
+// non-null, bt = every 32x32 tile transposed.  One warp per tile: coalesced row loads, the tile
+// staged in shared memory (rows padded to 33) so that the transposed stores are coalesced too.
+__global__ void __launch_bounds__(256) k_to_f32_tiles(int64_t ntiles, const double* __restrict__ a,
+                                                      float* __restrict__ b, float* __restrict__ bt) {
+  __shared__ float ts[8][32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t t = (int64_t)blockIdx.x * 8 + warp; t < ntiles; t += (int64_t)gridDim.x * 8) {
+    const double* at = a + (t << 10);
+    float* bo = b + (t << 10);
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+      const float v = (float)at[r * 32 + lane];
+      bo[r * 32 + lane] = v;
+      ts[warp][r][lane] = v;
+    }
+    __syncwarp();
+    if (bt) {
+      float* to = bt + (t << 10);
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c) to[c * 32 + lane] = ts[warp][lane][c];
+    }
+    __syncwarp();
+  }
+}
+
 __global__ void k_to_f32_tiles_t(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t t = e >> 10;

@@ -2099,7 +2099,15 @@ void device_compute_pre(riesz_handle& h, cudaStream_t s, bool aux_now) {
 void device_compute_post(riesz_handle& h, cudaStream_t s, bool aux_now) {
   const int npatch = (int)h.p_n.size();
   if (npatch) {
-    if (h.opts.precond_precision == RIESZ_PREC_FP32) {
+    if (h.opts.precond_precision == RIESZ_PREC_FP32 && h.factor_entries % 1024 == 0 &&
+        h.dinv_entries % 1024 == 0) {  // whole tiles: one pass per factor array
+      launch(h, RIESZ_K_TO_F32, s, [&] {
+        dev::k_to_f32_tiles<<<1184, 256, 0, s>>>(h.factor_entries >> 10, h.d_L64.p, h.d_L32.p, h.d_L32T.p);
+      });
+      launch(h, RIESZ_K_TO_F32, s, [&] {
+        dev::k_to_f32_tiles<<<296, 256, 0, s>>>(h.dinv_entries >> 10, h.d_D64.p, h.d_D32.p, h.d_D32T.p);
+      });
+    } else if (h.opts.precond_precision == RIESZ_PREC_FP32) {
       launch(h, RIESZ_K_TO_F32, s, [&] {
         dev::k_to_f32<<<1184, 256, 0, s>>>(h.factor_entries, h.d_L64.p, h.d_L32.p);
       });
