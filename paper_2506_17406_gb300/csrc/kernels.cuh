@@ -2217,12 +2217,13 @@ __device__ __forceinline__ void scalar_op(int op, double s0, double s1, double* 
 // partial sums; the last block to finish (atomic ticket after a fence) adds
 // partials of the grid in a fixed order, applies the scalar step and resets
 // the ticket.  No block waits for another.
-__device__ __forceinline__ void reduce2_finish(double v0, double v1, double* __restrict__ part,
-                                               unsigned* __restrict__ ticket, int op, double* __restrict__ scal) {
-  // one grid row per right-hand side
-  part += (int64_t)blockIdx.y * 2 * RED_BLOCKS;
-  ticket += blockIdx.y;
-  scal += blockIdx.y * SCAL_STRIDE;
+// rhs: the right-hand side of this block; bi, nb: its partial's index and the number of partials
+__device__ __forceinline__ void reduce2_finish_at(double v0, double v1, double* __restrict__ part,
+                                                  unsigned* __restrict__ ticket, int op, double* __restrict__ scal,
+                                                  int rhs, int bi, int nb) {
+  part += (int64_t)rhs * 2 * RED_BLOCKS;
+  ticket += rhs;
+  scal += rhs * SCAL_STRIDE;
   __shared__ double sh[2][NT / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -2239,16 +2240,16 @@ __device__ __forceinline__ void reduce2_finish(double v0, double v1, double* __r
       a += sh[0][w];
       b += sh[1][w];
     }
-    part[blockIdx.x] = a;
-    part[RED_BLOCKS + blockIdx.x] = b;
+    part[bi] = a;
+    part[RED_BLOCKS + bi] = b;
     __threadfence();
-    last = (atomicAdd(ticket, 1u) == (unsigned)(gridDim.x - 1));
+    last = (atomicAdd(ticket, 1u) == (unsigned)(nb - 1));
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) {
+  for (int i = threadIdx.x; i < nb; i += NT) {
     a += __ldcg(part + i);
     b += __ldcg(part + RED_BLOCKS + i);
   }
@@ -2271,6 +2272,12 @@ __device__ __forceinline__ void reduce2_finish(double v0, double v1, double* __r
   }
 }
 
+// one grid row per right-hand side: blockIdx.y = right-hand side, blockIdx.x = partial
+__device__ __forceinline__ void reduce2_finish(double v0, double v1, double* __restrict__ part,
+                                               unsigned* __restrict__ ticket, int op, double* __restrict__ scal) {
+  reduce2_finish_at(v0, v1, part, ticket, op, scal, (int)blockIdx.y, (int)blockIdx.x, (int)gridDim.x);
+}
+
 // a.b (and a.c when c != nullptr) followed by the scalar step op
 __global__ void __launch_bounds__(NT) k_dot2(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
                                             const double* __restrict__ c, double* __restrict__ part,
@@ -2288,10 +2295,12 @@ __global__ void __launch_bounds__(NT) k_dot2(int64_t n, const double* __restrict
 }
 
 // k_gather_iface fused with the PCG reduction that follows every search-direction product:
-// one grid row per right-hand side walks all N rows in the partition of k_dot2, assembles the
-// interface rows (as k_gather_iface), reads the interior rows the cell kernel wrote, and
-// accumulates (x, y) -> scalar step op.  Same values and the same partial sums as the gather
-// followed by k_dot2, one launch fewer.
+// for each right-hand side the blocks walk all N rows in the partition of k_dot2, assemble the
+// interface rows (as k_gather_iface), read the interior rows the cell kernel wrote, and
+// accumulate (x, y) -> scalar step op.  Same values and the same partial sums as the gather
+// followed by k_dot2, one launch fewer.  The grid is (right-hand side, partial): the blocks of all
+// right-hand sides for one range of rows are adjacent in launch order, so the gather's index
+// lists are fetched from DRAM once and served from L2 to the other right-hand sides.
 __global__ void __launch_bounds__(NT) k_gather_iface_dot(int64_t nifd, const int64_t* __restrict__ ptr,
                                                         const int32_t* __restrict__ pos,
                                                         const double* __restrict__ Ycell, int64_t ystride,
@@ -2300,12 +2309,12 @@ __global__ void __launch_bounds__(NT) k_gather_iface_dot(int64_t nifd, const int
                                                         const double* __restrict__ x, double* __restrict__ part,
                                                         unsigned* __restrict__ ticket, int op,
                                                         double* __restrict__ scal) {
-  const int r = blockIdx.y;
+  const int r = blockIdx.x;  // right-hand side fastest: the right-hand sides of one row range run together
   Ycell += r * ystride;
   y += r * N;
   x += r * N;
   double v0 = 0.0;
-  for (int64_t d = blockIdx.x * (int64_t)NT + threadIdx.x; d < N; d += (int64_t)gridDim.x * NT) {
+  for (int64_t d = blockIdx.y * (int64_t)NT + threadIdx.x; d < N; d += (int64_t)gridDim.y * NT) {
     double yd;
     if (d < nifd) {
       if (dmask && dmask[d]) {
@@ -2320,7 +2329,7 @@ __global__ void __launch_bounds__(NT) k_gather_iface_dot(int64_t nifd, const int
     }
     v0 = fma(x[d], yd, v0);
   }
-  reduce2_finish(v0, 0.0, part, ticket, op, scal);
+  reduce2_finish_at(v0, 0.0, part, ticket, op, scal, r, (int)blockIdx.y, (int)gridDim.y);
 }
 
 // x += alpha p ; r -= alpha Ap ; r.r -> RR
@@ -2406,9 +2415,10 @@ __global__ void __launch_bounds__(NT) k_residual(int64_t n, const double* __rest
   reduce2_finish(v0, 0.0, part, ticket, 7, scal);
 }
 
-// Preconditioner gather fused with the next PCG reduction (one grid row per
-// right-hand side): z = Jacobi / patch sum as k_precond_gather, then r.z (and
-// r.zold for the flexible variant) -> scalar step op.
+// Preconditioner gather fused with the next PCG reduction (grid: right-hand
+// side, partial, as k_gather_iface_dot): z = Jacobi / patch sum as
+// k_precond_gather, then r.z (and r.zold for the flexible variant) -> scalar
+// step op.
 __global__ void __launch_bounds__(NT) k_precond_gather_dot(int64_t N, int64_t nifd, const int64_t* __restrict__ ptr,
                                                           const int32_t* __restrict__ pos,
                                                           const double* __restrict__ zpatch,
@@ -2421,21 +2431,22 @@ __global__ void __launch_bounds__(NT) k_precond_gather_dot(int64_t N, int64_t ni
                                                           const double* __restrict__ zc, int64_t n0,
                                                           const uint8_t* __restrict__ dmask,
                                                           const double* __restrict__ zg) {
-  const int64_t o = blockIdx.y * N;
-  zpatch += blockIdx.y * zstride;
+  const int rh = blockIdx.x;  // right-hand side fastest (see k_gather_iface_dot)
+  const int64_t o = rh * N;
+  zpatch += rh * zstride;
   r += o;
   z += o;
   if (zold) zold += o;
   double v0 = 0.0, v1 = 0.0;
-  for (int64_t d = blockIdx.x * (int64_t)NT + threadIdx.x; d < N; d += (int64_t)gridDim.x * NT) {
+  for (int64_t d = blockIdx.y * (int64_t)NT + threadIdx.x; d < N; d += (int64_t)gridDim.y * NT) {
     double zi;
     if (d < nifd && dmask && dmask[d]) {
       zi = r[d];  // identity block of a Dirichlet DOF
     } else if (d < nifd) {
       zi = 0.0;
       for (int64_t k = ptr[d]; k < ptr[d + 1]; ++k) zi += zpatch[pos[k]];
-      if (cidx && cidx[d] >= 0) zi += zc[blockIdx.y * n0 + cidx[d]];
-      if (zg) zi += zg[blockIdx.y * nifd + d];
+      if (cidx && cidx[d] >= 0) zi += zc[rh * n0 + cidx[d]];
+      if (zg) zi += zg[rh * nifd + d];
     } else {
       zi = dinv[d - nifd] * r[d];
     }
@@ -2444,7 +2455,7 @@ __global__ void __launch_bounds__(NT) k_precond_gather_dot(int64_t N, int64_t ni
     v0 = fma(ri, zi, v0);
     if (zold) v1 = fma(ri, zold[d], v1);
   }
-  reduce2_finish(v0, v1, part, ticket, op, scal);
+  reduce2_finish_at(v0, v1, part, ticket, op, scal, rh, (int)blockIdx.y, (int)gridDim.y);
 }
 
 // ---------------------------------------------------------------------------

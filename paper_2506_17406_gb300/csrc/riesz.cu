@@ -951,7 +951,7 @@ void op_apply(riesz_handle& h, const double* x, double* y, int nrhs, cudaStream_
   const int64_t nI = h.mesh.n_interface;
   if (scal) {
     launch(h, RIESZ_K_GATHER, s, [&] {
-      dev::k_gather_iface_dot<<<dim3(dev::red_blocks(N), nrhs), dev::NT, 0, s>>>(
+      dev::k_gather_iface_dot<<<dim3(nrhs, dev::red_blocks(N)), dev::NT, 0, s>>>(
           nI, h.d_sc_ptr.p, h.d_sc_pos.p, h.d_Ycell.p, (int64_t)h.nif * C, y, N, h.dmask(), x, h.d_part.p,
           h.d_ticket.p, op, scal);
     });
@@ -1255,7 +1255,7 @@ void op_precond_dot(riesz_handle& h, const double* r, double* z, const double* z
   coarse_join(h, s);
   ht_join(h, s);
   launch(h, RIESZ_K_PRECOND_GATHER, s, [&] {
-    dev::k_precond_gather_dot<<<dim3(dev::red_blocks(h.N()), nrhs), dev::NT, 0, s>>>(
+    dev::k_precond_gather_dot<<<dim3(nrhs, dev::red_blocks(h.N())), dev::NT, 0, s>>>(
         N, h.mesh.n_interface, h.d_pz_ptr.p, h.d_pz_pos.p, h.d_zpatch.p, h.d_dinv.p, r, z, zold, h.d_part.p,
         h.d_ticket.p, op, scal, (int64_t)h.p_dofs.size(), h.coarse_on ? h.d_cidx.p : nullptr, h.d_zc.p, h.N0,
         h.dmask(), h.ht ? h.d_zg.p : nullptr);
