@@ -99,6 +99,30 @@ class Server:
         self.in_use = 0
         self.active = 0
 
+    def warm(self, spaces, degrees, threads=4):
+        """Build the host reference elements of every (space, degree) pair before serving, as a
+        server does at start-up: one host-only handle per pair on a single cube with this server's
+        options, so the auxiliary spaces its decompositions use (the potentials' CG space, the
+        lowest-order coarse space) are built as well.  The tables depend on neither the mesh nor the
+        precisions and are cached process-wide, so a request then pays only its own mesh maps.
+        Returns {(space, degree): host milliseconds of its handle}."""
+        from concurrent.futures import ThreadPoolExecutor
+        verts, cells = kuhn_mesh(1)
+
+        def one(pair):
+            space, p = pair
+            opts = dict(precond_precision=self.prec, apply_precision=self.aprec, autotune=0)
+            if self.recommended:
+                opts["decomposition"] = RECOMMENDED[space]
+            h = rz.Riesz(space, p, verts, cells, device=False, **opts)
+            ms = float(h.stats()["setup_host_ms"])
+            h.close()
+            return ms
+
+        pairs = [(space, p) for space in spaces for p in degrees]
+        with ThreadPoolExecutor(max(1, threads)) as ex:
+            return dict(zip(pairs, ex.map(one, pairs)))
+
     def _prepare(self, req):
         verts, cells = kuhn_mesh(req.n, req.amp, req.seed % 1000)
         # no setup-time autotuning: its timing runs would add latency and compete with the other requests
