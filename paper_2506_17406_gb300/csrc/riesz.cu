@@ -368,9 +368,23 @@ dev::Mat3 ref_edge_inverse() {
 // A_V; only nonzero tiles are stored, in block-row order.
 // Plan one patch: its DOFs pd[0..np) (ascending interface DOFs) and the cells
 // of its star (cells whose interface DOFs may touch it); `center` is a point
-// of the star (the Fiedler ordering uses coordinates relative to it).
-void plan_patch(riesz_handle& h, const int32_t* pd, int np, const int32_t* star, int64_t nstar, const double* center,
-                int64_t& foff, int64_t& dioff) {
+// of the star (the Fiedler ordering uses coordinates relative to it).  The plan
+// depends on the patch alone (build_plans computes the plans of many patches at
+// once on host threads), and append_patch adds it to the handle in patch order.
+struct PatchPlan {
+  int np = 0, nb = 0, nt = 0;
+  std::vector<int32_t> dofs;           // the patch DOFs in factor order
+  std::vector<int32_t> meta;           // [nb][nb] tile index (-1: zero tile), then the column of every tile
+  std::vector<int32_t> cells;          // star cells holding patch DOFs
+  std::vector<int64_t> cell_end;       // end of each cell's entries in ent
+  std::vector<int32_t> ent;            // (local DOF j) | (factor position << 10) per (cell, patch DOF)
+  int64_t tile_ops = 0;
+  std::vector<double> col_flops;       // flops of each block column of the factorisation
+};
+
+PatchPlan plan_patch(const riesz_handle& h, const int32_t* pd, int np, const int32_t* star, int64_t nstar,
+                     const double* center) {
+  PatchPlan P;
   const MeshMaps& M = h.mesh;
   const int n = M.nref;
   // entities: contiguous runs of the sorted patch DOF list with the same entity
@@ -492,43 +506,63 @@ void plan_patch(riesz_handle& h, const int32_t* pd, int np, const int32_t* star,
           for (int J = c0; J <= c1; ++J) nz[(size_t)std::max(I, J) * nb + std::min(I, J)] = 1;
       }
   std::vector<int> col;
+  P.col_flops.reserve(nb);
   for (int K = 0; K < nb; ++K) {
     col.clear();
     for (int I = K + 1; I < nb; ++I)
       if (nz[(size_t)I * nb + K]) col.push_back(I);
-    h.tile_ops += 1 + (int64_t)col.size() + (int64_t)col.size() * (col.size() + 1) / 2;
+    P.tile_ops += 1 + (int64_t)col.size() + (int64_t)col.size() * (col.size() + 1) / 2;
     // diagonal factor (n^3/3) + its inverse (n^3/3), panel (triangular, 32*528 FMA per tile),
     // trailing tile products (32^3 FMA each)
-    h.chol_flops += 2.0 * 32768.0 / 3.0 + 2.0 * 16896.0 * col.size() + 65536.0 * (col.size() * (col.size() + 1) / 2);
+    P.col_flops.push_back(2.0 * 32768.0 / 3.0 + 2.0 * 16896.0 * col.size() +
+                          65536.0 * (col.size() * (col.size() + 1) / 2));
     for (size_t a = 0; a < col.size(); ++a)
       for (size_t bb = 0; bb <= a; ++bb) nz[(size_t)col[a] * nb + col[bb]] = 1;
   }
-  const int64_t moff = (int64_t)h.p_meta.size();
-  h.p_meta.resize(moff + (size_t)nb * nb, -1);
+  P.meta.assign((size_t)nb * nb, -1);
   int32_t nt = 0;
   std::vector<int32_t> tcol;
   for (int I = 0; I < nb; ++I)
     for (int J = 0; J <= I; ++J)
       if (nz[(size_t)I * nb + J]) {
-        h.p_meta[moff + (size_t)I * nb + J] = nt++;
+        P.meta[(size_t)I * nb + J] = nt++;
         tcol.push_back(J);
       }
-  h.p_meta.insert(h.p_meta.end(), tcol.begin(), tcol.end());
-  // record the patch
-  h.p_n.push_back(np);
+  P.meta.insert(P.meta.end(), tcol.begin(), tcol.end());
+  P.np = np;
+  P.nb = nb;
+  P.nt = nt;
+  P.dofs = std::move(dofs_new);
+  for (size_t ci = 0; ci < cell_ids.size(); ++ci) {
+    for (const auto& jk : cell_locs[ci]) P.ent.push_back(jk.first | (int32_t)(newpos[jk.second] << 10));
+    P.cells.push_back(cell_ids[ci]);
+    P.cell_end.push_back((int64_t)P.ent.size());
+  }
+  return P;
+}
+
+// Add a patch plan to the handle: offsets of its factor tiles, inverted diagonal tiles, tile
+// map and DOFs, and its cell contributions for the assembly.
+void append_patch(riesz_handle& h, const PatchPlan& P, int64_t& foff, int64_t& dioff) {
+  const int64_t moff = (int64_t)h.p_meta.size();
+  h.p_meta.insert(h.p_meta.end(), P.meta.begin(), P.meta.end());
+  h.p_n.push_back(P.np);
   h.p_doff.push_back((int64_t)h.p_dofs.size());
   h.p_foff.push_back(foff);
   h.p_dioff.push_back(dioff);
   h.p_moff.push_back(moff);
-  foff += (int64_t)nt * 1024;
-  dioff += (int64_t)nb * 1024;
-  h.p_dofs.insert(h.p_dofs.end(), dofs_new.begin(), dofs_new.end());
-  for (size_t ci = 0; ci < cell_ids.size(); ++ci) {
-    for (const auto& jk : cell_locs[ci]) h.pb_ent.push_back(jk.first | (int32_t)(newpos[jk.second] << 10));
-    h.pb_cell.push_back(cell_ids[ci]);
-    h.pb_off.push_back((int64_t)h.pb_ent.size());
+  foff += (int64_t)P.nt * 1024;
+  dioff += (int64_t)P.nb * 1024;
+  h.p_dofs.insert(h.p_dofs.end(), P.dofs.begin(), P.dofs.end());
+  const int64_t e0 = (int64_t)h.pb_ent.size();
+  h.pb_ent.insert(h.pb_ent.end(), P.ent.begin(), P.ent.end());
+  for (size_t ci = 0; ci < P.cells.size(); ++ci) {
+    h.pb_cell.push_back(P.cells[ci]);
+    h.pb_off.push_back(e0 + P.cell_end[ci]);
   }
   h.pb_ptr.push_back((int64_t)h.pb_cell.size());
+  h.tile_ops += P.tile_ops;
+  for (double f : P.col_flops) h.chol_flops += f;
 }
 
 // Index of the sorted edge (a, b), a < b, in the lexicographic edge list.
@@ -814,6 +848,8 @@ void build_plans(riesz_handle& h) {
   h.tile_ops = 0;
   h.chol_flops = 0.0;
   int64_t foff = 0, dioff = 0;
+  // the patches in launch order (largest first): edges for edge stars, vertices for vertex stars
+  std::vector<int64_t> ids;
   if (h.edge_star) {  // edge stars instead of vertex stars
     std::vector<int64_t> eorder(h.es_ptr.size() - 1);
     for (size_t e = 0; e < eorder.size(); ++e) eorder[e] = (int64_t)e;
@@ -821,9 +857,23 @@ void build_plans(riesz_handle& h) {
       return (h.es_ptr[a + 1] - h.es_ptr[a]) > (h.es_ptr[b + 1] - h.es_ptr[b]);
     });
     for (int64_t e : eorder) {
-      const int np = (int)(h.es_ptr[e + 1] - h.es_ptr[e]);
+      const int64_t np = h.es_ptr[e + 1] - h.es_ptr[e];
       if (np == 0) continue;
       if (np > 32 * dev::MAXNB) throw Err(RIESZ_ERR_INVALID_ARG, "patch larger than 4096 DOFs");
+      ids.push_back(e);
+    }
+  } else if (!h.apply_only) {
+    for (int64_t v : order) {
+      const int64_t np = M.patch_ptr[v + 1] - M.patch_ptr[v];
+      if (np == 0) continue;
+      if (np > 32 * dev::MAXNB) throw Err(RIESZ_ERR_INVALID_ARG, "patch larger than 4096 DOFs");
+      ids.push_back(v);
+    }
+  }
+  auto plan_of = [&](int64_t id) {
+    if (h.edge_star) {
+      const int64_t e = id;
+      const int np = (int)(h.es_ptr[e + 1] - h.es_ptr[e]);
       const int32_t a = M.edges[e * 2], b = M.edges[e * 2 + 1];
       std::vector<int32_t> cells;  // cells containing both endpoints
       for (int64_t k = M.star_ptr[a]; k < M.star_ptr[a + 1]; ++k) {
@@ -836,17 +886,22 @@ void build_plans(riesz_handle& h) {
       }
       double center[3];
       for (int q = 0; q < 3; ++q) center[q] = 0.5 * (h.verts[(size_t)a * 3 + q] + h.verts[(size_t)b * 3 + q]);
-      plan_patch(h, &h.es_dofs[h.es_ptr[e]], np, cells.data(), (int64_t)cells.size(), center, foff, dioff);
+      return plan_patch(h, &h.es_dofs[h.es_ptr[e]], np, cells.data(), (int64_t)cells.size(), center);
     }
-  } else if (!h.apply_only) {
-    for (int64_t v : order) {
-      const int64_t b = M.patch_ptr[v], e = M.patch_ptr[v + 1];
-      const int np = (int)(e - b);
-      if (np == 0) continue;
-      if (np > 32 * dev::MAXNB) throw Err(RIESZ_ERR_INVALID_ARG, "patch larger than 4096 DOFs");
-      plan_patch(h, &M.patch_dofs[b], np, &M.star_cells[M.star_ptr[v]], M.star_ptr[v + 1] - M.star_ptr[v],
-                 &h.verts[(size_t)v * 3], foff, dioff);
-    }
+    const int64_t v = id, b = M.patch_ptr[v];
+    const int np = (int)(M.patch_ptr[v + 1] - b);
+    return plan_patch(h, &M.patch_dofs[b], np, &M.star_cells[M.star_ptr[v]], M.star_ptr[v + 1] - M.star_ptr[v],
+                      &h.verts[(size_t)v * 3]);
+  };
+  // plans of a chunk of patches on the host threads, then appended in launch order: the same handle
+  // as planning them one after the other, with bounded memory for the plans in flight
+  constexpr int64_t CHUNK = 4096;
+  std::vector<PatchPlan> plans;
+  for (int64_t c0 = 0; c0 < (int64_t)ids.size(); c0 += CHUNK) {
+    const int cn = (int)std::min<int64_t>(CHUNK, (int64_t)ids.size() - c0);
+    plans.assign(cn, PatchPlan());
+    parallel_for(cn, [&](int i) { plans[i] = plan_of(ids[c0 + i]); });
+    for (const PatchPlan& P : plans) append_patch(h, P, foff, dioff);
   }
   h.factor_entries = foff;
   h.dinv_entries = dioff;
